@@ -1,0 +1,288 @@
+"""FP64 reference of the RIOT inner loop and its incremental 4D-Var setting.
+
+Test infrastructure: a plain, slow, dense restatement of the method that the
+GPU library is checked against.  Citations are to the paper's sections,
+equations and algorithms (Bousserez, Guerrette & Henze, arXiv:1906.01413).
+
+Notation (Section 2.1 and Algorithm 3):
+  x        model initial state (the control of Lorenz-96 4D-Var)
+  L        prior square root, B = L L^T (Eq. 3), dx = L dv
+  d        innovation d = H(x) - y           (Algorithm 3 sign; Eq. 3 uses y - H(x))
+  A        prior-preconditioned Hessian A = L^T H^T R^-1 H L (Eq. 4)
+  b        b = L^T H^T R^-1 d; the increment acts on g = b + v (Algorithm 3)
+  Omega    Gaussian sketch, Y = A Omega, Q = orth(Y), K Q^T Omega = Q^T Y,
+           K = Z Lambda Z^T, U = Q Z                           (Algorithm 3)
+  LRA/LRU  increment and covariance forms of Eqs. 8-10, chosen by the
+           smallest retained eigenvalue (Algorithm 3: lambda_m > 1 -> LRA)
+
+Readings where the paper is ambiguous (each is also listed in the design notes):
+  * Eqs. 8/9 print L^T(...)L; with B = L L^T the posterior covariance is
+    L(...)L^T, which is what is computed here.
+  * The LRA/LRU switch follows Algorithm 3 (strict lambda_m > 1), not the
+    ">= 1" of Eq. 11; lambda are eigenvalues of A (not I + A).
+  * K solves K (Q^T W) = Q^T Y by an LU solve with pivoting and is then
+    symmetrised, K <- (K + K^T)/2.  With power iterations, W is the last
+    block fed to the Hessian (Halko et al. subspace iteration, Section 2.2
+    mentions randomized power iteration as a remedy for flat spectra).
+  * Eigenpairs are sorted by decreasing eigenvalue (Eq. 8 "decreasing
+    eigenvalue order"), and each eigenvector's sign is fixed so that its
+    largest-magnitude component is positive.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import l96
+
+
+@dataclass
+class L96Problem:
+    """One Lorenz-96 assimilation window (Section 3.1)."""
+    n: int
+    T: int
+    dt: float
+    F: float
+    obs_step: np.ndarray     # (p,) int, step of each observation, 0..T
+    obs_idx: np.ndarray      # (p,) int, observed variable
+    y: np.ndarray            # (p,) observed values
+    sigma_o: np.ndarray      # (p,) observation error standard deviations
+    L: np.ndarray            # (n, n) prior square root
+    x_b: np.ndarray          # (n,) background
+
+    @property
+    def p(self):
+        return self.obs_idx.size
+
+    @property
+    def rinv(self):
+        return 1.0 / (self.sigma_o * self.sigma_o)
+
+
+# --- model pieces ---------------------------------------------------------------
+
+def trajectory(prob, x):
+    """Integrate and store the trajectory H(x) (Algorithm 3, outer loop)."""
+    return l96.nl(x, prob.T, prob.dt, prob.F)
+
+
+def observe(prob, states):
+    """Observation operator: state (T+1, n) -> values at (obs_step, obs_idx)."""
+    return states[prob.obs_step, prob.obs_idx]
+
+
+def innovation(prob, traj):
+    """d = H(x) - y (Algorithm 3)."""
+    return observe(prob, traj) - prob.y
+
+
+def obs_forcing(prob, r):
+    """Dense adjoint forcing: scatter r (p,) into a (T+1, n) array (H^T r)."""
+    f = np.zeros((prob.T + 1, prob.n))
+    np.add.at(f, (prob.obs_step, prob.obs_idx), r)
+    return f
+
+
+def cost(prob, traj, v):
+    """Non-quadratic cost (Eq. 2) in control space:
+    J = 1/2 ||R^-1/2 (H(x) - y)||^2 + 1/2 ||v||^2, with x - x_b = L v."""
+    d = innovation(prob, traj)
+    return 0.5 * float(np.sum(d * d * prob.rinv)) + 0.5 * float(np.dot(v, v))
+
+
+def gradient_b(prob, traj, d):
+    """b = L^T H^T R^-1 d: one adjoint integration (Algorithm 3)."""
+    lam0 = l96.ad(traj, obs_forcing(prob, d * prob.rinv), prob.dt, prob.F)
+    return prob.L.T @ lam0
+
+
+def hvp(prob, traj, W):
+    """A W for the columns of W (n, m): A w = L^T sum_t M_{0->t}^T H_t^T R^-1 H_t M_{0->t} L w
+    (Eq. 4, Algorithm 3: one TL forward and one AD backward integration per column)."""
+    W = np.atleast_2d(np.asarray(W, dtype=np.float64).T).T
+    out = np.empty_like(W)
+    for j in range(W.shape[1]):
+        dx0 = prob.L @ W[:, j]
+        dxs = l96.tl(traj, dx0, prob.dt, prob.F)
+        r = observe(prob, dxs) * prob.rinv
+        lam0 = l96.ad(traj, obs_forcing(prob, r), prob.dt, prob.F)
+        out[:, j] = prob.L.T @ lam0
+    return out
+
+
+def dense_hessian(prob, traj):
+    """A as a dense matrix, by applying it to the identity (tiny n only)."""
+    return hvp(prob, traj, np.eye(prob.n))
+
+
+def tl_matrix(prob, traj):
+    """G = d(observations)/d(v): the (p, n) Jacobian H M L (tiny n only)."""
+    G = np.empty((prob.p, prob.n))
+    for j in range(prob.n):
+        dxs = l96.tl(traj, prob.L[:, j], prob.dt, prob.F)
+        G[:, j] = observe(prob, dxs)
+    return G
+
+
+# --- inner-loop solvers ------------------------------------------------------------
+
+def cg_solve(apply, rhs, tol=1e-13, maxiter=None):
+    """Conjugate gradients for an SPD operator (textbook, Hestenes-Stiefel)."""
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    r0 = np.sqrt(rr)
+    maxiter = maxiter or 10 * rhs.size
+    for _ in range(maxiter):
+        if np.sqrt(rr) <= tol * r0 or r0 == 0.0:
+            break
+        Ap = apply(p)
+        alpha = rr / float(p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x
+
+
+def converged_increment(prob, traj, g, tol=1e-13):
+    """The exact inner-loop minimiser dv* = -(I + A)^-1 g by CG (Eq. 3 with
+    Algorithm 3's g = b + v)."""
+    return -cg_solve(lambda p: p + hvp(prob, traj, p[:, None])[:, 0], g, tol=tol)
+
+
+def varcg(prob, traj, g, m):
+    """Algorithm 1 (VarCG in Lanczos form) with full re-orthogonalisation.
+    Readings of its typos: beta_0 = ||r_0||, and the three-term recurrence
+    subtracts beta_{i-1} q_{i-1}.  Returns (dv, theta, U)."""
+    n = g.size
+    Qs = []
+    alphas, betas = [], []
+    r = g.copy()
+    beta = np.linalg.norm(r)
+    q_prev = np.zeros(n)
+    beta_prev = 0.0
+    for i in range(m):
+        if beta == 0.0:
+            break
+        q = r / beta
+        Qs.append(q)
+        w = hvp(prob, traj, q[:, None])[:, 0]
+        alpha = float(q @ w)
+        r = w - alpha * q - beta_prev * q_prev
+        Qm = np.array(Qs).T
+        r -= Qm @ (Qm.T @ r)
+        r -= Qm @ (Qm.T @ r)
+        alphas.append(alpha)
+        beta_prev, q_prev = beta, q
+        beta = np.linalg.norm(r)
+        betas.append(beta)
+    mm = len(alphas)
+    Tm = np.diag(alphas) + np.diag(betas[:mm - 1], 1) + np.diag(betas[:mm - 1], -1)
+    theta, Z = np.linalg.eigh(Tm)
+    U = np.array(Qs).T @ Z
+    c = U.T @ g
+    dv = -U @ (c / (1.0 + theta))
+    return dv, theta, U
+
+
+def orthonormal_basis(Y):
+    """Q of a Householder QR of Y (LAPACK geqrf/orgqr via numpy)."""
+    Q, _ = np.linalg.qr(Y, mode="reduced")
+    return Q
+
+
+def fix_signs(U):
+    """Make the largest-magnitude entry of each column positive."""
+    idx = np.argmax(np.abs(U), axis=0)
+    s = np.sign(U[idx, np.arange(U.shape[1])])
+    s[s == 0] = 1.0
+    return U * s
+
+
+def rsvd(prob, traj, Omega, q=0, exact_rr=False, apply=None):
+    """Randomized eigendecomposition of A (Algorithm 3, inner loop).
+
+    Omega: (n, m) sketch.  Y = A Omega; q rounds of subspace iteration
+    (Q = orth(Y); Y = A Q); Q = orth(Y); K solves K (Q^T W) = Q^T Y with W
+    the last block applied, symmetrised (or K = Q^T A Q when exact_rr);
+    K = Z Lambda Z^T; U = Q Z.  Returns (lam descending, U (n, m), info)."""
+    apply = apply or (lambda W: hvp(prob, traj, W))
+    W = np.asarray(Omega, dtype=np.float64)
+    Y = apply(W)
+    for _ in range(q):
+        W = orthonormal_basis(Y)
+        Y = apply(W)
+    Q = orthonormal_basis(Y)
+    if exact_rr:
+        K = Q.T @ apply(Q)
+    else:
+        Mq = Q.T @ W
+        Nq = Q.T @ Y
+        K = np.linalg.solve(Mq.T, Nq.T).T
+    K = 0.5 * (K + K.T)
+    lam, Z = np.linalg.eigh(K)
+    order = np.argsort(-lam, kind="stable")
+    lam, Z = lam[order], Z[:, order]
+    U = fix_signs(Q @ Z)
+    return lam, U, {"Q": Q, "K": K, "Y": Y, "W": W}
+
+
+def increment(lam, U, g):
+    """Adaptive increment of Algorithm 3 (Eqs. 8-11):
+    lambda_m > 1: dv = -U diag(1/(1+lambda)) U^T g              (LRA, mode 0)
+    otherwise:    dv = -(g - U diag(lambda/(1+lambda)) U^T g)   (LRU, mode 1)."""
+    c = U.T @ g
+    if lam[-1] > 1.0:
+        return -(U @ (c / (1.0 + lam))), 0
+    return -(g - U @ (c * lam / (1.0 + lam))), 1
+
+
+def analysis_cov_lowrank(L, lam, U):
+    """Low-rank posterior covariance (Eqs. 8/9 with B = L L^T):
+    LRU: P_a = B - (L U) diag(lambda/(1+lambda)) (L U)^T
+    LRA: P_a = (L U) diag(1/(1+lambda)) (L U)^T.
+    Returns (LU, coefficients, mode) with the same mode rule as the increment."""
+    LU = L @ U
+    if lam[-1] > 1.0:
+        return LU, 1.0 / (1.0 + lam), 0
+    return LU, lam / (1.0 + lam), 1
+
+
+def analysis_cov_dense(L, lam, U):
+    LU, coef, mode = analysis_cov_lowrank(L, lam, U)
+    low = (LU * coef) @ LU.T
+    if mode == 0:
+        return low
+    return L @ L.T - low
+
+
+def dofs(lam):
+    """Degrees of freedom for signal, sum lambda/(1+lambda) (Section 3.2)."""
+    lam = np.asarray(lam)
+    return float(np.sum(lam / (1.0 + lam)))
+
+
+# --- outer loop ---------------------------------------------------------------------
+
+def outer_step(prob, x, v, Omega, q=0, exact_rr=False):
+    """One cycle of Algorithm 3 (precond = rotation = false).
+    Returns a dict with J (at x), g, lam, U, dv, mode, and the updated x, v."""
+    traj = trajectory(prob, x)
+    d = innovation(prob, traj)
+    J = cost(prob, traj, v)
+    b = gradient_b(prob, traj, d)
+    g = b + v
+    lam, U, info = rsvd(prob, traj, Omega, q=q, exact_rr=exact_rr)
+    dv, mode = increment(lam, U, g)
+    return {"traj": traj, "J": J, "b": b, "g": g, "lam": lam, "U": U, "dv": dv, "mode": mode,
+            "x_next": x + prob.L @ dv, "v_next": v + dv, "info": info}
+
+
+def quadratic_cost(prob, traj, d, v, dv):
+    """Inner-loop quadratic cost J~(dv) = 1/2||R^-1/2(d + H M L dv)||^2 + 1/2||v + dv||^2
+    (Eq. 3 with Algorithm 3's sign of d and accumulated control v)."""
+    dxs = l96.tl(traj, prob.L @ dv, prob.dt, prob.F)
+    r = d + observe(prob, dxs)
+    return 0.5 * float(np.sum(r * r * prob.rinv)) + 0.5 * float(np.dot(v + dv, v + dv))
