@@ -32,14 +32,19 @@ def _sigma_vec(n):
 
 
 def test_gaussian_sqrt_reproduces_B():
-    for n, ell in [(40, 2.0), (33, 1.5)]:
+    # B = L L^T must be the Gaussian correlation exp(-d^2/(2 l^2)) scaled by
+    # sigma_i sigma_j (|sigma| <= 1.5), up to the lattice term
+    # 2 exp(-pi^2 l^2 / 2) and, on short rings, the periodic images
+    # exp(-(n - d)^2 / (2 l^2)) that the ring distance leaves out.
+    for n, ell, tol in [(40, 2.0, 5e-8), (33, 3.0, 5e-7), (64, 4.0, 5e-14)]:
         sig = _sigma_vec(n)
         L = bcov.bsqrt(n, ell, sig)
         B = sig[:, None] * bcov.gaussian_corr(n, ell) * sig[None, :]
-        np.testing.assert_allclose(L @ L.T, B, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(L @ L.T, B, rtol=0, atol=tol)
         S = bcov.sqrt_corr(n, ell)
+        np.testing.assert_allclose(S, S.T, rtol=0, atol=0)
         # circulant: every row is the previous one shifted by one place
-        np.testing.assert_allclose(np.roll(S[0], 5), S[5], rtol=0, atol=1e-11)
+        np.testing.assert_allclose(np.roll(S[0], 5), S[5], rtol=0, atol=0)
 
 
 def test_single_time_full_observation_gives_LtL():
