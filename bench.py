@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the RIOT inner loop on one GB300 (and N independent replicas).
+
+Workload: Lorenz-96, n = 4096, F = 8, dt = 0.05, 200-step window, 25% of the
+variables observed at fixed random indices every 4 steps (51 200
+observations, sigma_o = 1), Gaussian B (sigma_b = 1, length 4), k = 512
+Gaussian sketch columns, q = 1 power iteration.  A step is one full inner
+loop: sketch draw, 2 x 512 Hessian-vector products (tangent-linear +
+adjoint integrations), CholeskyQR, the projected matrix K, its FP64 Jacobi
+eigendecomposition, the Ritz vectors and the adaptive increment.  The
+outer-loop prerequisites (nonlinear trajectory, gradient) run once before
+the timed region.
+
+Metric: Hessian-vector products per second of inner-loop wall time (with the
+inner-loop milliseconds), for the mixed-precision path and the plain FP64
+GPU form of the same algorithm.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import configs  # noqa: E402
+
+WORKLOAD = "l96_n4096_F8_T200_obs25pct_every4_k512_q1"
+METRIC = "RIOT inner-loop Hessian-vector products per second (inner-loop wall time)"
+UNIT = "HVP/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="riot", choices=["riot", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def band_width(n, ell):
+    """Number of taps of the banded Gaussian square-root kernel (same rule as the library)."""
+    d = np.arange(n, dtype=np.float64)
+    reach = int(math.ceil(40.0 * ell / n)) + 1
+    row = sum(np.exp(-((d + j * n) ** 2) / (ell * ell)) for j in range(-reach, reach + 1))
+    row = row / np.sqrt(np.sum(row * row))
+    h = 0
+    for dd in range(1, n // 2 + 1):
+        if abs(row[dd]) > 1e-18 * row[0]:
+            h = dd
+    return n if 2 * h + 1 >= n else 2 * h + 1
+
+
+def hvp_flops(n, T, p, taps):
+    """Algorithmic FLOPs of one Hessian-vector product (FMA = 2):
+    TL RK4 step 33 n, AD RK4 step 34 n, L and L^T band 2 * 2 * taps * n,
+    observation scaling and scatter 3 per observation."""
+    return 67.0 * n * T + 4.0 * taps * n + 3.0 * p
+
+
+class ClockSampler:
+    def __init__(self, path, index):
+        self.path = path
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_problem(R, torch, cfg, dev, precision, kmax):
+    """Synthetic twin experiment built with the library itself: truth spun up
+    on the attractor, observations of the truth plus noise, background =
+    truth + L eps_b (random draws from the seeded Philox streams)."""
+    n, T = cfg.n, cfg.T
+    x_init = torch.tensor(cfg.F + cfg.truth_sd * cfg.truth_perturbation(), device=dev)
+    x0 = torch.empty(n, dtype=torch.float64, device=dev)
+    R.riot_l96_forecast(n, cfg.spinup, cfg.dt, cfg.F, x_init, x0, store_all=False)
+    traj = torch.empty(T + 1, n, dtype=torch.float64, device=dev)
+    R.riot_l96_forecast(n, T, cfg.dt, cfg.F, x0, traj)
+    st, ix = cfg.obs_layout_arrays()
+    sig = np.full(st.size, cfg.sigma_o)
+    y = traj[torch.tensor(st, device=dev), torch.tensor(ix, device=dev)].cpu().numpy() + sig * cfg.obs_noise(st.size)
+    ctx = R.Context(n=n, T=T, dt=cfg.dt, F=cfg.F, obs_step=st, obs_idx=ix, obs_y=y, obs_sigma=sig,
+                    length=cfg.ell, sigma_b=cfg.sigma_b, precision=precision, kmax=kmax, seed=cfg.seed)
+    eps = torch.tensor(cfg.background_perturbation(), device=dev)
+    xb = torch.empty(n, dtype=torch.float64, device=dev)
+    R.riot_bsqrt_apply(ctx.h, eps, xb)
+    xb += x0
+    return ctx, xb, st.size
+
+
+def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv):
+    """Per-step CUDA-event times of riot_rsvd + riot_increment (L2 flushed between steps)."""
+    s = torch.cuda.current_stream()
+    times, phases = [], []
+    for i in range(warmup + steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        lam = R.riot_rsvd(ctx.h, cfg.k, cfg.q, sketch_stream=configs.STREAM_SKETCH0)
+        mode = R.riot_increment(ctx.h, dv)
+        e1.record(s)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            times.append(e0.elapsed_time(e1))
+            phases.append(R.riot_rsvd_timings(ctx.h))
+    return times, phases, lam, mode
+
+
+def cpu_oracle_hvps(cfg, seconds, min_cols=2):
+    """FP64 CPU oracle Hessian-vector products on the same workload, single thread."""
+    from oracle import problem, riot as orc
+    prob = problem.build(cfg)
+    traj = orc.trajectory(prob, prob.x_b)
+    t0 = time.perf_counter()
+    done = 0
+    j = 0
+    while True:
+        W = cfg.sketch(0, k=1, n=cfg.n)[:, :].T if j == 0 else np.random.default_rng(j).standard_normal((cfg.n, 1))
+        orc.hvp(prob, traj, W)
+        done += 1
+        j += 1
+        el = time.perf_counter() - t0
+        if done >= min_cols and el >= seconds:
+            break
+    return done, el
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import _clib
+    _clib.build()
+    cfg = configs.l96_large()
+    from oracle import problem, riot as orc
+    prob = problem.build(cfg)
+    traj = orc.trajectory(prob, prob.x_b)
+    cols = 4
+    Om = cfg.sketch(0, k=cols).T
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        orc.hvp(prob, traj, Om)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    per = statistics.mean(times)
+    value = cols / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": cfg.n, "T": cfg.T, "k": cfg.k, "q": cfg.q},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d Hessian-vector products of the workload per step "
+                                       "(FP64 C TL/AD + numpy L, 1 thread)" % cols},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    from paper_1906_01413_gb300 import riot as R
+    rank, world, local = dist_env()
+    R.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    cfg = configs.l96_large()
+    n, k, q, T = cfg.n, cfg.k, cfg.q, cfg.T
+
+    # ---- mixed-precision path ------------------------------------------------------
+    ctx, xb, p = build_problem(R, torch, cfg, dev, R.RIOT_PREC_MIXED, k)
+    R.riot_outer_begin(ctx.h, xb)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    dv = torch.empty(n, dtype=torch.float64, device=dev)
+    time_inner_loop(R, torch, ctx, cfg, 0, args.warmup, flush, dv)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    launches0 = R.riot_kernel_launches()
+    wall0 = time.perf_counter()
+    with ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
+                      if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv",
+                      local) as clk:
+        times, phases, lam, mode = time_inner_loop(R, torch, ctx, cfg, args.steps, 0, flush, dv)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = R.riot_kernel_launches() - launches0
+    ms = statistics.mean(times)
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    hvps_per_step = (q + 1) * k
+    value = world * hvps_per_step / (ms * 1e-3)
+
+    ph = {key: statistics.mean(p_[key] for p_ in phases) for key in phases[0]}
+    hvp_launch_ms = ph["hvp"] / (q + 1)
+    taps = band_width(n, cfg.ell)
+    flop_hvp = hvp_flops(n, T, p, taps)
+    achieved = flop_hvp * k / (hvp_launch_ms * 1e-3) / 1e12
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
+
+    # ---- end to end through the C ABI with host buffers ------------------------------
+    Om_host = torch.from_numpy(cfg.sketch(0).astype(np.float32)).pin_memory()
+    Om_dev = torch.empty(k, n, dtype=torch.float32, device=dev)
+    dv_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for i in range(args.warmup + max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Om_dev.copy_(Om_host, non_blocking=True)
+        lam_e = R.riot_rsvd(ctx.h, k, q, Omega=Om_dev)
+        R.riot_increment(ctx.h, dv)
+        dv_host.copy_(dv, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_times)
+
+    # ---- plain FP64 GPU form -----------------------------------------------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        ctx.close()
+        ctx64, xb64, _ = build_problem(R, torch, cfg, dev, R.RIOT_PREC_FP64, k)
+        R.riot_outer_begin(ctx64.h, xb64)
+        t64, ph64, lam64, _ = time_inner_loop(R, torch, ctx64, cfg, args.fp64_steps, 1, flush, dv)
+        ms64 = statistics.mean(t64)
+        fp64 = {"ms_per_step": ms64, "value": hvps_per_step / (ms64 * 1e-3), "unit": UNIT,
+                "hvp_ms": statistics.mean(p_["hvp"] for p_ in ph64),
+                "speedup_of_mixed": ms64 / ms,
+                "lambda1_rel_diff_mixed_vs_fp64": float(abs(lam[0] - lam64[0]) / abs(lam64[0]))}
+        ctx64.close()
+    else:
+        ctx.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "T": T, "k": k, "q": q, "p_obs": int(p),
+                       "precision": "TL/AD f32; Gram, Cholesky, Jacobi eig, increment f64",
+                       "l2": "256 MB buffer written between timed steps (flush)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "inner_loop_ms": ms},
+            "phases_ms": ph,
+            "roofline": {"bound": "alu", "kernel": "l96_hvp_kernel<float,8>", "achieved": achieved,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sm_count, sm_max),
+                         "flop_per_hvp": flop_hvp, "hvp_per_launch": k, "launch_ms": hvp_launch_ms},
+            "e2e": {"value": world * hvps_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(n * k * 4),
+                    "d2h_bytes_per_step": int(n * 8 + k * 8)},
+            "gpu_launches": int(launches),
+            "wall_s_timed": wall}
+    if fp64:
+        line["fp64_gpu_form"] = fp64
+    cs = clk.summary()
+    if cs:
+        line["clocks"] = cs
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import _clib
+        _clib.build()
+        done, el = cpu_oracle_hvps(cfg, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "%d Hessian-vector products of the same window (FP64 C TL/AD + numpy L, "
+                                          "1 thread, %.1f s)" % (done, el)}
+    if rank == 0:
+        print(json.dumps(line))
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

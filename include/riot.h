@@ -1,0 +1,210 @@
+/*
+ * riot.h -- C ABI of a single-GPU (GB300, sm_103a) library for the inner loop
+ * of RIOT, the Randomized Incremental Optimal Technique for incremental
+ * 4D-Var (Bousserez, Guerrette & Henze, arXiv:1906.01413).
+ *
+ * The library owns one assimilation window per context.  Each outer
+ * iteration integrates the nonlinear model and forms the gradient
+ * (riot_outer_begin); the inner loop is a randomized eigendecomposition of
+ * the prior-preconditioned Hessian A = L^T H^T R^-1 H L built from batched
+ * tangent-linear + adjoint integrations (riot_hessian_apply, riot_rsvd),
+ * followed by the adaptive low-rank increment (riot_increment) and the
+ * low-rank analysis covariance (riot_analysis_cov_lowrank).
+ *
+ * Conventions shared by every entry point
+ *  - Arguments named *_dev are device pointers on the context's device,
+ *    owned by the caller; the library never frees them.  Host arrays are
+ *    read during the call only.
+ *  - Vectors of length n are contiguous.  Blocks of column vectors are
+ *    column-major: column j of an n x m block starts at ptr + j*ld.
+ *  - Element type of the Hessian blocks (W, Y, Omega): float when the
+ *    context was created with RIOT_PREC_MIXED, double with RIOT_PREC_FP64.
+ *    Outer-loop vectors (x, v, dv, U, L U) are always double.
+ *  - Work is queued on the stream given to riot_setup.  Calls that return
+ *    host scalars (J, eigenvalues, mode) synchronise that stream; the
+ *    others are asynchronous.
+ *  - Calls never throw; they return a riot_status.  riot_last_error gives a
+ *    one-line message for the last failing call on the context.  Calls made
+ *    out of order (e.g. riot_increment before riot_rsvd) return RIOT_ESTATE.
+ *  - Sign conventions follow Algorithm 3: d = H(x) - y, dv = -(...)(b + v).
+ *    Eigenvalues are those of A (not I + A), sorted in decreasing order.
+ *  - One context is not safe to use from two host threads at once.
+ */
+#ifndef RIOT_H
+#define RIOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RIOT_OK = 0,
+    RIOT_EINVAL = -1,    /* bad argument or descriptor                        */
+    RIOT_ENOMEM = -2,    /* device allocation failed                          */
+    RIOT_ECUDA = -3,     /* a CUDA runtime call failed                        */
+    RIOT_ENOTSPD = -4,   /* Cholesky met a non-positive pivot (no fallback)   */
+    RIOT_ETIMEOUT = -5,  /* a bounded device wait ran out                     */
+    RIOT_ESTATE = -6,    /* call out of order                                 */
+    RIOT_ENOCONV = -7,   /* the eigensolver did not converge                  */
+    RIOT_ENONFINITE = -8 /* a NaN or Inf reached a reduction                  */
+} riot_status;
+
+enum { RIOT_MODEL_L96 = 1 };
+enum { RIOT_B_GAUSS_RING = 1 };
+enum { RIOT_PREC_MIXED = 0, RIOT_PREC_FP64 = 1 };
+
+/* Model of the window (Section 3.1 for Lorenz-96).
+ * L96: dx_i/dt = (x_{i+1} - x_{i-2}) x_{i-1} - x_i + F on a periodic ring of
+ * n variables, advanced by T classical RK4 steps of length dt.
+ * Limits: 16 <= n <= 8192, 0 <= T, dt > 0. */
+typedef struct {
+    int32_t kind;   /* RIOT_MODEL_L96                                        */
+    int32_t T;      /* number of time steps in the window                     */
+    int64_t n;      /* number of model variables (= control size)             */
+    double dt;      /* step length                                            */
+    double F;       /* forcing                                                */
+} riot_model_desc;
+
+/* Observations y with diagonal error covariance R = diag(sigma^2)
+ * (Section 2.1, Eq. 2).  Observation j is of variable idx[j] at the end of
+ * step step[j] (step 0 = the initial state).  Entries must be sorted by step
+ * (nondecreasing); several observations of one (step, idx) pair are allowed.
+ * All arrays are host arrays of length p; p = 0 is allowed. */
+typedef struct {
+    int64_t p;
+    const int32_t *step;   /* 0..T                          */
+    const int32_t *idx;    /* 0..n-1                        */
+    const double *y;       /* observed value                */
+    const double *sigma;   /* error standard deviation > 0  */
+} riot_obs_desc;
+
+/* Prior covariance B = L L^T (Section 2.1, Eq. 3), Gaussian correlations
+ * (Section 3.1).  RIOT_B_GAUSS_RING: L = diag(s) S with S the periodic
+ * Gaussian convolution S_d = alpha sum_j exp(-(d + j n)^2 / length^2),
+ * normalised so that (S S^T)_ii = 1.  Then B = L L^T has the Gaussian
+ * correlation exp(-d^2 / (2 length^2)) up to lattice terms of relative size
+ * 2 exp(-pi^2 length^2 / 2).  S is applied as a band of the offsets whose
+ * weight exceeds 1e-18 of the peak.
+ * s = sigma_vec (host, length n) when non-NULL, else sigma_b everywhere. */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double length;
+    double sigma_b;
+    const double *sigma_vec;
+} riot_bcov_desc;
+
+typedef struct {
+    int32_t precision;  /* RIOT_PREC_MIXED: FP32 TL/AD and FP32 block storage,
+                           FP64 Gram/Cholesky, eigensolver and increment;
+                           RIOT_PREC_FP64: double everywhere                  */
+    int32_t kmax;       /* largest number of sketch columns used per call (>= 1) */
+    int32_t exact_rr;   /* 0: K solves K (Q^T W) = Q^T Y (Algorithm 3);
+                           1: K = Q^T A Q (k more Hessian applications)       */
+    int32_t reserved;
+    uint64_t seed;      /* key of the device-drawn Gaussian sketch            */
+} riot_options;
+
+typedef struct riot_ctx riot_ctx;
+
+/* Create a context on the current CUDA device.  Copies the model, the
+ * observations and the B descriptor to the device, builds L, and allocates
+ * all workspace for kmax sketch columns.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream).  On failure *out is NULL. */
+riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_obs_desc *obs,
+                       const riot_bcov_desc *B, const riot_options *opt, void *cuda_stream);
+
+/* Outer-loop prerequisites (Algorithm 3, top of the outer loop): set the
+ * current state x (and control-space increment sum v, NULL = 0 on the first
+ * call, else the context's own v), integrate and store the trajectory in
+ * FP64, form d = H(x) - y, the cost J = 1/2 ||R^-1/2 d||^2 + 1/2 ||v||^2,
+ * the gradient b = L^T H^T R^-1 d (one FP64 adjoint integration) and
+ * g = b + v.  x_dev NULL keeps the context's x (updated by riot_increment).
+ * J_out (host, may be NULL) receives J; this synchronises. */
+riot_status riot_outer_begin(riot_ctx *ctx, const double *x_dev, const double *v_dev, double *J_out);
+
+/* Y = A W (+ W when add_identity), A = L^T sum_t M_{0->t}^T H_t^T R^-1 H_t
+ * M_{0->t} L (Eq. 4): for every column, one tangent-linear integration
+ * forward and one adjoint integration backward along the stored trajectory
+ * (Algorithm 3, "do in parallel").  W and Y are n x ncols blocks with
+ * leading dimension ld >= n (element type per the precision).  ncols may
+ * exceed kmax (processed in slices).  Requires riot_outer_begin. */
+riot_status riot_hessian_apply(riot_ctx *ctx, const void *W_dev, void *Y_dev, int64_t ld,
+                               int32_t ncols, int32_t add_identity);
+
+/* Randomized eigendecomposition of A (Algorithm 3 inner loop): draw Omega
+ * (n x k, N(0,1)) from the context seed and sketch_stream with Philox4x32-10
+ * + Box-Muller unless Omega_dev (n x k, ld = n) is given; Y = A Omega; q
+ * rounds of subspace iteration Q = orth(Y), Y = A Q; Q = orth(Y) by shifted
+ * CholeskyQR with two cleanup passes; K from Q^T W and Q^T Y (or Q^T A Q);
+ * K = Z Lambda Z^T by cyclic Jacobi in FP64; U = Q Z.  1 <= k <= min(kmax, n).
+ * lambda_out (host, k doubles, may be NULL) receives the eigenvalues in
+ * decreasing order; this synchronises.  Requires riot_outer_begin. */
+riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream,
+                      const void *Omega_dev, double *lambda_out);
+
+/* Adaptive increment (Algorithm 3, Eqs. 8-11): with c = U^T g,
+ * LRA (mode 0) when the smallest retained eigenvalue is > 1:
+ *     dv = -U diag(1/(1+lambda)) c
+ * LRU (mode 1) otherwise:  dv = -(g - U diag(lambda/(1+lambda)) c).
+ * Then v += dv and x += L dv in the context.  dv_dev (n doubles) and
+ * mode_out may be NULL; a non-NULL mode_out synchronises.  Requires
+ * riot_rsvd since the last riot_outer_begin.  The stored trajectory and g
+ * are those of the last riot_outer_begin until the next one, so repeated
+ * riot_rsvd / riot_increment calls redo the same inner loop. */
+riot_status riot_increment(riot_ctx *ctx, double *dv_dev, int32_t *mode_out);
+
+/* Low-rank analysis covariance (Eqs. 8/9 with B = L L^T):
+ * LRU: P_a = B - (LU) diag(coef) (LU)^T, coef = lambda/(1+lambda)
+ * LRA: P_a = (LU) diag(coef) (LU)^T,     coef = 1/(1+lambda)
+ * for the leading m <= k eigenpairs.  LU_dev: n x m doubles (ld = n);
+ * coef_out: host m doubles (may be NULL; synchronises); mode by the same
+ * rule as riot_increment applied to the m retained eigenvalues. */
+riot_status riot_analysis_cov_lowrank(riot_ctx *ctx, int32_t m, double *LU_dev, double *coef_out,
+                                      int32_t *mode_out);
+
+/* out = L in (transpose = 0) or L^T in (transpose = 1) for ncols columns of
+ * n doubles (ld = n). */
+riot_status riot_bsqrt_apply(riot_ctx *ctx, const double *in_dev, double *out_dev, int32_t transpose,
+                             int32_t ncols);
+
+/* Copy the context's state out: x, v, g (n doubles each), the eigenvectors
+ * U (n x k doubles) and eigenvalues (k doubles, device); NULL skips one. */
+riot_status riot_get_state(riot_ctx *ctx, double *x_dev, double *v_dev, double *g_dev,
+                           double *U_dev, double *lambda_dev);
+
+/* Gaussian block from the Philox4x32-10 + Box-Muller stream (seed, stream):
+ * element (i, j) of the n x ncols block is stream element j*n + i, written
+ * at out[j*ld + i] as float (is_double = 0) or double. */
+riot_status riot_draw_normal(uint64_t seed, int64_t stream, int64_t n, int32_t ncols, int64_t ld,
+                             int32_t is_double, void *out_dev, void *cuda_stream);
+
+/* Standalone FP64 Lorenz-96 forecast: traj_dev ((T+1) x n doubles) gets the
+ * RK4 trajectory from x0_dev, or only the final state when
+ * store_all = 0 (traj_dev then holds n doubles).  Used to build synthetic
+ * truths without a context. */
+riot_status riot_l96_forecast(int64_t n, int32_t T, double dt, double F, const double *x0_dev,
+                              double *traj_dev, int32_t store_all, void *cuda_stream);
+
+/* Timings of the phases of the last riot_rsvd in milliseconds (CUDA events on
+ * the context stream): [0] Hessian applications, [1] orthonormalisation,
+ * [2] projected matrix K, [3] eigensolver, [4] Ritz vectors, [5] total.
+ * Synchronises. */
+riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6);
+
+/* Number of kernel launches the library has issued in this process (all
+ * contexts); a benchmark reads it before and after a timed region. */
+uint64_t riot_kernel_launches(void);
+
+const char *riot_last_error(const riot_ctx *ctx);
+const char *riot_status_string(riot_status s);
+void riot_destroy(riot_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIOT_H */

@@ -1,0 +1,557 @@
+// C ABI of the RIOT inner-loop library (see include/riot.h for the contract).
+//
+// Host orchestration only: every arithmetic step of the inner loop runs in
+// the kernels of l96.cu, rng.cu and linalg.cu on the context's stream.  The
+// host builds the model tables once in riot_setup (observation pointers and
+// slots, the banded Gaussian square-root kernel) and then only launches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.h"
+
+using namespace riot;
+
+struct riot_ctx {
+    int dev = 0;
+    cudaStream_t s = nullptr;
+    int prec = RIOT_PREC_MIXED;
+    int kmax = 0, exact_rr = 0;
+    uint64_t seed = 0;
+    L96Dev m;
+    std::vector<void *> allocs;
+    // model tables
+    int *optr = nullptr, *oslot = nullptr, *oidx = nullptr;
+    double *y = nullptr, *rinv64 = nullptr, *band64 = nullptr, *sig64 = nullptr;
+    float *rinv32 = nullptr, *band32 = nullptr, *sig32 = nullptr;
+    // outer-loop state
+    double *x = nullptr, *v = nullptr, *g = nullptr, *dv = nullptr, *tmp = nullptr;
+    double *traj = nullptr, *d = nullptr, *rd = nullptr, *jo = nullptr;
+    float2 *coef32 = nullptr;
+    double2 *coef64 = nullptr;
+    // inner-loop workspace
+    void *Wblk = nullptr, *Yblk = nullptr, *rscr = nullptr;
+    double *Q = nullptr, *U = nullptr;
+    double *G = nullptr, *Mm = nullptr, *Nm = nullptr, *Km = nullptr, *Z = nullptr, *lam = nullptr, *cvec = nullptr;
+    double *jwork = nullptr;
+    int *info = nullptr;  // [0..7] Cholesky passes, [8..9] Jacobi, [10] mode, [11] finite flag
+    int have_traj = 0, have_rsvd = 0, k_last = 0, v_init = 0, jacobi_sweeps = 0;
+    // timing
+    cudaEvent_t ev[32];
+    int nev = 0;
+    int ev_phase[32];
+    char err[512] = {0};
+};
+
+namespace {
+
+riot_status fail(riot_ctx *c, riot_status st, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define CU(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(ctx, RIOT_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                   \
+    } while (0)
+
+template <typename T>
+riot_status dalloc(riot_ctx *ctx, T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RIOT_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    *p = (T *)q;
+    return RIOT_OK;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        riot_status st_ = (x);          \
+        if (st_ != RIOT_OK) return st_; \
+    } while (0)
+
+size_t real_size(const riot_ctx *c) { return c->prec == RIOT_PREC_FP64 ? sizeof(double) : sizeof(float); }
+char real_tag(const riot_ctx *c) { return c->prec == RIOT_PREC_FP64 ? 'd' : 'f'; }
+
+// Periodic Gaussian square-root kernel, unit-variance normalised, as a band.
+void build_band(int n, double ell, std::vector<double> &band, int &hl, int &hh)
+{
+    std::vector<double> row(n, 0.0);
+    const int reach = (int)ceil(40.0 * ell / n) + 1;
+    for (int d = 0; d < n; ++d) {
+        double s = 0.0;
+        for (int j = -reach; j <= reach; ++j) {
+            const double z = (double)d + (double)j * n;
+            s += exp(-z * z / (ell * ell));
+        }
+        row[d] = s;
+    }
+    double ss = 0.0;
+    for (int d = 0; d < n; ++d) ss += row[d] * row[d];
+    const double alpha = 1.0 / sqrt(ss);
+    for (int d = 0; d < n; ++d) row[d] *= alpha;
+    int h = 0;
+    for (int d = 1; d <= n / 2; ++d)
+        if (fabs(row[d]) > 1e-18 * row[0]) h = d;
+    if (2 * h + 1 >= n) {
+        hl = (n - 1) / 2;
+        hh = n / 2;
+    } else {
+        hl = hh = h;
+    }
+    band.assign(hl + hh + 1, 0.0);
+    for (int d = -hl; d <= hh; ++d) band[d + hl] = row[((d % n) + n) % n];
+}
+
+void ev_mark(riot_ctx *c, int phase)
+{
+    if (c->nev < 32) {
+        cudaEventRecord(c->ev[c->nev], c->s);
+        c->ev_phase[c->nev] = phase;
+        ++c->nev;
+    }
+}
+
+riot_status hvp(riot_ctx *ctx, const void *W, void *Y, int64_t ld, int ncols, int add_identity)
+{
+    const size_t rs = real_size(ctx);
+    for (int c0 = 0; c0 < ncols; c0 += ctx->kmax) {
+        const int nc = (ncols - c0 < ctx->kmax) ? ncols - c0 : ctx->kmax;
+        const char *w = (const char *)W + (size_t)c0 * ld * rs;
+        char *yv = (char *)Y + (size_t)c0 * ld * rs;
+        if (ctx->prec == RIOT_PREC_FP64)
+            CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, (const double *)w, (double *)yv, ld, nc, add_identity,
+                                  (double *)ctx->rscr, 0, ctx->s));
+        else
+            CU(l96_hvp_launch_f32(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
+                                  (float *)ctx->rscr, 0, ctx->s));
+    }
+    return RIOT_OK;
+}
+
+// Q (FP64, n x k) = orthonormal basis of Y (real, n x k): shifted CholeskyQR
+// (shift 11 (n k + k (k + 1)) u ||Y||_F^2, Fukaya et al. 2020) followed by two
+// unshifted CholeskyQR passes.
+riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
+{
+    const int n = ctx->m.geom.n;
+    CU(convert_block(Y, real_tag(ctx), n, ctx->Q, 'd', n, n, k, ctx->s));
+    for (int pass = 0; pass < 3; ++pass) {
+        CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Q, 'd', n, 0.0, ctx->G, 'd', k, ctx->s));
+        const double u = ldexp(1.0, -53);
+        const double shift = (pass == 0) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
+        CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, nullptr, ctx->s));
+        CU(trsm_right_lt(ctx->Q, n, k, n, ctx->G, k, ctx->s));
+    }
+    return RIOT_OK;
+}
+
+riot_status check_cholesky(riot_ctx *ctx, int base, int count, const char *what)
+{
+    int h[8] = {0};
+    CU(cudaMemcpyAsync(h, ctx->info + base, sizeof(int) * count, cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    for (int i = 0; i < count; ++i)
+        if (h[i] != 0)
+            return fail(ctx, RIOT_ENOTSPD, "%s: Cholesky pass %d met a non-positive pivot at column %d", what, i,
+                        h[i] - 1);
+    return RIOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *riot_status_string(riot_status s)
+{
+    switch (s) {
+    case RIOT_OK: return "ok";
+    case RIOT_EINVAL: return "invalid argument";
+    case RIOT_ENOMEM: return "out of device memory";
+    case RIOT_ECUDA: return "CUDA error";
+    case RIOT_ENOTSPD: return "matrix not positive definite";
+    case RIOT_ETIMEOUT: return "device wait timed out";
+    case RIOT_ESTATE: return "call out of order";
+    case RIOT_ENOCONV: return "eigensolver did not converge";
+    case RIOT_ENONFINITE: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+const char *riot_last_error(const riot_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+uint64_t riot_kernel_launches(void) { return (uint64_t)launches_total(); }
+
+void riot_destroy(riot_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->dev);
+    if (ctx->s) cudaStreamSynchronize(ctx->s);
+    for (void *p : ctx->allocs) cudaFree(p);
+    for (int i = 0; i < 32; ++i)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    delete ctx;
+}
+
+riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_obs_desc *obs, const riot_bcov_desc *B,
+                       const riot_options *opt, void *cuda_stream)
+{
+    if (!out) return RIOT_EINVAL;
+    *out = nullptr;
+    if (!model || !obs || !B || !opt) return RIOT_EINVAL;
+    riot_ctx *ctx = new riot_ctx();
+    for (int i = 0; i < 32; ++i) ctx->ev[i] = nullptr;
+    riot_status st = RIOT_OK;
+    auto bail = [&](riot_status s2) {
+        // keep the message readable for the caller through stderr; the context is gone
+        fprintf(stderr, "riot_setup: %s\n", ctx->err);
+        riot_destroy(ctx);
+        return s2;
+    };
+    if (model->kind != RIOT_MODEL_L96) return bail(fail(ctx, RIOT_EINVAL, "unknown model kind %d", model->kind));
+    const int64_t n64 = model->n;
+    if (n64 < 16 || n64 > 8192) return bail(fail(ctx, RIOT_EINVAL, "n = %lld outside [16, 8192]", (long long)n64));
+    const int n = (int)n64;
+    if (model->T < 0 || !(model->dt > 0.0) || !isfinite(model->F))
+        return bail(fail(ctx, RIOT_EINVAL, "bad T / dt / F"));
+    if (B->kind != RIOT_B_GAUSS_RING || !(B->length > 0.0))
+        return bail(fail(ctx, RIOT_EINVAL, "bad B descriptor (kind %d, length %g)", B->kind, B->length));
+    if (opt->kmax < 1 || opt->kmax > 4096) return bail(fail(ctx, RIOT_EINVAL, "kmax = %d outside [1, 4096]", opt->kmax));
+    if (opt->precision != RIOT_PREC_MIXED && opt->precision != RIOT_PREC_FP64)
+        return bail(fail(ctx, RIOT_EINVAL, "unknown precision %d", opt->precision));
+    const int64_t p64 = obs->p;
+    if (p64 < 0 || p64 > (int64_t)1 << 30) return bail(fail(ctx, RIOT_EINVAL, "bad observation count"));
+    const int p = (int)p64;
+    if (p > 0 && (!obs->step || !obs->idx || !obs->y || !obs->sigma))
+        return bail(fail(ctx, RIOT_EINVAL, "null observation array"));
+    const int T = model->T;
+    for (int j = 0; j < p; ++j) {
+        if (obs->step[j] < 0 || obs->step[j] > T || obs->idx[j] < 0 || obs->idx[j] >= n || !(obs->sigma[j] > 0.0) ||
+            !isfinite(obs->y[j]))
+            return bail(fail(ctx, RIOT_EINVAL, "observation %d out of range", j));
+        if (j > 0 && obs->step[j] < obs->step[j - 1])
+            return bail(fail(ctx, RIOT_EINVAL, "observations not sorted by step at %d", j));
+    }
+    if (B->sigma_vec)
+        for (int i = 0; i < n; ++i)
+            if (!isfinite(B->sigma_vec[i])) return bail(fail(ctx, RIOT_EINVAL, "non-finite sigma_vec[%d]", i));
+
+    cudaGetDevice(&ctx->dev);
+    ctx->s = (cudaStream_t)cuda_stream;
+    ctx->prec = opt->precision;
+    ctx->kmax = opt->kmax;
+    ctx->exact_rr = opt->exact_rr;
+    ctx->seed = opt->seed;
+    L96Dev &m = ctx->m;
+    if (!choose_geom(n, &m.geom)) return bail(fail(ctx, RIOT_EINVAL, "no thread layout for n = %d", n));
+    m.T = T;
+    m.dt = model->dt;
+    m.F = model->F;
+    m.p = p;
+
+    // host tables
+    std::vector<int> optr(T + 2, p), oslot(p), oidx(p);
+    std::vector<double> rinv(p), yv(p);
+    std::vector<float> rinv32(p);
+    {
+        int j = 0;
+        for (int t = 0; t <= T + 1; ++t) {
+            while (j < p && obs->step[j] < t) ++j;
+            optr[t] = j;
+        }
+    }
+    for (int j = 0; j < p; ++j) {
+        oidx[j] = obs->idx[j];
+        oslot[j] = m.geom.slot(obs->idx[j]);
+        rinv[j] = 1.0 / (obs->sigma[j] * obs->sigma[j]);
+        rinv32[j] = (float)rinv[j];
+        yv[j] = obs->y[j];
+    }
+    std::vector<double> band;
+    int hl = 0, hh = 0;
+    build_band(n, B->length, band, hl, hh);
+    std::vector<float> band32(band.begin(), band.end());
+    std::vector<double> sig(n);
+    std::vector<float> sig32(n);
+    for (int i = 0; i < n; ++i) {
+        sig[i] = B->sigma_vec ? B->sigma_vec[i] : B->sigma_b;
+        sig32[i] = (float)sig[i];
+    }
+    m.band.hl = hl;
+    m.band.hh = hh;
+
+    const size_t np = (size_t)n, k = (size_t)ctx->kmax, rs = real_size(ctx);
+    if ((st = dalloc(ctx, &ctx->optr, T + 2)) || (st = dalloc(ctx, &ctx->oslot, p)) || (st = dalloc(ctx, &ctx->oidx, p)) ||
+        (st = dalloc(ctx, &ctx->y, p)) || (st = dalloc(ctx, &ctx->rinv64, p)) || (st = dalloc(ctx, &ctx->rinv32, p)) ||
+        (st = dalloc(ctx, &ctx->band64, band.size())) || (st = dalloc(ctx, &ctx->band32, band.size())) ||
+        (st = dalloc(ctx, &ctx->sig64, np)) || (st = dalloc(ctx, &ctx->sig32, np)) || (st = dalloc(ctx, &ctx->x, np)) ||
+        (st = dalloc(ctx, &ctx->v, np)) || (st = dalloc(ctx, &ctx->g, np)) || (st = dalloc(ctx, &ctx->dv, np)) ||
+        (st = dalloc(ctx, &ctx->tmp, np)) || (st = dalloc(ctx, &ctx->traj, (T + 1) * np)) ||
+        (st = dalloc(ctx, &ctx->d, p)) || (st = dalloc(ctx, &ctx->rd, p)) || (st = dalloc(ctx, &ctx->jo, 2)) ||
+        (st = dalloc(ctx, &ctx->coef64, (size_t)T * 4 * m.geom.Np + 1)) ||
+        (ctx->prec == RIOT_PREC_MIXED && (st = dalloc(ctx, &ctx->coef32, (size_t)T * 4 * m.geom.Np + 1))) ||
+        (st = dalloc(ctx, (char **)&ctx->Wblk, np * k * rs)) || (st = dalloc(ctx, (char **)&ctx->Yblk, np * k * rs)) ||
+        (st = dalloc(ctx, (char **)&ctx->rscr, (size_t)p * k * rs + 16)) || (st = dalloc(ctx, &ctx->Q, np * k)) ||
+        (st = dalloc(ctx, &ctx->U, np * k)) || (st = dalloc(ctx, &ctx->G, k * k)) || (st = dalloc(ctx, &ctx->Mm, k * k)) ||
+        (st = dalloc(ctx, &ctx->Nm, k * k)) || (st = dalloc(ctx, &ctx->Km, k * k)) || (st = dalloc(ctx, &ctx->Z, k * k)) ||
+        (st = dalloc(ctx, &ctx->lam, k)) || (st = dalloc(ctx, &ctx->cvec, k)) ||
+        (st = dalloc(ctx, &ctx->jwork, jacobi_work_doubles((int)k))) || (st = dalloc(ctx, &ctx->info, 16)))
+        return bail(st);
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->s) : cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = up(ctx->optr, optr.data(), sizeof(int) * (T + 2))) || (e = up(ctx->oslot, oslot.data(), sizeof(int) * p)) ||
+        (e = up(ctx->oidx, oidx.data(), sizeof(int) * p)) || (e = up(ctx->y, yv.data(), sizeof(double) * p)) ||
+        (e = up(ctx->rinv64, rinv.data(), sizeof(double) * p)) || (e = up(ctx->rinv32, rinv32.data(), sizeof(float) * p)) ||
+        (e = up(ctx->band64, band.data(), sizeof(double) * band.size())) ||
+        (e = up(ctx->band32, band32.data(), sizeof(float) * band.size())) ||
+        (e = up(ctx->sig64, sig.data(), sizeof(double) * n)) || (e = up(ctx->sig32, sig32.data(), sizeof(float) * n)) ||
+        (e = cudaMemsetAsync(ctx->v, 0, sizeof(double) * n, ctx->s)) ||
+        (e = cudaMemsetAsync(ctx->x, 0, sizeof(double) * n, ctx->s)) || (e = cudaStreamSynchronize(ctx->s)))
+        return bail(fail(ctx, RIOT_ECUDA, "setup upload failed: %s", cudaGetErrorString(e)));
+    for (int i = 0; i < 32; ++i)
+        if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) return bail(fail(ctx, RIOT_ECUDA, "cudaEventCreate failed"));
+    m.optr = ctx->optr;
+    m.oslot = ctx->oslot;
+    m.oidx = ctx->oidx;
+    m.y = ctx->y;
+    m.rinv64 = ctx->rinv64;
+    m.rinv32 = ctx->rinv32;
+    m.band64 = ctx->band64;
+    m.band32 = ctx->band32;
+    m.sig64 = ctx->sig64;
+    m.sig32 = ctx->sig32;
+    *out = ctx;
+    return RIOT_OK;
+}
+
+riot_status riot_outer_begin(riot_ctx *ctx, const double *x_dev, const double *v_dev, double *J_out)
+{
+    if (!ctx) return RIOT_EINVAL;
+    CU(cudaSetDevice(ctx->dev));
+    const int n = ctx->m.geom.n;
+    if (x_dev) CU(cudaMemcpyAsync(ctx->x, x_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->s));
+    if (v_dev) CU(cudaMemcpyAsync(ctx->v, v_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->s));
+    CU(cudaMemsetAsync(ctx->jo, 0, sizeof(double) * 2, ctx->s));
+    CU(l96_nl_launch(ctx->m, ctx->x, ctx->traj, ctx->coef32, ctx->coef64, ctx->d, ctx->jo, nullptr, ctx->s));
+    // gradient b = L^T H^T R^-1 d: one FP64 adjoint integration, then g = b + v
+    CU(mul(ctx->m.p, ctx->d, ctx->rinv64, ctx->rd, ctx->s));
+    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->g, n, 1, 0, ctx->rd, 1, ctx->s));
+    CU(axpby(n, 1.0, ctx->v, 1.0, ctx->g, ctx->s));
+    CU(add_half_sq(n, ctx->v, ctx->jo, ctx->s));
+    ctx->have_traj = 1;
+    ctx->have_rsvd = 0;
+    if (J_out) {
+        CU(cudaMemcpyAsync(J_out, ctx->jo, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+        CU(cudaStreamSynchronize(ctx->s));
+    }
+    return RIOT_OK;
+}
+
+riot_status riot_hessian_apply(riot_ctx *ctx, const void *W_dev, void *Y_dev, int64_t ld, int32_t ncols,
+                               int32_t add_identity)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_hessian_apply before riot_outer_begin");
+    if (ncols < 0 || ld < ctx->m.geom.n) return fail(ctx, RIOT_EINVAL, "bad ncols / ld");
+    if (ncols == 0) return RIOT_OK;
+    if (!W_dev || !Y_dev) return fail(ctx, RIOT_EINVAL, "null W or Y");
+    CU(cudaSetDevice(ctx->dev));
+    return hvp(ctx, W_dev, Y_dev, ld, ncols, add_identity);
+}
+
+riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const void *Omega_dev,
+                      double *lambda_out)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_rsvd before riot_outer_begin");
+    const int n = ctx->m.geom.n;
+    if (k < 1 || k > ctx->kmax || k > n) return fail(ctx, RIOT_EINVAL, "k = %d outside [1, min(kmax, n)]", k);
+    if (q < 0 || q > 64) return fail(ctx, RIOT_EINVAL, "q = %d outside [0, 64]", q);
+    CU(cudaSetDevice(ctx->dev));
+    const char tr = real_tag(ctx);
+    const size_t rs = real_size(ctx);
+    cudaStream_t s = ctx->s;
+    ctx->nev = 0;
+    CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 16, s));
+    ev_mark(ctx, -1);
+    if (Omega_dev)
+        CU(cudaMemcpyAsync(ctx->Wblk, Omega_dev, (size_t)n * k * rs, cudaMemcpyDeviceToDevice, s));
+    else
+        CU(normal_launch(ctx->seed, (uint32_t)sketch_stream, n, k, n, ctx->prec == RIOT_PREC_FP64, ctx->Wblk, s));
+    ev_mark(ctx, 0);
+    TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
+    for (int it = 0; it < q; ++it) {
+        ev_mark(ctx, 1);
+        TRY(orth(ctx, ctx->Yblk, k, 0));
+        CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
+        ev_mark(ctx, 0);
+        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
+    }
+    ev_mark(ctx, 1);
+    TRY(orth(ctx, ctx->Yblk, k, 3));
+    ev_mark(ctx, 2);
+    if (ctx->exact_rr) {
+        // K = Q^T A Q
+        CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
+        ev_mark(ctx, 0);
+        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
+        ev_mark(ctx, 2);
+        CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Km, 'd', k, s));
+    } else {
+        // K (Q^T W) = Q^T Y  <=>  K (M M^T) = N M^T with M = Q^T W, N = Q^T Y
+        CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Wblk, tr, n, 0.0, ctx->Mm, 'd', k, s));
+        CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Nm, 'd', k, s));
+        CU(gemm('N', 'T', k, k, k, 1.0, ctx->Mm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->G, 'd', k, s));
+        CU(gemm('N', 'T', k, k, k, 1.0, ctx->Nm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->Km, 'd', k, s));
+        CU(cholesky(ctx->G, k, k, 0.0, ctx->info + 6, nullptr, s));
+        CU(trsm_right_lt(ctx->Km, k, k, k, ctx->G, k, s));
+        CU(trsm_right_l(ctx->Km, k, k, k, ctx->G, k, s));
+    }
+    CU(symmetrize(ctx->Km, k, k, s));
+    ev_mark(ctx, 3);
+    CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 8, s));
+    ev_mark(ctx, 4);
+    CU(gemm('N', 'N', n, k, k, 1.0, ctx->Q, 'd', n, ctx->Z, 'd', k, 0.0, ctx->U, 'd', n, s));
+    CU(fix_col_signs(ctx->U, n, k, n, s));
+    ev_mark(ctx, -2);
+    TRY(check_cholesky(ctx, 0, 7, "riot_rsvd"));
+    int jinfo[2] = {0, 0};
+    CU(cudaMemcpyAsync(jinfo, ctx->info + 8, sizeof(jinfo), cudaMemcpyDeviceToHost, s));
+    if (lambda_out) CU(cudaMemcpyAsync(lambda_out, ctx->lam, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (jinfo[0] < 0) return fail(ctx, RIOT_ENOCONV, "Jacobi did not converge in %d sweeps", -jinfo[0]);
+    ctx->jacobi_sweeps = jinfo[0];
+    ctx->have_rsvd = 1;
+    ctx->k_last = k;
+    return RIOT_OK;
+}
+
+riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6)
+{
+    if (!ctx || !ms_out6) return RIOT_EINVAL;
+    CU(cudaStreamSynchronize(ctx->s));
+    for (int i = 0; i < 6; ++i) ms_out6[i] = 0.0;
+    for (int i = 0; i + 1 < ctx->nev; ++i) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+        const int ph = ctx->ev_phase[i];
+        if (ph >= 0 && ph < 5) ms_out6[ph] += ms;
+    }
+    if (ctx->nev >= 2) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[ctx->nev - 1]));
+        ms_out6[5] = ms;
+    }
+    return RIOT_OK;
+}
+
+riot_status riot_increment(riot_ctx *ctx, double *dv_dev, int32_t *mode_out)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->have_rsvd) return fail(ctx, RIOT_ESTATE, "riot_increment before riot_rsvd");
+    CU(cudaSetDevice(ctx->dev));
+    const int n = ctx->m.geom.n, k = ctx->k_last;
+    cudaStream_t s = ctx->s;
+    // c = U^T g; scale by the adaptive rule; dv = U c (- g for LRU)
+    CU(gemm('T', 'N', k, 1, n, 1.0, ctx->U, 'd', n, ctx->g, 'd', n, 0.0, ctx->cvec, 'd', k, s));
+    CU(increment_coef(ctx->lam, k, ctx->cvec, ctx->info + 10, s));
+    CU(gemm('N', 'N', n, 1, k, 1.0, ctx->U, 'd', n, ctx->cvec, 'd', k, 0.0, ctx->dv, 'd', n, s));
+    CU(add_if_flag(ctx->info + 10, 1, n, -1.0, ctx->g, ctx->dv, s));
+    // v += dv, x += L dv
+    CU(axpby(n, 1.0, ctx->dv, 1.0, ctx->v, s));
+    CU(bsqrt_launch(ctx->m, ctx->dv, ctx->tmp, 0, 1, s));
+    CU(axpby(n, 1.0, ctx->tmp, 1.0, ctx->x, s));
+    if (dv_dev) CU(cudaMemcpyAsync(dv_dev, ctx->dv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (mode_out) {
+        CU(cudaMemcpyAsync(mode_out, ctx->info + 10, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    return RIOT_OK;
+}
+
+riot_status riot_analysis_cov_lowrank(riot_ctx *ctx, int32_t m, double *LU_dev, double *coef_out, int32_t *mode_out)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->have_rsvd) return fail(ctx, RIOT_ESTATE, "riot_analysis_cov_lowrank before riot_rsvd");
+    if (m < 1 || m > ctx->k_last) return fail(ctx, RIOT_EINVAL, "m = %d outside [1, k]", m);
+    CU(cudaSetDevice(ctx->dev));
+    cudaStream_t s = ctx->s;
+    CU(cov_coef(ctx->lam, m, ctx->cvec, ctx->info + 10, s));
+    if (LU_dev) CU(bsqrt_launch(ctx->m, ctx->U, LU_dev, 0, m, s));
+    if (coef_out) CU(cudaMemcpyAsync(coef_out, ctx->cvec, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    if (mode_out) CU(cudaMemcpyAsync(mode_out, ctx->info + 10, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (coef_out || mode_out) CU(cudaStreamSynchronize(s));
+    return RIOT_OK;
+}
+
+riot_status riot_bsqrt_apply(riot_ctx *ctx, const double *in_dev, double *out_dev, int32_t transpose, int32_t ncols)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (ncols < 0 || (ncols > 0 && (!in_dev || !out_dev))) return fail(ctx, RIOT_EINVAL, "bad arguments");
+    CU(cudaSetDevice(ctx->dev));
+    CU(bsqrt_launch(ctx->m, in_dev, out_dev, transpose, ncols, ctx->s));
+    return RIOT_OK;
+}
+
+riot_status riot_get_state(riot_ctx *ctx, double *x_dev, double *v_dev, double *g_dev, double *U_dev, double *lambda_dev)
+{
+    if (!ctx) return RIOT_EINVAL;
+    CU(cudaSetDevice(ctx->dev));
+    const int n = ctx->m.geom.n;
+    cudaStream_t s = ctx->s;
+    if (x_dev) CU(cudaMemcpyAsync(x_dev, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (v_dev) CU(cudaMemcpyAsync(v_dev, ctx->v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (g_dev) CU(cudaMemcpyAsync(g_dev, ctx->g, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if ((U_dev || lambda_dev) && !ctx->have_rsvd) return fail(ctx, RIOT_ESTATE, "no eigenpairs yet");
+    if (U_dev) CU(cudaMemcpyAsync(U_dev, ctx->U, sizeof(double) * n * ctx->k_last, cudaMemcpyDeviceToDevice, s));
+    if (lambda_dev) CU(cudaMemcpyAsync(lambda_dev, ctx->lam, sizeof(double) * ctx->k_last, cudaMemcpyDeviceToDevice, s));
+    return RIOT_OK;
+}
+
+riot_status riot_draw_normal(uint64_t seed, int64_t stream, int64_t n, int32_t ncols, int64_t ld, int32_t is_double,
+                             void *out_dev, void *cuda_stream)
+{
+    if (n < 0 || ncols < 0 || ld < n || (n * ncols > 0 && !out_dev)) return RIOT_EINVAL;
+    cudaError_t e = normal_launch(seed, (uint32_t)stream, n, ncols, ld, is_double, out_dev, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? RIOT_OK : RIOT_ECUDA;
+}
+
+riot_status riot_l96_forecast(int64_t n, int32_t T, double dt, double F, const double *x0_dev, double *traj_dev,
+                              int32_t store_all, void *cuda_stream)
+{
+    if (n < 16 || n > 8192 || T < 0 || !(dt > 0.0) || !x0_dev || !traj_dev) return RIOT_EINVAL;
+    L96Dev m;
+    if (!choose_geom((int)n, &m.geom)) return RIOT_EINVAL;
+    m.T = T;
+    m.dt = dt;
+    m.F = F;
+    m.p = 0;
+    cudaError_t e = l96_nl_launch(m, x0_dev, store_all ? traj_dev : nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  store_all ? nullptr : traj_dev, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? RIOT_OK : RIOT_ECUDA;
+}
+
+}  // extern "C"

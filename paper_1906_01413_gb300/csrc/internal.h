@@ -1,0 +1,147 @@
+// Internal declarations shared by the translation units of the RIOT library.
+// Nothing here is part of the public C ABI (include/riot.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/riot.h"
+
+namespace riot {
+
+// ---------------------------------------------------------------------------
+// Chunked layout of one Lorenz-96 state across the threads that own it.
+// Thread t of a probe holds len(t) consecutive variables starting at
+// start(t); len is E for the first Tp-g threads and E-1 for the last g.
+// Per-thread arrays ("slots") are padded to E: slot = t*E + j.
+// ---------------------------------------------------------------------------
+struct ChunkGeom {
+    int n = 0;   // variables
+    int E = 0;   // elements per thread (template parameter of the kernels)
+    int Tp = 0;  // threads per probe
+    int g = 0;   // number of short (E-1) chunks, at the end
+    int Np = 0;  // Tp*E
+    __host__ __device__ int start(int t) const {
+        int over = t - (Tp - g);
+        return t * E - (over > 0 ? over : 0);
+    }
+    __host__ __device__ int len(int t) const { return t < Tp - g ? E : E - 1; }
+    // slot of variable i
+    __host__ __device__ int slot(int i) const {
+        int full = (Tp - g) * E;
+        if (i < full) return i;
+        int r = i - full;
+        int t = (Tp - g) + r / (E - 1);
+        return t * E + r % (E - 1);
+    }
+};
+
+// Pick E in {4, 8, 16} and fill the geometry; returns false if n is out of range.
+bool choose_geom(int n, ChunkGeom *geom);
+
+// Gaussian square-root band (L = diag(sigma) S, S symmetric circulant):
+// S_d for d in [-hl, hh], stored at band[d + hl].
+struct Band {
+    int hl = 0, hh = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Lorenz-96 kernels (l96.cu)
+// ---------------------------------------------------------------------------
+struct L96Dev {
+    ChunkGeom geom;
+    int T = 0;
+    double dt = 0, F = 0;
+    // observations, sorted by step
+    int p = 0;
+    const int *optr = nullptr;    // [T+2]: obs of step t are optr[t] .. optr[t+1]-1
+    const int *oslot = nullptr;   // [p] slot of the observed variable
+    const int *oidx = nullptr;    // [p] observed variable
+    const double *y = nullptr;    // [p]
+    const double *rinv64 = nullptr;  // [p] 1/sigma^2
+    const float *rinv32 = nullptr;
+    // prior square root
+    Band band;
+    const double *band64 = nullptr;
+    const float *band32 = nullptr;
+    const double *sig64 = nullptr;   // [n]
+    const float *sig32 = nullptr;
+};
+
+// Nonlinear FP64 trajectory of one state; writes traj (T+1)*n (natural
+// layout, may be null), stage coefficients (float2 / double2, may be null),
+// the innovation d = H(x) - y (may be null) and 1/2 sum d^2/sigma^2 into
+// *jo (may be null, accumulated with atomicAdd: zero it first).
+cudaError_t l96_nl_launch(const L96Dev &m, const double *x0, double *traj, float2 *coef32,
+                          double2 *coef64, double *d, double *jo, double *xT, cudaStream_t s);
+
+// Batched Hessian-vector product.  mode 0: Y = A W (+W); mode 1: adjoint only
+// with the given forcing r (one column, length p): Y = L^T lambda_0;
+// mode 2: tangent linear only: r = R^-1 H M L W.
+cudaError_t l96_hvp_launch_f32(const L96Dev &m, const float2 *coef, const float *W, float *Y,
+                               int64_t ld, int ncols, int add_identity, float *r, int mode,
+                               cudaStream_t s);
+cudaError_t l96_hvp_launch_f64(const L96Dev &m, const double2 *coef, const double *W, double *Y,
+                               int64_t ld, int ncols, int add_identity, double *r, int mode,
+                               cudaStream_t s);
+
+// out = L in or L^T in (FP64), ncols columns (ld = n)
+cudaError_t bsqrt_launch(const L96Dev &m, const double *in, double *out, int transpose, int ncols,
+                         cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Random numbers (rng.cu)
+// ---------------------------------------------------------------------------
+cudaError_t normal_launch(uint64_t seed, uint32_t stream, int64_t n, int ncols, int64_t ld,
+                          int is_double, void *out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Dense linear algebra, column-major (linalg.cu)
+// ---------------------------------------------------------------------------
+// C = alpha op(A) op(B) + beta C with double accumulation.
+// Types: 'f' float, 'd' double for A, B and C.
+cudaError_t gemm(char ta, char tb, int m, int n, int k, double alpha, const void *A, char tA,
+                 int64_t lda, const void *B, char tB, int64_t ldb, double beta, void *C, char tC,
+                 int64_t ldc, cudaStream_t s);
+cudaError_t convert_block(const void *in, char tin, int64_t ldin, void *out, char tout, int64_t ldout,
+                          int64_t rows, int cols, cudaStream_t s);
+// In-place blocked Cholesky of the k x k SPD matrix G (lower factor); adds
+// shift_scale * trace(G) to the diagonal first when shift_scale > 0.
+// info[0] = 0 on success, else 1 + first failing pivot.
+cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *scratch,
+                     cudaStream_t s);
+// X <- X L^-T (X: m x k, L: k x k lower Cholesky factor): right-side solve.
+cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl,
+                          cudaStream_t s);
+// X <- X L^-1 (L lower, non-unit): right-side solve.
+cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl,
+                         cudaStream_t s);
+// Symmetric eigendecomposition by parallel cyclic Jacobi (cooperative
+// launch).  A (k x k, ld = k) is destroyed; lam gets eigenvalues sorted in
+// decreasing order, Z (k x k, ld = k) the eigenvectors with the
+// largest-magnitude entry of each made positive.  work: 3*k*k + 64 doubles
+// (ke = k rounded up to even).  info[0] = number of sweeps (< 0: no convergence).
+cudaError_t jacobi_eig(double *A, int k, double *lam, double *Z, double *work, int *info,
+                       cudaStream_t s);
+size_t jacobi_work_doubles(int k);
+// elementwise helpers
+cudaError_t symmetrize(double *A, int k, int64_t lda, cudaStream_t s);
+cudaError_t transpose_sq(const double *A, double *B, int k, cudaStream_t s);
+cudaError_t axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s);
+// increment helper: c (k) -> scaled coefficients by mode; writes mode to *mode_dev
+cudaError_t increment_coef(const double *lam, int k, double *c, int *mode_dev, cudaStream_t s);
+cudaError_t cov_coef(const double *lam, int m, double *coef, int *mode_dev, cudaStream_t s);
+cudaError_t check_finite(const double *x, int64_t n, int *flag, cudaStream_t s);
+// y += a x when flag[0] == want (flag read on the device)
+cudaError_t add_if_flag(const int *flag, int want, int64_t n, double a, const double *x, double *y, cudaStream_t s);
+cudaError_t mul(int64_t n, const double *a, const double *b, double *out, cudaStream_t s);
+cudaError_t add_half_sq(int64_t n, const double *x, double *out, cudaStream_t s);
+// largest-magnitude entry of each of the k columns made positive
+cudaError_t fix_col_signs(double *U, int64_t n, int k, int64_t ld, cudaStream_t s);
+
+int num_sms();
+// host-side count of kernel launches issued by the library
+void count_launch();
+unsigned long long launches_total();
+
+}  // namespace riot

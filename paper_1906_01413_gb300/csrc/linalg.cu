@@ -1,0 +1,720 @@
+// Dense linear algebra of the RIOT inner loop (column-major, FP64 arithmetic).
+//
+// The k x k pieces of Algorithm 3 (Gram matrices of CholeskyQR, Cholesky,
+// the projected matrix K and its eigendecomposition) and the n x k x k
+// products around them.  GB300 runs FP64 on the CUDA cores only, so these
+// kernels are plain tiled SIMT code whose bound is the FP64 FMA rate; they
+// are spread across all SMs (tile grids, row-parallel triangular solves,
+// one cooperative Jacobi launch) rather than run in one CTA.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace riot {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+int num_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// ---------------------------------------------------------------------------
+// GEMM: C = alpha op(A) op(B) + beta C, double accumulation.
+// 32 x 32 output tile per CTA, 256 threads, 2 x 2 outputs per thread.
+// ---------------------------------------------------------------------------
+template <typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(256) gemm_kernel(int ta, int tb, int m, int n, int K, double alpha,
+                                                   const TA *__restrict__ A, long long lda,
+                                                   const TB *__restrict__ B, long long ldb, double beta,
+                                                   TC *__restrict__ C, long long ldc)
+{
+    constexpr int BM = 32, BN = 32, BK = 32;
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = tid + 256 * r;
+            // A tile: op(A)[i][kk], i in [m0, m0+32), kk in [k0, k0+32)
+            int i, kk;
+            if (!ta) { i = idx & 31; kk = idx >> 5; } else { kk = idx & 31; i = idx >> 5; }
+            double va = 0.0;
+            if (m0 + i < m && k0 + kk < K)
+                va = ta ? (double)A[(k0 + kk) + (long long)(m0 + i) * lda]
+                        : (double)A[(m0 + i) + (long long)(k0 + kk) * lda];
+            As[kk][i] = va;
+            // B tile: op(B)[kk][j]
+            int j;
+            if (!tb) { kk = idx & 31; j = idx >> 5; } else { j = idx & 31; kk = idx >> 5; }
+            double vb = 0.0;
+            if (n0 + j < n && k0 + kk < K)
+                vb = tb ? (double)B[(n0 + j) + (long long)(k0 + kk) * ldb]
+                        : (double)B[(k0 + kk) + (long long)(n0 + j) * ldb];
+            Bs[kk][j] = vb;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
+            const double a0 = As[kk][tx], a1 = As[kk][tx + 16];
+            const double b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int i = m0 + tx + 16 * r, j = n0 + ty + 16 * c;
+            if (i < m && j < n) {
+                TC *p = C + i + (long long)j * ldc;
+                const double old = (beta != 0.0) ? (double)*p : 0.0;
+                *p = (TC)(alpha * acc[r][c] + beta * old);
+            }
+        }
+}
+
+template <typename TA, typename TB, typename TC>
+static cudaError_t gemm_t(int ta, int tb, int m, int n, int k, double alpha, const void *A, int64_t lda,
+                          const void *B, int64_t ldb, double beta, void *C, int64_t ldc, cudaStream_t s)
+{
+    dim3 grid((m + 31) / 32, (n + 31) / 32);
+    count_launch();
+    gemm_kernel<TA, TB, TC><<<grid, 256, 0, s>>>(ta, tb, m, n, k, alpha, (const TA *)A, lda, (const TB *)B, ldb,
+                                                 beta, (TC *)C, ldc);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm(char ta, char tb, int m, int n, int k, double alpha, const void *A, char tA, int64_t lda,
+                 const void *B, char tB, int64_t ldb, double beta, void *C, char tC, int64_t ldc, cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    const int a = (ta == 'T'), b = (tb == 'T');
+#define RIOT_GEMM_CASE(XA, XB, XC, TA_, TB_, TC_) \
+    if (tA == XA && tB == XB && tC == XC) return gemm_t<TA_, TB_, TC_>(a, b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    RIOT_GEMM_CASE('d', 'd', 'd', double, double, double)
+    RIOT_GEMM_CASE('f', 'd', 'd', float, double, double)
+    RIOT_GEMM_CASE('d', 'f', 'd', double, float, double)
+    RIOT_GEMM_CASE('f', 'f', 'd', float, float, double)
+    RIOT_GEMM_CASE('d', 'd', 'f', double, double, float)
+    RIOT_GEMM_CASE('f', 'd', 'f', float, double, float)
+#undef RIOT_GEMM_CASE
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Block conversion / copy
+// ---------------------------------------------------------------------------
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI *in, int64_t ldin, TO *out, int64_t ldout, int64_t rows, int cols)
+{
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / rows, i = e - j * rows;
+        out[i + j * ldout] = (TO)in[i + j * ldin];
+    }
+}
+
+cudaError_t convert_block(const void *in, char tin, int64_t ldin, void *out, char tout, int64_t ldout, int64_t rows,
+                          int cols, cudaStream_t s)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    int blocks = (int)((rows * cols + 255) / 256);
+    if (blocks > 8192) blocks = 8192;
+    if (tin == 'f' && tout == 'd')
+        { count_launch(); convert_kernel<float, double><<<blocks, 256, 0, s>>>((const float *)in, ldin, (double *)out, ldout, rows, cols); }
+    else if (tin == 'd' && tout == 'f')
+        { count_launch(); convert_kernel<double, float><<<blocks, 256, 0, s>>>((const double *)in, ldin, (float *)out, ldout, rows, cols); }
+    else if (tin == 'd' && tout == 'd')
+        { count_launch(); convert_kernel<double, double><<<blocks, 256, 0, s>>>((const double *)in, ldin, (double *)out, ldout, rows, cols); }
+    else if (tin == 'f' && tout == 'f')
+        { count_launch(); convert_kernel<float, float><<<blocks, 256, 0, s>>>((const float *)in, ldin, (float *)out, ldout, rows, cols); }
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky (blocked, right-looking, nb = 32)
+// ---------------------------------------------------------------------------
+constexpr int NB = 32;
+
+// G_ii += shift_scale * trace(G)  (one CTA)
+__global__ void shift_diag_kernel(double *G, int k, int64_t ldg, double shift_scale)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) s += G[i + i * ldg];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+        red[0] = t;
+    }
+    __syncthreads();
+    const double sh = shift_scale * red[0];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) G[i + i * ldg] += sh;
+}
+
+// Unblocked Cholesky of the jb x jb diagonal block at (J, J); records the
+// first failing pivot in info (1-based) and continues with pivot 1.
+__global__ void potrf_diag_kernel(double *G, int64_t ldg, int J, int jb, int *info)
+{
+    __shared__ double a[NB][NB + 1];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < jb * jb; e += blockDim.x) {
+        const int i = e % jb, j = e / jb;
+        a[i][j] = G[(J + i) + (int64_t)(J + j) * ldg];
+    }
+    __syncthreads();
+    for (int j = 0; j < jb; ++j) {
+        if (tid == 0) {
+            double d = a[j][j];
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (info[0] == 0) info[0] = J + j + 1;
+                d = 1.0;
+            }
+            a[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        const double djj = a[j][j];
+        for (int i = j + 1 + tid; i < jb; i += blockDim.x) a[i][j] /= djj;
+        __syncthreads();
+        for (int e = tid; e < (jb - j - 1) * (jb - j - 1); e += blockDim.x) {
+            const int i = j + 1 + e % (jb - j - 1), c = j + 1 + e / (jb - j - 1);
+            if (c <= i) a[i][c] -= a[i][j] * a[c][j];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < jb * jb; e += blockDim.x) {
+        const int i = e % jb, j = e / jb;
+        G[(J + i) + (int64_t)(J + j) * ldg] = (j <= i) ? a[i][j] : 0.0;
+    }
+}
+
+// X[r, 0:jb] <- X[r, 0:jb] L^-T for each row r (L = the jb x jb lower block
+// at Ld with leading dimension ldl): forward substitution per row.
+__global__ void trsm_rows_lt_kernel(double *X, int m, int64_t ldx, const double *Ld, int64_t ldl, int jb)
+{
+    __shared__ double Ls[NB][NB + 1];
+    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+        const int i = e % jb, j = e / jb;
+        Ls[i][j] = Ld[i + (int64_t)j * ldl];
+    }
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < jb) x[j] = X[r + (int64_t)j * ldx];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < jb) {
+            double v = x[j];
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+                if (i < j) v -= x[i] * Ls[j][i];
+            x[j] = v / Ls[j][j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < jb) X[r + (int64_t)j * ldx] = x[j];
+}
+
+// X[r, 0:jb] <- X[r, 0:jb] L^-1 (L lower): backward substitution per row.
+__global__ void trsm_rows_l_kernel(double *X, int m, int64_t ldx, const double *Ld, int64_t ldl, int jb)
+{
+    __shared__ double Ls[NB][NB + 1];
+    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+        const int i = e % jb, j = e / jb;
+        Ls[i][j] = Ld[i + (int64_t)j * ldl];
+    }
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < jb) x[j] = X[r + (int64_t)j * ldx];
+#pragma unroll
+    for (int jj = NB - 1; jj >= 0; --jj) {
+        if (jj < jb) {
+            double v = x[jj];
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+                if (i > jj && i < jb) v -= x[i] * Ls[i][jj];
+            x[jj] = v / Ls[jj][jj];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < jb) X[r + (int64_t)j * ldx] = x[j];
+}
+
+cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if (shift_scale > 0.0) { count_launch(); shift_diag_kernel<<<1, 1024, 0, s>>>(G, k, ldg, shift_scale); }
+    for (int J = 0; J < k; J += NB) {
+        const int jb = (k - J < NB) ? k - J : NB;
+        { count_launch(); potrf_diag_kernel<<<1, 256, 0, s>>>(G, ldg, J, jb, info); }
+        const int m2 = k - J - jb;
+        if (m2 > 0) {
+            double *A21 = G + (J + jb) + (int64_t)J * ldg;
+            { count_launch(); trsm_rows_lt_kernel<<<(m2 + 127) / 128, 128, 0, s>>>(A21, m2, ldg, G + J + (int64_t)J * ldg, ldg, jb); }
+            double *A22 = G + (J + jb) + (int64_t)(J + jb) * ldg;
+            e = gemm('N', 'T', m2, m2, jb, -1.0, A21, 'd', ldg, A21, 'd', ldg, 1.0, A22, 'd', ldg, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    // zero the strict upper triangle so that G holds exactly the factor L
+    return cudaGetLastError();
+}
+
+cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s)
+{
+    for (int J = 0; J < k; J += NB) {
+        const int jb = (k - J < NB) ? k - J : NB;
+        count_launch();
+        trsm_rows_lt_kernel<<<(m + 127) / 128, 128, 0, s>>>(X + (int64_t)J * ldx, m, ldx, L + J + (int64_t)J * ldl,
+                                                          ldl, jb);
+        const int rest = k - J - jb;
+        if (rest > 0) {
+            cudaError_t e = gemm('N', 'T', m, rest, jb, -1.0, X + (int64_t)J * ldx, 'd', ldx,
+                                 L + (J + jb) + (int64_t)J * ldl, 'd', ldl, 1.0, X + (int64_t)(J + jb) * ldx, 'd',
+                                 ldx, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s)
+{
+    const int nblk = (k + NB - 1) / NB;
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int J = b * NB;
+        const int jb = (k - J < NB) ? k - J : NB;
+        count_launch();
+        trsm_rows_l_kernel<<<(m + 127) / 128, 128, 0, s>>>(X + (int64_t)J * ldx, m, ldx, L + J + (int64_t)J * ldl,
+                                                         ldl, jb);
+        if (J > 0) {
+            cudaError_t e = gemm('N', 'N', m, J, jb, -1.0, X + (int64_t)J * ldx, 'd', ldx, L + J, 'd', ldl, 1.0, X,
+                                 'd', ldx, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric eigendecomposition: parallel cyclic Jacobi (round-robin pairs).
+// Each round applies ke/2 disjoint rotations at once: A <- J^T A J on 2 x 2
+// blocks (double-buffered), V <- V J.  A sweep is ke-1 rounds; iteration
+// stops after a sweep in which no pair needed a rotation, i.e.
+// |a_pq| <= tol * sqrt(|a_pp a_qq|) everywhere (relative-accuracy
+// threshold of Demmel & Veselic).
+// ---------------------------------------------------------------------------
+size_t jacobi_work_doubles(int k)
+{
+    const size_t ke = (size_t)(k + (k & 1));
+    return 3 * ke * ke + 256;
+}
+
+__device__ __forceinline__ int rr_player(int x, int r, int ke)
+{
+    return x == 0 ? 0 : ((x - 1 + r) % (ke - 1)) + 1;
+}
+
+__device__ __forceinline__ void jac_rot(double app, double aqq, double apq, double tol, double floor_abs, double &c,
+                                        double &s, bool &rot)
+{
+    if (fabs(apq) <= tol * sqrt(fabs(app * aqq)) || fabs(apq) <= floor_abs) {
+        c = 1.0; s = 0.0; rot = false;
+        return;
+    }
+    const double tau = (aqq - app) / (2.0 * apq);
+    const double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+    c = 1.0 / sqrt(1.0 + t * t);
+    s = t * c;
+    rot = true;
+}
+
+__global__ void jacobi_init_kernel(const double *K, int k, int ke, double *A0, double *V)
+{
+    const int64_t total = (int64_t)ke * ke;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % ke), j = (int)(e / ke);
+        A0[e] = (i < k && j < k) ? 0.5 * (K[i + (int64_t)j * k] + K[j + (int64_t)i * k]) : 0.0;
+        V[e] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) jacobi_kernel(double *Abuf, double *V, int ke, double tol, int maxsweeps,
+                                                     int *counters, int *info)
+{
+    cg::grid_group grid = cg::this_grid();
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int half = ke / 2;
+    double *Ain = Abuf, *Aout = Abuf + (int64_t)ke * ke;
+    // ||A||_F^2 for the absolute rotation floor (rounding level of the input)
+    double *frob = (double *)(counters + 128);
+    double part = 0.0;
+    for (int64_t e = gtid; e < (int64_t)ke * ke; e += nthreads) part += Ain[e] * Ain[e];
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(frob, part);
+    grid.sync();
+    const double floor_abs = 1e-17 * sqrt(*((volatile double *)frob));
+    int sweep = 0;
+    for (; sweep < maxsweeps; ++sweep) {
+        int myrot = 0;
+        for (int r = 0; r < ke - 1; ++r) {
+            // A <- J^T A J on all 2 x 2 blocks
+            for (int64_t e = gtid; e < (int64_t)half * half; e += nthreads) {
+                const int P = (int)(e % half), Q = (int)(e / half);
+                int p = rr_player(P, r, ke), q = rr_player(ke - 1 - P, r, ke);
+                if (p > q) { int tmp = p; p = q; q = tmp; }
+                int u = rr_player(Q, r, ke), w = rr_player(ke - 1 - Q, r, ke);
+                if (u > w) { int tmp = u; u = w; w = tmp; }
+                double cP, sP, cQ, sQ;
+                bool rP, rQ;
+                jac_rot(Ain[p + (int64_t)p * ke], Ain[q + (int64_t)q * ke], Ain[p + (int64_t)q * ke], tol, floor_abs, cP, sP, rP);
+                jac_rot(Ain[u + (int64_t)u * ke], Ain[w + (int64_t)w * ke], Ain[u + (int64_t)w * ke], tol, floor_abs, cQ, sQ, rQ);
+                if (P == Q && rP) ++myrot;
+                const double apu = Ain[p + (int64_t)u * ke], apw = Ain[p + (int64_t)w * ke];
+                const double aqu = Ain[q + (int64_t)u * ke], aqw = Ain[q + (int64_t)w * ke];
+                // T = blk R_Q
+                const double t00 = apu * cQ - apw * sQ, t01 = apu * sQ + apw * cQ;
+                const double t10 = aqu * cQ - aqw * sQ, t11 = aqu * sQ + aqw * cQ;
+                // R_P^T T
+                double n00 = cP * t00 - sP * t10, n01 = cP * t01 - sP * t11;
+                double n10 = sP * t00 + cP * t10, n11 = sP * t01 + cP * t11;
+                if (P == Q && rP) { n01 = 0.0; n10 = 0.0; }
+                Aout[p + (int64_t)u * ke] = n00;
+                Aout[p + (int64_t)w * ke] = n01;
+                Aout[q + (int64_t)u * ke] = n10;
+                Aout[q + (int64_t)w * ke] = n11;
+            }
+            // V <- V J
+            for (int64_t e = gtid; e < (int64_t)ke * half; e += nthreads) {
+                const int i = (int)(e % ke), P = (int)(e / ke);
+                int p = rr_player(P, r, ke), q = rr_player(ke - 1 - P, r, ke);
+                if (p > q) { int tmp = p; p = q; q = tmp; }
+                double c, s;
+                bool rot;
+                jac_rot(Ain[p + (int64_t)p * ke], Ain[q + (int64_t)q * ke], Ain[p + (int64_t)q * ke], tol, floor_abs, c, s, rot);
+                if (rot) {
+                    const double vp = V[i + (int64_t)p * ke], vq = V[i + (int64_t)q * ke];
+                    V[i + (int64_t)p * ke] = vp * c - vq * s;
+                    V[i + (int64_t)q * ke] = vp * s + vq * c;
+                }
+            }
+            grid.sync();
+            double *tmp = Ain; Ain = Aout; Aout = tmp;
+        }
+        if (myrot) atomicAdd(&counters[sweep], myrot);
+        grid.sync();
+        const int nrot = *((volatile int *)&counters[sweep]);
+        if (nrot == 0) break;
+    }
+    if (gtid == 0) {
+        info[0] = (sweep < maxsweeps) ? sweep + 1 : -maxsweeps;
+        info[1] = (Ain == Abuf) ? 0 : 1;   // which buffer holds the result
+    }
+}
+
+// Sort eigenvalues descending (stable by index), gather eigenvectors with sign fix.
+__global__ void jacobi_finish_kernel(const double *Abuf, const double *V, const int *info, int k, int ke, double *lam,
+                                     double *Z)
+{
+    const double *A = Abuf + (info[1] ? (int64_t)ke * ke : 0);
+    const int i = blockIdx.x;  // one CTA per eigenpair (source index i)
+    if (i >= k) return;
+    const double li = A[i + (int64_t)i * ke];
+    __shared__ int rank_s;
+    __shared__ double best_s[32];
+    __shared__ int bidx_s[32];
+    if (threadIdx.x == 0) rank_s = 0;
+    __syncthreads();
+    int cnt = 0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const double lj = A[j + (int64_t)j * ke];
+        if (lj > li || (lj == li && j < i)) ++cnt;
+    }
+    atomicAdd(&rank_s, cnt);
+    // sign: largest-magnitude component positive (first one on ties)
+    double best = -1.0;
+    int bidx = 0;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+        const double v = fabs(V[r + (int64_t)i * ke]);
+        if (v > best) { best = v; bidx = r; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { best_s[threadIdx.x >> 5] = best; bidx_s[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x + 31) / 32; ++w)
+            if (best_s[w] > best_s[0] || (best_s[w] == best_s[0] && bidx_s[w] < bidx_s[0])) {
+                best_s[0] = best_s[w];
+                bidx_s[0] = bidx_s[w];
+            }
+    }
+    __syncthreads();
+    const double sgn = (V[bidx_s[0] + (int64_t)i * ke] < 0.0) ? -1.0 : 1.0;
+    const int rk = rank_s;
+    if (threadIdx.x == 0) lam[rk] = li;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) Z[r + (int64_t)rk * k] = sgn * V[r + (int64_t)i * ke];
+}
+
+cudaError_t jacobi_eig(double *K, int k, double *lam, double *Z, double *work, int *info, cudaStream_t s)
+{
+    const int ke = k + (k & 1);
+    double *Abuf = work;                         // 2 ke^2
+    double *V = work + 2 * (size_t)ke * ke;       // ke^2
+    int *counters = (int *)(V + (size_t)ke * ke); // 128 ints, then the Frobenius accumulator
+    const int maxsweeps = 60;
+    cudaError_t e = cudaMemsetAsync(counters, 0, 128 * sizeof(int) + 2 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    { count_launch(); jacobi_init_kernel<<<256, 256, 0, s>>>(K, k, ke, Abuf, V); }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ke >= 2) {
+        int dev = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 256, 0);
+        if (per_sm < 1) per_sm = 1;
+        int need = (int)(((int64_t)ke * (ke / 2) + 255) / 256);
+        int grid = num_sms() * per_sm;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        double tol = 1e-15 * (double)(k > 16 ? k : 16) * 0.0625;
+        void *args[] = {&Abuf, &V, (void *)&ke, &tol, (void *)&maxsweeps, &counters, &info};
+        count_launch();
+        e = cudaLaunchCooperativeKernel((void *)jacobi_kernel, grid, 256, args, 0, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        int one[2] = {1, 0};
+        e = cudaMemcpyAsync(info, one, sizeof(one), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    { count_launch(); jacobi_finish_kernel<<<k, 128, 0, s>>>(Abuf, V, info, k, ke, lam, Z); }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Small elementwise helpers
+// ---------------------------------------------------------------------------
+__global__ void symmetrize_kernel(double *A, int k, int64_t lda)
+{
+    const int64_t total = (int64_t)k * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % k), j = (int)(e / k);
+        if (i < j) {
+            const double v = 0.5 * (A[i + j * lda] + A[j + i * lda]);
+            A[i + j * lda] = v;
+            A[j + i * lda] = v;
+        }
+    }
+}
+
+cudaError_t symmetrize(double *A, int k, int64_t lda, cudaStream_t s)
+{
+    { count_launch(); symmetrize_kernel<<<256, 256, 0, s>>>(A, k, lda); }
+    return cudaGetLastError();
+}
+
+__global__ void transpose_kernel(const double *A, double *B, int k)
+{
+    const int64_t total = (int64_t)k * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % k), j = (int)(e / k);
+        B[j + (int64_t)i * k] = A[e];
+    }
+}
+
+cudaError_t transpose_sq(const double *A, double *B, int k, cudaStream_t s)
+{
+    { count_launch(); transpose_kernel<<<256, 256, 0, s>>>(A, B, k); }
+    return cudaGetLastError();
+}
+
+__global__ void axpby_kernel(int64_t n, double a, const double *x, double b, double *y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+
+cudaError_t axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s)
+{
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) return cudaSuccess;
+    { count_launch(); axpby_kernel<<<blocks, 256, 0, s>>>(n, a, x, b, y); }
+    return cudaGetLastError();
+}
+
+// c_i <- -c_i / (1 + l_i) (LRA, smallest retained lambda > 1) or
+// c_i <- c_i l_i / (1 + l_i) (LRU); mode written to mode_dev.
+__global__ void increment_coef_kernel(const double *lam, int k, double *c, int *mode_dev)
+{
+    const int mode = (lam[k - 1] > 1.0) ? 0 : 1;
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+        c[i] = mode == 0 ? -c[i] / (1.0 + lam[i]) : c[i] * lam[i] / (1.0 + lam[i]);
+    if (threadIdx.x == 0) mode_dev[0] = mode;
+}
+
+cudaError_t increment_coef(const double *lam, int k, double *c, int *mode_dev, cudaStream_t s)
+{
+    { count_launch(); increment_coef_kernel<<<1, 1024, 0, s>>>(lam, k, c, mode_dev); }
+    return cudaGetLastError();
+}
+
+__global__ void cov_coef_kernel(const double *lam, int m, double *coef, int *mode_dev)
+{
+    const int mode = (lam[m - 1] > 1.0) ? 0 : 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+        coef[i] = mode == 0 ? 1.0 / (1.0 + lam[i]) : lam[i] / (1.0 + lam[i]);
+    if (threadIdx.x == 0) mode_dev[0] = mode;
+}
+
+cudaError_t cov_coef(const double *lam, int m, double *coef, int *mode_dev, cudaStream_t s)
+{
+    { count_launch(); cov_coef_kernel<<<1, 1024, 0, s>>>(lam, m, coef, mode_dev); }
+    return cudaGetLastError();
+}
+
+__global__ void check_finite_kernel(const double *x, int64_t n, int *flag)
+{
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(x[i])) bad = 1;
+    if (bad) atomicOr(flag, 1);
+}
+
+__global__ void add_if_flag_kernel(const int *flag, int want, int64_t n, double a, const double *x, double *y)
+{
+    if (flag[0] != want) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
+cudaError_t add_if_flag(const int *flag, int want, int64_t n, double a, const double *x, double *y, cudaStream_t s)
+{
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) return cudaSuccess;
+    { count_launch(); add_if_flag_kernel<<<blocks, 256, 0, s>>>(flag, want, n, a, x, y); }
+    return cudaGetLastError();
+}
+
+__global__ void mul_kernel(int64_t n, const double *a, const double *b, double *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] * b[i];
+}
+
+cudaError_t mul(int64_t n, const double *a, const double *b, double *out, cudaStream_t s)
+{
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) return cudaSuccess;
+    { count_launch(); mul_kernel<<<blocks, 256, 0, s>>>(n, a, b, out); }
+    return cudaGetLastError();
+}
+
+// out[0] += 0.5 * sum x_i^2
+__global__ void half_sq_kernel(int64_t n, const double *x, double *out)
+{
+    double part = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        part += x[i] * x[i];
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(out, 0.5 * part);
+}
+
+cudaError_t add_half_sq(int64_t n, const double *x, double *out, cudaStream_t s)
+{
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 256) blocks = 256;
+    if (blocks < 1) return cudaSuccess;
+    { count_launch(); half_sq_kernel<<<blocks, 256, 0, s>>>(n, x, out); }
+    return cudaGetLastError();
+}
+
+// Make the largest-magnitude entry of every column positive (first index on ties).
+__global__ void fix_col_signs_kernel(double *U, int64_t n, int64_t ld)
+{
+    __shared__ double best_s[32];
+    __shared__ int64_t bidx_s[32];
+    double *u = U + (int64_t)blockIdx.x * ld;
+    double best = -1.0;
+    int64_t bidx = 0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+        const double v = fabs(u[r]);
+        if (v > best) { best = v; bidx = r; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int64_t oi = __shfl_down_sync(0xffffffffu, bidx, off);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { best_s[threadIdx.x >> 5] = best; bidx_s[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x + 31) / 32; ++w)
+            if (best_s[w] > best_s[0] || (best_s[w] == best_s[0] && bidx_s[w] < bidx_s[0])) {
+                best_s[0] = best_s[w];
+                bidx_s[0] = bidx_s[w];
+            }
+    }
+    __syncthreads();
+    if (u[bidx_s[0]] < 0.0)
+        for (int64_t r = threadIdx.x; r < n; r += blockDim.x) u[r] = -u[r];
+}
+
+cudaError_t fix_col_signs(double *U, int64_t n, int k, int64_t ld, cudaStream_t s)
+{
+    if (k <= 0) return cudaSuccess;
+    { count_launch(); fix_col_signs_kernel<<<k, 256, 0, s>>>(U, n, ld); }
+    return cudaGetLastError();
+}
+
+cudaError_t check_finite(const double *x, int64_t n, int *flag, cudaStream_t s)
+{
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) return cudaSuccess;
+    { count_launch(); check_finite_kernel<<<blocks, 256, 0, s>>>(x, n, flag); }
+    return cudaGetLastError();
+}
+
+}  // namespace riot

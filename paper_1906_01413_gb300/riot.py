@@ -1,0 +1,228 @@
+"""Python binding of the RIOT C ABI (include/riot.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes
+device pointers of torch tensors (torch is used for device memory and
+streams only).  There is no fallback: if libriot.so is missing or fails to
+load, ``load()`` raises.
+"""
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_uint64, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libriot.so")
+
+RIOT_OK = 0
+RIOT_MODEL_L96 = 1
+RIOT_B_GAUSS_RING = 1
+RIOT_PREC_MIXED = 0
+RIOT_PREC_FP64 = 1
+STATUS = {0: "RIOT_OK", -1: "RIOT_EINVAL", -2: "RIOT_ENOMEM", -3: "RIOT_ECUDA", -4: "RIOT_ENOTSPD",
+          -5: "RIOT_ETIMEOUT", -6: "RIOT_ESTATE", -7: "RIOT_ENOCONV", -8: "RIOT_ENONFINITE"}
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("T", c_int32), ("n", c_int64), ("dt", c_double), ("F", c_double)]
+
+
+class ObsDesc(ctypes.Structure):
+    _fields_ = [("p", c_int64), ("step", POINTER(c_int32)), ("idx", POINTER(c_int32)),
+                ("y", POINTER(c_double)), ("sigma", POINTER(c_double))]
+
+
+class BcovDesc(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("reserved", c_int32), ("length", c_double), ("sigma_b", c_double),
+                ("sigma_vec", POINTER(c_double))]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("kmax", c_int32), ("exact_rr", c_int32), ("reserved", c_int32),
+                ("seed", c_uint64)]
+
+
+class RiotError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__("%s returned %s: %s" % (fn, STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libriot.so (built in-tree by ``build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libriot.so is not built (%s); run __graft_entry__.build() or "
+                           "python -m paper_1906_01413_gb300.build" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp = c_void_p
+    L.riot_setup.argtypes = [POINTER(vp), POINTER(ModelDesc), POINTER(ObsDesc), POINTER(BcovDesc),
+                             POINTER(Options), vp]
+    L.riot_outer_begin.argtypes = [vp, vp, vp, POINTER(c_double)]
+    L.riot_hessian_apply.argtypes = [vp, vp, vp, c_int64, c_int32, c_int32]
+    L.riot_rsvd.argtypes = [vp, c_int32, c_int32, c_int64, vp, POINTER(c_double)]
+    L.riot_increment.argtypes = [vp, vp, POINTER(c_int32)]
+    L.riot_analysis_cov_lowrank.argtypes = [vp, c_int32, vp, POINTER(c_double), POINTER(c_int32)]
+    L.riot_bsqrt_apply.argtypes = [vp, vp, vp, c_int32, c_int32]
+    L.riot_get_state.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.riot_draw_normal.argtypes = [c_uint64, c_int64, c_int64, c_int32, c_int64, c_int32, vp, vp]
+    L.riot_l96_forecast.argtypes = [c_int64, c_int32, c_double, c_double, vp, vp, c_int32, vp]
+    L.riot_rsvd_timings.argtypes = [vp, POINTER(c_double)]
+    L.riot_last_error.argtypes = [vp]
+    L.riot_last_error.restype = c_char_p
+    L.riot_status_string.argtypes = [c_int32]
+    L.riot_status_string.restype = c_char_p
+    L.riot_kernel_launches.argtypes = []
+    L.riot_kernel_launches.restype = c_uint64
+    L.riot_destroy.argtypes = [vp]
+    L.riot_destroy.restype = None
+    for name in ("riot_setup", "riot_outer_begin", "riot_hessian_apply", "riot_rsvd", "riot_increment",
+                 "riot_analysis_cov_lowrank", "riot_bsqrt_apply", "riot_get_state", "riot_draw_normal",
+                 "riot_l96_forecast", "riot_rsvd_timings"):
+        getattr(L, name).restype = c_int32
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    return None if t is None else c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def _check(ctx, fn, status):
+    if status != RIOT_OK:
+        msg = load().riot_last_error(ctx).decode() if ctx else load().riot_status_string(status).decode()
+        raise RiotError(fn, status, msg)
+
+
+# ---- C entry points ------------------------------------------------------------------
+
+def riot_setup(n, T, dt, F, obs_step, obs_idx, obs_y, obs_sigma, length, sigma_b=1.0, sigma_vec=None,
+               precision=RIOT_PREC_MIXED, kmax=64, exact_rr=False, seed=0, stream=None):
+    """Create a context (host numpy arrays for the observations); returns the handle."""
+    L = load()
+    st = np.ascontiguousarray(obs_step, dtype=np.int32)
+    ix = np.ascontiguousarray(obs_idx, dtype=np.int32)
+    yy = np.ascontiguousarray(obs_y, dtype=np.float64)
+    sg = np.ascontiguousarray(obs_sigma, dtype=np.float64)
+    md = ModelDesc(RIOT_MODEL_L96, int(T), int(n), float(dt), float(F))
+    od = ObsDesc(int(st.size), st.ctypes.data_as(POINTER(c_int32)), ix.ctypes.data_as(POINTER(c_int32)),
+                 yy.ctypes.data_as(POINTER(c_double)), sg.ctypes.data_as(POINTER(c_double)))
+    sv = None if sigma_vec is None else np.ascontiguousarray(sigma_vec, dtype=np.float64)
+    bd = BcovDesc(RIOT_B_GAUSS_RING, 0, float(length), float(sigma_b),
+                  None if sv is None else sv.ctypes.data_as(POINTER(c_double)))
+    op = Options(int(precision), int(kmax), int(bool(exact_rr)), 0, int(seed))
+    h = c_void_p()
+    status = L.riot_setup(ctypes.byref(h), ctypes.byref(md), ctypes.byref(od), ctypes.byref(bd),
+                          ctypes.byref(op), _stream_handle(stream))
+    _check(None, "riot_setup", status)
+    return h
+
+
+def riot_outer_begin(ctx, x=None, v=None):
+    J = c_double(0.0)
+    _check(ctx, "riot_outer_begin", load().riot_outer_begin(ctx, _ptr(x), _ptr(v), ctypes.byref(J)))
+    return J.value
+
+
+def riot_hessian_apply(ctx, W, Y, ncols=None, add_identity=False):
+    """Y[:, j] = A W[:, j] (+ W) for column blocks stored as (ncols, n) row-major tensors."""
+    ncols = W.shape[0] if ncols is None else ncols
+    ld = W.stride(0)
+    assert Y.stride(0) == ld and W.is_contiguous() and Y.is_contiguous()
+    _check(ctx, "riot_hessian_apply",
+           load().riot_hessian_apply(ctx, _ptr(W), _ptr(Y), int(ld), int(ncols), int(bool(add_identity))))
+
+
+def riot_rsvd(ctx, k, q=0, sketch_stream=0, Omega=None):
+    lam = (c_double * k)()
+    _check(ctx, "riot_rsvd", load().riot_rsvd(ctx, int(k), int(q), int(sketch_stream), _ptr(Omega), lam))
+    return np.array(lam[:])
+
+
+def riot_increment(ctx, dv=None):
+    mode = c_int32(-1)
+    _check(ctx, "riot_increment", load().riot_increment(ctx, _ptr(dv), ctypes.byref(mode)))
+    return mode.value
+
+
+def riot_analysis_cov_lowrank(ctx, m, LU=None):
+    coef = (c_double * m)()
+    mode = c_int32(-1)
+    _check(ctx, "riot_analysis_cov_lowrank",
+           load().riot_analysis_cov_lowrank(ctx, int(m), _ptr(LU), coef, ctypes.byref(mode)))
+    return np.array(coef[:]), mode.value
+
+
+def riot_bsqrt_apply(ctx, x_in, x_out, transpose=False, ncols=1):
+    _check(ctx, "riot_bsqrt_apply",
+           load().riot_bsqrt_apply(ctx, _ptr(x_in), _ptr(x_out), int(bool(transpose)), int(ncols)))
+
+
+def riot_get_state(ctx, x=None, v=None, g=None, U=None, lam=None):
+    _check(ctx, "riot_get_state", load().riot_get_state(ctx, _ptr(x), _ptr(v), _ptr(g), _ptr(U), _ptr(lam)))
+
+
+def riot_draw_normal(seed, stream_id, n, ncols, out, ld=None, stream=None):
+    import torch
+    is_double = int(out.dtype == torch.float64)
+    ld = n if ld is None else ld
+    status = load().riot_draw_normal(int(seed), int(stream_id), int(n), int(ncols), int(ld), is_double,
+                                     _ptr(out), _stream_handle(stream))
+    _check(None, "riot_draw_normal", status)
+
+
+def riot_l96_forecast(n, T, dt, F, x0, out, store_all=True, stream=None):
+    status = load().riot_l96_forecast(int(n), int(T), float(dt), float(F), _ptr(x0), _ptr(out),
+                                      int(bool(store_all)), _stream_handle(stream))
+    _check(None, "riot_l96_forecast", status)
+
+
+def riot_rsvd_timings(ctx):
+    ms = (c_double * 6)()
+    _check(ctx, "riot_rsvd_timings", load().riot_rsvd_timings(ctx, ms))
+    return dict(zip(["hvp", "orth", "kmat", "eig", "ritz", "total"], ms[:]))
+
+
+def riot_kernel_launches():
+    return int(load().riot_kernel_launches())
+
+
+def riot_destroy(ctx):
+    if ctx:
+        load().riot_destroy(ctx)
+
+
+class Context:
+    """Owning wrapper: ``with Context(...) as c: riot_rsvd(c.h, ...)``."""
+
+    def __init__(self, **kw):
+        self.n = int(kw["n"])
+        self.h = riot_setup(**kw)
+
+    def close(self):
+        if self.h:
+            riot_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

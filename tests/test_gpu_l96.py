@@ -1,0 +1,321 @@
+"""GPU parity of the Lorenz-96 RIOT path against the FP64 oracle (through the C ABI).
+
+Tolerances:
+  FP64 library path vs FP64 oracle: the two compute the same quantities in a
+  different order (FMA contraction, gather vs scatter adjoint, band vs dense
+  L), so results agree to a few hundred ulps of the largest term; 1e-10
+  relative is used for Hessian products and gradients, 1e-9 for eigenpairs.
+  FP32 Hessian products (mixed precision): each RK4 stage rounds at 2^-24;
+  over T steps the relative error of a column grows like sqrt(4T) * 2^-24 *
+  (error growth along the trajectory); for the 20-step window this is below
+  1e-5, tested at 2e-5 of the column norm.
+"""
+import numpy as np
+import pytest
+
+from oracle import bcov, l96, problem, riot as orc
+from synth import configs, philox
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+def _ctx(R, prob, ell, sigma_b=1.0, precision=None, kmax=64, exact_rr=False, sigma_vec=None):
+    if precision is None:
+        precision = R.RIOT_PREC_FP64
+    return R.Context(n=prob.n, T=prob.T, dt=prob.dt, F=prob.F, obs_step=prob.obs_step, obs_idx=prob.obs_idx,
+                     obs_y=prob.y, obs_sigma=prob.sigma_o, length=ell, sigma_b=sigma_b, sigma_vec=sigma_vec,
+                     precision=precision, kmax=kmax, exact_rr=exact_rr)
+
+
+def _t(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+@pytest.fixture(scope="module")
+def small():
+    cfg = configs.l96_small()
+    prob = problem.build(cfg)
+    traj = orc.trajectory(prob, prob.x_b)
+    return cfg, prob, traj
+
+
+def _random_problem(n, T, ell, obs_frac, obs_every, seed, sigma_vec=None, dup=False):
+    rng = np.random.default_rng(seed)
+    x0 = l96.nl(8.0 + rng.standard_normal(n), 200, 0.05, 8.0)[-1]
+    steps = np.arange(0, T + 1, obs_every)
+    m = max(1, int(obs_frac * n))
+    st_list, ix_list = [], []
+    for s in steps:
+        ix = np.sort(rng.choice(n, m, replace=False))
+        if dup:
+            ix = np.sort(np.concatenate([ix, ix[: max(1, m // 4)]]))
+        st_list.append(np.full(ix.size, s))
+        ix_list.append(ix)
+    st = np.concatenate(st_list)
+    ix = np.concatenate(ix_list)
+    sig_o = 0.5 + rng.random(st.size)
+    truth = l96.nl(x0, T, 0.05, 8.0)
+    y = truth[st, ix] + sig_o * rng.standard_normal(st.size)
+    sv = 1.0 if sigma_vec is None else sigma_vec
+    L = bcov.bsqrt(n, ell, sv)
+    xb = x0 + L @ rng.standard_normal(n)
+    return orc.L96Problem(n=n, T=T, dt=0.05, F=8.0, obs_step=st, obs_idx=ix, y=y, sigma_o=sig_o, L=L, x_b=xb)
+
+
+def test_device_normals_match_host_generator(gpu_lib):
+    R = gpu_lib
+    n, k = 1000, 7
+    out = torch.empty(k, n, dtype=torch.float64, device=DEV)
+    R.riot_draw_normal(123456789, 21, n, k, out)
+    ref = philox.normals(123456789, 21, n * k).reshape(k, n)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-13, atol=1e-13)
+    out32 = torch.empty(k, n, dtype=torch.float32, device=DEV)
+    R.riot_draw_normal(123456789, 21, n, k, out32)
+    np.testing.assert_allclose(out32.cpu().numpy(), ref.astype(np.float32), rtol=2e-7, atol=1e-7)
+
+
+@pytest.mark.parametrize("n,T", [(40, 30), (41, 17), (100, 50), (4096, 20), (8192, 5), (5001, 3)])
+def test_forecast_matches_oracle(gpu_lib, n, T):
+    R = gpu_lib
+    rng = np.random.default_rng(n)
+    x0 = 8.0 + rng.standard_normal(n)
+    ref = l96.nl(x0, T, 0.05, 8.0)
+    out = torch.empty(T + 1, n, dtype=torch.float64, device=DEV)
+    R.riot_l96_forecast(n, T, 0.05, 8.0, _t(x0), out)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    last = torch.empty(n, dtype=torch.float64, device=DEV)
+    R.riot_l96_forecast(n, T, 0.05, 8.0, _t(x0), last, store_all=False)
+    np.testing.assert_allclose(last.cpu().numpy(), ref[-1], rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def _hvp_gpu(R, ctx, W, dtype, add_identity=False):
+    Wt = _t(W.T, dtype)                    # (ncols, n) rows = columns
+    Yt = torch.empty_like(Wt)
+    R.riot_hessian_apply(ctx.h, Wt, Yt, add_identity=add_identity)
+    torch.cuda.synchronize()
+    return Yt.double().cpu().numpy().T
+
+
+def _col_rel_err(Y, ref):
+    return np.linalg.norm(Y - ref, axis=0) / np.maximum(np.linalg.norm(ref, axis=0), 1e-300)
+
+
+def test_hvp_fp64_small(gpu_lib, small):
+    R = gpu_lib
+    cfg, prob, traj = small
+    ctx = _ctx(R, prob, cfg.ell, kmax=16)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    W = cfg.sketch(5, k=37).T                # 37 columns, kmax 16: three slices
+    ref = orc.hvp(prob, traj, W)
+    Y = _hvp_gpu(R, ctx, W, torch.float64)
+    assert _col_rel_err(Y, ref).max() < 1e-10
+    Y1 = _hvp_gpu(R, ctx, W, torch.float64, add_identity=True)
+    assert _col_rel_err(Y1, ref + W).max() < 1e-10
+    ctx.close()
+
+
+def test_hvp_fp32_small(gpu_lib, small):
+    R = gpu_lib
+    cfg, prob, traj = small
+    ctx = _ctx(R, prob, cfg.ell, precision=R.RIOT_PREC_MIXED, kmax=64)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    W = cfg.sketch(6, k=40).T
+    ref = orc.hvp(prob, traj, W.astype(np.float32).astype(np.float64))
+    Y = _hvp_gpu(R, ctx, W, torch.float32)
+    err = _col_rel_err(Y, ref)
+    assert err.max() < 2e-5, err.max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("n,T,every,frac,dup", [(16, 4, 1, 1.0, False), (41, 9, 2, 0.3, True),
+                                                (100, 13, 3, 0.5, False), (257, 7, 1, 0.1, True),
+                                                (1000, 6, 2, 0.25, False), (4100, 3, 1, 0.05, True)])
+def test_hvp_fp64_ragged_sizes(gpu_lib, n, T, every, frac, dup):
+    R = gpu_lib
+    sv = 0.5 + np.arange(n) / n
+    prob = _random_problem(n, T, 2.5, frac, every, seed=n, sigma_vec=sv, dup=dup)
+    traj = orc.trajectory(prob, prob.x_b)
+    ctx = _ctx(R, prob, 2.5, sigma_vec=sv, kmax=8)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    W = np.random.default_rng(1).standard_normal((n, 11))
+    ref = orc.hvp(prob, traj, W)
+    Y = _hvp_gpu(R, ctx, W, torch.float64)
+    assert _col_rel_err(Y, ref).max() < 1e-10
+    # gradient g = b + v at v = 0 and the cost
+    g = torch.empty(n, dtype=torch.float64, device=DEV)
+    R.riot_get_state(ctx.h, g=g)
+    gref = orc.gradient_b(prob, traj, orc.innovation(prob, traj))
+    np.testing.assert_allclose(g.cpu().numpy(), gref, rtol=0, atol=1e-10 * np.abs(gref).max())
+    ctx.close()
+
+
+def test_hvp_symmetry_on_gpu(gpu_lib):
+    # <A w1, w2> = <w1, A w2>: the adjoint kernel is the transpose of the TL kernel.
+    R = gpu_lib
+    n = 300
+    prob = _random_problem(n, 40, 3.0, 0.3, 2, seed=7)
+    ctx = _ctx(R, prob, 3.0, kmax=4)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    W = np.random.default_rng(2).standard_normal((n, 2))
+    Y = _hvp_gpu(R, ctx, W, torch.float64)
+    a, b = W[:, 1] @ Y[:, 0], W[:, 0] @ Y[:, 1]
+    assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
+    ctx.close()
+
+
+def test_no_observations_gives_zero_hessian(gpu_lib):
+    R = gpu_lib
+    n, T = 64, 5
+    prob = _random_problem(n, T, 2.0, 0.5, 1, seed=3)
+    prob.obs_step = prob.obs_step[:0]
+    prob.obs_idx = prob.obs_idx[:0]
+    prob.y = prob.y[:0]
+    prob.sigma_o = prob.sigma_o[:0]
+    ctx = _ctx(R, prob, 2.0, kmax=4)
+    J = R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    assert J == 0.0
+    W = np.random.default_rng(2).standard_normal((n, 3))
+    Y = _hvp_gpu(R, ctx, W, torch.float64, add_identity=True)
+    np.testing.assert_array_equal(Y, W)
+    ctx.close()
+
+
+def test_cost_gradient_and_bsqrt(gpu_lib, small):
+    R = gpu_lib
+    cfg, prob, traj = small
+    ctx = _ctx(R, prob, cfg.ell)
+    J = R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    Jref = orc.cost(prob, traj, np.zeros(cfg.n))
+    assert abs(J - Jref) <= 1e-11 * Jref
+    x = np.random.default_rng(4).standard_normal((3, cfg.n))
+    out = torch.empty(3, cfg.n, dtype=torch.float64, device=DEV)
+    R.riot_bsqrt_apply(ctx.h, _t(x), out, transpose=False, ncols=3)
+    np.testing.assert_allclose(out.cpu().numpy(), (prob.L @ x.T).T, rtol=0, atol=1e-13)
+    R.riot_bsqrt_apply(ctx.h, _t(x), out, transpose=True, ncols=3)
+    np.testing.assert_allclose(out.cpu().numpy(), (prob.L.T @ x.T).T, rtol=0, atol=1e-13)
+    ctx.close()
+
+
+def _gpu_outer(R, ctx, prob, cfg, outer_iter, k, q, dtype):
+    Om = _t(cfg.sketch(outer_iter, k=k), dtype)
+    lam = R.riot_rsvd(ctx.h, k, q, Omega=Om)
+    dv = torch.empty(prob.n, dtype=torch.float64, device=DEV)
+    mode = R.riot_increment(ctx.h, dv)
+    return lam, dv.cpu().numpy(), mode
+
+
+def test_full_rank_inner_loop_fp64(gpu_lib, small):
+    R = gpu_lib
+    cfg, prob, traj = small
+    ctx = _ctx(R, prob, cfg.ell, kmax=cfg.k)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    lam, dv, mode = _gpu_outer(R, ctx, prob, cfg, 0, cfg.k, cfg.q, torch.float64)
+    st = orc.outer_step(prob, prob.x_b, np.zeros(cfg.n), cfg.sketch(0).T, q=cfg.q)
+    np.testing.assert_allclose(lam, st["lam"], rtol=1e-9, atol=1e-9 * st["lam"][0])
+    assert mode == st["mode"]
+    assert np.linalg.norm(dv - st["dv"]) <= 1e-9 * np.linalg.norm(st["dv"])
+    U = torch.empty(cfg.k, cfg.n, dtype=torch.float64, device=DEV)
+    R.riot_get_state(ctx.h, U=U)
+    U = U.cpu().numpy().T
+    # eigenvectors of well-separated eigenvalues agree column by column (signs fixed alike)
+    gap = np.minimum(np.abs(np.diff(st["lam"], prepend=np.inf)), np.abs(np.diff(st["lam"], append=-np.inf)))
+    sep = gap > 1e-3 * st["lam"][0]
+    np.testing.assert_allclose(U[:, sep], st["U"][:, sep], rtol=0, atol=1e-7)
+    # the exact minimiser (full rank): dv = -(I + A)^-1 g
+    A = orc.dense_hessian(prob, traj)
+    exact = -np.linalg.solve(np.eye(cfg.n) + A, st["g"])
+    assert np.linalg.norm(dv - exact) <= 1e-8 * np.linalg.norm(exact)
+    # analysis covariance
+    LU = torch.empty(cfg.k, cfg.n, dtype=torch.float64, device=DEV)
+    coef, cmode = R.riot_analysis_cov_lowrank(ctx.h, cfg.k, LU)
+    LUr, coefr, moder = orc.analysis_cov_lowrank(prob.L, st["lam"], st["U"])
+    assert cmode == moder
+    np.testing.assert_allclose(coef, coefr, rtol=1e-9)
+    Pa = (LU.cpu().numpy().T * coef) @ LU.cpu().numpy()
+    Pa_ref = orc.analysis_cov_dense(prob.L, st["lam"], st["U"])
+    if cmode == 1:
+        Pa = prob.L @ prob.L.T - Pa
+    np.testing.assert_allclose(Pa, Pa_ref, rtol=0, atol=1e-9 * np.abs(Pa_ref).max())
+    ctx.close()
+
+
+def test_outer_loops_fp64_track_oracle(gpu_lib, small):
+    R = gpu_lib
+    cfg, prob, _ = small
+    ctx = _ctx(R, prob, cfg.ell, kmax=cfg.k)
+    x, v = prob.x_b.copy(), np.zeros(cfg.n)
+    J = R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    for it in range(cfg.outer):
+        st = orc.outer_step(prob, x, v, cfg.sketch(it).T, q=cfg.q)
+        assert abs(J - st["J"]) <= 1e-8 * st["J"]
+        lam, dv, mode = _gpu_outer(R, ctx, prob, cfg, it, cfg.k, cfg.q, torch.float64)
+        assert np.linalg.norm(dv - st["dv"]) <= 1e-8 * np.linalg.norm(st["dv"])
+        x, v = st["x_next"], st["v_next"]
+        J = R.riot_outer_begin(ctx.h)
+    xg = torch.empty(cfg.n, dtype=torch.float64, device=DEV)
+    R.riot_get_state(ctx.h, x=xg)
+    np.testing.assert_allclose(xg.cpu().numpy(), x, rtol=0, atol=1e-8 * np.abs(x).max())
+    ctx.close()
+
+
+@pytest.mark.parametrize("k,q,exact_rr", [(12, 0, False), (12, 1, False), (12, 2, True), (1, 0, False)])
+def test_partial_rank_fp64(gpu_lib, small, k, q, exact_rr):
+    R = gpu_lib
+    cfg, prob, traj = small
+    ctx = _ctx(R, prob, cfg.ell, kmax=k, exact_rr=exact_rr)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    Om = cfg.sketch(2, k=k)
+    lam = R.riot_rsvd(ctx.h, k, q, Omega=_t(Om))
+    d = orc.innovation(prob, traj)
+    g = orc.gradient_b(prob, traj, d)
+    lr, Ur, _ = orc.rsvd(prob, traj, Om.T, q=q, exact_rr=exact_rr)
+    np.testing.assert_allclose(lam, lr, rtol=1e-8, atol=1e-9 * lr[0])
+    dv = torch.empty(cfg.n, dtype=torch.float64, device=DEV)
+    mode = R.riot_increment(ctx.h, dv)
+    dvr, moder = orc.increment(lr, Ur, g)
+    assert mode == moder
+    assert np.linalg.norm(dv.cpu().numpy() - dvr) <= 1e-7 * np.linalg.norm(dvr)
+    ctx.close()
+
+
+def test_mixed_precision_small(gpu_lib, small):
+    R = gpu_lib
+    cfg, prob, traj = small
+    ctx = _ctx(R, prob, cfg.ell, precision=R.RIOT_PREC_MIXED, kmax=cfg.k)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    Om = cfg.sketch(0)
+    lam, dv, mode = _gpu_outer(R, ctx, prob, cfg, 0, cfg.k, cfg.q, torch.float32)
+    st = orc.outer_step(prob, prob.x_b, np.zeros(cfg.n), Om.astype(np.float32).astype(np.float64).T, q=cfg.q)
+    lead = st["lam"] > 1e-3 * st["lam"][0]
+    rel = np.abs(lam - st["lam"]) / st["lam"][0]
+    assert rel.max() < 1e-4
+    assert (np.abs(lam[lead] - st["lam"][lead]) / st["lam"][lead]).max() < 1e-3
+    assert np.linalg.norm(dv - st["dv"]) <= 1e-3 * np.linalg.norm(st["dv"])
+    ctx.close()
+
+
+def test_call_order_and_argument_errors(gpu_lib, small):
+    R = gpu_lib
+    cfg, prob, _ = small
+    ctx = _ctx(R, prob, cfg.ell, kmax=8)
+    with pytest.raises(R.RiotError) as e:
+        R.riot_rsvd(ctx.h, 4)
+    assert e.value.status == -6
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    with pytest.raises(R.RiotError) as e:
+        R.riot_increment(ctx.h)
+    assert e.value.status == -6
+    with pytest.raises(R.RiotError) as e:
+        R.riot_rsvd(ctx.h, 9)
+    assert e.value.status == -1
+    W = torch.zeros(0, cfg.n, dtype=torch.float64, device=DEV)
+    R.riot_hessian_apply(ctx.h, W, W.clone(), ncols=0)     # empty block: no-op
+    ctx.close()
+    with pytest.raises(R.RiotError):
+        R.Context(n=8, T=3, dt=0.05, F=8.0, obs_step=[0], obs_idx=[0], obs_y=[0.0], obs_sigma=[1.0], length=2.0)
+    with pytest.raises(R.RiotError):
+        R.Context(n=40, T=3, dt=0.05, F=8.0, obs_step=[2, 1], obs_idx=[0, 1], obs_y=[0.0, 0.0],
+                  obs_sigma=[1.0, 1.0], length=2.0)
