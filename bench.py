@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile", action="store_true",
+                    help="bracket the first timed step with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -148,22 +150,29 @@ def build_problem(R, torch, cfg, dev, precision, kmax):
     return ctx, xb, st.size
 
 
-def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv):
+def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False):
     """Per-step CUDA-event times of riot_rsvd + riot_increment (L2 flushed between steps)."""
     s = torch.cuda.current_stream()
     times, phases = [], []
     for i in range(warmup + steps):
         flush.zero_()
         torch.cuda.synchronize()
+        prof = profile and i == warmup
+        if prof:
+            torch.cuda.profiler.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
         lam = R.riot_rsvd(ctx.h, cfg.k, cfg.q, sketch_stream=configs.STREAM_SKETCH0)
         mode = R.riot_increment(ctx.h, dv)
         e1.record(s)
         torch.cuda.synchronize()
+        if prof:
+            torch.cuda.profiler.stop()
         if i >= warmup:
             times.append(e0.elapsed_time(e1))
-            phases.append(R.riot_rsvd_timings(ctx.h))
+            ph = R.riot_rsvd_timings(ctx.h)
+            ph["jacobi_sweeps"] = R.riot_rsvd_sweeps(ctx.h)
+            phases.append(ph)
     return times, phases, lam, mode
 
 
@@ -250,7 +259,7 @@ def main():
     with ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv",
                       local) as clk:
-        times, phases, lam, mode = time_inner_loop(R, torch, ctx, cfg, args.steps, 0, flush, dv)
+        times, phases, lam, mode = time_inner_loop(R, torch, ctx, cfg, args.steps, 0, flush, dv, args.profile)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = R.riot_kernel_launches() - launches0

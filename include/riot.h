@@ -195,6 +195,9 @@ riot_status riot_l96_forecast(int64_t n, int32_t T, double dt, double F, const d
  * Synchronises. */
 riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6);
 
+/* Number of Jacobi sweeps of the last successful riot_rsvd (-1: no context). */
+int32_t riot_rsvd_sweeps(const riot_ctx *ctx);
+
 /* Number of kernel launches the library has issued in this process (all
  * contexts); a benchmark reads it before and after a timed region. */
 uint64_t riot_kernel_launches(void);

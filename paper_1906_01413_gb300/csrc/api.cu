@@ -39,7 +39,7 @@ struct riot_ctx {
     double *Q = nullptr, *U = nullptr;
     double *G = nullptr, *Mm = nullptr, *Nm = nullptr, *Km = nullptr, *Z = nullptr, *lam = nullptr, *cvec = nullptr;
     double *jwork = nullptr;
-    int *info = nullptr;  // [0..7] Cholesky passes, [8..9] Jacobi, [10] mode, [11] finite flag
+    int *info = nullptr;  // [0..9] CholeskyQR passes, [10] K Cholesky, [12..13] Jacobi, [14] mode
     int have_traj = 0, have_rsvd = 0, k_last = 0, v_init = 0, jacobi_sweeps = 0;
     // timing
     cudaEvent_t ev[32];
@@ -157,10 +157,14 @@ riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
 {
     const int n = ctx->m.geom.n;
     CU(convert_block(Y, real_tag(ctx), n, ctx->Q, 'd', n, n, k, ctx->s));
-    for (int pass = 0; pass < 3; ++pass) {
-        CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Q, 'd', n, 0.0, ctx->G, 'd', k, ctx->s));
+    // Each shifted pass divides the condition number by about
+    // 1 / sqrt(11 (n k + k^2) u k); FP32 blocks carry at most ~1e8 of it,
+    // FP64 blocks up to ~1e16.
+    const int shifted = (ctx->prec == RIOT_PREC_FP64) ? 3 : 1;
+    for (int pass = 0; pass < shifted + 2; ++pass) {
+        CU(gram_lower(n, k, ctx->Q, 'd', n, ctx->G, k, ctx->s));
         const double u = ldexp(1.0, -53);
-        const double shift = (pass == 0) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
+        const double shift = (pass < shifted) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
         CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, nullptr, ctx->s));
         CU(trsm_right_lt(ctx->Q, n, k, n, ctx->G, k, ctx->s));
     }
@@ -169,7 +173,8 @@ riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
 
 riot_status check_cholesky(riot_ctx *ctx, int base, int count, const char *what)
 {
-    int h[8] = {0};
+    int h[16] = {0};
+    if (count > 16) count = 16;
     CU(cudaMemcpyAsync(h, ctx->info + base, sizeof(int) * count, cudaMemcpyDeviceToHost, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
     for (int i = 0; i < count; ++i)
@@ -316,7 +321,7 @@ riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_
         (st = dalloc(ctx, &ctx->U, np * k)) || (st = dalloc(ctx, &ctx->G, k * k)) || (st = dalloc(ctx, &ctx->Mm, k * k)) ||
         (st = dalloc(ctx, &ctx->Nm, k * k)) || (st = dalloc(ctx, &ctx->Km, k * k)) || (st = dalloc(ctx, &ctx->Z, k * k)) ||
         (st = dalloc(ctx, &ctx->lam, k)) || (st = dalloc(ctx, &ctx->cvec, k)) ||
-        (st = dalloc(ctx, &ctx->jwork, jacobi_work_doubles((int)k))) || (st = dalloc(ctx, &ctx->info, 16)))
+        (st = dalloc(ctx, &ctx->jwork, jacobi_work_doubles((int)k))) || (st = dalloc(ctx, &ctx->info, 32)))
         return bail(st);
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->s) : cudaSuccess;
@@ -395,7 +400,7 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
     const size_t rs = real_size(ctx);
     cudaStream_t s = ctx->s;
     ctx->nev = 0;
-    CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 16, s));
+    CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 32, s));
     ev_mark(ctx, -1);
     if (Omega_dev)
         CU(cudaMemcpyAsync(ctx->Wblk, Omega_dev, (size_t)n * k * rs, cudaMemcpyDeviceToDevice, s));
@@ -411,7 +416,7 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
         TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
     }
     ev_mark(ctx, 1);
-    TRY(orth(ctx, ctx->Yblk, k, 3));
+    TRY(orth(ctx, ctx->Yblk, k, 5));
     ev_mark(ctx, 2);
     if (ctx->exact_rr) {
         // K = Q^T A Q
@@ -426,20 +431,20 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
         CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Nm, 'd', k, s));
         CU(gemm('N', 'T', k, k, k, 1.0, ctx->Mm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->G, 'd', k, s));
         CU(gemm('N', 'T', k, k, k, 1.0, ctx->Nm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->Km, 'd', k, s));
-        CU(cholesky(ctx->G, k, k, 0.0, ctx->info + 6, nullptr, s));
+        CU(cholesky(ctx->G, k, k, 0.0, ctx->info + 10, nullptr, s));
         CU(trsm_right_lt(ctx->Km, k, k, k, ctx->G, k, s));
         CU(trsm_right_l(ctx->Km, k, k, k, ctx->G, k, s));
     }
     CU(symmetrize(ctx->Km, k, k, s));
     ev_mark(ctx, 3);
-    CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 8, s));
+    CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
     ev_mark(ctx, 4);
     CU(gemm('N', 'N', n, k, k, 1.0, ctx->Q, 'd', n, ctx->Z, 'd', k, 0.0, ctx->U, 'd', n, s));
     CU(fix_col_signs(ctx->U, n, k, n, s));
     ev_mark(ctx, -2);
-    TRY(check_cholesky(ctx, 0, 7, "riot_rsvd"));
+    TRY(check_cholesky(ctx, 0, 11, "riot_rsvd"));
     int jinfo[2] = {0, 0};
-    CU(cudaMemcpyAsync(jinfo, ctx->info + 8, sizeof(jinfo), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(jinfo, ctx->info + 12, sizeof(jinfo), cudaMemcpyDeviceToHost, s));
     if (lambda_out) CU(cudaMemcpyAsync(lambda_out, ctx->lam, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (jinfo[0] < 0) return fail(ctx, RIOT_ENOCONV, "Jacobi did not converge in %d sweeps", -jinfo[0]);
@@ -468,6 +473,8 @@ riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6)
     return RIOT_OK;
 }
 
+int32_t riot_rsvd_sweeps(const riot_ctx *ctx) { return ctx ? ctx->jacobi_sweeps : -1; }
+
 riot_status riot_increment(riot_ctx *ctx, double *dv_dev, int32_t *mode_out)
 {
     if (!ctx) return RIOT_EINVAL;
@@ -477,16 +484,16 @@ riot_status riot_increment(riot_ctx *ctx, double *dv_dev, int32_t *mode_out)
     cudaStream_t s = ctx->s;
     // c = U^T g; scale by the adaptive rule; dv = U c (- g for LRU)
     CU(gemm('T', 'N', k, 1, n, 1.0, ctx->U, 'd', n, ctx->g, 'd', n, 0.0, ctx->cvec, 'd', k, s));
-    CU(increment_coef(ctx->lam, k, ctx->cvec, ctx->info + 10, s));
+    CU(increment_coef(ctx->lam, k, ctx->cvec, ctx->info + 14, s));
     CU(gemm('N', 'N', n, 1, k, 1.0, ctx->U, 'd', n, ctx->cvec, 'd', k, 0.0, ctx->dv, 'd', n, s));
-    CU(add_if_flag(ctx->info + 10, 1, n, -1.0, ctx->g, ctx->dv, s));
+    CU(add_if_flag(ctx->info + 14, 1, n, -1.0, ctx->g, ctx->dv, s));
     // v += dv, x += L dv
     CU(axpby(n, 1.0, ctx->dv, 1.0, ctx->v, s));
     CU(bsqrt_launch(ctx->m, ctx->dv, ctx->tmp, 0, 1, s));
     CU(axpby(n, 1.0, ctx->tmp, 1.0, ctx->x, s));
     if (dv_dev) CU(cudaMemcpyAsync(dv_dev, ctx->dv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     if (mode_out) {
-        CU(cudaMemcpyAsync(mode_out, ctx->info + 10, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(mode_out, ctx->info + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
     }
     return RIOT_OK;
@@ -499,10 +506,10 @@ riot_status riot_analysis_cov_lowrank(riot_ctx *ctx, int32_t m, double *LU_dev, 
     if (m < 1 || m > ctx->k_last) return fail(ctx, RIOT_EINVAL, "m = %d outside [1, k]", m);
     CU(cudaSetDevice(ctx->dev));
     cudaStream_t s = ctx->s;
-    CU(cov_coef(ctx->lam, m, ctx->cvec, ctx->info + 10, s));
+    CU(cov_coef(ctx->lam, m, ctx->cvec, ctx->info + 14, s));
     if (LU_dev) CU(bsqrt_launch(ctx->m, ctx->U, LU_dev, 0, m, s));
     if (coef_out) CU(cudaMemcpyAsync(coef_out, ctx->cvec, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
-    if (mode_out) CU(cudaMemcpyAsync(mode_out, ctx->info + 10, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (mode_out) CU(cudaMemcpyAsync(mode_out, ctx->info + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (coef_out || mode_out) CU(cudaStreamSynchronize(s));
     return RIOT_OK;
 }

@@ -103,6 +103,8 @@ cudaError_t normal_launch(uint64_t seed, uint32_t stream, int64_t n, int ncols, 
 cudaError_t gemm(char ta, char tb, int m, int n, int k, double alpha, const void *A, char tA,
                  int64_t lda, const void *B, char tB, int64_t ldb, double beta, void *C, char tC,
                  int64_t ldc, cudaStream_t s);
+// lower-triangular tiles of G = A^T A (A: n x k), the rest of G untouched
+cudaError_t gram_lower(int n, int k, const void *A, char tA, int64_t lda, double *G, int64_t ldg, cudaStream_t s);
 cudaError_t convert_block(const void *in, char tin, int64_t ldin, void *out, char tout, int64_t ldout,
                           int64_t rows, int cols, cudaStream_t s);
 // In-place blocked Cholesky of the k x k SPD matrix G (lower factor); adds

@@ -39,9 +39,10 @@ template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(256) gemm_kernel(int ta, int tb, int m, int n, int K, double alpha,
                                                    const TA *__restrict__ A, long long lda,
                                                    const TB *__restrict__ B, long long ldb, double beta,
-                                                   TC *__restrict__ C, long long ldc)
+                                                   TC *__restrict__ C, long long ldc, int lower_only)
 {
     constexpr int BM = 32, BN = 32, BK = 32;
+    if (lower_only && blockIdx.y > blockIdx.x) return;   // tile strictly above the diagonal
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
     const int tid = threadIdx.x;
@@ -96,13 +97,22 @@ __global__ void __launch_bounds__(256) gemm_kernel(int ta, int tb, int m, int n,
 
 template <typename TA, typename TB, typename TC>
 static cudaError_t gemm_t(int ta, int tb, int m, int n, int k, double alpha, const void *A, int64_t lda,
-                          const void *B, int64_t ldb, double beta, void *C, int64_t ldc, cudaStream_t s)
+                          const void *B, int64_t ldb, double beta, void *C, int64_t ldc, cudaStream_t s,
+                          int lower_only = 0)
 {
     dim3 grid((m + 31) / 32, (n + 31) / 32);
     count_launch();
     gemm_kernel<TA, TB, TC><<<grid, 256, 0, s>>>(ta, tb, m, n, k, alpha, (const TA *)A, lda, (const TB *)B, ldb,
-                                                 beta, (TC *)C, ldc);
+                                                 beta, (TC *)C, ldc, lower_only);
     return cudaGetLastError();
+}
+
+cudaError_t gram_lower(int n, int k, const void *A, char tA, int64_t lda, double *G, int64_t ldg, cudaStream_t s)
+{
+    if (k <= 0) return cudaSuccess;
+    if (tA == 'd') return gemm_t<double, double, double>(1, 0, k, k, n, 1.0, A, lda, A, lda, 0.0, G, ldg, s, 1);
+    if (tA == 'f') return gemm_t<float, float, double>(1, 0, k, k, n, 1.0, A, lda, A, lda, 0.0, G, ldg, s, 1);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t gemm(char ta, char tb, int m, int n, int k, double alpha, const void *A, char tA, int64_t lda,
@@ -343,7 +353,7 @@ cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, 
 size_t jacobi_work_doubles(int k)
 {
     const size_t ke = (size_t)(k + (k & 1));
-    return 3 * ke * ke + 256;
+    return 3 * ke * ke + 256 + ke;
 }
 
 __device__ __forceinline__ int rr_player(int x, int r, int ke)
@@ -376,13 +386,14 @@ __global__ void jacobi_init_kernel(const double *K, int k, int ke, double *A0, d
 }
 
 __global__ void __launch_bounds__(256) jacobi_kernel(double *Abuf, double *V, int ke, double tol, int maxsweeps,
-                                                     int *counters, int *info)
+                                                     int *counters, int *info, double *rot)
 {
     cg::grid_group grid = cg::this_grid();
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int half = ke / 2;
     double *Ain = Abuf, *Aout = Abuf + (int64_t)ke * ke;
+    double *rc = rot, *rs = rot + half;
     // ||A||_F^2 for the absolute rotation floor (rounding level of the input)
     double *frob = (double *)(counters + 128);
     double part = 0.0;
@@ -395,6 +406,19 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double *Abuf, double *V, in
     for (; sweep < maxsweeps; ++sweep) {
         int myrot = 0;
         for (int r = 0; r < ke - 1; ++r) {
+            // rotation of every pair of this round, once
+            for (int64_t P = gtid; P < half; P += nthreads) {
+                int p = rr_player((int)P, r, ke), q = rr_player(ke - 1 - (int)P, r, ke);
+                if (p > q) { int tmp = p; p = q; q = tmp; }
+                double c, sn;
+                bool rt;
+                jac_rot(Ain[p + (int64_t)p * ke], Ain[q + (int64_t)q * ke], Ain[p + (int64_t)q * ke], tol, floor_abs, c,
+                        sn, rt);
+                rc[P] = c;
+                rs[P] = rt ? sn : 0.0;
+                if (rt) ++myrot;
+            }
+            grid.sync();
             // A <- J^T A J on all 2 x 2 blocks
             for (int64_t e = gtid; e < (int64_t)half * half; e += nthreads) {
                 const int P = (int)(e % half), Q = (int)(e / half);
@@ -402,11 +426,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double *Abuf, double *V, in
                 if (p > q) { int tmp = p; p = q; q = tmp; }
                 int u = rr_player(Q, r, ke), w = rr_player(ke - 1 - Q, r, ke);
                 if (u > w) { int tmp = u; u = w; w = tmp; }
-                double cP, sP, cQ, sQ;
-                bool rP, rQ;
-                jac_rot(Ain[p + (int64_t)p * ke], Ain[q + (int64_t)q * ke], Ain[p + (int64_t)q * ke], tol, floor_abs, cP, sP, rP);
-                jac_rot(Ain[u + (int64_t)u * ke], Ain[w + (int64_t)w * ke], Ain[u + (int64_t)w * ke], tol, floor_abs, cQ, sQ, rQ);
-                if (P == Q && rP) ++myrot;
+                const double cP = rc[P], sP = rs[P], cQ = rc[Q], sQ = rs[Q];
                 const double apu = Ain[p + (int64_t)u * ke], apw = Ain[p + (int64_t)w * ke];
                 const double aqu = Ain[q + (int64_t)u * ke], aqw = Ain[q + (int64_t)w * ke];
                 // T = blk R_Q
@@ -415,7 +435,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double *Abuf, double *V, in
                 // R_P^T T
                 double n00 = cP * t00 - sP * t10, n01 = cP * t01 - sP * t11;
                 double n10 = sP * t00 + cP * t10, n11 = sP * t01 + cP * t11;
-                if (P == Q && rP) { n01 = 0.0; n10 = 0.0; }
+                if (P == Q && sP != 0.0) { n01 = 0.0; n10 = 0.0; }
                 Aout[p + (int64_t)u * ke] = n00;
                 Aout[p + (int64_t)w * ke] = n01;
                 Aout[q + (int64_t)u * ke] = n10;
@@ -424,15 +444,14 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double *Abuf, double *V, in
             // V <- V J
             for (int64_t e = gtid; e < (int64_t)ke * half; e += nthreads) {
                 const int i = (int)(e % ke), P = (int)(e / ke);
-                int p = rr_player(P, r, ke), q = rr_player(ke - 1 - P, r, ke);
-                if (p > q) { int tmp = p; p = q; q = tmp; }
-                double c, s;
-                bool rot;
-                jac_rot(Ain[p + (int64_t)p * ke], Ain[q + (int64_t)q * ke], Ain[p + (int64_t)q * ke], tol, floor_abs, c, s, rot);
-                if (rot) {
+                const double s_ = rs[P];
+                if (s_ != 0.0) {
+                    int p = rr_player(P, r, ke), q = rr_player(ke - 1 - P, r, ke);
+                    if (p > q) { int tmp = p; p = q; q = tmp; }
+                    const double c = rc[P];
                     const double vp = V[i + (int64_t)p * ke], vq = V[i + (int64_t)q * ke];
-                    V[i + (int64_t)p * ke] = vp * c - vq * s;
-                    V[i + (int64_t)q * ke] = vp * s + vq * c;
+                    V[i + (int64_t)p * ke] = vp * c - vq * s_;
+                    V[i + (int64_t)q * ke] = vp * s_ + vq * c;
                 }
             }
             grid.sync();
@@ -502,6 +521,7 @@ cudaError_t jacobi_eig(double *K, int k, double *lam, double *Z, double *work, i
     double *Abuf = work;                         // 2 ke^2
     double *V = work + 2 * (size_t)ke * ke;       // ke^2
     int *counters = (int *)(V + (size_t)ke * ke); // 128 ints, then the Frobenius accumulator
+    double *rot = V + (size_t)ke * ke + 256;       // cos / sin of the ke/2 pairs of a round
     const int maxsweeps = 60;
     cudaError_t e = cudaMemsetAsync(counters, 0, 128 * sizeof(int) + 2 * sizeof(double), s);
     if (e != cudaSuccess) return e;
@@ -512,12 +532,12 @@ cudaError_t jacobi_eig(double *K, int k, double *lam, double *Z, double *work, i
         cudaGetDevice(&dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 256, 0);
         if (per_sm < 1) per_sm = 1;
-        int need = (int)(((int64_t)ke * (ke / 2) + 255) / 256);
+        int need = (int)(((int64_t)(ke / 2) * (ke / 2) + 255) / 256);
         int grid = num_sms() * per_sm;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
         double tol = 1e-15 * (double)(k > 16 ? k : 16) * 0.0625;
-        void *args[] = {&Abuf, &V, (void *)&ke, &tol, (void *)&maxsweeps, &counters, &info};
+        void *args[] = {&Abuf, &V, (void *)&ke, &tol, (void *)&maxsweeps, &counters, &info, &rot};
         count_launch();
         e = cudaLaunchCooperativeKernel((void *)jacobi_kernel, grid, 256, args, 0, s);
         if (e != cudaSuccess) return e;

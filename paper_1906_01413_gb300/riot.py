@@ -77,6 +77,8 @@ def load():
     L.riot_last_error.restype = c_char_p
     L.riot_status_string.argtypes = [c_int32]
     L.riot_status_string.restype = c_char_p
+    L.riot_rsvd_sweeps.argtypes = [vp]
+    L.riot_rsvd_sweeps.restype = c_int32
     L.riot_kernel_launches.argtypes = []
     L.riot_kernel_launches.restype = c_uint64
     L.riot_destroy.argtypes = [vp]
@@ -192,6 +194,10 @@ def riot_rsvd_timings(ctx):
     ms = (c_double * 6)()
     _check(ctx, "riot_rsvd_timings", load().riot_rsvd_timings(ctx, ms))
     return dict(zip(["hvp", "orth", "kmat", "eig", "ritz", "total"], ms[:]))
+
+
+def riot_rsvd_sweeps(ctx):
+    return int(load().riot_rsvd_sweeps(ctx))
 
 
 def riot_kernel_launches():
