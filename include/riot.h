@@ -135,6 +135,30 @@ riot_status riot_outer_begin(riot_ctx *ctx, const double *x_dev, const double *v
 riot_status riot_hessian_apply(riot_ctx *ctx, const void *W_dev, void *Y_dev, int64_t ld,
                                int32_t ncols, int32_t add_identity);
 
+/* Same result as riot_hessian_apply, for callers that must not allocate
+ * device memory when they apply the Hessian: for example code that runs
+ * under a memory pool or budget that forbids cudaMalloc after start-up, or
+ * a context created with a small kmax whose residual workspace is too small
+ * for the block at hand.  (The paper has no counterpart: this is a property
+ * of the library, not of the method.)  The tangent-linear residuals that
+ * wait for the adjoint pass go to a fixed 16 MiB device array inside the
+ * library instead of the context's workspace; the columns are processed in
+ * slices that fit it, so any ncols is accepted.  If one column alone needs
+ * more than 16 MiB (p observations x 4 bytes in RIOT_PREC_MIXED, x 8 bytes in
+ * RIOT_PREC_FP64) the call returns RIOT_EINVAL and does nothing.
+ *  - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ *  - The array belongs to the process, one copy per device that loaded the
+ *    library, held until exit.  Its device address is looked up the first time
+ *    this entry point runs on a device; make that first call before any stream
+ *    capture.
+ *  - All calls share the array and it keeps the last call's contents.  Each
+ *    call writes every residual it reads, so nothing needs clearing, but two
+ *    calls that overlap on the GPU (other streams, other contexts on the same
+ *    device) race on it.
+ * Arguments, layout and errors are those of riot_hessian_apply. */
+riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y_dev, int64_t ld,
+                                       int32_t ncols, int32_t add_identity);
+
 /* Randomized eigendecomposition of A (Algorithm 3 inner loop): draw Omega
  * (n x k, N(0,1)) from the context seed and sketch_stream with Philox4x32-10
  * + Box-Muller unless Omega_dev (n x k, ld = n) is given; Y = A Omega; q

@@ -11,6 +11,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -182,6 +183,35 @@ riot_status check_cholesky(riot_ctx *ctx, int base, int count, const char *what)
             return fail(ctx, RIOT_ENOTSPD, "%s: Cholesky pass %d met a non-positive pivot at column %d", what, i,
                         h[i] - 1);
     return RIOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Residual scratch of riot_hessian_apply_noalloc: a fixed device array that
+// every GPU loading the library holds until the process exits, so that call
+// never allocates.  Host code only sees a stand-in symbol; the device
+// address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (first call per
+// device looks it up; that first call must not be inside a stream capture).
+cudaError_t noalloc_scratch(int dev, void **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -385,6 +415,40 @@ riot_status riot_hessian_apply(riot_ctx *ctx, const void *W_dev, void *Y_dev, in
     if (!W_dev || !Y_dev) return fail(ctx, RIOT_EINVAL, "null W or Y");
     CU(cudaSetDevice(ctx->dev));
     return hvp(ctx, W_dev, Y_dev, ld, ncols, add_identity);
+}
+
+riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y_dev, int64_t ld, int32_t ncols,
+                                       int32_t add_identity)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_hessian_apply_noalloc before riot_outer_begin");
+    if (ncols < 0 || ld < ctx->m.geom.n) return fail(ctx, RIOT_EINVAL, "bad ncols / ld");
+    if (ncols == 0) return RIOT_OK;
+    if (!W_dev || !Y_dev) return fail(ctx, RIOT_EINVAL, "null W or Y");
+    CU(cudaSetDevice(ctx->dev));
+    const size_t rs = real_size(ctx);
+    const size_t per_col = (size_t)ctx->m.p * rs;
+    if (per_col > kNoAllocScratchBytes)
+        return fail(ctx, RIOT_EINVAL,
+                    "riot_hessian_apply_noalloc: one column needs %zu bytes of residual scratch (%d observations), "
+                    "the static array holds %zu bytes",
+                    per_col, ctx->m.p, kNoAllocScratchBytes);
+    void *scr = nullptr;
+    CU(noalloc_scratch(ctx->dev, &scr));
+    size_t slice = per_col ? kNoAllocScratchBytes / per_col : (size_t)ncols;
+    if (slice > (size_t)ncols) slice = (size_t)ncols;
+    for (int c0 = 0; c0 < ncols; c0 += (int)slice) {
+        const int nc = (ncols - c0 < (int)slice) ? ncols - c0 : (int)slice;
+        const char *w = (const char *)W_dev + (size_t)c0 * ld * rs;
+        char *yv = (char *)Y_dev + (size_t)c0 * ld * rs;
+        if (ctx->prec == RIOT_PREC_FP64)
+            CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, (const double *)w, (double *)yv, ld, nc, add_identity,
+                                  (double *)scr, 0, ctx->s));
+        else
+            CU(l96_hvp_launch_f32(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
+                                  (float *)scr, 0, ctx->s));
+    }
+    return RIOT_OK;
 }
 
 riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const void *Omega_dev,

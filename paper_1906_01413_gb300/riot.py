@@ -65,6 +65,7 @@ def load():
                              POINTER(Options), vp]
     L.riot_outer_begin.argtypes = [vp, vp, vp, POINTER(c_double)]
     L.riot_hessian_apply.argtypes = [vp, vp, vp, c_int64, c_int32, c_int32]
+    L.riot_hessian_apply_noalloc.argtypes = [vp, vp, vp, c_int64, c_int32, c_int32]
     L.riot_rsvd.argtypes = [vp, c_int32, c_int32, c_int64, vp, POINTER(c_double)]
     L.riot_increment.argtypes = [vp, vp, POINTER(c_int32)]
     L.riot_analysis_cov_lowrank.argtypes = [vp, c_int32, vp, POINTER(c_double), POINTER(c_int32)]
@@ -83,7 +84,8 @@ def load():
     L.riot_kernel_launches.restype = c_uint64
     L.riot_destroy.argtypes = [vp]
     L.riot_destroy.restype = None
-    for name in ("riot_setup", "riot_outer_begin", "riot_hessian_apply", "riot_rsvd", "riot_increment",
+    for name in ("riot_setup", "riot_outer_begin", "riot_hessian_apply", "riot_hessian_apply_noalloc",
+                 "riot_rsvd", "riot_increment",
                  "riot_analysis_cov_lowrank", "riot_bsqrt_apply", "riot_get_state", "riot_draw_normal",
                  "riot_l96_forecast", "riot_rsvd_timings"):
         getattr(L, name).restype = c_int32
@@ -144,6 +146,16 @@ def riot_hessian_apply(ctx, W, Y, ncols=None, add_identity=False):
     assert Y.stride(0) == ld and W.is_contiguous() and Y.is_contiguous()
     _check(ctx, "riot_hessian_apply",
            load().riot_hessian_apply(ctx, _ptr(W), _ptr(Y), int(ld), int(ncols), int(bool(add_identity))))
+
+
+def riot_hessian_apply_noalloc(ctx, W, Y, ncols=None, add_identity=False):
+    """As riot_hessian_apply, with the residual scratch in the library's static
+    device array (no allocation by the library at call time)."""
+    ncols = W.shape[0] if ncols is None else ncols
+    ld = W.stride(0)
+    assert Y.stride(0) == ld and W.is_contiguous() and Y.is_contiguous()
+    _check(ctx, "riot_hessian_apply_noalloc",
+           load().riot_hessian_apply_noalloc(ctx, _ptr(W), _ptr(Y), int(ld), int(ncols), int(bool(add_identity))))
 
 
 def riot_rsvd(ctx, k, q=0, sketch_stream=0, Omega=None):
