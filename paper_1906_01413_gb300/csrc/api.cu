@@ -41,6 +41,7 @@ struct riot_ctx {
     double *G = nullptr, *Mm = nullptr, *Nm = nullptr, *Km = nullptr, *Z = nullptr, *lam = nullptr, *cvec = nullptr;
     double *jwork = nullptr;
     int *info = nullptr;  // [0..9] CholeskyQR passes, [10] K Cholesky, [12..13] Jacobi, [14] mode
+    int *errflag = nullptr;  // set by a kernel whose bounded wait ran out
     int have_traj = 0, have_rsvd = 0, k_last = 0, v_init = 0, jacobi_sweeps = 0;
     // timing
     cudaEvent_t ev[32];
@@ -145,8 +146,8 @@ riot_status hvp(riot_ctx *ctx, const void *W, void *Y, int64_t ld, int ncols, in
             CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, (const double *)w, (double *)yv, ld, nc, add_identity,
                                   (double *)ctx->rscr, 0, ctx->s));
         else
-            CU(l96_hvp_launch_f32(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
-                                  (float *)ctx->rscr, 0, ctx->s));
+            CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
+                                  (float *)ctx->rscr, 0, ctx->errflag, ctx->s));
     }
     return RIOT_OK;
 }
@@ -351,7 +352,7 @@ riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_
         (st = dalloc(ctx, &ctx->U, np * k)) || (st = dalloc(ctx, &ctx->G, k * k)) || (st = dalloc(ctx, &ctx->Mm, k * k)) ||
         (st = dalloc(ctx, &ctx->Nm, k * k)) || (st = dalloc(ctx, &ctx->Km, k * k)) || (st = dalloc(ctx, &ctx->Z, k * k)) ||
         (st = dalloc(ctx, &ctx->lam, k)) || (st = dalloc(ctx, &ctx->cvec, k)) ||
-        (st = dalloc(ctx, &ctx->jwork, jacobi_work_doubles((int)k))) || (st = dalloc(ctx, &ctx->info, 32)))
+        (st = dalloc(ctx, &ctx->jwork, jacobi_work_doubles((int)k))) || (st = dalloc(ctx, &ctx->info, 32)) || (st = dalloc(ctx, &ctx->errflag, 4)))
         return bail(st);
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->s) : cudaSuccess;
@@ -364,6 +365,7 @@ riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_
         (e = up(ctx->band32, band32.data(), sizeof(float) * band.size())) ||
         (e = up(ctx->sig64, sig.data(), sizeof(double) * n)) || (e = up(ctx->sig32, sig32.data(), sizeof(float) * n)) ||
         (e = cudaMemsetAsync(ctx->v, 0, sizeof(double) * n, ctx->s)) ||
+        (e = cudaMemsetAsync(ctx->errflag, 0, sizeof(int) * 4, ctx->s)) ||
         (e = cudaMemsetAsync(ctx->x, 0, sizeof(double) * n, ctx->s)) || (e = cudaStreamSynchronize(ctx->s)))
         return bail(fail(ctx, RIOT_ECUDA, "setup upload failed: %s", cudaGetErrorString(e)));
     for (int i = 0; i < 32; ++i)
@@ -445,8 +447,8 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
             CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, (const double *)w, (double *)yv, ld, nc, add_identity,
                                   (double *)scr, 0, ctx->s));
         else
-            CU(l96_hvp_launch_f32(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
-                                  (float *)scr, 0, ctx->s));
+            CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
+                                  (float *)scr, 0, ctx->errflag, ctx->s));
     }
     return RIOT_OK;
 }
@@ -512,6 +514,10 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
     if (lambda_out) CU(cudaMemcpyAsync(lambda_out, ctx->lam, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (jinfo[0] < 0) return fail(ctx, RIOT_ENOCONV, "Jacobi did not converge in %d sweeps", -jinfo[0]);
+    int eflag = 0;
+    CU(cudaMemcpyAsync(&eflag, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (eflag) return fail(ctx, RIOT_ETIMEOUT, "a bounded wait on a coefficient copy ran out in the Hessian kernel");
     ctx->jacobi_sweeps = jinfo[0];
     ctx->have_rsvd = 1;
     ctx->k_last = k;

@@ -85,6 +85,12 @@ cudaError_t l96_hvp_launch_f64(const L96Dev &m, const double2 *coef, const doubl
                                int64_t ld, int ncols, int add_identity, double *r, int mode,
                                cudaStream_t s);
 
+// FP32 Hessian-vector product with the stage coefficients streamed into
+// shared memory by 1-D TMA copies (same modes as above); *err is set to 1 if
+// a bounded wait on a copy ran out.
+cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float *W, float *Y, int64_t ld,
+                               int ncols, int add_identity, float *r, int mode, int *err, cudaStream_t s);
+
 // out = L in or L^T in (FP64), ncols columns (ld = n)
 cudaError_t bsqrt_launch(const L96Dev &m, const double *in, double *out, int transpose, int ncols,
                          cudaStream_t s);

@@ -152,6 +152,26 @@ def test_hvp_fp64_ragged_sizes(gpu_lib, n, T, every, frac, dup):
     ctx.close()
 
 
+@pytest.mark.parametrize("n,T,every,frac,dup", [(16, 4, 1, 1.0, False), (41, 9, 2, 0.3, True),
+                                                (100, 13, 3, 0.5, False), (257, 7, 1, 0.1, True),
+                                                (4096, 6, 2, 0.25, False), (5001, 5, 1, 0.05, True),
+                                                (8192, 3, 1, 0.1, False)])
+def test_hvp_fp32_ragged_sizes(gpu_lib, n, T, every, frac, dup):
+    # FP32 kernel with streamed stage coefficients: every chunk width (E = 4, 8,
+    # 16), ragged last chunks, duplicate observations and several probes per CTA.
+    R = gpu_lib
+    sv = 0.5 + np.arange(n) / n
+    prob = _random_problem(n, T, 2.5, frac, every, seed=n + 1, sigma_vec=sv, dup=dup)
+    traj = orc.trajectory(prob, prob.x_b)
+    ctx = _ctx(R, prob, 2.5, sigma_vec=sv, kmax=16, precision=R.RIOT_PREC_MIXED)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    W = np.random.default_rng(2).standard_normal((n, 13)).astype(np.float32).astype(np.float64)
+    ref = orc.hvp(prob, traj, W)
+    Y = _hvp_gpu(R, ctx, W, torch.float32)
+    assert _col_rel_err(Y, ref).max() < 2e-5
+    ctx.close()
+
+
 def test_hvp_symmetry_on_gpu(gpu_lib):
     # <A w1, w2> = <w1, A w2>: the adjoint kernel is the transpose of the TL kernel.
     R = gpu_lib
