@@ -55,6 +55,7 @@ typedef enum {
 enum { RIOT_MODEL_L96 = 1 };
 enum { RIOT_B_GAUSS_RING = 1 };
 enum { RIOT_PREC_MIXED = 0, RIOT_PREC_FP64 = 1 };
+enum { RIOT_EIG_TRIDIAG = 0, RIOT_EIG_JACOBI = 1 };
 
 /* Model of the window (Section 3.1 for Lorenz-96).
  * L96: dx_i/dt = (x_{i+1} - x_{i-2}) x_{i-1} - x_i + F on a periodic ring of
@@ -104,7 +105,9 @@ typedef struct {
     int32_t kmax;       /* largest number of sketch columns used per call (>= 1) */
     int32_t exact_rr;   /* 0: K solves K (Q^T W) = Q^T Y (Algorithm 3);
                            1: K = Q^T A Q (k more Hessian applications)       */
-    int32_t reserved;
+    int32_t eig_method; /* k x k eigensolver, FP64: RIOT_EIG_TRIDIAG (Householder
+                           tridiagonalisation + bisection + inverse iteration,
+                           default) or RIOT_EIG_JACOBI (parallel cyclic Jacobi) */
     uint64_t seed;      /* key of the device-drawn Gaussian sketch            */
 } riot_options;
 
@@ -164,7 +167,7 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
  * + Box-Muller unless Omega_dev (n x k, ld = n) is given; Y = A Omega; q
  * rounds of subspace iteration Q = orth(Y), Y = A Q; Q = orth(Y) by shifted
  * CholeskyQR with two cleanup passes; K from Q^T W and Q^T Y (or Q^T A Q);
- * K = Z Lambda Z^T by cyclic Jacobi in FP64; U = Q Z.  1 <= k <= min(kmax, n).
+ * K = Z Lambda Z^T in FP64 (options.eig_method); U = Q Z.  1 <= k <= min(kmax, n).
  * lambda_out (host, k doubles, may be NULL) receives the eigenvalues in
  * decreasing order; this synchronises.  Requires riot_outer_begin. */
 riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream,
@@ -212,6 +215,14 @@ riot_status riot_draw_normal(uint64_t seed, int64_t stream, int64_t n, int32_t n
  * truths without a context. */
 riot_status riot_l96_forecast(int64_t n, int32_t T, double dt, double F, const double *x0_dev,
                               double *traj_dev, int32_t store_all, void *cuda_stream);
+
+/* The k x k symmetric eigensolver of riot_rsvd on its own (Algorithm 3,
+ * K = Z Lambda Z^T, FP64): K_dev (k x k, column-major, read only),
+ * lambda_dev (k, decreasing), Z_dev (k x k eigenvectors).  method is
+ * RIOT_EIG_TRIDIAG or RIOT_EIG_JACOBI.  Allocates and frees its own
+ * workspace; synchronises the stream.  1 <= k <= 4096. */
+riot_status riot_symm_eig(const double *K_dev, int32_t k, double *lambda_dev, double *Z_dev, int32_t method,
+                          void *cuda_stream);
 
 /* Timings of the phases of the last riot_rsvd in milliseconds (CUDA events on
  * the context stream): [0] Hessian applications, [1] orthonormalisation,

@@ -22,7 +22,7 @@ struct riot_ctx {
     int dev = 0;
     cudaStream_t s = nullptr;
     int prec = RIOT_PREC_MIXED;
-    int kmax = 0, exact_rr = 0;
+    int kmax = 0, exact_rr = 0, eig_method = 0;
     uint64_t seed = 0;
     L96Dev m;
     std::vector<void *> allocs;
@@ -38,8 +38,10 @@ struct riot_ctx {
     // inner-loop workspace
     void *Wblk = nullptr, *Yblk = nullptr, *rscr = nullptr;
     double *Q = nullptr, *U = nullptr;
+    float *Q32 = nullptr, *M32 = nullptr, *N32 = nullptr, *L32 = nullptr;   // mixed precision only
     double *G = nullptr, *Mm = nullptr, *Nm = nullptr, *Km = nullptr, *Z = nullptr, *lam = nullptr, *cvec = nullptr;
     double *jwork = nullptr;
+    double *gws = nullptr;   // split-K partial Grams, 8 kmax^2
     int *info = nullptr;  // [0..9] CholeskyQR passes, [10] K Cholesky, [12..13] Jacobi, [14] mode
     int *errflag = nullptr;  // set by a kernel whose bounded wait ran out
     int have_traj = 0, have_rsvd = 0, k_last = 0, v_init = 0, jacobi_sweeps = 0;
@@ -164,11 +166,29 @@ riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
     // FP64 blocks up to ~1e16.
     const int shifted = (ctx->prec == RIOT_PREC_FP64) ? 3 : 1;
     for (int pass = 0; pass < shifted + 2; ++pass) {
-        CU(gram_lower(n, k, ctx->Q, 'd', n, ctx->G, k, ctx->s));
+        CU(gram_lower(n, k, ctx->Q, 'd', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
         const double u = ldexp(1.0, -53);
         const double shift = (pass < shifted) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
-        CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, nullptr, ctx->s));
-        CU(trsm_right_lt(ctx->Q, n, k, n, ctx->G, k, ctx->s));
+        CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
+        CU(trsm_right_lt(ctx->Q, n, k, n, ctx->G, k, ctx->s, ctx->gws));
+    }
+    return RIOT_OK;
+}
+
+// Mixed precision: Q32 = orthonormal basis of Y (FP32 block).  Grams are
+// accumulated and factorised in FP64 (the step that needs the range); the
+// triangular solves run in FP32, like the block they act on.
+riot_status orth32(riot_ctx *ctx, const float *Y, int k, int info_base, int passes)
+{
+    const int n = ctx->m.geom.n;
+    CU(cudaMemcpyAsync(ctx->Q32, Y, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, ctx->s));
+    for (int pass = 0; pass < passes; ++pass) {
+        CU(gram_lower(n, k, ctx->Q32, 'f', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
+        const double u = ldexp(1.0, -53);
+        const double shift = (pass == 0) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
+        CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
+        CU(convert_block(ctx->G, 'd', k, ctx->L32, 'f', k, k, k, ctx->s));
+        CU(strsm_right_lt(ctx->Q32, n, k, n, ctx->L32, k, ctx->s));
     }
     return RIOT_OK;
 }
@@ -298,6 +318,9 @@ riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_
     ctx->prec = opt->precision;
     ctx->kmax = opt->kmax;
     ctx->exact_rr = opt->exact_rr;
+    ctx->eig_method = opt->eig_method;
+    if (ctx->eig_method != RIOT_EIG_TRIDIAG && ctx->eig_method != RIOT_EIG_JACOBI)
+        return bail(fail(ctx, RIOT_EINVAL, "unknown eig_method %d", ctx->eig_method));
     ctx->seed = opt->seed;
     L96Dev &m = ctx->m;
     if (!choose_geom(n, &m.geom)) return bail(fail(ctx, RIOT_EINVAL, "no thread layout for n = %d", n));
@@ -349,10 +372,13 @@ riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_
         (ctx->prec == RIOT_PREC_MIXED && (st = dalloc(ctx, &ctx->coef32, (size_t)T * 4 * m.geom.Np + 1))) ||
         (st = dalloc(ctx, (char **)&ctx->Wblk, np * k * rs)) || (st = dalloc(ctx, (char **)&ctx->Yblk, np * k * rs)) ||
         (st = dalloc(ctx, (char **)&ctx->rscr, (size_t)p * k * rs + 16)) || (st = dalloc(ctx, &ctx->Q, np * k)) ||
-        (st = dalloc(ctx, &ctx->U, np * k)) || (st = dalloc(ctx, &ctx->G, k * k)) || (st = dalloc(ctx, &ctx->Mm, k * k)) ||
+        (st = dalloc(ctx, &ctx->U, np * k)) ||
+        (ctx->prec == RIOT_PREC_MIXED &&
+         ((st = dalloc(ctx, &ctx->Q32, np * k)) || (st = dalloc(ctx, &ctx->M32, k * k)) ||
+          (st = dalloc(ctx, &ctx->N32, k * k)) || (st = dalloc(ctx, &ctx->L32, k * k)))) || (st = dalloc(ctx, &ctx->G, k * k)) || (st = dalloc(ctx, &ctx->Mm, k * k)) ||
         (st = dalloc(ctx, &ctx->Nm, k * k)) || (st = dalloc(ctx, &ctx->Km, k * k)) || (st = dalloc(ctx, &ctx->Z, k * k)) ||
         (st = dalloc(ctx, &ctx->lam, k)) || (st = dalloc(ctx, &ctx->cvec, k)) ||
-        (st = dalloc(ctx, &ctx->jwork, jacobi_work_doubles((int)k))) || (st = dalloc(ctx, &ctx->info, 32)) || (st = dalloc(ctx, &ctx->errflag, 4)))
+        (st = dalloc(ctx, &ctx->jwork, jacobi_work_doubles((int)k) > eig_work_doubles((int)k) ? jacobi_work_doubles((int)k) : eig_work_doubles((int)k))) || (st = dalloc(ctx, &ctx->gws, 8 * k * k)) || (st = dalloc(ctx, &ctx->info, 32)) || (st = dalloc(ctx, &ctx->errflag, 4)))
         return bail(st);
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->s) : cudaSuccess;
@@ -474,38 +500,70 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
         CU(normal_launch(ctx->seed, (uint32_t)sketch_stream, n, k, n, ctx->prec == RIOT_PREC_FP64, ctx->Wblk, s));
     ev_mark(ctx, 0);
     TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
+    const bool mixed = (ctx->prec == RIOT_PREC_MIXED);
+    float *W32 = (float *)ctx->Wblk, *Y32 = (float *)ctx->Yblk;
     for (int it = 0; it < q; ++it) {
         ev_mark(ctx, 1);
-        TRY(orth(ctx, ctx->Yblk, k, 0));
-        CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
+        if (mixed) {
+            // a power-iteration basis only has to span the block well: shifted pass + one plain pass
+            TRY(orth32(ctx, Y32, k, 0, 2));
+            CU(cudaMemcpyAsync(W32, ctx->Q32, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
+        } else {
+            TRY(orth(ctx, ctx->Yblk, k, 0));
+            CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
+        }
         ev_mark(ctx, 0);
         TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
     }
     ev_mark(ctx, 1);
-    TRY(orth(ctx, ctx->Yblk, k, 5));
+    if (mixed) TRY(orth32(ctx, Y32, k, 5, 3));
+    else TRY(orth(ctx, ctx->Yblk, k, 5));
     ev_mark(ctx, 2);
     if (ctx->exact_rr) {
         // K = Q^T A Q
-        CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
+        if (mixed) CU(cudaMemcpyAsync(W32, ctx->Q32, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
+        else CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
         ev_mark(ctx, 0);
         TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
         ev_mark(ctx, 2);
-        CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Km, 'd', k, s));
+        if (mixed) {
+            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, Y32, n, 0.f, ctx->N32, k, s));
+            CU(convert_block(ctx->N32, 'f', k, ctx->Km, 'd', k, k, k, s));
+        } else {
+            CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Km, 'd', k, s));
+        }
     } else {
         // K (Q^T W) = Q^T Y  <=>  K (M M^T) = N M^T with M = Q^T W, N = Q^T Y
-        CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Wblk, tr, n, 0.0, ctx->Mm, 'd', k, s));
-        CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Nm, 'd', k, s));
+        if (mixed) {
+            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, W32, n, 0.f, ctx->M32, k, s));
+            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, Y32, n, 0.f, ctx->N32, k, s));
+            CU(convert_block(ctx->M32, 'f', k, ctx->Mm, 'd', k, k, k, s));
+            CU(convert_block(ctx->N32, 'f', k, ctx->Nm, 'd', k, k, k, s));
+        } else {
+            CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Wblk, tr, n, 0.0, ctx->Mm, 'd', k, s));
+            CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Nm, 'd', k, s));
+        }
         CU(gemm('N', 'T', k, k, k, 1.0, ctx->Mm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->G, 'd', k, s));
         CU(gemm('N', 'T', k, k, k, 1.0, ctx->Nm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->Km, 'd', k, s));
-        CU(cholesky(ctx->G, k, k, 0.0, ctx->info + 10, nullptr, s));
-        CU(trsm_right_lt(ctx->Km, k, k, k, ctx->G, k, s));
-        CU(trsm_right_l(ctx->Km, k, k, k, ctx->G, k, s));
+        CU(cholesky(ctx->G, k, k, 0.0, ctx->info + 10, ctx->gws, s));
+        CU(trsm_right_lt(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
+        CU(trsm_right_l(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
     }
     CU(symmetrize(ctx->Km, k, k, s));
     ev_mark(ctx, 3);
-    CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
+    if (ctx->eig_method == RIOT_EIG_JACOBI)
+        CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
+    else
+        CU(tridiag_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
     ev_mark(ctx, 4);
-    CU(gemm('N', 'N', n, k, k, 1.0, ctx->Q, 'd', n, ctx->Z, 'd', k, 0.0, ctx->U, 'd', n, s));
+    if (mixed) {
+        // U = Q Z in FP32 (Y block reused as scratch), then widened
+        CU(convert_block(ctx->Z, 'd', k, ctx->M32, 'f', k, k, k, s));
+        CU(sgemm('N', 'N', n, k, k, 1.f, ctx->Q32, n, ctx->M32, k, 0.f, Y32, n, s));
+        CU(convert_block(Y32, 'f', n, ctx->U, 'd', n, n, k, s));
+    } else {
+        CU(gemm('N', 'N', n, k, k, 1.0, ctx->Q, 'd', n, ctx->Z, 'd', k, 0.0, ctx->U, 'd', n, s));
+    }
     CU(fix_col_signs(ctx->U, n, k, n, s));
     ev_mark(ctx, -2);
     TRY(check_cholesky(ctx, 0, 11, "riot_rsvd"));
@@ -513,12 +571,15 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
     CU(cudaMemcpyAsync(jinfo, ctx->info + 12, sizeof(jinfo), cudaMemcpyDeviceToHost, s));
     if (lambda_out) CU(cudaMemcpyAsync(lambda_out, ctx->lam, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    if (jinfo[0] < 0) return fail(ctx, RIOT_ENOCONV, "Jacobi did not converge in %d sweeps", -jinfo[0]);
+    if (ctx->eig_method == RIOT_EIG_JACOBI && jinfo[0] < 0)
+        return fail(ctx, RIOT_ENOCONV, "Jacobi did not converge in %d sweeps", -jinfo[0]);
+    if (ctx->eig_method == RIOT_EIG_TRIDIAG && (jinfo[0] != 0 || jinfo[1] != 0))
+        return fail(ctx, RIOT_ENOCONV, "orthonormalisation of the tridiagonal eigenvectors failed");
     int eflag = 0;
     CU(cudaMemcpyAsync(&eflag, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (eflag) return fail(ctx, RIOT_ETIMEOUT, "a bounded wait on a coefficient copy ran out in the Hessian kernel");
-    ctx->jacobi_sweeps = jinfo[0];
+    ctx->jacobi_sweeps = (ctx->eig_method == RIOT_EIG_JACOBI) ? jinfo[0] : 0;
     ctx->have_rsvd = 1;
     ctx->k_last = k;
     return RIOT_OK;
@@ -614,6 +675,38 @@ riot_status riot_draw_normal(uint64_t seed, int64_t stream, int64_t n, int32_t n
     if (n < 0 || ncols < 0 || ld < n || (n * ncols > 0 && !out_dev)) return RIOT_EINVAL;
     cudaError_t e = normal_launch(seed, (uint32_t)stream, n, ncols, ld, is_double, out_dev, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? RIOT_OK : RIOT_ECUDA;
+}
+
+riot_status riot_symm_eig(const double *K_dev, int32_t k, double *lambda_dev, double *Z_dev, int32_t method,
+                          void *cuda_stream)
+{
+    if (k < 1 || k > 4096 || !K_dev || !lambda_dev || !Z_dev) return RIOT_EINVAL;
+    if (method != RIOT_EIG_TRIDIAG && method != RIOT_EIG_JACOBI) return RIOT_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t nw = method == RIOT_EIG_JACOBI ? jacobi_work_doubles(k) : eig_work_doubles(k);
+    double *work = nullptr, *Kc = nullptr;
+    int *info = nullptr;
+    if (cudaMalloc(&work, nw * sizeof(double)) != cudaSuccess) return RIOT_ENOMEM;
+    if (cudaMalloc(&Kc, (size_t)k * k * sizeof(double)) != cudaSuccess || cudaMalloc(&info, 4 * sizeof(int)) != cudaSuccess) {
+        cudaFree(work);
+        cudaFree(Kc);
+        return RIOT_ENOMEM;
+    }
+    riot_status st = RIOT_OK;
+    cudaError_t e = cudaMemcpyAsync(Kc, K_dev, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = (method == RIOT_EIG_JACOBI) ? jacobi_eig(Kc, k, lambda_dev, Z_dev, work, info, s)
+                                        : tridiag_eig(Kc, k, lambda_dev, Z_dev, work, info, s);
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = RIOT_ECUDA;
+    else if (method == RIOT_EIG_JACOBI && h[0] < 0) st = RIOT_ENOCONV;
+    else if (method == RIOT_EIG_TRIDIAG && (h[0] || h[1])) st = RIOT_ENOCONV;
+    cudaFree(work);
+    cudaFree(Kc);
+    cudaFree(info);
+    return st;
 }
 
 riot_status riot_l96_forecast(int64_t n, int32_t T, double dt, double F, const double *x0_dev, double *traj_dev,

@@ -1,0 +1,475 @@
+// Symmetric eigendecomposition of the k x k projected matrix K (Algorithm 3:
+// K = Z Lambda Z^T) in FP64, laid out for a GPU whose FP64 rate is low per SM:
+// every stage spreads its work over all SMs and the number of grid-wide
+// synchronisations is O(k), not O(k x sweeps).
+//
+//  1. Householder tridiagonalisation Q^T K Q = T in one cooperative launch,
+//     two grid barriers per column (matrix-vector products, then the rank-2
+//     update with the next column's reflector computed by the warp that
+//     owns it); Q is accumulated as Q^T on the fly.
+//  2. T splits where an off-diagonal is negligible; each unreduced block's
+//     eigenvalues come from bisection with Sturm counts (one thread each).
+//  3. Eigenvectors of T by inverse iteration from distinct pseudo-random
+//     starts (tridiagonal LU with partial pivoting, one thread each), then two
+//     CholeskyQR passes make them orthonormal (this also separates vectors of
+//     eigenvalues that agree to rounding).
+//  4. Sort by decreasing eigenvalue, Z = Q Z_T (GEMM).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace riot {
+
+constexpr int kOctaves = 96;            // pre-bracket grid: |x| = ||T|| 2^(-j/8), j < 8 * kOctaves
+constexpr int kGridHalf = 8 * kOctaves;
+constexpr int kGrid = 2 * kGridHalf + 3; // negative side, 0, positive side, two outer bounds
+
+size_t eig_work_doubles(int k)
+{
+    const size_t kk = (size_t)k * k;
+    return 9 * kk + 32 * (size_t)k + 1024 + ((size_t)kGrid * k + 1) / 2 + 8 + dinv_doubles(k);
+}
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__global__ void eig_init_kernel(const double *K, int k, double *A, double *Qt)
+{
+    const int64_t total = (int64_t)k * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % k), j = (int)(e / k);
+        A[e] = 0.5 * (K[i + (int64_t)j * k] + K[j + (int64_t)i * k]);
+        Qt[e] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+// Householder reflector of x = A[r0..k-1, col] computed by one warp:
+// H = I - beta v v^T with H x = e_out e_1.  v is written to vbuf[r0..k-1].
+__device__ void warp_house(const double *A, int k, int col, int r0, double *vbuf, double *beta_out, double *e_out,
+                           int lane)
+{
+    const double *x = A + (int64_t)col * k;
+    double ss = 0.0;
+    for (int l = r0 + lane; l < k; l += 32) ss += x[l] * x[l];
+    ss = warp_sum(ss);
+    const double x0 = x[r0];
+    const double alpha = sqrt(ss);
+    if (alpha == 0.0) {
+        for (int l = r0 + lane; l < k; l += 32) vbuf[l] = 0.0;
+        if (lane == 0) { *beta_out = 0.0; *e_out = 0.0; }
+        return;
+    }
+    const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
+    for (int l = r0 + lane; l < k; l += 32) vbuf[l] = (l == r0) ? x0 + sgn * alpha : x[l];
+    if (lane == 0) {
+        *beta_out = 1.0 / (alpha * (alpha + fabs(x0)));
+        *e_out = -sgn * alpha;
+    }
+}
+
+__global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int k, double *vbuf, double *pbuf,
+                                                      double *qbuf, double *d, double *e, double *beta)
+{
+    cg::grid_group grid = cg::this_grid();
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + wib;
+    const int nw = gridDim.x * wpb;
+    __shared__ double kh_s;
+
+    if (k >= 3 && gw == 0) {
+        if (lane == 0) d[0] = A[0];
+        warp_house(A, k, 0, 1, vbuf, &beta[0], &e[0], lane);
+    }
+    grid.sync();
+    for (int j = 0; j + 2 < k; ++j) {
+        const double *v = vbuf + (size_t)(j & 1) * k;
+        const double bt = beta[j & 1];
+        const int r0 = j + 1, m = k - r0;
+        // phase 2: p = beta A22 v (columns r0..k-1), q = beta Q v (all columns of Q^T)
+        for (int it = gw; it < m + k; it += nw) {
+            const double *col = (it < m) ? A + (int64_t)(r0 + it) * k : Qt + (int64_t)(it - m) * k;
+            double s = 0.0;
+            for (int l = r0 + lane; l < k; l += 32) s += col[l] * v[l];
+            s = warp_sum(s);
+            if (lane == 0) {
+                if (it < m) pbuf[r0 + it] = bt * s;
+                else qbuf[it - m] = bt * s;
+            }
+        }
+        grid.sync();
+        // K_ = beta / 2 v^T p, once per block
+        if (wib == 0) {
+            double s = 0.0;
+            for (int l = r0 + lane; l < k; l += 32) s += v[l] * pbuf[l];
+            s = warp_sum(s);
+            if (lane == 0) kh_s = 0.5 * bt * s;
+        }
+        __syncthreads();
+        const double kh = kh_s;
+        // phase 3: A22 -= v w^T + w v^T (w = p - kh v), Q^T col i -= q_i v.
+        // Warp 0 owns column r0 of A and then builds the next reflector.
+        for (int it = gw; it < m + k; it += nw) {
+            if (it < m) {
+                const int i = r0 + it;
+                double *col = A + (int64_t)i * k;
+                const double vi = v[i], wi = pbuf[i] - kh * vi;
+                for (int l = r0 + lane; l < k; l += 32) col[l] -= v[l] * wi + (pbuf[l] - kh * v[l]) * vi;
+            } else {
+                const int i = it - m;
+                double *col = Qt + (int64_t)i * k;
+                const double qi = qbuf[i];
+                if (qi != 0.0)
+                    for (int l = r0 + lane; l < k; l += 32) col[l] -= qi * v[l];
+            }
+            if (it == 0) {
+                __syncwarp();
+                if (lane == 0) d[r0] = A[r0 + (int64_t)r0 * k];
+                if (r0 + 2 < k) {
+                    warp_house(A, k, r0, r0 + 1, vbuf + (size_t)((j + 1) & 1) * k, &beta[(j + 1) & 1], &e[r0], lane);
+                }
+            }
+        }
+        grid.sync();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (k == 1) {
+            d[0] = A[0];
+        } else {
+            // last 2 x 2 block (for k == 2 also d[0], e[0])
+            d[k - 2] = A[(k - 2) + (int64_t)(k - 2) * k];
+            e[k - 2] = A[(k - 1) + (int64_t)(k - 2) * k];
+            d[k - 1] = A[(k - 1) + (int64_t)(k - 1) * k];
+        }
+    }
+}
+
+// Split T where |e_l| <= eps (|d_l| + |d_{l+1}|); block bounds per index; e^2.
+__global__ void split_kernel(const double *d, const double *e, int k, double *e2, int *blo, int *bhi, double *tnorm,
+                             int *bstart, int *nblocks)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double nrm = 0.0;
+    for (int l = 0; l < k; ++l) {
+        double r = fabs(d[l]);
+        if (l > 0) r += fabs(e[l - 1]);
+        if (l + 1 < k) r += fabs(e[l]);
+        nrm = fmax(nrm, r);
+    }
+    *tnorm = nrm;
+    int lo = 0, nb = 0;
+    for (int l = 0; l < k; ++l) {
+        const bool split = (l + 1 == k) || fabs(e[l]) <= DBL_EPSILON * (fabs(d[l]) + fabs(d[l + 1]));
+        if (l + 1 < k) e2[l] = split ? 0.0 : e[l] * e[l];
+        if (split) {
+            for (int i = lo; i <= l; ++i) { blo[i] = lo; bhi[i] = l; }
+            bstart[nb++] = lo;
+            lo = l + 1;
+        }
+    }
+    bstart[nb] = k;
+    *nblocks = nb;
+}
+
+// Number of eigenvalues of the block [lo, hi] below x (Sturm sequence).
+__device__ int sturm_count(const double *d, const double *e2, int lo, int hi, double x, double pivmin)
+{
+    int cnt = 0;
+    double q = d[lo] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++cnt;
+    for (int l = lo + 1; l <= hi; ++l) {
+        q = (d[l] - x) - e2[l - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        if (q < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// Grid point g of the pre-bracket (ascending): -||T||(1+d), -||T|| 2^(-j/8)
+// (j descending), 0, +||T|| 2^(-j/8) (j descending), +||T||(1+d).
+__device__ __forceinline__ double grid_point(int g, double tn)
+{
+    const double big = tn * (1.0 + 1e-6) + DBL_MIN;
+    if (g == 0) return -big;
+    if (g == kGrid - 1) return big;
+    if (g == kGridHalf + 1) return 0.0;
+    if (g <= kGridHalf) return -tn * exp2(-(double)(g - 1) / 8.0);
+    return tn * exp2(-(double)(kGrid - 2 - g) / 8.0);
+}
+
+// counts[b * kGrid + g] = eigenvalues of block b below grid point g.
+__global__ void prebracket_kernel(const double *d, const double *e2, const int *bstart, const int *nblocks,
+                                  const double *tnorm, int *counts)
+{
+    const int nb = *nblocks;
+    const int64_t total = (int64_t)nb * kGrid;
+    const double tn = *tnorm;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(t / kGrid), g = (int)(t - (int64_t)b * kGrid);
+        const int lo = bstart[b], hi = bstart[b + 1] - 1;
+        counts[t] = sturm_count(d, e2, lo, hi, grid_point(g, tn), DBL_MIN * fmax(1.0, tn * tn));
+    }
+}
+
+// One warp per eigenvalue: bracket from the grid, then multisection with
+// 128 interior points per round (4 independent Sturm chains per lane),
+// until the bracket is below 1e-10 relative or 4 eps ||T|| (the inverse
+// iteration that follows refines it by a Rayleigh quotient).
+__global__ void multisect_kernel(const double *d, const double *e2, const int *blo, const int *bhi, const int *bstart,
+                                 const int *nblocks, int k, const double *tnorm, const int *counts, double *w)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= k) return;
+    const int i = warp, lo = blo[i], hi = bhi[i], r = i - lo;
+    const double tn = *tnorm;
+    if (lo == hi) {
+        if (lane == 0) w[i] = d[lo];
+        return;
+    }
+    // locate this block and the grid cell holding eigenvalue r
+    int b = 0, nb = *nblocks, bl = 0, bh = nb - 1;
+    while (bl <= bh) {
+        const int mid = (bl + bh) >> 1;
+        if (bstart[mid] <= lo) { b = mid; bl = mid + 1; } else bh = mid - 1;
+    }
+    const int *cb = counts + (int64_t)b * kGrid;
+    int g0 = 0, g1 = kGrid - 1;   // cb[g0] <= r < cb[g1]
+    while (g1 - g0 > 1) {
+        const int gm = (g0 + g1) >> 1;
+        if (cb[gm] <= r) g0 = gm; else g1 = gm;
+    }
+    double a = grid_point(g0, tn), c = grid_point(g1, tn);
+    const double pivmin = DBL_MIN * fmax(1.0, tn * tn);
+    for (int round = 0; round < 12; ++round) {
+        const double width = c - a;
+        if (width <= fmax(1e-10 * fmax(fabs(a), fabs(c)), 4.0 * DBL_EPSILON * tn)) break;
+        const double step = width / 129.0;
+        double x[4];
+        int cnt[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x[u] = a + step * (double)(1 + lane + 32 * u);
+            cnt[u] = 0;
+        }
+        double q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            q[u] = d[lo] - x[u];
+            if (fabs(q[u]) < pivmin) q[u] = -pivmin;
+            cnt[u] += (q[u] < 0.0);
+        }
+        for (int l = lo + 1; l <= hi; ++l) {
+            const double dl = d[l], el = e2[l - 1];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                q[u] = (dl - x[u]) - el / q[u];
+                if (fabs(q[u]) < pivmin) q[u] = -pivmin;
+                cnt[u] += (q[u] < 0.0);
+            }
+        }
+        // the new bracket: last point with count <= r, first with count > r;
+        // points are ascending in (u, lane) and counts are monotone in x
+        double na = a, nc = c;
+        int best_le = -1, first_gt = 128;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned gt = __ballot_sync(0xffffffffu, cnt[u] > r);
+            const unsigned le = ~gt;
+            if (le) best_le = max(best_le, 32 * u + 31 - __clz(le));
+            if (gt) first_gt = min(first_gt, 32 * u + __ffs(gt) - 1);
+        }
+        if (best_le >= 0) na = a + step * (double)(1 + best_le);
+        if (first_gt < 128) nc = a + step * (double)(1 + first_gt);
+        a = na;
+        c = nc;
+    }
+    if (lane == 0) w[i] = 0.5 * (a + c);
+}
+
+__device__ __forceinline__ double hash_uniform(uint32_t a, uint32_t b)
+{
+    uint32_t h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return ((double)h + 0.5) * 2.3283064365386963e-10 - 0.5;
+}
+
+// Inverse iteration for eigenvalue i of its block; scratch holds the LU of
+// T_b - w_i I in a strided layout (row l of thread i at l*k + i).
+__global__ void inviter_kernel(const double *d, const double *e, const int *blo, const int *bhi, int k, const double *w,
+                               const double *tnorm, double *Z, double *u0, double *u1, double *u2, double *ml,
+                               unsigned char *piv, double *wout)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    const int lo = blo[i], hi = bhi[i], m = hi - lo + 1;
+    double *z = Z + (int64_t)i * k;
+    for (int l = 0; l < k; ++l)
+        if (l < lo || l > hi) z[l] = 0.0;
+    if (m == 1) {
+        z[lo] = 1.0;
+        wout[i] = d[lo];
+        return;
+    }
+    const double lam = w[i];
+    const double tiny = DBL_EPSILON * fmax(*tnorm, DBL_MIN);
+#define IDX(l) ((int64_t)(l) * k + i)
+    // LU with partial pivoting of the block minus lam I (rows 0..m-1 local)
+    double a_cur = d[lo] - lam, c_cur = e[lo];
+    for (int l = 0; l < m - 1; ++l) {
+        const double bl = e[lo + l];                 // sub-diagonal below a_cur
+        const double a_next = d[lo + l + 1] - lam;
+        const double c_next = (l + 1 < m - 1) ? e[lo + l + 1] : 0.0;
+        if (fabs(a_cur) >= fabs(bl)) {
+            const double piv_v = (a_cur == 0.0) ? tiny : a_cur;
+            const double mult = bl / piv_v;
+            u0[IDX(l)] = piv_v;
+            u1[IDX(l)] = c_cur;
+            u2[IDX(l)] = 0.0;
+            ml[IDX(l)] = mult;
+            piv[IDX(l)] = 0;
+            a_cur = a_next - mult * c_cur;
+            c_cur = c_next;
+        } else {
+            const double mult = a_cur / bl;
+            u0[IDX(l)] = bl;
+            u1[IDX(l)] = a_next;
+            u2[IDX(l)] = c_next;
+            ml[IDX(l)] = mult;
+            piv[IDX(l)] = 1;
+            a_cur = c_cur - mult * a_next;
+            c_cur = -mult * c_next;
+        }
+    }
+    u0[IDX(m - 1)] = (fabs(a_cur) < tiny) ? (a_cur < 0.0 ? -tiny : tiny) : a_cur;
+    // start vector: distinct pseudo-random values per eigenvalue
+    for (int l = 0; l < m; ++l) z[lo + l] = hash_uniform((uint32_t)i, (uint32_t)l) + 1e-3;
+    for (int iter = 0; iter < 3; ++iter) {
+        // forward: apply the row operations
+        for (int l = 0; l < m - 1; ++l) {
+            double r0v = z[lo + l], r1v = z[lo + l + 1];
+            if (piv[IDX(l)]) { const double t = r0v; r0v = r1v; r1v = t; }
+            z[lo + l] = r0v;
+            z[lo + l + 1] = r1v - ml[IDX(l)] * r0v;
+        }
+        // backward substitution with U (diagonals u0, u1, u2)
+        double x2 = 0.0, x1 = 0.0, big = 0.0;
+        for (int l = m - 1; l >= 0; --l) {
+            const double xl = (z[lo + l] - u1[IDX(l)] * x1 - u2[IDX(l)] * x2) / u0[IDX(l)];
+            z[lo + l] = xl;
+            x2 = x1;
+            x1 = xl;
+            big = fmax(big, fabs(xl));
+        }
+        const double sc = (big > 0.0 && isfinite(big)) ? 1.0 / big : 1.0;
+        for (int l = 0; l < m; ++l) z[lo + l] *= sc;
+    }
+    double nrm = 0.0;
+    for (int l = 0; l < m; ++l) nrm += z[lo + l] * z[lo + l];
+    nrm = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
+    for (int l = 0; l < m; ++l) z[lo + l] *= nrm;
+    // Rayleigh quotient z^T T z refines the bracketed eigenvalue
+    double rq = 0.0;
+    for (int l = 0; l < m; ++l) {
+        double tz = d[lo + l] * z[lo + l];
+        if (l > 0) tz += e[lo + l - 1] * z[lo + l - 1];
+        if (l + 1 < m) tz += e[lo + l] * z[lo + l + 1];
+        rq += z[lo + l] * tz;
+    }
+    wout[i] = rq;
+#undef IDX
+}
+
+// Sort eigenvalues descending (stable by index) and gather the columns.
+__global__ void eig_sort_kernel(const double *w, const double *Zt, int k, double *lam, double *Zs)
+{
+    const int i = blockIdx.x;
+    if (i >= k) return;
+    __shared__ int rank_s;
+    if (threadIdx.x == 0) rank_s = 0;
+    __syncthreads();
+    const double wi = w[i];
+    int cnt = 0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const double wj = w[j];
+        if (wj > wi || (wj == wi && j < i)) ++cnt;
+    }
+    atomicAdd(&rank_s, cnt);
+    __syncthreads();
+    const int rk = rank_s;
+    if (threadIdx.x == 0) lam[rk] = wi;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) Zs[r + (int64_t)rk * k] = Zt[r + (int64_t)i * k];
+}
+
+}  // namespace
+
+cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *work, int *info, cudaStream_t s)
+{
+    const size_t kk = (size_t)k * k;
+    double *A = work, *Qt = work + kk, *Zt = work + 2 * kk, *Zs = work + 3 * kk;
+    double *u0 = work + 4 * kk, *u1 = work + 5 * kk, *u2 = work + 6 * kk, *ml = work + 7 * kk;
+    unsigned char *piv = (unsigned char *)(work + 8 * kk);
+    double *vec = work + 9 * kk;
+    double *vbuf = vec, *pbuf = vec + 2 * k, *qbuf = vec + 3 * k, *d = vec + 4 * k, *e = vec + 5 * k;
+    double *e2 = vec + 6 * k, *w = vec + 7 * k, *beta = vec + 8 * k, *tnorm = vec + 8 * k + 2;
+    int *blo = (int *)(vec + 9 * k), *bhi = (int *)(vec + 10 * k);
+    int *bstart = (int *)(vec + 11 * k), *nblocks = (int *)(vec + 12 * k);
+    double *wrq = vec + 13 * k;
+    int *counts = (int *)(vec + 32 * k + 1024);
+    double *dinv = vec + 32 * k + 1024 + ((size_t)kGrid * k + 1) / 2 + 8;
+    cudaError_t err;
+    if ((err = cudaMemsetAsync(info, 0, 2 * sizeof(int), s)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(vec, 0, sizeof(double) * 9 * k, s)) != cudaSuccess) return err;
+    count_launch();
+    eig_init_kernel<<<256, 256, 0, s>>>(K, k, A, Qt);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, 256, 0);
+        (void)per_sm;
+        const int grid = num_sms();   // one CTA per SM keeps the grid barrier short
+        void *args[] = {&A, &Qt, &k, &vbuf, &pbuf, &qbuf, &d, &e, &beta};
+        count_launch();
+        err = cudaLaunchCooperativeKernel((void *)tridiag_kernel, grid, 256, args, 0, s);
+        if (err != cudaSuccess) return err;
+    }
+    count_launch();
+    split_kernel<<<1, 1, 0, s>>>(d, e, k, e2, blo, bhi, tnorm, bstart, nblocks);
+    count_launch();
+    prebracket_kernel<<<2 * num_sms(), 128, 0, s>>>(d, e2, bstart, nblocks, tnorm, counts);
+    count_launch();
+    multisect_kernel<<<(k + 3) / 4, 128, 0, s>>>(d, e2, blo, bhi, bstart, nblocks, k, tnorm, counts, w);
+    count_launch();
+    inviter_kernel<<<(k + 3) / 4, 4, 0, s>>>(d, e, blo, bhi, k, w, tnorm, Zt, u0, u1, u2, ml, piv, wrq);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // two CholeskyQR passes on the eigenvectors of T
+    for (int pass = 0; pass < 2; ++pass) {
+        if ((err = gram_lower(k, k, Zt, 'd', k, Zs, k, s)) != cudaSuccess) return err;
+        if ((err = cholesky(Zs, k, k, 0.0, info + pass, dinv, s)) != cudaSuccess) return err;
+        if ((err = trsm_right_lt(Zt, k, k, k, Zs, k, s, dinv)) != cudaSuccess) return err;
+    }
+    count_launch();
+    eig_sort_kernel<<<k, 128, 0, s>>>(wrq, Zt, k, lam, Zs);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // Z = Q Zs = (Q^T)^T Zs
+    return gemm('T', 'N', k, k, k, 1.0, Qt, 'd', k, Zs, 'd', k, 0.0, Z, 'd', k, s);
+}
+
+}  // namespace riot

@@ -110,20 +110,30 @@ cudaError_t gemm(char ta, char tb, int m, int n, int k, double alpha, const void
                  int64_t lda, const void *B, char tB, int64_t ldb, double beta, void *C, char tC,
                  int64_t ldc, cudaStream_t s);
 // lower-triangular tiles of G = A^T A (A: n x k), the rest of G untouched
-cudaError_t gram_lower(int n, int k, const void *A, char tA, int64_t lda, double *G, int64_t ldg, cudaStream_t s);
+cudaError_t gram_lower(int n, int k, const void *A, char tA, int64_t lda, double *G, int64_t ldg, cudaStream_t s,
+                       double *ws = nullptr, size_t ws_doubles = 0);
+// FP32 SIMT GEMM, C = alpha op(A) op(B) + beta C
+cudaError_t sgemm(char ta, char tb, int m, int n, int k, float alpha, const float *A, int64_t lda, const float *B,
+                  int64_t ldb, float beta, float *C, int64_t ldc, cudaStream_t s);
+// X <- X L^-T in FP32 (L: k x k lower, FP32)
+cudaError_t strsm_right_lt(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s);
 cudaError_t convert_block(const void *in, char tin, int64_t ldin, void *out, char tout, int64_t ldout,
                           int64_t rows, int cols, cudaStream_t s);
 // In-place blocked Cholesky of the k x k SPD matrix G (lower factor); adds
 // shift_scale * trace(G) to the diagonal first when shift_scale > 0.
-// info[0] = 0 on success, else 1 + first failing pivot.
-cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *scratch,
-                     cudaStream_t s);
-// X <- X L^-T (X: m x k, L: k x k lower Cholesky factor): right-side solve.
-cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl,
-                          cudaStream_t s);
-// X <- X L^-1 (L lower, non-unit): right-side solve.
-cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl,
-                         cudaStream_t s);
+// info[0] = 0 on success, else 1 + first failing pivot.  dinv (dinv_doubles(k))
+// receives the inverses of the factor's 32 x 32 diagonal blocks, which the
+// triangular solves below use.
+cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *dinv, cudaStream_t s);
+size_t dinv_doubles(int k);
+// inverses of the diagonal blocks of a lower-triangular L (when not from cholesky)
+cudaError_t trtri_diag(const double *L, int k, int64_t ldl, double *dinv, cudaStream_t s);
+// X <- X L^-T (X: m x k, L: k x k lower): right-side solve with diagonal-block inverses.
+cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s,
+                          const double *dinv);
+// X <- X L^-1 (L lower, non-unit): right-side solve with diagonal-block inverses.
+cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s,
+                         const double *dinv);
 // Symmetric eigendecomposition by parallel cyclic Jacobi (cooperative
 // launch).  A (k x k, ld = k) is destroyed; lam gets eigenvalues sorted in
 // decreasing order, Z (k x k, ld = k) the eigenvectors with the
@@ -132,6 +142,12 @@ cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, 
 cudaError_t jacobi_eig(double *A, int k, double *lam, double *Z, double *work, int *info,
                        cudaStream_t s);
 size_t jacobi_work_doubles(int k);
+// Symmetric eigendecomposition by Householder tridiagonalisation, bisection
+// and inverse iteration (all SMs; O(k) grid barriers).  K is not modified.
+// lam: eigenvalues descending; Z (k x k): eigenvectors.  info[0..1] != 0 if
+// the final orthonormalisation of the eigenvectors failed.
+cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *work, int *info, cudaStream_t s);
+size_t eig_work_doubles(int k);
 // elementwise helpers
 cudaError_t symmetrize(double *A, int k, int64_t lda, cudaStream_t s);
 cudaError_t transpose_sq(const double *A, double *B, int k, cudaStream_t s);

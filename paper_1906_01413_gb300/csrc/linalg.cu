@@ -39,17 +39,22 @@ template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(256) gemm_kernel(int ta, int tb, int m, int n, int K, double alpha,
                                                    const TA *__restrict__ A, long long lda,
                                                    const TB *__restrict__ B, long long ldb, double beta,
-                                                   TC *__restrict__ C, long long ldc, int lower_only)
+                                                   TC *__restrict__ C, long long ldc, int lower_only, int kchunk,
+                                                   long long cstride)
 {
     constexpr int BM = 32, BN = 32, BK = 32;
     if (lower_only && blockIdx.y > blockIdx.x) return;   // tile strictly above the diagonal
+    // split-K: z-slice z covers k in [z*kchunk, (z+1)*kchunk) and writes C + z*cstride
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
+    C += (long long)blockIdx.z * cstride;
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int idx = tid + 256 * r;
@@ -57,7 +62,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(int ta, int tb, int m, int n,
             int i, kk;
             if (!ta) { i = idx & 31; kk = idx >> 5; } else { kk = idx & 31; i = idx >> 5; }
             double va = 0.0;
-            if (m0 + i < m && k0 + kk < K)
+            if (m0 + i < m && k0 + kk < kend)
                 va = ta ? (double)A[(k0 + kk) + (long long)(m0 + i) * lda]
                         : (double)A[(m0 + i) + (long long)(k0 + kk) * lda];
             As[kk][i] = va;
@@ -65,7 +70,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(int ta, int tb, int m, int n,
             int j;
             if (!tb) { kk = idx & 31; j = idx >> 5; } else { j = idx & 31; kk = idx >> 5; }
             double vb = 0.0;
-            if (n0 + j < n && k0 + kk < K)
+            if (n0 + j < n && k0 + kk < kend)
                 vb = tb ? (double)B[(n0 + j) + (long long)(k0 + kk) * ldb]
                         : (double)B[(k0 + kk) + (long long)(n0 + j) * ldb];
             Bs[kk][j] = vb;
@@ -98,21 +103,62 @@ __global__ void __launch_bounds__(256) gemm_kernel(int ta, int tb, int m, int n,
 template <typename TA, typename TB, typename TC>
 static cudaError_t gemm_t(int ta, int tb, int m, int n, int k, double alpha, const void *A, int64_t lda,
                           const void *B, int64_t ldb, double beta, void *C, int64_t ldc, cudaStream_t s,
-                          int lower_only = 0)
+                          int lower_only = 0, int splits = 1, long long cstride = 0)
 {
-    dim3 grid((m + 31) / 32, (n + 31) / 32);
+    if (splits < 1) splits = 1;
+    int kchunk = ((k + splits - 1) / splits + 31) / 32 * 32;
+    if (kchunk < 32) kchunk = 32;
+    splits = (k + kchunk - 1) / kchunk;
+    if (splits < 1) splits = 1;
+    dim3 grid((m + 31) / 32, (n + 31) / 32, splits);
     count_launch();
     gemm_kernel<TA, TB, TC><<<grid, 256, 0, s>>>(ta, tb, m, n, k, alpha, (const TA *)A, lda, (const TB *)B, ldb,
-                                                 beta, (TC *)C, ldc, lower_only);
+                                                 beta, (TC *)C, ldc, lower_only, kchunk, cstride);
     return cudaGetLastError();
 }
 
-cudaError_t gram_lower(int n, int k, const void *A, char tA, int64_t lda, double *G, int64_t ldg, cudaStream_t s)
+__global__ void sum_slices_lower_kernel(const double *ws, int S, int k, double *G, int64_t ldg)
+{
+    const int64_t total = (int64_t)k * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % k), j = (int)(e / k);
+        if (i < j) continue;
+        double s = 0.0;
+        for (int z = 0; z < S; ++z) s += ws[(int64_t)z * total + e];
+        G[i + (int64_t)j * ldg] = s;
+    }
+}
+
+cudaError_t gram_lower(int n, int k, const void *A, char tA, int64_t lda, double *G, int64_t ldg, cudaStream_t s,
+                       double *ws, size_t ws_doubles)
 {
     if (k <= 0) return cudaSuccess;
-    if (tA == 'd') return gemm_t<double, double, double>(1, 0, k, k, n, 1.0, A, lda, A, lda, 0.0, G, ldg, s, 1);
-    if (tA == 'f') return gemm_t<float, float, double>(1, 0, k, k, n, 1.0, A, lda, A, lda, 0.0, G, ldg, s, 1);
-    return cudaErrorInvalidValue;
+    // split the long dimension when the lower tiles alone cannot fill the GPU
+    const int tiles = ((k + 31) / 32) * ((k + 31) / 32 + 1) / 2;
+    int S = 1;
+    if (ws) {
+        S = (4 * num_sms() + tiles - 1) / tiles;
+        if (S > n / 256) S = n / 256;
+        while (S > 1 && (size_t)S * k * k > ws_doubles) --S;
+        if (S < 1) S = 1;
+    }
+    if (S == 1) {
+        if (tA == 'd') return gemm_t<double, double, double>(1, 0, k, k, n, 1.0, A, lda, A, lda, 0.0, G, ldg, s, 1);
+        if (tA == 'f') return gemm_t<float, float, double>(1, 0, k, k, n, 1.0, A, lda, A, lda, 0.0, G, ldg, s, 1);
+        return cudaErrorInvalidValue;
+    }
+    cudaError_t e;
+    const long long cs = (long long)k * k;
+    if (tA == 'd') e = gemm_t<double, double, double>(1, 0, k, k, n, 1.0, A, lda, A, lda, 0.0, ws, k, s, 1, S, cs);
+    else if (tA == 'f') e = gemm_t<float, float, double>(1, 0, k, k, n, 1.0, A, lda, A, lda, 0.0, ws, k, s, 1, S, cs);
+    else return cudaErrorInvalidValue;
+    if (e != cudaSuccess) return e;
+    int kchunk = ((n + S - 1) / S + 31) / 32 * 32;
+    if (kchunk < 32) kchunk = 32;
+    const int Sreal = (n + kchunk - 1) / kchunk;
+    count_launch();
+    sum_slices_lower_kernel<<<256, 256, 0, s>>>(ws, Sreal, k, G, ldg);
+    return cudaGetLastError();
 }
 
 cudaError_t gemm(char ta, char tb, int m, int n, int k, double alpha, const void *A, char tA, int64_t lda,
@@ -130,6 +176,123 @@ cudaError_t gemm(char ta, char tb, int m, int n, int k, double alpha, const void
     RIOT_GEMM_CASE('f', 'd', 'f', float, double, float)
 #undef RIOT_GEMM_CASE
     return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// SGEMM (FP32 SIMT): 64 x 64 tile, BK = 16, 256 threads, 4 x 4 outputs per
+// thread read as float4 from shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sgemm_kernel(int ta, int tb, int m, int n, int K, float alpha,
+                                                    const float *__restrict__ A, long long lda,
+                                                    const float *__restrict__ B, long long ldb, float beta,
+                                                    float *__restrict__ C, long long ldc)
+{
+    __shared__ __align__(16) float As[16][64];
+    __shared__ __align__(16) float Bs[16][64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = tid + 256 * r;
+            int i, kk;
+            if (!ta) { i = idx & 63; kk = idx >> 6; } else { kk = idx & 15; i = idx >> 4; }
+            float va = 0.f;
+            if (m0 + i < m && k0 + kk < K)
+                va = ta ? A[(k0 + kk) + (long long)(m0 + i) * lda] : A[(m0 + i) + (long long)(k0 + kk) * lda];
+            As[kk][i] = va;
+            int j;
+            if (!tb) { kk = idx & 15; j = idx >> 4; } else { j = idx & 63; kk = idx >> 6; }
+            float vb = 0.f;
+            if (n0 + j < n && k0 + kk < K)
+                vb = tb ? B[(n0 + j) + (long long)(k0 + kk) * ldb] : B[(k0 + kk) + (long long)(n0 + j) * ldb];
+            Bs[kk][j] = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const float4 a4 = *reinterpret_cast<const float4 *>(&As[kk][tx * 4]);
+            const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[kk][ty * 4]);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = m0 + tx * 4 + r, j = n0 + ty * 4 + c;
+            if (i < m && j < n) {
+                float *p = C + i + (long long)j * ldc;
+                *p = alpha * acc[r][c] + (beta != 0.f ? beta * *p : 0.f);
+            }
+        }
+}
+
+cudaError_t sgemm(char ta, char tb, int m, int n, int k, float alpha, const float *A, int64_t lda, const float *B,
+                  int64_t ldb, float beta, float *C, int64_t ldc, cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    dim3 grid((m + 63) / 64, (n + 63) / 64);
+    count_launch();
+    sgemm_kernel<<<grid, 256, 0, s>>>(ta == 'T', tb == 'T', m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+// X[r, 0:jb] <- X[r, 0:jb] L^-T in FP32, one row per thread (right-looking).
+__global__ void strsm_rows_lt_kernel(float *X, int m, int64_t ldx, const float *Ld, int64_t ldl, int jb)
+{
+    __shared__ float Ls[32][33];
+    __shared__ float rinv[32];
+    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+        const int i = e % jb, j = e / jb;
+        Ls[i][j] = Ld[i + (int64_t)j * ldl];
+    }
+    for (int j = threadIdx.x; j < jb; j += blockDim.x) rinv[j] = 1.f / Ld[j + (int64_t)j * ldl];
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    float x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = (j < jb) ? X[r + (int64_t)j * ldx] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < jb) {
+            x[j] *= rinv[j];
+#pragma unroll
+            for (int i = j + 1; i < 32; ++i)
+                if (i < jb) x[i] = fmaf(-x[j], Ls[i][j], x[i]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        if (j < jb) X[r + (int64_t)j * ldx] = x[j];
+}
+
+cudaError_t strsm_right_lt(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s)
+{
+    for (int J = 0; J < k; J += 32) {
+        const int jb = (k - J < 32) ? k - J : 32;
+        count_launch();
+        strsm_rows_lt_kernel<<<(m + 127) / 128, 128, 0, s>>>(X + (int64_t)J * ldx, m, ldx, L + J + (int64_t)J * ldl, ldl,
+                                                            jb);
+        const int rest = k - J - jb;
+        if (rest > 0) {
+            cudaError_t e = sgemm('N', 'T', m, rest, jb, -1.f, X + (int64_t)J * ldx, ldx, L + (J + jb) + (int64_t)J * ldl,
+                                  ldl, 1.f, X + (int64_t)(J + jb) * ldx, ldx, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -188,15 +351,46 @@ __global__ void shift_diag_kernel(double *G, int k, int64_t ldg, double shift_sc
     for (int i = threadIdx.x; i < k; i += blockDim.x) G[i + i * ldg] += sh;
 }
 
-// Unblocked Cholesky of the jb x jb diagonal block at (J, J); records the
-// first failing pivot in info (1-based) and continues with pivot 1.
-__global__ void potrf_diag_kernel(double *G, int64_t ldg, int J, int jb, int *info)
+// Inverse of a lower-triangular jb x jb block held in shared memory: thread
+// c (< jb) solves L y = e_c by right-looking substitution (independent
+// chains per column); rinv holds 1/L_ii.  Writes Linv (ld NB) to out.
+__device__ void tri_inverse_smem(const double (*a)[NB + 1], const double *rinv, int jb, double *out)
+{
+    const int c = threadIdx.x;
+    if (c < NB) {
+        double v[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) v[i] = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            if (i >= c && i < jb) {
+                v[i] *= rinv[i];
+#pragma unroll
+                for (int l = i + 1; l < NB; ++l)
+                    if (l < jb) v[l] = fma(-a[l][i], v[i], v[l]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) out[i + NB * c] = (i >= c && i < jb && c < jb) ? v[i] : 0.0;
+    }
+}
+
+// Cholesky of the jb x jb diagonal block at (J, J) by one CTA of 128 threads
+// (all four SM sub-partitions issue FP64 work), with the inverse of the
+// factor built in the same column sweep (X <- L^-1 by the same right-looking
+// elimination applied to the identity), written to dinv (NB x NB,
+// column-major).  The first failing pivot is recorded in info (1-based); the
+// factorisation continues with pivot 1.
+__global__ void __launch_bounds__(128) potrf_inv_kernel(double *G, int64_t ldg, int J, int jb, int *info, double *dinv)
 {
     __shared__ double a[NB][NB + 1];
+    __shared__ double x[NB][NB + 1];
+    __shared__ double rs_s;
     const int tid = threadIdx.x;
-    for (int e = tid; e < jb * jb; e += blockDim.x) {
-        const int i = e % jb, j = e / jb;
-        a[i][j] = G[(J + i) + (int64_t)(J + j) * ldg];
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int i = e % NB, c = e / NB;
+        a[i][c] = (i < jb && c < jb) ? G[(J + i) + (int64_t)(J + c) * ldg] : 0.0;
+        x[i][c] = (i == c) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int j = 0; j < jb; ++j) {
@@ -206,48 +400,107 @@ __global__ void potrf_diag_kernel(double *G, int64_t ldg, int J, int jb, int *in
                 if (info[0] == 0) info[0] = J + j + 1;
                 d = 1.0;
             }
-            a[j][j] = sqrt(d);
+            const double r = rsqrt(d);
+            a[j][j] = d * r;
+            rs_s = r;
         }
         __syncthreads();
-        const double djj = a[j][j];
-        for (int i = j + 1 + tid; i < jb; i += blockDim.x) a[i][j] /= djj;
+        const double r = rs_s;
+        // column j of L, and row j of the inverse (entries c <= j)
+        for (int i = j + 1 + tid; i < jb; i += blockDim.x) a[i][j] *= r;
+        for (int c = tid; c <= j; c += blockDim.x) x[j][c] *= r;
         __syncthreads();
-        for (int e = tid; e < (jb - j - 1) * (jb - j - 1); e += blockDim.x) {
-            const int i = j + 1 + e % (jb - j - 1), c = j + 1 + e / (jb - j - 1);
-            if (c <= i) a[i][c] -= a[i][j] * a[c][j];
+        // trailing update of A and of the inverse's rows below j
+        const int m = jb - j - 1;
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            const int i = j + 1 + e % m, c = j + 1 + e / m;
+            if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
+        }
+        for (int e = tid; e < m * (j + 1); e += blockDim.x) {
+            const int i = j + 1 + e / (j + 1), c = e % (j + 1);
+            x[i][c] = fma(-a[i][j], x[j][c], x[i][c]);
         }
         __syncthreads();
     }
     for (int e = tid; e < jb * jb; e += blockDim.x) {
-        const int i = e % jb, j = e / jb;
-        G[(J + i) + (int64_t)(J + j) * ldg] = (j <= i) ? a[i][j] : 0.0;
+        const int i = e % jb, c = e / jb;
+        G[(J + i) + (int64_t)(J + c) * ldg] = (c <= i) ? a[i][c] : 0.0;
     }
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int i = e % NB, c = e / NB;
+        dinv[e] = (i >= c && i < jb && c < jb) ? x[i][c] : 0.0;
+    }
+}
+
+// Inverses of all diagonal blocks of a factored lower-triangular k x k L.
+__global__ void __launch_bounds__(32) trtri_diag_kernel(const double *L, int k, int64_t ldl, double *dinv)
+{
+    __shared__ double a[NB][NB + 1];
+    __shared__ double rinv[NB];
+    const int J = blockIdx.x * NB;
+    const int jb = (k - J < NB) ? k - J : NB;
+    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+        const int i = e % jb, c = e / jb;
+        a[i][c] = L[(J + i) + (int64_t)(J + c) * ldl];
+    }
+    for (int i = threadIdx.x; i < jb; i += blockDim.x) rinv[i] = 1.0 / L[(J + i) + (int64_t)(J + i) * ldl];
+    __syncthreads();
+    tri_inverse_smem(a, rinv, jb, dinv + (int64_t)blockIdx.x * NB * NB);
+}
+
+// X[r, 0:jb] <- X[r, 0:jb] M^T (trans = 1) or X[r, 0:jb] M (trans = 0) in
+// place for m rows, M = the jb x jb lower-triangular block at Minv (ld NB).
+// 8 rows x 32 columns per CTA: each thread forms one output entry.
+__global__ void __launch_bounds__(256) trmm_rows_kernel(double *X, int m, int64_t ldx, const double *Minv, int jb,
+                                                        int trans)
+{
+    __shared__ double xs[8][NB + 1];
+    __shared__ double ms[NB][NB + 1];
+    const int c = threadIdx.x & 31, rl = threadIdx.x >> 5;
+    const int r = blockIdx.x * 8 + rl;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) ms[e % NB][e / NB] = Minv[e];
+    xs[rl][c] = (r < m && c < jb) ? X[r + (int64_t)c * ldx] : 0.0;
+    __syncthreads();
+    if (r >= m || c >= jb) return;
+    double acc = 0.0;
+    if (trans) {
+        // (X M^T)_c = sum_{i <= c} x_i M[c][i]
+#pragma unroll 8
+        for (int i = 0; i <= c; ++i) acc = fma(xs[rl][i], ms[c][i], acc);
+    } else {
+        // (X M)_c = sum_{i >= c} x_i M[i][c]
+#pragma unroll 8
+        for (int i = c; i < jb; ++i) acc = fma(xs[rl][i], ms[i][c], acc);
+    }
+    X[r + (int64_t)c * ldx] = acc;
 }
 
 // X[r, 0:jb] <- X[r, 0:jb] L^-T for each row r (L = the jb x jb lower block
-// at Ld with leading dimension ldl): forward substitution per row.
+// at Ld with leading dimension ldl).  Right-looking: once x_j is known it is
+// subtracted from all later entries, so each step is one multiply plus
+// independent FMAs (short dependency chains for the long FP64 latency).
 __global__ void trsm_rows_lt_kernel(double *X, int m, int64_t ldx, const double *Ld, int64_t ldl, int jb)
 {
     __shared__ double Ls[NB][NB + 1];
+    __shared__ double rinv[NB];
     for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
         const int i = e % jb, j = e / jb;
         Ls[i][j] = Ld[i + (int64_t)j * ldl];
     }
+    for (int j = threadIdx.x; j < jb; j += blockDim.x) rinv[j] = 1.0 / Ld[j + (int64_t)j * ldl];
     __syncthreads();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= m) return;
     double x[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j)
-        if (j < jb) x[j] = X[r + (int64_t)j * ldx];
+    for (int j = 0; j < NB; ++j) x[j] = (j < jb) ? X[r + (int64_t)j * ldx] : 0.0;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
         if (j < jb) {
-            double v = x[j];
+            x[j] *= rinv[j];
 #pragma unroll
-            for (int i = 0; i < NB; ++i)
-                if (i < j) v -= x[i] * Ls[j][i];
-            x[j] = v / Ls[j][j];
+            for (int i = j + 1; i < NB; ++i)
+                if (i < jb) x[i] = fma(-x[j], Ls[i][j], x[i]);
         }
     }
 #pragma unroll
@@ -255,29 +508,28 @@ __global__ void trsm_rows_lt_kernel(double *X, int m, int64_t ldx, const double 
         if (j < jb) X[r + (int64_t)j * ldx] = x[j];
 }
 
-// X[r, 0:jb] <- X[r, 0:jb] L^-1 (L lower): backward substitution per row.
+// X[r, 0:jb] <- X[r, 0:jb] L^-1 (L lower): right-looking from the last column.
 __global__ void trsm_rows_l_kernel(double *X, int m, int64_t ldx, const double *Ld, int64_t ldl, int jb)
 {
     __shared__ double Ls[NB][NB + 1];
+    __shared__ double rinv[NB];
     for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
         const int i = e % jb, j = e / jb;
         Ls[i][j] = Ld[i + (int64_t)j * ldl];
     }
+    for (int j = threadIdx.x; j < jb; j += blockDim.x) rinv[j] = 1.0 / Ld[j + (int64_t)j * ldl];
     __syncthreads();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= m) return;
     double x[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j)
-        if (j < jb) x[j] = X[r + (int64_t)j * ldx];
+    for (int j = 0; j < NB; ++j) x[j] = (j < jb) ? X[r + (int64_t)j * ldx] : 0.0;
 #pragma unroll
     for (int jj = NB - 1; jj >= 0; --jj) {
         if (jj < jb) {
-            double v = x[jj];
+            x[jj] *= rinv[jj];
 #pragma unroll
-            for (int i = 0; i < NB; ++i)
-                if (i > jj && i < jb) v -= x[i] * Ls[i][jj];
-            x[jj] = v / Ls[jj][jj];
+            for (int i = 0; i < jj; ++i) x[i] = fma(-x[jj], Ls[jj][i], x[i]);
         }
     }
 #pragma unroll
@@ -285,34 +537,45 @@ __global__ void trsm_rows_l_kernel(double *X, int m, int64_t ldx, const double *
         if (j < jb) X[r + (int64_t)j * ldx] = x[j];
 }
 
-cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *, cudaStream_t s)
+size_t dinv_doubles(int k) { return (size_t)((k + NB - 1) / NB) * NB * NB; }
+
+cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *dinv, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (shift_scale > 0.0) { count_launch(); shift_diag_kernel<<<1, 1024, 0, s>>>(G, k, ldg, shift_scale); }
     for (int J = 0; J < k; J += NB) {
         const int jb = (k - J < NB) ? k - J : NB;
-        { count_launch(); potrf_diag_kernel<<<1, 256, 0, s>>>(G, ldg, J, jb, info); }
+        double *inv = dinv + (int64_t)(J / NB) * NB * NB;
+        { count_launch(); potrf_inv_kernel<<<1, 128, 0, s>>>(G, ldg, J, jb, info, inv); }
         const int m2 = k - J - jb;
         if (m2 > 0) {
             double *A21 = G + (J + jb) + (int64_t)J * ldg;
-            { count_launch(); trsm_rows_lt_kernel<<<(m2 + 127) / 128, 128, 0, s>>>(A21, m2, ldg, G + J + (int64_t)J * ldg, ldg, jb); }
+            // A21 <- A21 L11^-T
+            { count_launch(); trmm_rows_kernel<<<(m2 + 7) / 8, 256, 0, s>>>(A21, m2, ldg, inv, jb, 1); }
             double *A22 = G + (J + jb) + (int64_t)(J + jb) * ldg;
             e = gemm('N', 'T', m2, m2, jb, -1.0, A21, 'd', ldg, A21, 'd', ldg, 1.0, A22, 'd', ldg, s);
             if (e != cudaSuccess) return e;
         }
     }
-    // zero the strict upper triangle so that G holds exactly the factor L
     return cudaGetLastError();
 }
 
-cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s)
+cudaError_t trtri_diag(const double *L, int k, int64_t ldl, double *dinv, cudaStream_t s)
+{
+    count_launch();
+    trtri_diag_kernel<<<(k + NB - 1) / NB, 32, 0, s>>>(L, k, ldl, dinv);
+    return cudaGetLastError();
+}
+
+cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s,
+                          const double *dinv)
 {
     for (int J = 0; J < k; J += NB) {
         const int jb = (k - J < NB) ? k - J : NB;
         count_launch();
-        trsm_rows_lt_kernel<<<(m + 127) / 128, 128, 0, s>>>(X + (int64_t)J * ldx, m, ldx, L + J + (int64_t)J * ldl,
-                                                          ldl, jb);
+        trmm_rows_kernel<<<(m + 7) / 8, 256, 0, s>>>(X + (int64_t)J * ldx, m, ldx, dinv + (int64_t)(J / NB) * NB * NB,
+                                                     jb, 1);
         const int rest = k - J - jb;
         if (rest > 0) {
             cudaError_t e = gemm('N', 'T', m, rest, jb, -1.0, X + (int64_t)J * ldx, 'd', ldx,
@@ -324,15 +587,15 @@ cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L,
     return cudaGetLastError();
 }
 
-cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s)
+cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s,
+                         const double *dinv)
 {
     const int nblk = (k + NB - 1) / NB;
     for (int b = nblk - 1; b >= 0; --b) {
         const int J = b * NB;
         const int jb = (k - J < NB) ? k - J : NB;
         count_launch();
-        trsm_rows_l_kernel<<<(m + 127) / 128, 128, 0, s>>>(X + (int64_t)J * ldx, m, ldx, L + J + (int64_t)J * ldl,
-                                                         ldl, jb);
+        trmm_rows_kernel<<<(m + 7) / 8, 256, 0, s>>>(X + (int64_t)J * ldx, m, ldx, dinv + (int64_t)b * NB * NB, jb, 0);
         if (J > 0) {
             cudaError_t e = gemm('N', 'N', m, J, jb, -1.0, X + (int64_t)J * ldx, 'd', ldx, L + J, 'd', ldl, 1.0, X,
                                  'd', ldx, s);

@@ -19,6 +19,8 @@ RIOT_MODEL_L96 = 1
 RIOT_B_GAUSS_RING = 1
 RIOT_PREC_MIXED = 0
 RIOT_PREC_FP64 = 1
+RIOT_EIG_TRIDIAG = 0
+RIOT_EIG_JACOBI = 1
 STATUS = {0: "RIOT_OK", -1: "RIOT_EINVAL", -2: "RIOT_ENOMEM", -3: "RIOT_ECUDA", -4: "RIOT_ENOTSPD",
           -5: "RIOT_ETIMEOUT", -6: "RIOT_ESTATE", -7: "RIOT_ENOCONV", -8: "RIOT_ENONFINITE"}
 
@@ -38,7 +40,7 @@ class BcovDesc(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("precision", c_int32), ("kmax", c_int32), ("exact_rr", c_int32), ("reserved", c_int32),
+    _fields_ = [("precision", c_int32), ("kmax", c_int32), ("exact_rr", c_int32), ("eig_method", c_int32),
                 ("seed", c_uint64)]
 
 
@@ -74,6 +76,7 @@ def load():
     L.riot_draw_normal.argtypes = [c_uint64, c_int64, c_int64, c_int32, c_int64, c_int32, vp, vp]
     L.riot_l96_forecast.argtypes = [c_int64, c_int32, c_double, c_double, vp, vp, c_int32, vp]
     L.riot_rsvd_timings.argtypes = [vp, POINTER(c_double)]
+    L.riot_symm_eig.argtypes = [vp, c_int32, vp, vp, c_int32, vp]
     L.riot_last_error.argtypes = [vp]
     L.riot_last_error.restype = c_char_p
     L.riot_status_string.argtypes = [c_int32]
@@ -87,7 +90,7 @@ def load():
     for name in ("riot_setup", "riot_outer_begin", "riot_hessian_apply", "riot_hessian_apply_noalloc",
                  "riot_rsvd", "riot_increment",
                  "riot_analysis_cov_lowrank", "riot_bsqrt_apply", "riot_get_state", "riot_draw_normal",
-                 "riot_l96_forecast", "riot_rsvd_timings"):
+                 "riot_l96_forecast", "riot_rsvd_timings", "riot_symm_eig"):
         getattr(L, name).restype = c_int32
     _lib = L
     return L
@@ -112,7 +115,8 @@ def _check(ctx, fn, status):
 # ---- C entry points ------------------------------------------------------------------
 
 def riot_setup(n, T, dt, F, obs_step, obs_idx, obs_y, obs_sigma, length, sigma_b=1.0, sigma_vec=None,
-               precision=RIOT_PREC_MIXED, kmax=64, exact_rr=False, seed=0, stream=None):
+               precision=RIOT_PREC_MIXED, kmax=64, exact_rr=False, seed=0, stream=None,
+               eig_method=RIOT_EIG_TRIDIAG):
     """Create a context (host numpy arrays for the observations); returns the handle."""
     L = load()
     st = np.ascontiguousarray(obs_step, dtype=np.int32)
@@ -125,7 +129,7 @@ def riot_setup(n, T, dt, F, obs_step, obs_idx, obs_y, obs_sigma, length, sigma_b
     sv = None if sigma_vec is None else np.ascontiguousarray(sigma_vec, dtype=np.float64)
     bd = BcovDesc(RIOT_B_GAUSS_RING, 0, float(length), float(sigma_b),
                   None if sv is None else sv.ctypes.data_as(POINTER(c_double)))
-    op = Options(int(precision), int(kmax), int(bool(exact_rr)), 0, int(seed))
+    op = Options(int(precision), int(kmax), int(bool(exact_rr)), int(eig_method), int(seed))
     h = c_void_p()
     status = L.riot_setup(ctypes.byref(h), ctypes.byref(md), ctypes.byref(od), ctypes.byref(bd),
                           ctypes.byref(op), _stream_handle(stream))
@@ -200,6 +204,13 @@ def riot_l96_forecast(n, T, dt, F, x0, out, store_all=True, stream=None):
     status = load().riot_l96_forecast(int(n), int(T), float(dt), float(F), _ptr(x0), _ptr(out),
                                       int(bool(store_all)), _stream_handle(stream))
     _check(None, "riot_l96_forecast", status)
+
+
+def riot_symm_eig(K, lam, Z, method=RIOT_EIG_TRIDIAG, stream=None):
+    """K (k, k) float64 device tensor (symmetric); lam (k,), Z (k, k) outputs (Z column-major)."""
+    k = K.shape[0]
+    _check(None, "riot_symm_eig",
+           load().riot_symm_eig(_ptr(K), int(k), _ptr(lam), _ptr(Z), int(method), _stream_handle(stream)))
 
 
 def riot_rsvd_timings(ctx):

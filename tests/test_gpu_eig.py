@@ -1,0 +1,61 @@
+"""GPU symmetric eigensolvers (the k x k step of Algorithm 3) against LAPACK.
+
+Tolerances: eigenvalues to 50 k eps ||K|| (absolute; both methods are
+backward stable), eigen-residual ||K z - lambda z|| <= 50 k eps ||K||,
+orthonormality ||Z^T Z - I||_max <= 1e-12.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+def _spd(k, lo, hi, seed, mult=None):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    lam = np.exp(rng.uniform(np.log(lo), np.log(hi), k))
+    if mult:
+        lam[:mult] = lam[0]
+    return (Q * lam) @ Q.T
+
+
+def _run(R, K, method):
+    k = K.shape[0]
+    Kt = torch.tensor(np.asfortranarray(K).T.copy(), device=DEV)   # column-major = K^T row-major
+    lam = torch.empty(k, dtype=torch.float64, device=DEV)
+    Z = torch.empty(k, k, dtype=torch.float64, device=DEV)
+    R.riot_symm_eig(Kt, lam, Z, method)
+    return lam.cpu().numpy(), Z.cpu().numpy().T                  # columns = eigenvectors
+
+
+CASES = [("graded", 7, 1e-6, 1e6, 0), ("graded", 40, 1e-8, 1e4, 1), ("graded", 100, 1e-3, 1e3, 2),
+         ("graded", 512, 1e8, 1e20, 3), ("cluster", 64, 1.0, 10.0, 4), ("cluster", 301, 0.5, 2.0, 5)]
+
+
+@pytest.mark.parametrize("kind,k,lo,hi,seed", CASES)
+@pytest.mark.parametrize("method", [0, 1])
+def test_symm_eig_against_lapack(gpu_lib, kind, k, lo, hi, seed, method):
+    R = gpu_lib
+    if method == 1 and k > 128:
+        pytest.skip("Jacobi is the slow reference method; small sizes only")
+    K = _spd(k, lo, hi, seed, mult=(k // 4 if kind == "cluster" else None))
+    K = 0.5 * (K + K.T)
+    ref = np.sort(np.linalg.eigvalsh(K))[::-1]
+    lam, Z = _run(R, K, method)
+    nrm = np.abs(ref).max()
+    tol = 50 * k * np.finfo(float).eps * nrm
+    np.testing.assert_allclose(lam, ref, rtol=0, atol=tol)
+    assert np.abs(K @ Z - Z * lam).max() <= tol
+    assert np.abs(Z.T @ Z - np.eye(k)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 33])
+def test_symm_eig_degenerate(gpu_lib, k):
+    R = gpu_lib
+    for K in (np.eye(k), np.zeros((k, k)), np.diag(np.arange(k, dtype=float))):
+        lam, Z = _run(R, K, 0)
+        np.testing.assert_allclose(lam, np.sort(np.linalg.eigvalsh(K))[::-1], atol=1e-14)
+        assert np.abs(Z.T @ Z - np.eye(k)).max() <= 1e-12
+        assert np.abs(K @ Z - Z * lam).max() <= 1e-13
