@@ -230,6 +230,12 @@ riot_status riot_symm_eig(const double *K_dev, int32_t k, double *lambda_dev, do
  * Synchronises. */
 riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6);
 
+/* Launch shape of the mixed-precision Hessian kernel: sketch columns per CTA
+ * and depth of its shared-memory ring of streamed stage coefficients (2..8);
+ * 0 = automatic.  A shape that does not fit the device falls back to the
+ * automatic choice.  Used by the autotuner; results do not depend on it. */
+riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t ring_depth);
+
 /* Number of Jacobi sweeps of the last successful riot_rsvd (-1: no context). */
 int32_t riot_rsvd_sweeps(const riot_ctx *ctx);
 

@@ -23,6 +23,7 @@ struct riot_ctx {
     cudaStream_t s = nullptr;
     int prec = RIOT_PREC_MIXED;
     int kmax = 0, exact_rr = 0, eig_method = 0;
+    int hvp_P = 0, hvp_S = 0;   // launch shape of the FP32 Hessian kernel (0 = automatic)
     uint64_t seed = 0;
     L96Dev m;
     std::vector<void *> allocs;
@@ -149,7 +150,7 @@ riot_status hvp(riot_ctx *ctx, const void *W, void *Y, int64_t ld, int ncols, in
                                   (double *)ctx->rscr, 0, ctx->s));
         else
             CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
-                                  (float *)ctx->rscr, 0, ctx->errflag, ctx->s));
+                                  (float *)ctx->rscr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S));
     }
     return RIOT_OK;
 }
@@ -474,7 +475,7 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
                                   (double *)scr, 0, ctx->s));
         else
             CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
-                                  (float *)scr, 0, ctx->errflag, ctx->s));
+                                  (float *)scr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S));
     }
     return RIOT_OK;
 }
@@ -605,6 +606,16 @@ riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6)
 }
 
 int32_t riot_rsvd_sweeps(const riot_ctx *ctx) { return ctx ? ctx->jacobi_sweeps : -1; }
+
+riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t ring_depth)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (probes_per_cta < 0 || probes_per_cta > 64 || ring_depth < 0 || ring_depth > 8 || ring_depth == 1)
+        return fail(ctx, RIOT_EINVAL, "probes_per_cta in [0, 64], ring_depth 0 or in [2, 8]");
+    ctx->hvp_P = probes_per_cta;
+    ctx->hvp_S = ring_depth;
+    return RIOT_OK;
+}
 
 riot_status riot_increment(riot_ctx *ctx, double *dv_dev, int32_t *mode_out)
 {

@@ -69,18 +69,17 @@ struct L96Dev {
 };
 
 // Nonlinear FP64 trajectory of one state; writes traj (T+1)*n (natural
-// layout, may be null), stage coefficients (float2 / double2, may be null),
+// layout, may be null), stage coefficients (may be null): double2 by slot
+// t*E + j, and float2 interleaved by element pair ((j/2)*Tp + t as float4),
 // the innovation d = H(x) - y (may be null) and 1/2 sum d^2/sigma^2 into
 // *jo (may be null, accumulated with atomicAdd: zero it first).
 cudaError_t l96_nl_launch(const L96Dev &m, const double *x0, double *traj, float2 *coef32,
                           double2 *coef64, double *d, double *jo, double *xT, cudaStream_t s);
 
-// Batched Hessian-vector product.  mode 0: Y = A W (+W); mode 1: adjoint only
+// Batched FP64 Hessian-vector product (register-loaded coefficients, layout
+// [T][4][Np] double2 by slot).  mode 0: Y = A W (+W); mode 1: adjoint only
 // with the given forcing r (one column, length p): Y = L^T lambda_0;
 // mode 2: tangent linear only: r = R^-1 H M L W.
-cudaError_t l96_hvp_launch_f32(const L96Dev &m, const float2 *coef, const float *W, float *Y,
-                               int64_t ld, int ncols, int add_identity, float *r, int mode,
-                               cudaStream_t s);
 cudaError_t l96_hvp_launch_f64(const L96Dev &m, const double2 *coef, const double *W, double *Y,
                                int64_t ld, int ncols, int add_identity, double *r, int mode,
                                cudaStream_t s);
@@ -89,7 +88,8 @@ cudaError_t l96_hvp_launch_f64(const L96Dev &m, const double2 *coef, const doubl
 // shared memory by 1-D TMA copies (same modes as above); *err is set to 1 if
 // a bounded wait on a copy ran out.
 cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float *W, float *Y, int64_t ld,
-                               int ncols, int add_identity, float *r, int mode, int *err, cudaStream_t s);
+                               int ncols, int add_identity, float *r, int mode, int *err, cudaStream_t s,
+                               int P_hint = 0, int S_hint = 0);
 
 // out = L in or L^T in (FP64), ncols columns (ld = n)
 cudaError_t bsqrt_launch(const L96Dev &m, const double *in, double *out, int transpose, int ncols,

@@ -343,12 +343,6 @@ static cudaError_t hvp_launch(const L96Dev &m, const typename V2<real>::type *co
     return cudaGetLastError();
 }
 
-cudaError_t l96_hvp_launch_f32(const L96Dev &m, const float2 *coef, const float *W, float *Y, int64_t ld,
-                               int ncols, int add_identity, float *r, int mode, cudaStream_t s)
-{
-    return hvp_launch<float>(m, coef, W, Y, ld, ncols, add_identity, r, mode, m.rinv32, m.band32, m.sig32, s);
-}
-
 cudaError_t l96_hvp_launch_f64(const L96Dev &m, const double2 *coef, const double *W, double *Y, int64_t ld,
                                int ncols, int add_identity, double *r, int mode, cudaStream_t s)
 {
@@ -429,7 +423,12 @@ __global__ void __launch_bounds__(512) l96_nl_kernel(const NlArgs a)
                 double ca = xm1, cb = xp1 - xm2;
                 f[j] = cb * ca - X[j] + F;
                 if (j == E - 1 && !full) { ca = 0.0; cb = 0.0; f[j] = 0.0; }
-                if (a.coef32) a.coef32[cbase + j] = make_float2((float)ca, (float)cb);
+                // FP32 copy interleaved by element pair across threads: float4 index
+                // (j / 2) * Tp + t within the stage, so that the FP32 kernel's
+                // shared-memory reads of one pair are contiguous across threads
+                if (a.coef32)
+                    a.coef32[((size_t)tt * 4 + stage) * Np + (size_t)(j >> 1) * 2 * Tp + 2 * t + (j & 1)] =
+                        make_float2((float)ca, (float)cb);
                 if (a.coef64) a.coef64[cbase + j] = make_double2(ca, cb);
             }
             const double c = (stage == 2) ? h : h2;

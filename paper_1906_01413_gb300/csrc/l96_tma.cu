@@ -114,14 +114,19 @@ struct Ring {
         mbar_expect_tx(bar, bytes);
         bulk_g2s(smem_u32(buf + (size_t)slot * Np), coef + (size_t)blk(c) * Np, bytes, bar);
     }
-    // Called by every thread right after the stage's barrier: refill, then wait.
-    __device__ const float2 *acquire(int c, int *err) const
+    // Thread 0 only, before the stage's barrier: wait until stage c has landed.
+    // The barrier then makes the buffer visible to every thread.
+    __device__ void wait_ready(int c, int *err) const
+    {
+        if (threadIdx.x == 0) mbar_wait_bounded(bar0 + 8u * (c % S), (uint32_t)((c / S) & 1), err, abort_flag);
+    }
+    // Thread 0 only, after the stage's barrier (every thread is done with the
+    // buffer of stage c - 1): refill that buffer with stage c + S - 1.
+    __device__ void refill(int c) const
     {
         if (threadIdx.x == 0 && c + S - 1 < total && !*abort_flag) issue(c + S - 1);
-        const int slot = c % S;
-        mbar_wait_bounded(bar0 + 8u * slot, (uint32_t)((c / S) & 1), err, abort_flag);
-        return buf + (size_t)slot * Np;
     }
+    __device__ const float4 *slot4(int slot) const { return reinterpret_cast<const float4 *>(buf + (size_t)slot * Np); }
     // After an abort: wait (bounded) for the copies this CTA still has in flight.
     __device__ void drain(int next_c, int *err) const
     {
@@ -132,76 +137,115 @@ struct Ring {
     }
 };
 
-template <int E>
-__device__ __forceinline__ void tl_stage(const float (&s)[E], float (&k)[E], bool full, float *H, int nthr, int tid,
-                                         int left, int right, int &hb, const Ring &ring, int c, int tE, int *err)
+// Tangent-linear tendency k = J(X) s of one RK4 stage for the PR probes a
+// thread holds; coefficients of the stage come from ring buffer `slot`
+// (float4 pairs interleaved by thread) and are shared by the PR probes.
+template <int E, int PR>
+__device__ __forceinline__ void tl_stage(const float (&s)[PR][E], float (&k)[PR][E], bool full, float *H, int nthr,
+                                         int tid, int left, int right, int &hb, const Ring &ring, int c, int slot, int t,
+                                         int Tp, int *err)
 {
-    float *Hb = H + hb * 4 * nthr;
-    Hb[tid] = full ? s[E - 2] : s[E - 3];
-    Hb[nthr + tid] = full ? s[E - 1] : s[E - 2];
-    Hb[2 * nthr + tid] = s[0];
+    float *Hb = H + hb * 3 * PR * nthr;
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+        Hb[(0 * PR + r) * nthr + tid] = full ? s[r][E - 2] : s[r][E - 3];
+        Hb[(1 * PR + r) * nthr + tid] = full ? s[r][E - 1] : s[r][E - 2];
+        Hb[(2 * PR + r) * nthr + tid] = s[r][0];
+    }
+    ring.wait_ready(c, err);
     __syncthreads();
-    const float m2 = Hb[left], m1 = Hb[nthr + left], p1 = Hb[2 * nthr + right];
+    ring.refill(c);
+    float m2[PR], m1[PR], p1[PR];
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+        m2[r] = Hb[(0 * PR + r) * nthr + left];
+        m1[r] = Hb[(1 * PR + r) * nthr + left];
+        p1[r] = Hb[(2 * PR + r) * nthr + right];
+    }
     hb ^= 1;
-    const float4 *cf = reinterpret_cast<const float4 *>(ring.acquire(c, err) + tE);
+    const float4 *cf = ring.slot4(slot) + t;
 #pragma unroll
     for (int j2 = 0; j2 < E / 2; ++j2) {
-        const float4 cc = cf[j2];
+        const float4 cc = cf[j2 * Tp];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int j = 2 * j2 + h;
             const float ca = h ? cc.z : cc.x, cb = h ? cc.w : cc.y;
-            const float xm2 = (j == 0) ? m2 : (j == 1 ? m1 : s[j >= 2 ? j - 2 : 0]);
-            const float xm1 = (j == 0) ? m1 : s[j >= 1 ? j - 1 : 0];
-            float xp1;
-            if (j == E - 1) xp1 = p1;
-            else if (j == E - 2) xp1 = full ? s[E - 1] : p1;
-            else xp1 = s[j + 1 < E ? j + 1 : 0];
-            k[j] = fmaf(ca, xp1 - xm2, fmaf(cb, xm1, -s[j]));
+#pragma unroll
+            for (int r = 0; r < PR; ++r) {
+                const float xm2 = (j == 0) ? m2[r] : (j == 1 ? m1[r] : s[r][j >= 2 ? j - 2 : 0]);
+                const float xm1 = (j == 0) ? m1[r] : s[r][j >= 1 ? j - 1 : 0];
+                float xp1;
+                if (j == E - 1) xp1 = p1[r];
+                else if (j == E - 2) xp1 = full ? s[r][E - 1] : p1[r];
+                else xp1 = s[r][j + 1 < E ? j + 1 : 0];
+                k[r][j] = fmaf(ca, xp1 - xm2, fmaf(cb, xm1, -s[r][j]));
+            }
         }
     }
-    if (!full) k[E - 1] = 0.f;
+    if (!full)
+#pragma unroll
+        for (int r = 0; r < PR; ++r) k[r][E - 1] = 0.f;
 }
 
-template <int E>
-__device__ __forceinline__ void ad_stage(const float (&m)[E], float (&out)[E], bool full, float *H, int nthr, int tid,
-                                         int left, int right, int &hb, const Ring &ring, int c, int tE, int *err)
+// Adjoint tendency out = J(X)^T m.  The boundary values of m are exchanged
+// and the neighbours' coefficients read from the shared ring, so every
+// coefficient read follows the stage's barrier.
+template <int E, int PR>
+__device__ __forceinline__ void ad_stage(const float (&m)[PR][E], float (&out)[PR][E], bool full, float *H, int nthr,
+                                         int tid, int left, int right, int &hb, const Ring &ring, int c, int slot, int t,
+                                         int Tp, int offL, int oddL, int tr, int *err)
 {
-    // The coefficients are needed before the exchange here (p = a m, q = b m),
-    // so the stage waits first; the barrier below still orders the refill.
-    const float4 *cf = reinterpret_cast<const float4 *>(ring.acquire(c, err) + tE);
-    float pp[E], qq[E];
+    float *Hb = H + hb * 3 * PR * nthr;
 #pragma unroll
-    for (int j2 = 0; j2 < E / 2; ++j2) {
-        const float4 cc = cf[j2];
-        pp[2 * j2] = cc.x * m[2 * j2];
-        qq[2 * j2] = cc.y * m[2 * j2];
-        pp[2 * j2 + 1] = cc.z * m[2 * j2 + 1];
-        qq[2 * j2 + 1] = cc.w * m[2 * j2 + 1];
+    for (int r = 0; r < PR; ++r) {
+        Hb[(0 * PR + r) * nthr + tid] = full ? m[r][E - 1] : m[r][E - 2];
+        Hb[(1 * PR + r) * nthr + tid] = m[r][0];
+        Hb[(2 * PR + r) * nthr + tid] = m[r][1];
     }
-    float *Hb = H + hb * 4 * nthr;
-    Hb[tid] = full ? pp[E - 1] : pp[E - 2];
-    Hb[nthr + tid] = pp[0];
-    Hb[2 * nthr + tid] = pp[1];
-    Hb[3 * nthr + tid] = qq[0];
+    ring.wait_ready(c, err);
     __syncthreads();
-    const float pm1 = Hb[left], pR0 = Hb[nthr + right], pR1 = Hb[2 * nthr + right], qR0 = Hb[3 * nthr + right];
-    hb ^= 1;
+    ring.refill(c);
+    float mL[PR], mR0[PR], mR1[PR];
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-        const float pjm1 = (j == 0) ? pm1 : pp[j >= 1 ? j - 1 : 0];
-        float qjp1;
-        if (j <= E - 3) qjp1 = qq[j + 1 < E ? j + 1 : 0];
-        else if (j == E - 2) qjp1 = full ? qq[E - 1] : qR0;
-        else qjp1 = qR0;
-        float pjp2;
-        if (j <= E - 4) pjp2 = pp[j + 2 < E ? j + 2 : 0];
-        else if (j == E - 3) pjp2 = full ? pp[E - 1] : pR0;
-        else if (j == E - 2) pjp2 = full ? pR0 : pR1;
-        else pjp2 = pR1;
-        out[j] = (pjm1 - pjp2) + (qjp1 - m[j]);
+    for (int r = 0; r < PR; ++r) {
+        mL[r] = Hb[(0 * PR + r) * nthr + left];
+        mR0[r] = Hb[(1 * PR + r) * nthr + right];
+        mR1[r] = Hb[(2 * PR + r) * nthr + right];
     }
-    if (!full) out[E - 1] = 0.f;
+    hb ^= 1;
+    const float4 *s4 = ring.slot4(slot);
+    const float4 cl = s4[offL], cr = s4[tr];
+    const float aL = oddL ? cl.z : cl.x;
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+        float pp[E], qq[E];
+#pragma unroll
+        for (int j2 = 0; j2 < E / 2; ++j2) {
+            const float4 cc = s4[j2 * Tp + t];
+            pp[2 * j2] = cc.x * m[r][2 * j2];
+            qq[2 * j2] = cc.y * m[r][2 * j2];
+            pp[2 * j2 + 1] = cc.z * m[r][2 * j2 + 1];
+            qq[2 * j2 + 1] = cc.w * m[r][2 * j2 + 1];
+        }
+        const float pm1 = aL * mL[r];
+        const float pR0 = cr.x * mR0[r], qR0 = cr.y * mR0[r], pR1 = cr.z * mR1[r];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const float pjm1 = (j == 0) ? pm1 : pp[j >= 1 ? j - 1 : 0];
+            float qjp1;
+            if (j <= E - 3) qjp1 = qq[j + 1 < E ? j + 1 : 0];
+            else if (j == E - 2) qjp1 = full ? qq[E - 1] : qR0;
+            else qjp1 = qR0;
+            float pjp2;
+            if (j <= E - 4) pjp2 = pp[j + 2 < E ? j + 2 : 0];
+            else if (j == E - 3) pjp2 = full ? pp[E - 1] : pR0;
+            else if (j == E - 2) pjp2 = full ? pR0 : pR1;
+            else pjp2 = pR1;
+            out[r][j] = (pjm1 - pjp2) + (qjp1 - m[r][j]);
+        }
+        if (!full) out[r][E - 1] = 0.f;
+    }
 }
 
 template <int E>
@@ -222,7 +266,10 @@ __device__ __forceinline__ void band_apply_t(const float *st, const float *band,
     }
 }
 
-template <int E, int MAXT>
+// A CTA holds P thread groups of Tp threads; group g owns probes
+// blockIdx.x * P * PR + g * PR + r, r < PR, and thread t of a group keeps
+// chunk t of each of them in registers.
+template <int E, int PR, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -232,23 +279,23 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
     float2 *ringbuf = reinterpret_cast<float2 *>(smem_raw + 128);
     float *H = reinterpret_cast<float *>(ringbuf + (size_t)S * Np);
-    float *state = H + 8 * nthr;
+    float *state = H + 2 * 3 * PR * nthr;
     const int SP = stage_pad_t(Np);
 
     const int tid = threadIdx.x;
-    const int t = tid / P, pp = tid - t * P;
-    const int probe = blockIdx.x * P + pp;
-    const bool active = probe < a.ncols;
-    const int left = ((t == 0) ? Tp - 1 : t - 1) * P + pp;
-    const int right = ((t == Tp - 1) ? 0 : t + 1) * P + pp;
+    const int t = tid / P, g = tid - t * P;
+    const int probe0 = (blockIdx.x * P + g) * PR;
+    const int left = ((t == 0) ? Tp - 1 : t - 1) * P + g;
+    const int right = ((t == Tp - 1) ? 0 : t + 1) * P + g;
     const int s0 = G.start(t);
     const int len = G.len(t);
     const bool full = (len == E);
     const int tE = t * E;
-    float *st = state + pp * SP;
+    const int tl = (t == 0) ? Tp - 1 : t - 1, tr = (t == Tp - 1) ? 0 : t + 1;
+    const int lenL = G.len(tl);
+    const int offL = ((lenL - 1) >> 1) * Tp + tl, oddL = (lenL - 1) & 1;
     int hb = 0;
     const float h = a.dt, h2 = 0.5f * a.dt, h6 = a.dt / 6.f, h3 = a.dt / 3.f;
-    const size_t rbase = (size_t)(active ? probe : 0) * (size_t)a.p;
 
     Ring ring;
     ring.buf = ringbuf;
@@ -269,43 +316,79 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
     __syncthreads();
     if (tid == 0)
         for (int c = 0; c < S - 1 && c < ring.total; ++c) ring.issue(c);
-    int c = 0;   // stream position
+    int c = 0;      // stream position
+    int slot = 0;   // ring buffer of stream position c (c mod S)
 
-    float dx[E];
+    float dx[PR][E];
     if (a.mode != 1) {
-        const float *w = a.W + (size_t)(active ? probe : 0) * a.ld;
-        for (int i = t; i < n; i += Tp) st[swz(i)] = active ? w[i] : 0.f;
-        __syncthreads();
-        band_apply_t<E>(st, a.band, a.hl, a.hh, n, s0, len, dx);
 #pragma unroll
-        for (int j = 0; j < E; ++j) dx[j] = (j < len) ? dx[j] * a.sig[s0 + (j < len ? j : 0)] : 0.f;
+        for (int r = 0; r < PR; ++r) {
+            const int probe = probe0 + r;
+            const bool active = probe < a.ncols;
+            float *st = state + (g * PR + r) * SP;
+            const float *w = a.W + (size_t)(active ? probe : 0) * a.ld;
+            for (int i = t; i < n; i += Tp) st[swz(i)] = active ? w[i] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PR; ++r) {
+            float tmp[E];
+            band_apply_t<E>(state + (g * PR + r) * SP, a.band, a.hl, a.hh, n, s0, len, tmp);
+#pragma unroll
+            for (int j = 0; j < E; ++j) dx[r][j] = (j < len) ? tmp[j] * a.sig[s0 + (j < len ? j : 0)] : 0.f;
+        }
         __syncthreads();
         for (int tt = 0;; ++tt) {
             const int o0 = a.optr[tt], o1 = a.optr[tt + 1];
             if (o0 < o1) {
 #pragma unroll
-                for (int j = 0; j < E; ++j) st[swz(tE + j)] = dx[j];
+                for (int r = 0; r < PR; ++r) {
+                    float *st = state + (g * PR + r) * SP;
+#pragma unroll
+                    for (int j = 0; j < E; ++j) st[swz(tE + j)] = dx[r][j];
+                }
                 __syncthreads();
-                if (active)
-                    for (int o = o0 + t; o < o1; o += Tp) a.r[rbase + o] = a.rinv[o] * st[swz(a.oslot[o])];
+#pragma unroll
+                for (int r = 0; r < PR; ++r) {
+                    const int probe = probe0 + r;
+                    if (probe < a.ncols) {
+                        const float *st = state + (g * PR + r) * SP;
+                        float *rr = a.r + (size_t)probe * (size_t)a.p;
+                        for (int o = o0 + t; o < o1; o += Tp) rr[o] = a.rinv[o] * st[swz(a.oslot[o])];
+                    }
+                }
                 __syncthreads();
             }
             if (tt == a.T) break;
-            float s[E], k[E], acc[E];
+            float s[PR][E], k[PR][E], acc[PR][E];
 #pragma unroll
-            for (int j = 0; j < E; ++j) s[j] = dx[j];
-            tl_stage<E>(s, k, full, H, nthr, tid, left, right, hb, ring, c++, tE, a.err);
+            for (int r = 0; r < PR; ++r)
 #pragma unroll
-            for (int j = 0; j < E; ++j) { acc[j] = k[j]; s[j] = fmaf(h2, k[j], dx[j]); }
-            tl_stage<E>(s, k, full, H, nthr, tid, left, right, hb, ring, c++, tE, a.err);
+                for (int j = 0; j < E; ++j) s[r][j] = dx[r][j];
+            tl_stage<E, PR>(s, k, full, H, nthr, tid, left, right, hb, ring, c++, slot, t, Tp, a.err);
+            slot = (slot + 1 == S) ? 0 : slot + 1;
 #pragma unroll
-            for (int j = 0; j < E; ++j) { acc[j] = fmaf(2.f, k[j], acc[j]); s[j] = fmaf(h2, k[j], dx[j]); }
-            tl_stage<E>(s, k, full, H, nthr, tid, left, right, hb, ring, c++, tE, a.err);
+            for (int r = 0; r < PR; ++r)
 #pragma unroll
-            for (int j = 0; j < E; ++j) { acc[j] = fmaf(2.f, k[j], acc[j]); s[j] = fmaf(h, k[j], dx[j]); }
-            tl_stage<E>(s, k, full, H, nthr, tid, left, right, hb, ring, c++, tE, a.err);
+                for (int j = 0; j < E; ++j) { acc[r][j] = k[r][j]; s[r][j] = fmaf(h2, k[r][j], dx[r][j]); }
+            tl_stage<E, PR>(s, k, full, H, nthr, tid, left, right, hb, ring, c++, slot, t, Tp, a.err);
+            slot = (slot + 1 == S) ? 0 : slot + 1;
 #pragma unroll
-            for (int j = 0; j < E; ++j) { acc[j] += k[j]; dx[j] = fmaf(h6, acc[j], dx[j]); }
+            for (int r = 0; r < PR; ++r)
+#pragma unroll
+                for (int j = 0; j < E; ++j) { acc[r][j] = fmaf(2.f, k[r][j], acc[r][j]); s[r][j] = fmaf(h2, k[r][j], dx[r][j]); }
+            tl_stage<E, PR>(s, k, full, H, nthr, tid, left, right, hb, ring, c++, slot, t, Tp, a.err);
+            slot = (slot + 1 == S) ? 0 : slot + 1;
+#pragma unroll
+            for (int r = 0; r < PR; ++r)
+#pragma unroll
+                for (int j = 0; j < E; ++j) { acc[r][j] = fmaf(2.f, k[r][j], acc[r][j]); s[r][j] = fmaf(h, k[r][j], dx[r][j]); }
+            tl_stage<E, PR>(s, k, full, H, nthr, tid, left, right, hb, ring, c++, slot, t, Tp, a.err);
+            slot = (slot + 1 == S) ? 0 : slot + 1;
+#pragma unroll
+            for (int r = 0; r < PR; ++r)
+#pragma unroll
+                for (int j = 0; j < E; ++j) { acc[r][j] += k[r][j]; dx[r][j] = fmaf(h6, acc[r][j], dx[r][j]); }
         }
         if (a.mode == 2) {
             ring.drain(c, a.err);
@@ -314,72 +397,125 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
         __syncthreads();   // last tangent-linear stage read before the adjoint refills its buffer
     }
 
-    float lam[E];
+    float lam[PR][E];
 #pragma unroll
-    for (int j = 0; j < E; ++j) lam[j] = 0.f;
+    for (int r = 0; r < PR; ++r)
+#pragma unroll
+        for (int j = 0; j < E; ++j) lam[r][j] = 0.f;
     for (int tt = a.T;; --tt) {
         const int o0 = a.optr[tt], o1 = a.optr[tt + 1];
         if (o0 < o1) {
 #pragma unroll
-            for (int j = 0; j < E; ++j) st[swz(tE + j)] = lam[j];
-            __syncthreads();
-            if (active)
-                for (int o = o0 + t; o < o1; o += Tp) atomicAdd(&st[swz(a.oslot[o])], a.r[rbase + o]);
+            for (int r = 0; r < PR; ++r) {
+                float *st = state + (g * PR + r) * SP;
+#pragma unroll
+                for (int j = 0; j < E; ++j) st[swz(tE + j)] = lam[r][j];
+            }
             __syncthreads();
 #pragma unroll
-            for (int j = 0; j < E; ++j) lam[j] = (j < len) ? st[swz(tE + j)] : 0.f;
+            for (int r = 0; r < PR; ++r) {
+                const int probe = probe0 + r;
+                if (probe < a.ncols) {
+                    float *st = state + (g * PR + r) * SP;
+                    const float *rr = a.r + (size_t)probe * (size_t)a.p;
+                    for (int o = o0 + t; o < o1; o += Tp) atomicAdd(&st[swz(a.oslot[o])], rr[o]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < PR; ++r) {
+                const float *st = state + (g * PR + r) * SP;
+#pragma unroll
+                for (int j = 0; j < E; ++j) lam[r][j] = (j < len) ? st[swz(tE + j)] : 0.f;
+            }
         }
         if (tt == 0) break;
-        float lk[E], ls[E], lx[E];
+        float lk[PR][E], ls[PR][E], lx[PR][E];
 #pragma unroll
-        for (int j = 0; j < E; ++j) lk[j] = h6 * lam[j];
-        ad_stage<E>(lk, ls, full, H, nthr, tid, left, right, hb, ring, c++, tE, a.err);
+        for (int r = 0; r < PR; ++r)
 #pragma unroll
-        for (int j = 0; j < E; ++j) { lx[j] = lam[j] + ls[j]; lk[j] = fmaf(h3, lam[j], h * ls[j]); }
-        ad_stage<E>(lk, ls, full, H, nthr, tid, left, right, hb, ring, c++, tE, a.err);
+            for (int j = 0; j < E; ++j) lk[r][j] = h6 * lam[r][j];
+        ad_stage<E, PR>(lk, ls, full, H, nthr, tid, left, right, hb, ring, c++, slot, t, Tp, offL, oddL, tr, a.err);
+        slot = (slot + 1 == S) ? 0 : slot + 1;
 #pragma unroll
-        for (int j = 0; j < E; ++j) { lx[j] += ls[j]; lk[j] = fmaf(h3, lam[j], h2 * ls[j]); }
-        ad_stage<E>(lk, ls, full, H, nthr, tid, left, right, hb, ring, c++, tE, a.err);
+        for (int r = 0; r < PR; ++r)
 #pragma unroll
-        for (int j = 0; j < E; ++j) { lx[j] += ls[j]; lk[j] = fmaf(h6, lam[j], h2 * ls[j]); }
-        ad_stage<E>(lk, ls, full, H, nthr, tid, left, right, hb, ring, c++, tE, a.err);
+            for (int j = 0; j < E; ++j) { lx[r][j] = lam[r][j] + ls[r][j]; lk[r][j] = fmaf(h3, lam[r][j], h * ls[r][j]); }
+        ad_stage<E, PR>(lk, ls, full, H, nthr, tid, left, right, hb, ring, c++, slot, t, Tp, offL, oddL, tr, a.err);
+        slot = (slot + 1 == S) ? 0 : slot + 1;
 #pragma unroll
-        for (int j = 0; j < E; ++j) lam[j] = lx[j] + ls[j];
+        for (int r = 0; r < PR; ++r)
+#pragma unroll
+            for (int j = 0; j < E; ++j) { lx[r][j] += ls[r][j]; lk[r][j] = fmaf(h3, lam[r][j], h2 * ls[r][j]); }
+        ad_stage<E, PR>(lk, ls, full, H, nthr, tid, left, right, hb, ring, c++, slot, t, Tp, offL, oddL, tr, a.err);
+        slot = (slot + 1 == S) ? 0 : slot + 1;
+#pragma unroll
+        for (int r = 0; r < PR; ++r)
+#pragma unroll
+            for (int j = 0; j < E; ++j) { lx[r][j] += ls[r][j]; lk[r][j] = fmaf(h6, lam[r][j], h2 * ls[r][j]); }
+        ad_stage<E, PR>(lk, ls, full, H, nthr, tid, left, right, hb, ring, c++, slot, t, Tp, offL, oddL, tr, a.err);
+        slot = (slot + 1 == S) ? 0 : slot + 1;
+#pragma unroll
+        for (int r = 0; r < PR; ++r)
+#pragma unroll
+            for (int j = 0; j < E; ++j) lam[r][j] = lx[r][j] + ls[r][j];
     }
 
     ring.drain(c, a.err);
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < E; ++j)
-        if (j < len) st[swz(s0 + j)] = a.sig[s0 + j] * lam[j];
-    __syncthreads();
-    float y[E];
-    band_apply_t<E>(st, a.band, a.hl, a.hh, n, s0, len, y);
-    if (active) {
-        float *yo = a.Y + (size_t)probe * a.ld;
-        const float *w = a.W ? a.W + (size_t)probe * a.ld : nullptr;
+    for (int r = 0; r < PR; ++r) {
+        float *st = state + (g * PR + r) * SP;
 #pragma unroll
         for (int j = 0; j < E; ++j)
-            if (j < len) yo[s0 + j] = y[j] + ((a.add_identity && w) ? w[s0 + j] : 0.f);
+            if (j < len) st[swz(s0 + j)] = a.sig[s0 + j] * lam[r][j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+        const int probe = probe0 + r;
+        float y[E];
+        band_apply_t<E>(state + (g * PR + r) * SP, a.band, a.hl, a.hh, n, s0, len, y);
+        if (probe < a.ncols) {
+            float *yo = a.Y + (size_t)probe * a.ld;
+            const float *w = a.W ? a.W + (size_t)probe * a.ld : nullptr;
+#pragma unroll
+            for (int j = 0; j < E; ++j)
+                if (j < len) yo[s0 + j] = y[j] + ((a.add_identity && w) ? w[s0 + j] : 0.f);
+        }
     }
 }
 
-size_t tma_smem_bytes(int Np, int nthr, int P, int S)
+// Shared memory: barriers, S stage buffers, halo (2 buffers x 3 x PR x nthr),
+// state copies of the P * PR probes.
+size_t tma_smem_bytes(int Np, int nthr, int P, int S, int PR)
 {
-    return 128 + (size_t)S * Np * 8 + sizeof(float) * (8 * (size_t)nthr + (size_t)P * stage_pad_t(Np));
+    return 128 + (size_t)S * Np * 8 + sizeof(float) * (6 * (size_t)PR * nthr + (size_t)P * PR * stage_pad_t(Np));
 }
 
 }  // namespace
 
-// Choose P probes per CTA and ring depth S for the shared-memory budget.
-static bool tma_plan(const ChunkGeom &g, int ncols, int maxthr, size_t smem_max, int *P_out, int *S_out)
+// Choose P thread groups per CTA and ring depth S for the shared-memory
+// budget; positive hints are taken when they fit.
+static bool tma_plan(const ChunkGeom &g, int ncols, int PR, int maxthr, size_t smem_max, int P_hint, int S_hint,
+                     int *P_out, int *S_out)
 {
-    int P = maxthr / g.Tp;
-    if (P > 64) P = 64;
-    if (P > ncols) P = ncols;
-    for (; P >= 1; --P)
+    const int groups_needed = (ncols + PR - 1) / PR;
+    int Pmax = maxthr / g.Tp;
+    if (Pmax > 64) Pmax = 64;
+    if (Pmax > groups_needed) Pmax = groups_needed;
+    if (P_hint > 0 || S_hint > 0) {
+        const int P = (P_hint > 0 && P_hint <= Pmax) ? P_hint : Pmax;
+        const int S = (S_hint >= 2 && S_hint <= 8) ? S_hint : 4;
+        if (P >= 1 && tma_smem_bytes(g.Np, P * g.Tp, P, S, PR) <= smem_max) {
+            *P_out = P;
+            *S_out = S;
+            return true;
+        }
+    }
+    for (int P = Pmax; P >= 1; --P)
         for (int S = 4; S >= 2; --S)
-            if (tma_smem_bytes(g.Np, P * g.Tp, P, S) <= smem_max) {
+            if (tma_smem_bytes(g.Np, P * g.Tp, P, S, PR) <= smem_max) {
                 *P_out = P;
                 *S_out = S;
                 return true;
@@ -387,18 +523,31 @@ static bool tma_plan(const ChunkGeom &g, int ncols, int maxthr, size_t smem_max,
     return false;
 }
 
+template <int E, int PR, int MAXT>
+static cudaError_t launch_tma(const TmaArgs &a, int grid, int nthr, size_t sm, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(l96_hvp_tma_kernel<E, PR, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    l96_hvp_tma_kernel<E, PR, MAXT><<<grid, nthr, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float *W, float *Y, int64_t ld, int ncols,
-                               int add_identity, float *r, int mode, int *err, cudaStream_t s)
+                               int add_identity, float *r, int mode, int *err, cudaStream_t s, int P_hint, int S_hint)
 {
     if (ncols <= 0) return cudaSuccess;
     int dev = 0, smem_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int E = m.geom.E;
-    const int maxthr = (E <= 8) ? 1024 : 512;
+    // two probes per thread (registers) for E <= 8: 512-thread CTAs
+    const int PR = (E <= 8) ? 2 : 1;
+    const int maxthr = 512;
     int P = 1, S = 2;
-    // leave room for the kernel's static shared memory
-    if (!tma_plan(m.geom, ncols, maxthr, (size_t)smem_optin - 1024, &P, &S)) return cudaErrorInvalidConfiguration;
+    if (!tma_plan(m.geom, ncols, PR, maxthr, (size_t)smem_optin - 1024, P_hint, S_hint, &P, &S))
+        return cudaErrorInvalidConfiguration;
     TmaArgs a;
     a.geom = m.geom;
     a.T = m.T;
@@ -423,27 +572,15 @@ cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float 
     a.ld = ld;
     a.err = err;
     const int nthr = P * m.geom.Tp;
-    const size_t sm = tma_smem_bytes(m.geom.Np, nthr, P, S);
-    const int grid = (ncols + P - 1) / P;
-    cudaError_t e = cudaSuccess;
+    const size_t sm = tma_smem_bytes(m.geom.Np, nthr, P, S, PR);
+    const int per_cta = P * PR;
+    const int grid = (ncols + per_cta - 1) / per_cta;
     switch (E) {
-    case 4:
-        e = cudaFuncSetAttribute(l96_hvp_tma_kernel<4, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e == cudaSuccess) { count_launch(); l96_hvp_tma_kernel<4, 1024><<<grid, nthr, sm, s>>>(a); }
-        break;
-    case 8:
-        e = cudaFuncSetAttribute(l96_hvp_tma_kernel<8, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e == cudaSuccess) { count_launch(); l96_hvp_tma_kernel<8, 1024><<<grid, nthr, sm, s>>>(a); }
-        break;
-    case 16:
-        e = cudaFuncSetAttribute(l96_hvp_tma_kernel<16, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e == cudaSuccess) { count_launch(); l96_hvp_tma_kernel<16, 512><<<grid, nthr, sm, s>>>(a); }
-        break;
-    default:
-        return cudaErrorInvalidValue;
+    case 4: return launch_tma<4, 2, 512>(a, grid, nthr, sm, s);
+    case 8: return launch_tma<8, 2, 512>(a, grid, nthr, sm, s);
+    case 16: return launch_tma<16, 1, 512>(a, grid, nthr, sm, s);
+    default: return cudaErrorInvalidValue;
     }
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
 }
 
 }  // namespace riot

@@ -81,6 +81,8 @@ def load():
     L.riot_last_error.restype = c_char_p
     L.riot_status_string.argtypes = [c_int32]
     L.riot_status_string.restype = c_char_p
+    L.riot_set_hvp_config.argtypes = [vp, c_int32, c_int32]
+    L.riot_set_hvp_config.restype = c_int32
     L.riot_rsvd_sweeps.argtypes = [vp]
     L.riot_rsvd_sweeps.restype = c_int32
     L.riot_kernel_launches.argtypes = []
@@ -217,6 +219,10 @@ def riot_rsvd_timings(ctx):
     ms = (c_double * 6)()
     _check(ctx, "riot_rsvd_timings", load().riot_rsvd_timings(ctx, ms))
     return dict(zip(["hvp", "orth", "kmat", "eig", "ritz", "total"], ms[:]))
+
+
+def riot_set_hvp_config(ctx, probes_per_cta=0, ring_depth=0):
+    _check(ctx, "riot_set_hvp_config", load().riot_set_hvp_config(ctx, int(probes_per_cta), int(ring_depth)))
 
 
 def riot_rsvd_sweeps(ctx):
