@@ -52,38 +52,79 @@ typedef enum {
     RIOT_ENONFINITE = -8 /* a NaN or Inf reached a reduction                  */
 } riot_status;
 
-enum { RIOT_MODEL_L96 = 1 };
-enum { RIOT_B_GAUSS_RING = 1 };
+enum { RIOT_MODEL_L96 = 1, RIOT_MODEL_ADVDIFF = 2 };
+enum { RIOT_B_GAUSS_RING = 1, RIOT_B_EXP_SEPARABLE = 2 };
 enum { RIOT_PREC_MIXED = 0, RIOT_PREC_FP64 = 1 };
 enum { RIOT_EIG_TRIDIAG = 0, RIOT_EIG_JACOBI = 1 };
 
-/* Model of the window (Section 3.1 for Lorenz-96).
- * L96: dx_i/dt = (x_{i+1} - x_{i-2}) x_{i-1} - x_i + F on a periodic ring of
- * n variables, advanced by T classical RK4 steps of length dt.
- * Limits: 16 <= n <= 8192, 0 <= T, dt > 0. */
+/* Tracer transport for a surface-emission inversion (the setting of the
+ * paper's black-carbon experiments, Section 3.2, on a synthetic box model).
+ * Cells (i, j, l), i < nx periodic in x, j < ny between solid walls, l < nz
+ * levels with zero flux at the bottom and top; cell (i, j, l) is centred at
+ * (i, j, l) in cell units.  dc/dt = A c + s with
+ *  - upwind flux-form advection by the steady face winds amp[l] * u (x-face
+ *    i-1/2 of row j, u[j*nx + i]) and amp[l] * v (y-face j-1/2 of column i,
+ *    v[j*nx + i], j = 0..ny; rows 0 and ny are the walls and must be 0);
+ *  - vertical diffusion with diffusivity kz[l] on face l-1/2 (l = 1..nz-1;
+ *    kz[0] and kz[nz] are ignored: no flux through the bottom and top);
+ *  - the surface source s = E / dz in level 0, E = emis_b * exp(x) where the
+ *    control x holds one value per surface cell and emission block:
+ *    x[(b*ny + j)*nx + i], n = nblocks*ny*nx.  Step t (0-based) uses block
+ *    t*nblocks/T.  The tracer starts at 0.
+ * Time stepping is classical RK4 with s held over each step.  All arrays are
+ * host arrays read during riot_setup.  Limits: nx >= 2, 2 <= ny, 2 <= nz <= 32,
+ * 1 <= nblocks <= T, amp > 0, kz >= 0, emis_b finite. */
 typedef struct {
-    int32_t kind;   /* RIOT_MODEL_L96                                        */
+    int32_t nx, ny, nz, nblocks;
+    double dx, dy, dz;          /* cell sizes (m)                                 */
+    const double *u;            /* [ny][nx]   x-face velocities (m/s)             */
+    const double *v;            /* [ny+1][nx] y-face velocities (m/s)             */
+    const double *amp;          /* [nz]       level scaling of u and v            */
+    const double *kz;           /* [nz+1]     face diffusivities (m^2/s)          */
+    const double *emis_b;       /* [nblocks][ny][nx] background emissions         */
+} riot_advdiff_desc;
+
+/* Model of the window.
+ * RIOT_MODEL_L96 (Section 3.1): dx_i/dt = (x_{i+1} - x_{i-2}) x_{i-1} - x_i + F
+ * on a periodic ring of n variables, advanced by T classical RK4 steps of
+ * length dt.  Limits: 16 <= n <= 8192, 0 <= T, dt > 0.  advdiff is ignored.
+ * RIOT_MODEL_ADVDIFF: the tracer model of riot_advdiff_desc (required);
+ * n must equal nblocks*ny*nx, T >= 1 steps of length dt; F is ignored. */
+typedef struct {
+    int32_t kind;   /* RIOT_MODEL_L96 or RIOT_MODEL_ADVDIFF                   */
     int32_t T;      /* number of time steps in the window                     */
-    int64_t n;      /* number of model variables (= control size)             */
+    int64_t n;      /* control size                                           */
     double dt;      /* step length                                            */
-    double F;       /* forcing                                                */
+    double F;       /* forcing (Lorenz-96)                                    */
+    const riot_advdiff_desc *advdiff;   /* RIOT_MODEL_ADVDIFF only            */
 } riot_model_desc;
 
 /* Observations y with diagonal error covariance R = diag(sigma^2)
- * (Section 2.1, Eq. 2).  Observation j is of variable idx[j] at the end of
- * step step[j] (step 0 = the initial state).  Entries must be sorted by step
- * (nondecreasing); several observations of one (step, idx) pair are allowed.
- * All arrays are host arrays of length p; p = 0 is allowed. */
+ * (Section 2.1, Eq. 2), each taken at the end of step step[j] (step 0 = the
+ * initial state).  Entries must be sorted by step (nondecreasing).
+ * Lorenz-96: observation j is of variable idx[j]; several observations of
+ * one (step, idx) pair are allowed; pos is ignored.
+ * Tracer model: observation j is the trilinear interpolation of the tracer
+ * at pos[3j..3j+2] = (x, y, z) in cell units (x periodic, any real; y in
+ * [0, ny-1]; z in [0, nz-1]); idx is ignored; step >= 1.
+ * All arrays are host arrays of length p (pos: 3p); p = 0 is allowed. */
 typedef struct {
     int64_t p;
     const int32_t *step;   /* 0..T                          */
-    const int32_t *idx;    /* 0..n-1                        */
+    const int32_t *idx;    /* 0..n-1 (Lorenz-96)            */
     const double *y;       /* observed value                */
     const double *sigma;   /* error standard deviation > 0  */
+    const double *pos;     /* 3p cell coordinates (tracer)  */
 } riot_obs_desc;
 
-/* Prior covariance B = L L^T (Section 2.1, Eq. 3), Gaussian correlations
- * (Section 3.1).  RIOT_B_GAUSS_RING: L = diag(s) S with S the periodic
+/* Prior covariance B = L L^T (Section 2.1, Eq. 3).
+ * RIOT_B_EXP_SEPARABLE (tracer model only): L = sigma_b (S_y kron S_x) on
+ * each emission block, blocks independent, with S_x, S_y the symmetric
+ * square roots (eigenvalues below 0 set to 0) of the exponential
+ * correlations exp(-d / length), d the periodic x distance (times dx) and
+ * the y distance (times dy); sigma_vec must be NULL.
+ * RIOT_B_GAUSS_RING (Lorenz-96, the Gaussian correlations of Section 3.1):
+ * L = diag(s) S with S the periodic
  * Gaussian convolution S_d = alpha sum_j exp(-(d + j n)^2 / length^2),
  * normalised so that (S S^T)_ii = 1.  Then B = L L^T has the Gaussian
  * correlation exp(-d^2 / (2 length^2)) up to lattice terms of relative size
@@ -197,6 +238,11 @@ riot_status riot_analysis_cov_lowrank(riot_ctx *ctx, int32_t m, double *LU_dev, 
  * n doubles (ld = n). */
 riot_status riot_bsqrt_apply(riot_ctx *ctx, const double *in_dev, double *out_dev, int32_t transpose,
                              int32_t ncols);
+
+/* The innovation d = H(x) - y of the last riot_outer_begin (p doubles,
+ * device).  With y = 0 this is the model-equivalent H(x) of the observations,
+ * which is how synthetic observations are made from a truth. */
+riot_status riot_get_innovation(riot_ctx *ctx, double *d_dev);
 
 /* Copy the context's state out: x, v, g (n doubles each), the eigenvectors
  * U (n x k doubles) and eigenvalues (k doubles, device); NULL skips one. */

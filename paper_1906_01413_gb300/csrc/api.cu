@@ -20,12 +20,15 @@ using namespace riot;
 
 struct riot_ctx {
     int dev = 0;
+    int model = RIOT_MODEL_L96;
+    int n = 0, p = 0;   // control size, observation count
     cudaStream_t s = nullptr;
     int prec = RIOT_PREC_MIXED;
     int kmax = 0, exact_rr = 0, eig_method = 0;
     int hvp_P = 0, hvp_S = 0;   // launch shape of the FP32 Hessian kernel (0 = automatic)
     uint64_t seed = 0;
     L96Dev m;
+    AdvDev a;   // tracer model (RIOT_MODEL_ADVDIFF)
     std::vector<void *> allocs;
     // model tables
     int *optr = nullptr, *oslot = nullptr, *oidx = nullptr;
@@ -140,6 +143,10 @@ void ev_mark(riot_ctx *c, int phase)
 
 riot_status hvp(riot_ctx *ctx, const void *W, void *Y, int64_t ld, int ncols, int add_identity)
 {
+    if (ctx->model == RIOT_MODEL_ADVDIFF) {
+        CU(adv_hvp(ctx->a, ctx->prec == RIOT_PREC_FP64, W, Y, ld, ncols, add_identity, ctx->rscr, ctx->s));
+        return RIOT_OK;
+    }
     const size_t rs = real_size(ctx);
     for (int c0 = 0; c0 < ncols; c0 += ctx->kmax) {
         const int nc = (ncols - c0 < ctx->kmax) ? ncols - c0 : ctx->kmax;
@@ -155,12 +162,19 @@ riot_status hvp(riot_ctx *ctx, const void *W, void *Y, int64_t ld, int ncols, in
     return RIOT_OK;
 }
 
+// out = L in (transpose 0) or L^T in, ncols columns of n doubles
+cudaError_t bsqrt(riot_ctx *ctx, const double *in, double *out, int transpose, int ncols)
+{
+    if (ctx->model == RIOT_MODEL_ADVDIFF) return adv_bsqrt(ctx->a, in, out, ncols, ctx->s);   // L symmetric
+    return bsqrt_launch(ctx->m, in, out, transpose, ncols, ctx->s);
+}
+
 // Q (FP64, n x k) = orthonormal basis of Y (real, n x k): shifted CholeskyQR
 // (shift 11 (n k + k (k + 1)) u ||Y||_F^2, Fukaya et al. 2020) followed by two
 // unshifted CholeskyQR passes.
 riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
 {
-    const int n = ctx->m.geom.n;
+    const int n = ctx->n;
     CU(convert_block(Y, real_tag(ctx), n, ctx->Q, 'd', n, n, k, ctx->s));
     // Each shifted pass divides the condition number by about
     // 1 / sqrt(11 (n k + k^2) u k); FP32 blocks carry at most ~1e8 of it,
@@ -181,7 +195,7 @@ riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
 // triangular solves run in FP32, like the block they act on.
 riot_status orth32(riot_ctx *ctx, const float *Y, int k, int info_base, int passes)
 {
-    const int n = ctx->m.geom.n;
+    const int n = ctx->n;
     CU(cudaMemcpyAsync(ctx->Q32, Y, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, ctx->s));
     for (int pass = 0; pass < passes; ++pass) {
         CU(gram_lower(n, k, ctx->Q32, 'f', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
@@ -236,6 +250,348 @@ cudaError_t noalloc_scratch(int dev, void **out)
     return cudaSuccess;
 }
 
+template <typename T>
+cudaError_t up(riot_ctx *ctx, T *dst, const T *src, size_t count)
+{
+    return count ? cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, ctx->s) : cudaSuccess;
+}
+
+// FP64 and FP32 device copies of a host table
+riot_status upload2(riot_ctx *ctx, const std::vector<double> &h, const double **d64, const float **d32)
+{
+    double *p64 = nullptr;
+    float *p32 = nullptr;
+    TRY(dalloc(ctx, &p64, h.size()));
+    TRY(dalloc(ctx, &p32, h.size()));
+    std::vector<float> f(h.begin(), h.end());
+    cudaError_t e;
+    if ((e = up(ctx, p64, h.data(), h.size())) != cudaSuccess || (e = up(ctx, p32, f.data(), f.size())) != cudaSuccess ||
+        (e = cudaStreamSynchronize(ctx->s)) != cudaSuccess)
+        return fail(ctx, RIOT_ECUDA, "table upload failed: %s", cudaGetErrorString(e));
+    *d64 = p64;
+    *d32 = p32;
+    return RIOT_OK;
+}
+
+// Symmetric square root Z diag(sqrt(max(w, 0))) Z^T of the n x n row-major
+// matrix A by cyclic Jacobi rotations (host, setup only).
+void sym_sqrt_host(std::vector<double> &A, int n)
+{
+    std::vector<double> V((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double a2 = A[(size_t)i * n + j] * A[(size_t)i * n + j];
+                tot += a2;
+                if (i != j) off += a2;
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double tau = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double *r = &A[(size_t)k * n];
+                    const double akp = r[p], akq = r[q];
+                    r[p] = c * akp - sn * akq;
+                    r[q] = sn * akp + c * akq;
+                    double *v = &V[(size_t)k * n];
+                    const double vkp = v[p], vkq = v[q];
+                    v[p] = c * vkp - sn * vkq;
+                    v[q] = sn * vkp + c * vkq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    std::vector<double> sw(n);
+    for (int i = 0; i < n; ++i) {
+        const double w = A[(size_t)i * n + i];
+        sw[i] = w > 0.0 ? sqrt(w) : 0.0;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += V[(size_t)i * n + k] * sw[k] * V[(size_t)j * n + k];
+            A[(size_t)i * n + j] = acc;
+        }
+}
+
+riot_status setup_l96(riot_ctx *ctx, const riot_model_desc *model, const riot_obs_desc *obs, const riot_bcov_desc *B)
+{
+    const int64_t n64 = model->n;
+    if (n64 < 16 || n64 > 8192) return fail(ctx, RIOT_EINVAL, "n = %lld outside [16, 8192]", (long long)n64);
+    const int n = (int)n64, p = ctx->p, T = model->T;
+    if (!isfinite(model->F)) return fail(ctx, RIOT_EINVAL, "bad F");
+    if (B->kind != RIOT_B_GAUSS_RING || !(B->length > 0.0))
+        return fail(ctx, RIOT_EINVAL, "bad B descriptor (kind %d, length %g)", B->kind, B->length);
+    if (p > 0 && !obs->idx) return fail(ctx, RIOT_EINVAL, "null observation index array");
+    for (int j = 0; j < p; ++j)
+        if (obs->idx[j] < 0 || obs->idx[j] >= n) return fail(ctx, RIOT_EINVAL, "observation %d out of range", j);
+    if (B->sigma_vec)
+        for (int i = 0; i < n; ++i)
+            if (!isfinite(B->sigma_vec[i])) return fail(ctx, RIOT_EINVAL, "non-finite sigma_vec[%d]", i);
+    ctx->n = n;
+    L96Dev &m = ctx->m;
+    if (!choose_geom(n, &m.geom)) return fail(ctx, RIOT_EINVAL, "no thread layout for n = %d", n);
+    m.T = T;
+    m.dt = model->dt;
+    m.F = model->F;
+    m.p = p;
+
+    std::vector<int> optr(T + 2, p), oslot(p), oidx(p);
+    std::vector<double> rinv(p), yv(p);
+    std::vector<float> rinv32(p);
+    {
+        int j = 0;
+        for (int t = 0; t <= T + 1; ++t) {
+            while (j < p && obs->step[j] < t) ++j;
+            optr[t] = j;
+        }
+    }
+    for (int j = 0; j < p; ++j) {
+        oidx[j] = obs->idx[j];
+        oslot[j] = m.geom.slot(obs->idx[j]);
+        rinv[j] = 1.0 / (obs->sigma[j] * obs->sigma[j]);
+        rinv32[j] = (float)rinv[j];
+        yv[j] = obs->y[j];
+    }
+    std::vector<double> band;
+    int hl = 0, hh = 0;
+    build_band(n, B->length, band, hl, hh);
+    std::vector<float> band32(band.begin(), band.end());
+    std::vector<double> sig(n);
+    std::vector<float> sig32(n);
+    for (int i = 0; i < n; ++i) {
+        sig[i] = B->sigma_vec ? B->sigma_vec[i] : B->sigma_b;
+        sig32[i] = (float)sig[i];
+    }
+    m.band.hl = hl;
+    m.band.hh = hh;
+
+    const size_t np = (size_t)n, k = (size_t)ctx->kmax, rs = real_size(ctx);
+    riot_status st;
+    if ((st = dalloc(ctx, &ctx->optr, T + 2)) || (st = dalloc(ctx, &ctx->oslot, p)) || (st = dalloc(ctx, &ctx->oidx, p)) ||
+        (st = dalloc(ctx, &ctx->y, p)) || (st = dalloc(ctx, &ctx->rinv64, p)) || (st = dalloc(ctx, &ctx->rinv32, p)) ||
+        (st = dalloc(ctx, &ctx->band64, band.size())) || (st = dalloc(ctx, &ctx->band32, band.size())) ||
+        (st = dalloc(ctx, &ctx->sig64, np)) || (st = dalloc(ctx, &ctx->sig32, np)) ||
+        (st = dalloc(ctx, &ctx->traj, (T + 1) * np)) ||
+        (st = dalloc(ctx, &ctx->coef64, (size_t)T * 4 * m.geom.Np + 1)) ||
+        (ctx->prec == RIOT_PREC_MIXED && (st = dalloc(ctx, &ctx->coef32, (size_t)T * 4 * m.geom.Np + 1))) ||
+        (st = dalloc(ctx, (char **)&ctx->rscr, (size_t)p * k * rs + 16)))
+        return st;
+    cudaError_t e = cudaSuccess;
+    if ((e = up(ctx, ctx->optr, optr.data(), optr.size())) || (e = up(ctx, ctx->oslot, oslot.data(), oslot.size())) ||
+        (e = up(ctx, ctx->oidx, oidx.data(), oidx.size())) || (e = up(ctx, ctx->y, yv.data(), yv.size())) ||
+        (e = up(ctx, ctx->rinv64, rinv.data(), rinv.size())) || (e = up(ctx, ctx->rinv32, rinv32.data(), rinv32.size())) ||
+        (e = up(ctx, ctx->band64, band.data(), band.size())) || (e = up(ctx, ctx->band32, band32.data(), band32.size())) ||
+        (e = up(ctx, ctx->sig64, sig.data(), sig.size())) || (e = up(ctx, ctx->sig32, sig32.data(), sig32.size())) ||
+        (e = cudaStreamSynchronize(ctx->s)))
+        return fail(ctx, RIOT_ECUDA, "setup upload failed: %s", cudaGetErrorString(e));
+    m.optr = ctx->optr;
+    m.oslot = ctx->oslot;
+    m.oidx = ctx->oidx;
+    m.y = ctx->y;
+    m.rinv64 = ctx->rinv64;
+    m.rinv32 = ctx->rinv32;
+    m.band64 = ctx->band64;
+    m.band32 = ctx->band32;
+    m.sig64 = ctx->sig64;
+    m.sig32 = ctx->sig32;
+    return RIOT_OK;
+}
+
+riot_status setup_advdiff(riot_ctx *ctx, const riot_model_desc *model, const riot_obs_desc *obs, const riot_bcov_desc *B)
+{
+    const riot_advdiff_desc *ad = model->advdiff;
+    if (!ad) return fail(ctx, RIOT_EINVAL, "RIOT_MODEL_ADVDIFF needs model->advdiff");
+    const int nx = ad->nx, ny = ad->ny, nz = ad->nz, nb = ad->nblocks, T = model->T, p = ctx->p;
+    if (nx < 2 || ny < 2 || nz < 2 || nz > 32 || T < 1 || nb < 1 || nb > T)
+        return fail(ctx, RIOT_EINVAL, "bad grid nx=%d ny=%d nz=%d nblocks=%d T=%d", nx, ny, nz, nb, T);
+    if (!(ad->dx > 0.0) || !(ad->dy > 0.0) || !(ad->dz > 0.0) || !isfinite(ad->dx) || !isfinite(ad->dy) ||
+        !isfinite(ad->dz))
+        return fail(ctx, RIOT_EINVAL, "bad cell sizes");
+    if (!ad->u || !ad->v || !ad->amp || !ad->kz || !ad->emis_b) return fail(ctx, RIOT_EINVAL, "null model array");
+    const long long nyx = (long long)nx * ny, n = nyx * nb, ncells = nyx * nz;
+    if (n > (1LL << 30) || ncells > (1LL << 30)) return fail(ctx, RIOT_EINVAL, "grid too large");
+    if (model->n != n) return fail(ctx, RIOT_EINVAL, "n = %lld, expected nblocks*ny*nx = %lld", (long long)model->n, n);
+    for (long long i = 0; i < nyx; ++i)
+        if (!isfinite(ad->u[i])) return fail(ctx, RIOT_EINVAL, "non-finite u");
+    for (long long i = 0; i < nyx + nx; ++i)
+        if (!isfinite(ad->v[i])) return fail(ctx, RIOT_EINVAL, "non-finite v");
+    for (int i = 0; i < nx; ++i)
+        if (ad->v[i] != 0.0 || ad->v[(size_t)ny * nx + i] != 0.0) return fail(ctx, RIOT_EINVAL, "v must be 0 on the walls");
+    for (int l = 0; l < nz; ++l)
+        if (!(ad->amp[l] > 0.0) || !isfinite(ad->amp[l])) return fail(ctx, RIOT_EINVAL, "amp must be > 0");
+    for (int l = 0; l <= nz; ++l)
+        if (!(ad->kz[l] >= 0.0) || !isfinite(ad->kz[l])) return fail(ctx, RIOT_EINVAL, "kz must be >= 0");
+    for (long long i = 0; i < n; ++i)
+        if (!isfinite(ad->emis_b[i])) return fail(ctx, RIOT_EINVAL, "non-finite emis_b");
+    if (B->kind != RIOT_B_EXP_SEPARABLE || !(B->length > 0.0) || !isfinite(B->length) || !(B->sigma_b > 0.0) ||
+        !isfinite(B->sigma_b) || B->sigma_vec)
+        return fail(ctx, RIOT_EINVAL, "the tracer model needs RIOT_B_EXP_SEPARABLE with length, sigma_b > 0");
+    if (p > 0 && !obs->pos) return fail(ctx, RIOT_EINVAL, "null observation position array");
+    ctx->n = (int)n;
+    AdvDev &a = ctx->a;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.nb = nb;
+    a.T = T;
+    a.dt = model->dt;
+    a.dx = ad->dx;
+    a.dy = ad->dy;
+    a.dz = ad->dz;
+    a.sigma_b = B->sigma_b;
+    a.n = n;
+    a.ncells = ncells;
+    a.p = p;
+
+    // observations: trilinear corners and weights
+    a.optr_h.assign(T + 2, p);
+    {
+        int j = 0;
+        for (int t = 0; t <= T + 1; ++t) {
+            while (j < p && obs->step[j] < t) ++j;
+            a.optr_h[t] = j;
+        }
+    }
+    std::vector<int> cell((size_t)8 * p);
+    std::vector<double> w((size_t)8 * p), rinv(p), yv(p);
+    for (int j = 0; j < p; ++j) {
+        const double X = obs->pos[3 * j], Y = obs->pos[3 * j + 1], Z = obs->pos[3 * j + 2];
+        if (obs->step[j] < 1 || !isfinite(X) || !(Y >= 0.0 && Y <= ny - 1.0) || !(Z >= 0.0 && Z <= nz - 1.0))
+            return fail(ctx, RIOT_EINVAL, "observation %d: step or position out of range", j);
+        const double fx = floor(X);
+        long long i0 = (long long)fmod(fx, (double)nx);
+        if (i0 < 0) i0 += nx;
+        const int i1 = (int)((i0 + 1) % nx);
+        const double wx = X - fx;
+        int j0 = (int)floor(Y);
+        if (j0 > ny - 2) j0 = ny - 2;
+        const double wy = Y - j0;
+        int l0 = (int)floor(Z);
+        if (l0 > nz - 2) l0 = nz - 2;
+        const double wz = Z - l0;
+        int q = 0;
+        for (int dl = 0; dl < 2; ++dl)
+            for (int dj = 0; dj < 2; ++dj)
+                for (int di = 0; di < 2; ++di, ++q) {
+                    const int ii = di ? i1 : (int)i0;
+                    cell[(size_t)8 * j + q] = (int)(((long long)(l0 + dl) * ny + (j0 + dj)) * nx + ii);
+                    w[(size_t)8 * j + q] = (dl ? wz : 1.0 - wz) * (dj ? wy : 1.0 - wy) * (di ? wx : 1.0 - wx);
+                }
+        rinv[j] = 1.0 / (obs->sigma[j] * obs->sigma[j]);
+        yv[j] = obs->y[j];
+    }
+    // prior square roots of the exponential correlations
+    std::vector<double> Sx((size_t)nx * nx), Sy((size_t)ny * ny);
+    for (int i = 0; i < nx; ++i)
+        for (int j = 0; j < nx; ++j) {
+            int d = abs(i - j);
+            if (nx - d < d) d = nx - d;
+            Sx[(size_t)i * nx + j] = exp(-(double)d * ad->dx / B->length);
+        }
+    for (int i = 0; i < ny; ++i)
+        for (int j = 0; j < ny; ++j) Sy[(size_t)i * ny + j] = exp(-(double)abs(i - j) * ad->dy / B->length);
+    sym_sqrt_host(Sx, nx);
+    sym_sqrt_host(Sy, ny);
+
+    std::vector<double> u(ad->u, ad->u + nyx), v(ad->v, ad->v + nyx + nx), amp(ad->amp, ad->amp + nz),
+        kz(nz + 1, 0.0), Eb(ad->emis_b, ad->emis_b + n);
+    for (int l = 1; l < nz; ++l) kz[l] = ad->kz[l];
+    const double *rinv64 = nullptr, *w64 = nullptr;
+    const float *rinv32 = nullptr, *w32 = nullptr, *Eb32 = nullptr;
+    TRY(upload2(ctx, u, &a.u64, &a.u32));
+    TRY(upload2(ctx, v, &a.v64, &a.v32));
+    TRY(upload2(ctx, amp, &a.amp64, &a.amp32));
+    TRY(upload2(ctx, kz, &a.kz64, &a.kz32));
+    TRY(upload2(ctx, Sx, &a.Sx64, &a.Sx32));
+    TRY(upload2(ctx, Sy, &a.Sy64, &a.Sy32));
+    TRY(upload2(ctx, Eb, &a.Eb, &Eb32));
+    TRY(upload2(ctx, w, &w64, &w32));
+    TRY(upload2(ctx, rinv, &rinv64, &rinv32));
+    a.w64 = w64;
+    a.w32 = w32;
+    a.rinv64 = rinv64;
+    a.rinv32 = rinv32;
+    ctx->rinv64 = const_cast<double *>(rinv64);
+    int *cell_d = nullptr;
+    TRY(dalloc(ctx, &cell_d, cell.size()));
+    TRY(dalloc(ctx, &ctx->y, p));
+    cudaError_t e;
+    if ((e = up(ctx, cell_d, cell.data(), cell.size())) || (e = up(ctx, ctx->y, yv.data(), yv.size())))
+        return fail(ctx, RIOT_ECUDA, "setup upload failed: %s", cudaGetErrorString(e));
+    a.cell = cell_d;
+    a.y = ctx->y;
+
+    // workspace
+    const bool fp64 = ctx->prec == RIOT_PREC_FP64;
+    const size_t rs = real_size(ctx);
+    a.Pmax64 = ctx->kmax < 64 ? ctx->kmax : 64;
+    a.Pmax = fp64 ? a.Pmax64 : (ctx->kmax < 128 ? ctx->kmax : 128);
+    const size_t P = (size_t)a.Pmax;
+    char *cA = nullptr, *cB = nullptr, *src = nullptr, *ebar = nullptr, *tmp = nullptr;
+    TRY(dalloc(ctx, &cA, P * ncells * rs));
+    TRY(dalloc(ctx, &cB, P * ncells * rs));
+    TRY(dalloc(ctx, &src, P * n * rs));
+    TRY(dalloc(ctx, &ebar, P * n * rs));
+    TRY(dalloc(ctx, &tmp, P * n * rs));
+    a.cA = cA;
+    a.cB = cB;
+    a.src = src;
+    a.ebar = ebar;
+    a.tmp = tmp;
+    TRY(dalloc(ctx, &a.c64A, ncells));
+    TRY(dalloc(ctx, &a.c64B, ncells));
+    TRY(dalloc(ctx, &a.ebar64, n));
+    TRY(dalloc(ctx, &a.tmp64, (size_t)a.Pmax64 * n));
+    TRY(dalloc(ctx, &a.Es64, n));
+    TRY(dalloc(ctx, &a.Es32, n));
+    TRY(dalloc(ctx, (char **)&ctx->rscr, P * (size_t)p * rs + 16));
+    if ((e = cudaStreamSynchronize(ctx->s)) != cudaSuccess)
+        return fail(ctx, RIOT_ECUDA, "setup failed: %s", cudaGetErrorString(e));
+    return RIOT_OK;
+}
+
+// Outer-loop vectors and the model-independent inner-loop workspace.
+riot_status setup_common(riot_ctx *ctx)
+{
+    const size_t np = (size_t)ctx->n, k = (size_t)ctx->kmax, rs = real_size(ctx), p = (size_t)ctx->p;
+    riot_status st;
+    if ((st = dalloc(ctx, &ctx->x, np)) || (st = dalloc(ctx, &ctx->v, np)) || (st = dalloc(ctx, &ctx->g, np)) ||
+        (st = dalloc(ctx, &ctx->dv, np)) || (st = dalloc(ctx, &ctx->tmp, np)) || (st = dalloc(ctx, &ctx->d, p)) ||
+        (st = dalloc(ctx, &ctx->rd, p)) || (st = dalloc(ctx, &ctx->jo, 2)) ||
+        (st = dalloc(ctx, (char **)&ctx->Wblk, np * k * rs)) || (st = dalloc(ctx, (char **)&ctx->Yblk, np * k * rs)) ||
+        (st = dalloc(ctx, &ctx->Q, np * k)) || (st = dalloc(ctx, &ctx->U, np * k)) ||
+        (ctx->prec == RIOT_PREC_MIXED &&
+         ((st = dalloc(ctx, &ctx->Q32, np * k)) || (st = dalloc(ctx, &ctx->M32, k * k)) ||
+          (st = dalloc(ctx, &ctx->N32, k * k)) || (st = dalloc(ctx, &ctx->L32, k * k)))) ||
+        (st = dalloc(ctx, &ctx->G, k * k)) || (st = dalloc(ctx, &ctx->Mm, k * k)) || (st = dalloc(ctx, &ctx->Nm, k * k)) ||
+        (st = dalloc(ctx, &ctx->Km, k * k)) || (st = dalloc(ctx, &ctx->Z, k * k)) || (st = dalloc(ctx, &ctx->lam, k)) ||
+        (st = dalloc(ctx, &ctx->cvec, k)) ||
+        (st = dalloc(ctx, &ctx->jwork,
+                     jacobi_work_doubles((int)k) > eig_work_doubles((int)k) ? jacobi_work_doubles((int)k)
+                                                                           : eig_work_doubles((int)k))) ||
+        (st = dalloc(ctx, &ctx->gws, 8 * k * k)) || (st = dalloc(ctx, &ctx->info, 32)) ||
+        (st = dalloc(ctx, &ctx->errflag, 4)))
+        return st;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ctx->v, 0, sizeof(double) * np, ctx->s)) ||
+        (e = cudaMemsetAsync(ctx->errflag, 0, sizeof(int) * 4, ctx->s)) ||
+        (e = cudaMemsetAsync(ctx->x, 0, sizeof(double) * np, ctx->s)) || (e = cudaStreamSynchronize(ctx->s)))
+        return fail(ctx, RIOT_ECUDA, "setup failed: %s", cudaGetErrorString(e));
+    return RIOT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -279,134 +635,44 @@ riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_
     if (!model || !obs || !B || !opt) return RIOT_EINVAL;
     riot_ctx *ctx = new riot_ctx();
     for (int i = 0; i < 32; ++i) ctx->ev[i] = nullptr;
-    riot_status st = RIOT_OK;
     auto bail = [&](riot_status s2) {
         // keep the message readable for the caller through stderr; the context is gone
         fprintf(stderr, "riot_setup: %s\n", ctx->err);
         riot_destroy(ctx);
         return s2;
     };
-    if (model->kind != RIOT_MODEL_L96) return bail(fail(ctx, RIOT_EINVAL, "unknown model kind %d", model->kind));
-    const int64_t n64 = model->n;
-    if (n64 < 16 || n64 > 8192) return bail(fail(ctx, RIOT_EINVAL, "n = %lld outside [16, 8192]", (long long)n64));
-    const int n = (int)n64;
-    if (model->T < 0 || !(model->dt > 0.0) || !isfinite(model->F))
-        return bail(fail(ctx, RIOT_EINVAL, "bad T / dt / F"));
-    if (B->kind != RIOT_B_GAUSS_RING || !(B->length > 0.0))
-        return bail(fail(ctx, RIOT_EINVAL, "bad B descriptor (kind %d, length %g)", B->kind, B->length));
+    if (model->kind != RIOT_MODEL_L96 && model->kind != RIOT_MODEL_ADVDIFF)
+        return bail(fail(ctx, RIOT_EINVAL, "unknown model kind %d", model->kind));
     if (opt->kmax < 1 || opt->kmax > 4096) return bail(fail(ctx, RIOT_EINVAL, "kmax = %d outside [1, 4096]", opt->kmax));
     if (opt->precision != RIOT_PREC_MIXED && opt->precision != RIOT_PREC_FP64)
         return bail(fail(ctx, RIOT_EINVAL, "unknown precision %d", opt->precision));
     const int64_t p64 = obs->p;
     if (p64 < 0 || p64 > (int64_t)1 << 30) return bail(fail(ctx, RIOT_EINVAL, "bad observation count"));
-    const int p = (int)p64;
-    if (p > 0 && (!obs->step || !obs->idx || !obs->y || !obs->sigma))
+    if (p64 > 0 && (!obs->step || !obs->y || !obs->sigma))
         return bail(fail(ctx, RIOT_EINVAL, "null observation array"));
-    const int T = model->T;
-    for (int j = 0; j < p; ++j) {
-        if (obs->step[j] < 0 || obs->step[j] > T || obs->idx[j] < 0 || obs->idx[j] >= n || !(obs->sigma[j] > 0.0) ||
-            !isfinite(obs->y[j]))
-            return bail(fail(ctx, RIOT_EINVAL, "observation %d out of range", j));
+    if (model->T < 0 || !(model->dt > 0.0)) return bail(fail(ctx, RIOT_EINVAL, "bad T / dt"));
+    for (int64_t j = 0; j < p64; ++j) {
+        if (obs->step[j] < 0 || obs->step[j] > model->T || !(obs->sigma[j] > 0.0) || !isfinite(obs->y[j]))
+            return bail(fail(ctx, RIOT_EINVAL, "observation %lld out of range", (long long)j));
         if (j > 0 && obs->step[j] < obs->step[j - 1])
-            return bail(fail(ctx, RIOT_EINVAL, "observations not sorted by step at %d", j));
+            return bail(fail(ctx, RIOT_EINVAL, "observations not sorted by step at %lld", (long long)j));
     }
-    if (B->sigma_vec)
-        for (int i = 0; i < n; ++i)
-            if (!isfinite(B->sigma_vec[i])) return bail(fail(ctx, RIOT_EINVAL, "non-finite sigma_vec[%d]", i));
-
+    ctx->eig_method = opt->eig_method;
+    if (ctx->eig_method != RIOT_EIG_TRIDIAG && ctx->eig_method != RIOT_EIG_JACOBI)
+        return bail(fail(ctx, RIOT_EINVAL, "unknown eig_method %d", ctx->eig_method));
     cudaGetDevice(&ctx->dev);
     ctx->s = (cudaStream_t)cuda_stream;
     ctx->prec = opt->precision;
     ctx->kmax = opt->kmax;
     ctx->exact_rr = opt->exact_rr;
-    ctx->eig_method = opt->eig_method;
-    if (ctx->eig_method != RIOT_EIG_TRIDIAG && ctx->eig_method != RIOT_EIG_JACOBI)
-        return bail(fail(ctx, RIOT_EINVAL, "unknown eig_method %d", ctx->eig_method));
     ctx->seed = opt->seed;
-    L96Dev &m = ctx->m;
-    if (!choose_geom(n, &m.geom)) return bail(fail(ctx, RIOT_EINVAL, "no thread layout for n = %d", n));
-    m.T = T;
-    m.dt = model->dt;
-    m.F = model->F;
-    m.p = p;
-
-    // host tables
-    std::vector<int> optr(T + 2, p), oslot(p), oidx(p);
-    std::vector<double> rinv(p), yv(p);
-    std::vector<float> rinv32(p);
-    {
-        int j = 0;
-        for (int t = 0; t <= T + 1; ++t) {
-            while (j < p && obs->step[j] < t) ++j;
-            optr[t] = j;
-        }
-    }
-    for (int j = 0; j < p; ++j) {
-        oidx[j] = obs->idx[j];
-        oslot[j] = m.geom.slot(obs->idx[j]);
-        rinv[j] = 1.0 / (obs->sigma[j] * obs->sigma[j]);
-        rinv32[j] = (float)rinv[j];
-        yv[j] = obs->y[j];
-    }
-    std::vector<double> band;
-    int hl = 0, hh = 0;
-    build_band(n, B->length, band, hl, hh);
-    std::vector<float> band32(band.begin(), band.end());
-    std::vector<double> sig(n);
-    std::vector<float> sig32(n);
-    for (int i = 0; i < n; ++i) {
-        sig[i] = B->sigma_vec ? B->sigma_vec[i] : B->sigma_b;
-        sig32[i] = (float)sig[i];
-    }
-    m.band.hl = hl;
-    m.band.hh = hh;
-
-    const size_t np = (size_t)n, k = (size_t)ctx->kmax, rs = real_size(ctx);
-    if ((st = dalloc(ctx, &ctx->optr, T + 2)) || (st = dalloc(ctx, &ctx->oslot, p)) || (st = dalloc(ctx, &ctx->oidx, p)) ||
-        (st = dalloc(ctx, &ctx->y, p)) || (st = dalloc(ctx, &ctx->rinv64, p)) || (st = dalloc(ctx, &ctx->rinv32, p)) ||
-        (st = dalloc(ctx, &ctx->band64, band.size())) || (st = dalloc(ctx, &ctx->band32, band.size())) ||
-        (st = dalloc(ctx, &ctx->sig64, np)) || (st = dalloc(ctx, &ctx->sig32, np)) || (st = dalloc(ctx, &ctx->x, np)) ||
-        (st = dalloc(ctx, &ctx->v, np)) || (st = dalloc(ctx, &ctx->g, np)) || (st = dalloc(ctx, &ctx->dv, np)) ||
-        (st = dalloc(ctx, &ctx->tmp, np)) || (st = dalloc(ctx, &ctx->traj, (T + 1) * np)) ||
-        (st = dalloc(ctx, &ctx->d, p)) || (st = dalloc(ctx, &ctx->rd, p)) || (st = dalloc(ctx, &ctx->jo, 2)) ||
-        (st = dalloc(ctx, &ctx->coef64, (size_t)T * 4 * m.geom.Np + 1)) ||
-        (ctx->prec == RIOT_PREC_MIXED && (st = dalloc(ctx, &ctx->coef32, (size_t)T * 4 * m.geom.Np + 1))) ||
-        (st = dalloc(ctx, (char **)&ctx->Wblk, np * k * rs)) || (st = dalloc(ctx, (char **)&ctx->Yblk, np * k * rs)) ||
-        (st = dalloc(ctx, (char **)&ctx->rscr, (size_t)p * k * rs + 16)) || (st = dalloc(ctx, &ctx->Q, np * k)) ||
-        (st = dalloc(ctx, &ctx->U, np * k)) ||
-        (ctx->prec == RIOT_PREC_MIXED &&
-         ((st = dalloc(ctx, &ctx->Q32, np * k)) || (st = dalloc(ctx, &ctx->M32, k * k)) ||
-          (st = dalloc(ctx, &ctx->N32, k * k)) || (st = dalloc(ctx, &ctx->L32, k * k)))) || (st = dalloc(ctx, &ctx->G, k * k)) || (st = dalloc(ctx, &ctx->Mm, k * k)) ||
-        (st = dalloc(ctx, &ctx->Nm, k * k)) || (st = dalloc(ctx, &ctx->Km, k * k)) || (st = dalloc(ctx, &ctx->Z, k * k)) ||
-        (st = dalloc(ctx, &ctx->lam, k)) || (st = dalloc(ctx, &ctx->cvec, k)) ||
-        (st = dalloc(ctx, &ctx->jwork, jacobi_work_doubles((int)k) > eig_work_doubles((int)k) ? jacobi_work_doubles((int)k) : eig_work_doubles((int)k))) || (st = dalloc(ctx, &ctx->gws, 8 * k * k)) || (st = dalloc(ctx, &ctx->info, 32)) || (st = dalloc(ctx, &ctx->errflag, 4)))
-        return bail(st);
-    auto up = [&](void *dst, const void *src, size_t bytes) {
-        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->s) : cudaSuccess;
-    };
-    cudaError_t e = cudaSuccess;
-    if ((e = up(ctx->optr, optr.data(), sizeof(int) * (T + 2))) || (e = up(ctx->oslot, oslot.data(), sizeof(int) * p)) ||
-        (e = up(ctx->oidx, oidx.data(), sizeof(int) * p)) || (e = up(ctx->y, yv.data(), sizeof(double) * p)) ||
-        (e = up(ctx->rinv64, rinv.data(), sizeof(double) * p)) || (e = up(ctx->rinv32, rinv32.data(), sizeof(float) * p)) ||
-        (e = up(ctx->band64, band.data(), sizeof(double) * band.size())) ||
-        (e = up(ctx->band32, band32.data(), sizeof(float) * band.size())) ||
-        (e = up(ctx->sig64, sig.data(), sizeof(double) * n)) || (e = up(ctx->sig32, sig32.data(), sizeof(float) * n)) ||
-        (e = cudaMemsetAsync(ctx->v, 0, sizeof(double) * n, ctx->s)) ||
-        (e = cudaMemsetAsync(ctx->errflag, 0, sizeof(int) * 4, ctx->s)) ||
-        (e = cudaMemsetAsync(ctx->x, 0, sizeof(double) * n, ctx->s)) || (e = cudaStreamSynchronize(ctx->s)))
-        return bail(fail(ctx, RIOT_ECUDA, "setup upload failed: %s", cudaGetErrorString(e)));
+    ctx->model = model->kind;
+    ctx->p = (int)p64;
+    riot_status st = (model->kind == RIOT_MODEL_L96) ? setup_l96(ctx, model, obs, B) : setup_advdiff(ctx, model, obs, B);
+    if (st != RIOT_OK) return bail(st);
+    if ((st = setup_common(ctx)) != RIOT_OK) return bail(st);
     for (int i = 0; i < 32; ++i)
         if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) return bail(fail(ctx, RIOT_ECUDA, "cudaEventCreate failed"));
-    m.optr = ctx->optr;
-    m.oslot = ctx->oslot;
-    m.oidx = ctx->oidx;
-    m.y = ctx->y;
-    m.rinv64 = ctx->rinv64;
-    m.rinv32 = ctx->rinv32;
-    m.band64 = ctx->band64;
-    m.band32 = ctx->band32;
-    m.sig64 = ctx->sig64;
-    m.sig32 = ctx->sig32;
     *out = ctx;
     return RIOT_OK;
 }
@@ -415,14 +681,18 @@ riot_status riot_outer_begin(riot_ctx *ctx, const double *x_dev, const double *v
 {
     if (!ctx) return RIOT_EINVAL;
     CU(cudaSetDevice(ctx->dev));
-    const int n = ctx->m.geom.n;
+    const int n = ctx->n;
     if (x_dev) CU(cudaMemcpyAsync(ctx->x, x_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->s));
     if (v_dev) CU(cudaMemcpyAsync(ctx->v, v_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->s));
     CU(cudaMemsetAsync(ctx->jo, 0, sizeof(double) * 2, ctx->s));
-    CU(l96_nl_launch(ctx->m, ctx->x, ctx->traj, ctx->coef32, ctx->coef64, ctx->d, ctx->jo, nullptr, ctx->s));
-    // gradient b = L^T H^T R^-1 d: one FP64 adjoint integration, then g = b + v
-    CU(mul(ctx->m.p, ctx->d, ctx->rinv64, ctx->rd, ctx->s));
-    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->g, n, 1, 0, ctx->rd, 1, ctx->s));
+    if (ctx->model == RIOT_MODEL_ADVDIFF) {
+        CU(adv_outer(ctx->a, ctx->x, ctx->d, ctx->jo, ctx->rd, ctx->g, ctx->s));
+    } else {
+        CU(l96_nl_launch(ctx->m, ctx->x, ctx->traj, ctx->coef32, ctx->coef64, ctx->d, ctx->jo, nullptr, ctx->s));
+        // gradient b = L^T H^T R^-1 d: one FP64 adjoint integration, then g = b + v
+        CU(mul(ctx->p, ctx->d, ctx->rinv64, ctx->rd, ctx->s));
+        CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->g, n, 1, 0, ctx->rd, 1, ctx->s));
+    }
     CU(axpby(n, 1.0, ctx->v, 1.0, ctx->g, ctx->s));
     CU(add_half_sq(n, ctx->v, ctx->jo, ctx->s));
     ctx->have_traj = 1;
@@ -439,7 +709,7 @@ riot_status riot_hessian_apply(riot_ctx *ctx, const void *W_dev, void *Y_dev, in
 {
     if (!ctx) return RIOT_EINVAL;
     if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_hessian_apply before riot_outer_begin");
-    if (ncols < 0 || ld < ctx->m.geom.n) return fail(ctx, RIOT_EINVAL, "bad ncols / ld");
+    if (ncols < 0 || ld < ctx->n) return fail(ctx, RIOT_EINVAL, "bad ncols / ld");
     if (ncols == 0) return RIOT_OK;
     if (!W_dev || !Y_dev) return fail(ctx, RIOT_EINVAL, "null W or Y");
     CU(cudaSetDevice(ctx->dev));
@@ -451,26 +721,29 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
 {
     if (!ctx) return RIOT_EINVAL;
     if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_hessian_apply_noalloc before riot_outer_begin");
-    if (ncols < 0 || ld < ctx->m.geom.n) return fail(ctx, RIOT_EINVAL, "bad ncols / ld");
+    if (ncols < 0 || ld < ctx->n) return fail(ctx, RIOT_EINVAL, "bad ncols / ld");
     if (ncols == 0) return RIOT_OK;
     if (!W_dev || !Y_dev) return fail(ctx, RIOT_EINVAL, "null W or Y");
     CU(cudaSetDevice(ctx->dev));
     const size_t rs = real_size(ctx);
-    const size_t per_col = (size_t)ctx->m.p * rs;
+    const size_t per_col = (size_t)ctx->p * rs;
     if (per_col > kNoAllocScratchBytes)
         return fail(ctx, RIOT_EINVAL,
                     "riot_hessian_apply_noalloc: one column needs %zu bytes of residual scratch (%d observations), "
                     "the static array holds %zu bytes",
-                    per_col, ctx->m.p, kNoAllocScratchBytes);
+                    per_col, ctx->p, kNoAllocScratchBytes);
     void *scr = nullptr;
     CU(noalloc_scratch(ctx->dev, &scr));
     size_t slice = per_col ? kNoAllocScratchBytes / per_col : (size_t)ncols;
     if (slice > (size_t)ncols) slice = (size_t)ncols;
+    if (ctx->model == RIOT_MODEL_ADVDIFF && slice > (size_t)ctx->a.Pmax) slice = (size_t)ctx->a.Pmax;
     for (int c0 = 0; c0 < ncols; c0 += (int)slice) {
         const int nc = (ncols - c0 < (int)slice) ? ncols - c0 : (int)slice;
         const char *w = (const char *)W_dev + (size_t)c0 * ld * rs;
         char *yv = (char *)Y_dev + (size_t)c0 * ld * rs;
-        if (ctx->prec == RIOT_PREC_FP64)
+        if (ctx->model == RIOT_MODEL_ADVDIFF)
+            CU(adv_hvp(ctx->a, ctx->prec == RIOT_PREC_FP64, w, yv, ld, nc, add_identity, scr, ctx->s));
+        else if (ctx->prec == RIOT_PREC_FP64)
             CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, (const double *)w, (double *)yv, ld, nc, add_identity,
                                   (double *)scr, 0, ctx->s));
         else
@@ -485,7 +758,7 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
 {
     if (!ctx) return RIOT_EINVAL;
     if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_rsvd before riot_outer_begin");
-    const int n = ctx->m.geom.n;
+    const int n = ctx->n;
     if (k < 1 || k > ctx->kmax || k > n) return fail(ctx, RIOT_EINVAL, "k = %d outside [1, min(kmax, n)]", k);
     if (q < 0 || q > 64) return fail(ctx, RIOT_EINVAL, "q = %d outside [0, 64]", q);
     CU(cudaSetDevice(ctx->dev));
@@ -622,7 +895,7 @@ riot_status riot_increment(riot_ctx *ctx, double *dv_dev, int32_t *mode_out)
     if (!ctx) return RIOT_EINVAL;
     if (!ctx->have_rsvd) return fail(ctx, RIOT_ESTATE, "riot_increment before riot_rsvd");
     CU(cudaSetDevice(ctx->dev));
-    const int n = ctx->m.geom.n, k = ctx->k_last;
+    const int n = ctx->n, k = ctx->k_last;
     cudaStream_t s = ctx->s;
     // c = U^T g; scale by the adaptive rule; dv = U c (- g for LRU)
     CU(gemm('T', 'N', k, 1, n, 1.0, ctx->U, 'd', n, ctx->g, 'd', n, 0.0, ctx->cvec, 'd', k, s));
@@ -631,7 +904,7 @@ riot_status riot_increment(riot_ctx *ctx, double *dv_dev, int32_t *mode_out)
     CU(add_if_flag(ctx->info + 14, 1, n, -1.0, ctx->g, ctx->dv, s));
     // v += dv, x += L dv
     CU(axpby(n, 1.0, ctx->dv, 1.0, ctx->v, s));
-    CU(bsqrt_launch(ctx->m, ctx->dv, ctx->tmp, 0, 1, s));
+    CU(bsqrt(ctx, ctx->dv, ctx->tmp, 0, 1));
     CU(axpby(n, 1.0, ctx->tmp, 1.0, ctx->x, s));
     if (dv_dev) CU(cudaMemcpyAsync(dv_dev, ctx->dv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     if (mode_out) {
@@ -649,7 +922,7 @@ riot_status riot_analysis_cov_lowrank(riot_ctx *ctx, int32_t m, double *LU_dev, 
     CU(cudaSetDevice(ctx->dev));
     cudaStream_t s = ctx->s;
     CU(cov_coef(ctx->lam, m, ctx->cvec, ctx->info + 14, s));
-    if (LU_dev) CU(bsqrt_launch(ctx->m, ctx->U, LU_dev, 0, m, s));
+    if (LU_dev) CU(bsqrt(ctx, ctx->U, LU_dev, 0, m));
     if (coef_out) CU(cudaMemcpyAsync(coef_out, ctx->cvec, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
     if (mode_out) CU(cudaMemcpyAsync(mode_out, ctx->info + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (coef_out || mode_out) CU(cudaStreamSynchronize(s));
@@ -661,7 +934,17 @@ riot_status riot_bsqrt_apply(riot_ctx *ctx, const double *in_dev, double *out_de
     if (!ctx) return RIOT_EINVAL;
     if (ncols < 0 || (ncols > 0 && (!in_dev || !out_dev))) return fail(ctx, RIOT_EINVAL, "bad arguments");
     CU(cudaSetDevice(ctx->dev));
-    CU(bsqrt_launch(ctx->m, in_dev, out_dev, transpose, ncols, ctx->s));
+    CU(bsqrt(ctx, in_dev, out_dev, transpose, ncols));
+    return RIOT_OK;
+}
+
+riot_status riot_get_innovation(riot_ctx *ctx, double *d_dev)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_get_innovation before riot_outer_begin");
+    if (ctx->p > 0 && !d_dev) return fail(ctx, RIOT_EINVAL, "null d");
+    CU(cudaSetDevice(ctx->dev));
+    if (ctx->p > 0) CU(cudaMemcpyAsync(d_dev, ctx->d, sizeof(double) * ctx->p, cudaMemcpyDeviceToDevice, ctx->s));
     return RIOT_OK;
 }
 
@@ -669,7 +952,7 @@ riot_status riot_get_state(riot_ctx *ctx, double *x_dev, double *v_dev, double *
 {
     if (!ctx) return RIOT_EINVAL;
     CU(cudaSetDevice(ctx->dev));
-    const int n = ctx->m.geom.n;
+    const int n = ctx->n;
     cudaStream_t s = ctx->s;
     if (x_dev) CU(cudaMemcpyAsync(x_dev, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     if (v_dev) CU(cudaMemcpyAsync(v_dev, ctx->v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));

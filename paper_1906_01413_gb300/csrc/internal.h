@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/riot.h"
 
 namespace riot {
@@ -94,6 +96,47 @@ cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float 
 // out = L in or L^T in (FP64), ncols columns (ld = n)
 cudaError_t bsqrt_launch(const L96Dev &m, const double *in, double *out, int transpose, int ncols,
                          cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Tracer transport model (advdiff.cu)
+// ---------------------------------------------------------------------------
+struct AdvDev {
+    int nx = 0, ny = 0, nz = 0, nb = 0, T = 0;
+    double dt = 0, dx = 0, dy = 0, dz = 0, sigma_b = 0;
+    long long n = 0, ncells = 0;
+    int p = 0;
+    std::vector<int> optr_h;          // host copy [T+2]: obs of step t are optr[t] .. optr[t+1]-1
+    const int *cell = nullptr;        // [p*8] flat cell (l*ny + j)*nx + i of each trilinear corner
+    const double *w64 = nullptr;      // [p*8] trilinear weights
+    const float *w32 = nullptr;
+    const double *y = nullptr, *rinv64 = nullptr;
+    const float *rinv32 = nullptr;
+    const double *u64 = nullptr, *v64 = nullptr, *amp64 = nullptr, *kz64 = nullptr;
+    const float *u32 = nullptr, *v32 = nullptr, *amp32 = nullptr, *kz32 = nullptr;
+    const double *Sx64 = nullptr, *Sy64 = nullptr;   // symmetric square roots, row-major
+    const float *Sx32 = nullptr, *Sy32 = nullptr;
+    const double *Eb = nullptr;       // [n] background emissions
+    double *Es64 = nullptr;           // [n] E / dz at the current control
+    float *Es32 = nullptr;
+    // batch workspace (Pmax probes of the context precision)
+    int Pmax = 0, Pmax64 = 0;
+    void *cA = nullptr, *cB = nullptr, *src = nullptr, *ebar = nullptr, *tmp = nullptr;
+    // FP64 outer-loop workspace
+    double *c64A = nullptr, *c64B = nullptr, *ebar64 = nullptr, *tmp64 = nullptr;   // tmp64: Pmax64 * n
+};
+
+// Y = A W (+ W) for ncols columns (ld >= n), in FP64 or FP32 (per fp64); r
+// holds Pmax * p residuals of that type.
+cudaError_t adv_hvp(const AdvDev &m, bool fp64, const void *W, void *Y, int64_t ld, int ncols, int add_identity,
+                    void *r, cudaStream_t s);
+// Outer-loop prerequisites at control x (FP64): E / dz, d = H(x) - y,
+// jo += 1/2 sum d^2 / sigma^2 (atomic), rd = R^-1 d, b = L^T H'^T R^-1 d.
+cudaError_t adv_outer(const AdvDev &m, const double *x, double *d, double *jo, double *rd, double *b,
+                      cudaStream_t s);
+// out = L in (= L^T in), ncols columns of n doubles
+cudaError_t adv_bsqrt(const AdvDev &m, const double *in, double *out, int ncols, cudaStream_t s);
+// tracer field after `steps` steps from zero with emissions E_b exp(x) (FP64)
+cudaError_t adv_forecast(const AdvDev &m, const double *x, int steps, double *c_out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Random numbers (rng.cu)

@@ -16,7 +16,9 @@ LIB_PATH = os.path.join(HERE, "libriot.so")
 
 RIOT_OK = 0
 RIOT_MODEL_L96 = 1
+RIOT_MODEL_ADVDIFF = 2
 RIOT_B_GAUSS_RING = 1
+RIOT_B_EXP_SEPARABLE = 2
 RIOT_PREC_MIXED = 0
 RIOT_PREC_FP64 = 1
 RIOT_EIG_TRIDIAG = 0
@@ -25,13 +27,21 @@ STATUS = {0: "RIOT_OK", -1: "RIOT_EINVAL", -2: "RIOT_ENOMEM", -3: "RIOT_ECUDA", 
           -5: "RIOT_ETIMEOUT", -6: "RIOT_ESTATE", -7: "RIOT_ENOCONV", -8: "RIOT_ENONFINITE"}
 
 
+class AdvDiffDesc(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("nblocks", c_int32),
+                ("dx", c_double), ("dy", c_double), ("dz", c_double),
+                ("u", POINTER(c_double)), ("v", POINTER(c_double)), ("amp", POINTER(c_double)),
+                ("kz", POINTER(c_double)), ("emis_b", POINTER(c_double))]
+
+
 class ModelDesc(ctypes.Structure):
-    _fields_ = [("kind", c_int32), ("T", c_int32), ("n", c_int64), ("dt", c_double), ("F", c_double)]
+    _fields_ = [("kind", c_int32), ("T", c_int32), ("n", c_int64), ("dt", c_double), ("F", c_double),
+                ("advdiff", POINTER(AdvDiffDesc))]
 
 
 class ObsDesc(ctypes.Structure):
     _fields_ = [("p", c_int64), ("step", POINTER(c_int32)), ("idx", POINTER(c_int32)),
-                ("y", POINTER(c_double)), ("sigma", POINTER(c_double))]
+                ("y", POINTER(c_double)), ("sigma", POINTER(c_double)), ("pos", POINTER(c_double))]
 
 
 class BcovDesc(ctypes.Structure):
@@ -73,6 +83,7 @@ def load():
     L.riot_analysis_cov_lowrank.argtypes = [vp, c_int32, vp, POINTER(c_double), POINTER(c_int32)]
     L.riot_bsqrt_apply.argtypes = [vp, vp, vp, c_int32, c_int32]
     L.riot_get_state.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.riot_get_innovation.argtypes = [vp, vp]
     L.riot_draw_normal.argtypes = [c_uint64, c_int64, c_int64, c_int32, c_int64, c_int32, vp, vp]
     L.riot_l96_forecast.argtypes = [c_int64, c_int32, c_double, c_double, vp, vp, c_int32, vp]
     L.riot_rsvd_timings.argtypes = [vp, POINTER(c_double)]
@@ -92,7 +103,7 @@ def load():
     for name in ("riot_setup", "riot_outer_begin", "riot_hessian_apply", "riot_hessian_apply_noalloc",
                  "riot_rsvd", "riot_increment",
                  "riot_analysis_cov_lowrank", "riot_bsqrt_apply", "riot_get_state", "riot_draw_normal",
-                 "riot_l96_forecast", "riot_rsvd_timings", "riot_symm_eig"):
+                 "riot_l96_forecast", "riot_rsvd_timings", "riot_symm_eig", "riot_get_innovation"):
         getattr(L, name).restype = c_int32
     _lib = L
     return L
@@ -125,9 +136,9 @@ def riot_setup(n, T, dt, F, obs_step, obs_idx, obs_y, obs_sigma, length, sigma_b
     ix = np.ascontiguousarray(obs_idx, dtype=np.int32)
     yy = np.ascontiguousarray(obs_y, dtype=np.float64)
     sg = np.ascontiguousarray(obs_sigma, dtype=np.float64)
-    md = ModelDesc(RIOT_MODEL_L96, int(T), int(n), float(dt), float(F))
+    md = ModelDesc(RIOT_MODEL_L96, int(T), int(n), float(dt), float(F), None)
     od = ObsDesc(int(st.size), st.ctypes.data_as(POINTER(c_int32)), ix.ctypes.data_as(POINTER(c_int32)),
-                 yy.ctypes.data_as(POINTER(c_double)), sg.ctypes.data_as(POINTER(c_double)))
+                 yy.ctypes.data_as(POINTER(c_double)), sg.ctypes.data_as(POINTER(c_double)), None)
     sv = None if sigma_vec is None else np.ascontiguousarray(sigma_vec, dtype=np.float64)
     bd = BcovDesc(RIOT_B_GAUSS_RING, 0, float(length), float(sigma_b),
                   None if sv is None else sv.ctypes.data_as(POINTER(c_double)))
@@ -137,6 +148,38 @@ def riot_setup(n, T, dt, F, obs_step, obs_idx, obs_y, obs_sigma, length, sigma_b
                           ctypes.byref(op), _stream_handle(stream))
     _check(None, "riot_setup", status)
     return h
+
+
+def _dp(a):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+def riot_setup_advdiff(nx, ny, nz, nblocks, T, dt, dx, dy, dz, u, v, amp, kz, emis_b, obs_step, obs_pos, obs_y,
+                       obs_sigma, length, sigma_b, precision=RIOT_PREC_MIXED, kmax=64, exact_rr=False, seed=0,
+                       stream=None, eig_method=RIOT_EIG_TRIDIAG):
+    """riot_setup for the tracer model (RIOT_MODEL_ADVDIFF with RIOT_B_EXP_SEPARABLE)."""
+    L = load()
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (u, v, amp, kz, emis_b)]
+    ad = AdvDiffDesc(int(nx), int(ny), int(nz), int(nblocks), float(dx), float(dy), float(dz),
+                     *[_dp(a) for a in arrs])
+    n = int(nblocks) * int(ny) * int(nx)
+    md = ModelDesc(RIOT_MODEL_ADVDIFF, int(T), n, float(dt), 0.0, ctypes.pointer(ad))
+    st = np.ascontiguousarray(obs_step, dtype=np.int32)
+    pos = np.ascontiguousarray(obs_pos, dtype=np.float64).reshape(-1)
+    yy = np.ascontiguousarray(obs_y, dtype=np.float64)
+    sg = np.ascontiguousarray(obs_sigma, dtype=np.float64)
+    od = ObsDesc(int(st.size), st.ctypes.data_as(POINTER(c_int32)), None, _dp(yy), _dp(sg), _dp(pos))
+    bd = BcovDesc(RIOT_B_EXP_SEPARABLE, 0, float(length), float(sigma_b), None)
+    op = Options(int(precision), int(kmax), int(bool(exact_rr)), int(eig_method), int(seed))
+    h = c_void_p()
+    status = L.riot_setup(ctypes.byref(h), ctypes.byref(md), ctypes.byref(od), ctypes.byref(bd),
+                          ctypes.byref(op), _stream_handle(stream))
+    _check(None, "riot_setup", status)
+    return h
+
+
+def riot_get_innovation(ctx, d):
+    _check(ctx, "riot_get_innovation", load().riot_get_innovation(ctx, _ptr(d)))
 
 
 def riot_outer_begin(ctx, x=None, v=None):
@@ -242,8 +285,12 @@ class Context:
     """Owning wrapper: ``with Context(...) as c: riot_rsvd(c.h, ...)``."""
 
     def __init__(self, **kw):
-        self.n = int(kw["n"])
-        self.h = riot_setup(**kw)
+        if "nx" in kw:
+            self.n = int(kw["nblocks"]) * int(kw["ny"]) * int(kw["nx"])
+            self.h = riot_setup_advdiff(**kw)
+        else:
+            self.n = int(kw["n"])
+            self.h = riot_setup(**kw)
 
     def close(self):
         if self.h:
