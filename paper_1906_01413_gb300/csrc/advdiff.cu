@@ -30,8 +30,12 @@ namespace {
 
 constexpr int kHalo = 4;
 
+constexpr int kMaxNZ = 32;
+
 template <typename R>
 struct StepArgs {
+    R amp[kMaxNZ];        // level scaling of the winds (0 beyond nz)
+    R kzs[kMaxNZ + 1];    // Kz / dz^2 on face l-1/2 (0 on the bottom, the top and beyond)
     const R *cin;
     R *cout;
     long long pstride;    // cells per probe
@@ -39,9 +43,9 @@ struct StepArgs {
     long long sstride;
     R *ebar;              // source adjoint of this step's block (AD), per probe at estride
     long long estride;
-    const R *u, *v, *amp, *kzf;
+    const R *u, *v;
     int nx, ny, nz;
-    R h, rdx, rdy, rdz2;
+    R h, rdx, rdy;
 };
 
 template <typename R, int NZ, int TX, int TY, bool ADJ>
@@ -49,12 +53,9 @@ __global__ void __launch_bounds__((TX + 2 * kHalo) * (TY + 2 * kHalo), 1) adv_st
 {
     constexpr int RX = TX + 2 * kHalo, RY = TY + 2 * kHalo, PL = RX * RY;
     extern __shared__ __align__(16) unsigned char adv_smem[];
-    R *S = reinterpret_cast<R *>(adv_smem);   // [NZ][RY][RX] stage input
-    R *samp = S + NZ * PL;                     // [NZ]
-    R *skz = samp + NZ;                        // [NZ + 1]
+    // two [NZ][RY][RX] planes of stage inputs, used alternately: one barrier per stage
+    R *S0 = reinterpret_cast<R *>(adv_smem);
     const int tid = threadIdx.x;
-    if (tid < NZ) samp[tid] = tid < a.nz ? a.amp[tid] : R(0);
-    if (tid <= NZ) skz[tid] = (tid > 0 && tid < a.nz) ? a.kzf[tid] : R(0);
     const int rx = tid % RX, ry = tid / RX;
     const int nx = a.nx, ny = a.ny;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -99,11 +100,17 @@ __global__ void __launch_bounds__((TX + 2 * kHalo) * (TY + 2 * kHalo), 1) adv_st
     if (!ADJ && valid && a.src) s0 = a.src[(size_t)blockIdx.z * a.sstride + col];
     const R h = a.h, h2 = R(0.5) * a.h, h3 = a.h / R(3), h6 = a.h / R(6);
     R e0 = R(0);
-    __syncthreads();
 #pragma unroll
     for (int st = 1; st <= 4; ++st) {
+        R *S = S0 + (st & 1) * NZ * PL;
+        // the stage input is read on the region of this stage grown by one column;
+        // rows beyond the walls publish their zeros (their coefficients are 0, but
+        // a stale value times 0 would not be)
+        const bool pub = rx >= st - 1 && rx < RX - st + 1 && ry >= st - 1 && ry < RY - st + 1;
+        if (pub) {
 #pragma unroll
-        for (int z = 0; z < NZ; ++z) S[z * PL + ry * RX + rx] = w[z];
+            for (int z = 0; z < NZ; ++z) S[z * PL + ry * RX + rx] = w[z];
+        }
         if (ADJ) e0 += (st == 1 || st == 4) ? w[0] : R(2) * w[0];
         __syncthreads();
         const bool act = valid && rx >= st && rx < RX - st && ry >= st && ry < RY - st;
@@ -115,7 +122,7 @@ __global__ void __launch_bounds__((TX + 2 * kHalo) * (TY + 2 * kHalo), 1) adv_st
                 const R wp = (z + 1 < NZ) ? w[z + 1] : R(0);
                 const R *Sz = S + z * PL + ry * RX + rx;
                 const R hor = c0 * wz + cE * Sz[1] + cW * Sz[-1] + cN * Sz[RX] + cS * Sz[-RX];
-                R k = samp[z] * hor + (skz[z + 1] * (wp - wz) - skz[z] * (wz - wm)) * a.rdz2;
+                R k = a.amp[z] * hor + a.kzs[z + 1] * (wp - wz) - a.kzs[z] * (wz - wm);
                 if (!ADJ && z == 0) k += s0;
                 if (st == 1) {
                     acc[z] = c[z] + h6 * k;
@@ -132,7 +139,6 @@ __global__ void __launch_bounds__((TX + 2 * kHalo) * (TY + 2 * kHalo), 1) adv_st
                 wm = wz;
             }
         }
-        __syncthreads();
     }
     const int ix = rx - kHalo, iy = ry - kHalo;
     if (valid && ix >= 0 && ix < TX && iy >= 0 && iy < TY && x0 + ix < nx) {
@@ -326,7 +332,7 @@ cudaError_t step_nz(const StepArgs<R> &a, int P, cudaStream_t s)
 {
     constexpr int TX = TileShape<R>::TX, TY = TileShape<R>::TY;
     constexpr int RX = TX + 2 * kHalo, RY = TY + 2 * kHalo;
-    const size_t smem = sizeof(R) * ((size_t)NZ * RX * RY + 2 * NZ + 1);
+    const size_t smem = sizeof(R) * 2 * (size_t)NZ * RX * RY;
     auto kern = adv_step_kernel<R, NZ, TX, TY, ADJ>;
     static bool attr_done = false;
     if (!attr_done) {
@@ -354,15 +360,15 @@ cudaError_t step(const AdvDev &m, const R *cin, R *cout, int P, const R *src, lo
     a.estride = estride;
     a.u = Tab<R>::u(m);
     a.v = Tab<R>::v(m);
-    a.amp = Tab<R>::amp(m);
-    a.kzf = Tab<R>::kz(m);
+    for (int l = 0; l < kMaxNZ; ++l) a.amp[l] = l < m.nz ? (R)m.amp_h[l] : R(0);
+    for (int l = 0; l <= kMaxNZ; ++l)
+        a.kzs[l] = (l > 0 && l < m.nz) ? (R)(m.kz_h[l] / (m.dz * m.dz)) : R(0);
     a.nx = m.nx;
     a.ny = m.ny;
     a.nz = m.nz;
     a.h = (R)m.dt;
     a.rdx = (R)(1.0 / m.dx);
     a.rdy = (R)(1.0 / m.dy);
-    a.rdz2 = (R)(1.0 / (m.dz * m.dz));
     if (m.nz <= 8) return adj ? step_nz<R, 8, true>(a, P, s) : step_nz<R, 8, false>(a, P, s);
     if (m.nz <= 16) return adj ? step_nz<R, 16, true>(a, P, s) : step_nz<R, 16, false>(a, P, s);
     return adj ? step_nz<R, 32, true>(a, P, s) : step_nz<R, 32, false>(a, P, s);

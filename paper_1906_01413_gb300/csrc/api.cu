@@ -508,6 +508,8 @@ riot_status setup_advdiff(riot_ctx *ctx, const riot_model_desc *model, const rio
     std::vector<double> u(ad->u, ad->u + nyx), v(ad->v, ad->v + nyx + nx), amp(ad->amp, ad->amp + nz),
         kz(nz + 1, 0.0), Eb(ad->emis_b, ad->emis_b + n);
     for (int l = 1; l < nz; ++l) kz[l] = ad->kz[l];
+    a.amp_h = amp;
+    a.kz_h = kz;
     const double *rinv64 = nullptr, *w64 = nullptr;
     const float *rinv32 = nullptr, *w32 = nullptr, *Eb32 = nullptr;
     TRY(upload2(ctx, u, &a.u64, &a.u32));

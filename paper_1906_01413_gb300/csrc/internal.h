@@ -106,6 +106,7 @@ struct AdvDev {
     long long n = 0, ncells = 0;
     int p = 0;
     std::vector<int> optr_h;          // host copy [T+2]: obs of step t are optr[t] .. optr[t+1]-1
+    std::vector<double> amp_h, kz_h;  // host copies [nz], [nz+1] (kernel parameters)
     const int *cell = nullptr;        // [p*8] flat cell (l*ny + j)*nx + i of each trilinear corner
     const double *w64 = nullptr;      // [p*8] trilinear weights
     const float *w32 = nullptr;
