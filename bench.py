@@ -6,10 +6,11 @@ variables observed at fixed random indices every 4 steps (51 200
 observations, sigma_o = 1), Gaussian B (sigma_b = 1, length 4), k = 512
 Gaussian sketch columns, q = 1 power iteration.  A step is one full inner
 loop: sketch draw, 2 x 512 Hessian-vector products (tangent-linear +
-adjoint integrations), CholeskyQR, the projected matrix K, its FP64 Jacobi
-eigendecomposition, the Ritz vectors and the adaptive increment.  The
-outer-loop prerequisites (nonlinear trajectory, gradient) run once before
-the timed region.
+adjoint integrations), CholeskyQR, the projected matrix K, its FP64
+tridiagonal eigendecomposition, the Ritz vectors and the adaptive increment.
+The outer-loop prerequisites (nonlinear trajectory, gradient) run once before
+the timed region.  The same line carries the Hessian-vector products of the
+tracer-transport inversion on its full 192 x 192 x 30 grid (bc_transport).
 
 Metric: Hessian-vector products per second of inner-loop wall time (with the
 inner-loop milliseconds), for the mixed-precision path and the plain FP64
@@ -30,6 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from synth import advdiff as bc_synth  # noqa: E402
 from synth import configs  # noqa: E402
 
 WORKLOAD = "l96_n4096_F8_T200_obs25pct_every4_k512_q1"
@@ -46,6 +48,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-bc", action="store_true", help="skip the tracer-transport Hessian products")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the first timed step with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -129,25 +132,8 @@ class ClockSampler:
 
 
 def build_problem(R, torch, cfg, dev, precision, kmax):
-    """Synthetic twin experiment built with the library itself: truth spun up
-    on the attractor, observations of the truth plus noise, background =
-    truth + L eps_b (random draws from the seeded Philox streams)."""
-    n, T = cfg.n, cfg.T
-    x_init = torch.tensor(cfg.F + cfg.truth_sd * cfg.truth_perturbation(), device=dev)
-    x0 = torch.empty(n, dtype=torch.float64, device=dev)
-    R.riot_l96_forecast(n, cfg.spinup, cfg.dt, cfg.F, x_init, x0, store_all=False)
-    traj = torch.empty(T + 1, n, dtype=torch.float64, device=dev)
-    R.riot_l96_forecast(n, T, cfg.dt, cfg.F, x0, traj)
-    st, ix = cfg.obs_layout_arrays()
-    sig = np.full(st.size, cfg.sigma_o)
-    y = traj[torch.tensor(st, device=dev), torch.tensor(ix, device=dev)].cpu().numpy() + sig * cfg.obs_noise(st.size)
-    ctx = R.Context(n=n, T=T, dt=cfg.dt, F=cfg.F, obs_step=st, obs_idx=ix, obs_y=y, obs_sigma=sig,
-                    length=cfg.ell, sigma_b=cfg.sigma_b, precision=precision, kmax=kmax, seed=cfg.seed)
-    eps = torch.tensor(cfg.background_perturbation(), device=dev)
-    xb = torch.empty(n, dtype=torch.float64, device=dev)
-    R.riot_bsqrt_apply(ctx.h, eps, xb)
-    xb += x0
-    return ctx, xb, st.size
+    from paper_1906_01413_gb300 import workloads
+    return workloads.l96_twin(R, torch, cfg, dev, precision, kmax)
 
 
 def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False):
@@ -174,6 +160,47 @@ def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False)
             ph["jacobi_sweeps"] = R.riot_rsvd_sweeps(ctx.h)
             phases.append(ph)
     return times, phases, lam, mode
+
+
+def build_bc_problem(R, torch, cfg, dev, precision, kmax):
+    from paper_1906_01413_gb300 import workloads
+    return workloads.bc_twin(R, torch, cfg, dev, precision, kmax)
+
+
+def bench_bc_transport(R, torch, dev, flush, hbm_peak, ncols=128, reps=2):
+    """Hessian-vector products of the tracer inversion on its full grid
+    (192 x 192 x 30 cells, 240 steps, 8000 observations), one launch block of
+    ncols sketch columns per call, FP32 transport."""
+    cfg = bc_synth.bc_large()
+    ctx, xb, p = build_bc_problem(R, torch, cfg, dev, R.RIOT_PREC_MIXED, ncols)
+    R.riot_outer_begin(ctx.h, xb)
+    W = torch.empty(ncols, cfg.n, dtype=torch.float32, device=dev)
+    R.riot_draw_normal(cfg.seed, bc_synth.STREAM_SKETCH0, cfg.n, ncols, W)
+    Y = torch.empty_like(W)
+    R.riot_hessian_apply(ctx.h, W, Y)
+    s = torch.cuda.current_stream()
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        R.riot_hessian_apply(ctx.h, W, Y)
+        e1.record(s)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ctx.close()
+    ms = statistics.mean(times)
+    ncells = cfg.nx * cfg.ny * cfg.nz
+    bytes_per_hvp = 8.0 * ncells * cfg.T * 2
+    achieved = bytes_per_hvp * ncols / (ms * 1e-3) / 1e9
+    return {"workload": "bc_%dx%dx%d_T%d_obs%d_blocks%d" % (cfg.nx, cfg.ny, cfg.nz, cfg.T, p, cfg.nblocks),
+            "value": ncols / (ms * 1e-3), "unit": "HVP/s", "ms_per_hvp": ms / ncols, "columns_per_call": ncols,
+            "dtype": "f32",
+            "roofline": {"bound": "hbm", "kernel": "adv_step_kernel<float,32,32,4> (whole product timed)",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": None, "bytes_per_hvp": bytes_per_hvp,
+                         "bytes_basis": "one FP32 read and write of the tracer per RK4 step, TL and AD"}}
 
 
 def cpu_oracle_hvps(cfg, seconds, min_cols=2):
@@ -303,6 +330,11 @@ def main():
             e2e_times.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_times)
 
+    # ---- tracer-transport inversion (workload 3): Hessian products on the full grid ----
+    bc = None
+    if not args.no_bc:
+        bc = bench_bc_transport(R, torch, dev, flush, float(peaks.get("hbm_gbs", 6800.0)))
+
     # ---- plain FP64 GPU form -----------------------------------------------------------
     fp64 = None
     if args.fp64_steps > 0:
@@ -323,12 +355,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "T": T, "k": k, "q": q, "p_obs": int(p),
-                       "precision": "TL/AD f32; Gram, Cholesky, Jacobi eig, increment f64",
+                       "precision": "TL/AD f32; Gram, Cholesky, tridiagonal eig, increment f64",
                        "l2": "256 MB buffer written between timed steps (flush)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "inner_loop_ms": ms},
             "phases_ms": ph,
-            "roofline": {"bound": "alu", "kernel": "l96_hvp_kernel<float,8>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "l96_hvp_tma_kernel<8,2,512>", "achieved": achieved,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                          "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sm_count, sm_max),
                          "flop_per_hvp": flop_hvp, "hvp_per_launch": k, "launch_ms": hvp_launch_ms},
@@ -338,6 +370,8 @@ def main():
             "wall_s_timed": wall}
     if fp64:
         line["fp64_gpu_form"] = fp64
+    if bc:
+        line["bc_transport"] = bc
     cs = clk.summary()
     if cs:
         line["clocks"] = cs

@@ -289,6 +289,52 @@ int32_t riot_rsvd_sweeps(const riot_ctx *ctx);
  * contexts); a benchmark reads it before and after a timed region. */
 uint64_t riot_kernel_launches(void);
 
+/* ---- Batches of windows ------------------------------------------------------
+ * Many independent Lorenz-96 windows (contexts of any n, T, observations and
+ * k) run their inner loops together: the Hessian products of all windows in
+ * one persistent launch per Hessian application (a queue of (window, block)
+ * items over all SMs), the per-window linear algebra on parallel branches,
+ * and the whole inner loop captured once as a CUDA graph and replayed.  The
+ * paper runs its samples as independent jobs (Algorithm 3, "do in
+ * parallel"); this extends the same independence across windows.
+ * Contexts must be RIOT_PREC_MIXED, RIOT_MODEL_L96, on one device, each used
+ * by one batch at a time and not otherwise while the batch runs. */
+typedef struct riot_batch riot_batch;
+
+/* Create a batch of nwin windows: window w uses ctxs[w] with k[w] sketch
+ * columns (1 <= k[w] <= min(kmax, n)) and q power iterations.  The batch
+ * owns one stream per window; cuda_stream is the stream its work joins.
+ * The contexts are not copied: they must outlive the batch. */
+riot_status riot_batch_create(riot_batch **out, riot_ctx *const *ctxs, int32_t nwin, const int32_t *k, int32_t q,
+                              void *cuda_stream);
+
+/* Time the persistent Hessian launch for a set of launch shapes (probe
+ * groups per CTA capped at 0 = as many as fit, 32, 16, 8, 4, 2; ring depths
+ * 4, 3, 2), keep the fastest and report it (outputs may be NULL).  Writes
+ * Gaussian blocks into the windows' workspaces; requires riot_outer_begin on
+ * every window.  Results never depend on the shape. */
+riot_status riot_batch_autotune(riot_batch *b, int32_t *probes_cap_out, int32_t *ring_depth_out, double *ms_out);
+
+/* Set the launch shape directly (0 = automatic); drops a captured graph. */
+riot_status riot_batch_set_config(riot_batch *b, int32_t probes_cap, int32_t ring_depth);
+
+/* Y = A W for every window in one launch, W and Y being each context's
+ * internal sketch blocks (for timing and tests). */
+riot_status riot_batch_hessian_apply(riot_batch *b);
+
+/* One inner loop of every window: riot_rsvd (sketch from the window's seed
+ * and sketch_stream) followed by riot_increment, as one CUDA graph
+ * (use_graph = 1; captured on the first call and replayed while
+ * sketch_stream stays the same) or as plain stream work (use_graph = 0).
+ * Synchronises.  status_out (nwin, may be NULL) receives each window's
+ * status; the return value is the first failure.  Afterwards each context
+ * holds its eigenpairs and increment as after riot_rsvd + riot_increment
+ * (do not call riot_increment again for the same inner loop). */
+riot_status riot_batch_run(riot_batch *b, int64_t sketch_stream, int32_t use_graph, int32_t *status_out);
+
+const char *riot_batch_last_error(const riot_batch *b);
+void riot_batch_destroy(riot_batch *b);
+
 const char *riot_last_error(const riot_ctx *ctx);
 const char *riot_status_string(riot_status s);
 void riot_destroy(riot_ctx *ctx);

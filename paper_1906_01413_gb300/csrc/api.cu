@@ -45,7 +45,7 @@ struct riot_ctx {
     float *Q32 = nullptr, *M32 = nullptr, *N32 = nullptr, *L32 = nullptr;   // mixed precision only
     double *G = nullptr, *Mm = nullptr, *Nm = nullptr, *Km = nullptr, *Z = nullptr, *lam = nullptr, *cvec = nullptr;
     double *jwork = nullptr;
-    double *gws = nullptr;   // split-K partial Grams, 8 kmax^2
+    double *gws = nullptr;   // split-K partial Grams (8 kmax^2) and Cholesky block inverses (dinv_doubles(kmax))
     int *info = nullptr;  // [0..9] CholeskyQR passes, [10] K Cholesky, [12..13] Jacobi, [14] mode
     int *errflag = nullptr;  // set by a kernel whose bounded wait ran out
     int have_traj = 0, have_rsvd = 0, k_last = 0, v_init = 0, jacobi_sweeps = 0;
@@ -53,6 +53,26 @@ struct riot_ctx {
     cudaEvent_t ev[32];
     int nev = 0;
     int ev_phase[32];
+    char err[512] = {0};
+};
+
+// A batch of Lorenz-96 windows run together (riot_batch_*).
+struct riot_batch {
+    int dev = 0;
+    cudaStream_t s = nullptr;              // caller's stream
+    cudaStream_t main = nullptr;           // the batch's own stream: main branch of the graph
+    cudaEvent_t done = nullptr;
+    std::vector<riot_ctx *> ctx;
+    std::vector<int> k;
+    int q = 0;
+    std::vector<cudaStream_t> ws;          // one branch stream per window
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    std::vector<riot::HvpBatchWindow> wins;
+    riot::HvpBatchPlan plan;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_sketch = -1;
     char err[512] = {0};
 };
 
@@ -75,6 +95,12 @@ riot_status fail(riot_ctx *c, riot_status st, const char *fmt, ...)
         if (e_ != cudaSuccess)                                                                       \
             return fail(ctx, RIOT_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
                         __LINE__);                                                                   \
+    } while (0)
+
+#define CU_B(call)                                                                                   \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return bfail(b, RIOT_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
 template <typename T>
@@ -583,7 +609,8 @@ riot_status setup_common(riot_ctx *ctx)
         (st = dalloc(ctx, &ctx->jwork,
                      jacobi_work_doubles((int)k) > eig_work_doubles((int)k) ? jacobi_work_doubles((int)k)
                                                                            : eig_work_doubles((int)k))) ||
-        (st = dalloc(ctx, &ctx->gws, 8 * k * k)) || (st = dalloc(ctx, &ctx->info, 32)) ||
+        (st = dalloc(ctx, &ctx->gws, 8 * k * k > dinv_doubles((int)k) ? 8 * k * k : dinv_doubles((int)k))) ||
+        (st = dalloc(ctx, &ctx->info, 32)) ||
         (st = dalloc(ctx, &ctx->errflag, 4)))
         return st;
     cudaError_t e;
@@ -592,6 +619,244 @@ riot_status setup_common(riot_ctx *ctx)
         (e = cudaMemsetAsync(ctx->x, 0, sizeof(double) * np, ctx->s)) || (e = cudaStreamSynchronize(ctx->s)))
         return fail(ctx, RIOT_ECUDA, "setup failed: %s", cudaGetErrorString(e));
     return RIOT_OK;
+}
+
+riot_status rsvd_check_args(riot_ctx *ctx, int k, int q)
+{
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_rsvd before riot_outer_begin");
+    if (k < 1 || k > ctx->kmax || k > ctx->n) return fail(ctx, RIOT_EINVAL, "k = %d outside [1, min(kmax, n)]", k);
+    if (q < 0 || q > 64) return fail(ctx, RIOT_EINVAL, "q = %d outside [0, 64]", q);
+    return RIOT_OK;
+}
+
+// Inner loop of Algorithm 3 in phases that queue work on ctx->s and never
+// synchronise, so that a batch of windows can capture them in one graph:
+// rsvd_begin (sketch), [Hessian], rsvd_power + [Hessian] per power
+// iteration, rsvd_end (Q, K, eigenpairs, Ritz vectors), rsvd_collect (host
+// checks), increment_queue (the adaptive increment).
+riot_status rsvd_begin(riot_ctx *ctx, int k, int64_t sketch_stream, const void *Omega)
+{
+    const int n = ctx->n;
+    CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 32, ctx->s));
+    if (Omega)
+        CU(cudaMemcpyAsync(ctx->Wblk, Omega, (size_t)n * k * real_size(ctx), cudaMemcpyDeviceToDevice, ctx->s));
+    else
+        CU(normal_launch(ctx->seed, (uint32_t)sketch_stream, n, k, n, ctx->prec == RIOT_PREC_FP64, ctx->Wblk, ctx->s));
+    return RIOT_OK;
+}
+
+// W = orth(Y) for the next power iteration
+riot_status rsvd_power(riot_ctx *ctx, int k)
+{
+    const int n = ctx->n;
+    if (ctx->prec == RIOT_PREC_MIXED) {
+        // a power-iteration basis only has to span the block well: shifted pass + one plain pass
+        TRY(orth32(ctx, (const float *)ctx->Yblk, k, 0, 2));
+        CU(cudaMemcpyAsync(ctx->Wblk, ctx->Q32, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, ctx->s));
+    } else {
+        TRY(orth(ctx, ctx->Yblk, k, 0));
+        CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, real_tag(ctx), n, n, k, ctx->s));
+    }
+    return RIOT_OK;
+}
+
+// Q = orth(Y), K, K = Z Lambda Z^T, U = Q Z.  with_eig = false stops before
+// the eigensolver (rsvd_eig / rsvd_ritz then finish the window).
+riot_status rsvd_eig(riot_ctx *ctx, int k)
+{
+    if (ctx->eig_method == RIOT_EIG_JACOBI)
+        CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, ctx->s));
+    else
+        CU(tridiag_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, ctx->s));
+    return RIOT_OK;
+}
+
+riot_status rsvd_ritz(riot_ctx *ctx, int k)
+{
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    if (ctx->prec == RIOT_PREC_MIXED) {
+        // U = Q Z in FP32 (Y block reused as scratch), then widened
+        float *Y32 = (float *)ctx->Yblk;
+        CU(convert_block(ctx->Z, 'd', k, ctx->M32, 'f', k, k, k, s));
+        CU(sgemm('N', 'N', n, k, k, 1.f, ctx->Q32, n, ctx->M32, k, 0.f, Y32, n, s));
+        CU(convert_block(Y32, 'f', n, ctx->U, 'd', n, n, k, s));
+    } else {
+        CU(gemm('N', 'N', n, k, k, 1.0, ctx->Q, 'd', n, ctx->Z, 'd', k, 0.0, ctx->U, 'd', n, s));
+    }
+    CU(fix_col_signs(ctx->U, n, k, n, s));
+    return RIOT_OK;
+}
+
+riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
+{
+    const int n = ctx->n;
+    const char tr = real_tag(ctx);
+    cudaStream_t s = ctx->s;
+    const bool mixed = (ctx->prec == RIOT_PREC_MIXED);
+    float *W32 = (float *)ctx->Wblk, *Y32 = (float *)ctx->Yblk;
+    ev_mark(ctx, 1);
+    if (mixed) TRY(orth32(ctx, Y32, k, 5, 3));
+    else TRY(orth(ctx, ctx->Yblk, k, 5));
+    ev_mark(ctx, 2);
+    if (ctx->exact_rr) {
+        // K = Q^T A Q
+        if (mixed) CU(cudaMemcpyAsync(W32, ctx->Q32, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
+        else CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
+        ev_mark(ctx, 0);
+        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
+        ev_mark(ctx, 2);
+        if (mixed) {
+            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, Y32, n, 0.f, ctx->N32, k, s));
+            CU(convert_block(ctx->N32, 'f', k, ctx->Km, 'd', k, k, k, s));
+        } else {
+            CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Km, 'd', k, s));
+        }
+    } else {
+        // K (Q^T W) = Q^T Y  <=>  K (M M^T) = N M^T with M = Q^T W, N = Q^T Y
+        if (mixed) {
+            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, W32, n, 0.f, ctx->M32, k, s));
+            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, Y32, n, 0.f, ctx->N32, k, s));
+            CU(convert_block(ctx->M32, 'f', k, ctx->Mm, 'd', k, k, k, s));
+            CU(convert_block(ctx->N32, 'f', k, ctx->Nm, 'd', k, k, k, s));
+        } else {
+            CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Wblk, tr, n, 0.0, ctx->Mm, 'd', k, s));
+            CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Nm, 'd', k, s));
+        }
+        CU(gemm('N', 'T', k, k, k, 1.0, ctx->Mm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->G, 'd', k, s));
+        CU(gemm('N', 'T', k, k, k, 1.0, ctx->Nm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->Km, 'd', k, s));
+        CU(cholesky(ctx->G, k, k, 0.0, ctx->info + 10, ctx->gws, s));
+        CU(trsm_right_lt(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
+        CU(trsm_right_l(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
+    }
+    CU(symmetrize(ctx->Km, k, k, s));
+    if (!with_eig) return RIOT_OK;
+    ev_mark(ctx, 3);
+    TRY(rsvd_eig(ctx, k));
+    ev_mark(ctx, 4);
+    return rsvd_ritz(ctx, k);
+}
+
+// Host-side checks of a finished riot_rsvd; synchronises ctx->s.
+riot_status rsvd_collect(riot_ctx *ctx, int k, double *lambda_out)
+{
+    cudaStream_t s = ctx->s;
+    TRY(check_cholesky(ctx, 0, 11, "riot_rsvd"));
+    int jinfo[2] = {0, 0};
+    CU(cudaMemcpyAsync(jinfo, ctx->info + 12, sizeof(jinfo), cudaMemcpyDeviceToHost, s));
+    if (lambda_out) CU(cudaMemcpyAsync(lambda_out, ctx->lam, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (ctx->eig_method == RIOT_EIG_JACOBI && jinfo[0] < 0)
+        return fail(ctx, RIOT_ENOCONV, "Jacobi did not converge in %d sweeps", -jinfo[0]);
+    if (ctx->eig_method == RIOT_EIG_TRIDIAG && (jinfo[0] != 0 || jinfo[1] != 0))
+        return fail(ctx, RIOT_ENOCONV, "orthonormalisation of the tridiagonal eigenvectors failed");
+    int eflag = 0;
+    CU(cudaMemcpyAsync(&eflag, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (eflag) return fail(ctx, RIOT_ETIMEOUT, "a bounded wait on a coefficient copy ran out in the Hessian kernel");
+    ctx->jacobi_sweeps = (ctx->eig_method == RIOT_EIG_JACOBI) ? jinfo[0] : 0;
+    ctx->have_rsvd = 1;
+    ctx->k_last = k;
+    return RIOT_OK;
+}
+
+// Adaptive increment (queued, no synchronisation): dv, v += dv, x += L dv.
+riot_status increment_queue(riot_ctx *ctx, int k)
+{
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    // c = U^T g; scale by the adaptive rule; dv = U c (- g for LRU)
+    CU(gemm('T', 'N', k, 1, n, 1.0, ctx->U, 'd', n, ctx->g, 'd', n, 0.0, ctx->cvec, 'd', k, s));
+    CU(increment_coef(ctx->lam, k, ctx->cvec, ctx->info + 14, s));
+    CU(gemm('N', 'N', n, 1, k, 1.0, ctx->U, 'd', n, ctx->cvec, 'd', k, 0.0, ctx->dv, 'd', n, s));
+    CU(add_if_flag(ctx->info + 14, 1, n, -1.0, ctx->g, ctx->dv, s));
+    CU(axpby(n, 1.0, ctx->dv, 1.0, ctx->v, s));
+    CU(bsqrt(ctx, ctx->dv, ctx->tmp, 0, 1));
+    CU(axpby(n, 1.0, ctx->tmp, 1.0, ctx->x, s));
+    return RIOT_OK;
+}
+
+riot_status bfail(riot_batch *b, riot_status st, const char *fmt, ...)
+{
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof(b->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+// Queue one inner loop (Algorithm 3: sketch, Y = A Omega, q power
+// iterations, Q, K, eigenpairs, Ritz vectors, increment) of every window of
+// the batch: per-window work on the window's branch stream, the Hessian
+// products of all windows in one persistent launch on the main stream, the
+// eigensolvers (cooperative, all SMs) one after another on the main stream.
+riot_status batch_enqueue(riot_batch *b, int64_t sketch_stream)
+{
+    const int nw = (int)b->ctx.size();
+    std::vector<cudaStream_t> saved(nw);
+    for (int w = 0; w < nw; ++w) {
+        saved[w] = b->ctx[w]->s;
+        b->ctx[w]->s = b->ws[w];
+        b->ctx[w]->nev = 32;   // no phase events inside a batch
+    }
+    riot_status st = RIOT_OK;
+    cudaError_t e = cudaSuccess;
+    auto fork = [&]() {
+        if ((e = cudaEventRecord(b->fork, b->main)) != cudaSuccess) return false;
+        for (int w = 0; w < nw; ++w)
+            if ((e = cudaStreamWaitEvent(b->ws[w], b->fork, 0)) != cudaSuccess) return false;
+        return true;
+    };
+    auto join = [&]() {
+        for (int w = 0; w < nw; ++w) {
+            if ((e = cudaEventRecord(b->join[w], b->ws[w])) != cudaSuccess) return false;
+            if ((e = cudaStreamWaitEvent(b->main, b->join[w], 0)) != cudaSuccess) return false;
+        }
+        return true;
+    };
+    do {
+        if (!fork()) break;
+        for (int w = 0; w < nw && st == RIOT_OK; ++w) st = rsvd_begin(b->ctx[w], b->k[w], sketch_stream, nullptr);
+        if (st != RIOT_OK || !join()) break;
+        if ((e = hvp_batch_launch(b->plan, b->main)) != cudaSuccess) break;
+        for (int it = 0; it < b->q && st == RIOT_OK && e == cudaSuccess; ++it) {
+            if (!fork()) break;
+            for (int w = 0; w < nw && st == RIOT_OK; ++w) st = rsvd_power(b->ctx[w], b->k[w]);
+            if (st != RIOT_OK || !join()) break;
+            e = hvp_batch_launch(b->plan, b->main);
+        }
+        if (st != RIOT_OK || e != cudaSuccess) break;
+        if (!fork()) break;
+        for (int w = 0; w < nw && st == RIOT_OK; ++w) st = rsvd_end(b->ctx[w], b->k[w], false);
+        if (st != RIOT_OK || !join()) break;
+        for (int w = 0; w < nw && st == RIOT_OK; ++w) {
+            b->ctx[w]->s = b->main;
+            st = rsvd_eig(b->ctx[w], b->k[w]);
+            b->ctx[w]->s = b->ws[w];
+        }
+        if (st != RIOT_OK || !fork()) break;
+        for (int w = 0; w < nw && st == RIOT_OK; ++w) {
+            st = rsvd_ritz(b->ctx[w], b->k[w]);
+            if (st == RIOT_OK) st = increment_queue(b->ctx[w], b->k[w]);
+        }
+        if (st != RIOT_OK) break;
+        join();
+    } while (0);
+    for (int w = 0; w < nw; ++w) b->ctx[w]->s = saved[w];
+    if (st != RIOT_OK) return bfail(b, st, "batch: %s", "a window's inner-loop step failed (see its context)");
+    if (e != cudaSuccess) return bfail(b, RIOT_ECUDA, "batch: %s", cudaGetErrorString(e));
+    return RIOT_OK;
+}
+
+void batch_drop_graph(riot_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_sketch = -1;
 }
 
 }  // namespace
@@ -759,106 +1024,22 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
                       double *lambda_out)
 {
     if (!ctx) return RIOT_EINVAL;
-    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_rsvd before riot_outer_begin");
-    const int n = ctx->n;
-    if (k < 1 || k > ctx->kmax || k > n) return fail(ctx, RIOT_EINVAL, "k = %d outside [1, min(kmax, n)]", k);
-    if (q < 0 || q > 64) return fail(ctx, RIOT_EINVAL, "q = %d outside [0, 64]", q);
+    TRY(rsvd_check_args(ctx, k, q));
     CU(cudaSetDevice(ctx->dev));
-    const char tr = real_tag(ctx);
-    const size_t rs = real_size(ctx);
-    cudaStream_t s = ctx->s;
     ctx->nev = 0;
-    CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 32, s));
     ev_mark(ctx, -1);
-    if (Omega_dev)
-        CU(cudaMemcpyAsync(ctx->Wblk, Omega_dev, (size_t)n * k * rs, cudaMemcpyDeviceToDevice, s));
-    else
-        CU(normal_launch(ctx->seed, (uint32_t)sketch_stream, n, k, n, ctx->prec == RIOT_PREC_FP64, ctx->Wblk, s));
+    TRY(rsvd_begin(ctx, k, sketch_stream, Omega_dev));
     ev_mark(ctx, 0);
-    TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
-    const bool mixed = (ctx->prec == RIOT_PREC_MIXED);
-    float *W32 = (float *)ctx->Wblk, *Y32 = (float *)ctx->Yblk;
+    TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, ctx->n, k, 0));
     for (int it = 0; it < q; ++it) {
         ev_mark(ctx, 1);
-        if (mixed) {
-            // a power-iteration basis only has to span the block well: shifted pass + one plain pass
-            TRY(orth32(ctx, Y32, k, 0, 2));
-            CU(cudaMemcpyAsync(W32, ctx->Q32, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
-        } else {
-            TRY(orth(ctx, ctx->Yblk, k, 0));
-            CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
-        }
+        TRY(rsvd_power(ctx, k));
         ev_mark(ctx, 0);
-        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
+        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, ctx->n, k, 0));
     }
-    ev_mark(ctx, 1);
-    if (mixed) TRY(orth32(ctx, Y32, k, 5, 3));
-    else TRY(orth(ctx, ctx->Yblk, k, 5));
-    ev_mark(ctx, 2);
-    if (ctx->exact_rr) {
-        // K = Q^T A Q
-        if (mixed) CU(cudaMemcpyAsync(W32, ctx->Q32, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
-        else CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
-        ev_mark(ctx, 0);
-        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
-        ev_mark(ctx, 2);
-        if (mixed) {
-            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, Y32, n, 0.f, ctx->N32, k, s));
-            CU(convert_block(ctx->N32, 'f', k, ctx->Km, 'd', k, k, k, s));
-        } else {
-            CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Km, 'd', k, s));
-        }
-    } else {
-        // K (Q^T W) = Q^T Y  <=>  K (M M^T) = N M^T with M = Q^T W, N = Q^T Y
-        if (mixed) {
-            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, W32, n, 0.f, ctx->M32, k, s));
-            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, Y32, n, 0.f, ctx->N32, k, s));
-            CU(convert_block(ctx->M32, 'f', k, ctx->Mm, 'd', k, k, k, s));
-            CU(convert_block(ctx->N32, 'f', k, ctx->Nm, 'd', k, k, k, s));
-        } else {
-            CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Wblk, tr, n, 0.0, ctx->Mm, 'd', k, s));
-            CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Nm, 'd', k, s));
-        }
-        CU(gemm('N', 'T', k, k, k, 1.0, ctx->Mm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->G, 'd', k, s));
-        CU(gemm('N', 'T', k, k, k, 1.0, ctx->Nm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->Km, 'd', k, s));
-        CU(cholesky(ctx->G, k, k, 0.0, ctx->info + 10, ctx->gws, s));
-        CU(trsm_right_lt(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
-        CU(trsm_right_l(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
-    }
-    CU(symmetrize(ctx->Km, k, k, s));
-    ev_mark(ctx, 3);
-    if (ctx->eig_method == RIOT_EIG_JACOBI)
-        CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
-    else
-        CU(tridiag_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
-    ev_mark(ctx, 4);
-    if (mixed) {
-        // U = Q Z in FP32 (Y block reused as scratch), then widened
-        CU(convert_block(ctx->Z, 'd', k, ctx->M32, 'f', k, k, k, s));
-        CU(sgemm('N', 'N', n, k, k, 1.f, ctx->Q32, n, ctx->M32, k, 0.f, Y32, n, s));
-        CU(convert_block(Y32, 'f', n, ctx->U, 'd', n, n, k, s));
-    } else {
-        CU(gemm('N', 'N', n, k, k, 1.0, ctx->Q, 'd', n, ctx->Z, 'd', k, 0.0, ctx->U, 'd', n, s));
-    }
-    CU(fix_col_signs(ctx->U, n, k, n, s));
+    TRY(rsvd_end(ctx, k, true));
     ev_mark(ctx, -2);
-    TRY(check_cholesky(ctx, 0, 11, "riot_rsvd"));
-    int jinfo[2] = {0, 0};
-    CU(cudaMemcpyAsync(jinfo, ctx->info + 12, sizeof(jinfo), cudaMemcpyDeviceToHost, s));
-    if (lambda_out) CU(cudaMemcpyAsync(lambda_out, ctx->lam, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (ctx->eig_method == RIOT_EIG_JACOBI && jinfo[0] < 0)
-        return fail(ctx, RIOT_ENOCONV, "Jacobi did not converge in %d sweeps", -jinfo[0]);
-    if (ctx->eig_method == RIOT_EIG_TRIDIAG && (jinfo[0] != 0 || jinfo[1] != 0))
-        return fail(ctx, RIOT_ENOCONV, "orthonormalisation of the tridiagonal eigenvectors failed");
-    int eflag = 0;
-    CU(cudaMemcpyAsync(&eflag, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (eflag) return fail(ctx, RIOT_ETIMEOUT, "a bounded wait on a coefficient copy ran out in the Hessian kernel");
-    ctx->jacobi_sweeps = (ctx->eig_method == RIOT_EIG_JACOBI) ? jinfo[0] : 0;
-    ctx->have_rsvd = 1;
-    ctx->k_last = k;
-    return RIOT_OK;
+    return rsvd_collect(ctx, k, lambda_out);
 }
 
 riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6)
@@ -897,21 +1078,11 @@ riot_status riot_increment(riot_ctx *ctx, double *dv_dev, int32_t *mode_out)
     if (!ctx) return RIOT_EINVAL;
     if (!ctx->have_rsvd) return fail(ctx, RIOT_ESTATE, "riot_increment before riot_rsvd");
     CU(cudaSetDevice(ctx->dev));
-    const int n = ctx->n, k = ctx->k_last;
-    cudaStream_t s = ctx->s;
-    // c = U^T g; scale by the adaptive rule; dv = U c (- g for LRU)
-    CU(gemm('T', 'N', k, 1, n, 1.0, ctx->U, 'd', n, ctx->g, 'd', n, 0.0, ctx->cvec, 'd', k, s));
-    CU(increment_coef(ctx->lam, k, ctx->cvec, ctx->info + 14, s));
-    CU(gemm('N', 'N', n, 1, k, 1.0, ctx->U, 'd', n, ctx->cvec, 'd', k, 0.0, ctx->dv, 'd', n, s));
-    CU(add_if_flag(ctx->info + 14, 1, n, -1.0, ctx->g, ctx->dv, s));
-    // v += dv, x += L dv
-    CU(axpby(n, 1.0, ctx->dv, 1.0, ctx->v, s));
-    CU(bsqrt(ctx, ctx->dv, ctx->tmp, 0, 1));
-    CU(axpby(n, 1.0, ctx->tmp, 1.0, ctx->x, s));
-    if (dv_dev) CU(cudaMemcpyAsync(dv_dev, ctx->dv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    TRY(increment_queue(ctx, ctx->k_last));
+    if (dv_dev) CU(cudaMemcpyAsync(dv_dev, ctx->dv, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s));
     if (mode_out) {
-        CU(cudaMemcpyAsync(mode_out, ctx->info + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
+        CU(cudaMemcpyAsync(mode_out, ctx->info + 14, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+        CU(cudaStreamSynchronize(ctx->s));
     }
     return RIOT_OK;
 }
@@ -1018,6 +1189,198 @@ riot_status riot_l96_forecast(int64_t n, int32_t T, double dt, double F, const d
     cudaError_t e = l96_nl_launch(m, x0_dev, store_all ? traj_dev : nullptr, nullptr, nullptr, nullptr, nullptr,
                                   store_all ? nullptr : traj_dev, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? RIOT_OK : RIOT_ECUDA;
+}
+
+riot_status riot_batch_create(riot_batch **out, riot_ctx *const *ctxs, int32_t nwin, const int32_t *k, int32_t q,
+                              void *cuda_stream)
+{
+    if (!out) return RIOT_EINVAL;
+    *out = nullptr;
+    if (!ctxs || !k || nwin < 1 || nwin > 4096 || q < 0 || q > 64) return RIOT_EINVAL;
+    riot_batch *b = new riot_batch();
+    cudaGetDevice(&b->dev);
+    b->s = (cudaStream_t)cuda_stream;
+    b->q = q;
+    auto bail = [&](riot_status st) {
+        fprintf(stderr, "riot_batch_create: %s\n", b->err);
+        riot_batch_destroy(b);
+        return st;
+    };
+    for (int w = 0; w < nwin; ++w) {
+        riot_ctx *c = ctxs[w];
+        if (!c) return bail(bfail(b, RIOT_EINVAL, "window %d: null context", w));
+        if (c->model != RIOT_MODEL_L96 || c->prec != RIOT_PREC_MIXED || c->dev != b->dev)
+            return bail(bfail(b, RIOT_EINVAL, "window %d: batches take mixed-precision Lorenz-96 contexts on one device", w));
+        if (k[w] < 1 || k[w] > c->kmax || k[w] > c->n)
+            return bail(bfail(b, RIOT_EINVAL, "window %d: k = %d outside [1, min(kmax, n)]", w, k[w]));
+        if (c->m.geom.Tp > 512) return bail(bfail(b, RIOT_EINVAL, "window %d: n too large for the batch kernel", w));
+        for (int v = 0; v < w; ++v)
+            if (ctxs[v] == c) return bail(bfail(b, RIOT_EINVAL, "window %d repeats window %d", w, v));
+        b->ctx.push_back(c);
+        b->k.push_back(k[w]);
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(bfail(b, RIOT_ECUDA, "cudaStreamCreate failed"));
+        b->ws.push_back(st);
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return bail(bfail(b, RIOT_ECUDA, "cudaEventCreate failed"));
+        b->join.push_back(ev);
+        riot::HvpBatchWindow hw;
+        hw.m = &c->m;
+        hw.coef = c->coef32;
+        hw.W = (const float *)c->Wblk;
+        hw.Y = (float *)c->Yblk;
+        hw.ld = c->n;
+        hw.ncols = k[w];
+        hw.r = (float *)c->rscr;
+        hw.err = c->errflag;
+        b->wins.push_back(hw);
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(bfail(b, RIOT_ECUDA, "cudaEventCreate / cudaStreamCreate failed"));
+    cudaError_t e = hvp_batch_plan(b->wins.data(), nwin, 0, 0, &b->plan);
+    if (e != cudaSuccess) return bail(bfail(b, RIOT_ECUDA, "batch plan failed: %s", cudaGetErrorString(e)));
+    *out = b;
+    return RIOT_OK;
+}
+
+riot_status riot_batch_set_config(riot_batch *b, int32_t probes_cap, int32_t ring_depth)
+{
+    if (!b) return RIOT_EINVAL;
+    if (probes_cap < 0 || probes_cap > 64 || ring_depth < 0 || ring_depth > 8 || ring_depth == 1)
+        return bfail(b, RIOT_EINVAL, "probes_cap in [0, 64], ring_depth 0 or in [2, 8]");
+    CU_B(cudaSetDevice(b->dev));
+    CU_B(cudaStreamSynchronize(b->s));
+    CU_B(cudaStreamSynchronize(b->main));
+    batch_drop_graph(b);
+    CU_B(hvp_batch_plan(b->wins.data(), (int)b->wins.size(), probes_cap, ring_depth, &b->plan));
+    return RIOT_OK;
+}
+
+riot_status riot_batch_hessian_apply(riot_batch *b)
+{
+    if (!b) return RIOT_EINVAL;
+    for (size_t w = 0; w < b->ctx.size(); ++w)
+        if (!b->ctx[w]->have_traj) return bfail(b, RIOT_ESTATE, "window %zu: no riot_outer_begin yet", w);
+    CU_B(cudaSetDevice(b->dev));
+    CU_B(hvp_batch_launch(b->plan, b->s));
+    return RIOT_OK;
+}
+
+riot_status riot_batch_autotune(riot_batch *b, int32_t *probes_cap_out, int32_t *ring_depth_out, double *ms_out)
+{
+    if (!b) return RIOT_EINVAL;
+    for (size_t w = 0; w < b->ctx.size(); ++w)
+        if (!b->ctx[w]->have_traj) return bfail(b, RIOT_ESTATE, "window %zu: no riot_outer_begin yet", w);
+    CU_B(cudaSetDevice(b->dev));
+    // sketches in every W block, so that the timed products see real data
+    for (size_t w = 0; w < b->ctx.size(); ++w) {
+        riot_ctx *c = b->ctx[w];
+        CU_B(normal_launch(c->seed, 1u, c->n, b->k[w], c->n, 0, c->Wblk, b->s));
+    }
+    const int caps[] = {0, 32, 16, 8, 4, 2};
+    const int depths[] = {4, 3, 2};
+    cudaEvent_t e0, e1;
+    CU_B(cudaEventCreate(&e0));
+    CU_B(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bestP = 0, bestS = 0;
+    for (int P : caps)
+        for (int S : depths) {
+            if (hvp_batch_plan(b->wins.data(), (int)b->wins.size(), P, S, &b->plan) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            CU_B(hvp_batch_launch(b->plan, b->s));
+            CU_B(cudaEventRecord(e0, b->s));
+            for (int r = 0; r < 2; ++r) CU_B(hvp_batch_launch(b->plan, b->s));
+            CU_B(cudaEventRecord(e1, b->s));
+            CU_B(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CU_B(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms / 2 < best) {
+                best = ms / 2;
+                bestP = P;
+                bestS = S;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    batch_drop_graph(b);
+    CU_B(hvp_batch_plan(b->wins.data(), (int)b->wins.size(), bestP, bestS, &b->plan));
+    if (probes_cap_out) *probes_cap_out = bestP;
+    if (ring_depth_out) *ring_depth_out = bestS;
+    if (ms_out) *ms_out = best;
+    return RIOT_OK;
+}
+
+riot_status riot_batch_run(riot_batch *b, int64_t sketch_stream, int32_t use_graph, int32_t *status_out)
+{
+    if (!b) return RIOT_EINVAL;
+    const int nw = (int)b->ctx.size();
+    for (int w = 0; w < nw; ++w)
+        if (!b->ctx[w]->have_traj) return bfail(b, RIOT_ESTATE, "window %d: no riot_outer_begin yet", w);
+    CU_B(cudaSetDevice(b->dev));
+    // the batch's stream follows the caller's work, and the caller's follows the batch
+    CU_B(cudaEventRecord(b->done, b->s));
+    CU_B(cudaStreamWaitEvent(b->main, b->done, 0));
+    if (use_graph) {
+        if (!b->exec || b->graph_sketch != sketch_stream) {
+            batch_drop_graph(b);
+            CU_B(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed));
+            riot_status st = batch_enqueue(b, sketch_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(b->main, &g);
+            if (st != RIOT_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (ce != cudaSuccess) return bfail(b, RIOT_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+            b->graph = g;
+            ce = cudaGraphInstantiate(&b->exec, g, 0);
+            if (ce != cudaSuccess) {
+                batch_drop_graph(b);
+                return bfail(b, RIOT_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+            }
+            b->graph_sketch = sketch_stream;
+        }
+        CU_B(cudaGraphLaunch(b->exec, b->main));
+    } else {
+        riot_status st = batch_enqueue(b, sketch_stream);
+        if (st != RIOT_OK) return st;
+    }
+    CU_B(cudaEventRecord(b->done, b->main));
+    CU_B(cudaStreamWaitEvent(b->s, b->done, 0));
+    CU_B(cudaStreamSynchronize(b->main));
+    riot_status first = RIOT_OK;
+    for (int w = 0; w < nw; ++w) {
+        riot_status st = rsvd_collect(b->ctx[w], b->k[w], nullptr);
+        if (status_out) status_out[w] = st;
+        if (st != RIOT_OK && first == RIOT_OK) {
+            first = st;
+            bfail(b, st, "window %d: %s", w, b->ctx[w]->err);
+        }
+    }
+    return first;
+}
+
+const char *riot_batch_last_error(const riot_batch *b) { return b ? b->err : "no batch"; }
+
+void riot_batch_destroy(riot_batch *b)
+{
+    if (!b) return;
+    if (b->main) cudaStreamSynchronize(b->main);
+    batch_drop_graph(b);
+    if (b->main) cudaStreamDestroy(b->main);
+    if (b->done) cudaEventDestroy(b->done);
+    hvp_batch_free(&b->plan);
+    for (cudaStream_t st : b->ws) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
 }
 
 }  // extern "C"

@@ -93,6 +93,30 @@ cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float 
                                int ncols, int add_identity, float *r, int mode, int *err, cudaStream_t s,
                                int P_hint = 0, int S_hint = 0);
 
+// Several Lorenz-96 windows' FP32 Hessian products (Y = A W) in one
+// persistent launch over a queue of (window, CTA block) items.
+struct HvpBatchWindow {
+    const L96Dev *m;
+    const float2 *coef;
+    const float *W;
+    float *Y;
+    int64_t ld;
+    int ncols;
+    float *r;
+    int *err;
+};
+struct HvpBatchPlan {
+    int nwin = 0, nitems = 0, grid = 0, nthr = 0, P_cap = 0, S = 0;
+    size_t smem = 0;
+    void *d_args = nullptr, *d_items = nullptr;
+    int *d_counter = nullptr;
+};
+// P_cap caps the probe groups per CTA (0: as many as fit), S the ring depth
+// (0: 4, lowered per window to fit shared memory).  Allocates device tables.
+cudaError_t hvp_batch_plan(const HvpBatchWindow *w, int nwin, int P_cap, int S, HvpBatchPlan *plan);
+cudaError_t hvp_batch_launch(const HvpBatchPlan &plan, cudaStream_t s);
+void hvp_batch_free(HvpBatchPlan *plan);
+
 // out = L in or L^T in (FP64), ncols columns (ld = n)
 cudaError_t bsqrt_launch(const L96Dev &m, const double *in, double *out, int transpose, int ncols,
                          cudaStream_t s);

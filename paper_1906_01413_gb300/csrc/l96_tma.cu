@@ -18,6 +18,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "internal.h"
 
 namespace riot {
@@ -35,6 +38,11 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 }
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_inval(uint32_t bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -267,12 +275,13 @@ __device__ __forceinline__ void band_apply_t(const float *st, const float *band,
 }
 
 // A CTA holds P thread groups of Tp threads; group g owns probes
-// blockIdx.x * P * PR + g * PR + r, r < PR, and thread t of a group keeps
-// chunk t of each of them in registers.
-template <int E, int PR, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
+// blk * P * PR + g * PR + r, r < PR, and thread t of a group keeps chunk t of
+// each of them in registers.  Threads from P * Tp up to blockDim.x (a
+// persistent batch kernel runs windows of several sizes in one block shape)
+// are idle: they follow the barriers and touch only their own halo slots.
+template <int E, int PR>
+__device__ __forceinline__ void hvp_tma_body(const TmaArgs &a, int blk, unsigned char *smem_raw, int *abort_flag)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     const ChunkGeom &G = a.geom;
     const int Np = G.Np, n = G.n, Tp = G.Tp, P = a.P, S = a.S;
     const int nthr = blockDim.x;
@@ -283,8 +292,9 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
     const int SP = stage_pad_t(Np);
 
     const int tid = threadIdx.x;
-    const int t = tid / P, g = tid - t * P;
-    const int probe0 = (blockIdx.x * P + g) * PR;
+    const bool live = tid < P * Tp;
+    const int t = live ? tid / P : 0, g = live ? tid - (tid / P) * P : 0;
+    const int probe0 = (blk * P + g) * PR;
     const int left = ((t == 0) ? Tp - 1 : t - 1) * P + g;
     const int right = ((t == Tp - 1) ? 0 : t + 1) * P + g;
     const int s0 = G.start(t);
@@ -306,10 +316,8 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
     ring.coef = a.coef;
     ring.c0 = (a.mode == 1) ? 4 * a.T : 0;
     ring.total = ((a.mode == 2) ? 4 * a.T : 8 * a.T) - ring.c0;
-    __shared__ int abort_flag;
-    ring.abort_flag = &abort_flag;
+    ring.abort_flag = abort_flag;
     if (tid == 0) {
-        abort_flag = 0;
         for (int i = 0; i < S; ++i) mbar_init(ring.bar0 + 8u * i, 1);
         fence_mbar_init();
     }
@@ -327,7 +335,8 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
             const bool active = probe < a.ncols;
             float *st = state + (g * PR + r) * SP;
             const float *w = a.W + (size_t)(active ? probe : 0) * a.ld;
-            for (int i = t; i < n; i += Tp) st[swz(i)] = active ? w[i] : 0.f;
+            if (live)
+                for (int i = t; i < n; i += Tp) st[swz(i)] = active ? w[i] : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -341,17 +350,18 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
         for (int tt = 0;; ++tt) {
             const int o0 = a.optr[tt], o1 = a.optr[tt + 1];
             if (o0 < o1) {
+                if (live)
 #pragma unroll
-                for (int r = 0; r < PR; ++r) {
-                    float *st = state + (g * PR + r) * SP;
+                    for (int r = 0; r < PR; ++r) {
+                        float *st = state + (g * PR + r) * SP;
 #pragma unroll
-                    for (int j = 0; j < E; ++j) st[swz(tE + j)] = dx[r][j];
-                }
+                        for (int j = 0; j < E; ++j) st[swz(tE + j)] = dx[r][j];
+                    }
                 __syncthreads();
 #pragma unroll
                 for (int r = 0; r < PR; ++r) {
                     const int probe = probe0 + r;
-                    if (probe < a.ncols) {
+                    if (live && probe < a.ncols) {
                         const float *st = state + (g * PR + r) * SP;
                         float *rr = a.r + (size_t)probe * (size_t)a.p;
                         for (int o = o0 + t; o < o1; o += Tp) rr[o] = a.rinv[o] * st[swz(a.oslot[o])];
@@ -392,6 +402,9 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
         }
         if (a.mode == 2) {
             ring.drain(c, a.err);
+            __syncthreads();
+            if (tid == 0)
+                for (int i = 0; i < S; ++i) mbar_inval(ring.bar0 + 8u * i);
             return;
         }
         __syncthreads();   // last tangent-linear stage read before the adjoint refills its buffer
@@ -405,17 +418,18 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
     for (int tt = a.T;; --tt) {
         const int o0 = a.optr[tt], o1 = a.optr[tt + 1];
         if (o0 < o1) {
+            if (live)
 #pragma unroll
-            for (int r = 0; r < PR; ++r) {
-                float *st = state + (g * PR + r) * SP;
+                for (int r = 0; r < PR; ++r) {
+                    float *st = state + (g * PR + r) * SP;
 #pragma unroll
-                for (int j = 0; j < E; ++j) st[swz(tE + j)] = lam[r][j];
-            }
+                    for (int j = 0; j < E; ++j) st[swz(tE + j)] = lam[r][j];
+                }
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < PR; ++r) {
                 const int probe = probe0 + r;
-                if (probe < a.ncols) {
+                if (live && probe < a.ncols) {
                     float *st = state + (g * PR + r) * SP;
                     const float *rr = a.r + (size_t)probe * (size_t)a.p;
                     for (int o = o0 + t; o < o1; o += Tp) atomicAdd(&st[swz(a.oslot[o])], rr[o]);
@@ -463,20 +477,23 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
 
     ring.drain(c, a.err);
     __syncthreads();
+    if (tid == 0)
+        for (int i = 0; i < S; ++i) mbar_inval(ring.bar0 + 8u * i);
+    if (live)
 #pragma unroll
-    for (int r = 0; r < PR; ++r) {
-        float *st = state + (g * PR + r) * SP;
+        for (int r = 0; r < PR; ++r) {
+            float *st = state + (g * PR + r) * SP;
 #pragma unroll
-        for (int j = 0; j < E; ++j)
-            if (j < len) st[swz(s0 + j)] = a.sig[s0 + j] * lam[r][j];
-    }
+            for (int j = 0; j < E; ++j)
+                if (j < len) st[swz(s0 + j)] = a.sig[s0 + j] * lam[r][j];
+        }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < PR; ++r) {
         const int probe = probe0 + r;
         float y[E];
         band_apply_t<E>(state + (g * PR + r) * SP, a.band, a.hl, a.hh, n, s0, len, y);
-        if (probe < a.ncols) {
+        if (live && probe < a.ncols) {
             float *yo = a.Y + (size_t)probe * a.ld;
             const float *w = a.W ? a.W + (size_t)probe * a.ld : nullptr;
 #pragma unroll
@@ -485,6 +502,44 @@ __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
         }
     }
 }
+
+template <int E, int PR, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) abort_flag = 0;
+    hvp_tma_body<E, PR>(a, blockIdx.x, smem_raw, &abort_flag);
+}
+
+// Persistent kernel over a queue of (window, block) items of several
+// Lorenz-96 windows: each CTA takes the next item until the queue is empty,
+// so windows of different sizes share one launch.
+struct BatchItem {
+    int win, blk;
+};
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) l96_hvp_batch_kernel(const TmaArgs *args, const BatchItem *items, int nitems,
+                                                                int *counter)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int abort_flag, item_s;
+    if (threadIdx.x == 0) abort_flag = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = item_s;
+        if (it >= nitems) break;
+        const BatchItem bi = items[it];
+        const TmaArgs a = args[bi.win];
+        if (a.geom.E == 4) hvp_tma_body<4, 2>(a, bi.blk, smem_raw, &abort_flag);
+        else if (a.geom.E == 8) hvp_tma_body<8, 2>(a, bi.blk, smem_raw, &abort_flag);
+        else hvp_tma_body<16, 1>(a, bi.blk, smem_raw, &abort_flag);
+    }
+}
+
 
 // Shared memory: barriers, S stage buffers, halo (2 buffers x 3 x PR x nthr),
 // state copies of the P * PR probes.
@@ -581,6 +636,118 @@ cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float 
     case 16: return launch_tma<16, 1, 512>(a, grid, nthr, sm, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batch of windows in one persistent launch
+// ---------------------------------------------------------------------------
+void hvp_batch_free(HvpBatchPlan *plan)
+{
+    if (!plan) return;
+    cudaFree(plan->d_args);
+    cudaFree(plan->d_items);
+    cudaFree(plan->d_counter);
+    plan->d_args = plan->d_items = nullptr;
+    plan->d_counter = nullptr;
+    plan->nitems = plan->nwin = 0;
+}
+
+cudaError_t hvp_batch_plan(const HvpBatchWindow *w, int nwin, int P_cap, int S_req, HvpBatchPlan *plan)
+{
+    constexpr int kThreads = 512;
+    int dev = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t smax = (size_t)smem_optin - 1024;
+    std::vector<TmaArgs> args(nwin);
+    struct Cand {
+        double cost;
+        BatchItem it;
+    };
+    std::vector<Cand> items;
+    size_t smem = 0;
+    for (int i = 0; i < nwin; ++i) {
+        const L96Dev &m = *w[i].m;
+        const ChunkGeom &g = m.geom;
+        const int PR = (g.E <= 8) ? 2 : 1;
+        if (g.Tp > kThreads || w[i].ncols < 1) return cudaErrorInvalidConfiguration;
+        int P = kThreads / g.Tp;
+        if (P > 64) P = 64;
+        if (P_cap > 0 && P > P_cap) P = P_cap;
+        const int groups = (w[i].ncols + PR - 1) / PR;
+        if (P > groups) P = groups;
+        int S = (S_req >= 2 && S_req <= 8) ? S_req : 4;
+        while (S > 2 && tma_smem_bytes(g.Np, kThreads, P, S, PR) > smax) --S;
+        while (P > 1 && tma_smem_bytes(g.Np, kThreads, P, S, PR) > smax) --P;
+        const size_t sm = tma_smem_bytes(g.Np, kThreads, P, S, PR);
+        if (sm > smax) return cudaErrorInvalidConfiguration;
+        if (sm > smem) smem = sm;
+        TmaArgs &a = args[i];
+        a.geom = g;
+        a.T = m.T;
+        a.P = P;
+        a.S = S;
+        a.p = m.p;
+        a.hl = m.band.hl;
+        a.hh = m.band.hh;
+        a.ncols = w[i].ncols;
+        a.add_identity = 0;
+        a.mode = 0;
+        a.dt = (float)m.dt;
+        a.coef = w[i].coef;
+        a.optr = m.optr;
+        a.oslot = m.oslot;
+        a.rinv = m.rinv32;
+        a.band = m.band32;
+        a.sig = m.sig32;
+        a.W = w[i].W;
+        a.Y = w[i].Y;
+        a.r = w[i].r;
+        a.ld = w[i].ld;
+        a.err = w[i].err;
+        const int nblk = (w[i].ncols + P * PR - 1) / (P * PR);
+        // per-thread work of an item grows with T * E * PR: longest first
+        const double cost = (double)m.T * g.E * PR;
+        for (int b = 0; b < nblk; ++b) items.push_back({cost, {i, b}});
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Cand &x, const Cand &y) { return x.cost > y.cost; });
+    std::vector<BatchItem> its(items.size());
+    for (size_t i = 0; i < items.size(); ++i) its[i] = items[i].it;
+    hvp_batch_free(plan);
+    cudaError_t e;
+    if ((e = cudaMalloc(&plan->d_args, sizeof(TmaArgs) * nwin)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&plan->d_items, sizeof(BatchItem) * its.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&plan->d_counter, sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(plan->d_args, args.data(), sizeof(TmaArgs) * nwin, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpy(plan->d_items, its.data(), sizeof(BatchItem) * its.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return e;
+    // a copy from pageable memory may still be in flight when cudaMemcpy returns, and the batch
+    // kernel runs on streams that do not wait for the legacy stream: finish it here
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(l96_hvp_batch_kernel<kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    plan->nwin = nwin;
+    plan->nitems = (int)its.size();
+    plan->nthr = kThreads;
+    plan->smem = smem;
+    plan->grid = plan->nitems < num_sms() ? plan->nitems : num_sms();
+    plan->P_cap = P_cap;
+    plan->S = S_req;
+    return cudaSuccess;
+}
+
+cudaError_t hvp_batch_launch(const HvpBatchPlan &plan, cudaStream_t s)
+{
+    if (plan.nitems == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(plan.d_counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    l96_hvp_batch_kernel<512><<<plan.grid, plan.nthr, plan.smem, s>>>(
+        (const TmaArgs *)plan.d_args, (const BatchItem *)plan.d_items, plan.nitems, plan.d_counter);
+    return cudaGetLastError();
 }
 
 }  // namespace riot

@@ -100,10 +100,21 @@ def load():
     L.riot_kernel_launches.restype = c_uint64
     L.riot_destroy.argtypes = [vp]
     L.riot_destroy.restype = None
+    L.riot_batch_create.argtypes = [POINTER(vp), POINTER(vp), c_int32, POINTER(c_int32), c_int32, vp]
+    L.riot_batch_autotune.argtypes = [vp, POINTER(c_int32), POINTER(c_int32), POINTER(c_double)]
+    L.riot_batch_set_config.argtypes = [vp, c_int32, c_int32]
+    L.riot_batch_hessian_apply.argtypes = [vp]
+    L.riot_batch_run.argtypes = [vp, c_int64, c_int32, POINTER(c_int32)]
+    L.riot_batch_last_error.argtypes = [vp]
+    L.riot_batch_last_error.restype = c_char_p
+    L.riot_batch_destroy.argtypes = [vp]
+    L.riot_batch_destroy.restype = None
     for name in ("riot_setup", "riot_outer_begin", "riot_hessian_apply", "riot_hessian_apply_noalloc",
                  "riot_rsvd", "riot_increment",
                  "riot_analysis_cov_lowrank", "riot_bsqrt_apply", "riot_get_state", "riot_draw_normal",
-                 "riot_l96_forecast", "riot_rsvd_timings", "riot_symm_eig", "riot_get_innovation"):
+                 "riot_l96_forecast", "riot_rsvd_timings", "riot_symm_eig", "riot_get_innovation",
+                 "riot_batch_create", "riot_batch_autotune", "riot_batch_set_config", "riot_batch_hessian_apply",
+                 "riot_batch_run"):
         getattr(L, name).restype = c_int32
     _lib = L
     return L
@@ -279,6 +290,49 @@ def riot_kernel_launches():
 def riot_destroy(ctx):
     if ctx:
         load().riot_destroy(ctx)
+
+
+def _bcheck(b, fn, status):
+    if status != RIOT_OK:
+        msg = load().riot_batch_last_error(b).decode() if b else load().riot_status_string(status).decode()
+        raise RiotError(fn, status, msg)
+
+
+def riot_batch_create(ctxs, k, q, stream=None):
+    """Batch of contexts (handles), k per window; returns the batch handle."""
+    n = len(ctxs)
+    arr = (c_void_p * n)(*[c.value if isinstance(c, c_void_p) else c for c in ctxs])
+    ks = (c_int32 * n)(*[int(x) for x in k])
+    h = c_void_p()
+    _bcheck(None, "riot_batch_create", load().riot_batch_create(ctypes.byref(h), arr, n, ks, int(q),
+                                                                 _stream_handle(stream)))
+    return h
+
+
+def riot_batch_autotune(b):
+    P, S, ms = c_int32(0), c_int32(0), c_double(0.0)
+    _bcheck(b, "riot_batch_autotune", load().riot_batch_autotune(b, ctypes.byref(P), ctypes.byref(S), ctypes.byref(ms)))
+    return P.value, S.value, ms.value
+
+
+def riot_batch_set_config(b, probes_cap=0, ring_depth=0):
+    _bcheck(b, "riot_batch_set_config", load().riot_batch_set_config(b, int(probes_cap), int(ring_depth)))
+
+
+def riot_batch_hessian_apply(b):
+    _bcheck(b, "riot_batch_hessian_apply", load().riot_batch_hessian_apply(b))
+
+
+def riot_batch_run(b, nwin, sketch_stream=0, use_graph=True):
+    st = (c_int32 * nwin)()
+    status = load().riot_batch_run(b, int(sketch_stream), int(bool(use_graph)), st)
+    _bcheck(b, "riot_batch_run", status)
+    return list(st)
+
+
+def riot_batch_destroy(b):
+    if b:
+        load().riot_batch_destroy(b)
 
 
 class Context:

@@ -101,3 +101,29 @@ def l96_custom(name, n, T, obs_every, obs_frac, ell, k, q, F=8.0, outer=1,
     return L96Config(name=name, n=n, F=F, T=T, obs_every=obs_every, obs_frac=obs_frac,
                      obs_layout=obs_layout, ell=ell, k=k, q=q, outer=outer,
                      spinup=spinup, seed=seed)
+
+
+STREAM_BATCH = 10
+
+
+def batch_windows(nwin=96, seed=BASE_SEED, n_max=8192):
+    """Independent Lorenz-96 windows of uneven size for batched inner loops:
+    n log-uniform in [40, n_max], F uniform in [8, 16], T uniform in
+    {50, ..., 300}, k drawn from {16, 64, 128, 256, 512} and clipped to n,
+    observation density uniform in [0.1, 0.5] at fixed random indices every 4
+    steps, Gaussian B (sigma_b = 1, length 4), q = 1.  Window w draws its own
+    truth, observations and background from seed + 1000 + w."""
+    u = philox.uniforms(seed, STREAM_BATCH, 5 * nwin).reshape(nwin, 5)
+    ks = np.array([16, 64, 128, 256, 512])
+    out = []
+    for w in range(nwin):
+        n = int(round(np.exp(np.log(40.0) + u[w, 0] * (np.log(n_max) - np.log(40.0)))))
+        n = min(max(n, 40), n_max)
+        F = 8.0 + 8.0 * u[w, 1]
+        T = 50 + int(u[w, 2] * 251)
+        k = int(min(ks[min(int(u[w, 3] * 5), 4)], n))
+        frac = 0.1 + 0.4 * u[w, 4]
+        out.append(L96Config(name="batch_w%02d_n%d_T%d_k%d" % (w, n, T, k), n=n, F=F, T=min(T, 300), obs_every=4,
+                             obs_frac=frac, obs_layout="random", ell=4.0, k=k, q=1, outer=1,
+                             seed=seed + 1000 + w))
+    return out

@@ -1,0 +1,137 @@
+"""Batches of Lorenz-96 windows: one persistent Hessian launch per application,
+the inner loops of all windows captured as one CUDA graph.
+
+Every window of a batch must end exactly where the same window ends when run
+alone through riot_rsvd + riot_increment: the batch kernel runs the same
+per-column arithmetic (only the grouping of columns into CTAs differs) and
+the rest of the inner loop is the same code, so eigenvalues, increments and
+updated states are compared to 1e-12 (FP64 quantities built from identical
+FP32 Hessian blocks).
+"""
+import numpy as np
+import pytest
+
+from synth import configs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+def _windows():
+    # uneven sizes: every chunk width (E = 4, 8, 16), ragged chunks, k from 8 to n
+    spec = [(40, 30, 40), (100, 21, 16), (333, 17, 64), (1000, 12, 128), (4096, 6, 64), (5001, 5, 32),
+            (8192, 4, 48), (61, 9, 8)]
+    out = []
+    for i, (n, T, k) in enumerate(spec):
+        out.append(configs.L96Config(name="bw%d" % i, n=n, F=8.0 + i, T=T, obs_every=2, obs_frac=0.3,
+                                     obs_layout="random", ell=4.0, k=k, q=1, spinup=200,
+                                     seed=configs.BASE_SEED + 500 + i))
+    return out
+
+
+def _make(R, cfgs):
+    from paper_1906_01413_gb300 import workloads
+    ctxs, xbs = [], []
+    for c in cfgs:
+        ctx, xb, _ = workloads.l96_twin(R, torch, c, DEV, R.RIOT_PREC_MIXED, c.k)
+        R.riot_outer_begin(ctx.h, xb)
+        ctxs.append(ctx)
+        xbs.append(xb)
+    return ctxs, xbs
+
+
+def _state(R, ctx, n, k):
+    lam = torch.empty(k, dtype=torch.float64, device=DEV)
+    x = torch.empty(n, dtype=torch.float64, device=DEV)
+    v = torch.empty(n, dtype=torch.float64, device=DEV)
+    R.riot_get_state(ctx.h, x=x, v=v, lam=lam)
+    return lam.cpu().numpy(), x.cpu().numpy(), v.cpu().numpy()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_windows_run_alone(gpu_lib, use_graph):
+    R = gpu_lib
+    cfgs = _windows()
+    q = 1
+    # alone
+    ctxs, _ = _make(R, cfgs)
+    alone = []
+    for c, ctx in zip(cfgs, ctxs):
+        R.riot_rsvd(ctx.h, c.k, q, sketch_stream=configs.STREAM_SKETCH0)
+        R.riot_increment(ctx.h)
+        alone.append(_state(R, ctx, c.n, c.k))
+    for ctx in ctxs:
+        ctx.close()
+    # batched
+    ctxs, _ = _make(R, cfgs)
+    b = R.riot_batch_create([ctx.h for ctx in ctxs], [c.k for c in cfgs], q)
+    st = R.riot_batch_run(b, len(cfgs), sketch_stream=configs.STREAM_SKETCH0, use_graph=use_graph)
+    assert st == [0] * len(cfgs)
+    for i, (c, ctx) in enumerate(zip(cfgs, ctxs)):
+        lam, x, v = _state(R, ctx, c.n, c.k)
+        np.testing.assert_allclose(lam, alone[i][0], rtol=1e-12, err_msg=c.name)
+        np.testing.assert_allclose(x, alone[i][1], rtol=1e-12, atol=1e-12, err_msg=c.name)
+        np.testing.assert_allclose(v, alone[i][2], rtol=1e-12, atol=1e-12, err_msg=c.name)
+    R.riot_batch_destroy(b)
+    for ctx in ctxs:
+        ctx.close()
+
+
+def test_graph_replays_follow_new_outer_loops(gpu_lib):
+    """After riot_outer_begin at the updated states, a replay of the captured
+    graph runs the next inner loop: it must equal a fresh eager run."""
+    R = gpu_lib
+    cfgs = _windows()[:5]
+    q = 1
+    runs = {}
+    for mode in ("graph", "eager"):
+        ctxs, _ = _make(R, cfgs)
+        b = R.riot_batch_create([ctx.h for ctx in ctxs], [c.k for c in cfgs], q)
+        for outer in range(2):
+            if outer:
+                for ctx in ctxs:
+                    R.riot_outer_begin(ctx.h)
+            R.riot_batch_run(b, len(cfgs), sketch_stream=configs.STREAM_SKETCH0, use_graph=(mode == "graph"))
+        runs[mode] = [_state(R, ctx, c.n, c.k) for c, ctx in zip(cfgs, ctxs)]
+        R.riot_batch_destroy(b)
+        for ctx in ctxs:
+            ctx.close()
+    for a, e in zip(runs["graph"], runs["eager"]):
+        for u, w in zip(a, e):
+            np.testing.assert_allclose(u, w, rtol=1e-12, atol=1e-12)
+
+
+def test_autotuned_shape_gives_the_same_products(gpu_lib):
+    R = gpu_lib
+    cfgs = _windows()
+    ctxs, _ = _make(R, cfgs)
+    b = R.riot_batch_create([ctx.h for ctx in ctxs], [c.k for c in cfgs], 0)
+    P, S, ms = R.riot_batch_autotune(b)
+    assert P in (0, 32, 16, 8, 4, 2) and S in (2, 3, 4) and ms > 0
+    outs = []
+    for cfg_ in ((P, S), (1, 2), (0, 4)):
+        R.riot_batch_set_config(b, *cfg_)
+        st = R.riot_batch_run(b, len(cfgs), sketch_stream=7, use_graph=False)
+        assert st == [0] * len(cfgs)
+        # the eigenpairs depend on the stored trajectory only, not on the updated x, v
+        outs.append([_state(R, ctx, c.n, c.k)[0] for c, ctx in zip(cfgs, ctxs)])
+    for o in outs[1:]:
+        for a, e in zip(o, outs[0]):
+            np.testing.assert_array_equal(a, e)
+    R.riot_batch_destroy(b)
+    for ctx in ctxs:
+        ctx.close()
+
+
+def test_batch_rejects_bad_windows(gpu_lib):
+    R = gpu_lib
+    cfgs = _windows()[:2]
+    ctxs, _ = _make(R, cfgs)
+    with pytest.raises(R.RiotError):
+        R.riot_batch_create([ctxs[0].h, ctxs[0].h], [8, 8], 1)          # same context twice
+    with pytest.raises(R.RiotError):
+        R.riot_batch_create([ctxs[0].h], [cfgs[0].n + 1], 1)            # k > n
+    for ctx in ctxs:
+        ctx.close()
