@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-bc", action="store_true", help="skip the tracer-transport Hessian products")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch of 96 windows")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the first timed step with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -203,6 +204,75 @@ def bench_bc_transport(R, torch, dev, flush, hbm_peak, ncols=128, reps=2):
                          "bytes_basis": "one FP32 read and write of the tracer per RK4 step, TL and AD"}}
 
 
+def bench_batch(R, torch, dev, warmup, steps, fp64_baseline=True):
+    """96 independent Lorenz-96 windows of uneven n, T and k: one inner loop
+    of every window per step, batched (persistent Hessian launches, one CUDA
+    graph, autotuned launch shape) against the same windows one at a time
+    (mixed precision, and the plain FP64 form)."""
+    from paper_1906_01413_gb300 import workloads
+    wins = configs.batch_windows()
+    q = 1
+    hvps = sum((q + 1) * w.k for w in wins)
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    ctxs = []
+    for w in wins:
+        ctx, xb, _ = workloads.l96_twin(R, torch, w, dev, R.RIOT_PREC_MIXED, w.k)
+        R.riot_outer_begin(ctx.h, xb)
+        ctxs.append(ctx)
+    b = R.riot_batch_create([c.h for c in ctxs], [w.k for w in wins], q)
+    P, S, tune_ms = R.riot_batch_autotune(b)
+    launches0 = R.riot_kernel_launches()
+    for _ in range(warmup):
+        R.riot_batch_run(b, len(wins), sketch_stream=configs.STREAM_SKETCH0, use_graph=True)
+    l1 = R.riot_kernel_launches()
+    times = [timed(lambda: R.riot_batch_run(b, len(wins), sketch_stream=configs.STREAM_SKETCH0, use_graph=True))
+             for _ in range(steps)]
+    graph_launches = R.riot_kernel_launches() - l1    # host-issued launches while replaying: 0 expected
+    batched_ms = statistics.mean(times)
+    eager_ms = timed(lambda: R.riot_batch_run(b, len(wins), sketch_stream=configs.STREAM_SKETCH0, use_graph=False))
+    hvp_ms = timed(lambda: R.riot_batch_hessian_apply(b))
+    R.riot_batch_destroy(b)
+
+    def one_at_a_time(cs):
+        for w, c in zip(wins, cs):
+            R.riot_rsvd(c.h, w.k, q, sketch_stream=configs.STREAM_SKETCH0)
+            R.riot_increment(c.h)
+
+    alone_ms = timed(lambda: one_at_a_time(ctxs))
+    for c in ctxs:
+        c.close()
+    out = {"workload": "l96_batch%d_n%d-%d_T%d-%d_k%d-%d_q%d" % (
+               len(wins), min(w.n for w in wins), max(w.n for w in wins), min(w.T for w in wins),
+               max(w.T for w in wins), min(w.k for w in wins), max(w.k for w in wins), q),
+           "windows": len(wins), "hvps_per_step": hvps, "value": hvps / (batched_ms * 1e-3), "unit": "HVP/s",
+           "ms_per_step": batched_ms, "graph": True, "batched_eager_ms": eager_ms,
+           "batched_hvp_launch_ms": hvp_ms, "one_at_a_time_mixed_ms": alone_ms,
+           "speedup_vs_one_at_a_time_mixed": alone_ms / batched_ms,
+           "autotune": {"probes_cap": P, "ring_depth": S, "hvp_launch_ms": tune_ms},
+           "host_launches_per_graph_step": int(graph_launches) // max(1, steps)}
+    if fp64_baseline:
+        tot = 0.0
+        for w in wins:
+            c, xb, _ = workloads.l96_twin(R, torch, w, dev, R.RIOT_PREC_FP64, w.k)
+            R.riot_outer_begin(c.h, xb)
+            tot += timed(lambda: (R.riot_rsvd(c.h, w.k, q, sketch_stream=configs.STREAM_SKETCH0),
+                                  R.riot_increment(c.h)))
+            c.close()
+        out["one_at_a_time_fp64_ms"] = tot
+        out["speedup_vs_one_at_a_time_fp64"] = tot / batched_ms
+    return out
+
+
 def cpu_oracle_hvps(cfg, seconds, min_cols=2):
     """FP64 CPU oracle Hessian-vector products on the same workload, single thread."""
     from oracle import problem, riot as orc
@@ -331,6 +401,9 @@ def main():
     e2e_s = statistics.mean(e2e_times)
 
     # ---- tracer-transport inversion (workload 3): Hessian products on the full grid ----
+    batch = None
+    if not args.no_batch:
+        batch = bench_batch(R, torch, dev, args.warmup, max(3, args.steps // 3))
     bc = None
     if not args.no_bc:
         bc = bench_bc_transport(R, torch, dev, flush, float(peaks.get("hbm_gbs", 6800.0)))
@@ -372,6 +445,8 @@ def main():
         line["fp64_gpu_form"] = fp64
     if bc:
         line["bc_transport"] = bc
+    if batch:
+        line["batch_windows"] = batch
     cs = clk.summary()
     if cs:
         line["clocks"] = cs

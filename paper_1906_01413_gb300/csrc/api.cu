@@ -49,6 +49,11 @@ struct riot_ctx {
     int *info = nullptr;  // [0..9] CholeskyQR passes, [10] K Cholesky, [12..13] Jacobi, [14] mode
     int *errflag = nullptr;  // set by a kernel whose bounded wait ran out
     int have_traj = 0, have_rsvd = 0, k_last = 0, v_init = 0, jacobi_sweeps = 0;
+    // FP32 Hessian products are formed as 2^-scale_exp A (R^-1 scaled in rinv32) so that
+    // windows whose tangent-linear growth squared exceeds the FP32 range stay finite;
+    // eigenvalues are scaled back in FP64.
+    int scale_exp = 0;
+    double *nrm = nullptr;   // 4 doubles of norm accumulators
     // timing
     cudaEvent_t ev[32];
     int nev = 0;
@@ -197,7 +202,9 @@ cudaError_t bsqrt(riot_ctx *ctx, const double *in, double *out, int transpose, i
 
 // Q (FP64, n x k) = orthonormal basis of Y (real, n x k): shifted CholeskyQR
 // (shift 11 (n k + k (k + 1)) u ||Y||_F^2, Fukaya et al. 2020) followed by two
-// unshifted CholeskyQR passes.
+// unshifted CholeskyQR passes.  Each pass first scales the columns to unit
+// norm (the Gram is scaled alike), which removes the spread of column norms
+// that power-iteration blocks of strongly unstable windows carry.
 riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
 {
     const int n = ctx->n;
@@ -208,6 +215,7 @@ riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
     const int shifted = (ctx->prec == RIOT_PREC_FP64) ? 3 : 1;
     for (int pass = 0; pass < shifted + 2; ++pass) {
         CU(gram_lower(n, k, ctx->Q, 'd', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
+        if (k <= 1024) CU(equilibrate(ctx->G, k, k, ctx->Q, 'd', n, n, ctx->cvec, ctx->s));
         const double u = ldexp(1.0, -53);
         const double shift = (pass < shifted) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
         CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
@@ -225,6 +233,7 @@ riot_status orth32(riot_ctx *ctx, const float *Y, int k, int info_base, int pass
     CU(cudaMemcpyAsync(ctx->Q32, Y, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, ctx->s));
     for (int pass = 0; pass < passes; ++pass) {
         CU(gram_lower(n, k, ctx->Q32, 'f', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
+        if (k <= 1024) CU(equilibrate(ctx->G, k, k, ctx->Q32, 'f', n, n, ctx->cvec, ctx->s));
         const double u = ldexp(1.0, -53);
         const double shift = (pass == 0) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
         CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
@@ -610,7 +619,7 @@ riot_status setup_common(riot_ctx *ctx)
                      jacobi_work_doubles((int)k) > eig_work_doubles((int)k) ? jacobi_work_doubles((int)k)
                                                                            : eig_work_doubles((int)k))) ||
         (st = dalloc(ctx, &ctx->gws, 8 * k * k > dinv_doubles((int)k) ? 8 * k * k : dinv_doubles((int)k))) ||
-        (st = dalloc(ctx, &ctx->info, 32)) ||
+        (st = dalloc(ctx, &ctx->info, 32)) || (st = dalloc(ctx, &ctx->nrm, 4)) ||
         (st = dalloc(ctx, &ctx->errflag, 4)))
         return st;
     cudaError_t e;
@@ -618,6 +627,33 @@ riot_status setup_common(riot_ctx *ctx)
         (e = cudaMemsetAsync(ctx->errflag, 0, sizeof(int) * 4, ctx->s)) ||
         (e = cudaMemsetAsync(ctx->x, 0, sizeof(double) * np, ctx->s)) || (e = cudaStreamSynchronize(ctx->s)))
         return fail(ctx, RIOT_ECUDA, "setup failed: %s", cudaGetErrorString(e));
+    return RIOT_OK;
+}
+
+// Power-of-two scale of the FP32 Hessian products: |A w| / |w| for one
+// Gaussian w (FP64 product) bounds the leading eigenvalue from below by a
+// factor of order sqrt(n); the exponent keeps sqrt(n) * 16 * that ratio under
+// 2^96, well inside the FP32 range, and is 0 for windows that need none.
+riot_status choose_scale(riot_ctx *ctx)
+{
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    CU(normal_launch(ctx->seed ^ 0x9e3779b97f4a7c15ULL, 0x5ca1eu, n, 1, n, 1, ctx->tmp, s));
+    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, ctx->tmp, ctx->dv, n, 1, 0, ctx->rd, 0, s));
+    CU(cudaMemsetAsync(ctx->nrm, 0, 4 * sizeof(double), s));
+    CU(add_half_sq(n, ctx->tmp, ctx->nrm, s));
+    CU(add_half_sq(n, ctx->dv, ctx->nrm + 1, s));
+    double h[2] = {0.0, 0.0};
+    CU(cudaMemcpyAsync(h, ctx->nrm, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    int c = 0;
+    if (h[0] > 0.0 && h[1] > 0.0 && isfinite(h[1])) {
+        const double est = sqrt(h[1] / h[0]) * sqrt((double)n) * 16.0;
+        const int e = (int)ceil(log2(est));
+        c = e > 96 ? e - 96 : 0;
+    }
+    if (c != ctx->scale_exp || c > 0) CU(scale_to_f32(ctx->p, ctx->rinv64, ldexp(1.0, -c), ctx->rinv32, s));
+    ctx->scale_exp = c;
     return RIOT_OK;
 }
 
@@ -668,6 +704,7 @@ riot_status rsvd_eig(riot_ctx *ctx, int k)
         CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, ctx->s));
     else
         CU(tridiag_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, ctx->s));
+    if (ctx->scale_exp) CU(scal(k, ldexp(1.0, ctx->scale_exp), ctx->lam, ctx->s));
     return RIOT_OK;
 }
 
@@ -959,6 +996,7 @@ riot_status riot_outer_begin(riot_ctx *ctx, const double *x_dev, const double *v
         // gradient b = L^T H^T R^-1 d: one FP64 adjoint integration, then g = b + v
         CU(mul(ctx->p, ctx->d, ctx->rinv64, ctx->rd, ctx->s));
         CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->g, n, 1, 0, ctx->rd, 1, ctx->s));
+        if (ctx->prec == RIOT_PREC_MIXED) TRY(choose_scale(ctx));
     }
     CU(axpby(n, 1.0, ctx->v, 1.0, ctx->g, ctx->s));
     CU(add_half_sq(n, ctx->v, ctx->jo, ctx->s));
@@ -980,7 +1018,11 @@ riot_status riot_hessian_apply(riot_ctx *ctx, const void *W_dev, void *Y_dev, in
     if (ncols == 0) return RIOT_OK;
     if (!W_dev || !Y_dev) return fail(ctx, RIOT_EINVAL, "null W or Y");
     CU(cudaSetDevice(ctx->dev));
-    return hvp(ctx, W_dev, Y_dev, ld, ncols, add_identity);
+    if (!ctx->scale_exp) return hvp(ctx, W_dev, Y_dev, ld, ncols, add_identity);
+    TRY(hvp(ctx, W_dev, Y_dev, ld, ncols, 0));
+    CU(scale_add_cols(ctx->n, ncols, ld, ldexp(1.0, ctx->scale_exp), Y_dev, add_identity ? W_dev : nullptr,
+                      ctx->prec == RIOT_PREC_FP64, ctx->s));
+    return RIOT_OK;
 }
 
 riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y_dev, int64_t ld, int32_t ncols,
@@ -1013,9 +1055,14 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
         else if (ctx->prec == RIOT_PREC_FP64)
             CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, (const double *)w, (double *)yv, ld, nc, add_identity,
                                   (double *)scr, 0, ctx->s));
-        else
+        else if (!ctx->scale_exp)
             CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
                                   (float *)scr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S));
+        else {
+            CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, 0, (float *)scr, 0,
+                                  ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S));
+            CU(scale_add_cols(ctx->n, nc, ld, ldexp(1.0, ctx->scale_exp), yv, add_identity ? w : nullptr, 0, ctx->s));
+        }
     }
     return RIOT_OK;
 }

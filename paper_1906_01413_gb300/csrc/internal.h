@@ -228,6 +228,15 @@ cudaError_t check_finite(const double *x, int64_t n, int *flag, cudaStream_t s);
 cudaError_t add_if_flag(const int *flag, int want, int64_t n, double a, const double *x, double *y, cudaStream_t s);
 cudaError_t mul(int64_t n, const double *a, const double *b, double *out, cudaStream_t s);
 cudaError_t add_half_sq(int64_t n, const double *x, double *out, cudaStream_t s);
+cudaError_t scale_to_f32(int64_t n, const double *in, double a, float *out, cudaStream_t s);
+// Column equilibration of one CholeskyQR pass (k <= 1024): with d_j = 1/sqrt(G_jj),
+// G <- D G D (lower triangle) and Q <- Q D ('f' or 'd' block, n rows); d receives D.
+cudaError_t equilibrate(double *G, int k, int64_t ldg, void *Q, char tQ, int64_t n, int64_t ldq, double *d,
+                        cudaStream_t s);
+cudaError_t scal(int64_t n, double a, double *x, cudaStream_t s);
+// Y = a Y (+ W) column by column (n rows of ncols columns at ld), float or double
+cudaError_t scale_add_cols(int64_t n, int ncols, int64_t ld, double a, void *Y, const void *W, int is_double,
+                           cudaStream_t s);
 // largest-magnitude entry of each of the k columns made positive
 cudaError_t fix_col_signs(double *U, int64_t n, int k, int64_t ld, cudaStream_t s);
 

@@ -944,6 +944,102 @@ __global__ void half_sq_kernel(int64_t n, const double *x, double *out)
     if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(out, 0.5 * part);
 }
 
+// Column equilibration of a CholeskyQR pass: d_j = 1 / sqrt(G_jj) (1 for a
+// zero column), G <- D G D on the lower triangle, Q <- Q D.
+__global__ void equil_gram_kernel(double *G, int k, int64_t ldg, double *d)
+{
+    __shared__ double sd[1024];
+    for (int j = threadIdx.x; j < k && j < 1024; j += blockDim.x) {
+        const double g = G[(int64_t)j * ldg + j];
+        sd[j] = g > 0.0 ? 1.0 / sqrt(g) : 1.0;
+        if (blockIdx.x == 0) d[j] = sd[j];
+    }
+    __syncthreads();
+    const int col = blockIdx.x;
+    if (col >= k) return;
+    for (int i = col + threadIdx.x; i < k; i += blockDim.x) G[(int64_t)col * ldg + i] *= sd[i] * sd[col];
+}
+
+template <typename R>
+__global__ void scale_cols_kernel(R *Q, int64_t n, int k, int64_t ldq, const double *d)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * k) return;
+    const int64_t j = t / n, i = t - j * n;
+    Q[j * ldq + i] = (R)((double)Q[j * ldq + i] * d[j]);
+}
+
+cudaError_t equilibrate(double *G, int k, int64_t ldg, void *Q, char tQ, int64_t n, int64_t ldq, double *d,
+                        cudaStream_t s)
+{
+    if (k < 1) return cudaSuccess;
+    if (k > 1024) return cudaErrorInvalidValue;
+    count_launch();
+    equil_gram_kernel<<<k, 256, 0, s>>>(G, k, ldg, d);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = n * k;
+    count_launch();
+    if (tQ == 'd')
+        scale_cols_kernel<double><<<(unsigned)((total + 255) / 256), 256, 0, s>>>((double *)Q, n, k, ldq, d);
+    else
+        scale_cols_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, s>>>((float *)Q, n, k, ldq, d);
+    return cudaGetLastError();
+}
+
+__global__ void scale_to_f32_kernel(int64_t n, const double *in, double a, float *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)(a * in[i]);
+}
+
+cudaError_t scale_to_f32(int64_t n, const double *in, double a, float *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launch();
+    scale_to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, a, out);
+    return cudaGetLastError();
+}
+
+__global__ void scal_kernel(int64_t n, double a, double *x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] *= a;
+}
+
+cudaError_t scal(int64_t n, double a, double *x, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launch();
+    scal_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, x);
+    return cudaGetLastError();
+}
+
+// Y[j*ld + i] = a Y[j*ld + i] (+ W[j*ld + i]) for i < n, j < ncols (float or double)
+template <typename R>
+__global__ void scale_add_cols_kernel(int64_t n, int ncols, int64_t ld, R a, R *Y, const R *W)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * ncols) return;
+    const int64_t j = t / n, i = t - j * n;
+    const R v = a * Y[j * ld + i];
+    Y[j * ld + i] = W ? v + W[j * ld + i] : v;
+}
+
+cudaError_t scale_add_cols(int64_t n, int ncols, int64_t ld, double a, void *Y, const void *W, int is_double,
+                           cudaStream_t s)
+{
+    const int64_t total = n * ncols;
+    if (total <= 0) return cudaSuccess;
+    count_launch();
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    if (is_double)
+        scale_add_cols_kernel<double><<<grid, 256, 0, s>>>(n, ncols, ld, a, (double *)Y, (const double *)W);
+    else
+        scale_add_cols_kernel<float><<<grid, 256, 0, s>>>(n, ncols, ld, (float)a, (float *)Y, (const float *)W);
+    return cudaGetLastError();
+}
+
 cudaError_t add_half_sq(int64_t n, const double *x, double *out, cudaStream_t s)
 {
     int blocks = (int)((n + 255) / 256);

@@ -135,3 +135,23 @@ def test_batch_rejects_bad_windows(gpu_lib):
         R.riot_batch_create([ctxs[0].h], [cfgs[0].n + 1], 1)            # k > n
     for ctx in ctxs:
         ctx.close()
+
+
+def test_window_beyond_the_fp32_range(gpu_lib):
+    """F = 16 over 300 steps: the tangent-linear growth squared exceeds the
+    FP32 range, so the mixed path forms 2^-c A with a power-of-two c chosen
+    at riot_outer_begin.  Its leading eigenvalues must match the FP64 path."""
+    R = gpu_lib
+    from paper_1906_01413_gb300 import workloads
+    cfg = configs.L96Config(name="strong", n=64, F=16.0, T=300, obs_every=4, obs_frac=0.5, obs_layout="random",
+                            ell=4.0, k=16, q=1, spinup=300, seed=configs.BASE_SEED + 77)
+    lams = {}
+    for prec in (R.RIOT_PREC_MIXED, R.RIOT_PREC_FP64):
+        ctx, xb, _ = workloads.l96_twin(R, torch, cfg, DEV, prec, cfg.k)
+        R.riot_outer_begin(ctx.h, xb)
+        lams[prec] = R.riot_rsvd(ctx.h, cfg.k, cfg.q, sketch_stream=3)
+        ctx.close()
+    lm, l64 = lams[R.RIOT_PREC_MIXED], lams[R.RIOT_PREC_FP64]
+    assert l64[0] > 1e39            # beyond what an unscaled FP32 product can hold
+    assert np.all(np.isfinite(lm))
+    np.testing.assert_allclose(lm[:4], l64[:4], rtol=1e-3)
