@@ -232,21 +232,29 @@ def bench_batch(R, torch, dev, warmup, steps, fp64_baseline=True):
     b = R.riot_batch_create([c.h for c in ctxs], [w.k for w in wins], q)
     P, S, tune_ms = R.riot_batch_autotune(b)
     launches0 = R.riot_kernel_launches()
+    statuses = None
     for _ in range(warmup):
-        R.riot_batch_run(b, len(wins), sketch_stream=configs.STREAM_SKETCH0, use_graph=True)
+        statuses = R.riot_batch_run(b, len(wins), sketch_stream=configs.STREAM_SKETCH0, use_graph=True, check=False)
     l1 = R.riot_kernel_launches()
-    times = [timed(lambda: R.riot_batch_run(b, len(wins), sketch_stream=configs.STREAM_SKETCH0, use_graph=True))
+    times = [timed(lambda: R.riot_batch_run(b, len(wins), sketch_stream=configs.STREAM_SKETCH0, use_graph=True,
+                                            check=False))
              for _ in range(steps)]
     graph_launches = R.riot_kernel_launches() - l1    # host-issued launches while replaying: 0 expected
     batched_ms = statistics.mean(times)
-    eager_ms = timed(lambda: R.riot_batch_run(b, len(wins), sketch_stream=configs.STREAM_SKETCH0, use_graph=False))
+    eager_ms = timed(lambda: R.riot_batch_run(b, len(wins), sketch_stream=configs.STREAM_SKETCH0, use_graph=False,
+                                              check=False))
     hvp_ms = timed(lambda: R.riot_batch_hessian_apply(b))
     R.riot_batch_destroy(b)
 
+    alone_failed = []
+
     def one_at_a_time(cs):
-        for w, c in zip(wins, cs):
-            R.riot_rsvd(c.h, w.k, q, sketch_stream=configs.STREAM_SKETCH0)
-            R.riot_increment(c.h)
+        for i, (w, c) in enumerate(zip(wins, cs)):
+            try:
+                R.riot_rsvd(c.h, w.k, q, sketch_stream=configs.STREAM_SKETCH0)
+                R.riot_increment(c.h)
+            except R.RiotError:
+                alone_failed.append(i)
 
     alone_ms = timed(lambda: one_at_a_time(ctxs))
     for c in ctxs:
@@ -259,16 +267,27 @@ def bench_batch(R, torch, dev, warmup, steps, fp64_baseline=True):
            "batched_hvp_launch_ms": hvp_ms, "one_at_a_time_mixed_ms": alone_ms,
            "speedup_vs_one_at_a_time_mixed": alone_ms / batched_ms,
            "autotune": {"probes_cap": P, "ring_depth": S, "hvp_launch_ms": tune_ms},
-           "host_launches_per_graph_step": int(graph_launches) // max(1, steps)}
+           "host_launches_per_graph_step": int(graph_launches) // max(1, steps),
+           "windows_failed": [i for i, st in enumerate(statuses or []) if st != 0],
+           "one_at_a_time_mixed_windows_failed": alone_failed}
     if fp64_baseline:
         tot = 0.0
-        for w in wins:
+        fp64_failed = []
+        for i, w in enumerate(wins):
             c, xb, _ = workloads.l96_twin(R, torch, w, dev, R.RIOT_PREC_FP64, w.k)
             R.riot_outer_begin(c.h, xb)
-            tot += timed(lambda: (R.riot_rsvd(c.h, w.k, q, sketch_stream=configs.STREAM_SKETCH0),
-                                  R.riot_increment(c.h)))
+
+            def run64():
+                try:
+                    R.riot_rsvd(c.h, w.k, q, sketch_stream=configs.STREAM_SKETCH0)
+                    R.riot_increment(c.h)
+                except R.RiotError:
+                    fp64_failed.append(i)
+
+            tot += timed(run64)
             c.close()
         out["one_at_a_time_fp64_ms"] = tot
+        out["one_at_a_time_fp64_windows_failed"] = fp64_failed
         out["speedup_vs_one_at_a_time_fp64"] = tot / batched_ms
     return out
 

@@ -215,7 +215,7 @@ riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
     const int shifted = (ctx->prec == RIOT_PREC_FP64) ? 3 : 1;
     for (int pass = 0; pass < shifted + 2; ++pass) {
         CU(gram_lower(n, k, ctx->Q, 'd', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
-        if (k <= 1024) CU(equilibrate(ctx->G, k, k, ctx->Q, 'd', n, n, ctx->cvec, ctx->s));
+        CU(equilibrate(ctx->G, k, k, ctx->Q, 'd', n, n, ctx->cvec, ctx->s));
         const double u = ldexp(1.0, -53);
         const double shift = (pass < shifted) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
         CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
@@ -227,15 +227,15 @@ riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
 // Mixed precision: Q32 = orthonormal basis of Y (FP32 block).  Grams are
 // accumulated and factorised in FP64 (the step that needs the range); the
 // triangular solves run in FP32, like the block they act on.
-riot_status orth32(riot_ctx *ctx, const float *Y, int k, int info_base, int passes)
+riot_status orth32(riot_ctx *ctx, const float *Y, int k, int info_base, int passes, int shifted)
 {
     const int n = ctx->n;
     CU(cudaMemcpyAsync(ctx->Q32, Y, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, ctx->s));
     for (int pass = 0; pass < passes; ++pass) {
         CU(gram_lower(n, k, ctx->Q32, 'f', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
-        if (k <= 1024) CU(equilibrate(ctx->G, k, k, ctx->Q32, 'f', n, n, ctx->cvec, ctx->s));
+        CU(equilibrate(ctx->G, k, k, ctx->Q32, 'f', n, n, ctx->cvec, ctx->s));
         const double u = ldexp(1.0, -53);
-        const double shift = (pass == 0) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
+        const double shift = (pass < shifted) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
         CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
         CU(convert_block(ctx->G, 'd', k, ctx->L32, 'f', k, k, k, ctx->s));
         CU(strsm_right_lt(ctx->Q32, n, k, n, ctx->L32, k, ctx->s));
@@ -686,8 +686,8 @@ riot_status rsvd_power(riot_ctx *ctx, int k)
 {
     const int n = ctx->n;
     if (ctx->prec == RIOT_PREC_MIXED) {
-        // a power-iteration basis only has to span the block well: shifted pass + one plain pass
-        TRY(orth32(ctx, (const float *)ctx->Yblk, k, 0, 2));
+        // a power-iteration basis only has to span the block well: two shifted passes
+        TRY(orth32(ctx, (const float *)ctx->Yblk, k, 0, 2, 2));
         CU(cudaMemcpyAsync(ctx->Wblk, ctx->Q32, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, ctx->s));
     } else {
         TRY(orth(ctx, ctx->Yblk, k, 0));
@@ -733,7 +733,7 @@ riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
     const bool mixed = (ctx->prec == RIOT_PREC_MIXED);
     float *W32 = (float *)ctx->Wblk, *Y32 = (float *)ctx->Yblk;
     ev_mark(ctx, 1);
-    if (mixed) TRY(orth32(ctx, Y32, k, 5, 3));
+    if (mixed) TRY(orth32(ctx, Y32, k, 5, 3, 2));
     else TRY(orth(ctx, ctx->Yblk, k, 5));
     ev_mark(ctx, 2);
     if (ctx->exact_rr) {
@@ -778,6 +778,11 @@ riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
 riot_status rsvd_collect(riot_ctx *ctx, int k, double *lambda_out)
 {
     cudaStream_t s = ctx->s;
+    // a bounded wait that ran out invalidates everything after it: report it first
+    int eflag = 0;
+    CU(cudaMemcpyAsync(&eflag, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (eflag) return fail(ctx, RIOT_ETIMEOUT, "a bounded wait on a coefficient copy ran out in the Hessian kernel");
     TRY(check_cholesky(ctx, 0, 11, "riot_rsvd"));
     int jinfo[2] = {0, 0};
     CU(cudaMemcpyAsync(jinfo, ctx->info + 12, sizeof(jinfo), cudaMemcpyDeviceToHost, s));
@@ -787,10 +792,6 @@ riot_status rsvd_collect(riot_ctx *ctx, int k, double *lambda_out)
         return fail(ctx, RIOT_ENOCONV, "Jacobi did not converge in %d sweeps", -jinfo[0]);
     if (ctx->eig_method == RIOT_EIG_TRIDIAG && (jinfo[0] != 0 || jinfo[1] != 0))
         return fail(ctx, RIOT_ENOCONV, "orthonormalisation of the tridiagonal eigenvectors failed");
-    int eflag = 0;
-    CU(cudaMemcpyAsync(&eflag, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (eflag) return fail(ctx, RIOT_ETIMEOUT, "a bounded wait on a coefficient copy ran out in the Hessian kernel");
     ctx->jacobi_sweeps = (ctx->eig_method == RIOT_EIG_JACOBI) ? jinfo[0] : 0;
     ctx->have_rsvd = 1;
     ctx->k_last = k;

@@ -459,13 +459,13 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     count_launch();
     inviter_kernel<<<(k + 3) / 4, 4, 0, s>>>(d, e, blo, bhi, k, w, tnorm, Zt, u0, u1, u2, ml, piv, wrq);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    // CholeskyQR on the eigenvectors of T: a shifted pass (Fukaya et al. 2020), so that
-    // eigenvalues clustered below the resolution eps ||T|| (whose inverse-iteration
+    // CholeskyQR on the eigenvectors of T: two shifted passes (Fukaya et al. 2020), so
+    // that eigenvalues clustered below the resolution eps ||T|| (whose inverse-iteration
     // vectors nearly coincide) still yield an orthonormal set, then two plain passes
-    for (int pass = 0; pass < 3; ++pass) {
-        const double shift = pass == 0 ? 11.0 * ((double)k * k + (double)k * (k + 1)) * ldexp(1.0, -53) : 0.0;
+    for (int pass = 0; pass < 4; ++pass) {
+        const double shift = pass < 2 ? 11.0 * ((double)k * k + (double)k * (k + 1)) * ldexp(1.0, -53) : 0.0;
         if ((err = gram_lower(k, k, Zt, 'd', k, Zs, k, s)) != cudaSuccess) return err;
-        if ((err = cholesky(Zs, k, k, shift, info + (pass == 0 ? 0 : pass - 1), dinv, s)) != cudaSuccess) return err;
+        if ((err = cholesky(Zs, k, k, shift, info + (pass < 2 ? 0 : pass - 2), dinv, s)) != cudaSuccess) return err;
         if ((err = trsm_right_lt(Zt, k, k, k, Zs, k, s, dinv)) != cudaSuccess) return err;
     }
     count_launch();

@@ -229,7 +229,7 @@ cudaError_t add_if_flag(const int *flag, int want, int64_t n, double a, const do
 cudaError_t mul(int64_t n, const double *a, const double *b, double *out, cudaStream_t s);
 cudaError_t add_half_sq(int64_t n, const double *x, double *out, cudaStream_t s);
 cudaError_t scale_to_f32(int64_t n, const double *in, double a, float *out, cudaStream_t s);
-// Column equilibration of one CholeskyQR pass (k <= 1024): with d_j = 1/sqrt(G_jj),
+// Column equilibration of one CholeskyQR pass: with d_j = 1/sqrt(G_jj),
 // G <- D G D (lower triangle) and Q <- Q D ('f' or 'd' block, n rows); d receives D.
 cudaError_t equilibrate(double *G, int k, int64_t ldg, void *Q, char tQ, int64_t n, int64_t ldq, double *d,
                         cudaStream_t s);

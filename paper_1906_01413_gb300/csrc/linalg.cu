@@ -945,19 +945,23 @@ __global__ void half_sq_kernel(int64_t n, const double *x, double *out)
 }
 
 // Column equilibration of a CholeskyQR pass: d_j = 1 / sqrt(G_jj) (1 for a
-// zero column), G <- D G D on the lower triangle, Q <- Q D.
-__global__ void equil_gram_kernel(double *G, int k, int64_t ldg, double *d)
+// zero column), G <- D G D on the lower triangle, Q <- Q D.  The scales are
+// formed by their own kernel first: a block scaling its column must not race
+// with another block still reading that column's diagonal entry.
+__global__ void equil_scales_kernel(const double *G, int k, int64_t ldg, double *d)
 {
-    __shared__ double sd[1024];
-    for (int j = threadIdx.x; j < k && j < 1024; j += blockDim.x) {
-        const double g = G[(int64_t)j * ldg + j];
-        sd[j] = g > 0.0 ? 1.0 / sqrt(g) : 1.0;
-        if (blockIdx.x == 0) d[j] = sd[j];
-    }
-    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    const double g = G[(int64_t)j * ldg + j];
+    d[j] = g > 0.0 ? 1.0 / sqrt(g) : 1.0;
+}
+
+__global__ void equil_gram_kernel(double *G, int k, int64_t ldg, const double *d)
+{
     const int col = blockIdx.x;
     if (col >= k) return;
-    for (int i = col + threadIdx.x; i < k; i += blockDim.x) G[(int64_t)col * ldg + i] *= sd[i] * sd[col];
+    const double dc = d[col];
+    for (int i = col + threadIdx.x; i < k; i += blockDim.x) G[(int64_t)col * ldg + i] *= d[i] * dc;
 }
 
 template <typename R>
@@ -973,7 +977,8 @@ cudaError_t equilibrate(double *G, int k, int64_t ldg, void *Q, char tQ, int64_t
                         cudaStream_t s)
 {
     if (k < 1) return cudaSuccess;
-    if (k > 1024) return cudaErrorInvalidValue;
+    count_launch();
+    equil_scales_kernel<<<(k + 255) / 256, 256, 0, s>>>(G, k, ldg, d);
     count_launch();
     equil_gram_kernel<<<k, 256, 0, s>>>(G, k, ldg, d);
     cudaError_t e = cudaGetLastError();

@@ -323,10 +323,13 @@ def riot_batch_hessian_apply(b):
     _bcheck(b, "riot_batch_hessian_apply", load().riot_batch_hessian_apply(b))
 
 
-def riot_batch_run(b, nwin, sketch_stream=0, use_graph=True):
+def riot_batch_run(b, nwin, sketch_stream=0, use_graph=True, check=True):
+    """One inner loop of every window; returns the per-window statuses (raises
+    on the first failure unless check is False)."""
     st = (c_int32 * nwin)()
     status = load().riot_batch_run(b, int(sketch_stream), int(bool(use_graph)), st)
-    _bcheck(b, "riot_batch_run", status)
+    if check:
+        _bcheck(b, "riot_batch_run", status)
     return list(st)
 
 
