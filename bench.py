@@ -35,6 +35,11 @@ from synth import advdiff as bc_synth  # noqa: E402
 from synth import configs  # noqa: E402
 
 WORKLOAD = "l96_n4096_F8_T200_obs25pct_every4_k512_q1"
+# DRAM bytes (read + write) from one ncu capture of the current kernels, summarised under
+# profiles/: one 512-column Hessian launch of the workload above, and one RK4 step of one
+# tracer column on the 192 x 192 x 30 grid (a 32-column launch / 32).
+L96_HVP_DRAM_BYTES_PER_LAUNCH = 53.4912e6 + 69.8212e6
+BC_STEP_DRAM_BYTES_PER_COLUMN = (146.62656e6 + 103.566336e6) / 32
 METRIC = "RIOT inner-loop Hessian-vector products per second (inner-loop wall time)"
 UNIT = "HVP/s"
 
@@ -50,6 +55,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-bc", action="store_true", help="skip the tracer-transport Hessian products")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch of 96 windows")
+    ap.add_argument("--only", choices=["bc", "batch"], default=None,
+                    help="run one secondary leg alone and print its JSON (profiling)")
+    ap.add_argument("--bc-cols", type=int, default=128, help="sketch columns per tracer Hessian call")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the first timed step with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -200,7 +208,7 @@ def bench_bc_transport(R, torch, dev, flush, hbm_peak, ncols=128, reps=2):
             "dtype": "f32",
             "roofline": {"bound": "hbm", "kernel": "adv_step_kernel<float,32,32,4> (whole product timed)",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "traffic": None, "bytes_per_hvp": bytes_per_hvp,
+                         "traffic": BC_STEP_DRAM_BYTES_PER_COLUMN * 2 * cfg.T, "bytes_per_hvp": bytes_per_hvp,
                          "bytes_basis": "one FP32 read and write of the tracer per RK4 step, TL and AD"}}
 
 
@@ -358,6 +366,25 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
+    if args.only:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        if args.profile:
+            torch.cuda.profiler.start()
+        if args.only == "bc":
+            out = bench_bc_transport(R, torch, dev, flush, float(peaks.get("hbm_gbs", 6800.0)), ncols=args.bc_cols,
+                                     reps=max(1, args.steps))
+        else:
+            out = bench_batch(R, torch, dev, args.warmup, max(1, args.steps), fp64_baseline=False)
+        if args.profile:
+            torch.cuda.profiler.stop()
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
     cfg = configs.l96_large()
     n, k, q, T = cfg.n, cfg.k, cfg.q, cfg.T
 
@@ -453,7 +480,8 @@ def main():
                        "inner_loop_ms": ms},
             "phases_ms": ph,
             "roofline": {"bound": "alu", "kernel": "l96_hvp_tma_kernel<8,2,512>", "achieved": achieved,
-                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "traffic": L96_HVP_DRAM_BYTES_PER_LAUNCH,
                          "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sm_count, sm_max),
                          "flop_per_hvp": flop_hvp, "hvp_per_launch": k, "launch_ms": hvp_launch_ms},
             "e2e": {"value": world * hvps_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(n * k * 4),

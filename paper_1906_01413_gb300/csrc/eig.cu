@@ -461,11 +461,11 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // CholeskyQR on the eigenvectors of T: two shifted passes (Fukaya et al. 2020), so
     // that eigenvalues clustered below the resolution eps ||T|| (whose inverse-iteration
-    // vectors nearly coincide) still yield an orthonormal set, then two plain passes
-    for (int pass = 0; pass < 4; ++pass) {
+    // vectors nearly coincide) still yield an orthonormal set, then a plain pass
+    for (int pass = 0; pass < 3; ++pass) {
         const double shift = pass < 2 ? 11.0 * ((double)k * k + (double)k * (k + 1)) * ldexp(1.0, -53) : 0.0;
         if ((err = gram_lower(k, k, Zt, 'd', k, Zs, k, s)) != cudaSuccess) return err;
-        if ((err = cholesky(Zs, k, k, shift, info + (pass < 2 ? 0 : pass - 2), dinv, s)) != cudaSuccess) return err;
+        if ((err = cholesky(Zs, k, k, shift, info + (pass < 2 ? 0 : 1), dinv, s)) != cudaSuccess) return err;
         if ((err = trsm_right_lt(Zt, k, k, k, Zs, k, s, dinv)) != cudaSuccess) return err;
     }
     count_launch();
