@@ -335,6 +335,64 @@ riot_status riot_batch_run(riot_batch *b, int64_t sketch_stream, int32_t use_gra
 const char *riot_batch_last_error(const riot_batch *b);
 void riot_batch_destroy(riot_batch *b);
 
+/* ---- Learned sketch proposal ----------------------------------------------
+ * A periodic 1-D convolutional network maps C_in standardised snapshots of a
+ * Lorenz-96 background trajectory to m proposed sketch directions; it is
+ * trained on leading Hessian eigenvectors that RIOT produced for other
+ * windows.  This extends the randomized range finder of Section 2.2; the
+ * Gaussian sketch of Algorithm 3 remains the fallback and the judge
+ * (riot_rsvd_proposal).  Network: depth periodic conv layers of width ksize
+ * (odd, <= 7), tanh on the hidden layers, channels c_in -> width -> ... ->
+ * m_out.  Parameters are one FP32 vector: per layer W[C_out][C_in][ksize]
+ * then b[C_out].  conv(x)[o][i] = b[o] + sum_c sum_d W[o][c][d]
+ * x[c][(i + d - ksize/2) mod n].  Loss per window with target U (n x r,
+ * orthonormal columns) on the directions X (n x m):
+ *   ||X - U U^T X||_F^2 / ||X||_F^2 + mu ||X^T X / s - I||_F^2 / m^2,
+ *   s = ||X||_F^2 / m,
+ * averaged over the batch; training uses Adam (beta 0.9 / 0.999, eps 1e-8). */
+typedef struct riot_sketchnet riot_sketchnet;
+
+/* Create a network with zero parameters (set them with riot_sketchnet_set_params)
+ * for inputs of up to n_max variables, batches of up to batch_max windows and
+ * targets of up to r_max vectors. */
+riot_status riot_sketchnet_create(riot_sketchnet **out, int32_t c_in, int32_t width, int32_t m_out, int32_t depth,
+                                  int32_t ksize, int32_t n_max, int32_t batch_max, int32_t r_max, void *cuda_stream);
+int64_t riot_sketchnet_num_params(const riot_sketchnet *net);
+/* Copy the parameters in (and restart the optimiser) or out; device FP32 vectors. */
+riot_status riot_sketchnet_set_params(riot_sketchnet *net, const float *params_dev);
+riot_status riot_sketchnet_get_params(riot_sketchnet *net, float *params_dev);
+/* Z (batch x m_out x n, i.e. m_out directions of n) from x (batch x c_in x n).  bf16 = 1
+ * rounds weights and activations to BF16 (accumulation stays FP32). */
+riot_status riot_sketchnet_forward(riot_sketchnet *net, const float *x_dev, int32_t n, int32_t batch, float *Z_dev,
+                                   int32_t bf16);
+/* Mean loss (host, may be NULL; synchronises) and its gradient (device, num_params
+ * floats; NULL keeps it inside the network) for targets U (batch x r x n). */
+riot_status riot_sketchnet_loss_grad(riot_sketchnet *net, const float *x_dev, const float *U_dev, int32_t r, int32_t n,
+                                     int32_t batch, double mu, float *grad_dev, double *loss_out);
+/* One Adam step on one batch; loss_out (may be NULL) receives the loss before the step. */
+riot_status riot_sketchnet_train_step(riot_sketchnet *net, const float *x_dev, const float *U_dev, int32_t r, int32_t n,
+                                      int32_t batch, double mu, float lr, double *loss_out);
+/* Network input from a trajectory ((T+1) x n doubles, device): x (c_in x n floats) =
+ * the snapshots at steps floor(c T / c_in), standardised by their common mean and
+ * standard deviation.  Synchronises. */
+riot_status riot_sketchnet_input(const double *traj_dev, int32_t T, int64_t n, int32_t c_in, float *x_dev,
+                                 void *cuda_stream);
+void riot_sketchnet_destroy(riot_sketchnet *net);
+
+/* The stored FP64 trajectory ((T+1) x n doubles) of the last riot_outer_begin
+ * (Lorenz-96 contexts). */
+riot_status riot_get_trajectory(riot_ctx *ctx, double *traj_dev);
+
+/* riot_rsvd with a proposed block: the m directions P_dev (m x n floats) are
+ * orthonormalised into Q_p and the sketch is [Q_p, k - m Gaussian columns].
+ * The proposal is kept only if its Rayleigh residual
+ *   rho = ||A Q_p - Q_p (Q_p^T A Q_p)||_F / ||A Q_p||_F <= rho_max
+ * (those products are part of the sketch); otherwise the sketch falls back to
+ * k Gaussian columns, exactly as riot_rsvd.  rho_out (-1 when m = 0) and
+ * used_out (1 if the proposal was kept) may be NULL.  Mixed precision only. */
+riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const float *P_dev, int32_t m,
+                               double rho_max, double *lambda_out, double *rho_out, int32_t *used_out);
+
 const char *riot_last_error(const riot_ctx *ctx);
 const char *riot_status_string(riot_status s);
 void riot_destroy(riot_ctx *ctx);

@@ -21,7 +21,7 @@ on the directions as columns X = Z^T (n, m):
   L  = L1 + mu L2,   averaged over the windows of a batch.
 Optimiser: Adam (Kingma & Ba) with bias correction.
 
-Inputs: C_in snapshots of the trajectory at steps round(j T / C_in),
+Inputs: C_in snapshots of the trajectory at steps floor(j T / C_in),
 j = 0 .. C_in - 1, standardised by their common mean and standard deviation.
 """
 import numpy as np
@@ -156,9 +156,9 @@ class Adam:
 
 
 def snapshot_input(traj, c_in):
-    """C_in standardised snapshots of a trajectory (T+1, n) at steps round(j T / C_in)."""
+    """C_in standardised snapshots of a trajectory (T+1, n) at steps floor(j T / C_in)."""
     T = traj.shape[0] - 1
-    idx = [int(round(j * T / c_in)) for j in range(c_in)]
+    idx = [(j * T) // c_in for j in range(c_in)]
     x = traj[idx]
     return (x - x.mean()) / x.std()
 

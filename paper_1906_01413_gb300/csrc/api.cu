@@ -81,6 +81,18 @@ struct riot_batch {
     char err[512] = {0};
 };
 
+// A learned sketch network with its optimiser state and workspace (riot_sketchnet_*).
+struct riot_sketchnet {
+    int dev = 0;
+    cudaStream_t s = nullptr;
+    riot::SketchNet net;
+    riot::SketchWork w;
+    int n_max = 0, b_max = 0, r_max = 0, t = 0;
+    float *params = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+    double *loss = nullptr;
+    std::vector<void *> allocs;
+};
+
 namespace {
 
 riot_status fail(riot_ctx *c, riot_status st, const char *fmt, ...)
@@ -1429,6 +1441,216 @@ void riot_batch_destroy(riot_batch *b)
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
     delete b;
+}
+
+// ---------------------------------------------------------------------------
+// Learned sketch proposal
+// ---------------------------------------------------------------------------
+riot_status riot_get_trajectory(riot_ctx *ctx, double *traj_dev)
+{
+    if (!ctx || !traj_dev) return RIOT_EINVAL;
+    if (ctx->model != RIOT_MODEL_L96) return fail(ctx, RIOT_EINVAL, "riot_get_trajectory: Lorenz-96 contexts only");
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_get_trajectory before riot_outer_begin");
+    CU(cudaSetDevice(ctx->dev));
+    CU(cudaMemcpyAsync(traj_dev, ctx->traj, sizeof(double) * (size_t)(ctx->m.T + 1) * ctx->n, cudaMemcpyDeviceToDevice,
+                       ctx->s));
+    return RIOT_OK;
+}
+
+riot_status riot_sketchnet_create(riot_sketchnet **out, int32_t c_in, int32_t width, int32_t m_out, int32_t depth,
+                                  int32_t ksize, int32_t n_max, int32_t batch_max, int32_t r_max, void *cuda_stream)
+{
+    if (!out) return RIOT_EINVAL;
+    *out = nullptr;
+    if (c_in < 1 || c_in > 256 || width < 1 || width > 1024 || m_out < 1 || m_out > 1024 || depth < 2 || depth > 8 ||
+        ksize < 1 || ksize > 7 || (ksize & 1) == 0 || n_max < ksize || batch_max < 1 || r_max < 1 || r_max > n_max)
+        return RIOT_EINVAL;
+    riot_sketchnet *net = new riot_sketchnet();
+    cudaGetDevice(&net->dev);
+    net->s = (cudaStream_t)cuda_stream;
+    net->net.c_in = c_in;
+    net->net.width = width;
+    net->net.m = m_out;
+    net->net.depth = depth;
+    net->net.K = ksize;
+    net->net.chan[0] = c_in;
+    for (int l = 1; l < depth; ++l) net->net.chan[l] = width;
+    net->net.chan[depth] = m_out;
+    net->n_max = n_max;
+    net->b_max = batch_max;
+    net->r_max = r_max;
+    const size_t np = (size_t)net->net.num_params();
+    const size_t n = (size_t)n_max, B = (size_t)batch_max, m = (size_t)m_out;
+    const size_t wide = (size_t)(width > c_in ? width : c_in);
+    auto alloc = [&](auto **p, size_t count) {
+        *p = nullptr;
+        if (cudaMalloc((void **)p, (count ? count : 1) * sizeof(**p)) != cudaSuccess) return false;
+        net->allocs.push_back((void *)*p);
+        return true;
+    };
+    SketchWork &w = net->w;
+    if (!alloc(&net->params, np) || !alloc(&net->grad, np) || !alloc(&net->m1, np) || !alloc(&net->m2, np) ||
+        !alloc(&w.Z, B * m * n) || !alloc(&w.gZ, B * m * n) || !alloc(&w.acts, (size_t)(depth - 1) * B * width * n) ||
+        !alloc(&w.g0, B * wide * n) || !alloc(&w.g1, B * wide * n) || !alloc(&w.R, n * m) || !alloc(&w.XE, n * m) ||
+        !alloc(&w.UtX, (size_t)r_max * m) || !alloc(&w.G, m * m) || !alloc(&w.E, m * m) || !alloc(&w.sc, 4 * B) ||
+        !alloc(&net->loss, 1)) {
+        riot_sketchnet_destroy(net);
+        return RIOT_ENOMEM;
+    }
+    if (cudaMemsetAsync(net->params, 0, np * sizeof(float), net->s) != cudaSuccess ||
+        cudaMemsetAsync(net->m1, 0, np * sizeof(float), net->s) != cudaSuccess ||
+        cudaMemsetAsync(net->m2, 0, np * sizeof(float), net->s) != cudaSuccess ||
+        cudaStreamSynchronize(net->s) != cudaSuccess) {
+        riot_sketchnet_destroy(net);
+        return RIOT_ECUDA;
+    }
+    *out = net;
+    return RIOT_OK;
+}
+
+int64_t riot_sketchnet_num_params(const riot_sketchnet *net) { return net ? net->net.num_params() : -1; }
+
+riot_status riot_sketchnet_set_params(riot_sketchnet *net, const float *params_dev)
+{
+    if (!net || !params_dev) return RIOT_EINVAL;
+    if (cudaMemcpyAsync(net->params, params_dev, sizeof(float) * net->net.num_params(), cudaMemcpyDeviceToDevice,
+                        net->s) != cudaSuccess)
+        return RIOT_ECUDA;
+    // a new set of weights restarts the optimiser
+    if (cudaMemsetAsync(net->m1, 0, sizeof(float) * net->net.num_params(), net->s) != cudaSuccess ||
+        cudaMemsetAsync(net->m2, 0, sizeof(float) * net->net.num_params(), net->s) != cudaSuccess)
+        return RIOT_ECUDA;
+    net->t = 0;
+    return RIOT_OK;
+}
+
+riot_status riot_sketchnet_get_params(riot_sketchnet *net, float *params_dev)
+{
+    if (!net || !params_dev) return RIOT_EINVAL;
+    return cudaMemcpyAsync(params_dev, net->params, sizeof(float) * net->net.num_params(), cudaMemcpyDeviceToDevice,
+                           net->s) == cudaSuccess
+               ? RIOT_OK
+               : RIOT_ECUDA;
+}
+
+riot_status riot_sketchnet_forward(riot_sketchnet *net, const float *x_dev, int32_t n, int32_t batch, float *Z_dev,
+                                   int32_t bf16)
+{
+    if (!net || !x_dev || !Z_dev || n < net->net.K || n > net->n_max || batch < 1 || batch > net->b_max)
+        return RIOT_EINVAL;
+    return sketchnet_forward(net->net, net->params, x_dev, n, batch, Z_dev, bf16 != 0, net->w.acts, net->s) ==
+                   cudaSuccess
+               ? RIOT_OK
+               : RIOT_ECUDA;
+}
+
+riot_status riot_sketchnet_loss_grad(riot_sketchnet *net, const float *x_dev, const float *U_dev, int32_t r, int32_t n,
+                                     int32_t batch, double mu, float *grad_dev, double *loss_out)
+{
+    if (!net || !x_dev || !U_dev || n < net->net.K || n > net->n_max || batch < 1 || batch > net->b_max || r < 1 ||
+        r > net->r_max)
+        return RIOT_EINVAL;
+    float *g = grad_dev ? grad_dev : net->grad;
+    if (sketchnet_loss_grad(net->net, net->params, x_dev, U_dev, r, n, batch, mu, g, net->loss, net->w, net->s) !=
+        cudaSuccess)
+        return RIOT_ECUDA;
+    if (loss_out) {
+        if (cudaMemcpyAsync(loss_out, net->loss, sizeof(double), cudaMemcpyDeviceToHost, net->s) != cudaSuccess ||
+            cudaStreamSynchronize(net->s) != cudaSuccess)
+            return RIOT_ECUDA;
+    }
+    return RIOT_OK;
+}
+
+riot_status riot_sketchnet_train_step(riot_sketchnet *net, const float *x_dev, const float *U_dev, int32_t r, int32_t n,
+                                      int32_t batch, double mu, float lr, double *loss_out)
+{
+    riot_status st = riot_sketchnet_loss_grad(net, x_dev, U_dev, r, n, batch, mu, nullptr, nullptr);
+    if (st != RIOT_OK) return st;
+    net->t += 1;
+    if (sketchnet_adam(net->net, net->params, net->grad, net->m1, net->m2, net->t, lr, net->s) != cudaSuccess)
+        return RIOT_ECUDA;
+    if (loss_out) {
+        if (cudaMemcpyAsync(loss_out, net->loss, sizeof(double), cudaMemcpyDeviceToHost, net->s) != cudaSuccess ||
+            cudaStreamSynchronize(net->s) != cudaSuccess)
+            return RIOT_ECUDA;
+    }
+    return RIOT_OK;
+}
+
+riot_status riot_sketchnet_input(const double *traj_dev, int32_t T, int64_t n, int32_t c_in, float *x_dev,
+                                 void *cuda_stream)
+{
+    if (!traj_dev || !x_dev || T < 0 || n < 1 || c_in < 1) return RIOT_EINVAL;
+    double *st = nullptr;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (cudaMalloc(&st, 2 * sizeof(double)) != cudaSuccess) return RIOT_ENOMEM;
+    cudaError_t e = sketchnet_input(traj_dev, T, n, c_in, x_dev, st, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(st);
+    return e == cudaSuccess ? RIOT_OK : RIOT_ECUDA;
+}
+
+void riot_sketchnet_destroy(riot_sketchnet *net)
+{
+    if (!net) return;
+    if (net->s) cudaStreamSynchronize(net->s);
+    for (void *p : net->allocs) cudaFree(p);
+    delete net;
+}
+
+riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const float *P_dev, int32_t m,
+                               double rho_max, double *lambda_out, double *rho_out, int32_t *used_out)
+{
+    if (!ctx) return RIOT_EINVAL;
+    TRY(rsvd_check_args(ctx, k, q));
+    if (ctx->prec != RIOT_PREC_MIXED) return fail(ctx, RIOT_EINVAL, "riot_rsvd_proposal: mixed-precision contexts only");
+    if (m < 0 || m > k || (m > 0 && !P_dev)) return fail(ctx, RIOT_EINVAL, "m = %d outside [0, k] or null proposal", m);
+    CU(cudaSetDevice(ctx->dev));
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    float *W32 = (float *)ctx->Wblk, *Y32 = (float *)ctx->Yblk;
+    ctx->nev = 0;
+    ev_mark(ctx, -1);
+    int used = 0;
+    double rho = -1.0;
+    if (m > 0) {
+        CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 32, s));
+        // the proposal, orthonormalised, then Gaussian columns for the rest of the sketch
+        TRY(orth32(ctx, P_dev, m, 16, 3, 2));
+        CU(cudaMemcpyAsync(W32, ctx->Q32, sizeof(float) * (size_t)n * m, cudaMemcpyDeviceToDevice, s));
+        if (k > m) CU(normal_launch(ctx->seed, (uint32_t)sketch_stream, n, k - m, n, 0, W32 + (size_t)n * m, s));
+        ev_mark(ctx, 0);
+        TRY(hvp(ctx, W32, Y32, n, k, 0));
+        // Rayleigh residual of the proposed block: rho^2 = 1 - ||Q^T A Q||_F^2 / ||A Q||_F^2
+        CU(sgemm('T', 'N', m, m, n, 1.f, W32, n, Y32, n, 0.f, ctx->N32, m, s));
+        CU(cudaMemsetAsync(ctx->nrm, 0, 4 * sizeof(double), s));
+        CU(sumsq(ctx->N32, (size_t)m * m, ctx->nrm, s));
+        CU(sumsq(Y32, (size_t)n * m, ctx->nrm + 1, s));
+        double h[2] = {0, 0};
+        int oi[3] = {0, 0, 0};
+        CU(cudaMemcpyAsync(h, ctx->nrm, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(oi, ctx->info + 16, sizeof(oi), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (h[1] > 0.0 && isfinite(h[0]) && isfinite(h[1])) rho = sqrt(fmax(0.0, 1.0 - h[0] / h[1]));
+        used = (rho >= 0.0 && rho <= rho_max && oi[0] == 0 && oi[1] == 0 && oi[2] == 0);
+    }
+    if (!used) {
+        TRY(rsvd_begin(ctx, k, sketch_stream, nullptr));
+        ev_mark(ctx, 0);
+        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
+    }
+    for (int it = 0; it < q; ++it) {
+        ev_mark(ctx, 1);
+        TRY(rsvd_power(ctx, k));
+        ev_mark(ctx, 0);
+        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
+    }
+    TRY(rsvd_end(ctx, k, true));
+    ev_mark(ctx, -2);
+    if (rho_out) *rho_out = rho;
+    if (used_out) *used_out = used;
+    return rsvd_collect(ctx, k, lambda_out);
 }
 
 }  // extern "C"

@@ -164,6 +164,35 @@ cudaError_t adv_bsqrt(const AdvDev &m, const double *in, double *out, int ncols,
 cudaError_t adv_forecast(const AdvDev &m, const double *x, int steps, double *c_out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// Learned sketch proposal (sketchnet.cu)
+// ---------------------------------------------------------------------------
+struct SketchNet {
+    int c_in = 0, width = 0, m = 0, depth = 0, K = 0;
+    int chan[9] = {0};   // channels of layer inputs/outputs: c_in, width .. width, m
+    int64_t num_params() const;
+    int64_t w_offset(int l) const;   // offset of layer l's weights in the flat vector
+};
+struct SketchWork {
+    float *Z = nullptr, *acts = nullptr, *gZ = nullptr, *g0 = nullptr, *g1 = nullptr;
+    float *R = nullptr, *UtX = nullptr, *G = nullptr, *E = nullptr, *XE = nullptr;
+    double *sc = nullptr;   // 4 doubles per window
+};
+// Z (B x m x n) from x (B x c_in x n); hidden activations into acts ((depth-1) x B x width x n)
+cudaError_t sketchnet_forward(const SketchNet &net, const float *params, const float *x, int n, int B, float *Z,
+                              bool bf16, float *acts, cudaStream_t s);
+// mean subspace loss over B windows (targets U: B x r x n, orthonormal columns) into *loss_dev
+// and its parameter gradient into grad
+cudaError_t sketchnet_loss_grad(const SketchNet &net, const float *params, const float *x, const float *U, int r,
+                                int n, int B, double mu, float *grad, double *loss_dev, SketchWork &w,
+                                cudaStream_t s);
+cudaError_t sketchnet_adam(const SketchNet &net, float *params, const float *grad, float *m1, float *m2, int t,
+                           float lr, cudaStream_t s);
+// x (C x n) = standardised snapshots of traj ((T+1) x n, FP64) at steps floor(c T / C); st: 2 doubles
+cudaError_t sketchnet_input(const double *traj, int T, int64_t n, int C, float *x, double *st, cudaStream_t s);
+// out[0] += sum of squares of x (double accumulation)
+cudaError_t sumsq(const float *x, size_t n, double *out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // Random numbers (rng.cu)
 // ---------------------------------------------------------------------------
 cudaError_t normal_launch(uint64_t seed, uint32_t stream, int64_t n, int ncols, int64_t ld,

@@ -109,12 +109,30 @@ def load():
     L.riot_batch_last_error.restype = c_char_p
     L.riot_batch_destroy.argtypes = [vp]
     L.riot_batch_destroy.restype = None
+    L.riot_get_trajectory.argtypes = [vp, vp]
+    L.riot_sketchnet_create.argtypes = [POINTER(vp), c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                        c_int32, vp]
+    L.riot_sketchnet_num_params.argtypes = [vp]
+    L.riot_sketchnet_num_params.restype = c_int64
+    L.riot_sketchnet_set_params.argtypes = [vp, vp]
+    L.riot_sketchnet_get_params.argtypes = [vp, vp]
+    L.riot_sketchnet_forward.argtypes = [vp, vp, c_int32, c_int32, vp, c_int32]
+    L.riot_sketchnet_loss_grad.argtypes = [vp, vp, vp, c_int32, c_int32, c_int32, c_double, vp, POINTER(c_double)]
+    L.riot_sketchnet_train_step.argtypes = [vp, vp, vp, c_int32, c_int32, c_int32, c_double, ctypes.c_float,
+                                            POINTER(c_double)]
+    L.riot_sketchnet_input.argtypes = [vp, c_int32, c_int64, c_int32, vp, vp]
+    L.riot_sketchnet_destroy.argtypes = [vp]
+    L.riot_sketchnet_destroy.restype = None
+    L.riot_rsvd_proposal.argtypes = [vp, c_int32, c_int32, c_int64, vp, c_int32, c_double, POINTER(c_double),
+                                     POINTER(c_double), POINTER(c_int32)]
     for name in ("riot_setup", "riot_outer_begin", "riot_hessian_apply", "riot_hessian_apply_noalloc",
                  "riot_rsvd", "riot_increment",
                  "riot_analysis_cov_lowrank", "riot_bsqrt_apply", "riot_get_state", "riot_draw_normal",
                  "riot_l96_forecast", "riot_rsvd_timings", "riot_symm_eig", "riot_get_innovation",
                  "riot_batch_create", "riot_batch_autotune", "riot_batch_set_config", "riot_batch_hessian_apply",
-                 "riot_batch_run"):
+                 "riot_batch_run", "riot_get_trajectory", "riot_sketchnet_create", "riot_sketchnet_set_params",
+                 "riot_sketchnet_get_params", "riot_sketchnet_forward", "riot_sketchnet_loss_grad",
+                 "riot_sketchnet_train_step", "riot_sketchnet_input", "riot_rsvd_proposal"):
         getattr(L, name).restype = c_int32
     _lib = L
     return L
@@ -336,6 +354,88 @@ def riot_batch_run(b, nwin, sketch_stream=0, use_graph=True, check=True):
 def riot_batch_destroy(b):
     if b:
         load().riot_batch_destroy(b)
+
+
+def _need_contiguous(*ts):
+    for t in ts:
+        if t is not None and not t.is_contiguous():
+            raise ValueError("tensor arguments must be contiguous (the C ABI takes plain pointers)")
+
+
+def riot_get_trajectory(ctx, traj):
+    _check(ctx, "riot_get_trajectory", load().riot_get_trajectory(ctx, _ptr(traj)))
+
+
+def riot_sketchnet_create(c_in, width, m_out, depth=4, ksize=5, n_max=4096, batch_max=8, r_max=None, stream=None):
+    h = c_void_p()
+    r_max = m_out if r_max is None else r_max
+    _check(None, "riot_sketchnet_create",
+           load().riot_sketchnet_create(ctypes.byref(h), int(c_in), int(width), int(m_out), int(depth), int(ksize),
+                                        int(n_max), int(batch_max), int(r_max), _stream_handle(stream)))
+    return h
+
+
+def riot_sketchnet_num_params(net):
+    return int(load().riot_sketchnet_num_params(net))
+
+
+def riot_sketchnet_set_params(net, params):
+    _check(None, "riot_sketchnet_set_params", load().riot_sketchnet_set_params(net, _ptr(params)))
+
+
+def riot_sketchnet_get_params(net, params):
+    _check(None, "riot_sketchnet_get_params", load().riot_sketchnet_get_params(net, _ptr(params)))
+
+
+def riot_sketchnet_forward(net, x, Z, bf16=False):
+    """x: (B, c_in, n) float32, Z: (B, m, n) float32 (device tensors)."""
+    _need_contiguous(x, Z)
+    B, _, n = x.shape
+    _check(None, "riot_sketchnet_forward", load().riot_sketchnet_forward(net, _ptr(x), int(n), int(B), _ptr(Z),
+                                                                          int(bool(bf16))))
+
+
+def riot_sketchnet_loss_grad(net, x, U, mu, grad=None):
+    """U: (B, r, n) float32 orthonormal targets; returns the mean loss."""
+    _need_contiguous(x, U, grad)
+    B, _, n = x.shape
+    L = c_double(0.0)
+    _check(None, "riot_sketchnet_loss_grad",
+           load().riot_sketchnet_loss_grad(net, _ptr(x), _ptr(U), int(U.shape[1]), int(n), int(B), float(mu),
+                                           _ptr(grad), ctypes.byref(L)))
+    return L.value
+
+
+def riot_sketchnet_train_step(net, x, U, mu, lr):
+    _need_contiguous(x, U)
+    B, _, n = x.shape
+    L = c_double(0.0)
+    _check(None, "riot_sketchnet_train_step",
+           load().riot_sketchnet_train_step(net, _ptr(x), _ptr(U), int(U.shape[1]), int(n), int(B), float(mu),
+                                            float(lr), ctypes.byref(L)))
+    return L.value
+
+
+def riot_sketchnet_input(traj, T, n, c_in, x, stream=None):
+    _check(None, "riot_sketchnet_input", load().riot_sketchnet_input(_ptr(traj), int(T), int(n), int(c_in), _ptr(x),
+                                                                      _stream_handle(stream)))
+
+
+def riot_sketchnet_destroy(net):
+    if net:
+        load().riot_sketchnet_destroy(net)
+
+
+def riot_rsvd_proposal(ctx, k, q, P, m, rho_max=1e-2, sketch_stream=0):
+    """riot_rsvd with the proposal P (m, n) float32; returns (lam, rho, used)."""
+    _need_contiguous(P)
+    lam = (c_double * k)()
+    rho = c_double(-1.0)
+    used = c_int32(0)
+    _check(ctx, "riot_rsvd_proposal",
+           load().riot_rsvd_proposal(ctx, int(k), int(q), int(sketch_stream), _ptr(P), int(m), float(rho_max), lam,
+                                     ctypes.byref(rho), ctypes.byref(used)))
+    return np.array(lam[:]), rho.value, used.value
 
 
 class Context:
