@@ -49,10 +49,11 @@ struct riot_ctx {
     int *info = nullptr;  // [0..9] CholeskyQR passes, [10] K Cholesky, [12..13] Jacobi, [14] mode
     int *errflag = nullptr;  // set by a kernel whose bounded wait ran out
     int have_traj = 0, have_rsvd = 0, k_last = 0, v_init = 0, jacobi_sweeps = 0;
-    // FP32 Hessian products are formed as 2^-scale_exp A (R^-1 scaled in rinv32) so that
-    // windows whose tangent-linear growth squared exceeds the FP32 range stay finite;
-    // eigenvalues are scaled back in FP64.
-    int scale_exp = 0;
+    // FP32 Hessian products are formed as 2^-scale_exp A (R^-1 scaled by 2^-scale_rinv in
+    // rinv32, the input and output by 2^-scale_in through sig32) so that windows whose
+    // tangent-linear growth exceeds the FP32 range stay finite; eigenvalues are scaled
+    // back in FP64.
+    int scale_exp = 0, scale_in = 0, scale_rinv = 0;
     double *nrm = nullptr;   // 4 doubles of norm accumulators
     // timing
     cudaEvent_t ev[32];
@@ -658,14 +659,29 @@ riot_status choose_scale(riot_ctx *ctx)
     double h[2] = {0.0, 0.0};
     CU(cudaMemcpyAsync(h, ctx->nrm, sizeof(h), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    int c = 0;
+    // e = log2 of the bound.  The tangent-linear states grow like 2^(e/2) and the adjoint states
+    // like 2^e: beyond 2^100 the input is scaled by 2^-a (in sigma, which also scales the L^T of
+    // the output) and R^-1 by 2^-c, so that both stay below 2^100 and the products are
+    // 2^-(2a + c) A.  2^-c must stay a normal FP32 number: windows beyond that need FP64.
+    int a = 0, c = 0;
     if (h[0] > 0.0 && h[1] > 0.0 && isfinite(h[1])) {
         const double est = sqrt(h[1] / h[0]) * sqrt((double)n) * 16.0;
         const int e = (int)ceil(log2(est));
-        c = e > 96 ? e - 96 : 0;
+        const int eh = (e + 1) / 2;
+        a = eh > 100 ? eh - 100 : 0;
+        c = e - a > 100 ? e - a - 100 : 0;
+    } else if (!isfinite(h[1])) {
+        return fail(ctx, RIOT_ENONFINITE, "the FP64 Hessian product overflowed: the window is beyond any precision");
     }
-    if (c != ctx->scale_exp || c > 0) CU(scale_to_f32(ctx->p, ctx->rinv64, ldexp(1.0, -c), ctx->rinv32, s));
-    ctx->scale_exp = c;
+    if (c > 120)
+        return fail(ctx, RIOT_ENONFINITE,
+                    "tangent-linear growth of this window (about 2^%d in the Hessian) is beyond the FP32 range; "
+                    "use RIOT_PREC_FP64", a + c + 100);
+    if (c != ctx->scale_rinv || c > 0) CU(scale_to_f32(ctx->p, ctx->rinv64, ldexp(1.0, -c), ctx->rinv32, s));
+    if (a != ctx->scale_in || a > 0) CU(scale_to_f32(n, ctx->sig64, ldexp(1.0, -a), ctx->sig32, s));
+    ctx->scale_rinv = c;
+    ctx->scale_in = a;
+    ctx->scale_exp = 2 * a + c;
     return RIOT_OK;
 }
 

@@ -155,3 +155,24 @@ def test_window_beyond_the_fp32_range(gpu_lib):
     assert l64[0] > 1e39            # beyond what an unscaled FP32 product can hold
     assert np.all(np.isfinite(lm))
     np.testing.assert_allclose(lm[:4], l64[:4], rtol=1e-3)
+
+
+def test_window_beyond_any_fp32_scaling_is_refused(gpu_lib):
+    """F = 16 over 600 steps: the Hessian reaches ~2^390, beyond what one
+    power-of-two scaling of FP32 products can hold.  The mixed path must say so
+    at riot_outer_begin (RIOT_ENONFINITE) instead of returning garbage; the
+    FP64 path handles the window."""
+    R = gpu_lib
+    from paper_1906_01413_gb300 import workloads
+    cfg = configs.L96Config(name="stronger", n=48, F=16.0, T=600, obs_every=8, obs_frac=0.5, obs_layout="random",
+                            ell=4.0, k=8, q=1, spinup=300, seed=configs.BASE_SEED + 78)
+    ctx, xb, _ = workloads.l96_twin(R, torch, cfg, DEV, R.RIOT_PREC_MIXED, cfg.k)
+    with pytest.raises(R.RiotError) as e:
+        R.riot_outer_begin(ctx.h, xb)
+    assert e.value.status == -8 and "FP64" in str(e.value)
+    ctx.close()
+    ctx, xb, _ = workloads.l96_twin(R, torch, cfg, DEV, R.RIOT_PREC_FP64, cfg.k)
+    R.riot_outer_begin(ctx.h, xb)
+    lam = R.riot_rsvd(ctx.h, cfg.k, cfg.q, sketch_stream=3)
+    assert np.all(np.isfinite(lam)) and lam[0] > 1e70
+    ctx.close()
