@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-bc", action="store_true", help="skip the tracer-transport Hessian products")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch of 96 windows")
-    ap.add_argument("--only", choices=["bc", "batch"], default=None,
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned sketch proposal leg")
+    ap.add_argument("--only", choices=["bc", "batch", "learned"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling)")
     ap.add_argument("--bc-cols", type=int, default=128, help="sketch columns per tracer Hessian call")
     ap.add_argument("--profile", action="store_true",
@@ -300,6 +301,125 @@ def bench_batch(R, torch, dev, warmup, steps, fp64_baseline=True):
     return out
 
 
+def bench_learned_sketch(R, torch, dev, n_train=64, n_test=8, steps=500):
+    """Learned sketch proposal on Lorenz-96 n=4096, F=12, T=300 windows: a
+    periodic conv-net (4 layers, 64 channels, 8 input snapshots, 128
+    directions) trained on the leading 128 eigenvectors that riot_rsvd (k=512
+    Gaussian, q=1) produced on n_train windows, then used on n_test unseen
+    windows as [128 proposed | k - 128 Gaussian] sketches, gated by the
+    Rayleigh residual (rho <= 1e-2, else pure Gaussian).  Reports the cost
+    reduction of the resulting increments against Gaussian sketches."""
+    from paper_1906_01413_gb300 import workloads
+    n, T, m, C, width = 4096, 300, 128, 8, 64
+    ks = [128, 256, 384, 512]
+
+    def wcfg(w):
+        # the workload gives no step length: the paper's Lorenz-96 step dt = 0.01 (Section 3.1)
+        return configs.L96Config(name="ls%d" % w, n=n, F=12.0, dt=0.01, T=T, obs_every=4, obs_frac=0.25,
+                                 obs_layout="random", ell=4.0, k=512, q=1, seed=configs.BASE_SEED + 5000 + w)
+
+    def window(w):
+        cfg = wcfg(w)
+        ctx, xb, _ = workloads.l96_twin(R, torch, cfg, dev, R.RIOT_PREC_MIXED, 512)
+        R.riot_outer_begin(ctx.h, xb)
+        traj = torch.empty(T + 1, n, dtype=torch.float64, device=dev)
+        R.riot_get_trajectory(ctx.h, traj)
+        x = torch.empty(C, n, dtype=torch.float32, device=dev)
+        R.riot_sketchnet_input(traj, T, n, C, x)
+        return ctx, x
+
+    t0 = time.perf_counter()
+    xs, Us = [], []
+    for w in range(n_train):
+        ctx, x = window(w)
+        R.riot_rsvd(ctx.h, 512, 1, sketch_stream=configs.STREAM_SKETCH0)
+        U = torch.empty(512, n, dtype=torch.float64, device=dev)
+        R.riot_get_state(ctx.h, U=U)
+        xs.append(x)
+        Us.append(U[:m].float())
+        ctx.close()
+    X = torch.stack(xs).contiguous()
+    Ut = torch.stack(Us).contiguous()
+    data_s = time.perf_counter() - t0
+    from synth import learned
+    flat = torch.tensor(learned.initial_params(C, width, m).astype(np.float32), device=dev)
+    net = R.riot_sketchnet_create(C, width, m, n_max=n, batch_max=8, r_max=m)
+    R.riot_sketchnet_set_params(net, flat)
+    rng = np.random.default_rng(1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = []
+    for it in range(steps):
+        idx = torch.tensor(rng.choice(n_train, 8, replace=False), device=dev)
+        losses.append(R.riot_sketchnet_train_step(net, X[idx].contiguous(), Ut[idx].contiguous(), 0.1, 2e-3))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+
+    def dJ(ctx64, dv):
+        # reduction of the quadratic inner cost, -(g.dv + |dv|^2/2 + dv.A dv/2), with an FP64
+        # product (these windows' Hessians exceed the FP32 range)
+        g = torch.empty(n, dtype=torch.float64, device=dev)
+        R.riot_get_state(ctx64.h, g=g)
+        w = dv.reshape(1, n).contiguous()
+        Aw = torch.empty_like(w)
+        R.riot_hessian_apply(ctx64.h, w, Aw)
+        return -float(g @ dv + 0.5 * dv @ dv + 0.5 * dv @ Aw[0])
+
+    rows = {"gauss": {k: [] for k in ks}, "proposal_gated": {k: [] for k in ks[1:]},
+            "proposal_ungated": {k: [] for k in ks[1:]}}
+    rhos, used = [], []
+    capture = []
+    for w in range(n_test):
+        ctx, x = window(10000 + w)
+        ctx64, xb64, _ = workloads.l96_twin(R, torch, wcfg(10000 + w), dev, R.RIOT_PREC_FP64, 1)
+        R.riot_outer_begin(ctx64.h, xb64)
+        Z = torch.empty(1, m, n, dtype=torch.float32, device=dev)
+        R.riot_sketchnet_forward(net, x.reshape(1, C, n).contiguous(), Z, bf16=True)
+        P = Z[0].contiguous()
+        dv = torch.empty(n, dtype=torch.float64, device=dev)
+        for k in ks:
+            R.riot_rsvd(ctx.h, k, 1, sketch_stream=configs.STREAM_SKETCH0)
+            if k == 512:
+                U = torch.empty(512, n, dtype=torch.float64, device=dev)
+                R.riot_get_state(ctx.h, U=U)
+                Q, _ = torch.linalg.qr(P.double().T)
+                capture.append(float((U[:m] @ Q).pow(2).sum()) / m)
+            R.riot_increment(ctx.h, dv)
+            rows["gauss"][k].append(dJ(ctx64, dv))
+        for k in ks[1:]:
+            _, rho, u = R.riot_rsvd_proposal(ctx.h, k, 1, P, m, rho_max=1e-2, sketch_stream=configs.STREAM_SKETCH0)
+            R.riot_increment(ctx.h, dv)
+            rows["proposal_gated"][k].append(dJ(ctx64, dv))
+            if k == 256:
+                rhos.append(rho)
+                used.append(u)
+            R.riot_rsvd_proposal(ctx.h, k, 1, P, m, rho_max=1e30, sketch_stream=configs.STREAM_SKETCH0)
+            R.riot_increment(ctx.h, dv)
+            rows["proposal_ungated"][k].append(dJ(ctx64, dv))
+        ctx.close()
+        ctx64.close()
+    R.riot_sketchnet_destroy(net)
+    mean = {key: {k: float(np.mean(v)) for k, v in d.items()} for key, d in rows.items()}
+    target = mean["gauss"][512]
+
+    def k_needed(d):
+        for k in sorted(d):
+            if d[k] >= target * (1 - 1e-3):
+                return k
+        return None
+
+    return {"workload": "l96_n4096_F12_dt0.01_T300_obs25pct_every4_proposal128", "train_windows": n_train,
+            "test_windows": n_test, "train_steps": steps, "net": "4 periodic conv layers, 64 channels, kernel 5, "
+            "8 snapshots -> 128 directions, FP32 training, BF16 inference",
+            "data_s": data_s, "train_s": train_s, "loss_first": losses[0], "loss_last": losses[-1],
+            "held_out_capture_of_leading_128": float(np.mean(capture)), "random_capture": m / n,
+            "rho_at_k256": rhos, "proposal_used_at_k256": used,
+            "mean_cost_reduction": {key: {str(k): v for k, v in d.items()} for key, d in mean.items()},
+            "k_for_gauss512_reduction": {"gauss": k_needed(mean["gauss"]),
+                                         "proposal_gated": k_needed(mean["proposal_gated"]),
+                                         "proposal_ungated": k_needed(mean["proposal_ungated"])}}
+
+
 def cpu_oracle_hvps(cfg, seconds, min_cols=2):
     """FP64 CPU oracle Hessian-vector products on the same workload, single thread."""
     from oracle import problem, riot as orc
@@ -375,7 +495,9 @@ def main():
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         if args.profile:
             torch.cuda.profiler.start()
-        if args.only == "bc":
+        if args.only == "learned":
+            out = bench_learned_sketch(R, torch, dev)
+        elif args.only == "bc":
             out = bench_bc_transport(R, torch, dev, flush, float(peaks.get("hbm_gbs", 6800.0)), ncols=args.bc_cols,
                                      reps=max(1, args.steps))
         else:
@@ -447,6 +569,9 @@ def main():
     e2e_s = statistics.mean(e2e_times)
 
     # ---- tracer-transport inversion (workload 3): Hessian products on the full grid ----
+    learned = None
+    if not args.no_learned:
+        learned = bench_learned_sketch(R, torch, dev)
     batch = None
     if not args.no_batch:
         batch = bench_batch(R, torch, dev, args.warmup, max(3, args.steps // 3))
@@ -494,6 +619,8 @@ def main():
         line["bc_transport"] = bc
     if batch:
         line["batch_windows"] = batch
+    if learned:
+        line["learned_sketch"] = learned
     cs = clk.summary()
     if cs:
         line["clocks"] = cs

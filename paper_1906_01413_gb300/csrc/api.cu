@@ -36,6 +36,7 @@ struct riot_ctx {
     float *rinv32 = nullptr, *band32 = nullptr, *sig32 = nullptr;
     // outer-loop state
     double *x = nullptr, *v = nullptr, *g = nullptr, *dv = nullptr, *tmp = nullptr;
+    double *xsave = nullptr, *vsave = nullptr;   // x, v before a batched inner loop (to redo one window)
     double *traj = nullptr, *d = nullptr, *rd = nullptr, *jo = nullptr;
     float2 *coef32 = nullptr;
     double2 *coef64 = nullptr;
@@ -54,6 +55,7 @@ struct riot_ctx {
     // tangent-linear growth exceeds the FP32 range stay finite; eigenvalues are scaled
     // back in FP64.
     int scale_exp = 0, scale_in = 0, scale_rinv = 0;
+    int k_shift = 0;   // shift the K normal equations (set for one retry after a failed solve)
     double *nrm = nullptr;   // 4 doubles of norm accumulators
     // timing
     cudaEvent_t ev[32];
@@ -619,6 +621,7 @@ riot_status setup_common(riot_ctx *ctx)
     riot_status st;
     if ((st = dalloc(ctx, &ctx->x, np)) || (st = dalloc(ctx, &ctx->v, np)) || (st = dalloc(ctx, &ctx->g, np)) ||
         (st = dalloc(ctx, &ctx->dv, np)) || (st = dalloc(ctx, &ctx->tmp, np)) || (st = dalloc(ctx, &ctx->d, p)) ||
+        (st = dalloc(ctx, &ctx->xsave, np)) || (st = dalloc(ctx, &ctx->vsave, np)) ||
         (st = dalloc(ctx, &ctx->rd, p)) || (st = dalloc(ctx, &ctx->jo, 2)) ||
         (st = dalloc(ctx, (char **)&ctx->Wblk, np * k * rs)) || (st = dalloc(ctx, (char **)&ctx->Yblk, np * k * rs)) ||
         (st = dalloc(ctx, &ctx->Q, np * k)) || (st = dalloc(ctx, &ctx->U, np * k)) ||
@@ -790,7 +793,11 @@ riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
         }
         CU(gemm('N', 'T', k, k, k, 1.0, ctx->Mm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->G, 'd', k, s));
         CU(gemm('N', 'T', k, k, k, 1.0, ctx->Nm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->Km, 'd', k, s));
-        CU(cholesky(ctx->G, k, k, 0.0, ctx->info + 10, ctx->gws, s));
+        // M M^T is singular to working precision when the window's spectrum spans more than the
+        // precision (A Q0 then loses Q0's trailing directions): a retry with a shift of the order
+        // of the Cholesky backward error (8 k u tr) keeps the solve defined (see rsvd_retry_k)
+        const double ushift = ctx->k_shift ? 8.0 * k * ldexp(1.0, -53) : 0.0;
+        CU(cholesky(ctx->G, k, k, ushift, ctx->info + 10, ctx->gws, s));
         CU(trsm_right_lt(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
         CU(trsm_right_l(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
     }
@@ -824,6 +831,22 @@ riot_status rsvd_collect(riot_ctx *ctx, int k, double *lambda_out)
     ctx->have_rsvd = 1;
     ctx->k_last = k;
     return RIOT_OK;
+}
+
+// When the unshifted Cholesky of the K normal equations failed (info[10]), redo the end of the
+// inner loop with the shifted solve; the blocks Q0 (W) and Y are unchanged by rsvd_end.
+riot_status rsvd_retry_k(riot_ctx *ctx, int k, double *lambda_out, riot_status st)
+{
+    if (st != RIOT_ENOTSPD) return st;
+    int i10 = 0;
+    CU(cudaMemcpyAsync(&i10, ctx->info + 10, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    if (i10 == 0) return st;
+    ctx->k_shift = 1;
+    riot_status st2 = rsvd_end(ctx, k, true);
+    ctx->k_shift = 0;
+    if (st2 != RIOT_OK) return st2;
+    return rsvd_collect(ctx, k, lambda_out);
 }
 
 // Adaptive increment (queued, no synchronisation): dv, v += dv, x += L dv.
@@ -884,7 +907,14 @@ riot_status batch_enqueue(riot_batch *b, int64_t sketch_stream)
     };
     do {
         if (!fork()) break;
-        for (int w = 0; w < nw && st == RIOT_OK; ++w) st = rsvd_begin(b->ctx[w], b->k[w], sketch_stream, nullptr);
+        for (int w = 0; w < nw && st == RIOT_OK; ++w) {
+            riot_ctx *c = b->ctx[w];
+            if ((e = cudaMemcpyAsync(c->xsave, c->x, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->s)) ||
+                (e = cudaMemcpyAsync(c->vsave, c->v, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->s)))
+                break;
+            st = rsvd_begin(c, b->k[w], sketch_stream, nullptr);
+        }
+        if (e != cudaSuccess) break;
         if (st != RIOT_OK || !join()) break;
         if ((e = hvp_batch_launch(b->plan, b->main)) != cudaSuccess) break;
         for (int it = 0; it < b->q && st == RIOT_OK && e == cudaSuccess; ++it) {
@@ -1115,7 +1145,7 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
     }
     TRY(rsvd_end(ctx, k, true));
     ev_mark(ctx, -2);
-    return rsvd_collect(ctx, k, lambda_out);
+    return rsvd_retry_k(ctx, k, lambda_out, rsvd_collect(ctx, k, lambda_out));
 }
 
 riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6)
@@ -1434,6 +1464,18 @@ riot_status riot_batch_run(riot_batch *b, int64_t sketch_stream, int32_t use_gra
     riot_status first = RIOT_OK;
     for (int w = 0; w < nw; ++w) {
         riot_status st = rsvd_collect(b->ctx[w], b->k[w], nullptr);
+        if (st == RIOT_ENOTSPD) {
+            // redo this window's end of the inner loop alone with the shifted K solve, then its
+            // increment from the state it had before the batch ran
+            riot_ctx *c = b->ctx[w];
+            if (cudaMemcpyAsync(c->x, c->xsave, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->s) != cudaSuccess ||
+                cudaMemcpyAsync(c->v, c->vsave, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->s) != cudaSuccess)
+                st = RIOT_ECUDA;
+            else
+                st = rsvd_retry_k(c, b->k[w], nullptr, st);
+            if (st == RIOT_OK) st = increment_queue(b->ctx[w], b->k[w]);
+            if (st == RIOT_OK && cudaStreamSynchronize(b->ctx[w]->s) != cudaSuccess) st = RIOT_ECUDA;
+        }
         if (status_out) status_out[w] = st;
         if (st != RIOT_OK && first == RIOT_OK) {
             first = st;
@@ -1666,7 +1708,7 @@ riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sket
     ev_mark(ctx, -2);
     if (rho_out) *rho_out = rho;
     if (used_out) *used_out = used;
-    return rsvd_collect(ctx, k, lambda_out);
+    return rsvd_retry_k(ctx, k, lambda_out, rsvd_collect(ctx, k, lambda_out));
 }
 
 }  // extern "C"
