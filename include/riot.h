@@ -393,6 +393,16 @@ riot_status riot_get_trajectory(riot_ctx *ctx, double *traj_dev);
 riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const float *P_dev, int32_t m,
                                double rho_max, double *lambda_out, double *rho_out, int32_t *used_out);
 
+/* The FP32 sketch GEMM of the mixed-precision path on its own, for checks:
+ * C = alpha op(A) op(B) + beta C (column-major FP32, op 'N' or 'T') on the
+ * tcgen05 tensor cores, each operand split into three BF16 terms and the six
+ * leading term products accumulated in FP32 (FP32 accuracy).  Allocates and
+ * frees its own workspace; synchronises the stream.  RIOT_ETIMEOUT if a
+ * bounded wait on the tensor cores ran out. */
+riot_status riot_tc_sgemm(char ta, char tb, int32_t m, int32_t n, int32_t k, float alpha, const float *A_dev,
+                          int64_t lda, const float *B_dev, int64_t ldb, float beta, float *C_dev, int64_t ldc,
+                          void *cuda_stream);
+
 const char *riot_last_error(const riot_ctx *ctx);
 const char *riot_status_string(riot_status s);
 void riot_destroy(riot_ctx *ctx);

@@ -1711,4 +1711,32 @@ riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sket
     return rsvd_retry_k(ctx, k, lambda_out, rsvd_collect(ctx, k, lambda_out));
 }
 
+riot_status riot_tc_sgemm(char ta, char tb, int32_t m, int32_t n, int32_t k, float alpha, const float *A_dev,
+                          int64_t lda, const float *B_dev, int64_t ldb, float beta, float *C_dev, int64_t ldc,
+                          void *cuda_stream)
+{
+    if (m < 0 || n < 0 || k < 0 || (ta != 'N' && ta != 'T') || (tb != 'N' && tb != 'T')) return RIOT_EINVAL;
+    if (m == 0 || n == 0) return RIOT_OK;
+    if (!A_dev || !B_dev || !C_dev || ldc < m || lda < (ta == 'N' ? m : k) || ldb < (tb == 'N' ? k : n))
+        return RIOT_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t wsf = tc_sgemm_ws_floats(m, n, k);
+    float *ws = nullptr;
+    int *err = nullptr;
+    if (wsf && cudaMalloc(&ws, wsf * sizeof(float)) != cudaSuccess) return RIOT_ENOMEM;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaFree(ws);
+        return RIOT_ENOMEM;
+    }
+    int herr = 0;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = tc_sgemm(ta, tb, m, n, k, alpha, A_dev, lda, B_dev, ldb, beta, C_dev, ldc, ws, wsf, err, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(ws);
+    cudaFree(err);
+    if (e != cudaSuccess) return RIOT_ECUDA;
+    return herr ? RIOT_ETIMEOUT : RIOT_OK;
+}
+
 }  // extern "C"

@@ -212,6 +212,14 @@ cudaError_t gram_lower(int n, int k, const void *A, char tA, int64_t lda, double
 // FP32 SIMT GEMM, C = alpha op(A) op(B) + beta C
 cudaError_t sgemm(char ta, char tb, int m, int n, int k, float alpha, const float *A, int64_t lda, const float *B,
                   int64_t ldb, float beta, float *C, int64_t ldc, cudaStream_t s);
+// FP32-accurate GEMM on tcgen05 tensor cores (three BF16 terms per value, six MMAs per
+// K step, FP32 accumulation in tensor memory): C = alpha op(A) op(B) + beta C,
+// column-major.  ws (tc_sgemm_ws_floats floats, may be null) holds split-K partial tiles;
+// err is set if a bounded wait on the MMAs ran out.
+cudaError_t tc_sgemm(char ta, char tb, int m, int n, int k, float alpha, const float *A, int64_t lda, const float *B,
+                     int64_t ldb, float beta, float *C, int64_t ldc, float *ws, size_t ws_floats, int *err,
+                     cudaStream_t s);
+size_t tc_sgemm_ws_floats(int m, int n, int k);
 // X <- X L^-T in FP32 (L: k x k lower, FP32)
 cudaError_t strsm_right_lt(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s);
 cudaError_t convert_block(const void *in, char tin, int64_t ldin, void *out, char tout, int64_t ldout,

@@ -1,0 +1,330 @@
+// FP32-accurate GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// C = alpha op(A) op(B) + beta C, column-major FP32 operands.  Each FP32
+// value is split into three BF16 terms a = a1 + a2 + a3 (8 significant bits
+// each, together the 24 of FP32), and the products a_i b_j with i + j <= 4
+// (six tcgen05.mma per K step) are accumulated in FP32 in tensor memory: the
+// result has FP32 accuracy at tensor-core speed.  This is how the sketch GEMMs
+// of the randomized eigendecomposition (Q^T W, Q^T Y, U = Q Z) run in mixed
+// precision.
+//
+// One CTA of 128 threads owns a 128 x 128 tile of C (its FP32 accumulator in
+// 128 TMEM columns) and a slice of K (split-K over blockIdx.z, partial tiles
+// reduced by a second kernel).  Per 64-wide K chunk the threads load the
+// FP32 tiles (any transpose), split them and store the BF16 terms in shared
+// memory in the canonical K-major core-matrix layout (8 rows x 16 bytes per
+// core matrix, no swizzle); one thread issues the MMAs and commits them to an
+// mbarrier that the CTA waits on (bounded) before refilling shared memory.
+// The epilogue reads the accumulator with tcgen05.ld (each warp its 32 lanes).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace riot {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int kSplits = 3;                         // BF16 terms per FP32 value
+constexpr int kTileBytes = BM * BK * 2;            // one BF16 term of one operand tile (16 KB)
+// 32 KB of slack past the last tile keeps every address an MMA could form from
+// these descriptors inside the CTA's allocation
+constexpr int kSmemBytes = 2 * kSplits * kTileBytes + 32768 + 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle.  LBO = byte distance
+// between core matrices adjacent in K, SBO = between core matrices adjacent
+// in M (or N); addresses and offsets in 16-byte units; bits 46-47 = 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (r, k) of a 128 x 64 K-major tile in core-matrix
+// layout: core (r / 8, k / 8) at ((k / 8) * 16 + r / 8) * 128, rows 16 bytes.
+__device__ __forceinline__ uint32_t core_off(int r, int k)
+{
+    return (uint32_t)((((k >> 3) * 16 + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ void split3(float v, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c)
+{
+    a = __float2bfloat16(v);
+    const float r1 = v - __bfloat162float(a);
+    b = __float2bfloat16(r1);
+    c = __float2bfloat16(r1 - __bfloat162float(b));
+}
+
+// Load a 128 x 64 tile of X (element (r, k) at X[k + r ld] when k_contig, else
+// X[r + k ld]), rows r0.., k0.., zero outside rows x kvalid, split into three
+// BF16 terms stored at dst + s * kTileBytes.
+__device__ __forceinline__ void load_tile(const float *X, long long ld, bool k_contig, int r0, int rows, int k0,
+                                          int kvalid, unsigned char *dst)
+{
+    const int tid = threadIdx.x;
+    if (k_contig) {
+        // 8 threads per row, 8 consecutive k each: one core-matrix row per thread
+        for (int p = 0; p < BM / 16; ++p) {
+            const int r = p * 16 + tid / 8, kq = (tid & 7) * 8;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int gr = r0 + r, gk = k0 + kq + q;
+                v[q] = (gr < rows && gk < kvalid) ? X[(long long)gk + (long long)gr * ld] : 0.f;
+            }
+            __align__(16) __nv_bfloat16 t[kSplits][8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) split3(v[q], t[0][q], t[1][q], t[2][q]);
+            const uint32_t off = core_off(r, kq);
+#pragma unroll
+            for (int s = 0; s < kSplits; ++s)
+                *reinterpret_cast<uint4 *>(dst + s * kTileBytes + off) = *reinterpret_cast<const uint4 *>(t[s]);
+        }
+    } else {
+        // one row per thread, rows contiguous in memory across the warp
+        const int r = tid;
+        const int gr = r0 + r;
+        for (int kq = 0; kq < BK; kq += 8) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int gk = k0 + kq + q;
+                v[q] = (gr < rows && gk < kvalid) ? X[(long long)gr + (long long)gk * ld] : 0.f;
+            }
+            __align__(16) __nv_bfloat16 t[kSplits][8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) split3(v[q], t[0][q], t[1][q], t[2][q]);
+            const uint32_t off = core_off(r, kq);
+#pragma unroll
+            for (int s = 0; s < kSplits; ++s)
+                *reinterpret_cast<uint4 *>(dst + s * kTileBytes + off) = *reinterpret_cast<const uint4 *>(t[s]);
+        }
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    for (int i = 0; i < (1 << 22); ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (i > 64) __nanosleep(32);
+    }
+    return false;
+}
+
+struct TcArgs {
+    const float *A, *B;
+    float *C;          // output (the workspace when split: slice z at C + z * cslice)
+    long long lda, ldb, ldc, cslice;
+    int M, N, K, kchunk;
+    int a_kcontig, b_kcontig;
+    float alpha, beta;  // applied here only when not split
+    int *err;
+};
+
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;                                  // 3 terms x 16 KB
+    unsigned char *sB = base + kSplits * kTileBytes;           // 3 terms x 16 KB
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_s;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kbeg = blockIdx.z * g.kchunk;
+    const int kend = min(g.K, kbeg + g.kchunk);
+    const uint32_t bar_a = smem_u32(&bar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        abort_s = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+    constexpr uint32_t idesc = instr_desc(BM, BN);
+    const bool has_k = kbeg < kend;
+    float *C = g.C + (long long)blockIdx.z * g.cslice;
+    int phase = 0;
+    bool first = true;
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        load_tile(g.A, g.lda, g.a_kcontig, m0, g.M, k0, kend, sA);
+        load_tile(g.B, g.ldb, g.b_kcontig, n0, g.N, k0, kend, sB);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && !abort_s) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // products a_i b_j with i + j <= 4 (terms counted from 1)
+            const int pa[6] = {0, 0, 1, 0, 1, 2};
+            const int pb[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    const uint32_t a_addr = smem_u32(sA + pa[p] * kTileBytes) + ks * 4096;
+                    const uint32_t b_addr = smem_u32(sB + pb[p] * kTileBytes) + ks * 4096;
+                    const uint64_t ad = smem_desc(a_addr, 2048, 128);
+                    const uint64_t bd = smem_desc(b_addr, 2048, 128);
+                    const uint32_t acc = first ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                    first = false;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
+                         : "memory");
+            if (!mbar_wait_bounded(bar_a, (uint32_t)phase)) {
+                abort_s = 1;
+                atomicExch(g.err, 1);
+            }
+        }
+        phase ^= 1;
+        __syncthreads();   // the MMAs of this chunk have finished reading shared memory
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp w reads lanes 32w..32w+31 (rows), 32 columns at a time
+    const int row = m0 + warp * 32 + (tid & 31);
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < g.M) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = n0 + c0 + j;
+                if (col < g.N) {
+                    float *p = C + row + (long long)col * g.ldc;
+                    const float v = has_k ? __uint_as_float(r[j]) : 0.f;
+                    *p = g.alpha * v + (g.beta != 0.f ? g.beta * *p : 0.f);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+__global__ void sum_splits_kernel(const float *ws, int S, int M, int N, float alpha, float beta, float *C, long long ldc)
+{
+    const long long total = (long long)M * N;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % M), j = (int)(e / M);
+        float s = 0.f;
+        for (int z = 0; z < S; ++z) s += ws[(long long)z * total + e];
+        float *p = C + i + (long long)j * ldc;
+        *p = alpha * s + (beta != 0.f ? beta * *p : 0.f);
+    }
+}
+
+}  // namespace
+
+size_t tc_sgemm_ws_floats(int m, int n, int k)
+{
+    const int tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+    int S = (num_sms() + tiles - 1) / tiles;
+    const int kchunks = (k + BK - 1) / BK;
+    if (S > kchunks) S = kchunks;
+    if (S > 16) S = 16;
+    return S > 1 ? (size_t)S * m * n : 0;
+}
+
+cudaError_t tc_sgemm(char ta, char tb, int m, int n, int k, float alpha, const float *A, int64_t lda, const float *B,
+                     int64_t ldb, float beta, float *C, int64_t ldc, float *ws, size_t ws_floats, int *err,
+                     cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const int tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
+    int S = (num_sms() + tiles_m * tiles_n - 1) / (tiles_m * tiles_n);
+    const int kchunks = (k + BK - 1) / BK;
+    if (S > kchunks) S = kchunks;
+    if (S > 16) S = 16;
+    if (S < 1) S = 1;
+    while (S > 1 && (!ws || (size_t)S * m * n > ws_floats)) --S;
+    const int kc = ((kchunks + S - 1) / S) * BK;
+    S = (k + kc - 1) / kc;
+    if (S < 1) S = 1;
+    TcArgs g;
+    g.A = A;
+    g.B = B;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.M = m;
+    g.N = n;
+    g.K = k;
+    g.kchunk = kc > 0 ? kc : BK;
+    g.a_kcontig = (ta == 'T');
+    g.b_kcontig = (tb != 'T');
+    g.err = err;
+    if (S == 1) {
+        g.C = C;
+        g.ldc = ldc;
+        g.cslice = 0;
+        g.alpha = alpha;
+        g.beta = beta;
+    } else {
+        g.C = ws;
+        g.ldc = m;
+        g.cslice = (long long)m * n;
+        g.alpha = 1.f;
+        g.beta = 0.f;
+    }
+    dim3 grid(tiles_m, tiles_n, S);
+    count_launch();
+    tc_gemm_kernel<<<grid, 128, kSmemBytes, s>>>(g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || S == 1) return e;
+    count_launch();
+    sum_splits_kernel<<<256, 256, 0, s>>>(ws, S, m, n, alpha, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace riot

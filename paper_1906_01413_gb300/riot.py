@@ -110,6 +110,9 @@ def load():
     L.riot_batch_destroy.argtypes = [vp]
     L.riot_batch_destroy.restype = None
     L.riot_get_trajectory.argtypes = [vp, vp]
+    L.riot_tc_sgemm.argtypes = [ctypes.c_char, ctypes.c_char, c_int32, c_int32, c_int32, ctypes.c_float, vp, c_int64,
+                                vp, c_int64, ctypes.c_float, vp, c_int64, vp]
+    L.riot_tc_sgemm.restype = c_int32
     L.riot_sketchnet_create.argtypes = [POINTER(vp), c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
                                         c_int32, vp]
     L.riot_sketchnet_num_params.argtypes = [vp]
@@ -360,6 +363,13 @@ def _need_contiguous(*ts):
     for t in ts:
         if t is not None and not t.is_contiguous():
             raise ValueError("tensor arguments must be contiguous (the C ABI takes plain pointers)")
+
+
+def riot_tc_sgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
+    """Column-major FP32 GEMM on the tensor cores (pointers of device tensors)."""
+    _check(None, "riot_tc_sgemm",
+           load().riot_tc_sgemm(ta.encode(), tb.encode(), int(m), int(n), int(k), float(alpha), _ptr(A), int(lda),
+                                _ptr(B), int(ldb), float(beta), _ptr(C), int(ldc), _stream_handle(stream)))
 
 
 def riot_get_trajectory(ctx, traj):
