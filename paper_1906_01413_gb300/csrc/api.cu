@@ -44,6 +44,8 @@ struct riot_ctx {
     void *Wblk = nullptr, *Yblk = nullptr, *rscr = nullptr;
     double *Q = nullptr, *U = nullptr;
     float *Q32 = nullptr, *M32 = nullptr, *N32 = nullptr, *L32 = nullptr;   // mixed precision only
+    float *tcws = nullptr;   // split-K workspace of the tensor-core sketch GEMMs
+    size_t tcws_floats = 0;
     double *G = nullptr, *Mm = nullptr, *Nm = nullptr, *Km = nullptr, *Z = nullptr, *lam = nullptr, *cvec = nullptr;
     double *jwork = nullptr;
     double *gws = nullptr;   // split-K partial Grams (8 kmax^2) and Cholesky block inverses (dinv_doubles(kmax))
@@ -614,9 +616,16 @@ riot_status setup_advdiff(riot_ctx *ctx, const riot_model_desc *model, const rio
     return RIOT_OK;
 }
 
+size_t tcws_size(int n, int kmax)
+{
+    const size_t a = tc_sgemm_ws_floats(kmax, kmax, n), b = tc_sgemm_ws_floats(n, kmax, kmax);
+    return a > b ? a : b;
+}
+
 // Outer-loop vectors and the model-independent inner-loop workspace.
 riot_status setup_common(riot_ctx *ctx)
 {
+    ctx->tcws_floats = (ctx->prec == RIOT_PREC_MIXED) ? tcws_size(ctx->n, ctx->kmax) : 0;
     const size_t np = (size_t)ctx->n, k = (size_t)ctx->kmax, rs = real_size(ctx), p = (size_t)ctx->p;
     riot_status st;
     if ((st = dalloc(ctx, &ctx->x, np)) || (st = dalloc(ctx, &ctx->v, np)) || (st = dalloc(ctx, &ctx->g, np)) ||
@@ -627,7 +636,8 @@ riot_status setup_common(riot_ctx *ctx)
         (st = dalloc(ctx, &ctx->Q, np * k)) || (st = dalloc(ctx, &ctx->U, np * k)) ||
         (ctx->prec == RIOT_PREC_MIXED &&
          ((st = dalloc(ctx, &ctx->Q32, np * k)) || (st = dalloc(ctx, &ctx->M32, k * k)) ||
-          (st = dalloc(ctx, &ctx->N32, k * k)) || (st = dalloc(ctx, &ctx->L32, k * k)))) ||
+          (st = dalloc(ctx, &ctx->N32, k * k)) || (st = dalloc(ctx, &ctx->L32, k * k)) ||
+          (st = dalloc(ctx, &ctx->tcws, tcws_size(ctx->n, ctx->kmax))))) ||
         (st = dalloc(ctx, &ctx->G, k * k)) || (st = dalloc(ctx, &ctx->Mm, k * k)) || (st = dalloc(ctx, &ctx->Nm, k * k)) ||
         (st = dalloc(ctx, &ctx->Km, k * k)) || (st = dalloc(ctx, &ctx->Z, k * k)) || (st = dalloc(ctx, &ctx->lam, k)) ||
         (st = dalloc(ctx, &ctx->cvec, k)) ||
@@ -686,6 +696,17 @@ riot_status choose_scale(riot_ctx *ctx)
     ctx->scale_in = a;
     ctx->scale_exp = 2 * a + c;
     return RIOT_OK;
+}
+
+// FP32 sketch GEMMs of the mixed path: tensor cores (FP32-accurate three-term BF16
+// splitting) for blocks of at least one 128 x 128 tile, SIMT otherwise.
+cudaError_t sketch_gemm(riot_ctx *ctx, char ta, char tb, int m, int n, int k, const float *A, int64_t lda,
+                        const float *B, int64_t ldb, float *C, int64_t ldc)
+{
+    if (m >= 128 && n >= 128 && k >= 64)
+        return tc_sgemm(ta, tb, m, n, k, 1.f, A, lda, B, ldb, 0.f, C, ldc, ctx->tcws, ctx->tcws_floats, ctx->errflag,
+                        ctx->s);
+    return sgemm(ta, tb, m, n, k, 1.f, A, lda, B, ldb, 0.f, C, ldc, ctx->s);
 }
 
 riot_status rsvd_check_args(riot_ctx *ctx, int k, int q)
@@ -747,7 +768,7 @@ riot_status rsvd_ritz(riot_ctx *ctx, int k)
         // U = Q Z in FP32 (Y block reused as scratch), then widened
         float *Y32 = (float *)ctx->Yblk;
         CU(convert_block(ctx->Z, 'd', k, ctx->M32, 'f', k, k, k, s));
-        CU(sgemm('N', 'N', n, k, k, 1.f, ctx->Q32, n, ctx->M32, k, 0.f, Y32, n, s));
+        CU(sketch_gemm(ctx, 'N', 'N', n, k, k, ctx->Q32, n, ctx->M32, k, Y32, n));
         CU(convert_block(Y32, 'f', n, ctx->U, 'd', n, n, k, s));
     } else {
         CU(gemm('N', 'N', n, k, k, 1.0, ctx->Q, 'd', n, ctx->Z, 'd', k, 0.0, ctx->U, 'd', n, s));
@@ -775,7 +796,7 @@ riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
         TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
         ev_mark(ctx, 2);
         if (mixed) {
-            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, Y32, n, 0.f, ctx->N32, k, s));
+            CU(sketch_gemm(ctx, 'T', 'N', k, k, n, ctx->Q32, n, Y32, n, ctx->N32, k));
             CU(convert_block(ctx->N32, 'f', k, ctx->Km, 'd', k, k, k, s));
         } else {
             CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Km, 'd', k, s));
@@ -783,8 +804,8 @@ riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
     } else {
         // K (Q^T W) = Q^T Y  <=>  K (M M^T) = N M^T with M = Q^T W, N = Q^T Y
         if (mixed) {
-            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, W32, n, 0.f, ctx->M32, k, s));
-            CU(sgemm('T', 'N', k, k, n, 1.f, ctx->Q32, n, Y32, n, 0.f, ctx->N32, k, s));
+            CU(sketch_gemm(ctx, 'T', 'N', k, k, n, ctx->Q32, n, W32, n, ctx->M32, k));
+            CU(sketch_gemm(ctx, 'T', 'N', k, k, n, ctx->Q32, n, Y32, n, ctx->N32, k));
             CU(convert_block(ctx->M32, 'f', k, ctx->Mm, 'd', k, k, k, s));
             CU(convert_block(ctx->N32, 'f', k, ctx->Nm, 'd', k, k, k, s));
         } else {
@@ -817,7 +838,7 @@ riot_status rsvd_collect(riot_ctx *ctx, int k, double *lambda_out)
     int eflag = 0;
     CU(cudaMemcpyAsync(&eflag, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    if (eflag) return fail(ctx, RIOT_ETIMEOUT, "a bounded wait on a coefficient copy ran out in the Hessian kernel");
+    if (eflag) return fail(ctx, RIOT_ETIMEOUT, "a bounded device wait ran out (Hessian kernel coefficient copy or tensor-core GEMM)");
     TRY(check_cholesky(ctx, 0, 11, "riot_rsvd"));
     int jinfo[2] = {0, 0};
     CU(cudaMemcpyAsync(jinfo, ctx->info + 12, sizeof(jinfo), cudaMemcpyDeviceToHost, s));
