@@ -8,14 +8,15 @@
 // of the randomized eigendecomposition (Q^T W, Q^T Y, U = Q Z) run in mixed
 // precision.
 //
-// One CTA of 128 threads owns a 128 x 128 tile of C (its FP32 accumulator in
+// One CTA of 256 threads owns a 128 x 128 tile of C (its FP32 accumulator in
 // 128 TMEM columns) and a slice of K (split-K over blockIdx.z, partial tiles
 // reduced by a second kernel).  Per 64-wide K chunk the threads load the
 // FP32 tiles (any transpose), split them and store the BF16 terms in shared
 // memory in the canonical K-major core-matrix layout (8 rows x 16 bytes per
-// core matrix, no swizzle); one thread issues the MMAs and commits them to an
-// mbarrier that the CTA waits on (bounded) before refilling shared memory.
-// The epilogue reads the accumulator with tcgen05.ld (each warp its 32 lanes).
+// core matrix, no swizzle), alternating between two stages; one thread issues
+// the MMAs and commits them to the stage's mbarrier, which is waited on
+// (bounded) before that stage is refilled.  The epilogue reads the
+// accumulator with tcgen05.ld (each warp its 32 lanes, half the columns).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -27,11 +28,11 @@ namespace riot {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int kThreads = 256;
 constexpr int kSplits = 3;                         // BF16 terms per FP32 value
 constexpr int kTileBytes = BM * BK * 2;            // one BF16 term of one operand tile (16 KB)
-// 32 KB of slack past the last tile keeps every address an MMA could form from
-// these descriptors inside the CTA's allocation
-constexpr int kSmemBytes = 2 * kSplits * kTileBytes + 32768 + 1024;
+constexpr int kStageBytes = 2 * kSplits * kTileBytes;   // A and B terms of one K chunk (96 KB)
+constexpr int kSmemBytes = 2 * kStageBytes + 1024;       // two stages
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -69,49 +70,51 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16 &a, __nv_bfloat16 
     c = __float2bfloat16(r1 - __bfloat162float(b));
 }
 
+__device__ __forceinline__ void store_terms(const float (&v)[8], unsigned char *dst, uint32_t off)
+{
+    __align__(16) __nv_bfloat16 t[kSplits][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) split3(v[q], t[0][q], t[1][q], t[2][q]);
+#pragma unroll
+    for (int s = 0; s < kSplits; ++s)
+        *reinterpret_cast<uint4 *>(dst + s * kTileBytes + off) = *reinterpret_cast<const uint4 *>(t[s]);
+}
+
 // Load a 128 x 64 tile of X (element (r, k) at X[k + r ld] when k_contig, else
 // X[r + k ld]), rows r0.., k0.., zero outside rows x kvalid, split into three
-// BF16 terms stored at dst + s * kTileBytes.
+// BF16 terms stored at dst + s * kTileBytes.  Each thread handles runs of 8 k
+// of one row (one core-matrix row); the eight threads that store neighbouring
+// 16-byte rows of a core matrix are consecutive, so the stores do not conflict.
 __device__ __forceinline__ void load_tile(const float *X, long long ld, bool k_contig, int r0, int rows, int k0,
                                           int kvalid, unsigned char *dst)
 {
     const int tid = threadIdx.x;
     if (k_contig) {
-        // 8 threads per row, 8 consecutive k each: one core-matrix row per thread
-        for (int p = 0; p < BM / 16; ++p) {
-            const int r = p * 16 + tid / 8, kq = (tid & 7) * 8;
+        // tid = (kq8, rg, rr): rr = row within 8, kq8 = 8-wide k run, 4 row groups per pass
+        const int rr = tid & 7, kq = ((tid >> 3) & 7) * 8, rg = tid >> 6;
+        for (int p = 0; p < BM / 32; ++p) {
+            const int r = p * 32 + rg * 8 + rr;
+            const int gr = r0 + r;
             float v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int gr = r0 + r, gk = k0 + kq + q;
+                const int gk = k0 + kq + q;
                 v[q] = (gr < rows && gk < kvalid) ? X[(long long)gk + (long long)gr * ld] : 0.f;
             }
-            __align__(16) __nv_bfloat16 t[kSplits][8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) split3(v[q], t[0][q], t[1][q], t[2][q]);
-            const uint32_t off = core_off(r, kq);
-#pragma unroll
-            for (int s = 0; s < kSplits; ++s)
-                *reinterpret_cast<uint4 *>(dst + s * kTileBytes + off) = *reinterpret_cast<const uint4 *>(t[s]);
+            store_terms(v, dst, core_off(r, kq));
         }
     } else {
-        // one row per thread, rows contiguous in memory across the warp
-        const int r = tid;
+        // one row per thread, rows contiguous in memory across the warp; two halves of k
+        const int r = tid & (BM - 1), kh = (tid >> 7) * (BK / 2);
         const int gr = r0 + r;
-        for (int kq = 0; kq < BK; kq += 8) {
+        for (int kq = kh; kq < kh + BK / 2; kq += 8) {
             float v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int gk = k0 + kq + q;
                 v[q] = (gr < rows && gk < kvalid) ? X[(long long)gr + (long long)gk * ld] : 0.f;
             }
-            __align__(16) __nv_bfloat16 t[kSplits][8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) split3(v[q], t[0][q], t[1][q], t[2][q]);
-            const uint32_t off = core_off(r, kq);
-#pragma unroll
-            for (int s = 0; s < kSplits; ++s)
-                *reinterpret_cast<uint4 *>(dst + s * kTileBytes + off) = *reinterpret_cast<const uint4 *>(t[s]);
+            store_terms(v, dst, core_off(r, kq));
         }
     }
 }
@@ -143,20 +146,21 @@ struct TcArgs {
     int *err;
 };
 
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcArgs g)
+// Two shared-memory stages: while the tensor cores multiply chunk c, the
+// threads load and split chunk c + 1 into the other stage; a stage is
+// refilled only after the mbarrier committed with its MMAs has completed.
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs g)
 {
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA = base;                                  // 3 terms x 16 KB
-    unsigned char *sB = base + kSplits * kTileBytes;           // 3 terms x 16 KB
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bars[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_s;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int kbeg = blockIdx.z * g.kchunk;
     const int kend = min(g.K, kbeg + g.kchunk);
-    const uint32_t bar_a = smem_u32(&bar);
+    const int nchunks = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
                      "r"(BN)
@@ -165,7 +169,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcArgs g)
     }
     if (tid == 0) {
         abort_s = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -173,11 +178,24 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcArgs g)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder;
     constexpr uint32_t idesc = instr_desc(BM, BN);
-    const bool has_k = kbeg < kend;
     float *C = g.C + (long long)blockIdx.z * g.cslice;
-    int phase = 0;
-    bool first = true;
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    uint32_t ph[2] = {0u, 0u};   // parity of the next completion of each stage's barrier (thread 0)
+    for (int c = 0; c < nchunks; ++c) {
+        const int st = c & 1;
+        unsigned char *sA = base + st * kStageBytes;
+        unsigned char *sB = sA + kSplits * kTileBytes;
+        if (c >= 2) {
+            // this stage still feeds the MMAs of chunk c - 2
+            if (tid == 0 && !abort_s) {
+                if (!mbar_wait_bounded(smem_u32(&bars[st]), ph[st])) {
+                    abort_s = 1;
+                    atomicExch(g.err, 1);
+                }
+                ph[st] ^= 1u;
+            }
+            __syncthreads();
+        }
+        const int k0 = kbeg + c * BK;
         load_tile(g.A, g.lda, g.a_kcontig, m0, g.M, k0, kend, sA);
         load_tile(g.B, g.ldb, g.b_kcontig, n0, g.N, k0, kend, sB);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -195,32 +213,40 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcArgs g)
                     const uint32_t b_addr = smem_u32(sB + pb[p] * kTileBytes) + ks * 4096;
                     const uint64_t ad = smem_desc(a_addr, 2048, 128);
                     const uint64_t bd = smem_desc(b_addr, 2048, 128);
-                    const uint32_t acc = first ? 0u : 1u;
+                    const uint32_t acc = (c > 0 || ks > 0 || p > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "setp.ne.b32 p, %4, 0;\n\t"
                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                         : "memory");
-                    first = false;
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bars[st]))
                          : "memory");
-            if (!mbar_wait_bounded(bar_a, (uint32_t)phase)) {
+        }
+    }
+    // wait for the MMAs still in flight (the last two chunks)
+    if (tid == 0 && !abort_s) {
+        for (int c = (nchunks >= 2 ? nchunks - 2 : 0); c < nchunks; ++c) {
+            const int st = c & 1;
+            if (!mbar_wait_bounded(smem_u32(&bars[st]), ph[st])) {
                 abort_s = 1;
                 atomicExch(g.err, 1);
+                break;
             }
+            ph[st] ^= 1u;
         }
-        phase ^= 1;
-        __syncthreads();   // the MMAs of this chunk have finished reading shared memory
     }
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w reads lanes 32w..32w+31 (rows), 32 columns at a time
-    const int row = m0 + warp * 32 + (tid & 31);
-    for (int c0 = 0; c0 < BN; c0 += 32) {
+    // epilogue: warp w reads lanes 32 (w % 4) .. + 31 (rows); warps 0-3 columns 0-63, 4-7 columns 64-127
+    const int row = m0 + (warp & 3) * 32 + (tid & 31);
+    const int cbeg = (warp >> 2) * (BN / 2);
+    for (int c0 = cbeg; c0 < cbeg + BN / 2; c0 += 32) {
         uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
             "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -236,7 +262,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcArgs g)
                 const int col = n0 + c0 + j;
                 if (col < g.N) {
                     float *p = C + row + (long long)col * g.ldc;
-                    const float v = has_k ? __uint_as_float(r[j]) : 0.f;
+                    const float v = nchunks > 0 ? __uint_as_float(r[j]) : 0.f;
                     *p = g.alpha * v + (g.beta != 0.f ? g.beta * *p : 0.f);
                 }
             }
@@ -319,7 +345,7 @@ cudaError_t tc_sgemm(char ta, char tb, int m, int n, int k, float alpha, const f
     }
     dim3 grid(tiles_m, tiles_n, S);
     count_launch();
-    tc_gemm_kernel<<<grid, 128, kSmemBytes, s>>>(g);
+    tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(g);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || S == 1) return e;
     count_launch();
