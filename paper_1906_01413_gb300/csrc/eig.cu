@@ -8,7 +8,8 @@
 //     update with the next column's reflector computed by the warp that
 //     owns it); Q is accumulated as Q^T on the fly.
 //  2. T splits where an off-diagonal is negligible; each unreduced block's
-//     eigenvalues come from bisection with Sturm counts (one thread each).
+//     eigenvalues come from a grid of Sturm counts followed by multisection
+//     (one warp per eigenvalue, 32 Sturm counts per round).
 //  3. Eigenvectors of T by inverse iteration from distinct pseudo-random
 //     starts (tridiagonal LU with partial pivoting, one thread each), then two
 //     CholeskyQR passes make them orthonormal (this also separates vectors of
@@ -224,20 +225,25 @@ __global__ void prebracket_kernel(const double *d, const double *e2, const int *
     }
 }
 
-// One warp per eigenvalue: bracket from the grid, then multisection with
-// 128 interior points per round (4 independent Sturm chains per lane),
-// until the bracket is below 1e-10 relative or 4 eps ||T|| (the inverse
-// iteration that follows refines it by a Rayleigh quotient).
+// Multisection for one eigenvalue per segment of G lanes, U Sturm chains per
+// lane: P = G U interior points per round, the bracket shrinks (P + 1)-fold.
+// Fewer points per round cost more rounds but less FP64 work in total (the
+// counts run on the FP64 pipe, which is narrow on this GPU).
+template <int G, int U>
 __global__ void multisect_kernel(const double *d, const double *e2, const int *blo, const int *bhi, const int *bstart,
                                  const int *nblocks, int k, const double *tnorm, const int *counts, double *w)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    constexpr int P = G * U;
+    const int gl = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (warp >= k) return;
-    const int i = warp, lo = blo[i], hi = bhi[i], r = i - lo;
+    const int sl = lane % G;                                  // lane within the segment
+    const unsigned seg_mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - sl));
+    const int i = gl / G;
+    if (i >= k) return;
+    const int lo = blo[i], hi = bhi[i], r = i - lo;
     const double tn = *tnorm;
     if (lo == hi) {
-        if (lane == 0) w[i] = d[lo];
+        if (sl == 0) w[i] = d[lo];
         return;
     }
     // locate this block and the grid cell holding eigenvalue r
@@ -254,50 +260,45 @@ __global__ void multisect_kernel(const double *d, const double *e2, const int *b
     }
     double a = grid_point(g0, tn), c = grid_point(g1, tn);
     const double pivmin = DBL_MIN * fmax(1.0, tn * tn);
-    for (int round = 0; round < 12; ++round) {
+    for (int round = 0; round < 64; ++round) {
         const double width = c - a;
         if (width <= fmax(1e-10 * fmax(fabs(a), fabs(c)), 4.0 * DBL_EPSILON * tn)) break;
-        const double step = width / 129.0;
-        double x[4];
-        int cnt[4];
+        const double step = width / (double)(P + 1);
+        double x[U], q[U];
+        int cnt[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            x[u] = a + step * (double)(1 + lane + 32 * u);
-            cnt[u] = 0;
-        }
-        double q[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
+            x[u] = a + step * (double)(1 + sl + G * u);
             q[u] = d[lo] - x[u];
             if (fabs(q[u]) < pivmin) q[u] = -pivmin;
-            cnt[u] += (q[u] < 0.0);
+            cnt[u] = (q[u] < 0.0);
         }
         for (int l = lo + 1; l <= hi; ++l) {
             const double dl = d[l], el = e2[l - 1];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 q[u] = (dl - x[u]) - el / q[u];
                 if (fabs(q[u]) < pivmin) q[u] = -pivmin;
                 cnt[u] += (q[u] < 0.0);
             }
         }
         // the new bracket: last point with count <= r, first with count > r;
-        // points are ascending in (u, lane) and counts are monotone in x
-        double na = a, nc = c;
-        int best_le = -1, first_gt = 128;
+        // points ascend with (u, sl) and counts are monotone in x
+        int best_le = -1, first_gt = P;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const unsigned gt = __ballot_sync(0xffffffffu, cnt[u] > r);
-            const unsigned le = ~gt;
-            if (le) best_le = max(best_le, 32 * u + 31 - __clz(le));
-            if (gt) first_gt = min(first_gt, 32 * u + __ffs(gt) - 1);
+        for (int u = 0; u < U; ++u) {
+            const unsigned gt = __ballot_sync(seg_mask, cnt[u] > r) >> (lane - sl);
+            const unsigned le = ~gt & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u));
+            if (le) best_le = max(best_le, G * u + 31 - __clz(le));
+            if (gt) first_gt = min(first_gt, G * u + __ffs(gt) - 1);
         }
-        if (best_le >= 0) na = a + step * (double)(1 + best_le);
-        if (first_gt < 128) nc = a + step * (double)(1 + first_gt);
+        const double na = (best_le >= 0) ? a + step * (double)(1 + best_le) : a;
+        const double nc = (first_gt < P) ? a + step * (double)(1 + first_gt) : c;
+        if (!(nc - na < width)) break;   // no progress: the width is at the resolution of the arithmetic
         a = na;
         c = nc;
     }
-    if (lane == 0) w[i] = 0.5 * (a + c);
+    if (sl == 0) w[i] = 0.5 * (a + c);
 }
 
 __device__ __forceinline__ double hash_uniform(uint32_t a, uint32_t b)
@@ -454,8 +455,14 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     split_kernel<<<1, 1, 0, s>>>(d, e, k, e2, blo, bhi, tnorm, bstart, nblocks);
     count_launch();
     prebracket_kernel<<<2 * num_sms(), 128, 0, s>>>(d, e2, bstart, nblocks, tnorm, counts);
-    count_launch();
-    multisect_kernel<<<(k + 3) / 4, 128, 0, s>>>(d, e2, blo, bhi, bstart, nblocks, k, tnorm, counts, w);
+    {
+        // one warp of single chains per eigenvalue (33-fold shrink per round): measured on
+        // k = 512 against 8 to 128 points per round, the least FP64 work that still fills the GPU
+        constexpr int G = 32, U = 1;
+        count_launch();
+        multisect_kernel<G, U><<<(int)(((int64_t)k * G + 127) / 128), 128, 0, s>>>(d, e2, blo, bhi, bstart, nblocks, k,
+                                                                                 tnorm, counts, w);
+    }
     count_launch();
     inviter_kernel<<<(k + 3) / 4, 4, 0, s>>>(d, e, blo, bhi, k, w, tnorm, Zt, u0, u1, u2, ml, piv, wrq);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
