@@ -403,6 +403,22 @@ riot_status riot_tc_sgemm(char ta, char tb, int32_t m, int32_t n, int32_t k, flo
                           int64_t lda, const float *B_dev, int64_t ldb, float beta, float *C_dev, int64_t ldc,
                           void *cuda_stream);
 
+/* The Gram matrix of the mixed-precision CholeskyQR (Section 2.2, the
+ * orthonormalisation Q = orth(Y) of Algorithm 3) on its own, for checks: the
+ * lower triangle (i >= j) of G = Y^T Y, Y n x k FP32 column-major (leading
+ * dimension ldy >= n), G k x k FP64 column-major (ldg >= k; the strict upper
+ * triangle is not written).  Computed on the tcgen05 tensor cores by exact
+ * integer slicing: each column is scaled by a power of two and split into five
+ * BF16 slices whose products and sums are exact, so the only error off the
+ * diagonal is the truncation of each value below 2^-36 of its column's largest
+ * magnitude (and the slice products of weight below 2^-42 that are left out);
+ * the diagonal is summed in FP64 on the CUDA cores.  A column
+ * holding Inf or NaN gives NaN in its row and column of G.  n = 0 gives G = 0.
+ * Allocates and frees its own workspace; synchronises the stream.
+ * RIOT_ETIMEOUT if a bounded wait on the tensor cores ran out. */
+riot_status riot_tc_gram(int32_t n, int32_t k, const float *Y_dev, int64_t ldy, double *G_dev, int64_t ldg,
+                         void *cuda_stream);
+
 const char *riot_last_error(const riot_ctx *ctx);
 const char *riot_status_string(riot_status s);
 void riot_destroy(riot_ctx *ctx);

@@ -241,18 +241,27 @@ riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
     return RIOT_OK;
 }
 
-// Mixed precision: Q32 = orthonormal basis of Y (FP32 block).  Grams are
-// accumulated and factorised in FP64 (the step that needs the range); the
-// triangular solves run in FP32, like the block they act on.
+// Mixed precision: Q32 = orthonormal basis of Y (FP32 block).  Grams come
+// from the tensor cores to FP64-level accuracy (exact slice products) and are
+// factorised in FP64 (the step that needs the range); the triangular solves
+// run in FP32, like the block they act on.
 riot_status orth32(riot_ctx *ctx, const float *Y, int k, int info_base, int passes, int shifted)
 {
     const int n = ctx->n;
     CU(cudaMemcpyAsync(ctx->Q32, Y, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, ctx->s));
     for (int pass = 0; pass < passes; ++pass) {
-        CU(gram_lower(n, k, ctx->Q32, 'f', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
+        CU(tc_gram_f32(n, k, ctx->Q32, n, ctx->G, k, ctx->gws, ctx->errflag, ctx->s));
         CU(equilibrate(ctx->G, k, k, ctx->Q32, 'f', n, n, ctx->cvec, ctx->s));
+        // The shift must exceed the Gram's error as well as the Cholesky's.  The sliced
+        // tensor-core Gram truncates each value below 2^-36 of its column maximum; with
+        // random signs that puts its 2-norm error near 2^-31 (k / n)^(1/2) of the unit
+        // diagonal for columns of Gaussian-like entries.  The FP64 rounding term
+        // 11 (n k + k (k + 1)) u stays above that only for large blocks: a floor of 2^-29
+        // covers small ones (and thin proposal blocks) with margin.
         const double u = ldexp(1.0, -53);
-        const double shift = (pass < shifted) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
+        const double shift = (pass < shifted)
+                                 ? fmax(11.0 * ((double)n * k + (double)k * (k + 1)) * u, ldexp(1.0, -29) / k)
+                                 : 0.0;
         CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
         CU(convert_block(ctx->G, 'd', k, ctx->L32, 'f', k, k, k, ctx->s));
         CU(strsm_right_lt(ctx->Q32, n, k, n, ctx->L32, k, ctx->s));
@@ -1752,6 +1761,31 @@ riot_status riot_tc_sgemm(char ta, char tb, int32_t m, int32_t n, int32_t k, flo
     int herr = 0;
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = tc_sgemm(ta, tb, m, n, k, alpha, A_dev, lda, B_dev, ldb, beta, C_dev, ldc, ws, wsf, err, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(ws);
+    cudaFree(err);
+    if (e != cudaSuccess) return RIOT_ECUDA;
+    return herr ? RIOT_ETIMEOUT : RIOT_OK;
+}
+
+riot_status riot_tc_gram(int32_t n, int32_t k, const float *Y_dev, int64_t ldy, double *G_dev, int64_t ldg,
+                         void *cuda_stream)
+{
+    if (n < 0 || k < 0) return RIOT_EINVAL;
+    if (k == 0) return RIOT_OK;
+    if ((n > 0 && !Y_dev) || !G_dev || ldy < (n > 1 ? n : 1) || ldg < k) return RIOT_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    void *ws = nullptr;
+    int *err = nullptr;
+    if (cudaMalloc(&ws, tc_gram_ws_bytes(k)) != cudaSuccess) return RIOT_ENOMEM;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaFree(ws);
+        return RIOT_ENOMEM;
+    }
+    int herr = 0;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = tc_gram_f32(n, k, Y_dev, ldy, G_dev, ldg, ws, err, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(ws);

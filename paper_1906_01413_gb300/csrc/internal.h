@@ -220,6 +220,13 @@ cudaError_t tc_sgemm(char ta, char tb, int m, int n, int k, float alpha, const f
                      int64_t ldb, float beta, float *C, int64_t ldc, float *ws, size_t ws_floats, int *err,
                      cudaStream_t s);
 size_t tc_sgemm_ws_floats(int m, int n, int k);
+// Lower triangle of G = Y^T Y (Y: n x k FP32, column-major) to FP64-level
+// accuracy on the tensor cores (error-free slicing, exact integer
+// accumulation, FP64 diagonal).  ws: tc_gram_ws_bytes(k) bytes of device
+// memory, 16-byte aligned; err is set if a bounded wait on the tensor cores ran out.
+cudaError_t tc_gram_f32(int n, int k, const float *Y, int64_t ldy, double *G, int64_t ldg, void *ws, int *err,
+                        cudaStream_t s);
+size_t tc_gram_ws_bytes(int k);
 // X <- X L^-T in FP32 (L: k x k lower, FP32)
 cudaError_t strsm_right_lt(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s);
 cudaError_t convert_block(const void *in, char tin, int64_t ldin, void *out, char tout, int64_t ldout,

@@ -285,6 +285,290 @@ __global__ void sum_splits_kernel(const float *ws, int S, int M, int N, float al
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// G = Y^T Y of an FP32 block Y (n x k) to FP64-level accuracy on the tensor
+// cores, by error-free splitting (Ozaki, Ogita, Oishi and Rump 2012):
+// column j is scaled by 2^-e_j (|y| < 2^e_j) and split into five integer
+// slices of 8, 7, 7, 7 and 7 bits,
+//     y = 2^e_j (s1 2^-7 + s2 2^-14 + s3 2^-21 + s4 2^-28 + s5 2^-35) + r,
+//     |r| <= 2^(e_j - 36),
+// |s1| <= 128, |s2..5| <= 64, each exact in BF16.  A product of two slices is
+// an integer below 2^14 in magnitude; slice pairs (a, b) of equal weight
+// 2^-7(a+b) share one FP32 accumulator in tensor memory (w = a + b = 2..6:
+// 1 to 5 pairs, five accumulators of 64 columns for a 128 x 64 tile of G), and
+// a K range of at most kGramMaxKR rows keeps every partial sum of every
+// accumulator below 2^23, so the tensor-core accumulation is exact.  The
+// epilogue combines the five integers in 64-bit arithmetic and adds its K
+// range's part atomically into an int64 Gram; a last kernel scales that by
+// 2^(e_i + e_j - 42) into FP64.  What is dropped (pairs with w >= 7, the
+// residuals r) is below about 2^-35 of max|y_i| max|y_j| per row of Y and of
+// random sign off the diagonal; on the diagonal the dropped s4^2 terms all
+// have the same sign, so the diagonal is summed in FP64 on the CUDA cores
+// instead (n k FMAs, next to the column maxima).
+// ---------------------------------------------------------------------------
+constexpr int kGramBK = 32;                            // K rows per chunk
+constexpr int kGramBN = 64;                            // columns of a Gram tile
+constexpr int kGramSlices = 5;
+constexpr int kGramPairs = kGramSlices * (kGramSlices + 1) / 2;     // pairs with a + b <= 6 (1-based)
+constexpr int kGramTileBytes = BM * kGramBK * 2;       // one slice of one operand, 128-row layout (8 KB)
+constexpr int kGramStageBytes = 2 * kGramSlices * kGramTileBytes;   // 80 KB
+constexpr int kGramSmemBytes = 2 * kGramStageBytes + 1024;
+constexpr int kGramMaxKR = 288;                        // 288 * 7 * 2^12 < 2^23
+constexpr int kGramAccCols = 512;                      // five accumulators of 64 columns (allocation: a power of 2)
+constexpr int kGramNonFinite = -100000;                // exponent of a column with Inf or NaN
+
+// Exponent e (max |y| < 2^e), the two power-of-two factors f1 f2 = 2^(7 - e)
+// (two so that both stay normal FP32 numbers) and the FP64 sum of squares of
+// each column.
+__global__ void gram_colscale_kernel(const float *Y, int n, int k, long long ldy, int *colexp, float2 *colscale,
+                                     double *coldiag)
+{
+    const int j = blockIdx.x;
+    if (j >= k) return;
+    const float *y = Y + (long long)j * ldy;
+    float m = 0.f;
+    double ss = 0.0;
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float v = y[i];
+        bad |= !isfinite(v);
+        m = fmaxf(m, fabsf(v));
+        ss = fma((double)v, (double)v, ss);
+    }
+    __shared__ float red[32];
+    __shared__ double reds[32];
+    for (int off = 16; off > 0; off >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        ss += __shfl_xor_sync(0xffffffffu, ss, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = m;
+        reds[threadIdx.x >> 5] = ss;
+    }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            m = fmaxf(m, red[w]);
+            ss += reds[w];
+        }
+        coldiag[j] = bad ? __longlong_as_double(0x7ff8000000000000LL) : ss;
+        int e = 0;
+        if (m > 0.f) frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
+        const int se = 7 - e, x1 = se < 127 ? se : 127, x2 = se - x1;
+        colexp[j] = bad ? kGramNonFinite : e;
+        colscale[j] = bad ? make_float2(0.f, 0.f)
+                          : make_float2(__int_as_float((127 + x1) << 23), __int_as_float((127 + x2) << 23));
+    }
+}
+
+__device__ __forceinline__ void slice5(float y, float2 f, float (&s)[kGramSlices])
+{
+    float t = (y * f.x) * f.y;   // |t| < 128, exact
+#pragma unroll
+    for (int q = 0; q < kGramSlices; ++q) {
+        s[q] = rintf(t);
+        t = (t - s[q]) * 128.f;  // exact: t - s is the fraction left over
+    }
+}
+
+// Rows r0 .. r0 + ROWS - 1 of the Gram (columns of Y), K rows k0 .. k0 + 31,
+// in the 128-row core-matrix layout: element (r, l) is Y[l + r ldy]; each
+// thread handles runs of 8 l of one row.
+template <int ROWS>
+__device__ __forceinline__ void gram_load_tile(const float *Y, long long ldy, int r0, int k, int k0, int kend,
+                                               const float2 *colscale, unsigned char *dst)
+{
+    const int tid = threadIdx.x;
+    const int rr = tid & 7, kq = ((tid >> 3) & 3) * 8, rg = tid >> 5;
+#pragma unroll
+    for (int p = 0; p < ROWS / 64; ++p) {
+        const int r = p * 64 + rg * 8 + rr;
+        const int gr = r0 + r;
+        const float2 f = (gr < k) ? colscale[gr] : make_float2(0.f, 0.f);
+        __align__(16) __nv_bfloat16 t[kGramSlices][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int gl = k0 + kq + q;
+            const float v = (gr < k && gl < kend) ? Y[(long long)gl + (long long)gr * ldy] : 0.f;
+            float s[kGramSlices];
+            slice5(v, f, s);
+#pragma unroll
+            for (int z = 0; z < kGramSlices; ++z) t[z][q] = __float2bfloat16_rn(s[z]);
+        }
+        const uint32_t off = core_off(r, kq);
+#pragma unroll
+        for (int z = 0; z < kGramSlices; ++z)
+            *reinterpret_cast<uint4 *>(dst + z * kGramTileBytes + off) = *reinterpret_cast<const uint4 *>(t[z]);
+    }
+}
+
+struct GramArgs {
+    const float *Y;
+    long long ldy;
+    int n, k, kr;               // rows of Y, columns of Y, K rows per split
+    const float2 *colscale;
+    unsigned long long *acc;    // k x k int64 Gram (two's complement), column-major
+    int *err;
+};
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// blockIdx.x = tile (ti, tj) of 128 rows x 64 columns reaching the lower triangle
+// (tj <= 2 ti + 1), row by row; blockIdx.y = K split.
+__global__ void __launch_bounds__(kThreads, 1) tc_gram_kernel(GramArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_s;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tk2 = (g.k + kGramBN - 1) / kGramBN;
+    int ti = 0, rem = blockIdx.x;
+    while (rem >= min(2 * ti + 2, tk2)) { rem -= min(2 * ti + 2, tk2); ++ti; }
+    const int tj = rem;
+    const bool diag = (tj >= 2 * ti);     // the tile's columns are rows of its own A tile
+    const int m0 = ti * BM, n0 = tj * kGramBN;
+    const int kbeg = blockIdx.y * g.kr;
+    const int kend = min(g.n, kbeg + g.kr);
+    const int nchunks = kend > kbeg ? (kend - kbeg + kGramBK - 1) / kGramBK : 0;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(kGramAccCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        abort_s = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+    constexpr uint32_t idesc = instr_desc(BM, kGramBN);
+    uint32_t ph[2] = {0u, 0u};
+    for (int c = 0; c < nchunks; ++c) {
+        const int st = c & 1;
+        unsigned char *sA = base + st * kGramStageBytes;
+        unsigned char *sB = diag ? sA + (tj - 2 * ti) * 1024 : sA + kGramSlices * kGramTileBytes;
+        if (c >= 2) {
+            if (tid == 0 && !abort_s) {
+                if (!mbar_wait_bounded(smem_u32(&bars[st]), ph[st])) {
+                    abort_s = 1;
+                    atomicExch(g.err, 1);
+                }
+                ph[st] ^= 1u;
+            }
+            __syncthreads();
+        }
+        const int k0 = kbeg + c * kGramBK;
+        gram_load_tile<BM>(g.Y, g.ldy, m0, g.k, k0, kend, g.colscale, sA);
+        if (!diag) gram_load_tile<kGramBN>(g.Y, g.ldy, n0, g.k, k0, kend, g.colscale, sB);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && !abort_s) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // slice pairs (a, b), 0-based, grouped by weight a + b = 0 .. 4 (accumulator a + b)
+            const int pa[kGramPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
+            const int pb[kGramPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
+#pragma unroll
+            for (int ks = 0; ks < kGramBK / 16; ++ks) {
+#pragma unroll
+                for (int p = 0; p < kGramPairs; ++p) {
+                    const int w = pa[p] + pb[p];
+                    const bool first_of_group = (pa[p] == 0);
+                    const uint32_t a_addr = smem_u32(sA + pa[p] * kGramTileBytes) + ks * 4096;
+                    const uint32_t b_addr = smem_u32(sB + pb[p] * kGramTileBytes) + ks * 4096;
+                    const uint64_t ad = smem_desc(a_addr, 2048, 128);
+                    const uint64_t bd = smem_desc(b_addr, 2048, 128);
+                    const uint32_t acc = (c > 0 || ks > 0 || !first_of_group) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (uint32_t)(w * kGramBN)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bars[st]))
+                         : "memory");
+        }
+    }
+    if (tid == 0 && !abort_s) {
+        for (int c = (nchunks >= 2 ? nchunks - 2 : 0); c < nchunks; ++c) {
+            const int st = c & 1;
+            if (!mbar_wait_bounded(smem_u32(&bars[st]), ph[st])) {
+                abort_s = 1;
+                atomicExch(g.err, 1);
+                break;
+            }
+            ph[st] ^= 1u;
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) ..; warps 0-3 columns 0-31, warps 4-7 columns 32-63
+    const int row = m0 + (warp & 3) * 32 + (tid & 31);
+    const int cbeg = (warp >> 2) * (kGramBN / 2);
+    if (nchunks > 0 && !abort_s) {
+        for (int c0 = cbeg; c0 < cbeg + kGramBN / 2; c0 += 16) {
+            uint32_t r[kGramSlices][16];
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+#pragma unroll
+            for (int w = 0; w < kGramSlices; ++w) tmem_ld16(taddr + (uint32_t)(w * kGramBN), r[w]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < g.k) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int col = n0 + c0 + q;
+                    if (col < g.k && col < row) {
+                        long long t = 0;
+#pragma unroll
+                        for (int w = 0; w < kGramSlices; ++w)
+                            t += (long long)__float2int_rn(__uint_as_float(r[w][q])) << (7 * (kGramSlices - 1 - w));
+                        atomicAdd(g.acc + row + (long long)col * g.k, (unsigned long long)t);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGramAccCols) : "memory");
+}
+
+// G (strict lower triangle) = int64 Gram * 2^(e_i + e_j - 42), the diagonal from the FP64
+// column sums; NaN where a column held Inf or NaN.
+__global__ void gram_finish_kernel(const unsigned long long *acc, const int *colexp, const double *coldiag, int k,
+                                   double *G, long long ldg)
+{
+    const long long total = (long long)k * k;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % k), j = (int)(e / k);
+        if (i < j) continue;
+        const int ei = colexp[i], ej = colexp[j];
+        double v;
+        if (ei == kGramNonFinite || ej == kGramNonFinite) v = __longlong_as_double(0x7ff8000000000000LL);
+        else if (i == j) v = coldiag[i];
+        else v = ldexp((double)(long long)acc[e], ei + ej - 42);
+        G[i + (long long)j * ldg] = v;
+    }
+}
+
 }  // namespace
 
 size_t tc_sgemm_ws_floats(int m, int n, int k)
@@ -350,6 +634,59 @@ cudaError_t tc_sgemm(char ta, char tb, int m, int n, int k, float alpha, const f
     if (e != cudaSuccess || S == 1) return e;
     count_launch();
     sum_splits_kernel<<<256, 256, 0, s>>>(ws, S, m, n, alpha, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+size_t tc_gram_ws_bytes(int k)
+{
+    return (size_t)k * k * sizeof(unsigned long long) + (size_t)k * (sizeof(int) + sizeof(float2) + sizeof(double)) +
+           64;
+}
+
+cudaError_t tc_gram_f32(int n, int k, const float *Y, int64_t ldy, double *G, int64_t ldg, void *ws, int *err,
+                        cudaStream_t s)
+{
+    if (k <= 0) return cudaSuccess;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kGramSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    unsigned long long *acc = (unsigned long long *)ws;
+    int *colexp = (int *)(acc + (size_t)k * k);
+    float2 *colscale = (float2 *)(((uintptr_t)(colexp + k) + 15) & ~(uintptr_t)15);
+    double *coldiag = (double *)(colscale + k);
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)k * k * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    gram_colscale_kernel<<<k, 256, 0, s>>>(Y, n, k, ldy, colexp, colscale, coldiag);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int tk = (k + BM - 1) / BM, tk2 = (k + kGramBN - 1) / kGramBN;
+    int tiles = 0;
+    for (int ti = 0; ti < tk; ++ti) tiles += (2 * ti + 2 < tk2) ? 2 * ti + 2 : tk2;
+    // K splits: as many as fill the GPU once, each at most kGramMaxKR rows (exactness bound)
+    int S = num_sms() / tiles;
+    if (S < 1) S = 1;
+    int kr = ((n + S - 1) / S + kGramBK - 1) / kGramBK * kGramBK;
+    if (kr > kGramMaxKR) kr = kGramMaxKR;
+    if (kr < kGramBK) kr = kGramBK;
+    S = n > 0 ? (n + kr - 1) / kr : 1;
+    GramArgs g;
+    g.Y = Y;
+    g.ldy = ldy;
+    g.n = n;
+    g.k = k;
+    g.kr = kr;
+    g.colscale = colscale;
+    g.acc = acc;
+    g.err = err;
+    count_launch();
+    tc_gram_kernel<<<dim3(tiles, S), kThreads, kGramSmemBytes, s>>>(g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    count_launch();
+    gram_finish_kernel<<<2 * num_sms(), 256, 0, s>>>(acc, colexp, coldiag, k, G, ldg);
     return cudaGetLastError();
 }
 

@@ -113,6 +113,8 @@ def load():
     L.riot_tc_sgemm.argtypes = [ctypes.c_char, ctypes.c_char, c_int32, c_int32, c_int32, ctypes.c_float, vp, c_int64,
                                 vp, c_int64, ctypes.c_float, vp, c_int64, vp]
     L.riot_tc_sgemm.restype = c_int32
+    L.riot_tc_gram.argtypes = [c_int32, c_int32, vp, c_int64, vp, c_int64, vp]
+    L.riot_tc_gram.restype = c_int32
     L.riot_sketchnet_create.argtypes = [POINTER(vp), c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
                                         c_int32, vp]
     L.riot_sketchnet_num_params.argtypes = [vp]
@@ -370,6 +372,12 @@ def riot_tc_sgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=N
     _check(None, "riot_tc_sgemm",
            load().riot_tc_sgemm(ta.encode(), tb.encode(), int(m), int(n), int(k), float(alpha), _ptr(A), int(lda),
                                 _ptr(B), int(ldb), float(beta), _ptr(C), int(ldc), _stream_handle(stream)))
+
+
+def riot_tc_gram(n, k, Y, ldy, G, ldg, stream=None):
+    """Lower triangle of G = Y^T Y (column-major FP32 Y, FP64 G) on the tensor cores."""
+    _check(None, "riot_tc_gram",
+           load().riot_tc_gram(int(n), int(k), _ptr(Y), int(ldy), _ptr(G), int(ldg), _stream_handle(stream)))
 
 
 def riot_get_trajectory(ctx, traj):
