@@ -161,11 +161,117 @@ cudaError_t gram_lower(int n, int k, const void *A, char tA, int64_t lda, double
     return cudaGetLastError();
 }
 
+// FP64 GEMM with 16 x 16 output tiles (one output per thread) for the thin
+// updates of the blocked Cholesky and triangular solves (K = 32): FP64 issue
+// per SM is the limit on this GPU, so many small tiles spread over all SMs
+// finish sooner than few large ones.  lower_only skips tiles above the
+// diagonal.
+__global__ void __launch_bounds__(256) gemm16_kernel(int ta, int tb, int m, int n, int K, double alpha,
+                                                     const double *__restrict__ A, long long lda,
+                                                     const double *__restrict__ B, long long ldb, double beta,
+                                                     double *__restrict__ C, long long ldc, int lower_only)
+{
+    if (lower_only && blockIdx.y > blockIdx.x) return;
+    __shared__ double As[32][17];
+    __shared__ double Bs[32][17];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int m0 = blockIdx.x * 16, n0 = blockIdx.y * 16;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int e = t + 256 * r;
+            int i, kk;
+            if (!ta) { i = e & 15; kk = e >> 4; } else { kk = e & 31; i = e >> 5; }
+            As[kk][i] = (m0 + i < m && k0 + kk < K)
+                            ? (ta ? A[(k0 + kk) + (long long)(m0 + i) * lda] : A[(m0 + i) + (long long)(k0 + kk) * lda])
+                            : 0.0;
+            int j;
+            if (!tb) { kk = e & 31; j = e >> 5; } else { j = e & 15; kk = e >> 4; }
+            Bs[kk][j] = (n0 + j < n && k0 + kk < K)
+                            ? (tb ? B[(n0 + j) + (long long)(k0 + kk) * ldb] : B[(k0 + kk) + (long long)(n0 + j) * ldb])
+                            : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) acc = fma(As[kk][tx], Bs[kk][ty], acc);
+        __syncthreads();
+    }
+    const int i = m0 + tx, j = n0 + ty;
+    if (i < m && j < n) {
+        double *p = C + i + (long long)j * ldc;
+        *p = alpha * acc + (beta != 0.0 ? beta * *p : 0.0);
+    }
+}
+
+static cudaError_t gemm16(char ta, char tb, int m, int n, int k, double alpha, const double *A, int64_t lda,
+                          const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t s,
+                          int lower_only = 0)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    dim3 grid((m + 15) / 16, (n + 15) / 16);
+    count_launch();
+    gemm16_kernel<<<grid, 256, 0, s>>>(ta == 'T', tb == 'T', m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, lower_only);
+    return cudaGetLastError();
+}
+
+// Single-column products (y = alpha op(A) x + beta y, FP64), which the tiled
+// GEMM would run at 1/32 of its lanes: y = A^T x takes one warp per output
+// (lanes stride the long dimension); y = A x takes 32 rows per CTA of 8 warps,
+// the warps splitting the columns, partial sums reduced in shared memory.
+__global__ void __launch_bounds__(256) gemv_t_kernel(int m, int K, double alpha, const double *__restrict__ A,
+                                                     long long lda, const double *__restrict__ x, double beta,
+                                                     double *__restrict__ y)
+{
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= m) return;
+    const double *a = A + (long long)j * lda;
+    double s0 = 0.0, s1 = 0.0;
+    int l = lane;
+    for (; l + 32 < K; l += 64) {
+        s0 = fma(a[l], x[l], s0);
+        s1 = fma(a[l + 32], x[l + 32], s1);
+    }
+    if (l < K) s0 = fma(a[l], x[l], s0);
+    double v = s0 + s1;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) y[j] = alpha * v + (beta != 0.0 ? beta * y[j] : 0.0);
+}
+
+__global__ void __launch_bounds__(256) gemv_n_kernel(int m, int K, double alpha, const double *__restrict__ A,
+                                                     long long lda, const double *__restrict__ x, double beta,
+                                                     double *__restrict__ y)
+{
+    __shared__ double part[8][33];
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31), w = threadIdx.x >> 5;
+    double v = 0.0;
+    if (i < m)
+        for (int l = w; l < K; l += 8) v = fma(A[i + (long long)l * lda], x[l], v);
+    part[w][threadIdx.x & 31] = v;
+    __syncthreads();
+    if (w == 0 && i < m) {
+        double t = 0.0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) t += part[r][threadIdx.x];
+        y[i] = alpha * t + (beta != 0.0 ? beta * y[i] : 0.0);
+    }
+}
+
 cudaError_t gemm(char ta, char tb, int m, int n, int k, double alpha, const void *A, char tA, int64_t lda,
                  const void *B, char tB, int64_t ldb, double beta, void *C, char tC, int64_t ldc, cudaStream_t s)
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
     const int a = (ta == 'T'), b = (tb == 'T');
+    if (n == 1 && tb == 'N' && tA == 'd' && tB == 'd' && tC == 'd' && k > 0) {
+        count_launch();
+        if (a)
+            gemv_t_kernel<<<(m + 7) / 8, 256, 0, s>>>(m, k, alpha, (const double *)A, lda, (const double *)B, beta,
+                                                      (double *)C);
+        else
+            gemv_n_kernel<<<(m + 31) / 32, 256, 0, s>>>(m, k, alpha, (const double *)A, lda, (const double *)B, beta,
+                                                        (double *)C);
+        return cudaGetLastError();
+    }
 #define RIOT_GEMM_CASE(XA, XB, XC, TA_, TB_, TC_) \
     if (tA == XA && tB == XB && tC == XC) return gemm_t<TA_, TB_, TC_>(a, b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
     RIOT_GEMM_CASE('d', 'd', 'd', double, double, double)
@@ -375,60 +481,101 @@ __device__ void tri_inverse_smem(const double (*a)[NB + 1], const double *rinv, 
     }
 }
 
-// Cholesky of the jb x jb diagonal block at (J, J) by one CTA of 128 threads
-// (all four SM sub-partitions issue FP64 work), with the inverse of the
-// factor built in the same column sweep (X <- L^-1 by the same right-looking
-// elimination applied to the identity), written to dinv (NB x NB,
-// column-major).  The first failing pivot is recorded in info (1-based); the
+// Cholesky of the jb x jb diagonal block at (J, J) by one CTA of 128 threads,
+// then the inverse of the factor, written to dinv (NB x NB, column-major).
+// Factorisation: thread t holds row t / 4 of the block in registers, columns
+// t % 4 + 4 s (s < 8); per column j the pivot and the new column of L go
+// through shared memory (double-buffered, two barriers per column), and a
+// warp issues the FP64 update of a column slot only when some lane of it has
+// work: FP64 issue is the cost on this GPU.  Inverse: with L in shared
+// memory, four lanes per column c solve L x = e_c by forward substitution
+// (rows split by i mod 4, x_j passed by shuffles), so no block barrier is
+// needed.  The first failing pivot is recorded in info (1-based); the
 // factorisation continues with pivot 1.
 __global__ void __launch_bounds__(128) potrf_inv_kernel(double *G, int64_t ldg, int J, int jb, int *info, double *dinv)
 {
-    __shared__ double a[NB][NB + 1];
-    __shared__ double x[NB][NB + 1];
-    __shared__ double rs_s;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int i = e % NB, c = e / NB;
-        a[i][c] = (i < jb && c < jb) ? G[(J + i) + (int64_t)(J + c) * ldg] : 0.0;
-        x[i][c] = (i == c) ? 1.0 : 0.0;
+    __shared__ double colb[2][NB];   // l_ij of column j, rows i > j
+    __shared__ double piv[2];
+    __shared__ double Ls[NB][NB + 1];
+    __shared__ double rinv[NB];
+    const int t = threadIdx.x, i = t >> 2, q = t & 3, w = t >> 5;
+    double a[NB / 4];
+#pragma unroll
+    for (int s = 0; s < NB / 4; ++s) {
+        const int c = 4 * s + q;
+        a[s] = (i < jb && c <= i) ? G[(J + i) + (int64_t)(J + c) * ldg] : 0.0;
     }
-    __syncthreads();
-    for (int j = 0; j < jb; ++j) {
-        if (tid == 0) {
-            double d = a[j][j];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j >= jb) break;
+        const int b = j & 1;
+        if (i == j && q == (j & 3)) {
+            double d = a[j >> 2];
             if (!(d > 0.0) || !isfinite(d)) {
                 if (info[0] == 0) info[0] = J + j + 1;
                 d = 1.0;
             }
             const double r = rsqrt(d);
-            a[j][j] = d * r;
-            rs_s = r;
+            a[j >> 2] = d * r;
+            piv[b] = r;
+            rinv[j] = r;
         }
         __syncthreads();
-        const double r = rs_s;
-        // column j of L, and row j of the inverse (entries c <= j)
-        for (int i = j + 1 + tid; i < jb; i += blockDim.x) a[i][j] *= r;
-        for (int c = tid; c <= j; c += blockDim.x) x[j][c] *= r;
-        __syncthreads();
-        // trailing update of A and of the inverse's rows below j
-        const int m = jb - j - 1;
-        for (int e = tid; e < m * m; e += blockDim.x) {
-            const int i = j + 1 + e % m, c = j + 1 + e / m;
-            if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
-        }
-        for (int e = tid; e < m * (j + 1); e += blockDim.x) {
-            const int i = j + 1 + e / (j + 1), c = e % (j + 1);
-            x[i][c] = fma(-a[i][j], x[j][c], x[i][c]);
+        if (i > j && q == (j & 3)) {
+            a[j >> 2] *= piv[b];
+            colb[b][i] = a[j >> 2];
         }
         __syncthreads();
+        if (8 * w + 7 > j && i > j) {
+            const double lij = colb[b][i];
+#pragma unroll
+            for (int s = 0; s < NB / 4; ++s) {
+                const int c = 4 * s + q;
+                if (4 * s + 3 > j && 4 * s <= 8 * w + 7) {   // warp-uniform: some lane may have c in (j, i]
+                    if (c > j && c <= i) a[s] = fma(-lij, colb[b][c], a[s]);
+                }
+            }
+        }
     }
-    for (int e = tid; e < jb * jb; e += blockDim.x) {
-        const int i = e % jb, c = e / jb;
-        G[(J + i) + (int64_t)(J + c) * ldg] = (c <= i) ? a[i][c] : 0.0;
+#pragma unroll
+    for (int s = 0; s < NB / 4; ++s) {
+        const int c = 4 * s + q;
+        const double v = (i < jb && c < jb && c <= i) ? a[s] : 0.0;
+        Ls[i][c] = v;
+        if (i < jb && c < jb) G[(J + i) + (int64_t)(J + c) * ldg] = v;
     }
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int i = e % NB, c = e / NB;
-        dinv[e] = (i >= c && i < jb && c < jb) ? x[i][c] : 0.0;
+    __syncthreads();
+    // column c = t / 4 of X = L^-1; lane q keeps rows i = q + 4 s
+    {
+        const int c = t >> 2;
+        double xv[NB / 4];
+#pragma unroll
+        for (int s = 0; s < NB / 4; ++s) xv[s] = (4 * s + q == c) ? 1.0 : 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            if (j >= jb) break;
+            // x_j = x_j / l_jj is held by lane j % 4 of this column's group, slot j / 4
+            double xj = 0.0;
+            if (q == (j & 3)) {
+                xv[j >> 2] *= rinv[j];
+                xj = xv[j >> 2];
+            }
+            xj = __shfl_sync(0xffffffffu, xj, (t & 31 & ~3) | (j & 3));
+            if (j >= 8 * w) {      // warp-uniform: columns of this warp are 8 w .. 8 w + 7 <= j possible
+#pragma unroll
+                for (int s = 0; s < NB / 4; ++s) {
+                    const int r = 4 * s + q;
+                    if (4 * s + 3 > j) {
+                        if (r > j && c <= j) xv[s] = fma(-Ls[r][j], xj, xv[s]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NB / 4; ++s) {
+            const int r = 4 * s + q;
+            dinv[r + NB * c] = (r >= c && r < jb && c < jb) ? xv[s] : 0.0;
+        }
     }
 }
 
@@ -553,8 +700,9 @@ cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *inf
             double *A21 = G + (J + jb) + (int64_t)J * ldg;
             // A21 <- A21 L11^-T
             { count_launch(); trmm_rows_kernel<<<(m2 + 7) / 8, 256, 0, s>>>(A21, m2, ldg, inv, jb, 1); }
+            // A22 -= A21 A21^T, lower tiles only (the factorisation never reads above the diagonal)
             double *A22 = G + (J + jb) + (int64_t)(J + jb) * ldg;
-            e = gemm('N', 'T', m2, m2, jb, -1.0, A21, 'd', ldg, A21, 'd', ldg, 1.0, A22, 'd', ldg, s);
+            e = gemm16('N', 'T', m2, m2, jb, -1.0, A21, ldg, A21, ldg, 1.0, A22, ldg, s, 1);
             if (e != cudaSuccess) return e;
         }
     }
@@ -578,9 +726,8 @@ cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L,
                                                      jb, 1);
         const int rest = k - J - jb;
         if (rest > 0) {
-            cudaError_t e = gemm('N', 'T', m, rest, jb, -1.0, X + (int64_t)J * ldx, 'd', ldx,
-                                 L + (J + jb) + (int64_t)J * ldl, 'd', ldl, 1.0, X + (int64_t)(J + jb) * ldx, 'd',
-                                 ldx, s);
+            cudaError_t e = gemm16('N', 'T', m, rest, jb, -1.0, X + (int64_t)J * ldx, ldx, L + (J + jb) + (int64_t)J * ldl,
+                                   ldl, 1.0, X + (int64_t)(J + jb) * ldx, ldx, s);
             if (e != cudaSuccess) return e;
         }
     }
@@ -597,8 +744,7 @@ cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, 
         count_launch();
         trmm_rows_kernel<<<(m + 7) / 8, 256, 0, s>>>(X + (int64_t)J * ldx, m, ldx, dinv + (int64_t)b * NB * NB, jb, 0);
         if (J > 0) {
-            cudaError_t e = gemm('N', 'N', m, J, jb, -1.0, X + (int64_t)J * ldx, 'd', ldx, L + J, 'd', ldl, 1.0, X,
-                                 'd', ldx, s);
+            cudaError_t e = gemm16('N', 'N', m, J, jb, -1.0, X + (int64_t)J * ldx, ldx, L + J, ldl, 1.0, X, ldx, s);
             if (e != cudaSuccess) return e;
         }
     }
