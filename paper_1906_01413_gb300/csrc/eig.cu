@@ -4,9 +4,10 @@
 // synchronisations is O(k), not O(k x sweeps).
 //
 //  1. Householder tridiagonalisation Q^T K Q = T in one cooperative launch,
-//     two grid barriers per column (matrix-vector products, then the rank-2
-//     update with the next column's reflector computed by the warp that
-//     owns it); Q is accumulated as Q^T on the fly.
+//     one grid barrier per column: every CTA derives the next reflector
+//     itself, and each warp's rank-2 update of a column is followed at once
+//     by that column's product with the next reflector; Q is accumulated as
+//     Q^T on the fly.
 //  2. T splits where an off-diagonal is negligible; each unreduced block's
 //     eigenvalues come from a grid of Sturm counts followed by multisection
 //     (one warp per eigenvalue, 32 Sturm counts per round).
@@ -55,105 +56,188 @@ __global__ void eig_init_kernel(const double *K, int k, double *A, double *Qt)
     }
 }
 
-// Householder reflector of x = A[r0..k-1, col] computed by one warp:
-// H = I - beta v v^T with H x = e_out e_1.  v is written to vbuf[r0..k-1].
-__device__ void warp_house(const double *A, int k, int col, int r0, double *vbuf, double *beta_out, double *e_out,
-                           int lane)
+// Block-wide sum of one value per thread (blockDim.x = 256); every thread gets it.
+__device__ __forceinline__ double block_sum(double v, double *red)
 {
-    const double *x = A + (int64_t)col * k;
-    double ss = 0.0;
-    for (int l = r0 + lane; l < k; l += 32) ss += x[l] * x[l];
-    ss = warp_sum(ss);
-    const double x0 = x[r0];
-    const double alpha = sqrt(ss);
-    if (alpha == 0.0) {
-        for (int l = r0 + lane; l < k; l += 32) vbuf[l] = 0.0;
-        if (lane == 0) { *beta_out = 0.0; *e_out = 0.0; }
-        return;
-    }
-    const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
-    for (int l = r0 + lane; l < k; l += 32) vbuf[l] = (l == r0) ? x0 + sgn * alpha : x[l];
-    if (lane == 0) {
-        *beta_out = 1.0 / (alpha * (alpha + fabs(x0)));
-        *e_out = -sgn * alpha;
-    }
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __syncthreads();   // red is free again
+    if (lane == 0) red[wib] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w];
+    return t;
 }
 
-__global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int k, double *vbuf, double *pbuf,
-                                                      double *qbuf, double *d, double *e, double *beta)
+// Householder reflector of x = col[r0..k-1], computed by the whole CTA (every
+// CTA forms the same one): H = I - beta v v^T, H x = e_out e_1; v goes to
+// vs[r0..k-1] (zero below r0).
+__device__ void block_house(const double *col, int k, int r0, double *vs, double *beta_out, double *e_out,
+                            double *red)
+{
+    double ss = 0.0;
+    for (int l = r0 + threadIdx.x; l < k; l += blockDim.x) ss += col[l] * col[l];
+    ss = block_sum(ss, red);
+    const double x0 = col[r0];
+    const double alpha = sqrt(ss);
+    const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
+    for (int l = threadIdx.x; l < k; l += blockDim.x)
+        vs[l] = (l < r0 || alpha == 0.0) ? 0.0 : (l == r0 ? x0 + sgn * alpha : col[l]);
+    if (threadIdx.x == 0) {
+        *beta_out = (alpha == 0.0) ? 0.0 : 1.0 / (alpha * (alpha + fabs(x0)));
+        *e_out = (alpha == 0.0) ? 0.0 : -sgn * alpha;
+    }
+    __syncthreads();
+}
+
+// Householder tridiagonalisation Q^T K Q = T, one grid barrier per column.
+// Column j: with p = beta A22 v and q = beta Q^T-columns . v of reflector j
+// complete, every CTA forms K_ = beta / 2 v^T p, w = p - K_ v, the updated
+// column j + 1 and from it reflector j + 1 (the same in every CTA, so nothing
+// is exchanged); then each warp updates its A22 or Q^T column (rank 2 or
+// rank 1) and at once takes its dot product with reflector j + 1, which is
+// the next column's p or q.  Column j + 1 itself is left to the CTAs (each
+// derives it), so no CTA writes what another still reads.  p and q are
+// double-buffered across the barrier.
+__global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int k, double *pq, double *d, double *e)
 {
     cg::grid_group grid = cg::this_grid();
+    extern __shared__ double sm[];
+    double *vcur = sm, *vnext = sm + k, *w = sm + 2 * k, *colj = sm + 3 * k, *red = sm + 4 * k;
+    __shared__ double bcur_s, bnext_s, enext_s;
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    const int gw = blockIdx.x * wpb + wib;
-    const int nw = gridDim.x * wpb;
-    __shared__ double kh_s;
-
-    if (k >= 3 && gw == 0) {
-        if (lane == 0) d[0] = A[0];
-        warp_house(A, k, 0, 1, vbuf, &beta[0], &e[0], lane);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    if (k < 3) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            d[0] = A[0];
+            if (k == 2) {
+                e[0] = A[1];
+                d[1] = A[1 + (int64_t)k];
+            }
+        }
+        return;
+    }
+    // reflector 0 from column 0, and its p, q
+    block_house(A, k, 1, vcur, &bcur_s, &enext_s, red);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d[0] = A[0];
+        e[0] = enext_s;
+    }
+    {
+        const double bt = bcur_s;
+        const int m = k - 1;
+        for (int it = gw; it < m + k; it += nw) {
+            const double *col = (it < m) ? A + (int64_t)(1 + it) * k : Qt + (int64_t)(it - m) * k;
+            double s = 0.0;
+            for (int l = 1 + lane; l < k; l += 32) s += col[l] * vcur[l];
+            s = warp_sum(s);
+            if (lane == 0) {
+                if (it < m) pq[1 + it] = bt * s;           // p of column 0 in buffer 0
+                else pq[2 * k + it - m] = bt * s;          // q of column 0 in buffer 0
+            }
+        }
     }
     grid.sync();
     for (int j = 0; j + 2 < k; ++j) {
-        const double *v = vbuf + (size_t)(j & 1) * k;
-        const double bt = beta[j & 1];
-        const int r0 = j + 1, m = k - r0;
-        // phase 2: p = beta A22 v (columns r0..k-1), q = beta Q v (all columns of Q^T)
-        for (int it = gw; it < m + k; it += nw) {
-            const double *col = (it < m) ? A + (int64_t)(r0 + it) * k : Qt + (int64_t)(it - m) * k;
-            double s = 0.0;
-            for (int l = r0 + lane; l < k; l += 32) s += col[l] * v[l];
-            s = warp_sum(s);
-            if (lane == 0) {
-                if (it < m) pbuf[r0 + it] = bt * s;
-                else qbuf[it - m] = bt * s;
+        const int r0 = j + 1, m = k - r0, par = j & 1;
+        const bool next = (j + 3 < k);   // another reflector follows (column j + 1 has rows below r0 + 1)
+        const double bt = bcur_s;
+        const double *p = pq + (size_t)par * k, *q = pq + 2 * (size_t)k + (size_t)par * k;
+        // p and column r0 of A (rows r0..) fetched together, then K_ and w = p - K_ v
+        {
+            const double *a = A + (int64_t)r0 * k;
+            for (int l = threadIdx.x; l < k; l += blockDim.x) {
+                const bool in = (l >= r0);
+                w[l] = in ? p[l] : 0.0;
+                colj[l] = (in && next) ? a[l] : 0.0;
             }
         }
-        grid.sync();
-        // K_ = beta / 2 v^T p, once per block
-        if (wib == 0) {
-            double s = 0.0;
-            for (int l = r0 + lane; l < k; l += 32) s += v[l] * pbuf[l];
-            s = warp_sum(s);
-            if (lane == 0) kh_s = 0.5 * bt * s;
-        }
+        double s = 0.0;   // same partition of l as the fetch above: no barrier needed in between
+        for (int l = threadIdx.x; l < k; l += blockDim.x)
+            if (l >= r0) s += vcur[l] * w[l];
+        const double kh = 0.5 * bt * block_sum(s, red);
+        for (int l = threadIdx.x; l < k; l += blockDim.x)
+            if (l >= r0) w[l] -= kh * vcur[l];
         __syncthreads();
-        const double kh = kh_s;
-        // phase 3: A22 -= v w^T + w v^T (w = p - kh v), Q^T col i -= q_i v.
-        // Warp 0 owns column r0 of A and then builds the next reflector.
+        double bn = 0.0;
+        if (next) {
+            // column r0 after this step's update, rows r0..; then reflector j + 1 from rows r0 + 1..
+            const double wr = w[r0], vr = vcur[r0];
+            for (int l = r0 + threadIdx.x; l < k; l += blockDim.x) colj[l] -= vcur[l] * wr + w[l] * vr;
+            __syncthreads();
+            block_house(colj, k, r0 + 1, vnext, &bnext_s, &enext_s, red);
+            __syncthreads();
+            bn = bnext_s;
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                d[r0] = colj[r0];
+                e[r0] = enext_s;
+            }
+        }
+        const int r1 = r0 + 1;
+        double *pn = pq + (size_t)(par ^ 1) * k, *qn = pq + 2 * (size_t)k + (size_t)(par ^ 1) * k;
         for (int it = gw; it < m + k; it += nw) {
             if (it < m) {
                 const int i = r0 + it;
+                if (next && i == r0) continue;   // derived by every CTA above; never written
                 double *col = A + (int64_t)i * k;
-                const double vi = v[i], wi = pbuf[i] - kh * vi;
-                for (int l = r0 + lane; l < k; l += 32) col[l] -= v[l] * wi + (pbuf[l] - kh * v[l]) * vi;
+                const double vi = vcur[i], wi = w[i];
+                double t = 0.0;
+                for (int l0 = r0 + lane; l0 < k; l0 += 128) {   // four loads in flight per lane
+                    double x[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) x[u] = (l0 + 32 * u < k) ? col[l0 + 32 * u] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int l = l0 + 32 * u;
+                        if (l < k) {
+                            x[u] -= vcur[l] * wi + w[l] * vi;
+                            col[l] = x[u];
+                            if (l >= r1) t = fma(x[u], vnext[l], t);
+                        }
+                    }
+                }
+                if (next) {
+                    t = warp_sum(t);
+                    if (lane == 0) pn[i] = bn * t;
+                }
             } else {
                 const int i = it - m;
                 double *col = Qt + (int64_t)i * k;
-                const double qi = qbuf[i];
-                if (qi != 0.0)
-                    for (int l = r0 + lane; l < k; l += 32) col[l] -= qi * v[l];
-            }
-            if (it == 0) {
-                __syncwarp();
-                if (lane == 0) d[r0] = A[r0 + (int64_t)r0 * k];
-                if (r0 + 2 < k) {
-                    warp_house(A, k, r0, r0 + 1, vbuf + (size_t)((j + 1) & 1) * k, &beta[(j + 1) & 1], &e[r0], lane);
+                const double qi = q[i];
+                double t = 0.0;
+                for (int l0 = r0 + lane; l0 < k; l0 += 128) {
+                    double x[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) x[u] = (l0 + 32 * u < k) ? col[l0 + 32 * u] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int l = l0 + 32 * u;
+                        if (l < k) {
+                            x[u] -= qi * vcur[l];
+                            col[l] = x[u];
+                            if (l >= r1) t = fma(x[u], vnext[l], t);
+                        }
+                    }
+                }
+                if (next) {
+                    t = warp_sum(t);
+                    if (lane == 0) qn[i] = bn * t;
                 }
             }
         }
+        // reflector j + 1 becomes the current one, once every warp of the CTA is done with both
+        __syncthreads();
+        for (int l = threadIdx.x; l < k; l += blockDim.x) vcur[l] = vnext[l];
+        if (threadIdx.x == 0) bcur_s = bn;
         grid.sync();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (k == 1) {
-            d[0] = A[0];
-        } else {
-            // last 2 x 2 block (for k == 2 also d[0], e[0])
-            d[k - 2] = A[(k - 2) + (int64_t)(k - 2) * k];
-            e[k - 2] = A[(k - 1) + (int64_t)(k - 2) * k];
-            d[k - 1] = A[(k - 1) + (int64_t)(k - 1) * k];
-        }
+        // last 2 x 2 block
+        d[k - 2] = A[(k - 2) + (int64_t)(k - 2) * k];
+        e[k - 2] = A[(k - 1) + (int64_t)(k - 2) * k];
+        d[k - 1] = A[(k - 1) + (int64_t)(k - 1) * k];
     }
 }
 
@@ -428,8 +512,8 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     double *u0 = work + 4 * kk, *u1 = work + 5 * kk, *u2 = work + 6 * kk, *ml = work + 7 * kk;
     unsigned char *piv = (unsigned char *)(work + 8 * kk);
     double *vec = work + 9 * kk;
-    double *vbuf = vec, *pbuf = vec + 2 * k, *qbuf = vec + 3 * k, *d = vec + 4 * k, *e = vec + 5 * k;
-    double *e2 = vec + 6 * k, *w = vec + 7 * k, *beta = vec + 8 * k, *tnorm = vec + 8 * k + 2;
+    double *pq = vec, *d = vec + 4 * k, *e = vec + 5 * k;   // pq: p and q of two consecutive columns
+    double *e2 = vec + 6 * k, *w = vec + 7 * k, *tnorm = vec + 8 * k + 2;
     int *blo = (int *)(vec + 9 * k), *bhi = (int *)(vec + 10 * k);
     int *bstart = (int *)(vec + 11 * k), *nblocks = (int *)(vec + 12 * k);
     double *wrq = vec + 13 * k;
@@ -442,13 +526,18 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     eig_init_kernel<<<256, 256, 0, s>>>(K, k, A, Qt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     {
+        const size_t smem = sizeof(double) * (4 * (size_t)k + 8);
+        if ((err = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return err;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, 256, 0);
-        (void)per_sm;
+        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, 256, smem)) != cudaSuccess)
+            return err;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
         const int grid = num_sms();   // one CTA per SM keeps the grid barrier short
-        void *args[] = {&A, &Qt, &k, &vbuf, &pbuf, &qbuf, &d, &e, &beta};
+        void *args[] = {&A, &Qt, &k, &pq, &d, &e};
         count_launch();
-        err = cudaLaunchCooperativeKernel((void *)tridiag_kernel, grid, 256, args, 0, s);
+        err = cudaLaunchCooperativeKernel((void *)tridiag_kernel, grid, 256, args, smem, s);
         if (err != cudaSuccess) return err;
     }
     count_launch();
