@@ -264,7 +264,8 @@ riot_status orth32(riot_ctx *ctx, const float *Y, int k, int info_base, int pass
                                  : 0.0;
         CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
         CU(convert_block(ctx->G, 'd', k, ctx->L32, 'f', k, k, k, ctx->s));
-        CU(strsm_right_lt(ctx->Q32, n, k, n, ctx->L32, k, ctx->s));
+        CU(put_block_inverses(ctx->L32, k, k, ctx->gws, ctx->s));
+        CU(strsm_right_lt_inv(ctx->Q32, n, k, n, ctx->L32, k, ctx->s));
     }
     return RIOT_OK;
 }

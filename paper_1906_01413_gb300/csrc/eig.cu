@@ -241,31 +241,73 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
     }
 }
 
-// Split T where |e_l| <= eps (|d_l| + |d_{l+1}|); block bounds per index; e^2.
-__global__ void split_kernel(const double *d, const double *e, int k, double *e2, int *blo, int *bhi, double *tnorm,
-                             int *bstart, int *nblocks)
+// Split T where |e_l| <= eps (|d_l| + |d_{l+1}|); block bounds per index; e^2;
+// ||T||_inf.  One CTA of 1024 threads: split flags in parallel, block starts
+// by a prefix count over 1024-index tiles, bounds written per index.
+__global__ void __launch_bounds__(1024) split_kernel(const double *d, const double *e, int k, double *e2, int *blo,
+                                                     int *bhi, double *tnorm, int *bstart, int *nblocks)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    __shared__ int cnt[1024];
+    __shared__ double red[32];
+    __shared__ int base_s, lo_carry_s;
+    const int t = threadIdx.x;
     double nrm = 0.0;
-    for (int l = 0; l < k; ++l) {
+    for (int l = t; l < k; l += blockDim.x) {
         double r = fabs(d[l]);
         if (l > 0) r += fabs(e[l - 1]);
         if (l + 1 < k) r += fabs(e[l]);
         nrm = fmax(nrm, r);
     }
-    *tnorm = nrm;
-    int lo = 0, nb = 0;
-    for (int l = 0; l < k; ++l) {
-        const bool split = (l + 1 == k) || fabs(e[l]) <= DBL_EPSILON * (fabs(d[l]) + fabs(d[l + 1]));
-        if (l + 1 < k) e2[l] = split ? 0.0 : e[l] * e[l];
-        if (split) {
-            for (int i = lo; i <= l; ++i) { blo[i] = lo; bhi[i] = l; }
-            bstart[nb++] = lo;
-            lo = l + 1;
-        }
+    for (int off = 16; off > 0; off >>= 1) nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, off));
+    if ((t & 31) == 0) red[t >> 5] = nrm;
+    if (t == 0) {
+        base_s = 0;
+        lo_carry_s = 0;
     }
-    bstart[nb] = k;
-    *nblocks = nb;
+    __syncthreads();
+    if (t == 0) {
+        double m = 0.0;
+        for (int w = 0; w < 32; ++w) m = fmax(m, red[w]);
+        *tnorm = m;
+    }
+    // index l ends a block when l = k - 1 or e_l is negligible
+    for (int l0 = 0; l0 < k; l0 += blockDim.x) {
+        const int l = l0 + t;
+        bool split = false;
+        if (l < k) {
+            split = (l + 1 == k) || fabs(e[l]) <= DBL_EPSILON * (fabs(d[l]) + fabs(d[l + 1]));
+            if (l + 1 < k) e2[l] = split ? 0.0 : e[l] * e[l];
+        }
+        cnt[t] = split ? 1 : 0;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {   // inclusive prefix sum
+            const int v = (t >= off) ? cnt[t - off] : 0;
+            __syncthreads();
+            cnt[t] += v;
+            __syncthreads();
+        }
+        const int base = base_s;
+        if (l < k && split) bstart[base + cnt[t]] = l + 1;   // start of the next block
+        __syncthreads();
+        if (t == 0) base_s = base + cnt[1023];
+        __syncthreads();
+    }
+    if (t == 0) {
+        bstart[0] = 0;
+        *nblocks = base_s;
+    }
+    __syncthreads();
+    // bstart[b] = first index of block b, bstart[nb] = k; bounds of each index by binary search
+    const int nb = base_s;
+    for (int l = t; l < k; l += blockDim.x) {
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {   // last block b with bstart[b] <= l
+            const int mid = (lo + hi + 1) >> 1;
+            if (bstart[mid] <= l) lo = mid; else hi = mid - 1;
+        }
+        blo[l] = bstart[lo];
+        bhi[l] = bstart[lo + 1] - 1;
+    }
 }
 
 // Number of eigenvalues of the block [lo, hi] below x (Sturm sequence).
@@ -397,10 +439,16 @@ __device__ __forceinline__ double hash_uniform(uint32_t a, uint32_t b)
 }
 
 // Inverse iteration for eigenvalue i of its block; scratch holds the LU of
-// T_b - w_i I in a strided layout (row l of thread i at l*k + i).
-__global__ void inviter_kernel(const double *d, const double *e, const int *blo, const int *bhi, int k, const double *w,
-                               const double *tnorm, double *Z, double *u0, double *u1, double *u2, double *ml,
-                               unsigned char *piv, double *wout)
+// T_b - w_i I in a strided layout (row l of thread i at l*k + i).  One FP64
+// division per row (the reciprocal of the pivot, kept for the back
+// substitution), so the three solves are multiply-adds only; values carried
+// from row to row stay in registers and the loads of the stored factors do not
+// wait on the arithmetic.
+__global__ void inviter_kernel(const double *__restrict__ d, const double *__restrict__ e, const int *__restrict__ blo,
+                               const int *__restrict__ bhi, int k, const double *__restrict__ w,
+                               const double *__restrict__ tnorm, double *__restrict__ Z, double *__restrict__ u0,
+                               double *__restrict__ u1, double *__restrict__ u2, double *__restrict__ ml,
+                               unsigned char *__restrict__ piv, double *__restrict__ wout)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= k) return;
@@ -416,16 +464,16 @@ __global__ void inviter_kernel(const double *d, const double *e, const int *blo,
     const double lam = w[i];
     const double tiny = DBL_EPSILON * fmax(*tnorm, DBL_MIN);
 #define IDX(l) ((int64_t)(l) * k + i)
-    // LU with partial pivoting of the block minus lam I (rows 0..m-1 local)
+    // LU with partial pivoting of the block minus lam I (rows 0..m-1 local); u0 keeps 1 / pivot
     double a_cur = d[lo] - lam, c_cur = e[lo];
     for (int l = 0; l < m - 1; ++l) {
         const double bl = e[lo + l];                 // sub-diagonal below a_cur
         const double a_next = d[lo + l + 1] - lam;
         const double c_next = (l + 1 < m - 1) ? e[lo + l + 1] : 0.0;
         if (fabs(a_cur) >= fabs(bl)) {
-            const double piv_v = (a_cur == 0.0) ? tiny : a_cur;
-            const double mult = bl / piv_v;
-            u0[IDX(l)] = piv_v;
+            const double rp = 1.0 / ((a_cur == 0.0) ? tiny : a_cur);
+            const double mult = bl * rp;
+            u0[IDX(l)] = rp;
             u1[IDX(l)] = c_cur;
             u2[IDX(l)] = 0.0;
             ml[IDX(l)] = mult;
@@ -433,8 +481,9 @@ __global__ void inviter_kernel(const double *d, const double *e, const int *blo,
             a_cur = a_next - mult * c_cur;
             c_cur = c_next;
         } else {
-            const double mult = a_cur / bl;
-            u0[IDX(l)] = bl;
+            const double rp = 1.0 / bl;
+            const double mult = a_cur * rp;
+            u0[IDX(l)] = rp;
             u1[IDX(l)] = a_next;
             u2[IDX(l)] = c_next;
             ml[IDX(l)] = mult;
@@ -443,21 +492,25 @@ __global__ void inviter_kernel(const double *d, const double *e, const int *blo,
             c_cur = -mult * c_next;
         }
     }
-    u0[IDX(m - 1)] = (fabs(a_cur) < tiny) ? (a_cur < 0.0 ? -tiny : tiny) : a_cur;
+    u0[IDX(m - 1)] = 1.0 / ((fabs(a_cur) < tiny) ? (a_cur < 0.0 ? -tiny : tiny) : a_cur);
     // start vector: distinct pseudo-random values per eigenvalue
     for (int l = 0; l < m; ++l) z[lo + l] = hash_uniform((uint32_t)i, (uint32_t)l) + 1e-3;
     for (int iter = 0; iter < 3; ++iter) {
-        // forward: apply the row operations
+        // forward: apply the row operations (row l + 1 carried in a register)
+        double carry = z[lo];
         for (int l = 0; l < m - 1; ++l) {
-            double r0v = z[lo + l], r1v = z[lo + l + 1];
-            if (piv[IDX(l)]) { const double t = r0v; r0v = r1v; r1v = t; }
+            const double nxt = z[lo + l + 1];
+            const bool sw = piv[IDX(l)] != 0;
+            const double mlt = ml[IDX(l)];
+            const double r0v = sw ? nxt : carry, r1v = sw ? carry : nxt;
             z[lo + l] = r0v;
-            z[lo + l + 1] = r1v - ml[IDX(l)] * r0v;
+            carry = r1v - mlt * r0v;
         }
-        // backward substitution with U (diagonals u0, u1, u2)
+        z[lo + m - 1] = carry;
+        // backward substitution with U (1 / diagonal, u1, u2)
         double x2 = 0.0, x1 = 0.0, big = 0.0;
         for (int l = m - 1; l >= 0; --l) {
-            const double xl = (z[lo + l] - u1[IDX(l)] * x1 - u2[IDX(l)] * x2) / u0[IDX(l)];
+            const double xl = (z[lo + l] - u1[IDX(l)] * x1 - u2[IDX(l)] * x2) * u0[IDX(l)];
             z[lo + l] = xl;
             x2 = x1;
             x1 = xl;
@@ -541,7 +594,7 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
         if (err != cudaSuccess) return err;
     }
     count_launch();
-    split_kernel<<<1, 1, 0, s>>>(d, e, k, e2, blo, bhi, tnorm, bstart, nblocks);
+    split_kernel<<<1, 1024, 0, s>>>(d, e, k, e2, blo, bhi, tnorm, bstart, nblocks);
     count_launch();
     prebracket_kernel<<<2 * num_sms(), 128, 0, s>>>(d, e2, bstart, nblocks, tnorm, counts);
     {

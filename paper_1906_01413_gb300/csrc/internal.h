@@ -228,7 +228,11 @@ cudaError_t tc_gram_f32(int n, int k, const float *Y, int64_t ldy, double *G, in
                         cudaStream_t s);
 size_t tc_gram_ws_bytes(int k);
 // X <- X L^-T in FP32 (L: k x k lower, FP32)
-cudaError_t strsm_right_lt(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s);
+// Diagonal 32 x 32 blocks of L32 replaced by the FP32 rounding of the block
+// inverses dinv that cholesky leaves; strsm_right_lt_inv then solves
+// X <- X L^-T with products by those inverses (no substitution chains).
+cudaError_t put_block_inverses(float *L32, int k, int64_t ldl, const double *dinv, cudaStream_t s);
+cudaError_t strsm_right_lt_inv(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s);
 cudaError_t convert_block(const void *in, char tin, int64_t ldin, void *out, char tout, int64_t ldout,
                           int64_t rows, int cols, cudaStream_t s);
 // In-place blocked Cholesky of the k x k SPD matrix G (lower factor); adds

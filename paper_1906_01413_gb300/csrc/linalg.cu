@@ -354,43 +354,57 @@ cudaError_t sgemm(char ta, char tb, int m, int n, int k, float alpha, const floa
     return cudaGetLastError();
 }
 
-// X[r, 0:jb] <- X[r, 0:jb] L^-T in FP32, one row per thread (right-looking).
-__global__ void strsm_rows_lt_kernel(float *X, int m, int64_t ldx, const float *Ld, int64_t ldl, int jb)
+// X[r, 0:jb] <- X[r, 0:jb] M^T for m rows, M the jb x jb lower-triangular
+// block at Minv (ld ldm, FP32): 8 rows x 32 columns per CTA, one output per
+// thread (a product with the block inverse instead of a substitution: no
+// dependent chain, and enough CTAs to spread over every SM).
+__global__ void __launch_bounds__(256) strmm_rows_kernel(float *X, int m, int64_t ldx, const float *Minv, int64_t ldm,
+                                                         int jb)
 {
-    __shared__ float Ls[32][33];
-    __shared__ float rinv[32];
-    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
-        const int i = e % jb, j = e / jb;
-        Ls[i][j] = Ld[i + (int64_t)j * ldl];
+    __shared__ float xs[8][33];
+    __shared__ float ms[32][33];
+    const int c = threadIdx.x & 31, rl = threadIdx.x >> 5;
+    const int r = blockIdx.x * 8 + rl;
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int i = e & 31, j = e >> 5;
+        ms[i][j] = (i < jb && j < jb && j <= i) ? Minv[i + (int64_t)j * ldm] : 0.f;
     }
-    for (int j = threadIdx.x; j < jb; j += blockDim.x) rinv[j] = 1.f / Ld[j + (int64_t)j * ldl];
+    xs[rl][c] = (r < m && c < jb) ? X[r + (int64_t)c * ldx] : 0.f;
     __syncthreads();
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= m) return;
-    float x[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = (j < jb) ? X[r + (int64_t)j * ldx] : 0.f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        if (j < jb) {
-            x[j] *= rinv[j];
-#pragma unroll
-            for (int i = j + 1; i < 32; ++i)
-                if (i < jb) x[i] = fmaf(-x[j], Ls[i][j], x[i]);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-        if (j < jb) X[r + (int64_t)j * ldx] = x[j];
+    if (r >= m || c >= jb) return;
+    float acc = 0.f;
+#pragma unroll 8
+    for (int i = 0; i <= c; ++i) acc = fmaf(xs[rl][i], ms[c][i], acc);
+    X[r + (int64_t)c * ldx] = acc;
 }
 
-cudaError_t strsm_right_lt(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s)
+// Diagonal blocks of the FP32 factor L32 (ld ldl) replaced by the FP32
+// rounding of the block inverses dinv (NB x NB each, from cholesky).
+__global__ void put_block_inverses_kernel(float *L32, int k, int64_t ldl, const double *dinv)
+{
+    const int b = blockIdx.x, J = b * 32;
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int i = e & 31, j = e >> 5;
+        if (J + i < k && J + j < k) L32[(J + i) + (int64_t)(J + j) * ldl] = (float)dinv[(int64_t)b * 1024 + e];
+    }
+}
+
+cudaError_t put_block_inverses(float *L32, int k, int64_t ldl, const double *dinv, cudaStream_t s)
+{
+    if (k <= 0) return cudaSuccess;
+    count_launch();
+    put_block_inverses_kernel<<<(k + 31) / 32, 256, 0, s>>>(L32, k, ldl, dinv);
+    return cudaGetLastError();
+}
+
+// X <- X L^-T (X m x k FP32) where the diagonal blocks of L hold their inverses
+// (put_block_inverses) and the blocks below them the factor itself.
+cudaError_t strsm_right_lt_inv(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s)
 {
     for (int J = 0; J < k; J += 32) {
         const int jb = (k - J < 32) ? k - J : 32;
         count_launch();
-        strsm_rows_lt_kernel<<<(m + 127) / 128, 128, 0, s>>>(X + (int64_t)J * ldx, m, ldx, L + J + (int64_t)J * ldl, ldl,
-                                                            jb);
+        strmm_rows_kernel<<<(m + 7) / 8, 256, 0, s>>>(X + (int64_t)J * ldx, m, ldx, L + J + (int64_t)J * ldl, ldl, jb);
         const int rest = k - J - jb;
         if (rest > 0) {
             cudaError_t e = sgemm('N', 'T', m, rest, jb, -1.f, X + (int64_t)J * ldx, ldx, L + (J + jb) + (int64_t)J * ldl,
