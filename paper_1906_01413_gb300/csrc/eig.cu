@@ -558,7 +558,8 @@ __global__ void eig_sort_kernel(const double *w, const double *Zt, int k, double
 
 }  // namespace
 
-cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *work, int *info, cudaStream_t s)
+cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *work, int *info, cudaStream_t s,
+                        bool fp32_vectors)
 {
     const size_t kk = (size_t)k * k;
     double *A = work, *Qt = work + kk, *Zt = work + 2 * kk, *Zs = work + 3 * kk;
@@ -608,13 +609,18 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     count_launch();
     inviter_kernel<<<(k + 3) / 4, 4, 0, s>>>(d, e, blo, bhi, k, w, tnorm, Zt, u0, u1, u2, ml, piv, wrq);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    // CholeskyQR on the eigenvectors of T: two shifted passes (Fukaya et al. 2020), so
-    // that eigenvalues clustered below the resolution eps ||T|| (whose inverse-iteration
-    // vectors nearly coincide) still yield an orthonormal set, then a plain pass
-    for (int pass = 0; pass < 3; ++pass) {
-        const double shift = pass < 2 ? 11.0 * ((double)k * k + (double)k * (k + 1)) * ldexp(1.0, -53) : 0.0;
-        if ((err = gram_lower(k, k, Zt, 'd', k, Zs, k, s)) != cudaSuccess) return err;
-        if ((err = cholesky(Zs, k, k, shift, info + (pass < 2 ? 0 : 1), dinv, s)) != cudaSuccess) return err;
+    // CholeskyQR on the eigenvectors of T: shifted passes (Fukaya et al. 2020), so that
+    // eigenvalues clustered below the resolution eps ||T|| (whose inverse-iteration
+    // vectors nearly coincide) still yield an orthonormal set, then a plain pass.  Two
+    // shifted passes make the set orthonormal to FP64 working accuracy; one leaves it
+    // within about 1e-7, enough for vectors that are used in FP32 (fp32_vectors).
+    // The Grams are split over K in the LU scratch of the inverse iteration.
+    const int shifted = fp32_vectors ? 1 : 2;
+    for (int pass = 0; pass <= shifted; ++pass) {
+        const double shift =
+            pass < shifted ? 11.0 * ((double)k * k + (double)k * (k + 1)) * ldexp(1.0, -53) : 0.0;
+        if ((err = gram_lower(k, k, Zt, 'd', k, Zs, k, s, u0, 4 * kk)) != cudaSuccess) return err;
+        if ((err = cholesky(Zs, k, k, shift, info + (pass < shifted ? 0 : 1), dinv, s)) != cudaSuccess) return err;
         if ((err = trsm_right_lt(Zt, k, k, k, Zs, k, s, dinv)) != cudaSuccess) return err;
     }
     count_launch();

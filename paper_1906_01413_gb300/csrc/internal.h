@@ -262,7 +262,10 @@ size_t jacobi_work_doubles(int k);
 // and inverse iteration (all SMs; O(k) grid barriers).  K is not modified.
 // lam: eigenvalues descending; Z (k x k): eigenvectors.  info[0..1] != 0 if
 // the final orthonormalisation of the eigenvectors failed.
-cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *work, int *info, cudaStream_t s);
+// fp32_vectors: the eigenvectors are consumed in FP32, so their orthonormalisation
+// stops at about 1e-7 (one shifted CholeskyQR pass less)
+cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *work, int *info, cudaStream_t s,
+                        bool fp32_vectors = false);
 size_t eig_work_doubles(int k);
 // elementwise helpers
 cudaError_t symmetrize(double *A, int k, int64_t lda, cudaStream_t s);
