@@ -626,8 +626,14 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     count_launch();
     eig_sort_kernel<<<k, 128, 0, s>>>(wrq, Zt, k, lam, Zs);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    // Z = Q Zs = (Q^T)^T Zs
-    return gemm('T', 'N', k, k, k, 1.0, Qt, 'd', k, Zs, 'd', k, 0.0, Z, 'd', k, s);
+    // Z = Q Zs = (Q^T)^T Zs; for vectors consumed in FP32 the product runs in FP32
+    // (the LU scratch of the inverse iteration holds the FP32 copies)
+    if (!fp32_vectors) return gemm('T', 'N', k, k, k, 1.0, Qt, 'd', k, Zs, 'd', k, 0.0, Z, 'd', k, s);
+    float *Qt32 = (float *)u0, *Zs32 = (float *)u1, *Z32 = (float *)u2;
+    if ((err = convert_block(Qt, 'd', k, Qt32, 'f', k, k, k, s)) != cudaSuccess) return err;
+    if ((err = convert_block(Zs, 'd', k, Zs32, 'f', k, k, k, s)) != cudaSuccess) return err;
+    if ((err = sgemm('T', 'N', k, k, k, 1.f, Qt32, k, Zs32, k, 0.f, Z32, k, s)) != cudaSuccess) return err;
+    return convert_block(Z32, 'f', k, Z, 'd', k, k, k, s);
 }
 
 }  // namespace riot
