@@ -100,11 +100,18 @@ __device__ void block_house(const double *col, int k, int r0, double *vs, double
 // the next column's p or q.  Column j + 1 itself is left to the CTAs (each
 // derives it), so no CTA writes what another still reads.  p and q are
 // double-buffered across the barrier.
+// RES (2k warps or more): warp i owns column i of A and warp k + i column i of
+// Q^T for the whole run, kept in shared memory; only the column every CTA needs
+// next (j + 2, published one step ahead), the last 2 x 2 block and Q^T at the
+// end go back to global memory.  Otherwise warps stride over the columns in
+// global memory (L2), four loads in flight per lane.
+template <bool RES>
 __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int k, double *pq, double *d, double *e)
 {
     cg::grid_group grid = cg::this_grid();
     extern __shared__ double sm[];
     double *vcur = sm, *vnext = sm + k, *w = sm + 2 * k, *colj = sm + 3 * k, *red = sm + 4 * k;
+    double *own = sm + 4 * k + 8 + (size_t)(threadIdx.x >> 5) * k;   // RES: this warp's column
     __shared__ double bcur_s, bnext_s, enext_s;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -118,6 +125,13 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
             }
         }
         return;
+    }
+    // RES: owned column (A column gw, or Q^T column gw - k) into shared memory
+    const bool ownA = RES && gw < k, ownQ = RES && gw >= k && gw < 2 * k;
+    if (RES && (ownA || ownQ)) {
+        const double *src = ownA ? A + (int64_t)gw * k : Qt + (int64_t)(gw - k) * k;
+        for (int l = lane; l < k; l += 32) own[l] = src[l];
+        __syncwarp();
     }
     // reflector 0 from column 0, and its p, q
     block_house(A, k, 1, vcur, &bcur_s, &enext_s, red);
@@ -177,53 +191,89 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
         }
         const int r1 = r0 + 1;
         double *pn = pq + (size_t)(par ^ 1) * k, *qn = pq + 2 * (size_t)k + (size_t)(par ^ 1) * k;
-        for (int it = gw; it < m + k; it += nw) {
-            if (it < m) {
-                const int i = r0 + it;
-                if (next && i == r0) continue;   // derived by every CTA above; never written
-                double *col = A + (int64_t)i * k;
+        if constexpr (RES) {
+            if (ownA && gw >= r0 && !(next && gw == r0)) {
+                const int i = gw;
                 const double vi = vcur[i], wi = w[i];
                 double t = 0.0;
-                for (int l0 = r0 + lane; l0 < k; l0 += 128) {   // four loads in flight per lane
-                    double x[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) x[u] = (l0 + 32 * u < k) ? col[l0 + 32 * u] : 0.0;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int l = l0 + 32 * u;
-                        if (l < k) {
-                            x[u] -= vcur[l] * wi + w[l] * vi;
-                            col[l] = x[u];
-                            if (l >= r1) t = fma(x[u], vnext[l], t);
-                        }
-                    }
+                for (int l = r0 + lane; l < k; l += 32) {
+                    const double x = own[l] - (vcur[l] * wi + w[l] * vi);
+                    own[l] = x;
+                    if (l >= r1) t = fma(x, vnext[l], t);
                 }
                 if (next) {
                     t = warp_sum(t);
                     if (lane == 0) pn[i] = bn * t;
                 }
-            } else {
-                const int i = it - m;
-                double *col = Qt + (int64_t)i * k;
+                // the column every CTA derives at the next step, and the last 2 x 2 block
+                if (i == r1 || !next) {
+                    __syncwarp();
+                    double *dst = A + (int64_t)i * k;
+                    for (int l = r1 - 1 + lane; l < k; l += 32) dst[l] = own[l];
+                }
+            } else if (ownQ) {
+                const int i = gw - k;
                 const double qi = q[i];
                 double t = 0.0;
-                for (int l0 = r0 + lane; l0 < k; l0 += 128) {
-                    double x[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) x[u] = (l0 + 32 * u < k) ? col[l0 + 32 * u] : 0.0;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int l = l0 + 32 * u;
-                        if (l < k) {
-                            x[u] -= qi * vcur[l];
-                            col[l] = x[u];
-                            if (l >= r1) t = fma(x[u], vnext[l], t);
-                        }
-                    }
+                for (int l = r0 + lane; l < k; l += 32) {
+                    const double x = own[l] - qi * vcur[l];
+                    own[l] = x;
+                    if (l >= r1) t = fma(x, vnext[l], t);
                 }
                 if (next) {
                     t = warp_sum(t);
                     if (lane == 0) qn[i] = bn * t;
+                }
+            }
+        } else {
+            for (int it = gw; it < m + k; it += nw) {
+                if (it < m) {
+                    const int i = r0 + it;
+                    if (next && i == r0) continue;   // derived by every CTA above; never written
+                    double *col = A + (int64_t)i * k;
+                    const double vi = vcur[i], wi = w[i];
+                    double t = 0.0;
+                    for (int l0 = r0 + lane; l0 < k; l0 += 128) {   // four loads in flight per lane
+                        double x[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) x[u] = (l0 + 32 * u < k) ? col[l0 + 32 * u] : 0.0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int l = l0 + 32 * u;
+                            if (l < k) {
+                                x[u] -= vcur[l] * wi + w[l] * vi;
+                                col[l] = x[u];
+                                if (l >= r1) t = fma(x[u], vnext[l], t);
+                            }
+                        }
+                    }
+                    if (next) {
+                        t = warp_sum(t);
+                        if (lane == 0) pn[i] = bn * t;
+                    }
+                } else {
+                    const int i = it - m;
+                    double *col = Qt + (int64_t)i * k;
+                    const double qi = q[i];
+                    double t = 0.0;
+                    for (int l0 = r0 + lane; l0 < k; l0 += 128) {
+                        double x[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) x[u] = (l0 + 32 * u < k) ? col[l0 + 32 * u] : 0.0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int l = l0 + 32 * u;
+                            if (l < k) {
+                                x[u] -= qi * vcur[l];
+                                col[l] = x[u];
+                                if (l >= r1) t = fma(x[u], vnext[l], t);
+                            }
+                        }
+                    }
+                    if (next) {
+                        t = warp_sum(t);
+                        if (lane == 0) qn[i] = bn * t;
+                    }
                 }
             }
         }
@@ -232,6 +282,12 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
         for (int l = threadIdx.x; l < k; l += blockDim.x) vcur[l] = vnext[l];
         if (threadIdx.x == 0) bcur_s = bn;
         grid.sync();
+    }
+    if constexpr (RES) {
+        if (ownQ) {
+            double *dst = Qt + (int64_t)(gw - k) * k;
+            for (int l = lane; l < k; l += 32) dst[l] = own[l];
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // last 2 x 2 block
@@ -580,18 +636,19 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     eig_init_kernel<<<256, 256, 0, s>>>(K, k, A, Qt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     {
-        const size_t smem = sizeof(double) * (4 * (size_t)k + 8);
-        if ((err = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
+        const int grid = num_sms();   // one CTA per SM keeps the grid barrier short
+        // columns resident in shared memory when every column has a warp of its own
+        const bool res = 2 * k <= grid * 8;
+        const size_t smem = sizeof(double) * (4 * (size_t)k + 8 + (res ? 8 * (size_t)k : 0));
+        const void *fn = res ? (const void *)tridiag_kernel<true> : (const void *)tridiag_kernel<false>;
+        if ((err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return err;
         int per_sm = 0;
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, 256, smem)) != cudaSuccess)
-            return err;
+        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem)) != cudaSuccess) return err;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        const int grid = num_sms();   // one CTA per SM keeps the grid barrier short
         void *args[] = {&A, &Qt, &k, &pq, &d, &e};
         count_launch();
-        err = cudaLaunchCooperativeKernel((void *)tridiag_kernel, grid, 256, args, smem, s);
+        err = cudaLaunchCooperativeKernel(fn, grid, 256, args, smem, s);
         if (err != cudaSuccess) return err;
     }
     count_launch();
