@@ -823,6 +823,9 @@ riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
             CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Wblk, tr, n, 0.0, ctx->Mm, 'd', k, s));
             CU(gemm('T', 'N', k, k, n, 1.0, ctx->Q, 'd', n, ctx->Yblk, tr, n, 0.0, ctx->Nm, 'd', k, s));
         }
+        // K's products stay in FP64 on both paths: the solve with M M^T amplifies their
+        // error by its condition number (sliced tensor-core products, exact to 2^-36 of each
+        // column's maximum, moved lambda_1 of the large window by 5 %)
         CU(gemm('N', 'T', k, k, k, 1.0, ctx->Mm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->G, 'd', k, s));
         CU(gemm('N', 'T', k, k, k, 1.0, ctx->Nm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->Km, 'd', k, s));
         // M M^T is singular to working precision when the window's spectrum spans more than the

@@ -552,25 +552,55 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
     // start vector: distinct pseudo-random values per eigenvalue
     for (int l = 0; l < m; ++l) z[lo + l] = hash_uniform((uint32_t)i, (uint32_t)l) + 1e-3;
     for (int iter = 0; iter < 3; ++iter) {
-        // forward: apply the row operations (row l + 1 carried in a register)
+        // forward: apply the row operations (row l + 1 carried in a register); the
+        // stored factors of four rows are fetched before they are used
         double carry = z[lo];
-        for (int l = 0; l < m - 1; ++l) {
-            const double nxt = z[lo + l + 1];
-            const bool sw = piv[IDX(l)] != 0;
-            const double mlt = ml[IDX(l)];
-            const double r0v = sw ? nxt : carry, r1v = sw ? carry : nxt;
-            z[lo + l] = r0v;
-            carry = r1v - mlt * r0v;
+        for (int l0 = 0; l0 < m - 1; l0 += 4) {
+            double nx[4], mv[4];
+            bool sv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int l = l0 + u;
+                const bool in = l < m - 1;
+                nx[u] = in ? z[lo + l + 1] : 0.0;
+                mv[u] = in ? ml[IDX(l)] : 0.0;
+                sv[u] = in && piv[IDX(l)] != 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int l = l0 + u;
+                if (l < m - 1) {
+                    const double r0v = sv[u] ? nx[u] : carry, r1v = sv[u] ? carry : nx[u];
+                    z[lo + l] = r0v;
+                    carry = r1v - mv[u] * r0v;
+                }
+            }
         }
         z[lo + m - 1] = carry;
-        // backward substitution with U (1 / diagonal, u1, u2)
+        // backward substitution with U (1 / diagonal, u1, u2), four rows fetched ahead
         double x2 = 0.0, x1 = 0.0, big = 0.0;
-        for (int l = m - 1; l >= 0; --l) {
-            const double xl = (z[lo + l] - u1[IDX(l)] * x1 - u2[IDX(l)] * x2) * u0[IDX(l)];
-            z[lo + l] = xl;
-            x2 = x1;
-            x1 = xl;
-            big = fmax(big, fabs(xl));
+        for (int l0 = m - 1; l0 >= 0; l0 -= 4) {
+            double zv[4], a0[4], a1[4], a2[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int l = l0 - u;
+                const bool in = l >= 0;
+                zv[u] = in ? z[lo + l] : 0.0;
+                a0[u] = in ? u0[IDX(l)] : 0.0;
+                a1[u] = in ? u1[IDX(l)] : 0.0;
+                a2[u] = in ? u2[IDX(l)] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int l = l0 - u;
+                if (l >= 0) {
+                    const double xl = (zv[u] - a1[u] * x1 - a2[u] * x2) * a0[u];
+                    z[lo + l] = xl;
+                    x2 = x1;
+                    x1 = xl;
+                    big = fmax(big, fabs(xl));
+                }
+            }
         }
         const double sc = (big > 0.0 && isfinite(big)) ? 1.0 / big : 1.0;
         for (int l = 0; l < m; ++l) z[lo + l] *= sc;
