@@ -30,8 +30,10 @@ def _run(R, K, method):
     return lam.cpu().numpy(), Z.cpu().numpy().T                  # columns = eigenvectors
 
 
+# k = 700 takes the tridiagonalisation whose columns stream from L2 (more columns than warps)
 CASES = [("graded", 7, 1e-6, 1e6, 0), ("graded", 40, 1e-8, 1e4, 1), ("graded", 100, 1e-3, 1e3, 2),
-         ("graded", 512, 1e8, 1e20, 3), ("cluster", 64, 1.0, 10.0, 4), ("cluster", 301, 0.5, 2.0, 5)]
+         ("graded", 512, 1e8, 1e20, 3), ("cluster", 64, 1.0, 10.0, 4), ("cluster", 301, 0.5, 2.0, 5),
+         ("graded", 700, 1e-3, 1e3, 6)]
 
 
 @pytest.mark.parametrize("kind,k,lo,hi,seed", CASES)
@@ -59,3 +61,24 @@ def test_symm_eig_degenerate(gpu_lib, k):
         np.testing.assert_allclose(lam, np.sort(np.linalg.eigvalsh(K))[::-1], atol=1e-14)
         assert np.abs(Z.T @ Z - np.eye(k)).max() <= 1e-12
         assert np.abs(K @ Z - Z * lam).max() <= 1e-13
+
+
+def test_symm_eig_block_diagonal_splits(gpu_lib):
+    """Independent blocks make T split into unreduced blocks (zero off-diagonals at
+    the block boundaries); k > 1024 spreads the split flags over two tiles of the
+    split kernel's prefix count.  Same tolerances as above."""
+    R = gpu_lib
+    sizes = [1, 5, 300, 2, 700, 94, 1, 97]
+    k = sum(sizes)
+    K = np.zeros((k, k))
+    o = 0
+    for b, m in enumerate(sizes):
+        K[o:o + m, o:o + m] = _spd(m, 0.1 * (b + 1), 10.0 * (b + 1), 40 + b)
+        o += m
+    K = 0.5 * (K + K.T)
+    ref = np.sort(np.linalg.eigvalsh(K))[::-1]
+    lam, Z = _run(R, K, 0)
+    tol = 50 * k * np.finfo(float).eps * np.abs(ref).max()
+    np.testing.assert_allclose(lam, ref, rtol=0, atol=tol)
+    assert np.abs(K @ Z - Z * lam).max() <= tol
+    assert np.abs(Z.T @ Z - np.eye(k)).max() <= 1e-12
