@@ -138,7 +138,7 @@ cudaError_t gram_lower(int n, int k, const void *A, char tA, int64_t lda, double
     int S = 1;
     if (ws) {
         S = (4 * num_sms() + tiles - 1) / tiles;
-        if (S > n / 256) S = n / 256;
+        if (S > n / 128) S = n / 128;
         while (S > 1 && (size_t)S * k * k > ws_doubles) --S;
         if (S < 1) S = 1;
     }
