@@ -599,7 +599,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "T": T, "k": k, "q": q, "p_obs": int(p),
-                       "precision": "TL/AD f32; Gram, Cholesky, tridiagonal eig, increment f64",
+                       "precision": "TL/AD f32; CholeskyQR Grams exact on tensor cores (BF16 slices), Cholesky, tridiagonal eig, increment f64",
                        "l2": "256 MB buffer written between timed steps (flush)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "inner_loop_ms": ms},
