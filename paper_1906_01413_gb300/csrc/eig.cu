@@ -301,11 +301,13 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
 // ||T||_inf.  One CTA of 1024 threads: split flags in parallel, block starts
 // by a prefix count over 1024-index tiles, bounds written per index.
 __global__ void __launch_bounds__(1024) split_kernel(const double *d, const double *e, int k, double *e2, int *blo,
-                                                     int *bhi, double *tnorm, int *bstart, int *nblocks)
+                                                     int *bhi, double *tnorm, int *bstart, int *nblocks, double *ds,
+                                                     double *e2s, double *tsc)
 {
     __shared__ int cnt[1024];
     __shared__ double red[32];
     __shared__ int base_s, lo_carry_s;
+    __shared__ double sc_s;
     const int t = threadIdx.x;
     double nrm = 0.0;
     for (int l = t; l < k; l += blockDim.x) {
@@ -325,6 +327,17 @@ __global__ void __launch_bounds__(1024) split_kernel(const double *d, const doub
         double m = 0.0;
         for (int w = 0; w < 32; ++w) m = fmax(m, red[w]);
         *tnorm = m;
+        // the power of two 2^-es with ||T|| 2^-es below 1: the scaled copies that the Sturm
+        // counts use are exact, and their recurrences stay far from the FP64 range limits
+        int es = 0;
+        if (m > 0.0 && isfinite(m)) frexp(m, &es);
+        sc_s = ldexp(1.0, -es);
+        *tsc = sc_s;
+    }
+    __syncthreads();
+    {
+        const double sc = sc_s;
+        for (int l = t; l < k; l += blockDim.x) ds[l] = d[l] * sc;
     }
     // index l ends a block when l = k - 1 or e_l is negligible
     for (int l0 = 0; l0 < k; l0 += blockDim.x) {
@@ -332,7 +345,11 @@ __global__ void __launch_bounds__(1024) split_kernel(const double *d, const doub
         bool split = false;
         if (l < k) {
             split = (l + 1 == k) || fabs(e[l]) <= DBL_EPSILON * (fabs(d[l]) + fabs(d[l + 1]));
-            if (l + 1 < k) e2[l] = split ? 0.0 : e[l] * e[l];
+            if (l + 1 < k) {
+                e2[l] = split ? 0.0 : e[l] * e[l];
+                const double es_ = split ? 0.0 : e[l] * sc_s;
+                e2s[l] = es_ * es_;
+            }
         }
         cnt[t] = split ? 1 : 0;
         __syncthreads();
@@ -366,17 +383,38 @@ __global__ void __launch_bounds__(1024) split_kernel(const double *d, const doub
     }
 }
 
-// Number of eigenvalues of the block [lo, hi] below x (Sturm sequence).
-__device__ int sturm_count(const double *d, const double *e2, int lo, int hi, double x, double pivmin)
+// Number of eigenvalues of the block [lo, hi] below x: sign changes of the
+// characteristic polynomials of the leading sub-blocks, P_l = (d_l - x) P_(l-1)
+// - e_(l-1)^2 P_(l-2) (Sturm), on the copies scaled by a power of two (ds, e2s, xs).
+// One FMA per row on the critical path, where the ratio form q = P_l / P_(l-1)
+// needs an FP64 division (a long dependent sequence on this GPU); the pair
+// (P_(l-1), P_l) is rescaled by a power of two every 8 rows.  An exact zero
+// counts as a sign change (a tiny negative pivot in the ratio form).
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+__device__ __forceinline__ int sturm_count(const double *__restrict__ ds, const double *__restrict__ e2s, int lo,
+                                           int hi, double xs)
 {
-    int cnt = 0;
-    double q = d[lo] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0.0) ++cnt;
-    for (int l = lo + 1; l <= hi; ++l) {
-        q = (d[l] - x) - e2[l - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        if (q < 0.0) ++cnt;
+    double p0 = 1.0, p1 = ds[lo] - xs;
+    if ((dbits(p1) << 1) == 0) p1 = -DBL_MIN;
+    int cnt = dbits(p1) < 0;
+    int l = lo + 1;
+    while (l <= hi) {
+        const int lend = min(hi, l + 7);
+        for (; l <= lend; ++l) {
+            double p2 = fma(ds[l] - xs, p1, -e2s[l - 1] * p0);
+            if ((dbits(p2) << 1) == 0) p2 = (dbits(p1) < 0) ? DBL_MIN : -DBL_MIN;
+            cnt += (dbits(p2) ^ dbits(p1)) < 0;
+            p0 = p1;
+            p1 = p2;
+        }
+        // rescale by the power of two of the larger magnitude (exact)
+        const int e0 = (int)((dbits(p0) >> 52) & 0x7ff), e1 = (int)((dbits(p1) >> 52) & 0x7ff);
+        int sh = 1023 - max(e0, e1);
+        sh = max(-1000, min(1000, sh));
+        const double f = __longlong_as_double((long long)(1023 + sh) << 52);
+        p0 *= f;
+        p1 *= f;
     }
     return cnt;
 }
@@ -394,16 +432,16 @@ __device__ __forceinline__ double grid_point(int g, double tn)
 }
 
 // counts[b * kGrid + g] = eigenvalues of block b below grid point g.
-__global__ void prebracket_kernel(const double *d, const double *e2, const int *bstart, const int *nblocks,
-                                  const double *tnorm, int *counts)
+__global__ void prebracket_kernel(const double *ds, const double *e2s, const int *bstart, const int *nblocks,
+                                  const double *tnorm, const double *tsc, int *counts)
 {
     const int nb = *nblocks;
     const int64_t total = (int64_t)nb * kGrid;
-    const double tn = *tnorm;
+    const double tn = *tnorm, sc = *tsc;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(t / kGrid), g = (int)(t - (int64_t)b * kGrid);
         const int lo = bstart[b], hi = bstart[b + 1] - 1;
-        counts[t] = sturm_count(d, e2, lo, hi, grid_point(g, tn), DBL_MIN * fmax(1.0, tn * tn));
+        counts[t] = sturm_count(ds, e2s, lo, hi, grid_point(g, tn) * sc);
     }
 }
 
@@ -412,8 +450,9 @@ __global__ void prebracket_kernel(const double *d, const double *e2, const int *
 // Fewer points per round cost more rounds but less FP64 work in total (the
 // counts run on the FP64 pipe, which is narrow on this GPU).
 template <int G, int U>
-__global__ void multisect_kernel(const double *d, const double *e2, const int *blo, const int *bhi, const int *bstart,
-                                 const int *nblocks, int k, const double *tnorm, const int *counts, double *w)
+__global__ void multisect_kernel(const double *d, const double *ds, const double *e2s, const int *blo, const int *bhi,
+                                 const int *bstart, const int *nblocks, int k, const double *tnorm, const double *tsc,
+                                 const int *counts, double *w)
 {
     constexpr int P = G * U;
     const int gl = blockIdx.x * blockDim.x + threadIdx.x;
@@ -441,29 +480,14 @@ __global__ void multisect_kernel(const double *d, const double *e2, const int *b
         if (cb[gm] <= r) g0 = gm; else g1 = gm;
     }
     double a = grid_point(g0, tn), c = grid_point(g1, tn);
-    const double pivmin = DBL_MIN * fmax(1.0, tn * tn);
+    const double sc = *tsc;
     for (int round = 0; round < 64; ++round) {
         const double width = c - a;
         if (width <= fmax(1e-10 * fmax(fabs(a), fabs(c)), 4.0 * DBL_EPSILON * tn)) break;
         const double step = width / (double)(P + 1);
-        double x[U], q[U];
         int cnt[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            x[u] = a + step * (double)(1 + sl + G * u);
-            q[u] = d[lo] - x[u];
-            if (fabs(q[u]) < pivmin) q[u] = -pivmin;
-            cnt[u] = (q[u] < 0.0);
-        }
-        for (int l = lo + 1; l <= hi; ++l) {
-            const double dl = d[l], el = e2[l - 1];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                q[u] = (dl - x[u]) - el / q[u];
-                if (fabs(q[u]) < pivmin) q[u] = -pivmin;
-                cnt[u] += (q[u] < 0.0);
-            }
-        }
+        for (int u = 0; u < U; ++u) cnt[u] = sturm_count(ds, e2s, lo, hi, (a + step * (double)(1 + sl + G * u)) * sc);
         // the new bracket: last point with count <= r, first with count > r;
         // points ascend with (u, sl) and counts are monotone in x
         int best_le = -1, first_gt = P;
@@ -657,6 +681,7 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     int *blo = (int *)(vec + 9 * k), *bhi = (int *)(vec + 10 * k);
     int *bstart = (int *)(vec + 11 * k), *nblocks = (int *)(vec + 12 * k);
     double *wrq = vec + 13 * k;
+    double *ds = vec + 14 * k, *e2s = vec + 15 * k, *tsc = vec + 16 * k;   // scaled copies for the Sturm counts
     int *counts = (int *)(vec + 32 * k + 1024);
     double *dinv = vec + 32 * k + 1024 + ((size_t)kGrid * k + 1) / 2 + 8;
     cudaError_t err;
@@ -682,16 +707,16 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
         if (err != cudaSuccess) return err;
     }
     count_launch();
-    split_kernel<<<1, 1024, 0, s>>>(d, e, k, e2, blo, bhi, tnorm, bstart, nblocks);
+    split_kernel<<<1, 1024, 0, s>>>(d, e, k, e2, blo, bhi, tnorm, bstart, nblocks, ds, e2s, tsc);
     count_launch();
-    prebracket_kernel<<<2 * num_sms(), 128, 0, s>>>(d, e2, bstart, nblocks, tnorm, counts);
+    prebracket_kernel<<<2 * num_sms(), 128, 0, s>>>(ds, e2s, bstart, nblocks, tnorm, tsc, counts);
     {
         // one warp of single chains per eigenvalue (33-fold shrink per round): measured on
         // k = 512 against 8 to 128 points per round, the least FP64 work that still fills the GPU
         constexpr int G = 32, U = 1;
         count_launch();
-        multisect_kernel<G, U><<<(int)(((int64_t)k * G + 127) / 128), 128, 0, s>>>(d, e2, blo, bhi, bstart, nblocks, k,
-                                                                                 tnorm, counts, w);
+        multisect_kernel<G, U><<<(int)(((int64_t)k * G + 127) / 128), 128, 0, s>>>(d, ds, e2s, blo, bhi, bstart,
+                                                                                 nblocks, k, tnorm, tsc, counts, w);
     }
     count_launch();
     inviter_kernel<<<(k + 3) / 4, 4, 0, s>>>(d, e, blo, bhi, k, w, tnorm, Zt, u0, u1, u2, ml, piv, wrq);
