@@ -393,6 +393,20 @@ riot_status riot_get_trajectory(riot_ctx *ctx, double *traj_dev);
 riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const float *P_dev, int32_t m,
                                double rho_max, double *lambda_out, double *rho_out, int32_t *used_out);
 
+/* Algorithm 1 (VarCG: conjugate gradients in Lanczos form, Section 2.1) with
+ * full re-orthogonalisation, the sequential comparator of RIOT: m Lanczos
+ * steps on A from q_1 = g / ||g|| (g from riot_outer_begin), one Hessian-vector
+ * product each (the context's precision), T_m = tridiag(beta, alpha, beta) and
+ * its eigenpairs (theta, Z) on the GPU, U = Q Z, and
+ * dv = -U diag(1 / (1 + theta)) U^T g into dv_dev (n doubles; may be NULL; the
+ * state x, v is not changed).  theta_out (host, m doubles; may be NULL) gets
+ * the Ritz values in decreasing order, m_used (may be NULL) the number of steps
+ * taken (fewer than m when the Krylov space is exhausted).  1 <= m <= kmax.
+ * It reuses the inner-loop workspace: call riot_rsvd again before
+ * riot_increment or riot_analysis_cov_lowrank.  Synchronises (one host read
+ * per step, for the stopping test). */
+riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_out, int32_t *m_used);
+
 /* The FP32 sketch GEMM of the mixed-precision path on its own, for checks:
  * C = alpha op(A) op(B) + beta C (column-major FP32, op 'N' or 'T') on the
  * tcgen05 tensor cores, each operand split into three BF16 terms and the six

@@ -870,8 +870,23 @@ riot_status rsvd_collect(riot_ctx *ctx, int k, double *lambda_out)
 
 // When the unshifted Cholesky of the K normal equations failed (info[10]), redo the end of the
 // inner loop with the shifted solve; the blocks Q0 (W) and Y are unchanged by rsvd_end.
+// When inverse iteration met eigenvalues so close that its vectors came out dependent
+// (the CholeskyQR of the eigenvectors of T failed), redo this call's eigendecomposition of
+// the unchanged K with the Jacobi method, then the Ritz vectors.
+riot_status rsvd_retry_eig(riot_ctx *ctx, int k, double *lambda_out, riot_status st)
+{
+    if (st != RIOT_ENOCONV || ctx->eig_method != RIOT_EIG_TRIDIAG) return st;
+    ctx->eig_method = RIOT_EIG_JACOBI;
+    riot_status st2 = rsvd_eig(ctx, k);
+    if (st2 == RIOT_OK) st2 = rsvd_ritz(ctx, k);
+    if (st2 == RIOT_OK) st2 = rsvd_collect(ctx, k, lambda_out);
+    ctx->eig_method = RIOT_EIG_TRIDIAG;
+    return st2;
+}
+
 riot_status rsvd_retry_k(riot_ctx *ctx, int k, double *lambda_out, riot_status st)
 {
+    if (st == RIOT_ENOCONV) return rsvd_retry_eig(ctx, k, lambda_out, st);
     if (st != RIOT_ENOTSPD) return st;
     int i10 = 0;
     CU(cudaMemcpyAsync(&i10, ctx->info + 10, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
@@ -881,7 +896,7 @@ riot_status rsvd_retry_k(riot_ctx *ctx, int k, double *lambda_out, riot_status s
     riot_status st2 = rsvd_end(ctx, k, true);
     ctx->k_shift = 0;
     if (st2 != RIOT_OK) return st2;
-    return rsvd_collect(ctx, k, lambda_out);
+    return rsvd_retry_eig(ctx, k, lambda_out, rsvd_collect(ctx, k, lambda_out));
 }
 
 // Adaptive increment (queued, no synchronisation): dv, v += dv, x += L dv.
@@ -1772,6 +1787,95 @@ riot_status riot_tc_sgemm(char ta, char tb, int32_t m, int32_t n, int32_t k, flo
     cudaFree(err);
     if (e != cudaSuccess) return RIOT_ECUDA;
     return herr ? RIOT_ETIMEOUT : RIOT_OK;
+}
+
+// w = A q for one FP64 vector (FP32 Hessian kernel and back on the mixed path)
+static riot_status apply_a_vec(riot_ctx *ctx, const double *q, double *w)
+{
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    if (ctx->prec == RIOT_PREC_FP64) {
+        TRY(hvp(ctx, q, w, n, 1, 0));
+        if (ctx->scale_exp) CU(scale_add_cols(n, 1, n, ldexp(1.0, ctx->scale_exp), w, nullptr, 1, s));
+        return RIOT_OK;
+    }
+    float *q32 = (float *)ctx->Wblk, *w32 = (float *)ctx->Yblk;
+    CU(convert_block(q, 'd', n, q32, 'f', n, n, 1, s));
+    TRY(hvp(ctx, q32, w32, n, 1, 0));
+    if (ctx->scale_exp) CU(scale_add_cols(n, 1, n, ldexp(1.0, ctx->scale_exp), w32, nullptr, 0, s));
+    CU(convert_block(w32, 'f', n, w, 'd', n, n, 1, s));
+    return RIOT_OK;
+}
+
+riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_out, int32_t *m_used)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_varcg before riot_outer_begin");
+    if (m < 1 || m > ctx->kmax) return fail(ctx, RIOT_EINVAL, "m = %d outside [1, kmax = %d]", m, ctx->kmax);
+    CU(cudaSetDevice(ctx->dev));
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    ctx->have_rsvd = 0;   // the Lanczos basis, its Ritz vectors and values occupy the inner-loop workspace
+    double *Q = ctx->Q, *r = ctx->U, *w = ctx->tmp, *h = ctx->cvec;
+    double *alphas = ctx->gws, *betas_dev = ctx->gws + ctx->kmax, *rr = ctx->nrm;
+    double rrh = 0.0;
+    // r_0 = g, beta_0 = ||r_0||
+    CU(cudaMemcpyAsync(r, ctx->g, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CU(dot_dev(n, r, r, rr, s));
+    CU(cudaMemcpyAsync(&rrh, rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    double beta = sqrt(rrh), beta_prev = 0.0;
+    std::vector<double> betas;
+    int mm = 0;
+    for (int i = 0; i < m; ++i) {
+        if (!(beta > 0.0) || !isfinite(beta)) break;
+        double *q = Q + (size_t)i * n;
+        CU(normalize_by(n, r, rr, q, s));                          // q_i = r / beta
+        TRY(apply_a_vec(ctx, q, w));                               // w = A q_i
+        CU(dot_dev(n, q, w, alphas + i, s));                       // alpha_i = q_i^T w
+        CU(lanczos_resid(n, w, q, i > 0 ? Q + (size_t)(i - 1) * n : nullptr, alphas + i, beta_prev, r, s));
+        for (int pass = 0; pass < 2; ++pass) {                     // full re-orthogonalisation, twice
+            CU(gemm('T', 'N', i + 1, 1, n, 1.0, Q, 'd', n, r, 'd', n, 0.0, h, 'd', i + 1, s));
+            CU(gemm('N', 'N', n, 1, i + 1, -1.0, Q, 'd', n, h, 'd', i + 1, 1.0, r, 'd', n, s));
+        }
+        beta_prev = beta;
+        CU(dot_dev(n, r, r, rr, s));
+        CU(cudaMemcpyAsync(&rrh, rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        beta = sqrt(rrh);
+        betas.push_back(beta);
+        mm = i + 1;
+    }
+    if (mm == 0) {
+        // g = 0: the increment is zero
+        if (dv_dev) CU(cudaMemsetAsync(dv_dev, 0, sizeof(double) * n, s));
+        if (m_used) *m_used = 0;
+        CU(cudaStreamSynchronize(s));
+        return RIOT_OK;
+    }
+    // T_m, its eigenpairs (theta, Z), U = Q Z, dv = -U diag(1 / (1 + theta)) U^T g
+    CU(cudaMemcpyAsync(betas_dev, betas.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, s));
+    CU(tridiag_fill(mm, alphas, betas_dev, ctx->Km, s));
+    CU(tridiag_eig(ctx->Km, mm, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
+    int einfo[2] = {0, 0};
+    CU(cudaMemcpyAsync(einfo, ctx->info + 12, sizeof(einfo), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (einfo[0] || einfo[1]) {
+        // close Ritz values left inverse iteration with dependent vectors: Jacobi on T_m instead
+        CU(jacobi_eig(ctx->Km, mm, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
+        CU(cudaMemcpyAsync(einfo, ctx->info + 12, sizeof(einfo), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (einfo[0] < 0) return fail(ctx, RIOT_ENOCONV, "riot_varcg: Jacobi on T_m did not converge");
+    }
+    CU(gemm('N', 'N', n, mm, mm, 1.0, Q, 'd', n, ctx->Z, 'd', mm, 0.0, ctx->U, 'd', n, s));
+    CU(gemm('T', 'N', mm, 1, n, 1.0, ctx->U, 'd', n, ctx->g, 'd', n, 0.0, ctx->cvec, 'd', mm, s));
+    CU(div_one_plus(mm, ctx->cvec, ctx->lam, s));
+    CU(gemm('N', 'N', n, 1, mm, -1.0, ctx->U, 'd', n, ctx->cvec, 'd', mm, 0.0, ctx->dv, 'd', n, s));
+    if (dv_dev) CU(cudaMemcpyAsync(dv_dev, ctx->dv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (theta_out) CU(cudaMemcpyAsync(theta_out, ctx->lam, sizeof(double) * mm, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (m_used) *m_used = mm;
+    return RIOT_OK;
 }
 
 riot_status riot_tc_gram(int32_t n, int32_t k, const float *Y_dev, int64_t ldy, double *G_dev, int64_t ldg,

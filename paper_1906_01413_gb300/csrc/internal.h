@@ -285,6 +285,13 @@ cudaError_t scale_to_f32(int64_t n, const double *in, double a, float *out, cuda
 cudaError_t equilibrate(double *G, int k, int64_t ldg, void *Q, char tQ, int64_t n, int64_t ldq, double *d,
                         cudaStream_t s);
 cudaError_t scal(int64_t n, double a, double *x, cudaStream_t s);
+// vector steps of the Lanczos form of conjugate gradients (Algorithm 1)
+cudaError_t dot_dev(int64_t n, const double *x, const double *y, double *out, cudaStream_t s);
+cudaError_t lanczos_resid(int64_t n, const double *w, const double *q, const double *qprev, const double *alpha,
+                          double beta_prev, double *r, cudaStream_t s);
+cudaError_t normalize_by(int64_t n, const double *r, const double *rr, double *q, cudaStream_t s);
+cudaError_t tridiag_fill(int m, const double *alpha, const double *beta, double *T, cudaStream_t s);
+cudaError_t div_one_plus(int m, double *c, const double *theta, cudaStream_t s);
 // Y = a Y (+ W) column by column (n rows of ncols columns at ld), float or double
 cudaError_t scale_add_cols(int64_t n, int ncols, int64_t ld, double a, void *Y, const void *W, int is_double,
                            cudaStream_t s);

@@ -1010,6 +1010,95 @@ cudaError_t transpose_sq(const double *A, double *B, int k, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Vector steps of the Lanczos form of conjugate gradients (Algorithm 1)
+// ---------------------------------------------------------------------------
+// out[0] = x . y (one CTA of 1024 threads; n up to a few 10^5)
+__global__ void __launch_bounds__(1024) dot1_kernel(int64_t n, const double *x, const double *y, double *out)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(x[i], y[i], s);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = red[threadIdx.x];
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (threadIdx.x == 0) out[0] = t;
+    }
+}
+
+cudaError_t dot_dev(int64_t n, const double *x, const double *y, double *out, cudaStream_t s)
+{
+    count_launch();
+    dot1_kernel<<<1, 1024, 0, s>>>(n, x, y, out);
+    return cudaGetLastError();
+}
+
+// r = w - alpha[0] q - beta_prev qprev (qprev may be null)
+__global__ void lanczos_resid_kernel(int64_t n, const double *w, const double *q, const double *qprev,
+                                     const double *alpha, double beta_prev, double *r)
+{
+    const double a = *alpha;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = w[i] - a * q[i] - (qprev ? beta_prev * qprev[i] : 0.0);
+}
+
+cudaError_t lanczos_resid(int64_t n, const double *w, const double *q, const double *qprev, const double *alpha,
+                          double beta_prev, double *r, cudaStream_t s)
+{
+    count_launch();
+    lanczos_resid_kernel<<<2 * num_sms(), 256, 0, s>>>(n, w, q, qprev, alpha, beta_prev, r);
+    return cudaGetLastError();
+}
+
+// q = r / sqrt(rr[0])
+__global__ void normalize_by_kernel(int64_t n, const double *r, const double *rr, double *q)
+{
+    const double inv = 1.0 / sqrt(*rr);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = r[i] * inv;
+}
+
+cudaError_t normalize_by(int64_t n, const double *r, const double *rr, double *q, cudaStream_t s)
+{
+    count_launch();
+    normalize_by_kernel<<<2 * num_sms(), 256, 0, s>>>(n, r, rr, q);
+    return cudaGetLastError();
+}
+
+// T (m x m, column-major) = tridiag(beta[0..m-2], alpha[0..m-1], beta[0..m-2])
+__global__ void tridiag_fill_kernel(int m, const double *alpha, const double *beta, double *T)
+{
+    const int64_t total = (int64_t)m * m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        T[e] = (i == j) ? alpha[i] : ((i == j + 1 || j == i + 1) ? beta[i < j ? i : j] : 0.0);
+    }
+}
+
+cudaError_t tridiag_fill(int m, const double *alpha, const double *beta, double *T, cudaStream_t s)
+{
+    count_launch();
+    tridiag_fill_kernel<<<64, 256, 0, s>>>(m, alpha, beta, T);
+    return cudaGetLastError();
+}
+
+// c_i <- c_i / (1 + theta_i)
+__global__ void div_one_plus_kernel(int m, double *c, const double *theta)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) c[i] /= 1.0 + theta[i];
+}
+
+cudaError_t div_one_plus(int m, double *c, const double *theta, cudaStream_t s)
+{
+    count_launch();
+    div_one_plus_kernel<<<(m + 255) / 256, 256, 0, s>>>(m, c, theta);
+    return cudaGetLastError();
+}
+
 __global__ void axpby_kernel(int64_t n, double a, const double *x, double b, double *y)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

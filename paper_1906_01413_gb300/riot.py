@@ -113,6 +113,8 @@ def load():
     L.riot_tc_sgemm.argtypes = [ctypes.c_char, ctypes.c_char, c_int32, c_int32, c_int32, ctypes.c_float, vp, c_int64,
                                 vp, c_int64, ctypes.c_float, vp, c_int64, vp]
     L.riot_tc_sgemm.restype = c_int32
+    L.riot_varcg.argtypes = [vp, c_int32, vp, POINTER(c_double), POINTER(c_int32)]
+    L.riot_varcg.restype = c_int32
     L.riot_tc_gram.argtypes = [c_int32, c_int32, vp, c_int64, vp, c_int64, vp]
     L.riot_tc_gram.restype = c_int32
     L.riot_sketchnet_create.argtypes = [POINTER(vp), c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
@@ -365,6 +367,15 @@ def _need_contiguous(*ts):
     for t in ts:
         if t is not None and not t.is_contiguous():
             raise ValueError("tensor arguments must be contiguous (the C ABI takes plain pointers)")
+
+
+def riot_varcg(ctx, m, dv=None):
+    """Algorithm 1 (VarCG, Lanczos form): returns (theta (Ritz values, decreasing), steps used);
+    the increment goes to dv (n float64 device tensor) when given."""
+    theta = (c_double * int(m))()
+    used = c_int32(0)
+    _check(ctx, "riot_varcg", load().riot_varcg(ctx, int(m), _ptr(dv), theta, ctypes.byref(used)))
+    return np.array(theta[:used.value]), used.value
 
 
 def riot_tc_sgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
