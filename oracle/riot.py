@@ -280,6 +280,115 @@ def outer_step(prob, x, v, Omega, q=0, exact_rr=False):
             "x_next": x + prob.L @ dv, "v_next": v + dv, "info": info}
 
 
+# --- spectral preconditioner and rotation (Section 2.2 "Preconditioning", Eq. 7, Algorithm 3) ---
+
+class SpectralPreconditioner:
+    """P_k = P'_0 P'_1 ... P'_{k-1} of Algorithm 3 with P'_0 = I and, for each finished outer
+    loop j, P'_j = I + V_j (Lt_j^{-1/2} - I) V_j^T (the spectral form of Eq. 7), where V_j
+    (orthonormal columns) and Lt_j = Lambda_j + I are the Ritz vectors and the eigenvalues of
+    I + A_j estimated in loop j.  Since V_j^T V_j = I, P'_j^{-1} = I + V_j (Lt_j^{1/2} - I) V_j^T.
+
+    Reading (the listing mixes variables here): the control v of x = x_b + L v stays in the
+    unpreconditioned variable, so loop k solves for w with v = v_{k-1} + P_k w; its gradient is
+    P_k^T (b + v_{k-1}), its Hessian I + A_k with A_k = P_k^T P_k - I + P_k^T A P_k, and the
+    updates are v += P_k dw, x += L P_k dw.  At k = 1 (P_1 = I) this is the listing exactly.
+
+    Rotation: U_k is an orthonormal basis of [P_1 V_1, ..., P_{k-1} V_{k-1}] (taken here from an
+    SVD, which Algorithm 3 names) and each sketch column becomes P_k^{-1} (I - U_k U_k^T) omega."""
+
+    def __init__(self, n):
+        self.n = n
+        self.V = []      # V_j, (n, m_j)
+        self.lt = []     # Lt_j = lambda_j + 1, (m_j,)
+        self.rot = []    # P_j V_j, the resolved directions in the control variable
+
+    @property
+    def count(self):
+        return len(self.V)
+
+    @staticmethod
+    def _cols(X):
+        X = np.array(X, dtype=np.float64, copy=True)
+        return X[:, None] if X.ndim == 1 else X
+
+    def _factor(self, X, j, power):
+        V, lt = self.V[j], self.lt[j]
+        return X + V @ ((lt ** power - 1.0)[:, None] * (V.T @ X))
+
+    def apply(self, X):
+        """P_k X = P'_0 (P'_1 (... (P'_{k-1} X)))."""
+        X = self._cols(X)
+        for j in reversed(range(self.count)):
+            X = self._factor(X, j, -0.5)
+        return X
+
+    def apply_t(self, X):
+        """P_k^T X = P'_{k-1} (... (P'_0 X)) (each P'_j is symmetric)."""
+        X = self._cols(X)
+        for j in range(self.count):
+            X = self._factor(X, j, -0.5)
+        return X
+
+    def apply_inv(self, X):
+        """P_k^{-1} X = P'_{k-1}^{-1} (... (P'_0^{-1} X))."""
+        X = self._cols(X)
+        for j in range(self.count):
+            X = self._factor(X, j, 0.5)
+        return X
+
+    def push(self, lam, V):
+        """Append P'_k from outer loop k's eigenpairs (lam of A_k, V orthonormal): the next
+        loop runs with P_{k+1} = P_k P'_k.  P_k V is recorded for the rotation first."""
+        lam = np.asarray(lam, dtype=np.float64)
+        if np.any(lam + 1.0 <= 0.0):
+            raise ValueError("eigenvalues of I + A_k must be positive")
+        V = np.asarray(V, dtype=np.float64)
+        self.rot.append(self.apply(V))
+        self.V.append(V.copy())
+        self.lt.append(lam + 1.0)
+
+    def rotation_basis(self):
+        """U_k: orthonormal basis of the span of [P_1 V_1, ..., P_{k-1} V_{k-1}]."""
+        if not self.rot:
+            return np.zeros((self.n, 0))
+        X = np.hstack(self.rot)
+        U, s, _ = np.linalg.svd(X, full_matrices=False)
+        return U[:, s > s[0] * X.shape[1] * np.finfo(float).eps]
+
+    def rotate(self, Omega):
+        """Sketch columns restricted to the complement of the resolved directions and mapped
+        to the preconditioned variable: P_k^{-1} (I - U_k U_k^T) Omega."""
+        Ur = self.rotation_basis()
+        Om = np.asarray(Omega, dtype=np.float64)
+        return self.apply_inv(Om - Ur @ (Ur.T @ Om))
+
+    def hessian(self, apply_a):
+        """W -> A_k W = P_k^T P_k W - W + P_k^T A (P_k W) (Algorithm 3), apply_a: W -> A W."""
+        def op(W):
+            PW = self.apply(W)
+            return self.apply_t(PW) - W + self.apply_t(apply_a(PW))
+        return op
+
+
+def outer_step_precond(prob, x, v, Omega, pc, q=0, exact_rr=False, rotation=False):
+    """One cycle of Algorithm 3 with precond = true (rotation as given), with P_k held by pc
+    (the caller pushes this loop's eigenpairs afterwards, which forms P'_k for the next loop).
+    Returns the entries of outer_step plus dw (the increment of the preconditioned variable)."""
+    traj = trajectory(prob, x)
+    d = innovation(prob, traj)
+    J = cost(prob, traj, v)
+    b = gradient_b(prob, traj, d)
+    g = pc.apply_t(b + v)[:, 0]
+    Om = pc.rotate(Omega) if (rotation and pc.count) else np.asarray(Omega, dtype=np.float64)
+    op = pc.hessian(lambda W: hvp(prob, traj, W))
+    lam, U, info = rsvd(prob, traj, Om, q=q, exact_rr=exact_rr, apply=op)
+    dw, mode = increment(lam, U, g)
+    dv = pc.apply(dw)[:, 0]
+    info["Omega"] = Om
+    return {"traj": traj, "J": J, "b": b, "g": g, "lam": lam, "U": U, "dw": dw, "dv": dv, "mode": mode,
+            "x_next": x + prob.L @ dv, "v_next": v + dv, "info": info}
+
+
 def quadratic_cost(prob, traj, d, v, dv):
     """Inner-loop quadratic cost J~(dv) = 1/2||R^-1/2(d + H M L dv)||^2 + 1/2||v + dv||^2
     (Eq. 3 with Algorithm 3's sign of d and accumulated control v)."""
