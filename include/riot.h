@@ -407,6 +407,57 @@ riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sket
  * per step, for the stopping test). */
 riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_out, int32_t *m_used);
 
+/* Spectral preconditioner with rotation (Section 2.2 "Preconditioning", Eq. 7;
+ * Algorithm 3 with precond = true).  After outer loop j has run riot_rsvd and
+ * riot_increment, riot_precond_push(ctx, m) adds the factor
+ *     P'_j = I + V_j ((Lambda_j + I)^-1/2 - I) V_j^T
+ * built from that loop's leading m Ritz pairs (V_j = the first m columns of U,
+ * Lambda_j their eigenvalues of the preconditioned Hessian).  Every later loop k
+ * then runs with P_k = P'_1 ... P'_{k-1}:
+ *   - riot_outer_begin sets g = P_k^T (b + v)       (v stays the control of
+ *     x = x_b + L v: the problem of loop k is solved for w with v = v_{k-1} + P_k w);
+ *   - riot_rsvd decomposes A_k = P_k^T P_k - I + P_k^T A P_k instead of A (its
+ *     eigenvalues and Ritz vectors are those of A_k);
+ *   - riot_increment forms the adaptive increment dw of Algorithm 3 from g and
+ *     the pairs of A_k, then v += P_k dw and x += L P_k dw (dv_dev receives P_k dw).
+ * With rotation on, riot_rsvd first projects every sketch column (drawn or
+ * given) onto the orthogonal complement of the span of [P_1 V_1, ..., P_{k-1}
+ * V_{k-1}] (Algorithm 3's (I - U_k U_k^T); its following P_k^-1 is the identity
+ * on that complement and is not applied), and requires k + (resolved columns) <= n.
+ * After a push, riot_outer_begin must run before the next riot_rsvd or
+ * riot_increment (RIOT_ESTATE otherwise): the gradient depends on P_k.
+ * riot_varcg, riot_rsvd_proposal and batches refuse contexts with factors
+ * (RIOT_ESTATE / RIOT_EINVAL).
+ *
+ * The solve for K of Algorithm 3 can return trailing Ritz values below -1 on
+ * the flattened spectrum of a preconditioned loop; (Lambda + I)^-1/2 is then
+ * undefined, so push the leading pairs with positive eigenvalue (the
+ * benchmark and the tests take m = the number of positive values).
+ *
+ * riot_precond_enable(ctx, max_cols, rotation): drops all factors and reserves
+ * device storage for max_cols stored columns in total (0 <= max_cols <= n;
+ * 0 switches the preconditioner off and frees it); synchronises the stream.
+ * riot_precond_push: RIOT_ESTATE before riot_precond_enable, or unless
+ * riot_increment ran after the last riot_rsvd (one push per outer loop);
+ * RIOT_EINVAL if m is outside [1, k] or the storage is full; RIOT_ENONFINITE if
+ * an eigenvalue of I + A_k is not positive; RIOT_ENOTSPD if the new rotation
+ * directions are dependent on the old ones.  Synchronises.
+ * riot_precond_push_pairs(ctx, V, lambda, m): the same factor from given pairs
+ * (a preconditioner kept from an earlier cycle, or pairs computed elsewhere):
+ * V n x m FP64 on the device (column-major, ld n, orthonormal columns),
+ * lambda m host values (eigenvalues of the Hessian the factor preconditions);
+ * 1 <= m <= kmax.  RIOT_ESTATE between a riot_rsvd and its riot_increment;
+ * otherwise as riot_precond_push.
+ * riot_precond_apply(ctx, X, Y, ncols, op): Y = op(P_k) X for ncols FP64
+ * columns of length n (column-major, ld n; X == Y allowed), op 0 = P_k,
+ * 1 = P_k^T, 2 = P_k^-1.  Asynchronous on the context stream.
+ * riot_precond_count: the number of factors (-1 for a null context). */
+riot_status riot_precond_enable(riot_ctx *ctx, int32_t max_cols, int32_t rotation);
+riot_status riot_precond_push(riot_ctx *ctx, int32_t m);
+riot_status riot_precond_push_pairs(riot_ctx *ctx, const double *V_dev, const double *lambda, int32_t m);
+riot_status riot_precond_apply(riot_ctx *ctx, const double *X_dev, double *Y_dev, int32_t ncols, int32_t op);
+int32_t riot_precond_count(const riot_ctx *ctx);
+
 /* The FP32 sketch GEMM of the mixed-precision path on its own, for checks:
  * C = alpha op(A) op(B) + beta C (column-major FP32, op 'N' or 'T') on the
  * tcgen05 tensor cores, each operand split into three BF16 terms and the six

@@ -59,6 +59,18 @@ struct riot_ctx {
     int scale_exp = 0, scale_in = 0, scale_rinv = 0;
     int k_shift = 0;   // shift the K normal equations (set for one retry after a failed solve)
     double *nrm = nullptr;   // 4 doubles of norm accumulators
+    // Spectral preconditioner of Algorithm 3 (riot_precond_*): P_k = P'_1 ... P'_{k-1},
+    // P'_j = I + V_j diag(c_j) V_j^T with c_j = (lambda_j + 1)^-1/2 - 1 (its inverse takes
+    // ci_j = (lambda_j + 1)^1/2 - 1); factor j holds pc_m[j] columns from column pc_off[j].
+    int pc_cap = 0, pc_rot = 0, pc_cols = 0, rot_cols = 0;
+    int pc_ready = 0;   // riot_increment ran since the last riot_rsvd (and no push since)
+    int pc_open = 0;    // riot_rsvd finished, its riot_increment not yet run
+    int pc_dirty = 0;   // a factor was added after riot_outer_begin formed g with the old P_k
+    std::vector<int> pc_off, pc_m;
+    double *pcV = nullptr, *pcc = nullptr, *pci = nullptr, *pcT = nullptr;
+    double *pcB = nullptr;   // rotation: orthonormal basis of [P_1 V_1, ..., P_{k-1} V_{k-1}] (rot_cols columns)
+    float *pcV32 = nullptr, *pcB32 = nullptr, *pcT32 = nullptr;   // FP32 copies (mixed precision)
+    std::vector<void *> pc_allocs;
     // timing
     cudaEvent_t ev[32];
     int nev = 0;
@@ -222,23 +234,27 @@ cudaError_t bsqrt(riot_ctx *ctx, const double *in, double *out, int transpose, i
 // unshifted CholeskyQR passes.  Each pass first scales the columns to unit
 // norm (the Gram is scaled alike), which removes the spread of column norms
 // that power-iteration blocks of strongly unstable windows carry.
-riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
+riot_status cholqr64(riot_ctx *ctx, double *X, int k, int shifted, int info_base)
 {
     const int n = ctx->n;
-    CU(convert_block(Y, real_tag(ctx), n, ctx->Q, 'd', n, n, k, ctx->s));
-    // Each shifted pass divides the condition number by about
-    // 1 / sqrt(11 (n k + k^2) u k); FP32 blocks carry at most ~1e8 of it,
-    // FP64 blocks up to ~1e16.
-    const int shifted = (ctx->prec == RIOT_PREC_FP64) ? 3 : 1;
     for (int pass = 0; pass < shifted + 2; ++pass) {
-        CU(gram_lower(n, k, ctx->Q, 'd', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
-        CU(equilibrate(ctx->G, k, k, ctx->Q, 'd', n, n, ctx->cvec, ctx->s));
+        CU(gram_lower(n, k, X, 'd', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
+        CU(equilibrate(ctx->G, k, k, X, 'd', n, n, ctx->cvec, ctx->s));
         const double u = ldexp(1.0, -53);
         const double shift = (pass < shifted) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
         CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
-        CU(trsm_right_lt(ctx->Q, n, k, n, ctx->G, k, ctx->s, ctx->gws));
+        CU(trsm_right_lt(X, n, k, n, ctx->G, k, ctx->s, ctx->gws));
     }
     return RIOT_OK;
+}
+
+riot_status orth(riot_ctx *ctx, const void *Y, int k, int info_base)
+{
+    CU(convert_block(Y, real_tag(ctx), ctx->n, ctx->Q, 'd', ctx->n, ctx->n, k, ctx->s));
+    // Each shifted pass divides the condition number by about
+    // 1 / sqrt(11 (n k + k^2) u k); FP32 blocks carry at most ~1e8 of it,
+    // FP64 blocks up to ~1e16.
+    return cholqr64(ctx, ctx->Q, k, (ctx->prec == RIOT_PREC_FP64) ? 3 : 1, info_base);
 }
 
 // Mixed precision: Q32 = orthonormal basis of Y (FP32 block).  Grams come
@@ -711,12 +727,169 @@ riot_status choose_scale(riot_ctx *ctx)
 // FP32 sketch GEMMs of the mixed path: tensor cores (FP32-accurate three-term BF16
 // splitting) for blocks of at least one 128 x 128 tile, SIMT otherwise.
 cudaError_t sketch_gemm(riot_ctx *ctx, char ta, char tb, int m, int n, int k, const float *A, int64_t lda,
-                        const float *B, int64_t ldb, float *C, int64_t ldc)
+                        const float *B, int64_t ldb, float *C, int64_t ldc, float alpha = 1.f, float beta = 0.f)
 {
     if (m >= 128 && n >= 128 && k >= 64)
-        return tc_sgemm(ta, tb, m, n, k, 1.f, A, lda, B, ldb, 0.f, C, ldc, ctx->tcws, ctx->tcws_floats, ctx->errflag,
-                        ctx->s);
-    return sgemm(ta, tb, m, n, k, 1.f, A, lda, B, ldb, 0.f, C, ldc, ctx->s);
+        return tc_sgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ctx->tcws, ctx->tcws_floats,
+                        ctx->errflag, ctx->s);
+    return sgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ctx->s);
+}
+
+// ---------------------------------------------------------------------------
+// Spectral preconditioner of Algorithm 3 (Section 2.2, Eq. 7).  Each factor
+// acts on a block as X <- X + V_j diag(c_j) (V_j^T X): P_k applies the newest
+// factor first, P_k^T and P_k^-1 the oldest first (every P'_j is symmetric).
+// ---------------------------------------------------------------------------
+enum { PC_P = 0, PC_PT = 1, PC_PINV = 2 };
+
+void pc_free(riot_ctx *ctx)
+{
+    for (void *p : ctx->pc_allocs) cudaFree(p);
+    ctx->pc_allocs.clear();
+    ctx->pcV = ctx->pcc = ctx->pci = ctx->pcT = ctx->pcB = nullptr;
+    ctx->pcV32 = ctx->pcB32 = ctx->pcT32 = nullptr;
+    ctx->pc_off.clear();
+    ctx->pc_m.clear();
+    ctx->pc_cap = ctx->pc_rot = ctx->pc_cols = ctx->rot_cols = ctx->pc_ready = ctx->pc_open = ctx->pc_dirty = 0;
+}
+
+template <typename T>
+riot_status pc_alloc(riot_ctx *ctx, T **p, size_t count)
+{
+    void *q = nullptr;
+    if (cudaMalloc(&q, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RIOT_ENOMEM, "cudaMalloc of %zu bytes for the preconditioner failed", count * sizeof(T));
+    }
+    ctx->pc_allocs.push_back(q);
+    *p = (T *)q;
+    return RIOT_OK;
+}
+
+// X (n x ncols FP64, ld n, ncols <= kmax) <- op(P_k) X
+riot_status pc_apply64(riot_ctx *ctx, double *X, int ncols, int op)
+{
+    const int n = ctx->n, nf = (int)ctx->pc_m.size();
+    for (int t = 0; t < nf; ++t) {
+        const int j = (op == PC_P) ? nf - 1 - t : t;
+        const int m = ctx->pc_m[j];
+        const double *V = ctx->pcV + (size_t)ctx->pc_off[j] * n;
+        const double *c = (op == PC_PINV ? ctx->pci : ctx->pcc) + ctx->pc_off[j];
+        CU(gemm('T', 'N', m, ncols, n, 1.0, V, 'd', n, X, 'd', n, 0.0, ctx->pcT, 'd', m, ctx->s));
+        CU(scale_rows(m, ncols, m, c, ctx->pcT, 1, ctx->s));
+        CU(gemm('N', 'N', n, ncols, m, 1.0, V, 'd', n, ctx->pcT, 'd', m, 1.0, X, 'd', n, ctx->s));
+    }
+    return RIOT_OK;
+}
+
+// the same on an FP32 block with the FP32 copies of V_j (tensor-core GEMMs when large)
+riot_status pc_apply32(riot_ctx *ctx, float *X, int ncols, int op)
+{
+    const int n = ctx->n, nf = (int)ctx->pc_m.size();
+    for (int t = 0; t < nf; ++t) {
+        const int j = (op == PC_P) ? nf - 1 - t : t;
+        const int m = ctx->pc_m[j];
+        const float *V = ctx->pcV32 + (size_t)ctx->pc_off[j] * n;
+        const double *c = (op == PC_PINV ? ctx->pci : ctx->pcc) + ctx->pc_off[j];
+        CU(sketch_gemm(ctx, 'T', 'N', m, ncols, n, V, n, X, n, ctx->pcT32, m));
+        CU(scale_rows(m, ncols, m, c, ctx->pcT32, 0, ctx->s));
+        CU(sketch_gemm(ctx, 'N', 'N', n, ncols, m, V, n, ctx->pcT32, m, X, n, 1.f, 1.f));
+    }
+    return RIOT_OK;
+}
+
+// Hessian of the inner loop on k columns (ld n, the context's real type): A of Eq. 4, or
+// with preconditioner factors A_k = P_k^T P_k - I + P_k^T A P_k = P_k^T (I + A) P_k - I of
+// Algorithm 3.  On the mixed path everything is in the 2^-scale_exp scaling of the FP32
+// products.  The U block serves as scratch for P_k W (it is rewritten by rsvd_ritz).
+riot_status inner_hvp(riot_ctx *ctx, const void *W, void *Y, int k)
+{
+    const int n = ctx->n;
+    if (ctx->pc_m.empty()) return hvp(ctx, W, Y, n, k, 0);
+    const bool f64 = (ctx->prec == RIOT_PREC_FP64);
+    const double sc = ldexp(1.0, -ctx->scale_exp);
+    void *Z = ctx->U;
+    CU(cudaMemcpyAsync(Z, W, (size_t)n * k * real_size(ctx), cudaMemcpyDeviceToDevice, ctx->s));
+    if (f64) TRY(pc_apply64(ctx, (double *)Z, k, PC_P));
+    else TRY(pc_apply32(ctx, (float *)Z, k, PC_P));
+    TRY(hvp(ctx, Z, Y, n, k, 0));
+    CU(axpby_cols(n, k, n, sc, Z, 1.0, Y, f64, ctx->s));     // (I + A) P_k W
+    if (f64) TRY(pc_apply64(ctx, (double *)Y, k, PC_PT));
+    else TRY(pc_apply32(ctx, (float *)Y, k, PC_PT));
+    CU(axpby_cols(n, k, n, -sc, W, 1.0, Y, f64, ctx->s));    // - W
+    return RIOT_OK;
+}
+
+// Rotation of the sketch: W <- (I - U_k U_k^T) W with U_k the rotation basis, in column
+// chunks of at most kmax (orthonormal chunks, so the chunked projection is the same
+// projector).  Algorithm 3 then maps the columns by P_k^-1; that map is the identity on
+// the complement of the span of every P_j V_j (P_j^T z = z there, by induction over the
+// factors), so it is left out.
+riot_status pc_rotate(riot_ctx *ctx, void *W, int k)
+{
+    const int n = ctx->n;
+    const bool f64 = (ctx->prec == RIOT_PREC_FP64);
+    for (int c0 = 0; c0 < ctx->rot_cols; c0 += ctx->kmax) {
+        const int nc = (ctx->rot_cols - c0 < ctx->kmax) ? ctx->rot_cols - c0 : ctx->kmax;
+        if (f64) {
+            const double *B = ctx->pcB + (size_t)c0 * n;
+            CU(gemm('T', 'N', nc, k, n, 1.0, B, 'd', n, W, 'd', n, 0.0, ctx->pcT, 'd', nc, ctx->s));
+            CU(gemm('N', 'N', n, k, nc, -1.0, B, 'd', n, ctx->pcT, 'd', nc, 1.0, W, 'd', n, ctx->s));
+        } else {
+            const float *B = ctx->pcB32 + (size_t)c0 * n;
+            CU(sketch_gemm(ctx, 'T', 'N', nc, k, n, B, n, (const float *)W, n, ctx->pcT32, nc));
+            CU(sketch_gemm(ctx, 'N', 'N', n, k, nc, B, n, ctx->pcT32, nc, (float *)W, n, -1.f, 1.f));
+        }
+    }
+    return RIOT_OK;
+}
+
+// Append P'_j = I + V ((lambda + 1)^-1/2 - 1) V^T (V: n x m FP64 on the device, ld n, orthonormal
+// columns; lambda: m host values).  With rotation, P_k V (before the factor joins) is
+// orthogonalised against the rotation basis and orthonormalised onto its end.  Synchronises.
+riot_status pc_push(riot_ctx *ctx, const double *V, const double *lambda, int m)
+{
+    if (ctx->pc_cols + m > ctx->pc_cap)
+        return fail(ctx, RIOT_EINVAL, "%d stored columns plus m = %d exceed max_cols = %d", ctx->pc_cols, m, ctx->pc_cap);
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    std::vector<double> c(m), ci(m);
+    for (int i = 0; i < m; ++i) {
+        const double lt = lambda[i] + 1.0;   // eigenvalue of I + A_k
+        if (!(lt > 0.0) || !isfinite(lt))
+            return fail(ctx, RIOT_ENONFINITE, "riot_precond_push: eigenvalue %d of I + A_k is %g", i, lt);
+        c[i] = 1.0 / sqrt(lt) - 1.0;
+        ci[i] = sqrt(lt) - 1.0;
+    }
+    if (ctx->pc_rot) {
+        double *X = ctx->pcB + (size_t)ctx->rot_cols * n;
+        CU(cudaMemcpyAsync(X, V, sizeof(double) * (size_t)n * m, cudaMemcpyDeviceToDevice, s));
+        TRY(pc_apply64(ctx, X, m, PC_P));
+        for (int pass = 0; pass < 2; ++pass)
+            for (int c0 = 0; c0 < ctx->rot_cols; c0 += ctx->kmax) {
+                const int nc = (ctx->rot_cols - c0 < ctx->kmax) ? ctx->rot_cols - c0 : ctx->kmax;
+                const double *B = ctx->pcB + (size_t)c0 * n;
+                CU(gemm('T', 'N', nc, m, n, 1.0, B, 'd', n, X, 'd', n, 0.0, ctx->pcT, 'd', nc, s));
+                CU(gemm('N', 'N', n, m, nc, -1.0, B, 'd', n, ctx->pcT, 'd', nc, 1.0, X, 'd', n, s));
+            }
+        CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 8, s));
+        TRY(cholqr64(ctx, X, m, 3, 0));
+        TRY(check_cholesky(ctx, 0, 5, "riot_precond_push (rotation basis)"));
+        if (ctx->prec == RIOT_PREC_MIXED)
+            CU(convert_block(X, 'd', n, ctx->pcB32 + (size_t)ctx->rot_cols * n, 'f', n, n, m, s));
+    }
+    const int off = ctx->pc_cols;
+    CU(cudaMemcpyAsync(ctx->pcV + (size_t)off * n, V, sizeof(double) * (size_t)n * m, cudaMemcpyDeviceToDevice, s));
+    if (ctx->prec == RIOT_PREC_MIXED) CU(convert_block(V, 'd', n, ctx->pcV32 + (size_t)off * n, 'f', n, n, m, s));
+    CU(cudaMemcpyAsync(ctx->pcc + off, c.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ctx->pci + off, ci.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));   // the host coefficients go out of scope
+    ctx->pc_off.push_back(off);
+    ctx->pc_m.push_back(m);
+    ctx->pc_cols += m;
+    if (ctx->pc_rot) ctx->rot_cols += m;
+    ctx->pc_dirty = 1;
+    return RIOT_OK;
 }
 
 riot_status rsvd_check_args(riot_ctx *ctx, int k, int q)
@@ -724,6 +897,9 @@ riot_status rsvd_check_args(riot_ctx *ctx, int k, int q)
     if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_rsvd before riot_outer_begin");
     if (k < 1 || k > ctx->kmax || k > ctx->n) return fail(ctx, RIOT_EINVAL, "k = %d outside [1, min(kmax, n)]", k);
     if (q < 0 || q > 64) return fail(ctx, RIOT_EINVAL, "q = %d outside [0, 64]", q);
+    if (ctx->pc_rot && ctx->rot_cols + k > ctx->n)
+        return fail(ctx, RIOT_EINVAL, "rotation: k = %d plus %d resolved directions exceed n = %d", k, ctx->rot_cols,
+                    ctx->n);
     return RIOT_OK;
 }
 
@@ -740,6 +916,7 @@ riot_status rsvd_begin(riot_ctx *ctx, int k, int64_t sketch_stream, const void *
         CU(cudaMemcpyAsync(ctx->Wblk, Omega, (size_t)n * k * real_size(ctx), cudaMemcpyDeviceToDevice, ctx->s));
     else
         CU(normal_launch(ctx->seed, (uint32_t)sketch_stream, n, k, n, ctx->prec == RIOT_PREC_FP64, ctx->Wblk, ctx->s));
+    if (ctx->pc_rot && ctx->rot_cols > 0) TRY(pc_rotate(ctx, ctx->Wblk, k));
     return RIOT_OK;
 }
 
@@ -804,7 +981,7 @@ riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
         if (mixed) CU(cudaMemcpyAsync(W32, ctx->Q32, sizeof(float) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
         else CU(convert_block(ctx->Q, 'd', n, ctx->Wblk, tr, n, n, k, s));
         ev_mark(ctx, 0);
-        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, n, k, 0));
+        TRY(inner_hvp(ctx, ctx->Wblk, ctx->Yblk, k));
         ev_mark(ctx, 2);
         if (mixed) {
             CU(sketch_gemm(ctx, 'T', 'N', k, k, n, ctx->Q32, n, Y32, n, ctx->N32, k));
@@ -909,6 +1086,8 @@ riot_status increment_queue(riot_ctx *ctx, int k)
     CU(increment_coef(ctx->lam, k, ctx->cvec, ctx->info + 14, s));
     CU(gemm('N', 'N', n, 1, k, 1.0, ctx->U, 'd', n, ctx->cvec, 'd', k, 0.0, ctx->dv, 'd', n, s));
     CU(add_if_flag(ctx->info + 14, 1, n, -1.0, ctx->g, ctx->dv, s));
+    // preconditioned loop: dv = P_k dw in the control variable of x = x_b + L v
+    if (!ctx->pc_m.empty()) TRY(pc_apply64(ctx, ctx->dv, 1, PC_P));
     CU(axpby(n, 1.0, ctx->dv, 1.0, ctx->v, s));
     CU(bsqrt(ctx, ctx->dv, ctx->tmp, 0, 1));
     CU(axpby(n, 1.0, ctx->tmp, 1.0, ctx->x, s));
@@ -1034,6 +1213,7 @@ void riot_destroy(riot_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->dev);
     if (ctx->s) cudaStreamSynchronize(ctx->s);
+    pc_free(ctx);
     for (void *p : ctx->allocs) cudaFree(p);
     for (int i = 0; i < 32; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -1108,9 +1288,13 @@ riot_status riot_outer_begin(riot_ctx *ctx, const double *x_dev, const double *v
         if (ctx->prec == RIOT_PREC_MIXED) TRY(choose_scale(ctx));
     }
     CU(axpby(n, 1.0, ctx->v, 1.0, ctx->g, ctx->s));
+    // preconditioned loop: the gradient of the problem in w (v = v_{k-1} + P_k w) is P_k^T (b + v)
+    if (!ctx->pc_m.empty()) TRY(pc_apply64(ctx, ctx->g, 1, PC_PT));
     CU(add_half_sq(n, ctx->v, ctx->jo, ctx->s));
     ctx->have_traj = 1;
     ctx->have_rsvd = 0;
+    ctx->pc_open = 0;
+    ctx->pc_dirty = 0;
     if (J_out) {
         CU(cudaMemcpyAsync(J_out, ctx->jo, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
         CU(cudaStreamSynchronize(ctx->s));
@@ -1181,21 +1365,26 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
 {
     if (!ctx) return RIOT_EINVAL;
     TRY(rsvd_check_args(ctx, k, q));
+    if (ctx->pc_dirty) return fail(ctx, RIOT_ESTATE, "riot_rsvd after riot_precond_push needs riot_outer_begin first");
     CU(cudaSetDevice(ctx->dev));
     ctx->nev = 0;
+    ctx->pc_ready = 0;
+    ctx->pc_open = 0;
     ev_mark(ctx, -1);
     TRY(rsvd_begin(ctx, k, sketch_stream, Omega_dev));
     ev_mark(ctx, 0);
-    TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, ctx->n, k, 0));
+    TRY(inner_hvp(ctx, ctx->Wblk, ctx->Yblk, k));
     for (int it = 0; it < q; ++it) {
         ev_mark(ctx, 1);
         TRY(rsvd_power(ctx, k));
         ev_mark(ctx, 0);
-        TRY(hvp(ctx, ctx->Wblk, ctx->Yblk, ctx->n, k, 0));
+        TRY(inner_hvp(ctx, ctx->Wblk, ctx->Yblk, k));
     }
     TRY(rsvd_end(ctx, k, true));
     ev_mark(ctx, -2);
-    return rsvd_retry_k(ctx, k, lambda_out, rsvd_collect(ctx, k, lambda_out));
+    TRY(rsvd_retry_k(ctx, k, lambda_out, rsvd_collect(ctx, k, lambda_out)));
+    ctx->pc_open = 1;
+    return RIOT_OK;
 }
 
 riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6)
@@ -1233,8 +1422,11 @@ riot_status riot_increment(riot_ctx *ctx, double *dv_dev, int32_t *mode_out)
 {
     if (!ctx) return RIOT_EINVAL;
     if (!ctx->have_rsvd) return fail(ctx, RIOT_ESTATE, "riot_increment before riot_rsvd");
+    if (ctx->pc_dirty) return fail(ctx, RIOT_ESTATE, "riot_increment after riot_precond_push needs a new inner loop");
     CU(cudaSetDevice(ctx->dev));
     TRY(increment_queue(ctx, ctx->k_last));
+    ctx->pc_ready = 1;
+    ctx->pc_open = 0;
     if (dv_dev) CU(cudaMemcpyAsync(dv_dev, ctx->dv, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->s));
     if (mode_out) {
         CU(cudaMemcpyAsync(mode_out, ctx->info + 14, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
@@ -1477,8 +1669,10 @@ riot_status riot_batch_run(riot_batch *b, int64_t sketch_stream, int32_t use_gra
 {
     if (!b) return RIOT_EINVAL;
     const int nw = (int)b->ctx.size();
-    for (int w = 0; w < nw; ++w)
+    for (int w = 0; w < nw; ++w) {
         if (!b->ctx[w]->have_traj) return bfail(b, RIOT_ESTATE, "window %d: no riot_outer_begin yet", w);
+        if (b->ctx[w]->pc_cap) return bfail(b, RIOT_EINVAL, "window %d: batches run without the spectral preconditioner", w);
+    }
     CU_B(cudaSetDevice(b->dev));
     // the batch's stream follows the caller's work, and the caller's follows the batch
     CU_B(cudaEventRecord(b->done, b->s));
@@ -1714,6 +1908,7 @@ riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sket
     TRY(rsvd_check_args(ctx, k, q));
     if (ctx->prec != RIOT_PREC_MIXED) return fail(ctx, RIOT_EINVAL, "riot_rsvd_proposal: mixed-precision contexts only");
     if (m < 0 || m > k || (m > 0 && !P_dev)) return fail(ctx, RIOT_EINVAL, "m = %d outside [0, k] or null proposal", m);
+    if (!ctx->pc_m.empty()) return fail(ctx, RIOT_ESTATE, "riot_rsvd_proposal: not with the spectral preconditioner");
     CU(cudaSetDevice(ctx->dev));
     const int n = ctx->n;
     cudaStream_t s = ctx->s;
@@ -1812,6 +2007,7 @@ riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_o
     if (!ctx) return RIOT_EINVAL;
     if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_varcg before riot_outer_begin");
     if (m < 1 || m > ctx->kmax) return fail(ctx, RIOT_EINVAL, "m = %d outside [1, kmax = %d]", m, ctx->kmax);
+    if (!ctx->pc_m.empty()) return fail(ctx, RIOT_ESTATE, "riot_varcg: Algorithm 1 runs without the spectral preconditioner");
     CU(cudaSetDevice(ctx->dev));
     const int n = ctx->n;
     cudaStream_t s = ctx->s;
@@ -1877,6 +2073,76 @@ riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_o
     if (m_used) *m_used = mm;
     return RIOT_OK;
 }
+
+riot_status riot_precond_enable(riot_ctx *ctx, int32_t max_cols, int32_t rotation)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (max_cols < 0 || max_cols > ctx->n) return fail(ctx, RIOT_EINVAL, "max_cols = %d outside [0, n = %d]", max_cols, ctx->n);
+    CU(cudaSetDevice(ctx->dev));
+    CU(cudaStreamSynchronize(ctx->s));   // queued work may still read the old factors
+    pc_free(ctx);
+    if (max_cols == 0) return RIOT_OK;
+    const size_t n = (size_t)ctx->n, cap = (size_t)max_cols, kk = (size_t)ctx->kmax * ctx->kmax;
+    const bool mixed = (ctx->prec == RIOT_PREC_MIXED);
+    riot_status st;
+    if ((st = pc_alloc(ctx, &ctx->pcV, n * cap)) || (st = pc_alloc(ctx, &ctx->pcc, cap)) ||
+        (st = pc_alloc(ctx, &ctx->pci, cap)) || (st = pc_alloc(ctx, &ctx->pcT, kk)) ||
+        (rotation && (st = pc_alloc(ctx, &ctx->pcB, n * cap))) ||
+        (mixed && ((st = pc_alloc(ctx, &ctx->pcV32, n * cap)) || (st = pc_alloc(ctx, &ctx->pcT32, kk)) ||
+                   (rotation && (st = pc_alloc(ctx, &ctx->pcB32, n * cap)))))) {
+        pc_free(ctx);
+        return st;
+    }
+    ctx->pc_cap = max_cols;
+    ctx->pc_rot = rotation ? 1 : 0;
+    return RIOT_OK;
+}
+
+riot_status riot_precond_push(riot_ctx *ctx, int32_t m)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->pc_cap) return fail(ctx, RIOT_ESTATE, "riot_precond_push before riot_precond_enable");
+    if (!ctx->have_rsvd || !ctx->pc_ready)
+        return fail(ctx, RIOT_ESTATE, "riot_precond_push takes the pairs of an inner loop after its riot_increment");
+    if (m < 1 || m > ctx->k_last) return fail(ctx, RIOT_EINVAL, "m = %d outside [1, k = %d]", m, ctx->k_last);
+    CU(cudaSetDevice(ctx->dev));
+    std::vector<double> lam(m);
+    CU(cudaMemcpyAsync(lam.data(), ctx->lam, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    TRY(pc_push(ctx, ctx->U, lam.data(), m));
+    ctx->pc_ready = 0;
+    return RIOT_OK;
+}
+
+riot_status riot_precond_push_pairs(riot_ctx *ctx, const double *V_dev, const double *lambda, int32_t m)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->pc_cap) return fail(ctx, RIOT_ESTATE, "riot_precond_push_pairs before riot_precond_enable");
+    if (ctx->pc_open) return fail(ctx, RIOT_ESTATE, "riot_precond_push_pairs inside an inner loop (before its riot_increment)");
+    if (m < 1 || m > ctx->kmax || !V_dev || !lambda)
+        return fail(ctx, RIOT_EINVAL, "m = %d outside [1, kmax = %d] or null pairs", m, ctx->kmax);
+    CU(cudaSetDevice(ctx->dev));
+    return pc_push(ctx, V_dev, lambda, m);
+}
+
+riot_status riot_precond_apply(riot_ctx *ctx, const double *X_dev, double *Y_dev, int32_t ncols, int32_t op)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (ncols < 0 || (ncols > 0 && (!X_dev || !Y_dev)) || op < PC_P || op > PC_PINV)
+        return fail(ctx, RIOT_EINVAL, "riot_precond_apply: bad arguments");
+    if (ncols == 0) return RIOT_OK;
+    CU(cudaSetDevice(ctx->dev));
+    const int n = ctx->n;
+    if (X_dev != Y_dev)
+        CU(cudaMemcpyAsync(Y_dev, X_dev, sizeof(double) * (size_t)n * ncols, cudaMemcpyDeviceToDevice, ctx->s));
+    for (int c0 = 0; c0 < ncols; c0 += ctx->kmax) {
+        const int nc = (ncols - c0 < ctx->kmax) ? ncols - c0 : ctx->kmax;
+        TRY(pc_apply64(ctx, Y_dev + (size_t)c0 * n, nc, op));
+    }
+    return RIOT_OK;
+}
+
+int32_t riot_precond_count(const riot_ctx *ctx) { return ctx ? (int32_t)ctx->pc_m.size() : -1; }
 
 riot_status riot_tc_gram(int32_t n, int32_t k, const float *Y_dev, int64_t ldy, double *G_dev, int64_t ldg,
                          void *cuda_stream)

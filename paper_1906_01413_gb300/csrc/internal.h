@@ -295,6 +295,11 @@ cudaError_t div_one_plus(int m, double *c, const double *theta, cudaStream_t s);
 // Y = a Y (+ W) column by column (n rows of ncols columns at ld), float or double
 cudaError_t scale_add_cols(int64_t n, int ncols, int64_t ld, double a, void *Y, const void *W, int is_double,
                            cudaStream_t s);
+// T (m x ncols at ld, float or double) with row i scaled by coef[i]
+cudaError_t scale_rows(int m, int ncols, int64_t ld, const double *coef, void *T, int is_double, cudaStream_t s);
+// Y = a X + b Y on n rows of ncols columns at ld, float or double
+cudaError_t axpby_cols(int64_t n, int ncols, int64_t ld, double a, const void *X, double b, void *Y, int is_double,
+                       cudaStream_t s);
 // largest-magnitude entry of each of the k columns made positive
 cudaError_t fix_col_signs(double *U, int64_t n, int k, int64_t ld, cudaStream_t s);
 

@@ -1294,6 +1294,53 @@ cudaError_t scale_add_cols(int64_t n, int ncols, int64_t ld, double a, void *Y, 
     return cudaGetLastError();
 }
 
+// T[j*ld + i] *= coef[i] for i < m, j < ncols (float or double block, FP64 coefficients)
+template <typename R>
+__global__ void scale_rows_kernel(int m, int ncols, int64_t ld, const double *__restrict__ coef, R *T)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * ncols) return;
+    const int64_t j = t / m, i = t - j * m;
+    T[j * ld + i] = (R)(coef[i] * (double)T[j * ld + i]);
+}
+
+cudaError_t scale_rows(int m, int ncols, int64_t ld, const double *coef, void *T, int is_double, cudaStream_t s)
+{
+    const int64_t total = (int64_t)m * ncols;
+    if (total <= 0) return cudaSuccess;
+    count_launch();
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    if (is_double)
+        scale_rows_kernel<double><<<grid, 256, 0, s>>>(m, ncols, ld, coef, (double *)T);
+    else
+        scale_rows_kernel<float><<<grid, 256, 0, s>>>(m, ncols, ld, coef, (float *)T);
+    return cudaGetLastError();
+}
+
+// Y[j*ld + i] = a X[j*ld + i] + b Y[j*ld + i] for i < n, j < ncols (float or double)
+template <typename R>
+__global__ void axpby_cols_kernel(int64_t n, int ncols, int64_t ld, R a, const R *__restrict__ X, R b, R *Y)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * ncols) return;
+    const int64_t j = t / n, i = t - j * n;
+    Y[j * ld + i] = a * X[j * ld + i] + b * Y[j * ld + i];
+}
+
+cudaError_t axpby_cols(int64_t n, int ncols, int64_t ld, double a, const void *X, double b, void *Y, int is_double,
+                       cudaStream_t s)
+{
+    const int64_t total = n * ncols;
+    if (total <= 0) return cudaSuccess;
+    count_launch();
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    if (is_double)
+        axpby_cols_kernel<double><<<grid, 256, 0, s>>>(n, ncols, ld, a, (const double *)X, b, (double *)Y);
+    else
+        axpby_cols_kernel<float><<<grid, 256, 0, s>>>(n, ncols, ld, (float)a, (const float *)X, (float)b, (float *)Y);
+    return cudaGetLastError();
+}
+
 cudaError_t add_half_sq(int64_t n, const double *x, double *out, cudaStream_t s)
 {
     int blocks = (int)((n + 255) / 256);

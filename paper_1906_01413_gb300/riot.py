@@ -117,6 +117,16 @@ def load():
     L.riot_varcg.restype = c_int32
     L.riot_tc_gram.argtypes = [c_int32, c_int32, vp, c_int64, vp, c_int64, vp]
     L.riot_tc_gram.restype = c_int32
+    L.riot_precond_enable.argtypes = [vp, c_int32, c_int32]
+    L.riot_precond_enable.restype = c_int32
+    L.riot_precond_push.argtypes = [vp, c_int32]
+    L.riot_precond_push.restype = c_int32
+    L.riot_precond_push_pairs.argtypes = [vp, vp, POINTER(c_double), c_int32]
+    L.riot_precond_push_pairs.restype = c_int32
+    L.riot_precond_apply.argtypes = [vp, vp, vp, c_int32, c_int32]
+    L.riot_precond_apply.restype = c_int32
+    L.riot_precond_count.argtypes = [vp]
+    L.riot_precond_count.restype = c_int32
     L.riot_sketchnet_create.argtypes = [POINTER(vp), c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
                                         c_int32, vp]
     L.riot_sketchnet_num_params.argtypes = [vp]
@@ -465,6 +475,38 @@ def riot_rsvd_proposal(ctx, k, q, P, m, rho_max=1e-2, sketch_stream=0):
            load().riot_rsvd_proposal(ctx, int(k), int(q), int(sketch_stream), _ptr(P), int(m), float(rho_max), lam,
                                      ctypes.byref(rho), ctypes.byref(used)))
     return np.array(lam[:]), rho.value, used.value
+
+
+def riot_precond_enable(ctx, max_cols, rotation=True):
+    _check(ctx, "riot_precond_enable", load().riot_precond_enable(ctx, int(max_cols), int(bool(rotation))))
+
+
+def riot_precond_push(ctx, m):
+    _check(ctx, "riot_precond_push", load().riot_precond_push(ctx, int(m)))
+
+
+def riot_precond_push_pairs(ctx, V, lam):
+    """Factor from given pairs: V (m, n) row-major FP64 device tensor (row j = eigenvector j), lam (m,)."""
+    _need_contiguous(V)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    m = int(lam.size)
+    _check(ctx, "riot_precond_push_pairs",
+           load().riot_precond_push_pairs(ctx, _ptr(V), lam.ctypes.data_as(POINTER(c_double)), m))
+
+
+PRECOND_P, PRECOND_PT, PRECOND_PINV = 0, 1, 2
+
+
+def riot_precond_apply(ctx, X, Y, op=PRECOND_P):
+    """Y = op(P_k) X for (ncols, n) row-major FP64 tensors (column j of the operator = row j)."""
+    _need_contiguous(X)
+    _need_contiguous(Y)
+    ncols = X.shape[0] if X.dim() == 2 else 1
+    _check(ctx, "riot_precond_apply", load().riot_precond_apply(ctx, _ptr(X), _ptr(Y), int(ncols), int(op)))
+
+
+def riot_precond_count(ctx):
+    return int(load().riot_precond_count(ctx))
 
 
 class Context:
