@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-bc", action="store_true", help="skip the tracer-transport Hessian products")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch of 96 windows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned sketch proposal leg")
+    ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned inner-loop leg")
     ap.add_argument("--only", choices=["bc", "batch", "learned"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling)")
     ap.add_argument("--bc-cols", type=int, default=128, help="sketch columns per tracer Hessian call")
@@ -170,6 +171,30 @@ def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False)
             ph["jacobi_sweeps"] = R.riot_rsvd_sweeps(ctx.h)
             phases.append(ph)
     return times, phases, lam, mode
+
+
+def bench_precond(R, torch, ctx, cfg, flush, dv, warmup, steps, plain_ms):
+    """Algorithm 3 with precond = rotation = true on the same window: the last inner loop's
+    pairs with positive eigenvalue become the factor P'_k (riot_precond_push), then timed
+    preconditioned inner loops: riot_rsvd of A_k = P_k^T (I + A) P_k - I on a rotated sketch and
+    riot_increment mapped by P_k.  The context must have just run riot_rsvd + riot_increment."""
+    lam_t = torch.empty(cfg.k, dtype=torch.float64, device=dv.device)
+    R.riot_get_state(ctx.h, lam=lam_t)
+    lam = lam_t.cpu().numpy()
+    m = int(np.sum(lam > 0))
+    R.riot_precond_enable(ctx.h, m, True)
+    t0 = time.perf_counter()
+    R.riot_precond_push(ctx.h, m)
+    push_s = time.perf_counter() - t0
+    R.riot_outer_begin(ctx.h)
+    times, phases, lam2, mode = time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv)
+    R.riot_precond_enable(ctx.h, 0, False)
+    ms = statistics.mean(times)
+    ph = {key: statistics.mean(p_[key] for p_ in phases) for key in phases[0]}
+    return {"what": "inner loop of Algorithm 3 with precond = rotation = true (one factor of %d pairs)" % m,
+            "ms_per_step": ms, "value": (cfg.q + 1) * cfg.k / (ms * 1e-3), "unit": UNIT,
+            "overhead_vs_plain": ms / plain_ms - 1.0, "phases_ms": ph, "push_ms": push_s * 1e3,
+            "lambda1": float(lam2[0]), "mode": int(mode)}
 
 
 def build_bc_problem(R, torch, cfg, dev, precision, kmax):
@@ -567,6 +592,12 @@ def main():
         if i >= args.warmup:
             e2e_times.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_times)
+    precond = None
+    if not args.no_precond:
+        try:
+            precond = bench_precond(R, torch, ctx, cfg, flush, dv, 1, max(3, args.steps // 2), ms)
+        except R.RiotError as e:   # keep the headline line; report the leg's failure in it
+            precond = {"error": str(e)}
 
     # ---- tracer-transport inversion (workload 3): Hessian products on the full grid ----
     learned = None
@@ -621,6 +652,8 @@ def main():
         line["batch_windows"] = batch
     if learned:
         line["learned_sketch"] = learned
+    if precond:
+        line["precond_rotation"] = precond
     cs = clk.summary()
     if cs:
         line["clocks"] = cs

@@ -750,7 +750,7 @@ void pc_free(riot_ctx *ctx)
     ctx->pcV32 = ctx->pcB32 = ctx->pcT32 = nullptr;
     ctx->pc_off.clear();
     ctx->pc_m.clear();
-    ctx->pc_cap = ctx->pc_rot = ctx->pc_cols = ctx->rot_cols = ctx->pc_ready = ctx->pc_open = ctx->pc_dirty = 0;
+    ctx->pc_cap = ctx->pc_rot = ctx->pc_cols = ctx->rot_cols = 0;
 }
 
 template <typename T>
@@ -2080,6 +2080,9 @@ riot_status riot_precond_enable(riot_ctx *ctx, int32_t max_cols, int32_t rotatio
     if (max_cols < 0 || max_cols > ctx->n) return fail(ctx, RIOT_EINVAL, "max_cols = %d outside [0, n = %d]", max_cols, ctx->n);
     CU(cudaSetDevice(ctx->dev));
     CU(cudaStreamSynchronize(ctx->s));   // queued work may still read the old factors
+    // dropping factors leaves a gradient formed with them stale (riot_outer_begin again);
+    // the state of the current inner loop (rsvd / increment done) is kept
+    if (!ctx->pc_m.empty()) ctx->pc_dirty = 1;
     pc_free(ctx);
     if (max_cols == 0) return RIOT_OK;
     const size_t n = (size_t)ctx->n, cap = (size_t)max_cols, kk = (size_t)ctx->kmax * ctx->kmax;

@@ -233,4 +233,14 @@ def test_precond_call_order_and_errors(gpu_lib):
     R.riot_outer_begin(ctx.h)
     theta, used = R.riot_varcg(ctx.h, 4)
     assert used == 4
+    # enabling after an inner loop keeps that loop's pairs available to push
+    lam = R.riot_rsvd(ctx.h, cfg.k, 0, Omega=_t(cfg.sketch(0)))
+    R.riot_increment(ctx.h)
+    R.riot_precond_enable(ctx.h, cfg.k, True)
+    R.riot_precond_push(ctx.h, int(np.sum(lam > 0)))
+    with pytest.raises(R.RiotError) as e:
+        R.riot_rsvd(ctx.h, 4, 0)
+    assert e.value.status == -6
+    R.riot_outer_begin(ctx.h)
+    R.riot_rsvd(ctx.h, 4, 0, Omega=_t(cfg.sketch(3, k=4)))
     ctx.close()
