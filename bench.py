@@ -173,14 +173,15 @@ def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False)
     return times, phases, lam, mode
 
 
-def bench_precond(R, torch, ctx, cfg, flush, dv, warmup, steps, plain_ms):
-    """Algorithm 3 with precond = rotation = true on the same window: the last inner loop's
-    pairs with positive eigenvalue become the factor P'_k (riot_precond_push), then timed
-    preconditioned inner loops: riot_rsvd of A_k = P_k^T (I + A) P_k - I on a rotated sketch and
-    riot_increment mapped by P_k.  The context must have just run riot_rsvd + riot_increment."""
-    lam_t = torch.empty(cfg.k, dtype=torch.float64, device=dv.device)
-    R.riot_get_state(ctx.h, lam=lam_t)
-    lam = lam_t.cpu().numpy()
+def bench_precond(R, torch, ctx, xb, cfg, flush, dv, warmup, steps, plain_ms):
+    """Algorithm 3 with precond = rotation = true on the same window: outer loop 1 from the
+    background (the timed steps above moved x without re-linearising), its pairs with positive
+    eigenvalue become the factor P'_1 (riot_precond_push), then timed preconditioned inner loops
+    of outer loop 2: riot_rsvd of A_2 = P_2^T (I + A) P_2 - I on a rotated sketch and
+    riot_increment mapped by P_2."""
+    R.riot_outer_begin(ctx.h, xb, torch.zeros_like(xb))
+    lam = R.riot_rsvd(ctx.h, cfg.k, cfg.q, sketch_stream=configs.STREAM_SKETCH0)
+    R.riot_increment(ctx.h, dv)
     m = int(np.sum(lam > 0))
     R.riot_precond_enable(ctx.h, m, True)
     t0 = time.perf_counter()
@@ -595,7 +596,7 @@ def main():
     precond = None
     if not args.no_precond:
         try:
-            precond = bench_precond(R, torch, ctx, cfg, flush, dv, 1, max(3, args.steps // 2), ms)
+            precond = bench_precond(R, torch, ctx, xb, cfg, flush, dv, 1, max(3, args.steps // 2), ms)
         except R.RiotError as e:   # keep the headline line; report the leg's failure in it
             precond = {"error": str(e)}
 
