@@ -176,9 +176,11 @@ def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False)
 def bench_precond(R, torch, ctx, xb, cfg, flush, dv, warmup, steps, plain_ms):
     """Algorithm 3 with precond = rotation = true on the same window: outer loop 1 from the
     background (the timed steps above moved x without re-linearising), its pairs with positive
-    eigenvalue become the factor P'_1 (riot_precond_push), then timed preconditioned inner loops
-    of outer loop 2: riot_rsvd of A_2 = P_2^T (I + A) P_2 - I on a rotated sketch and
-    riot_increment mapped by P_2."""
+    eigenvalue become the factor P'_1 (riot_precond_push), then timed preconditioned inner loops:
+    riot_rsvd of A_2 = P_2^T (I + A) P_2 - I on a rotated sketch and riot_increment mapped by P_2.
+    Loop 2 is linearised at the background again: one full step on this 200-step window leaves
+    the attractor (the LRU step applies the unresolved part of a gradient grown by the
+    tangent-linear model unscaled), and the inner-loop cost does not depend on the state."""
     R.riot_outer_begin(ctx.h, xb, torch.zeros_like(xb))
     lam = R.riot_rsvd(ctx.h, cfg.k, cfg.q, sketch_stream=configs.STREAM_SKETCH0)
     R.riot_increment(ctx.h, dv)
@@ -187,7 +189,7 @@ def bench_precond(R, torch, ctx, xb, cfg, flush, dv, warmup, steps, plain_ms):
     t0 = time.perf_counter()
     R.riot_precond_push(ctx.h, m)
     push_s = time.perf_counter() - t0
-    R.riot_outer_begin(ctx.h)
+    R.riot_outer_begin(ctx.h, xb, torch.zeros_like(xb))
     times, phases, lam2, mode = time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv)
     R.riot_precond_enable(ctx.h, 0, False)
     ms = statistics.mean(times)
