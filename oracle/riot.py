@@ -187,6 +187,78 @@ def varcg(prob, traj, g, m):
     return dv, theta, U
 
 
+def gradient_samples(prob, x, v, eps_obs, eps_b):
+    """Starting block of Algorithm 2 (VarBL): for sample j, the gradient at the perturbed state
+    x + L eps_b_j with perturbed observations,
+        b_j = L^T H_j^T R^-1 d_j + v + eps_b_j,   d_j = H(x + L eps_b_j) - y + L_R eps_obs_j,
+    H_j^T the adjoint at x + L eps_b_j and L_R = diag(sigma_o) (R = L_R L_R^T).
+    eps_obs: (p, l), eps_b: (n, l); the listing sets eps_b_1 = 0, which is the caller's choice."""
+    eps_obs = np.asarray(eps_obs, dtype=np.float64)
+    eps_b = np.asarray(eps_b, dtype=np.float64)
+    l = eps_b.shape[1]
+    B = np.empty((prob.n, l))
+    for j in range(l):
+        traj = trajectory(prob, x + prob.L @ eps_b[:, j])
+        d = observe(prob, traj) - prob.y + prob.sigma_o * eps_obs[:, j]
+        B[:, j] = gradient_b(prob, traj, d) + v + eps_b[:, j]
+    return B
+
+
+def varbl(prob, traj, B0, m, g, apply=None):
+    """Algorithm 2 (VarBL): block Lanczos on A from the orthonormalised gradient samples B0
+    (n, l), m block steps.  Step i: Y_i = A Q_i, M_i = Q_i^T Y_i; unless i = m, the residual
+    r = Y_i - Q_i M_i - Q_{i-1} W_{i-1}^T is factored r = Q_{i+1} W_i (QR) and Q_{i+1} is
+    re-orthonormalised against Q_1 .. Q_i (twice, as the listing asks; the second QR's factor
+    is carried into W_i so that r = Q_{i+1} W_i still holds).  T (ml x ml) has M_i on
+    the diagonal and W_i / W_i^T below / above it; T = Z Lambda Z^T, U = Q Z and
+    dv = -U diag(1 / (1 + lambda)) U^T g.
+    Reading: the listing's final b is the gradient of the unperturbed problem, g = b + v at
+    x_{k-1} (the samples only span the Krylov space).  The recurrence stops early when a
+    residual block loses rank (|diag W_i| below 1e-12 of the largest |M| seen): the Krylov
+    space is then invariant.  Returns (dv, lam descending, U, T, Q)."""
+    apply = apply or (lambda W: hvp(prob, traj, W))
+    B0 = np.asarray(B0, dtype=np.float64)
+    l = B0.shape[1]
+    Qs = [orthonormal_basis(B0)]
+    Ms, Ws = [], []
+    scale = 0.0
+    for i in range(m):
+        Qi = Qs[-1]
+        Yi = apply(Qi)
+        Mi = Qi.T @ Yi
+        Ms.append(Mi)
+        scale = max(scale, float(np.abs(Mi).max()))
+        if i == m - 1:
+            break
+        r = Yi - Qi @ Mi
+        if i > 0:
+            r = r - Qs[-2] @ Ws[-1].T
+        Qn, Wi = np.linalg.qr(r, mode="reduced")
+        if np.abs(np.diag(Wi)).min() <= 1e-12 * scale:
+            break
+        Qprev = np.hstack(Qs)
+        for _ in range(2):
+            Qn = Qn - Qprev @ (Qprev.T @ Qn)
+        Qn, R2 = np.linalg.qr(Qn, mode="reduced")     # r = Q_{i+1} (R2 W_i) after the re-orthonormalisation
+        Ws.append(R2 @ Wi)
+        Qs.append(Qn)
+    nb = len(Ms)
+    T = np.zeros((nb * l, nb * l))
+    for i in range(nb):
+        T[i * l:(i + 1) * l, i * l:(i + 1) * l] = Ms[i]
+        if i + 1 < nb:
+            T[(i + 1) * l:(i + 2) * l, i * l:(i + 1) * l] = Ws[i]
+            T[i * l:(i + 1) * l, (i + 1) * l:(i + 2) * l] = Ws[i].T
+    T = 0.5 * (T + T.T)
+    lam, Z = np.linalg.eigh(T)
+    order = np.argsort(-lam, kind="stable")
+    lam, Z = lam[order], Z[:, order]
+    Q = np.hstack(Qs[:nb])
+    U = Q @ Z
+    dv = -U @ ((U.T @ g) / (1.0 + lam))
+    return dv, lam, U, T, Q
+
+
 def orthonormal_basis(Y):
     """Q of a Householder QR of Y (LAPACK geqrf/orgqr via numpy)."""
     Q, _ = np.linalg.qr(Y, mode="reduced")
