@@ -407,6 +407,29 @@ riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sket
  * per step, for the stopping test). */
 riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_out, int32_t *m_used);
 
+/* Algorithm 2 (VarBL): block Lanczos on A from l gradient samples, m block
+ * steps (Section 2.1, block-Lanczos paragraph; Algorithm 2).  B0_dev holds the
+ * samples b_j = L^T H_j^T R^-1 d_j + v + eps_b_j as n x l FP64 columns
+ * (column-major, ld n, on the device; the caller forms them, e.g. with one
+ * context per sample: riot_outer_begin at x + L eps_b_j on observations
+ * y - sigma eps_obs_j, then riot_get_state's g plus eps_b_j).  Q_1 = orth(B0);
+ * step i applies A to the l columns of Q_i (one batched launch), M_i = Q_i^T A Q_i,
+ * r = A Q_i - Q_i M_i - Q_{i-1} W_{i-1}^T re-orthogonalised against Q_1..Q_i twice,
+ * Q_{i+1} W_i = r by CholeskyQR (W_i = Q_{i+1}^T r).  The recurrence stops early
+ * when a residual block loses rank (a diagonal entry of W_i at or below 1e-12
+ * of the largest |M| entry so far, or a failed Cholesky): the block Krylov space
+ * is then invariant.  T (block tridiagonal, M_i / W_i / W_i^T) = Z Theta Z^T,
+ * U = Q Z, dv = -U diag(1 / (1 + theta)) U^T g with g the gradient of the
+ * context (riot_outer_begin).  dv_dev (n, may be NULL): the increment;
+ * theta_out (host, l m doubles, may be NULL): the Ritz values, descending, of
+ * which the first l * blocks_used are written; blocks_used (may be NULL).
+ * Requires riot_outer_begin (RIOT_ESTATE), 1 <= l m <= min(kmax, n)
+ * (RIOT_EINVAL), no preconditioner factors (RIOT_ESTATE); RIOT_ENOTSPD if the
+ * samples are linearly dependent.  Reuses the inner-loop workspace like
+ * riot_varcg.  Synchronises (once per block step). */
+riot_status riot_varbl(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev, double *dv_dev, double *theta_out,
+                       int32_t *blocks_used);
+
 /* Spectral preconditioner with rotation (Section 2.2 "Preconditioning", Eq. 7;
  * Algorithm 3 with precond = true).  After outer loop j has run riot_rsvd and
  * riot_increment, riot_precond_push(ctx, m) adds the factor

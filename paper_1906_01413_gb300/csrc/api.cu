@@ -1984,23 +1984,25 @@ riot_status riot_tc_sgemm(char ta, char tb, int32_t m, int32_t n, int32_t k, flo
     return herr ? RIOT_ETIMEOUT : RIOT_OK;
 }
 
-// w = A q for one FP64 vector (FP32 Hessian kernel and back on the mixed path)
-static riot_status apply_a_vec(riot_ctx *ctx, const double *q, double *w)
+// Y = A X for l <= kmax FP64 columns (ld n): the FP32 Hessian kernel and back on the mixed
+// path, the power-of-two scaling of its products undone in FP64
+static riot_status apply_a_block(riot_ctx *ctx, const double *X, double *Y, int l)
 {
     const int n = ctx->n;
     cudaStream_t s = ctx->s;
     if (ctx->prec == RIOT_PREC_FP64) {
-        TRY(hvp(ctx, q, w, n, 1, 0));
-        if (ctx->scale_exp) CU(scale_add_cols(n, 1, n, ldexp(1.0, ctx->scale_exp), w, nullptr, 1, s));
-        return RIOT_OK;
+        TRY(hvp(ctx, X, Y, n, l, 0));
+    } else {
+        float *x32 = (float *)ctx->Wblk, *y32 = (float *)ctx->Yblk;
+        CU(convert_block(X, 'd', n, x32, 'f', n, n, l, s));
+        TRY(hvp(ctx, x32, y32, n, l, 0));
+        CU(convert_block(y32, 'f', n, Y, 'd', n, n, l, s));
     }
-    float *q32 = (float *)ctx->Wblk, *w32 = (float *)ctx->Yblk;
-    CU(convert_block(q, 'd', n, q32, 'f', n, n, 1, s));
-    TRY(hvp(ctx, q32, w32, n, 1, 0));
-    if (ctx->scale_exp) CU(scale_add_cols(n, 1, n, ldexp(1.0, ctx->scale_exp), w32, nullptr, 0, s));
-    CU(convert_block(w32, 'f', n, w, 'd', n, n, 1, s));
+    if (ctx->scale_exp) CU(scale_add_cols(n, l, n, ldexp(1.0, ctx->scale_exp), Y, nullptr, 1, s));
     return RIOT_OK;
 }
+
+static riot_status apply_a_vec(riot_ctx *ctx, const double *q, double *w) { return apply_a_block(ctx, q, w, 1); }
 
 riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_out, int32_t *m_used)
 {
@@ -2071,6 +2073,116 @@ riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_o
     if (theta_out) CU(cudaMemcpyAsync(theta_out, ctx->lam, sizeof(double) * mm, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (m_used) *m_used = mm;
+    return RIOT_OK;
+}
+
+// Eigenpairs of the k x k matrix in Km (not modified by the tridiagonal solver) into lam, Z:
+// the tridiagonal solver, and Jacobi when close eigenvalues left inverse iteration with
+// dependent vectors.  Synchronises.
+static riot_status small_eig(riot_ctx *ctx, int k, const char *what)
+{
+    cudaStream_t s = ctx->s;
+    CU(tridiag_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
+    int einfo[2] = {0, 0};
+    CU(cudaMemcpyAsync(einfo, ctx->info + 12, sizeof(einfo), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (einfo[0] || einfo[1]) {
+        CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, s));
+        CU(cudaMemcpyAsync(einfo, ctx->info + 12, sizeof(einfo), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (einfo[0] < 0) return fail(ctx, RIOT_ENOCONV, "%s: Jacobi did not converge", what);
+    }
+    return RIOT_OK;
+}
+
+riot_status riot_varbl(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev, double *dv_dev, double *theta_out,
+                       int32_t *blocks_used)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_varbl before riot_outer_begin");
+    if (l < 1 || m < 1 || (int64_t)l * m > ctx->kmax || (int64_t)l * m > ctx->n)
+        return fail(ctx, RIOT_EINVAL, "l = %d, m = %d: 1 <= l m <= min(kmax = %d, n = %d) required", l, m, ctx->kmax,
+                    ctx->n);
+    if (!B0_dev) return fail(ctx, RIOT_EINVAL, "riot_varbl: null starting block");
+    if (!ctx->pc_m.empty()) return fail(ctx, RIOT_ESTATE, "riot_varbl: Algorithm 2 runs without the spectral preconditioner");
+    CU(cudaSetDevice(ctx->dev));
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    ctx->have_rsvd = 0;   // the block basis and its Ritz vectors occupy the inner-loop workspace
+    ctx->pc_open = 0;
+    double *Q = ctx->Q, *Y = ctx->U, *H = ctx->G, *blocks = ctx->jwork;
+    const int64_t ll = (int64_t)l * l;
+    // Q_1 = orth(B0)
+    CU(cudaMemcpyAsync(Q, B0_dev, sizeof(double) * (size_t)n * l, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 8, s));
+    TRY(cholqr64(ctx, Q, l, 3, 0));
+    TRY(check_cholesky(ctx, 0, 5, "riot_varbl (the gradient samples are dependent)"));
+    std::vector<double> hM((size_t)ll), hW((size_t)ll);
+    // B0 = Q_1 W_0 with W_0 = Q_1^T B0 upper triangular: a diagonal entry far below the largest
+    // means dependent samples (shifted CholeskyQR would otherwise orthonormalise rounding noise)
+    CU(gemm('T', 'N', l, l, n, 1.0, Q, 'd', n, B0_dev, 'd', n, 0.0, blocks, 'd', l, s));
+    CU(cudaMemcpyAsync(hW.data(), blocks, sizeof(double) * ll, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    {
+        double dmax = 0.0, dmin = INFINITY;
+        for (int j = 0; j < l; ++j) {
+            const double d = fabs(hW[j + (int64_t)j * l]);
+            dmax = fmax(dmax, d);
+            dmin = fmin(dmin, d);
+        }
+        if (!(dmin > 1e-12 * dmax))
+            return fail(ctx, RIOT_ENOTSPD, "riot_varbl: the gradient samples are dependent (%g of the largest)",
+                        dmax > 0 ? dmin / dmax : 0.0);
+    }
+    double scale = 0.0;
+    int nb = 0;
+    for (int i = 0; i < m; ++i) {
+        double *Qi = Q + (size_t)i * l * n;
+        double *Mi = blocks + i * ll;
+        TRY(apply_a_block(ctx, Qi, Y, l));                                                   // Y_i = A Q_i
+        CU(gemm('T', 'N', l, l, n, 1.0, Qi, 'd', n, Y, 'd', n, 0.0, Mi, 'd', l, s));         // M_i = Q_i^T Y_i
+        nb = i + 1;
+        if (i == m - 1) break;
+        CU(cudaMemcpyAsync(hM.data(), Mi, sizeof(double) * ll, cudaMemcpyDeviceToHost, s));
+        // r = Y_i - Q_i M_i - Q_{i-1} W_{i-1}^T, then re-orthogonalised against Q_1 .. Q_i twice
+        CU(gemm('N', 'N', n, l, l, -1.0, Qi, 'd', n, Mi, 'd', l, 1.0, Y, 'd', n, s));
+        if (i > 0)
+            CU(gemm('N', 'T', n, l, l, -1.0, Q + (size_t)(i - 1) * l * n, 'd', n, blocks + (m + i - 1) * ll, 'd', l,
+                    1.0, Y, 'd', n, s));
+        const int c = (i + 1) * l;
+        for (int pass = 0; pass < 2; ++pass) {
+            CU(gemm('T', 'N', c, l, n, 1.0, Q, 'd', n, Y, 'd', n, 0.0, H, 'd', c, s));
+            CU(gemm('N', 'N', n, l, c, -1.0, Q, 'd', n, H, 'd', c, 1.0, Y, 'd', n, s));
+        }
+        // Q_{i+1} W_i = r: CholeskyQR of a copy of r, then W_i = Q_{i+1}^T r (upper triangular,
+        // positive diagonal: the product of the passes' factors)
+        double *Qn = Q + (size_t)(i + 1) * l * n;
+        double *Wi = blocks + (m + i) * ll;
+        CU(cudaMemcpyAsync(Qn, Y, sizeof(double) * (size_t)n * l, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 8, s));
+        TRY(cholqr64(ctx, Qn, l, 3, 0));
+        CU(gemm('T', 'N', l, l, n, 1.0, Qn, 'd', n, Y, 'd', n, 0.0, Wi, 'd', l, s));
+        int h[5] = {0, 0, 0, 0, 0};
+        CU(cudaMemcpyAsync(h, ctx->info, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(hW.data(), Wi, sizeof(double) * ll, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        for (int64_t e = 0; e < ll; ++e) scale = fmax(scale, fabs(hM[e]));
+        bool lost = h[0] || h[1] || h[2] || h[3] || h[4];
+        for (int j = 0; j < l && !lost; ++j) lost = !(fabs(hW[j + (int64_t)j * l]) > 1e-12 * scale);
+        if (lost) break;   // the residual block lost rank: the block Krylov space is invariant
+    }
+    const int K = nb * l;
+    CU(block_tridiag_fill(nb, l, m, blocks, ctx->Km, s));
+    TRY(small_eig(ctx, K, "riot_varbl"));
+    // U = Q Z, dv = -U diag(1 / (1 + lambda)) U^T g
+    CU(gemm('N', 'N', n, K, K, 1.0, Q, 'd', n, ctx->Z, 'd', K, 0.0, ctx->U, 'd', n, s));
+    CU(gemm('T', 'N', K, 1, n, 1.0, ctx->U, 'd', n, ctx->g, 'd', n, 0.0, ctx->cvec, 'd', K, s));
+    CU(div_one_plus(K, ctx->cvec, ctx->lam, s));
+    CU(gemm('N', 'N', n, 1, K, -1.0, ctx->U, 'd', n, ctx->cvec, 'd', K, 0.0, ctx->dv, 'd', n, s));
+    if (dv_dev) CU(cudaMemcpyAsync(dv_dev, ctx->dv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (theta_out) CU(cudaMemcpyAsync(theta_out, ctx->lam, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (blocks_used) *blocks_used = nb;
     return RIOT_OK;
 }
 

@@ -292,6 +292,9 @@ cudaError_t lanczos_resid(int64_t n, const double *w, const double *q, const dou
 cudaError_t normalize_by(int64_t n, const double *r, const double *rr, double *q, cudaStream_t s);
 cudaError_t tridiag_fill(int m, const double *alpha, const double *beta, double *T, cudaStream_t s);
 cudaError_t div_one_plus(int m, double *c, const double *theta, cudaStream_t s);
+// block Lanczos (Algorithm 2): T (nb l square, ld nb l) from the blocks M_i (at blocks + i l^2)
+// and W_i (at blocks + (mcap + i) l^2), each l x l column-major
+cudaError_t block_tridiag_fill(int nb, int l, int mcap, const double *blocks, double *T, cudaStream_t s);
 // Y = a Y (+ W) column by column (n rows of ncols columns at ld), float or double
 cudaError_t scale_add_cols(int64_t n, int ncols, int64_t ld, double a, void *Y, const void *W, int is_double,
                            cudaStream_t s);

@@ -1085,6 +1085,38 @@ cudaError_t tridiag_fill(int m, const double *alpha, const double *beta, double 
     return cudaGetLastError();
 }
 
+// T (nb l x nb l, ld nb l) block tridiagonal from l x l blocks (column-major, ld l): diagonal
+// block i = (M_i + M_i^T) / 2 with M_i at blocks + i l^2, block (i + 1, i) = W_i and block
+// (i, i + 1) = W_i^T with W_i at blocks + (mcap + i) l^2
+__global__ void block_tridiag_fill_kernel(int nb, int l, int mcap, const double *blocks, double *T)
+{
+    const int K = nb * l;
+    const int64_t total = (int64_t)K * K;
+    const int64_t ll = (int64_t)l * l;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % K), c = (int)(e / K);
+        const int bi = r / l, bj = c / l, ri = r - bi * l, cj = c - bj * l;
+        double v = 0.0;
+        if (bi == bj) {
+            const double *M = blocks + bi * ll;
+            v = 0.5 * (M[ri + (int64_t)cj * l] + M[cj + (int64_t)ri * l]);
+        } else if (bi == bj + 1) {
+            v = blocks[(mcap + bj) * ll + ri + (int64_t)cj * l];
+        } else if (bj == bi + 1) {
+            v = blocks[(mcap + bi) * ll + cj + (int64_t)ri * l];
+        }
+        T[e] = v;
+    }
+}
+
+cudaError_t block_tridiag_fill(int nb, int l, int mcap, const double *blocks, double *T, cudaStream_t s)
+{
+    if (nb < 1 || l < 1) return cudaSuccess;
+    count_launch();
+    block_tridiag_fill_kernel<<<128, 256, 0, s>>>(nb, l, mcap, blocks, T);
+    return cudaGetLastError();
+}
+
 // c_i <- c_i / (1 + theta_i)
 __global__ void div_one_plus_kernel(int m, double *c, const double *theta)
 {

@@ -117,6 +117,8 @@ def load():
     L.riot_varcg.restype = c_int32
     L.riot_tc_gram.argtypes = [c_int32, c_int32, vp, c_int64, vp, c_int64, vp]
     L.riot_tc_gram.restype = c_int32
+    L.riot_varbl.argtypes = [vp, c_int32, c_int32, vp, vp, POINTER(c_double), POINTER(c_int32)]
+    L.riot_varbl.restype = c_int32
     L.riot_precond_enable.argtypes = [vp, c_int32, c_int32]
     L.riot_precond_enable.restype = c_int32
     L.riot_precond_push.argtypes = [vp, c_int32]
@@ -475,6 +477,16 @@ def riot_rsvd_proposal(ctx, k, q, P, m, rho_max=1e-2, sketch_stream=0):
            load().riot_rsvd_proposal(ctx, int(k), int(q), int(sketch_stream), _ptr(P), int(m), float(rho_max), lam,
                                      ctypes.byref(rho), ctypes.byref(used)))
     return np.array(lam[:]), rho.value, used.value
+
+
+def riot_varbl(ctx, l, m, B0, dv=None):
+    """Algorithm 2 from the gradient samples B0, an (l, n) row-major FP64 device tensor (row j =
+    sample j).  Returns (Ritz values descending, blocks used)."""
+    _need_contiguous(B0, dv)
+    theta = (c_double * (l * m))()
+    nb = c_int32(0)
+    _check(ctx, "riot_varbl", load().riot_varbl(ctx, int(l), int(m), _ptr(B0), _ptr(dv), theta, ctypes.byref(nb)))
+    return np.array(theta[: l * nb.value]), nb.value
 
 
 def riot_precond_enable(ctx, max_cols, rotation=True):
