@@ -72,6 +72,18 @@ def dist_env():
     return rank, world, local
 
 
+def job_value(ms_local, units_per_step, world, pg=None, device=None):
+    """Whole-job step time and throughput over independent replicas: the step time is the
+    maximum over ranks, and every rank processed units_per_step per step."""
+    ms = float(ms_local)
+    if pg is not None and world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_step / (ms * 1e-3)
+
+
 def band_width(n, ell):
     """Number of taps of the banded Gaussian square-root kernel (same rule as the library)."""
     d = np.arange(n, dtype=np.float64)
@@ -556,13 +568,8 @@ def main():
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = R.riot_kernel_launches() - launches0
-    ms = statistics.mean(times)
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
     hvps_per_step = (q + 1) * k
-    value = world * hvps_per_step / (ms * 1e-3)
+    ms, value = job_value(statistics.mean(times), hvps_per_step, world, pg, dev)
 
     ph = {key: statistics.mean(p_[key] for p_ in phases) for key in phases[0]}
     hvp_launch_ms = ph["hvp"] / (q + 1)

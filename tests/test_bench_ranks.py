@@ -1,0 +1,61 @@
+"""The benchmark's multi-rank host logic on CPU (gloo, two processes): the step
+time is the maximum over ranks and the value counts every rank's products; the
+reference arm runs on rank 0 only.  No GPU is used."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import json, os, sys
+sys.path.insert(0, sys.argv[1])
+import torch.distributed as dist
+import bench
+dist.init_process_group("gloo")
+rank, world, _ = bench.dist_env()
+ms, value = bench.job_value(10.0 * (rank + 1), 1024, world, dist, "cpu")
+print(json.dumps({"rank": rank, "ms": ms, "value": value}))
+dist.destroy_process_group()
+"""
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_job_value_takes_the_slowest_rank_over_gloo():
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                   MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", CHILD, ROOT], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=120)
+        assert p.returncode == 0, err
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    for o in outs:
+        assert o["ms"] == 20.0
+        assert abs(o["value"] - 2 * 1024 / 0.020) < 1e-6
+
+
+def test_job_value_single_rank():
+    sys.path.insert(0, ROOT)
+    import bench
+    ms, value = bench.job_value(12.5, 1024, 1)
+    assert ms == 12.5 and abs(value - 1024 / 0.0125) < 1e-9
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
