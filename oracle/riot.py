@@ -461,6 +461,55 @@ def outer_step_precond(prob, x, v, Omega, pc, q=0, exact_rr=False, rotation=Fals
             "x_next": x + prob.L @ dv, "v_next": v + dv, "info": info}
 
 
+# --- RIOT-PSAS: the observation-space dual (Appendix, Algorithm 4) --------------------------
+
+def dual_hvp(prob, traj, W):
+    """A_dual W = L_{R^-1} H B H^T L_{R^-1}^T W for the columns of W (p, m) (Algorithm 4), with
+    R = diag(sigma_o^2) so L_{R^-1} = diag(1 / sigma_o), and B = L L^T: per column one adjoint
+    integration from the observation-space forcing, L L^T, one tangent-linear integration."""
+    W = np.atleast_2d(np.asarray(W, dtype=np.float64).T).T
+    s = 1.0 / prob.sigma_o
+    out = np.empty_like(W)
+    for j in range(W.shape[1]):
+        lam0 = l96.ad(traj, obs_forcing(prob, s * W[:, j]), prob.dt, prob.F)
+        z = prob.L @ (prob.L.T @ lam0)
+        out[:, j] = s * observe(prob, l96.tl(traj, z, prob.dt, prob.F))
+    return out
+
+
+def psas_outer_step(prob, x, Omega, q=0, exact_rr=False):
+    """One cycle of Algorithm 4 (RIOT-PSAS).  d = y - H(x_{k-1}) (the dual's sign),
+    b' = H_{k-1}(x_b - x_{k-1}) (tangent linear), the randomized eigendecomposition of A_dual
+    (p x p) on the sketch Omega (p, m) exactly as in Algorithm 3 (K Q^T Omega = Q^T Y, or
+    K = Q^T A Q), and the adaptive weights
+        lambda_m > 1: dw = S U diag(1/(1+lambda)) U^T S (d - b')              (LRA)
+        otherwise:    dw = S (I - U diag(lambda/(1+lambda)) U^T) S (d - b')   (LRU)
+    with S = L_{R^-1} = diag(1 / sigma_o).
+    Reading: the state is x_k = x_b + B H^T dw.  Linearised about x_{k-1}, the minimiser of the
+    cost is x_b + B H^T (H B H^T + R)^-1 (d - b'); the listing's x_{k-1} + B H^T dw adds
+    x_{k-1} - x_b twice from the second loop on (both agree at k = 1, where x_0 = x_b).
+    Returns a dict with J (at x), d, bprime, lam, U, dw, mode, x_next."""
+    traj = trajectory(prob, x)
+    d = prob.y - observe(prob, traj)
+    J = 0.5 * float(np.sum(d * d * prob.rinv))
+    vb = np.linalg.solve(prob.L, x - prob.x_b)
+    J += 0.5 * float(vb @ vb)
+    bprime = observe(prob, l96.tl(traj, prob.x_b - x, prob.dt, prob.F))
+    lam, U, info = rsvd(prob, traj, Omega, q=q, exact_rr=exact_rr, apply=lambda W: dual_hvp(prob, traj, W))
+    s = 1.0 / prob.sigma_o
+    r = s * (d - bprime)
+    c = U.T @ r
+    if lam[-1] > 1.0:
+        w, mode = U @ (c / (1.0 + lam)), 0
+    else:
+        w, mode = r - U @ (c * lam / (1.0 + lam)), 1
+    dw = s * w
+    lam0 = l96.ad(traj, obs_forcing(prob, dw), prob.dt, prob.F)
+    x_next = prob.x_b + prob.L @ (prob.L.T @ lam0)
+    return {"traj": traj, "J": J, "d": d, "bprime": bprime, "lam": lam, "U": U, "dw": dw, "mode": mode,
+            "x_next": x_next, "info": info}
+
+
 def quadratic_cost(prob, traj, d, v, dv):
     """Inner-loop quadratic cost J~(dv) = 1/2||R^-1/2(d + H M L dv)||^2 + 1/2||v + dv||^2
     (Eq. 3 with Algorithm 3's sign of d and accumulated control v)."""
