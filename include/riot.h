@@ -430,6 +430,32 @@ riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_o
 riot_status riot_varbl(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev, double *dv_dev, double *theta_out,
                        int32_t *blocks_used);
 
+/* RIOT-PSAS (Appendix, Algorithm 4): one cycle of the observation-space dual
+ * at the state of the last riot_outer_begin (Lorenz-96 contexts).  With
+ * S = L_{R^-1} = diag(1/sigma_o) (R diagonal) it decomposes the p x p
+ * A_dual = S H B H^T S by the randomized steps of Algorithm 3 on a p x m
+ * sketch (Omega_dev: p x m FP64 column-major on the device, or NULL to draw it
+ * from sketch_stream; q power iterations; K from K Q^T W = Q^T Y, or
+ * K = Q^T A_dual Q when the context was set up with exact_rr), then forms
+ * the adaptive weights (lambda_m > 1: LRA, else LRU)
+ *     dw = S U diag(1/(1+lambda)) U^T S (d - b')      or
+ *     dw = S (I - U diag(lambda/(1+lambda)) U^T) S (d - b'),
+ * d = y - H(x), b' = H (x_b - x) (tangent linear), and sets
+ * x = x_b + B H^T dw, i.e. v = L^T H^T dw in the context's x = x_b + L v
+ * (the listing writes x_{k-1} + B H^T dw, which counts x_{k-1} - x_b twice
+ * from the second cycle on; both agree in the first).  Each product by
+ * A_dual is one adjoint launch from the forcing S w, L L^T, and one
+ * tangent-linear launch over all m columns, in FP64 on either precision.
+ * lambda_out (host, m, may be NULL): eigenvalues of A_dual, descending;
+ * dv_dev (n, may be NULL): the change of v; mode_out (may be NULL): 0 LRA,
+ * 1 LRU.  RIOT_ESTATE before riot_outer_begin or with preconditioner
+ * factors; RIOT_EINVAL for another model, m outside [1, min(kmax, p)] or q
+ * outside [0, 64]; RIOT_ENOTSPD if the basis or the solve for K fails.
+ * Allocates its observation-space workspace (6 p kmax doubles) at the first
+ * call.  Synchronises.  Call riot_outer_begin() before the next cycle. */
+riot_status riot_psas(riot_ctx *ctx, int32_t m, int32_t q, int64_t sketch_stream, const double *Omega_dev,
+                      double *lambda_out, double *dv_dev, int32_t *mode_out);
+
 /* Spectral preconditioner with rotation (Section 2.2 "Preconditioning", Eq. 7;
  * Algorithm 3 with precond = true).  After outer loop j has run riot_rsvd and
  * riot_increment, riot_precond_push(ctx, m) adds the factor

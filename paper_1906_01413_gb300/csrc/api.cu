@@ -71,6 +71,11 @@ struct riot_ctx {
     double *pcB = nullptr;   // rotation: orthonormal basis of [P_1 V_1, ..., P_{k-1} V_{k-1}] (rot_cols columns)
     float *pcV32 = nullptr, *pcB32 = nullptr, *pcT32 = nullptr;   // FP32 copies (mixed precision)
     std::vector<void *> pc_allocs;
+    // RIOT-PSAS (riot_psas), allocated at its first call: observation-space blocks (p x kmax
+    // FP64: sketch / basis input, products, basis, Ritz vectors, adjoint forcing, TL output),
+    // S = diag(1 / sigma_o) and sigma_o, and p-vectors
+    double *psW = nullptr, *psY = nullptr, *psQ = nullptr, *psU = nullptr, *psF = nullptr, *psR = nullptr;
+    double *psS = nullptr, *psSig = nullptr, *psr = nullptr, *psw = nullptr, *psc = nullptr;
     // timing
     cudaEvent_t ev[32];
     int nev = 0;
@@ -234,9 +239,11 @@ cudaError_t bsqrt(riot_ctx *ctx, const double *in, double *out, int transpose, i
 // unshifted CholeskyQR passes.  Each pass first scales the columns to unit
 // norm (the Gram is scaled alike), which removes the spread of column norms
 // that power-iteration blocks of strongly unstable windows carry.
-riot_status cholqr64(riot_ctx *ctx, double *X, int k, int shifted, int info_base)
+// X (rows x k FP64, ld rows; rows = n when < 0) <- orthonormal basis of its columns:
+// `shifted` shifted, equilibrated CholeskyQR passes, then two plain ones
+riot_status cholqr64(riot_ctx *ctx, double *X, int k, int shifted, int info_base, int rows = -1)
 {
-    const int n = ctx->n;
+    const int n = rows < 0 ? ctx->n : rows;
     for (int pass = 0; pass < shifted + 2; ++pass) {
         CU(gram_lower(n, k, X, 'd', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
         CU(equilibrate(ctx->G, k, k, X, 'd', n, n, ctx->cvec, ctx->s));
@@ -2183,6 +2190,144 @@ riot_status riot_varbl(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev
     if (theta_out) CU(cudaMemcpyAsync(theta_out, ctx->lam, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (blocks_used) *blocks_used = nb;
+    return RIOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// RIOT-PSAS (Appendix, Algorithm 4): the randomized eigendecomposition in observation space.
+// ---------------------------------------------------------------------------
+static riot_status psas_alloc(riot_ctx *ctx)
+{
+    if (ctx->psW) return RIOT_OK;
+    const size_t p = (size_t)ctx->p, pk = p * (size_t)ctx->kmax;
+    riot_status st;
+    if ((st = dalloc(ctx, &ctx->psW, pk)) || (st = dalloc(ctx, &ctx->psY, pk)) || (st = dalloc(ctx, &ctx->psQ, pk)) ||
+        (st = dalloc(ctx, &ctx->psU, pk)) || (st = dalloc(ctx, &ctx->psF, pk)) || (st = dalloc(ctx, &ctx->psR, pk)) ||
+        (st = dalloc(ctx, &ctx->psS, p)) || (st = dalloc(ctx, &ctx->psSig, p)) || (st = dalloc(ctx, &ctx->psr, p)) ||
+        (st = dalloc(ctx, &ctx->psw, p)) || (st = dalloc(ctx, &ctx->psc, (size_t)ctx->kmax))) {
+        ctx->psW = nullptr;
+        return st;
+    }
+    // S = diag(1 / sigma_o) and sigma_o from R^-1 = diag(1 / sigma_o^2)
+    std::vector<double> ri(p), sv(p), sg(p);
+    CU(cudaMemcpyAsync(ri.data(), ctx->rinv64, sizeof(double) * p, cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    for (size_t i = 0; i < p; ++i) {
+        sv[i] = sqrt(ri[i]);
+        sg[i] = 1.0 / sv[i];
+    }
+    CU(cudaMemcpyAsync(ctx->psS, sv.data(), sizeof(double) * p, cudaMemcpyHostToDevice, ctx->s));
+    CU(cudaMemcpyAsync(ctx->psSig, sg.data(), sizeof(double) * p, cudaMemcpyHostToDevice, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    return RIOT_OK;
+}
+
+// Y = A_dual W = S H B H^T S W for m <= kmax observation-space columns (ld p), FP64:
+// the adjoint from the forcing S w and L^T (Hessian kernel mode 1), then L, the tangent
+// linear model and R^-1 H (mode 2), then sigma_o (S R = diag(sigma_o)).  ctx->U holds the
+// n x m intermediate L^T H^T S W.
+static riot_status dual_hvp(riot_ctx *ctx, const double *W, double *Y, int m)
+{
+    const int n = ctx->n, p = ctx->p;
+    cudaStream_t s = ctx->s;
+    CU(cudaMemcpyAsync(ctx->psF, W, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
+    CU(scale_rows(p, m, p, ctx->psS, ctx->psF, 1, s));
+    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->U, n, m, 0, ctx->psF, 1, s));
+    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, ctx->U, nullptr, n, m, 0, ctx->psR, 2, s));
+    CU(cudaMemcpyAsync(Y, ctx->psR, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
+    CU(scale_rows(p, m, p, ctx->psSig, Y, 1, s));
+    return RIOT_OK;
+}
+
+riot_status riot_psas(riot_ctx *ctx, int32_t m, int32_t q, int64_t sketch_stream, const double *Omega_dev,
+                      double *lambda_out, double *dv_dev, int32_t *mode_out)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (ctx->model != RIOT_MODEL_L96) return fail(ctx, RIOT_EINVAL, "riot_psas: Lorenz-96 contexts only");
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_psas before riot_outer_begin");
+    if (m < 1 || m > ctx->kmax || m > ctx->p)
+        return fail(ctx, RIOT_EINVAL, "m = %d outside [1, min(kmax = %d, p = %d)]", m, ctx->kmax, ctx->p);
+    if (q < 0 || q > 64) return fail(ctx, RIOT_EINVAL, "q = %d outside [0, 64]", q);
+    if (!ctx->pc_m.empty()) return fail(ctx, RIOT_ESTATE, "riot_psas: Algorithm 4 runs without the spectral preconditioner");
+    CU(cudaSetDevice(ctx->dev));
+    TRY(psas_alloc(ctx));
+    const int n = ctx->n, p = ctx->p;
+    cudaStream_t s = ctx->s;
+    ctx->have_rsvd = 0;   // the primal Ritz pairs are not kept
+    ctx->pc_open = 0;
+    // r = S (d - b') with d = y - H(x) (the dual's sign; the context holds H(x) - y) and
+    // b' = H (x_b - x) = H L (-v): the tangent linear model of -v (mode 2 gives R^-1 H L (-v))
+    CU(cudaMemcpyAsync(ctx->tmp, ctx->v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CU(scal(n, -1.0, ctx->tmp, s));
+    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, ctx->tmp, nullptr, n, 1, 0, ctx->psR, 2, s));
+    CU(mul(p, ctx->psS, ctx->d, ctx->psr, s));                 // S (H(x) - y)
+    CU(mul(p, ctx->psSig, ctx->psR, ctx->psw, s));             // S b' = sigma_o (R^-1 b')
+    CU(axpby(p, -1.0, ctx->psw, -1.0, ctx->psr, s));           // r = -S (H(x) - y) - S b'
+    // sketch, products, power iterations, basis
+    CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 32, s));
+    if (Omega_dev)
+        CU(cudaMemcpyAsync(ctx->psW, Omega_dev, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
+    else
+        CU(normal_launch(ctx->seed, (uint32_t)sketch_stream, p, m, p, 1, ctx->psW, s));
+    TRY(dual_hvp(ctx, ctx->psW, ctx->psY, m));
+    for (int it = 0; it < q; ++it) {
+        CU(cudaMemcpyAsync(ctx->psW, ctx->psY, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
+        TRY(cholqr64(ctx, ctx->psW, m, 3, 0, p));
+        TRY(dual_hvp(ctx, ctx->psW, ctx->psY, m));
+    }
+    CU(cudaMemcpyAsync(ctx->psQ, ctx->psY, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
+    TRY(cholqr64(ctx, ctx->psQ, m, 3, 5, p));
+    TRY(check_cholesky(ctx, 0, 10, "riot_psas"));
+    // K: Q^T A Q (exact_rr) or K (Q^T W) = Q^T Y through K (M M^T) = N M^T, symmetrised
+    if (ctx->exact_rr) {
+        TRY(dual_hvp(ctx, ctx->psQ, ctx->psY, m));
+        CU(gemm('T', 'N', m, m, p, 1.0, ctx->psQ, 'd', p, ctx->psY, 'd', p, 0.0, ctx->Km, 'd', m, s));
+    } else {
+        CU(gemm('T', 'N', m, m, p, 1.0, ctx->psQ, 'd', p, ctx->psW, 'd', p, 0.0, ctx->Mm, 'd', m, s));
+        CU(gemm('T', 'N', m, m, p, 1.0, ctx->psQ, 'd', p, ctx->psY, 'd', p, 0.0, ctx->Nm, 'd', m, s));
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            CU(gemm('N', 'T', m, m, m, 1.0, ctx->Mm, 'd', m, ctx->Mm, 'd', m, 0.0, ctx->G, 'd', m, s));
+            CU(gemm('N', 'T', m, m, m, 1.0, ctx->Nm, 'd', m, ctx->Mm, 'd', m, 0.0, ctx->Km, 'd', m, s));
+            CU(cudaMemsetAsync(ctx->info + 10, 0, sizeof(int), s));
+            CU(cholesky(ctx->G, m, m, attempt ? 8.0 * m * ldexp(1.0, -53) : 0.0, ctx->info + 10, ctx->gws, s));
+            CU(trsm_right_lt(ctx->Km, m, m, m, ctx->G, m, s, ctx->gws));
+            CU(trsm_right_l(ctx->Km, m, m, m, ctx->G, m, s, ctx->gws));
+            int i10 = 0;
+            CU(cudaMemcpyAsync(&i10, ctx->info + 10, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            if (i10 == 0) break;
+            if (attempt) return fail(ctx, RIOT_ENOTSPD, "riot_psas: the solve for K failed (Q^T W singular)");
+        }
+    }
+    CU(symmetrize(ctx->Km, m, m, s));
+    TRY(small_eig(ctx, m, "riot_psas"));
+    CU(gemm('N', 'N', p, m, m, 1.0, ctx->psQ, 'd', p, ctx->Z, 'd', m, 0.0, ctx->psU, 'd', p, s));
+    CU(fix_col_signs(ctx->psU, p, m, p, s));
+    // adaptive weights: LRA w = U diag(1/(1+lambda)) U^T r, LRU w = r - U diag(lambda/(1+lambda)) U^T r
+    CU(gemm('T', 'N', m, 1, p, 1.0, ctx->psU, 'd', p, ctx->psr, 'd', p, 0.0, ctx->psc, 'd', m, s));
+    CU(cov_coef(ctx->lam, m, ctx->cvec, ctx->info + 14, s));
+    CU(mul(m, ctx->cvec, ctx->psc, ctx->psc, s));
+    int mode = 0;
+    CU(cudaMemcpyAsync(&mode, ctx->info + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (mode == 0) {
+        CU(gemm('N', 'N', p, 1, m, 1.0, ctx->psU, 'd', p, ctx->psc, 'd', m, 0.0, ctx->psw, 'd', p, s));
+    } else {
+        CU(cudaMemcpyAsync(ctx->psw, ctx->psr, sizeof(double) * p, cudaMemcpyDeviceToDevice, s));
+        CU(gemm('N', 'N', p, 1, m, -1.0, ctx->psU, 'd', p, ctx->psc, 'd', m, 1.0, ctx->psw, 'd', p, s));
+    }
+    CU(mul(p, ctx->psS, ctx->psw, ctx->psF, s));               // dw = S w
+    // x = x_b + B H^T dw = x_b + L v with v = L^T H^T dw (mode 1); dv = v_new - v
+    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->tmp, n, 1, 0, ctx->psF, 1, s));
+    CU(cudaMemcpyAsync(ctx->dv, ctx->tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CU(axpby(n, -1.0, ctx->v, 1.0, ctx->dv, s));
+    CU(cudaMemcpyAsync(ctx->v, ctx->tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CU(bsqrt(ctx, ctx->dv, ctx->tmp, 0, 1));
+    CU(axpby(n, 1.0, ctx->tmp, 1.0, ctx->x, s));
+    if (dv_dev) CU(cudaMemcpyAsync(dv_dev, ctx->dv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (lambda_out) CU(cudaMemcpyAsync(lambda_out, ctx->lam, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (mode_out) *mode_out = mode;
     return RIOT_OK;
 }
 

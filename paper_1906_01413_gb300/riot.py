@@ -117,6 +117,8 @@ def load():
     L.riot_varcg.restype = c_int32
     L.riot_tc_gram.argtypes = [c_int32, c_int32, vp, c_int64, vp, c_int64, vp]
     L.riot_tc_gram.restype = c_int32
+    L.riot_psas.argtypes = [vp, c_int32, c_int32, c_int64, vp, POINTER(c_double), vp, POINTER(c_int32)]
+    L.riot_psas.restype = c_int32
     L.riot_varbl.argtypes = [vp, c_int32, c_int32, vp, vp, POINTER(c_double), POINTER(c_int32)]
     L.riot_varbl.restype = c_int32
     L.riot_precond_enable.argtypes = [vp, c_int32, c_int32]
@@ -477,6 +479,17 @@ def riot_rsvd_proposal(ctx, k, q, P, m, rho_max=1e-2, sketch_stream=0):
            load().riot_rsvd_proposal(ctx, int(k), int(q), int(sketch_stream), _ptr(P), int(m), float(rho_max), lam,
                                      ctypes.byref(rho), ctypes.byref(used)))
     return np.array(lam[:]), rho.value, used.value
+
+
+def riot_psas(ctx, m, q=0, sketch_stream=0, Omega=None, dv=None):
+    """One RIOT-PSAS cycle; Omega (m, p) row-major FP64 device tensor (row j = sketch column j)
+    or None.  Returns (eigenvalues of the dual Hessian descending, mode)."""
+    _need_contiguous(Omega, dv)
+    lam = (c_double * m)()
+    mode = c_int32(-1)
+    _check(ctx, "riot_psas", load().riot_psas(ctx, int(m), int(q), int(sketch_stream), _ptr(Omega), lam, _ptr(dv),
+                                              ctypes.byref(mode)))
+    return np.array(lam[:]), mode.value
 
 
 def riot_varbl(ctx, l, m, B0, dv=None):
