@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batch of 96 windows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned sketch proposal leg")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned inner-loop leg")
-    ap.add_argument("--only", choices=["bc", "batch", "learned"], default=None,
+    ap.add_argument("--only", choices=["bc", "batch", "learned", "varcg", "varbl", "psas"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling)")
     ap.add_argument("--bc-cols", type=int, default=128, help="sketch columns per tracer Hessian call")
     ap.add_argument("--profile", action="store_true",
@@ -210,6 +210,52 @@ def bench_precond(R, torch, ctx, xb, cfg, flush, dv, warmup, steps, plain_ms):
             "ms_per_step": ms, "value": (cfg.q + 1) * cfg.k / (ms * 1e-3), "unit": UNIT,
             "overhead_vs_plain": ms / plain_ms - 1.0, "phases_ms": ph, "push_ms": push_s * 1e3,
             "lambda1": float(lam2[0]), "mode": int(mode)}
+
+
+def bench_comparator(R, torch, dev, flush, which, warmup, steps):
+    """The paper's other inner loops on the large Lorenz-96 window (mixed-precision context):
+    varcg = Algorithm 1 with m = 64 (one Hessian product per iteration, sequential);
+    varbl = Algorithm 2 with l = 64 samples and m = 8 block steps (512 products; the starting
+    block is the gradient plus Gaussian columns: its content does not change the cost);
+    psas = Algorithm 4 with m = 512 sketch columns and q = 1 in observation space (p = 51 200).
+    Each step is one call, timed with CUDA events after an L2 flush."""
+    cfg = configs.l96_large()
+    ctx, xb, p = build_problem(R, torch, cfg, dev, R.RIOT_PREC_MIXED, cfg.k)
+    R.riot_outer_begin(ctx.h, xb)
+    s = torch.cuda.current_stream()
+    n = cfg.n
+    if which == "varbl":
+        l, m = 64, 8
+        g = torch.empty(n, dtype=torch.float64, device=dev)
+        R.riot_get_state(ctx.h, g=g)
+        B0 = g[None, :] + torch.randn(l, n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(7)) \
+            * g.abs().mean()
+        B0 = B0.contiguous()
+    times, info = [], {}
+    for i in range(warmup + steps):
+        if which == "psas" and i:
+            R.riot_outer_begin(ctx.h, xb, torch.zeros_like(xb))
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        if which == "varcg":
+            theta, used = R.riot_varcg(ctx.h, 64)
+            info = {"m": used, "hvps": used, "theta1": float(theta.max())}
+        elif which == "varbl":
+            theta, nb = R.riot_varbl(ctx.h, l, m, B0)
+            info = {"l": l, "m": nb, "hvps": l * nb, "theta1": float(theta[0])}
+        else:
+            lam, mode = R.riot_psas(ctx.h, 512, 1, sketch_stream=configs.STREAM_SKETCH0)
+            info = {"m": 512, "q": 1, "p": int(p), "dual_products": 2 * 512, "lambda1": float(lam[0]), "mode": mode}
+        e1.record(s)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            times.append(e0.elapsed_time(e1))
+    ctx.close()
+    ms = statistics.mean(times)
+    units = info.get("hvps", info.get("dual_products", 0))
+    return {"leg": which, "workload": WORKLOAD, "ms_per_call": ms, "products_per_s": units / (ms * 1e-3), **info}
 
 
 def build_bc_problem(R, torch, cfg, dev, precision, kmax):
@@ -537,6 +583,8 @@ def main():
             torch.cuda.profiler.start()
         if args.only == "learned":
             out = bench_learned_sketch(R, torch, dev)
+        elif args.only in ("varcg", "varbl", "psas"):
+            out = bench_comparator(R, torch, dev, flush, args.only, args.warmup, max(1, args.steps))
         elif args.only == "bc":
             out = bench_bc_transport(R, torch, dev, flush, float(peaks.get("hbm_gbs", 6800.0)), ncols=args.bc_cols,
                                      reps=max(1, args.steps))
