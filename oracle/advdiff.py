@@ -416,3 +416,31 @@ def outer_step(prob, x, v, Omega, q=0, exact_rr=False):
     dv, mode = riot.increment(lam, U, g)
     return {"traj": traj, "J": J, "b": b, "g": g, "lam": lam, "U": U, "dv": dv, "mode": mode,
             "x_next": x + prob.Lop.apply(dv), "v_next": v + dv, "info": info}
+
+
+def dual_hvp(prob, traj, W):
+    """A_dual W = S H' B H'^T S W for the columns of W (p, m), S = diag(1 / sigma_o) (Appendix,
+    Algorithm 4): one adjoint run from the forcing S w, the source adjoint to the control,
+    B = L L^T, one tangent-linear run; vectorised over columns."""
+    W = np.atleast_2d(np.asarray(W, dtype=np.float64).T).T
+    s = 1.0 / prob.sigma_o
+    sb = run_adj(prob.m, prob.obs, (s[:, None] * W).T)                  # (m, nb, ny, nx)
+    z = prob.Lop.apply(prob.Lop.apply_t(_source_adj_to_control(prob, traj, sb)))
+    return s[:, None] * tl_obs(prob, traj, z).T
+
+
+def psas_outer_step(prob, x, Omega, q=0, exact_rr=False):
+    """One cycle of Algorithm 4 on the tracer problem: d = y - H(x), b' = H'(x_b - x), the
+    randomized eigendecomposition of A_dual on the sketch Omega (p, m), the adaptive weights,
+    x_next = x_b + B H'^T dw (the reading of the state update taken for the Lorenz-96 dual)."""
+    from . import riot
+    traj = trajectory(prob, x)
+    d = prob.y - traj["Hx"]
+    bprime = tl_obs(prob, traj, prob.x_b - x)[0]
+    lam, U, info = riot.rsvd(prob, traj, Omega, q=q, exact_rr=exact_rr,
+                             apply=lambda W: dual_hvp(prob, traj, W))
+    dw, mode = riot.psas_weights(lam, U, prob.sigma_o, d, bprime)
+    sb = run_adj(prob.m, prob.obs, dw[None, :])
+    x_next = prob.x_b + prob.Lop.apply(prob.Lop.apply_t(_source_adj_to_control(prob, traj, sb)))[0]
+    return {"traj": traj, "d": d, "bprime": bprime, "lam": lam, "U": U, "dw": dw, "mode": mode,
+            "x_next": x_next, "info": info}

@@ -477,14 +477,23 @@ def dual_hvp(prob, traj, W):
     return out
 
 
+def psas_weights(lam, U, sigma_o, d, bprime):
+    """Adaptive observation-space weights of Algorithm 4 with S = L_{R^-1} = diag(1 / sigma_o):
+        lambda_m > 1: dw = S U diag(1/(1+lambda)) U^T S (d - b')              (LRA, mode 0)
+        otherwise:    dw = S (I - U diag(lambda/(1+lambda)) U^T) S (d - b')   (LRU, mode 1)."""
+    s = 1.0 / sigma_o
+    r = s * (d - bprime)
+    c = U.T @ r
+    if lam[-1] > 1.0:
+        return s * (U @ (c / (1.0 + lam))), 0
+    return s * (r - U @ (c * lam / (1.0 + lam))), 1
+
+
 def psas_outer_step(prob, x, Omega, q=0, exact_rr=False):
     """One cycle of Algorithm 4 (RIOT-PSAS).  d = y - H(x_{k-1}) (the dual's sign),
     b' = H_{k-1}(x_b - x_{k-1}) (tangent linear), the randomized eigendecomposition of A_dual
     (p x p) on the sketch Omega (p, m) exactly as in Algorithm 3 (K Q^T Omega = Q^T Y, or
-    K = Q^T A Q), and the adaptive weights
-        lambda_m > 1: dw = S U diag(1/(1+lambda)) U^T S (d - b')              (LRA)
-        otherwise:    dw = S (I - U diag(lambda/(1+lambda)) U^T) S (d - b')   (LRU)
-    with S = L_{R^-1} = diag(1 / sigma_o).
+    K = Q^T A Q), and the adaptive weights of psas_weights.
     Reading: the state is x_k = x_b + B H^T dw.  Linearised about x_{k-1}, the minimiser of the
     cost is x_b + B H^T (H B H^T + R)^-1 (d - b'); the listing's x_{k-1} + B H^T dw adds
     x_{k-1} - x_b twice from the second loop on (both agree at k = 1, where x_0 = x_b).
@@ -496,14 +505,7 @@ def psas_outer_step(prob, x, Omega, q=0, exact_rr=False):
     J += 0.5 * float(vb @ vb)
     bprime = observe(prob, l96.tl(traj, prob.x_b - x, prob.dt, prob.F))
     lam, U, info = rsvd(prob, traj, Omega, q=q, exact_rr=exact_rr, apply=lambda W: dual_hvp(prob, traj, W))
-    s = 1.0 / prob.sigma_o
-    r = s * (d - bprime)
-    c = U.T @ r
-    if lam[-1] > 1.0:
-        w, mode = U @ (c / (1.0 + lam)), 0
-    else:
-        w, mode = r - U @ (c * lam / (1.0 + lam)), 1
-    dw = s * w
+    dw, mode = psas_weights(lam, U, prob.sigma_o, d, bprime)
     lam0 = l96.ad(traj, obs_forcing(prob, dw), prob.dt, prob.F)
     x_next = prob.x_b + prob.L @ (prob.L.T @ lam0)
     return {"traj": traj, "J": J, "d": d, "bprime": bprime, "lam": lam, "U": U, "dw": dw, "mode": mode,
