@@ -223,3 +223,50 @@ def test_outer_loop_reduces_cost_and_matches_gauss_newton(small):
     Js.append(riot.cost(p, riot.trajectory(p, x), v))
     assert Js[-1] < Js[0]
     assert Js[1] < Js[0]
+
+
+def test_range_finder_meets_the_gaussian_sketch_bound(small):
+    """Halko, Martinsson & Tropp (2011), Eq. (1.9): with a Gaussian sketch of k + p columns,
+    ||(I - Q Q^T) A|| <= [1 + 11 sqrt(k + p) sqrt(n)] sigma_{k+1} except with probability
+    at most 6 p^-p.  Eight seeded sketches with p = 6 (failure probability 1.3e-4 each)."""
+    cfg, prob, traj = small
+    A = riot.dense_hessian(prob, traj)
+    A = 0.5 * (A + A.T)
+    sv = np.sort(np.abs(np.linalg.eigvalsh(A)))[::-1]          # singular values of the PSD A
+    k, p = 6, 6
+    bound = (1.0 + 11.0 * np.sqrt(k + p) * np.sqrt(prob.n)) * sv[k]
+    for s in range(8):
+        Om = cfg.sketch(20 + s, k=k + p).T
+        _, _, info = riot.rsvd(prob, traj, Om, q=0)
+        Q = info["Q"]
+        err = np.linalg.norm(A - Q @ (Q.T @ A), 2)
+        assert err <= bound
+        assert err >= sv[k + p] * (1 - 1e-10)                 # no rank-(k+p) basis does better (Eckart-Young)
+
+
+def test_range_finder_error_decreases_with_nested_sketches(small):
+    """Section 2.2: more samples, smaller error.  With nested sketches the ranges are nested,
+    so the projection error cannot grow."""
+    cfg, prob, traj = small
+    A = riot.dense_hessian(prob, traj)
+    Om = cfg.sketch(30, k=24).T
+    errs = []
+    for k in (4, 8, 12, 16, 20, 24):
+        _, _, info = riot.rsvd(prob, traj, Om[:, :k], q=0)
+        Q = info["Q"]
+        errs.append(np.linalg.norm(A - Q @ (Q.T @ A), 2))
+    assert all(b <= a * (1 + 1e-10) for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-2 * errs[0]
+
+
+def test_rayleigh_ritz_values_interlace(small):
+    """K = Q^T A Q (exact_rr): lambda_i(A) >= theta_i >= lambda_{n-k+i}(A) (Cauchy)."""
+    cfg, prob, traj = small
+    A = riot.dense_hessian(prob, traj)
+    ev = np.sort(np.linalg.eigvalsh(0.5 * (A + A.T)))[::-1]
+    n = prob.n
+    for k in (5, 12, 25):
+        theta, _, _ = riot.rsvd(prob, traj, cfg.sketch(40, k=k).T, q=1, exact_rr=True)
+        tol = 1e-10 * ev[0]
+        assert np.all(theta <= ev[:k] + tol)
+        assert np.all(theta >= ev[n - k:] - tol)
