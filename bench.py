@@ -506,52 +506,125 @@ def bench_learned_sketch(R, torch, dev, n_train=64, n_test=8, steps=500):
                                          "proposal_ungated": k_needed(mean["proposal_ungated"])}}
 
 
-def cpu_oracle_hvps(cfg, seconds, min_cols=2):
-    """FP64 CPU oracle Hessian-vector products on the same workload, single thread."""
+def _oracle_worker(root, workload, seconds, seed, barrier, out):
+    """One process of the CPU baseline: build the workload, wait for the others (so that all
+    time the same interval), run FP64 oracle Hessian-vector products for `seconds`."""
+    if root not in sys.path:
+        sys.path.insert(0, root)
     from oracle import problem, riot as orc
+    from synth import configs as cf
+    cfg = getattr(cf, workload)()
     prob = problem.build(cfg)
     traj = orc.trajectory(prob, prob.x_b)
+    rng = np.random.default_rng(seed)
+    try:
+        barrier.wait(timeout=600)
+    except Exception:
+        out.put((0, 0.0))
+        return
     t0 = time.perf_counter()
     done = 0
-    j = 0
     while True:
-        W = cfg.sketch(0, k=1, n=cfg.n)[:, :].T if j == 0 else np.random.default_rng(j).standard_normal((cfg.n, 1))
-        orc.hvp(prob, traj, W)
+        orc.hvp(prob, traj, rng.standard_normal((cfg.n, 1)))
         done += 1
-        j += 1
         el = time.perf_counter() - t0
-        if done >= min_cols and el >= seconds:
+        if el >= seconds:
             break
-    return done, el
+    out.put((done, el))
+
+
+def cpu_oracle_rate(seconds, workers, workload="l96_large"):
+    """FP64 CPU oracle Hessian-vector products per second of the workload over `workers`
+    spawned processes, each with one BLAS / OpenMP thread, timed together after a barrier.
+    Returns (products, seconds, products per second)."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        barrier, out = ctx.Barrier(workers), ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker, args=(ROOT, workload, seconds, 100 + w, barrier, out))
+                 for w in range(workers)]
+        for pr in procs:
+            pr.start()
+        res = [out.get(timeout=900) for _ in procs]
+        for pr in procs:
+            pr.join(timeout=60)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    done = sum(d for d, _ in res)
+    el = max(e for _, e in res)
+    rate = sum(d / e for d, e in res if e > 0)
+    return done, el, rate
+
+
+def _reference_worker(root, workload, cols, nsteps, seed, barrier, out):
+    """One process of the reference arm: per step, after a barrier with the other processes,
+    `cols` FP64 oracle Hessian-vector products of the workload; reports each step's time."""
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from oracle import problem, riot as orc
+    from synth import configs as cf
+    cfg = getattr(cf, workload)()
+    prob = problem.build(cfg)
+    traj = orc.trajectory(prob, prob.x_b)
+    W = np.random.default_rng(seed).standard_normal((cfg.n, cols))
+    for i in range(nsteps):
+        try:
+            barrier.wait(timeout=600)
+        except Exception:
+            out.put((i, -1.0))
+            return
+        t0 = time.perf_counter()
+        orc.hvp(prob, traj, W)
+        out.put((i, time.perf_counter() - t0))
 
 
 def reference_arm(args):
+    """The FP64 CPU oracle on the host cores: every step, each of nproc spawned processes (one
+    BLAS thread each) computes `cols` Hessian-vector products of the workload; the step time is
+    the slowest process's."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    import multiprocessing as mp
     from oracle import _clib
     _clib.build()
     cfg = configs.l96_large()
-    from oracle import problem, riot as orc
-    prob = problem.build(cfg)
-    traj = orc.trajectory(prob, prob.x_b)
-    cols = 4
-    Om = cfg.sketch(0, k=cols).T
-    times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        orc.hvp(prob, traj, Om)
-        if i >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    per = statistics.mean(times)
-    value = cols / per
+    cores = os.cpu_count() or 1
+    cols = 2
+    nsteps = args.warmup + args.steps
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_reference_worker, args=(ROOT, "l96_large", cols, nsteps, 200 + w, barrier, out))
+             for w in range(cores)]
+    for pr in procs:
+        pr.start()
+    step_max = [0.0] * nsteps
+    for _ in range(cores * nsteps):
+        i, t = out.get(timeout=1800)
+        if t < 0:
+            raise RuntimeError("reference arm: a worker process failed to start its step")
+        step_max[i] = max(step_max[i], t)
+    for pr in procs:
+        pr.join(timeout=60)
+    per = statistics.mean(step_max[args.warmup:]) if args.steps > 0 else float("nan")
+    value = cores * cols / per
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": cfg.n, "T": cfg.T, "k": cfg.k, "q": cfg.q},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d Hessian-vector products of the workload per step "
-                                       "(FP64 C TL/AD + numpy L, 1 thread)" % cols},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d Hessian-vector products of the workload per step: %d per process on %d "
+                                       "processes (FP64 C TL/AD + numpy L, one thread each)" % (cores * cols, cols,
+                                                                                              cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -718,10 +791,14 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import _clib
         _clib.build()
-        done, el = cpu_oracle_hvps(cfg, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "%d Hessian-vector products of the same window (FP64 C TL/AD + numpy L, "
-                                          "1 thread, %.1f s)" % (done, el)}
+        cores = os.cpu_count() or 1
+        d1, e1, r1 = cpu_oracle_rate(args.cpu_seconds / 2, 1)
+        dn, en, rn = cpu_oracle_rate(args.cpu_seconds / 2, cores)
+        line["cpu_baseline"] = {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d Hessian-vector products of the same window in %.1f s on %d processes "
+                                          "(FP64 C TL/AD + numpy L, one thread each, probes independent)"
+                                          % (dn, en, cores),
+                                "one_core": {"value": r1, "products": d1, "seconds": e1}}
     if rank == 0:
         print(json.dumps(line))
     if pg:

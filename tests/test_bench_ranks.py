@@ -59,3 +59,13 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_cpu_baseline_processes_time_together():
+    """The CPU baseline's spawned processes (one BLAS thread each) all finish a sample; the
+    rate adds their products per second."""
+    sys.path.insert(0, ROOT)
+    import bench
+    done, el, rate = bench.cpu_oracle_rate(0.3, 2, workload="l96_small")
+    assert done >= 2 and el >= 0.3
+    assert rate > 0 and rate >= done / el * 0.5
