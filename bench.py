@@ -533,6 +533,14 @@ def _oracle_worker(root, workload, seconds, seed, barrier, out):
     out.put((done, el))
 
 
+def host_cores():
+    """Cores this process may run on (the affinity set respects cpusets; cpu_count may not)."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def cpu_oracle_rate(seconds, workers, workload="l96_large"):
     """FP64 CPU oracle Hessian-vector products per second of the workload over `workers`
     spawned processes, each with one BLAS / OpenMP thread, timed together after a barrier.
@@ -596,7 +604,7 @@ def reference_arm(args):
     from oracle import _clib
     _clib.build()
     cfg = configs.l96_large()
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     cols = 2
     nsteps = args.warmup + args.steps
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -791,7 +799,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import _clib
         _clib.build()
-        cores = os.cpu_count() or 1
+        cores = host_cores()
         d1, e1, r1 = cpu_oracle_rate(args.cpu_seconds / 2, 1)
         dn, en, rn = cpu_oracle_rate(args.cpu_seconds / 2, cores)
         line["cpu_baseline"] = {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
