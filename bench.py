@@ -533,6 +533,25 @@ def _oracle_worker(root, workload, seconds, seed, barrier, out):
     out.put((done, el))
 
 
+def _collect(out, procs, count, limit_s):
+    """`count` results from the workers' queue; stops early (terminating the workers this
+    process started) when one of them exits with an error or the time limit passes."""
+    import queue
+    res, deadline = [], time.time() + limit_s
+    while len(res) < count:
+        try:
+            res.append(out.get(timeout=5))
+        except queue.Empty:
+            if any(pr.exitcode not in (None, 0) for pr in procs) or time.time() > deadline:
+                for pr in procs:
+                    if pr.is_alive():
+                        pr.terminate()
+                raise RuntimeError("a CPU oracle worker process failed or ran out of time")
+    for pr in procs:
+        pr.join(timeout=60)
+    return res
+
+
 def host_cores():
     """Cores this process may run on (the affinity set respects cpusets; cpu_count may not)."""
     try:
@@ -556,9 +575,7 @@ def cpu_oracle_rate(seconds, workers, workload="l96_large"):
                  for w in range(workers)]
         for pr in procs:
             pr.start()
-        res = [out.get(timeout=900) for _ in procs]
-        for pr in procs:
-            pr.join(timeout=60)
+        res = _collect(out, procs, workers, 900)
     finally:
         for k, v in saved.items():
             if v is None:
@@ -616,13 +633,10 @@ def reference_arm(args):
     for pr in procs:
         pr.start()
     step_max = [0.0] * nsteps
-    for _ in range(cores * nsteps):
-        i, t = out.get(timeout=1800)
+    for i, t in _collect(out, procs, cores * nsteps, 1800):
         if t < 0:
             raise RuntimeError("reference arm: a worker process failed to start its step")
         step_max[i] = max(step_max[i], t)
-    for pr in procs:
-        pr.join(timeout=60)
     per = statistics.mean(step_max[args.warmup:]) if args.steps > 0 else float("nan")
     value = cores * cols / per
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -800,13 +814,16 @@ def main():
         from oracle import _clib
         _clib.build()
         cores = host_cores()
-        d1, e1, r1 = cpu_oracle_rate(args.cpu_seconds / 2, 1)
-        dn, en, rn = cpu_oracle_rate(args.cpu_seconds / 2, cores)
-        line["cpu_baseline"] = {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "%d Hessian-vector products of the same window in %.1f s on %d processes "
-                                          "(FP64 C TL/AD + numpy L, one thread each, probes independent)"
-                                          % (dn, en, cores),
-                                "one_core": {"value": r1, "products": d1, "seconds": e1}}
+        try:
+            d1, e1, r1 = cpu_oracle_rate(args.cpu_seconds / 2, 1)
+            dn, en, rn = cpu_oracle_rate(args.cpu_seconds / 2, cores)
+            line["cpu_baseline"] = {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": "%d Hessian-vector products of the same window in %.1f s on %d "
+                                              "processes (FP64 C TL/AD + numpy L, one thread each, probes "
+                                              "independent)" % (dn, en, cores),
+                                    "one_core": {"value": r1, "products": d1, "seconds": e1}}
+        except Exception as e:   # the headline line must not be lost to the CPU side
+            line["cpu_baseline"] = {"error": str(e), "kind": "oracle", "cores": cores}
     if rank == 0:
         print(json.dumps(line))
     if pg:
