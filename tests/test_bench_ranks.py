@@ -1,11 +1,15 @@
-"""The benchmark's multi-rank host logic on CPU (gloo, two processes): the step
-time is the maximum over ranks and the value counts every rank's products; the
-reference arm runs on rank 0 only.  No GPU is used."""
+"""The benchmark's host logic on CPU: the multi-rank aggregation (gloo, two
+processes: the step time is the maximum over ranks and the value counts every
+rank's products), the reference arm on rank 0 only, and the spawned processes of
+the CPU oracle baseline (timed together; a failed worker is reported, not waited
+for).  No GPU is used."""
 import json
 import os
 import socket
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -69,3 +73,13 @@ def test_cpu_baseline_processes_time_together():
     done, el, rate = bench.cpu_oracle_rate(0.3, 2, workload="l96_small")
     assert done >= 2 and el >= 0.3
     assert rate > 0 and rate >= done / el * 0.5
+
+
+def test_cpu_baseline_reports_a_failed_worker_instead_of_waiting():
+    sys.path.insert(0, ROOT)
+    import time
+    import bench
+    t0 = time.time()
+    with pytest.raises(RuntimeError):
+        bench.cpu_oracle_rate(0.1, 2, workload="no_such_workload")
+    assert time.time() - t0 < 60
