@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batch of 96 windows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned sketch proposal leg")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned inner-loop leg")
+    ap.add_argument("--clock-log", default=None,
+                    help="CSV of the nvidia-smi clock samples taken during the timed steps (%%d: rank); "
+                         "default: a file in the temporary directory")
     ap.add_argument("--only", choices=["bc", "batch", "learned", "varcg", "varbl", "psas"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling)")
     ap.add_argument("--bc-cols", type=int, default=128, help="sketch columns per tracer Hessian call")
@@ -704,9 +707,11 @@ def main():
     torch.cuda.synchronize()
     launches0 = R.riot_kernel_launches()
     wall0 = time.perf_counter()
-    with ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
-                      if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv",
-                      local) as clk:
+    clock_log = (args.clock_log % rank) if args.clock_log and "%d" in args.clock_log else args.clock_log
+    if not clock_log:
+        import tempfile
+        clock_log = os.path.join(tempfile.gettempdir(), "riot_bench_clocks_rank%d.csv" % rank)
+    with ClockSampler(clock_log, local) as clk:
         times, phases, lam, mode = time_inner_loop(R, torch, ctx, cfg, args.steps, 0, flush, dv, args.profile)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0

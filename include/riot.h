@@ -340,7 +340,7 @@ void riot_batch_destroy(riot_batch *b);
  * Lorenz-96 background trajectory to m proposed sketch directions; it is
  * trained on leading Hessian eigenvectors that RIOT produced for other
  * windows.  This extends the randomized range finder of Section 2.2; the
- * Gaussian sketch of Algorithm 3 remains the fallback and the judge
+ * Gaussian sketch of Algorithm 3 remains the fallback that decides
  * (riot_rsvd_proposal).  Network: depth periodic conv layers of width ksize
  * (odd, <= 7), tanh on the hidden layers, channels c_in -> width -> ... ->
  * m_out.  Parameters are one FP32 vector: per layer W[C_out][C_in][ksize]

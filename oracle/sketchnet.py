@@ -5,7 +5,7 @@ trajectory of a Lorenz-96 window to m proposed sketch directions; it is
 trained on the leading Hessian eigenvectors that RIOT itself produced for
 other windows (the paper's sketch is purely Gaussian, Algorithm 3; this is an
 extension of its randomized range finder, Section 2.2, with the Gaussian
-sketch kept as fallback and judge).
+sketch kept as the fallback that decides).
 
 Network (all layers periodic in the ring index i, kernel width K = 2h + 1):
   h_0 = input (C_in, n)
