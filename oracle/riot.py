@@ -27,6 +27,15 @@ Readings where the paper is ambiguous (each is also listed in the design notes):
   * Eigenpairs are sorted by decreasing eigenvalue (Eq. 8 "decreasing
     eigenvalue order"), and each eigenvector's sign is fixed so that its
     largest-magnitude component is positive.
+  * Spectral preconditioning (Algorithm 3, precond): v stays the control of
+    x = x_b + L v; loop k solves for w with v = v_{k-1} + P_k w, so its gradient
+    is P_k^T (b + v_{k-1}) and v += P_k dw.  Factors are built from the pairs
+    with positive eigenvalue (the solve for K can return values below -1).
+  * Algorithm 2 (VarBL): the final increment acts on the unperturbed gradient
+    g = b + v; L_R = diag(sigma_o).
+  * Algorithm 4 (RIOT-PSAS): d = y - H(x) (the dual's own sign), the state is
+    x_k = x_b + B H^T dw (the listing's x_{k-1} + B H^T dw counts x_{k-1} - x_b
+    twice from the second cycle on).
 """
 from dataclasses import dataclass
 
