@@ -365,7 +365,8 @@ def outer_step(prob, x, v, Omega, q=0, exact_rr=False):
 
 class SpectralPreconditioner:
     """P_k = P'_0 P'_1 ... P'_{k-1} of Algorithm 3 with P'_0 = I and, for each finished outer
-    loop j, P'_j = I + V_j (Lt_j^{-1/2} - I) V_j^T (the spectral form of Eq. 7), where V_j
+    loop j, P'_j = I + V_j (Lt_j^{-1/2} - I) V_j^T (the spectral form of Eq. 7, with the
+    eigenvalues of I + A as Algorithm 3 writes them, not of A as Eq. 7 does), where V_j
     (orthonormal columns) and Lt_j = Lambda_j + I are the Ritz vectors and the eigenvalues of
     I + A_j estimated in loop j.  Since V_j^T V_j = I, P'_j^{-1} = I + V_j (Lt_j^{1/2} - I) V_j^T.
 
