@@ -66,3 +66,12 @@ def test_status_strings_without_a_device(lib):
     assert lib.riot_status_string(0) == b"ok"
     assert lib.riot_status_string(-1) == b"invalid argument"
     assert lib.riot_status_string(12345) == b"unknown status"
+
+
+def test_every_entry_point_has_a_typed_binding(lib):
+    """Each declared function has ctypes argtypes in the binding: without them Python ints
+    would be passed as 32-bit ints (64-bit strides, stream ids and sizes truncated)."""
+    from paper_1906_01413_gb300 import riot as R
+    L = R.load()
+    untyped = [nm for nm in _declared_functions() if getattr(L, nm).argtypes is None]
+    assert not untyped, untyped
