@@ -36,12 +36,14 @@ CASES = [("graded", 7, 1e-6, 1e6, 0), ("graded", 40, 1e-8, 1e4, 1), ("graded", 1
          ("graded", 700, 1e-3, 1e3, 6)]
 
 
-@pytest.mark.parametrize("kind,k,lo,hi,seed", CASES)
-@pytest.mark.parametrize("method", [0, 1])
-def test_symm_eig_against_lapack(gpu_lib, kind, k, lo, hi, seed, method):
+# the tridiagonal solver (method 0) on every case; parallel Jacobi (method 1), the slow
+# reference method, on the cases up to k = 128
+METHOD_CASES = [(m,) + c for m in (0, 1) for c in CASES if m == 0 or c[1] <= 128]
+
+
+@pytest.mark.parametrize("method,kind,k,lo,hi,seed", METHOD_CASES)
+def test_symm_eig_against_lapack(gpu_lib, method, kind, k, lo, hi, seed):
     R = gpu_lib
-    if method == 1 and k > 128:
-        pytest.skip("Jacobi is the slow reference method; small sizes only")
     K = _spd(k, lo, hi, seed, mult=(k // 4 if kind == "cluster" else None))
     K = 0.5 * (K + K.T)
     ref = np.sort(np.linalg.eigvalsh(K))[::-1]
