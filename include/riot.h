@@ -29,6 +29,12 @@
  *  - Sign conventions follow Algorithm 3: d = H(x) - y, dv = -(...)(b + v).
  *    Eigenvalues are those of A (not I + A), sorted in decreasing order.
  *  - One context is not safe to use from two host threads at once.
+ *  - Kernels with bounded device waits (the mixed-precision Hessian kernel's
+ *    stage copies, the tensor-core GEMMs) never hang: a wait that runs out
+ *    raises a flag and the kernel finishes with invalid results.  Every call
+ *    that launches such kernels clears the flag when it starts and reads it
+ *    before it returns (this synchronises), returning RIOT_ETIMEOUT; the
+ *    context stays usable and the next call starts clean.
  */
 #ifndef RIOT_H
 #define RIOT_H
@@ -139,6 +145,16 @@ typedef struct {
     const double *sigma_vec;
 } riot_bcov_desc;
 
+/* Caller-supplied device allocator (riot_options.dev_alloc / dev_free), so that a
+ * host framework's caching allocator serves the context's workspace.  dev_alloc
+ * returns `bytes` of device memory on the current device, aligned to at least 256
+ * bytes, usable in stream order on cuda_stream (the context's stream), or NULL;
+ * dev_free gives back a pointer dev_alloc returned, with the same size and stream.
+ * Both are called from the thread that calls riot_setup, riot_precond_enable,
+ * riot_psas (first call) and riot_destroy, and only there. */
+typedef void *(*riot_dev_alloc_fn)(size_t bytes, void *cuda_stream, void *user);
+typedef void (*riot_dev_free_fn)(void *ptr, size_t bytes, void *cuda_stream, void *user);
+
 typedef struct {
     int32_t precision;  /* RIOT_PREC_MIXED: FP32 TL/AD and FP32 block storage,
                            FP64 Gram/Cholesky, eigensolver and increment;
@@ -150,14 +166,20 @@ typedef struct {
                            tridiagonalisation + bisection + inverse iteration,
                            default) or RIOT_EIG_JACOBI (parallel cyclic Jacobi) */
     uint64_t seed;      /* key of the device-drawn Gaussian sketch            */
+    riot_dev_alloc_fn dev_alloc; /* NULL (with dev_free NULL): cudaMalloc / cudaFree */
+    riot_dev_free_fn dev_free;   /* given together with dev_alloc                 */
+    void *alloc_user;            /* passed through to dev_alloc / dev_free        */
 } riot_options;
 
 typedef struct riot_ctx riot_ctx;
 
 /* Create a context on the current CUDA device.  Copies the model, the
  * observations and the B descriptor to the device, builds L, and allocates
- * all workspace for kmax sketch columns.  cuda_stream is a cudaStream_t
- * (NULL = legacy default stream).  On failure *out is NULL. */
+ * all workspace for kmax sketch columns (through opt->dev_alloc when given;
+ * a NULL from it is RIOT_ENOMEM, a pointer not aligned to 256 bytes
+ * RIOT_EINVAL).  It also looks up, once per device, the device address of
+ * the static scratch array of riot_hessian_apply_noalloc.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  On failure *out is NULL. */
 riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_obs_desc *obs,
                        const riot_bcov_desc *B, const riot_options *opt, void *cuda_stream);
 
@@ -192,9 +214,8 @@ riot_status riot_hessian_apply(riot_ctx *ctx, const void *W_dev, void *Y_dev, in
  * RIOT_PREC_FP64) the call returns RIOT_EINVAL and does nothing.
  *  - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
  *  - The array belongs to the process, one copy per device that loaded the
- *    library, held until exit.  Its device address is looked up the first time
- *    this entry point runs on a device; make that first call before any stream
- *    capture.
+ *    library, held until exit.  Its device address is looked up once per
+ *    device by riot_setup, so this entry point itself does no lookup.
  *  - All calls share the array and it keeps the last call's contents.  Each
  *    call writes every residual it reads, so nothing needs clearing, but two
  *    calls that overlap on the GPU (other streams, other contexts on the same
@@ -281,6 +302,24 @@ riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6);
  * 0 = automatic.  A shape that does not fit the device falls back to the
  * automatic choice.  Used by the autotuner; results do not depend on it. */
 riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t ring_depth);
+
+/* Bound of every wait of the mixed-precision Hessian kernel on its stage copies,
+ * in polls of the copy's mbarrier: polls >= 0 sets it (0 gives up at once, so
+ * the next Hessian application reports RIOT_ETIMEOUT without a fault: this is
+ * how the timeout report is tested), polls < 0 restores the default (about
+ * 2^20 polls, well under a second).  Whatever the bound, a kernel whose wait
+ * ran out still waits with the default bound for every copy it started
+ * before its blocks exit. */
+riot_status riot_set_wait_limit(riot_ctx *ctx, int32_t polls);
+
+/* Inner-loop quadratic cost (Eq. 3 with Algorithm 3's sign of d)
+ *     J~(dv) = 1/2 ||R^-1/2 (d + H M L dv)||^2 + 1/2 ||v + dv||^2
+ * at the linearisation of the last riot_outer_begin (its trajectory, d and
+ * v), in FP64 on either precision: one FP64 tangent-linear integration of
+ * L dv.  dv_dev: n doubles (NULL: J~(0), the cost J of riot_outer_begin).
+ * The cost reduction of an increment is J~(0) - J~(dv).  *J_out (host) gets
+ * the value; this synchronises.  Requires riot_outer_begin. */
+riot_status riot_quadratic_cost(riot_ctx *ctx, const double *dv_dev, double *J_out);
 
 /* Number of Jacobi sweeps of the last successful riot_rsvd (-1: no context). */
 int32_t riot_rsvd_sweeps(const riot_ctx *ctx);

@@ -384,6 +384,14 @@ def tl_obs(prob, traj, dx):
     return run(prob.m, prob.obs, dE / prob.m.dz)
 
 
+def quadratic_cost(prob, traj, d, v, dv):
+    """Inner-loop quadratic cost of Eq. 3 with Algorithm 3's sign of d and the
+    accumulated control v: J~(dv) = 1/2 ||R^-1/2 (d + H' L dv)||^2 + 1/2 ||v + dv||^2,
+    H' the tangent-linear observation operator at the trajectory's emissions."""
+    r = d + tl_obs(prob, traj, prob.Lop.apply(np.asarray(dv)[None, :]))[0]
+    return 0.5 * float(np.sum(r * r * prob.rinv)) + 0.5 * float(np.dot(v + dv, v + dv))
+
+
 def build(cfg, with_truth=False):
     """Twin experiment: truth x = 0 (E = E_b), y = H(truth) + sigma_o eps with
     sigma_o = rel * max(y_true, floor_frac * median(y_true)), background

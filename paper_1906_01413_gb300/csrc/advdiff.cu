@@ -575,6 +575,26 @@ cudaError_t adv_outer(const AdvDev &m, const double *x, double *d, double *jo, d
     return sep_apply<double>(m, m.ebar64, n, b, n, 1, m.tmp64, s);
 }
 
+cudaError_t adv_tl_obs(const AdvDev &m, const double *w, double *r, cudaStream_t s)
+{
+    cudaError_t e;
+    const long long n = m.n, nyx = (long long)m.ny * m.nx;
+    double *cA = m.c64A, *cB = m.c64B, *src = m.ebar64;
+    // source perturbation E / dz * (L w), then the tangent-linear window from zero
+    if ((e = sep_apply<double>(m, w, n, src, n, 1, m.tmp64, s)) != cudaSuccess) return e;
+    if ((e = colscale<double>(src, n, m.Es64, src, n, (int)n, 1, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cA, 0, (size_t)m.ncells * sizeof(double), s)) != cudaSuccess) return e;
+    for (int t = 0; t < m.T; ++t) {
+        const int bk = (int)(((long long)t * m.nb) / m.T);
+        if ((e = step<double>(m, cA, cB, 1, src + bk * nyx, n, nullptr, 0, false, s)) != cudaSuccess) return e;
+        double *sw = cA;
+        cA = cB;
+        cB = sw;
+        if ((e = gather<double>(m, cA, 1, t + 1, r, m.p, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t adv_bsqrt(const AdvDev &m, const double *in, double *out, int ncols, cudaStream_t s)
 {
     for (int c0 = 0; c0 < ncols; c0 += m.Pmax64) {

@@ -18,6 +18,12 @@
 
 using namespace riot;
 
+// One buffer a context owns, with its size (the caller's allocator may want it back).
+struct riot_alloc_rec {
+    void *p;
+    size_t bytes;
+};
+
 struct riot_ctx {
     int dev = 0;
     int model = RIOT_MODEL_L96;
@@ -29,13 +35,19 @@ struct riot_ctx {
     uint64_t seed = 0;
     L96Dev m;
     AdvDev a;   // tracer model (RIOT_MODEL_ADVDIFF)
-    std::vector<void *> allocs;
+    // device allocator of riot_options (NULL: cudaMalloc / cudaFree) and what it gave out
+    riot_dev_alloc_fn dev_alloc = nullptr;
+    riot_dev_free_fn dev_free = nullptr;
+    void *alloc_user = nullptr;
+    std::vector<riot_alloc_rec> allocs;
+    int wait_polls = -1;   // poll bound of the Hessian kernel's waits (-1: default; riot_set_wait_limit)
     // model tables
     int *optr = nullptr, *oslot = nullptr, *oidx = nullptr;
     double *y = nullptr, *rinv64 = nullptr, *band64 = nullptr, *sig64 = nullptr;
     float *rinv32 = nullptr, *band32 = nullptr, *sig32 = nullptr;
     // outer-loop state
     double *x = nullptr, *v = nullptr, *g = nullptr, *dv = nullptr, *tmp = nullptr;
+    double *v0 = nullptr;   // v at the last riot_outer_begin (the quadratic cost's control)
     double *xsave = nullptr, *vsave = nullptr;   // x, v before a batched inner loop (to redo one window)
     double *traj = nullptr, *d = nullptr, *rd = nullptr, *jo = nullptr;
     float2 *coef32 = nullptr;
@@ -70,7 +82,7 @@ struct riot_ctx {
     double *pcV = nullptr, *pcc = nullptr, *pci = nullptr, *pcT = nullptr;
     double *pcB = nullptr;   // rotation: orthonormal basis of [P_1 V_1, ..., P_{k-1} V_{k-1}] (rot_cols columns)
     float *pcV32 = nullptr, *pcB32 = nullptr, *pcT32 = nullptr;   // FP32 copies (mixed precision)
-    std::vector<void *> pc_allocs;
+    std::vector<riot_alloc_rec> pc_allocs;
     // RIOT-PSAS (riot_psas), allocated at its first call: observation-space blocks (p x kmax
     // FP64: sketch / basis input, products, basis, Ritz vectors, adjoint forcing, TL output),
     // S = diag(1 / sigma_o) and sigma_o, and p-vectors
@@ -142,18 +154,39 @@ riot_status fail(riot_ctx *c, riot_status st, const char *fmt, ...)
         if (e_ != cudaSuccess) return bfail(b, RIOT_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// Device memory of a context: from the caller's allocator when riot_options gave one,
+// else cudaMalloc.  Returns NULL on failure.
+void *ctx_malloc(riot_ctx *ctx, size_t bytes)
+{
+    if (ctx->dev_alloc) return ctx->dev_alloc(bytes, (void *)ctx->s, ctx->alloc_user);
+    void *q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return q;
+}
+
+void ctx_free(riot_ctx *ctx, const riot_alloc_rec &a)
+{
+    if (!a.p) return;
+    if (ctx->dev_free) ctx->dev_free(a.p, a.bytes, (void *)ctx->s, ctx->alloc_user);
+    else cudaFree(a.p);
+}
+
 template <typename T>
 riot_status dalloc(riot_ctx *ctx, T **p, size_t count)
 {
     *p = nullptr;
     if (count == 0) count = 1;
-    void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, RIOT_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    const size_t bytes = count * sizeof(T);
+    void *q = ctx_malloc(ctx, bytes);
+    if (!q) return fail(ctx, RIOT_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    if (((uintptr_t)q & 255) != 0) {
+        ctx_free(ctx, {q, bytes});
+        return fail(ctx, RIOT_EINVAL, "the device allocator returned a pointer not aligned to 256 bytes");
     }
-    ctx->allocs.push_back(q);
+    ctx->allocs.push_back({q, bytes});
     *p = (T *)q;
     return RIOT_OK;
 }
@@ -222,7 +255,8 @@ riot_status hvp(riot_ctx *ctx, const void *W, void *Y, int64_t ld, int ncols, in
                                   (double *)ctx->rscr, 0, ctx->s));
         else
             CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
-                                  (float *)ctx->rscr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S));
+                                  (float *)ctx->rscr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S,
+                                  ctx->wait_polls));
     }
     return RIOT_OK;
 }
@@ -304,6 +338,32 @@ riot_status check_cholesky(riot_ctx *ctx, int base, int count, const char *what)
             return fail(ctx, RIOT_ENOTSPD, "%s: Cholesky pass %d met a non-positive pivot at column %d", what, i,
                         h[i] - 1);
     return RIOT_OK;
+}
+
+// The flag of the kernels with bounded device waits (the mixed-precision Hessian
+// kernel's stage copies, the tensor-core GEMMs' MMA completions): every call that
+// launches them clears it first and reads it (synchronising) before it returns, so
+// each call reports its own timeout and a later call is not blamed for it.
+riot_status clear_timeout(riot_ctx *ctx)
+{
+    CU(cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->s));
+    return RIOT_OK;
+}
+
+riot_status check_timeout(riot_ctx *ctx)
+{
+    int eflag = 0;
+    CU(cudaMemcpyAsync(&eflag, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    if (!eflag) return RIOT_OK;
+    CU(cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->s));
+    if (eflag >= 2)
+        return fail(ctx, RIOT_ETIMEOUT,
+                    "a bounded device wait ran out and a bulk copy was still in flight when its CTA exited: every "
+                    "result of that launch is invalid");
+    return fail(ctx, RIOT_ETIMEOUT,
+                "a bounded device wait ran out (Hessian kernel stage copy or tensor-core GEMM): the results of this "
+                "call are invalid");
 }
 
 // ---------------------------------------------------------------------------
@@ -663,6 +723,7 @@ riot_status setup_common(riot_ctx *ctx)
     riot_status st;
     if ((st = dalloc(ctx, &ctx->x, np)) || (st = dalloc(ctx, &ctx->v, np)) || (st = dalloc(ctx, &ctx->g, np)) ||
         (st = dalloc(ctx, &ctx->dv, np)) || (st = dalloc(ctx, &ctx->tmp, np)) || (st = dalloc(ctx, &ctx->d, p)) ||
+        (st = dalloc(ctx, &ctx->v0, np)) ||
         (st = dalloc(ctx, &ctx->xsave, np)) || (st = dalloc(ctx, &ctx->vsave, np)) ||
         (st = dalloc(ctx, &ctx->rd, p)) || (st = dalloc(ctx, &ctx->jo, 2)) ||
         (st = dalloc(ctx, (char **)&ctx->Wblk, np * k * rs)) || (st = dalloc(ctx, (char **)&ctx->Yblk, np * k * rs)) ||
@@ -751,7 +812,7 @@ enum { PC_P = 0, PC_PT = 1, PC_PINV = 2 };
 
 void pc_free(riot_ctx *ctx)
 {
-    for (void *p : ctx->pc_allocs) cudaFree(p);
+    for (const riot_alloc_rec &a : ctx->pc_allocs) ctx_free(ctx, a);
     ctx->pc_allocs.clear();
     ctx->pcV = ctx->pcc = ctx->pci = ctx->pcT = ctx->pcB = nullptr;
     ctx->pcV32 = ctx->pcB32 = ctx->pcT32 = nullptr;
@@ -763,12 +824,10 @@ void pc_free(riot_ctx *ctx)
 template <typename T>
 riot_status pc_alloc(riot_ctx *ctx, T **p, size_t count)
 {
-    void *q = nullptr;
-    if (cudaMalloc(&q, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, RIOT_ENOMEM, "cudaMalloc of %zu bytes for the preconditioner failed", count * sizeof(T));
-    }
-    ctx->pc_allocs.push_back(q);
+    const size_t bytes = (count ? count : 1) * sizeof(T);
+    void *q = ctx_malloc(ctx, bytes);
+    if (!q) return fail(ctx, RIOT_ENOMEM, "device allocation of %zu bytes for the preconditioner failed", bytes);
+    ctx->pc_allocs.push_back({q, bytes});
     *p = (T *)q;
     return RIOT_OK;
 }
@@ -919,6 +978,7 @@ riot_status rsvd_begin(riot_ctx *ctx, int k, int64_t sketch_stream, const void *
 {
     const int n = ctx->n;
     CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 32, ctx->s));
+    TRY(clear_timeout(ctx));
     if (Omega)
         CU(cudaMemcpyAsync(ctx->Wblk, Omega, (size_t)n * k * real_size(ctx), cudaMemcpyDeviceToDevice, ctx->s));
     else
@@ -1033,10 +1093,7 @@ riot_status rsvd_collect(riot_ctx *ctx, int k, double *lambda_out)
 {
     cudaStream_t s = ctx->s;
     // a bounded wait that ran out invalidates everything after it: report it first
-    int eflag = 0;
-    CU(cudaMemcpyAsync(&eflag, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (eflag) return fail(ctx, RIOT_ETIMEOUT, "a bounded device wait ran out (Hessian kernel coefficient copy or tensor-core GEMM)");
+    TRY(check_timeout(ctx));
     TRY(check_cholesky(ctx, 0, 11, "riot_rsvd"));
     int jinfo[2] = {0, 0};
     CU(cudaMemcpyAsync(jinfo, ctx->info + 12, sizeof(jinfo), cudaMemcpyDeviceToHost, s));
@@ -1221,7 +1278,7 @@ void riot_destroy(riot_ctx *ctx)
     cudaSetDevice(ctx->dev);
     if (ctx->s) cudaStreamSynchronize(ctx->s);
     pc_free(ctx);
-    for (void *p : ctx->allocs) cudaFree(p);
+    for (const riot_alloc_rec &a : ctx->allocs) ctx_free(ctx, a);
     for (int i = 0; i < 32; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     delete ctx;
@@ -1266,11 +1323,25 @@ riot_status riot_setup(riot_ctx **out, const riot_model_desc *model, const riot_
     ctx->kmax = opt->kmax;
     ctx->exact_rr = opt->exact_rr;
     ctx->seed = opt->seed;
+    if ((opt->dev_alloc == nullptr) != (opt->dev_free == nullptr))
+        return bail(fail(ctx, RIOT_EINVAL, "dev_alloc and dev_free must be given together"));
+    ctx->dev_alloc = opt->dev_alloc;
+    ctx->dev_free = opt->dev_free;
+    ctx->alloc_user = opt->alloc_user;
     ctx->model = model->kind;
     ctx->p = (int)p64;
     riot_status st = (model->kind == RIOT_MODEL_L96) ? setup_l96(ctx, model, obs, B) : setup_advdiff(ctx, model, obs, B);
     if (st != RIOT_OK) return bail(st);
     if ((st = setup_common(ctx)) != RIOT_OK) return bail(st);
+    // the device address of riot_hessian_apply_noalloc's static scratch, looked up once per
+    // device here so that the entry point itself never loads a module or allocates
+    {
+        void *scr = nullptr;
+        const cudaError_t e = noalloc_scratch(ctx->dev, &scr);
+        if (e != cudaSuccess)
+            return bail(fail(ctx, RIOT_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                             cudaGetErrorString(e)));
+    }
     for (int i = 0; i < 32; ++i)
         if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) return bail(fail(ctx, RIOT_ECUDA, "cudaEventCreate failed"));
     *out = ctx;
@@ -1298,6 +1369,7 @@ riot_status riot_outer_begin(riot_ctx *ctx, const double *x_dev, const double *v
     // preconditioned loop: the gradient of the problem in w (v = v_{k-1} + P_k w) is P_k^T (b + v)
     if (!ctx->pc_m.empty()) TRY(pc_apply64(ctx, ctx->g, 1, PC_PT));
     CU(add_half_sq(n, ctx->v, ctx->jo, ctx->s));
+    CU(cudaMemcpyAsync(ctx->v0, ctx->v, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->s));
     ctx->have_traj = 1;
     ctx->have_rsvd = 0;
     ctx->pc_open = 0;
@@ -1318,11 +1390,15 @@ riot_status riot_hessian_apply(riot_ctx *ctx, const void *W_dev, void *Y_dev, in
     if (ncols == 0) return RIOT_OK;
     if (!W_dev || !Y_dev) return fail(ctx, RIOT_EINVAL, "null W or Y");
     CU(cudaSetDevice(ctx->dev));
-    if (!ctx->scale_exp) return hvp(ctx, W_dev, Y_dev, ld, ncols, add_identity);
-    TRY(hvp(ctx, W_dev, Y_dev, ld, ncols, 0));
-    CU(scale_add_cols(ctx->n, ncols, ld, ldexp(1.0, ctx->scale_exp), Y_dev, add_identity ? W_dev : nullptr,
-                      ctx->prec == RIOT_PREC_FP64, ctx->s));
-    return RIOT_OK;
+    TRY(clear_timeout(ctx));
+    if (!ctx->scale_exp) {
+        TRY(hvp(ctx, W_dev, Y_dev, ld, ncols, add_identity));
+    } else {
+        TRY(hvp(ctx, W_dev, Y_dev, ld, ncols, 0));
+        CU(scale_add_cols(ctx->n, ncols, ld, ldexp(1.0, ctx->scale_exp), Y_dev, add_identity ? W_dev : nullptr,
+                          ctx->prec == RIOT_PREC_FP64, ctx->s));
+    }
+    return check_timeout(ctx);
 }
 
 riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y_dev, int64_t ld, int32_t ncols,
@@ -1343,6 +1419,7 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
                     per_col, ctx->p, kNoAllocScratchBytes);
     void *scr = nullptr;
     CU(noalloc_scratch(ctx->dev, &scr));
+    TRY(clear_timeout(ctx));
     size_t slice = per_col ? kNoAllocScratchBytes / per_col : (size_t)ncols;
     if (slice > (size_t)ncols) slice = (size_t)ncols;
     if (ctx->model == RIOT_MODEL_ADVDIFF && slice > (size_t)ctx->a.Pmax) slice = (size_t)ctx->a.Pmax;
@@ -1357,14 +1434,14 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
                                   (double *)scr, 0, ctx->s));
         else if (!ctx->scale_exp)
             CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
-                                  (float *)scr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S));
+                                  (float *)scr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S, ctx->wait_polls));
         else {
             CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, 0, (float *)scr, 0,
-                                  ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S));
+                                  ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S, ctx->wait_polls));
             CU(scale_add_cols(ctx->n, nc, ld, ldexp(1.0, ctx->scale_exp), yv, add_identity ? w : nullptr, 0, ctx->s));
         }
     }
-    return RIOT_OK;
+    return check_timeout(ctx);
 }
 
 riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const void *Omega_dev,
@@ -1422,6 +1499,40 @@ riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t r
         return fail(ctx, RIOT_EINVAL, "probes_per_cta in [0, 64], ring_depth 0 or in [2, 8]");
     ctx->hvp_P = probes_per_cta;
     ctx->hvp_S = ring_depth;
+    return RIOT_OK;
+}
+
+riot_status riot_set_wait_limit(riot_ctx *ctx, int32_t polls)
+{
+    if (!ctx) return RIOT_EINVAL;
+    ctx->wait_polls = polls < 0 ? -1 : polls;
+    return RIOT_OK;
+}
+
+riot_status riot_quadratic_cost(riot_ctx *ctx, const double *dv_dev, double *J_out)
+{
+    if (!ctx || !J_out) return RIOT_EINVAL;
+    if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_quadratic_cost before riot_outer_begin");
+    CU(cudaSetDevice(ctx->dev));
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    double *r = nullptr;
+    if (dv_dev && ctx->p > 0) {
+        // r = R^-1 H M L dv: one FP64 tangent-linear integration along the stored trajectory
+        r = ctx->rd;
+        if (ctx->model == RIOT_MODEL_ADVDIFF) CU(adv_tl_obs(ctx->a, dv_dev, r, s));
+        else CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, dv_dev, nullptr, n, 1, 0, r, 2, s));
+    }
+    CU(cudaMemsetAsync(ctx->nrm + 2, 0, sizeof(double), s));
+    CU(obs_quad_cost(ctx->p, ctx->d, r, ctx->rinv64, ctx->nrm + 2, s));
+    // background term 1/2 ||v + dv||^2 with v of the last riot_outer_begin
+    CU(cudaMemcpyAsync(ctx->tmp, ctx->v0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (dv_dev) CU(axpby(n, 1.0, dv_dev, 1.0, ctx->tmp, s));
+    CU(add_half_sq(n, ctx->tmp, ctx->nrm + 2, s));
+    double h = 0.0;
+    CU(cudaMemcpyAsync(&h, ctx->nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    *J_out = h;
     return RIOT_OK;
 }
 
@@ -1926,6 +2037,7 @@ riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sket
     double rho = -1.0;
     if (m > 0) {
         CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 32, s));
+        TRY(clear_timeout(ctx));
         // the proposal, orthonormalised, then Gaussian columns for the rest of the sketch
         TRY(orth32(ctx, P_dev, m, 16, 3, 2));
         CU(cudaMemcpyAsync(W32, ctx->Q32, sizeof(float) * (size_t)n * m, cudaMemcpyDeviceToDevice, s));
@@ -2011,9 +2123,8 @@ static riot_status apply_a_block(riot_ctx *ctx, const double *X, double *Y, int 
 
 static riot_status apply_a_vec(riot_ctx *ctx, const double *q, double *w) { return apply_a_block(ctx, q, w, 1); }
 
-riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_out, int32_t *m_used)
+static riot_status varcg_body(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_out, int32_t *m_used)
 {
-    if (!ctx) return RIOT_EINVAL;
     if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_varcg before riot_outer_begin");
     if (m < 1 || m > ctx->kmax) return fail(ctx, RIOT_EINVAL, "m = %d outside [1, kmax = %d]", m, ctx->kmax);
     if (!ctx->pc_m.empty()) return fail(ctx, RIOT_ESTATE, "riot_varcg: Algorithm 1 runs without the spectral preconditioner");
@@ -2102,10 +2213,9 @@ static riot_status small_eig(riot_ctx *ctx, int k, const char *what)
     return RIOT_OK;
 }
 
-riot_status riot_varbl(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev, double *dv_dev, double *theta_out,
-                       int32_t *blocks_used)
+static riot_status varbl_body(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev, double *dv_dev,
+                              double *theta_out, int32_t *blocks_used)
 {
-    if (!ctx) return RIOT_EINVAL;
     if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_varbl before riot_outer_begin");
     if (l < 1 || m < 1 || (int64_t)l * m > ctx->kmax || (int64_t)l * m > ctx->n)
         return fail(ctx, RIOT_EINVAL, "l = %d, m = %d: 1 <= l m <= min(kmax = %d, n = %d) required", l, m, ctx->kmax,
@@ -2191,6 +2301,29 @@ riot_status riot_varbl(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev
     CU(cudaStreamSynchronize(s));
     if (blocks_used) *blocks_used = nb;
     return RIOT_OK;
+}
+
+// Algorithms 1 and 2 launch the Hessian kernel (bounded waits on the mixed path) once per step:
+// the wait flag is cleared before the first and read after the last
+riot_status riot_varcg(riot_ctx *ctx, int32_t m, double *dv_dev, double *theta_out, int32_t *m_used)
+{
+    if (!ctx) return RIOT_EINVAL;
+    CU(cudaSetDevice(ctx->dev));
+    TRY(clear_timeout(ctx));
+    const riot_status st = varcg_body(ctx, m, dv_dev, theta_out, m_used);
+    const riot_status tst = check_timeout(ctx);
+    return tst != RIOT_OK ? tst : st;
+}
+
+riot_status riot_varbl(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev, double *dv_dev, double *theta_out,
+                       int32_t *blocks_used)
+{
+    if (!ctx) return RIOT_EINVAL;
+    CU(cudaSetDevice(ctx->dev));
+    TRY(clear_timeout(ctx));
+    const riot_status st = varbl_body(ctx, l, m, B0_dev, dv_dev, theta_out, blocks_used);
+    const riot_status tst = check_timeout(ctx);
+    return tst != RIOT_OK ? tst : st;
 }
 
 // ---------------------------------------------------------------------------

@@ -87,11 +87,13 @@ cudaError_t l96_hvp_launch_f64(const L96Dev &m, const double2 *coef, const doubl
                                cudaStream_t s);
 
 // FP32 Hessian-vector product with the stage coefficients streamed into
-// shared memory by 1-D TMA copies (same modes as above); *err is set to 1 if
-// a bounded wait on a copy ran out.
+// shared memory by 1-D TMA copies (same modes as above); *err is raised to 1
+// if a bounded wait on a copy ran out, to 2 if a copy was still in flight when
+// its CTA exited after that.  wait_polls < 0: the default bound of each wait
+// (about 2^20 polls); >= 0: that many polls (tests of the timeout report).
 cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float *W, float *Y, int64_t ld,
                                int ncols, int add_identity, float *r, int mode, int *err, cudaStream_t s,
-                               int P_hint = 0, int S_hint = 0);
+                               int P_hint = 0, int S_hint = 0, int wait_polls = -1);
 
 // Several Lorenz-96 windows' FP32 Hessian products (Y = A W) in one
 // persistent launch over a queue of (window, CTA block) items.
@@ -158,6 +160,9 @@ cudaError_t adv_hvp(const AdvDev &m, bool fp64, const void *W, void *Y, int64_t 
 // jo += 1/2 sum d^2 / sigma^2 (atomic), rd = R^-1 d, b = L^T H'^T R^-1 d.
 cudaError_t adv_outer(const AdvDev &m, const double *x, double *d, double *jo, double *rd, double *b,
                       cudaStream_t s);
+// Tangent-linear observation residuals of one FP64 column w: r = R^-1 H' (L w), the forward
+// half of a Hessian product (uses the outer-loop workspace; p doubles out).
+cudaError_t adv_tl_obs(const AdvDev &m, const double *w, double *r, cudaStream_t s);
 // out = L in (= L^T in), ncols columns of n doubles
 cudaError_t adv_bsqrt(const AdvDev &m, const double *in, double *out, int ncols, cudaStream_t s);
 // tracer field after `steps` steps from zero with emissions E_b exp(x) (FP64)
@@ -279,6 +284,8 @@ cudaError_t check_finite(const double *x, int64_t n, int *flag, cudaStream_t s);
 cudaError_t add_if_flag(const int *flag, int want, int64_t n, double a, const double *x, double *y, cudaStream_t s);
 cudaError_t mul(int64_t n, const double *a, const double *b, double *out, cudaStream_t s);
 cudaError_t add_half_sq(int64_t n, const double *x, double *out, cudaStream_t s);
+// out += 1/2 sum (d + r / rinv)^2 rinv over p observations (r may be null: 1/2 sum d^2 rinv)
+cudaError_t obs_quad_cost(int64_t p, const double *d, const double *r, const double *rinv, double *out, cudaStream_t s);
 cudaError_t scale_to_f32(int64_t n, const double *in, double a, float *out, cudaStream_t s);
 // Column equilibration of one CholeskyQR pass: with d_j = 1/sqrt(G_jj),
 // G <- D G D (lower triangle) and Q <- Q D ('f' or 'd' block, n rows); d receives D.

@@ -71,24 +71,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait (about 2^20 polls, well under a second).  After one wait of
-// the CTA has run out, later waits return at once: the results are then
-// wrong, the flag says so, and the kernel still finishes promptly.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag)
+// Bounded wait of at most `polls` polls (default kWaitPolls, about 2^20 polls,
+// well under a second).  After one wait of the CTA has run out, later waits
+// return at once: the results are then wrong, the flag says so (value 1),
+// and the kernel still finishes promptly.
+constexpr int kWaitPolls = 1 << 20;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag,
+                                                  int polls)
 {
     if (*abort_flag) return false;
-    for (int i = 0; i < (1 << 20); ++i) {
+    for (int i = 0; i < polls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (i > 32) __nanosleep(64);
     }
     *abort_flag = 1;
-    atomicExch(err, 1);
+    atomicMax(err, 1);
     return false;
 }
 
 struct TmaArgs {
     ChunkGeom geom;
     int T, P, S, p, hl, hh, ncols, add_identity, mode;
+    int wait_polls;   // poll bound of each wait on a stage copy (kWaitPolls unless a test lowers it)
     float dt;
     const float2 *coef;
     const int *optr, *oslot;
@@ -101,11 +106,14 @@ struct TmaArgs {
 // Ring of stage buffers fed by thread 0.  Stream position c = 0.. counts the
 // stages this launch consumes; stage c of the stream is coefficient block
 // blk(c) of the [T][4] array: forward for the tangent-linear pass, backward
-// for the adjoint pass.
+// for the adjoint pass.  Thread 0 keeps `issued` (copies started) and
+// `landed` (stages whose copy it has seen complete) so that after an abort it
+// can still wait for every copy it started before the CTA exits.
 struct Ring {
     float2 *buf;
     uint32_t bar0;
-    int S, Np, total, c0, T;
+    int S, Np, total, c0, T, polls;
+    int issued, landed;
     const float2 *coef;
     volatile int *abort_flag;
     __device__ int blk(int c) const
@@ -113,7 +121,7 @@ struct Ring {
         const int u = c0 + c;
         return u < 4 * T ? u : 8 * T - 1 - u;
     }
-    __device__ void issue(int c) const
+    __device__ void issue(int c)
     {
         const int slot = c % S;
         const uint32_t bytes = (uint32_t)Np * 8u;
@@ -121,27 +129,38 @@ struct Ring {
         fence_proxy_async();
         mbar_expect_tx(bar, bytes);
         bulk_g2s(smem_u32(buf + (size_t)slot * Np), coef + (size_t)blk(c) * Np, bytes, bar);
+        issued = c + 1;
     }
     // Thread 0 only, before the stage's barrier: wait until stage c has landed.
     // The barrier then makes the buffer visible to every thread.
-    __device__ void wait_ready(int c, int *err) const
+    __device__ void wait_ready(int c, int *err)
     {
-        if (threadIdx.x == 0) mbar_wait_bounded(bar0 + 8u * (c % S), (uint32_t)((c / S) & 1), err, abort_flag);
+        if (threadIdx.x == 0 && mbar_wait_bounded(bar0 + 8u * (c % S), (uint32_t)((c / S) & 1), err, abort_flag, polls))
+            landed = c + 1;
     }
     // Thread 0 only, after the stage's barrier (every thread is done with the
     // buffer of stage c - 1): refill that buffer with stage c + S - 1.
-    __device__ void refill(int c) const
+    __device__ void refill(int c)
     {
         if (threadIdx.x == 0 && c + S - 1 < total && !*abort_flag) issue(c + S - 1);
     }
     __device__ const float4 *slot4(int slot) const { return reinterpret_cast<const float4 *>(buf + (size_t)slot * Np); }
-    // After an abort: wait (bounded) for the copies this CTA still has in flight.
-    __device__ void drain(int next_c, int *err) const
+    // After an abort: wait, with the full bound whatever the test limit, for every
+    // copy this CTA started and has not seen land.  Each such stage sits in its own
+    // buffer (a buffer is refilled only after its previous stage landed), so its
+    // phase parity identifies it.  A copy still in flight after that raises the
+    // flag to 2: it may land in shared memory the CTA no longer owns.
+    __device__ void drain(int *err)
     {
         if (threadIdx.x != 0 || !*abort_flag) return;
-        for (int c = next_c; c < total && c < next_c + S - 1; ++c)
-            for (int i = 0; i < (1 << 20); ++i)
-                if (mbar_try_wait(bar0 + 8u * (c % S), (uint32_t)((c / S) & 1))) break;
+        for (int c = landed; c < issued; ++c) {
+            bool done = false;
+            for (int i = 0; i < kWaitPolls && !done; ++i) {
+                done = mbar_try_wait(bar0 + 8u * (c % S), (uint32_t)((c / S) & 1));
+                if (!done && i > 32) __nanosleep(64);
+            }
+            if (!done) atomicMax(err, 2);
+        }
     }
 };
 
@@ -150,7 +169,7 @@ struct Ring {
 // (float4 pairs interleaved by thread) and are shared by the PR probes.
 template <int E, int PR>
 __device__ __forceinline__ void tl_stage(const float (&s)[PR][E], float (&k)[PR][E], bool full, float *H, int nthr,
-                                         int tid, int left, int right, int &hb, const Ring &ring, int c, int slot, int t,
+                                         int tid, int left, int right, int &hb, Ring &ring, int c, int slot, int t,
                                          int Tp, int *err)
 {
     float *Hb = H + hb * 3 * PR * nthr;
@@ -201,7 +220,7 @@ __device__ __forceinline__ void tl_stage(const float (&s)[PR][E], float (&k)[PR]
 // coefficient read follows the stage's barrier.
 template <int E, int PR>
 __device__ __forceinline__ void ad_stage(const float (&m)[PR][E], float (&out)[PR][E], bool full, float *H, int nthr,
-                                         int tid, int left, int right, int &hb, const Ring &ring, int c, int slot, int t,
+                                         int tid, int left, int right, int &hb, Ring &ring, int c, int slot, int t,
                                          int Tp, int offL, int oddL, int tr, int *err)
 {
     float *Hb = H + hb * 3 * PR * nthr;
@@ -316,6 +335,9 @@ __device__ __forceinline__ void hvp_tma_body(const TmaArgs &a, int blk, unsigned
     ring.coef = a.coef;
     ring.c0 = (a.mode == 1) ? 4 * a.T : 0;
     ring.total = ((a.mode == 2) ? 4 * a.T : 8 * a.T) - ring.c0;
+    ring.polls = a.wait_polls;
+    ring.issued = 0;
+    ring.landed = 0;
     ring.abort_flag = abort_flag;
     if (tid == 0) {
         for (int i = 0; i < S; ++i) mbar_init(ring.bar0 + 8u * i, 1);
@@ -401,7 +423,7 @@ __device__ __forceinline__ void hvp_tma_body(const TmaArgs &a, int blk, unsigned
                 for (int j = 0; j < E; ++j) { acc[r][j] += k[r][j]; dx[r][j] = fmaf(h6, acc[r][j], dx[r][j]); }
         }
         if (a.mode == 2) {
-            ring.drain(c, a.err);
+            ring.drain(a.err);
             __syncthreads();
             if (tid == 0)
                 for (int i = 0; i < S; ++i) mbar_inval(ring.bar0 + 8u * i);
@@ -475,7 +497,7 @@ __device__ __forceinline__ void hvp_tma_body(const TmaArgs &a, int blk, unsigned
             for (int j = 0; j < E; ++j) lam[r][j] = lx[r][j] + ls[r][j];
     }
 
-    ring.drain(c, a.err);
+    ring.drain(a.err);
     __syncthreads();
     if (tid == 0)
         for (int i = 0; i < S; ++i) mbar_inval(ring.bar0 + 8u * i);
@@ -590,7 +612,8 @@ static cudaError_t launch_tma(const TmaArgs &a, int grid, int nthr, size_t sm, c
 }
 
 cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float *W, float *Y, int64_t ld, int ncols,
-                               int add_identity, float *r, int mode, int *err, cudaStream_t s, int P_hint, int S_hint)
+                               int add_identity, float *r, int mode, int *err, cudaStream_t s, int P_hint, int S_hint,
+                               int wait_polls)
 {
     if (ncols <= 0) return cudaSuccess;
     int dev = 0, smem_optin = 0;
@@ -614,6 +637,7 @@ cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float 
     a.ncols = ncols;
     a.add_identity = add_identity;
     a.mode = mode;
+    a.wait_polls = wait_polls >= 0 ? wait_polls : kWaitPolls;
     a.dt = (float)m.dt;
     a.coef = coef;
     a.optr = m.optr;
@@ -693,6 +717,7 @@ cudaError_t hvp_batch_plan(const HvpBatchWindow *w, int nwin, int P_cap, int S_r
         a.ncols = w[i].ncols;
         a.add_identity = 0;
         a.mode = 0;
+        a.wait_polls = kWaitPolls;
         a.dt = (float)m.dt;
         a.coef = w[i].coef;
         a.optr = m.optr;

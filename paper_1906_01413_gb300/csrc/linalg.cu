@@ -1225,6 +1225,20 @@ __global__ void half_sq_kernel(int64_t n, const double *x, double *out)
     if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(out, 0.5 * part);
 }
 
+// out += 1/2 sum_o (d_o + r_o / rinv_o)^2 rinv_o: the observation term of the inner-loop
+// quadratic cost (Eq. 3) from the innovation d and the tangent-linear residuals
+// r = R^-1 H M L dv (rinv = 1 / sigma_o^2 > 0).
+__global__ void obs_quad_kernel(int64_t p, const double *d, const double *r, const double *rinv, double *out)
+{
+    double part = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+        const double e = d[i] + (r ? r[i] / rinv[i] : 0.0);
+        part += e * e * rinv[i];
+    }
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(out, 0.5 * part);
+}
+
 // Column equilibration of a CholeskyQR pass: d_j = 1 / sqrt(G_jj) (1 for a
 // zero column), G <- D G D on the lower triangle, Q <- Q D.  The scales are
 // formed by their own kernel first: a block scaling its column must not race
@@ -1379,6 +1393,15 @@ cudaError_t add_half_sq(int64_t n, const double *x, double *out, cudaStream_t s)
     if (blocks > 256) blocks = 256;
     if (blocks < 1) return cudaSuccess;
     { count_launch(); half_sq_kernel<<<blocks, 256, 0, s>>>(n, x, out); }
+    return cudaGetLastError();
+}
+
+cudaError_t obs_quad_cost(int64_t p, const double *d, const double *r, const double *rinv, double *out, cudaStream_t s)
+{
+    int blocks = (int)((p + 255) / 256);
+    if (blocks > 256) blocks = 256;
+    if (blocks < 1) return cudaSuccess;
+    { count_launch(); obs_quad_kernel<<<blocks, 256, 0, s>>>(p, d, r, rinv, out); }
     return cudaGetLastError();
 }
 

@@ -49,9 +49,45 @@ class BcovDesc(ctypes.Structure):
                 ("sigma_vec", POINTER(c_double))]
 
 
+DEV_ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, ctypes.c_size_t, c_void_p, c_void_p)
+DEV_FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, ctypes.c_size_t, c_void_p, c_void_p)
+
+
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("kmax", c_int32), ("exact_rr", c_int32), ("eig_method", c_int32),
-                ("seed", c_uint64)]
+                ("seed", c_uint64), ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN),
+                ("alloc_user", c_void_p)]
+
+
+def _torch_alloc(nbytes, stream, user):
+    """riot_dev_alloc_fn through PyTorch's caching allocator on the current device."""
+    try:
+        import torch
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+    except Exception:   # out of memory: the library reports RIOT_ENOMEM
+        return None
+
+
+def _torch_free(ptr, nbytes, stream, user):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+# One pair of callbacks for every context; each Context also keeps a reference, so the
+# C thunks outlive every context that may call them.
+TORCH_ALLOC = DEV_ALLOC_FN(_torch_alloc)
+TORCH_FREE = DEV_FREE_FN(_torch_free)
+
+
+def _options(precision, kmax, exact_rr, eig_method, seed, torch_allocator):
+    if torch_allocator:
+        return Options(int(precision), int(kmax), int(bool(exact_rr)), int(eig_method), int(seed), TORCH_ALLOC,
+                       TORCH_FREE, None)
+    return Options(int(precision), int(kmax), int(bool(exact_rr)), int(eig_method), int(seed),
+                   DEV_ALLOC_FN(), DEV_FREE_FN(), None)
 
 
 class RiotError(RuntimeError):
@@ -94,6 +130,10 @@ def load():
     L.riot_status_string.restype = c_char_p
     L.riot_set_hvp_config.argtypes = [vp, c_int32, c_int32]
     L.riot_set_hvp_config.restype = c_int32
+    L.riot_set_wait_limit.argtypes = [vp, c_int32]
+    L.riot_set_wait_limit.restype = c_int32
+    L.riot_quadratic_cost.argtypes = [vp, vp, POINTER(c_double)]
+    L.riot_quadratic_cost.restype = c_int32
     L.riot_rsvd_sweeps.argtypes = [vp]
     L.riot_rsvd_sweeps.restype = c_int32
     L.riot_kernel_launches.argtypes = []
@@ -179,7 +219,7 @@ def _check(ctx, fn, status):
 
 def riot_setup(n, T, dt, F, obs_step, obs_idx, obs_y, obs_sigma, length, sigma_b=1.0, sigma_vec=None,
                precision=RIOT_PREC_MIXED, kmax=64, exact_rr=False, seed=0, stream=None,
-               eig_method=RIOT_EIG_TRIDIAG):
+               eig_method=RIOT_EIG_TRIDIAG, torch_allocator=True):
     """Create a context (host numpy arrays for the observations); returns the handle."""
     L = load()
     st = np.ascontiguousarray(obs_step, dtype=np.int32)
@@ -192,7 +232,7 @@ def riot_setup(n, T, dt, F, obs_step, obs_idx, obs_y, obs_sigma, length, sigma_b
     sv = None if sigma_vec is None else np.ascontiguousarray(sigma_vec, dtype=np.float64)
     bd = BcovDesc(RIOT_B_GAUSS_RING, 0, float(length), float(sigma_b),
                   None if sv is None else sv.ctypes.data_as(POINTER(c_double)))
-    op = Options(int(precision), int(kmax), int(bool(exact_rr)), int(eig_method), int(seed))
+    op = _options(precision, kmax, exact_rr, eig_method, seed, torch_allocator)
     h = c_void_p()
     status = L.riot_setup(ctypes.byref(h), ctypes.byref(md), ctypes.byref(od), ctypes.byref(bd),
                           ctypes.byref(op), _stream_handle(stream))
@@ -206,7 +246,7 @@ def _dp(a):
 
 def riot_setup_advdiff(nx, ny, nz, nblocks, T, dt, dx, dy, dz, u, v, amp, kz, emis_b, obs_step, obs_pos, obs_y,
                        obs_sigma, length, sigma_b, precision=RIOT_PREC_MIXED, kmax=64, exact_rr=False, seed=0,
-                       stream=None, eig_method=RIOT_EIG_TRIDIAG):
+                       stream=None, eig_method=RIOT_EIG_TRIDIAG, torch_allocator=True):
     """riot_setup for the tracer model (RIOT_MODEL_ADVDIFF with RIOT_B_EXP_SEPARABLE)."""
     L = load()
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (u, v, amp, kz, emis_b)]
@@ -220,12 +260,24 @@ def riot_setup_advdiff(nx, ny, nz, nblocks, T, dt, dx, dy, dz, u, v, amp, kz, em
     sg = np.ascontiguousarray(obs_sigma, dtype=np.float64)
     od = ObsDesc(int(st.size), st.ctypes.data_as(POINTER(c_int32)), None, _dp(yy), _dp(sg), _dp(pos))
     bd = BcovDesc(RIOT_B_EXP_SEPARABLE, 0, float(length), float(sigma_b), None)
-    op = Options(int(precision), int(kmax), int(bool(exact_rr)), int(eig_method), int(seed))
+    op = _options(precision, kmax, exact_rr, eig_method, seed, torch_allocator)
     h = c_void_p()
     status = L.riot_setup(ctypes.byref(h), ctypes.byref(md), ctypes.byref(od), ctypes.byref(bd),
                           ctypes.byref(op), _stream_handle(stream))
     _check(None, "riot_setup", status)
     return h
+
+
+def riot_set_wait_limit(ctx, polls):
+    """Poll bound of the Hessian kernel's waits (< 0: the default); tests of the timeout report."""
+    _check(ctx, "riot_set_wait_limit", load().riot_set_wait_limit(ctx, int(polls)))
+
+
+def riot_quadratic_cost(ctx, dv=None):
+    """J~(dv) of Eq. 3 at the last riot_outer_begin's linearisation (FP64); dv None gives J~(0)."""
+    J = c_double(0.0)
+    _check(ctx, "riot_quadratic_cost", load().riot_quadratic_cost(ctx, _ptr(dv), ctypes.byref(J)))
+    return J.value
 
 
 def riot_get_innovation(ctx, d):
@@ -538,6 +590,7 @@ class Context:
     """Owning wrapper: ``with Context(...) as c: riot_rsvd(c.h, ...)``."""
 
     def __init__(self, **kw):
+        self._callbacks = (TORCH_ALLOC, TORCH_FREE)   # alive for as long as this context
         if "nx" in kw:
             self.n = int(kw["nblocks"]) * int(kw["ny"]) * int(kw["nx"])
             self.h = riot_setup_advdiff(**kw)

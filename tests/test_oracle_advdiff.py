@@ -212,3 +212,21 @@ def test_full_rank_riot_increment_is_the_exact_inner_solution(tiny):
     dv_exact = -riot.cg_solve(lambda p: p + A.hvp(prob, traj, p[:, None])[:, 0], res["g"], tol=1e-14)
     assert res["mode"] == 1           # rank-deficient Hessian: the smallest Ritz value is < 1
     np.testing.assert_allclose(res["dv"], dv_exact, rtol=1e-8, atol=1e-10 * np.abs(dv_exact).max())
+
+
+def test_quadratic_cost_is_the_taylor_quadratic(tiny):
+    """J~(dv) of Eq. 3 on the tracer problem equals J + g^T dv + 1/2 dv^T (I + A) dv (the
+    transport is linear in the emission perturbation, so the quadratic is exact): cost,
+    adjoint gradient and Hessian product are independent code paths."""
+    _, prob = tiny
+    rng = np.random.default_rng(12)
+    v = 0.2 * rng.standard_normal(prob.n)
+    traj = A.trajectory(prob, prob.x_b)
+    d = A.innovation(prob, traj)
+    g = A.gradient_b(prob, traj, d) + v
+    J = A.cost(prob, traj, v)
+    assert A.quadratic_cost(prob, traj, d, v, np.zeros(prob.n)) == pytest.approx(J, rel=1e-14)
+    for s in (1e-2, 0.5):
+        dv = s * rng.standard_normal(prob.n)
+        want = J + g @ dv + 0.5 * dv @ dv + 0.5 * dv @ A.hvp(prob, traj, dv[:, None])[:, 0]
+        assert A.quadratic_cost(prob, traj, d, v, dv) == pytest.approx(want, rel=1e-11, abs=1e-11 * J)

@@ -270,3 +270,21 @@ def test_rayleigh_ritz_values_interlace(small):
         tol = 1e-10 * ev[0]
         assert np.all(theta <= ev[:k] + tol)
         assert np.all(theta >= ev[n - k:] - tol)
+
+
+def test_quadratic_cost_is_the_taylor_quadratic(small):
+    """J~(dv) of Eq. 3 equals J + g^T dv + 1/2 dv^T (I + A) dv exactly (a quadratic), with J
+    from the nonlinear cost, g = b + v from the adjoint gradient and A dv from the Hessian
+    product: the three are computed by different code (TL residuals, adjoint, both), so a
+    sign, a dropped term or a wrong v in any of them breaks the identity."""
+    cfg, p, traj = small
+    d = riot.innovation(p, traj)
+    rng = np.random.default_rng(11)
+    v = 0.3 * rng.standard_normal(cfg.n)
+    g = riot.gradient_b(p, traj, d) + v
+    J = riot.cost(p, traj, v)
+    assert riot.quadratic_cost(p, traj, d, v, np.zeros(cfg.n)) == pytest.approx(J, rel=1e-14)
+    for s in (1e-3, 0.1, 2.0):
+        dv = s * rng.standard_normal(cfg.n)
+        want = J + g @ dv + 0.5 * dv @ dv + 0.5 * dv @ riot.hvp(p, traj, dv[:, None])[:, 0]
+        assert riot.quadratic_cost(p, traj, d, v, dv) == pytest.approx(want, rel=1e-11, abs=1e-11 * J)
