@@ -235,10 +235,16 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
 riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream,
                       const void *Omega_dev, double *lambda_out);
 
-/* Adaptive increment (Algorithm 3, Eqs. 8-11): with c = U^T g,
+/* Adaptive increment (Algorithm 3, Eqs. 8-11): with c = U^T g over the
+ * retained pairs,
  * LRA (mode 0) when the smallest retained eigenvalue is > 1:
  *     dv = -U diag(1/(1+lambda)) c
  * LRU (mode 1) otherwise:  dv = -(g - U diag(lambda/(1+lambda)) c).
+ * RIOT_PREC_FP64 retains all k pairs of riot_rsvd.  RIOT_PREC_MIXED retains
+ * the leading pairs with lambda >= 2^-24 lambda_1: an FP32 Hessian product
+ * carries an absolute error of about 2^-24 lambda_1 |w| (its rounding, carried
+ * along the window's leading growth), so smaller Ritz values are not
+ * determined by the products and would decide the mode at random.
  * Then v += dv and x += L dv in the context.  dv_dev (n doubles) and
  * mode_out may be NULL; a non-NULL mode_out synchronises.  Requires
  * riot_rsvd since the last riot_outer_begin.  The stored trajectory and g
@@ -298,18 +304,35 @@ riot_status riot_symm_eig(const double *K_dev, int32_t k, double *lambda_dev, do
 riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6);
 
 /* Launch shape of the mixed-precision Hessian kernel: sketch columns per CTA
- * and depth of its shared-memory ring of streamed stage coefficients (2..8);
- * 0 = automatic.  A shape that does not fit the device falls back to the
- * automatic choice.  Used by the autotuner; results do not depend on it. */
+ * and depth of its shared-memory ring(s) of streamed stage coefficients
+ * (2..8); 0 = automatic.  A shape that does not fit the device falls back to
+ * the automatic choice.  Used by the autotuner; results do not depend on it. */
 riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t ring_depth);
 
-/* Bound of every wait of the mixed-precision Hessian kernel on its stage copies,
- * in polls of the copy's mbarrier: polls >= 0 sets it (0 gives up at once, so
- * the next Hessian application reports RIOT_ETIMEOUT without a fault: this is
- * how the timeout report is tested), polls < 0 restores the default (about
- * 2^20 polls, well under a second).  Whatever the bound, a kernel whose wait
- * ran out still waits with the default bound for every copy it started
- * before its blocks exit. */
+/* Which FP32 Hessian kernel a mixed-precision Lorenz-96 context uses (both
+ * compute Eq. 4 in FP32 with the same stage coefficients, in different
+ * rounding order):
+ *  RIOT_HVP_CTA_BARRIER (default): the CTA streams the stage coefficients
+ *    through one shared ring (1-D TMA) and exchanges chunk halos in shared
+ *    memory behind one CTA-wide barrier per RK4 stage;
+ *  RIOT_HVP_WARP_PAIRS: every warp streams its own chunks' coefficients
+ *    through its own ring, and meets only its two neighbouring warps, at a
+ *    hardware named barrier per pair, after the elements that need no other
+ *    thread's values (windows with 8 or 16 variables per thread and 64 to 512
+ *    threads per column; others keep the default).
+ * Measured on the 4096-variable, 200-step window: the default is faster
+ * (the per-warp ring bookkeeping costs more instructions than the CTA barrier
+ * costs waiting). */
+enum { RIOT_HVP_CTA_BARRIER = 0, RIOT_HVP_WARP_PAIRS = 1 };
+riot_status riot_set_hvp_kernel(riot_ctx *ctx, int32_t kernel);
+
+/* Bound of every wait of the mixed-precision Hessian kernels (on a stage copy,
+ * or on a neighbouring warp's edge values), in tries of the waited mbarrier:
+ * polls >= 0 sets it (0 gives up at once, so the next Hessian application
+ * reports RIOT_ETIMEOUT without a fault: this is how the timeout report is
+ * tested), polls < 0 restores the default (a wait gives up after well under a
+ * second).  Whatever the bound, a kernel whose wait ran out still waits with
+ * the default bound for every copy it started before its blocks exit. */
 riot_status riot_set_wait_limit(riot_ctx *ctx, int32_t polls);
 
 /* Inner-loop quadratic cost (Eq. 3 with Algorithm 3's sign of d)
@@ -320,6 +343,10 @@ riot_status riot_set_wait_limit(riot_ctx *ctx, int32_t polls);
  * The cost reduction of an increment is J~(0) - J~(dv).  *J_out (host) gets
  * the value; this synchronises.  Requires riot_outer_begin. */
 riot_status riot_quadratic_cost(riot_ctx *ctx, const double *dv_dev, double *J_out);
+
+/* Number of eigenpairs the last riot_increment retained (m <= k, see
+ * riot_increment).  Synchronises. */
+riot_status riot_increment_pairs(riot_ctx *ctx, int32_t *m_out);
 
 /* Number of Jacobi sweeps of the last successful riot_rsvd (-1: no context). */
 int32_t riot_rsvd_sweeps(const riot_ctx *ctx);

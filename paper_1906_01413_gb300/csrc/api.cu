@@ -52,6 +52,8 @@ struct riot_ctx {
     double *traj = nullptr, *d = nullptr, *rd = nullptr, *jo = nullptr;
     float2 *coef32 = nullptr;
     double2 *coef64 = nullptr;
+    float4 *coefw = nullptr;   // per-warp FP32 stage coefficients of the warp-synchronous kernel (mixed)
+    int hvp_kernel = RIOT_HVP_CTA_BARRIER;   // FP32 Hessian kernel (riot_set_hvp_kernel)
     // inner-loop workspace
     void *Wblk = nullptr, *Yblk = nullptr, *rscr = nullptr;
     double *Q = nullptr, *U = nullptr;
@@ -253,6 +255,9 @@ riot_status hvp(riot_ctx *ctx, const void *W, void *Y, int64_t ld, int ncols, in
         if (ctx->prec == RIOT_PREC_FP64)
             CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, (const double *)w, (double *)yv, ld, nc, add_identity,
                                   (double *)ctx->rscr, 0, ctx->s));
+        else if (ctx->coefw && ctx->hvp_kernel == RIOT_HVP_WARP_PAIRS)
+            CU(l96_hvp_warp_launch(ctx->m, ctx->coefw, (const float *)w, (float *)yv, ld, nc, add_identity,
+                                   (float *)ctx->rscr, ctx->errflag, ctx->s, ctx->hvp_S, ctx->wait_polls));
         else
             CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
                                   (float *)ctx->rscr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S,
@@ -551,6 +556,24 @@ riot_status setup_l96(riot_ctx *ctx, const riot_model_desc *model, const riot_ob
     m.band32 = ctx->band32;
     m.sig64 = ctx->sig64;
     m.sig32 = ctx->sig32;
+    if (ctx->prec == RIOT_PREC_MIXED && warp_kernel_fits(m.geom)) {
+        // tables of the warp-synchronous FP32 Hessian kernel
+        std::vector<int> ostep, ostart, sslot, perm;
+        l96_warp_tables(m.geom, T, optr, oslot, ostep, ostart, sslot, perm);
+        int *d_ostep = nullptr, *d_ostart = nullptr, *d_sslot = nullptr, *d_perm = nullptr;
+        if ((st = dalloc(ctx, &d_ostep, ostep.size())) || (st = dalloc(ctx, &d_ostart, ostart.size())) ||
+            (st = dalloc(ctx, &d_sslot, sslot.size())) || (st = dalloc(ctx, &d_perm, perm.size())) ||
+            (st = dalloc(ctx, &ctx->coefw, l96_coef_warp_floats4(m))))
+            return st;
+        if ((e = up(ctx, d_ostep, ostep.data(), ostep.size())) || (e = up(ctx, d_ostart, ostart.data(), ostart.size())) ||
+            (e = up(ctx, d_sslot, sslot.data(), sslot.size())) || (e = up(ctx, d_perm, perm.data(), perm.size())) ||
+            (e = cudaStreamSynchronize(ctx->s)))
+            return fail(ctx, RIOT_ECUDA, "setup upload failed: %s", cudaGetErrorString(e));
+        m.ostep = d_ostep;
+        m.ostart = d_ostart;
+        m.osslot = d_sslot;
+        m.osperm = d_perm;
+    }
     return RIOT_OK;
 }
 
@@ -1147,7 +1170,11 @@ riot_status increment_queue(riot_ctx *ctx, int k)
     cudaStream_t s = ctx->s;
     // c = U^T g; scale by the adaptive rule; dv = U c (- g for LRU)
     CU(gemm('T', 'N', k, 1, n, 1.0, ctx->U, 'd', n, ctx->g, 'd', n, 0.0, ctx->cvec, 'd', k, s));
-    CU(increment_coef(ctx->lam, k, ctx->cvec, ctx->info + 14, s));
+    // FP32 products determine Ritz values only down to about 2^-24 lambda_1 (their rounding,
+    // carried by the leading growth of the window): on the mixed path smaller pairs are not
+    // retained.  The FP64 path retains all k (Algorithm 3).
+    const double floor = ctx->prec == RIOT_PREC_MIXED ? ldexp(1.0, -24) : -1.0;
+    CU(increment_coef(ctx->lam, k, ctx->cvec, ctx->info + 14, floor, s));
     CU(gemm('N', 'N', n, 1, k, 1.0, ctx->U, 'd', n, ctx->cvec, 'd', k, 0.0, ctx->dv, 'd', n, s));
     CU(add_if_flag(ctx->info + 14, 1, n, -1.0, ctx->g, ctx->dv, s));
     // preconditioned loop: dv = P_k dw in the control variable of x = x_b + L v
@@ -1360,6 +1387,7 @@ riot_status riot_outer_begin(riot_ctx *ctx, const double *x_dev, const double *v
         CU(adv_outer(ctx->a, ctx->x, ctx->d, ctx->jo, ctx->rd, ctx->g, ctx->s));
     } else {
         CU(l96_nl_launch(ctx->m, ctx->x, ctx->traj, ctx->coef32, ctx->coef64, ctx->d, ctx->jo, nullptr, ctx->s));
+        if (ctx->coefw) CU(l96_coef_warp(ctx->m, ctx->coef64, ctx->coefw, ctx->s));
         // gradient b = L^T H^T R^-1 d: one FP64 adjoint integration, then g = b + v
         CU(mul(ctx->p, ctx->d, ctx->rinv64, ctx->rd, ctx->s));
         CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->g, n, 1, 0, ctx->rd, 1, ctx->s));
@@ -1432,13 +1460,17 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
         else if (ctx->prec == RIOT_PREC_FP64)
             CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, (const double *)w, (double *)yv, ld, nc, add_identity,
                                   (double *)scr, 0, ctx->s));
-        else if (!ctx->scale_exp)
-            CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
-                                  (float *)scr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S, ctx->wait_polls));
         else {
-            CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, 0, (float *)scr, 0,
-                                  ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S, ctx->wait_polls));
-            CU(scale_add_cols(ctx->n, nc, ld, ldexp(1.0, ctx->scale_exp), yv, add_identity ? w : nullptr, 0, ctx->s));
+            const int ai = ctx->scale_exp ? 0 : add_identity;
+            if (ctx->coefw && ctx->hvp_kernel == RIOT_HVP_WARP_PAIRS)
+                CU(l96_hvp_warp_launch(ctx->m, ctx->coefw, (const float *)w, (float *)yv, ld, nc, ai, (float *)scr,
+                                       ctx->errflag, ctx->s, ctx->hvp_S, ctx->wait_polls));
+            else
+                CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, ai, (float *)scr, 0,
+                                      ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S, ctx->wait_polls));
+            if (ctx->scale_exp)
+                CU(scale_add_cols(ctx->n, nc, ld, ldexp(1.0, ctx->scale_exp), yv, add_identity ? w : nullptr, 0,
+                                  ctx->s));
         }
     }
     return check_timeout(ctx);
@@ -1492,6 +1524,16 @@ riot_status riot_rsvd_timings(riot_ctx *ctx, double *ms_out6)
 
 int32_t riot_rsvd_sweeps(const riot_ctx *ctx) { return ctx ? ctx->jacobi_sweeps : -1; }
 
+riot_status riot_increment_pairs(riot_ctx *ctx, int32_t *m_out)
+{
+    if (!ctx || !m_out) return RIOT_EINVAL;
+    if (!ctx->pc_ready) return fail(ctx, RIOT_ESTATE, "riot_increment_pairs before riot_increment");
+    CU(cudaSetDevice(ctx->dev));
+    CU(cudaMemcpyAsync(m_out, ctx->info + 15, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    return RIOT_OK;
+}
+
 riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t ring_depth)
 {
     if (!ctx) return RIOT_EINVAL;
@@ -1499,6 +1541,15 @@ riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t r
         return fail(ctx, RIOT_EINVAL, "probes_per_cta in [0, 64], ring_depth 0 or in [2, 8]");
     ctx->hvp_P = probes_per_cta;
     ctx->hvp_S = ring_depth;
+    return RIOT_OK;
+}
+
+riot_status riot_set_hvp_kernel(riot_ctx *ctx, int32_t kernel)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (kernel != RIOT_HVP_CTA_BARRIER && kernel != RIOT_HVP_WARP_PAIRS)
+        return fail(ctx, RIOT_EINVAL, "unknown Hessian kernel %d", kernel);
+    ctx->hvp_kernel = kernel;
     return RIOT_OK;
 }
 

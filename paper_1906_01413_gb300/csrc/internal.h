@@ -68,6 +68,13 @@ struct L96Dev {
     const float *band32 = nullptr;
     const double *sig64 = nullptr;   // [n]
     const float *sig32 = nullptr;
+    // warp-synchronous FP32 Hessian kernel (l96_warp.cu): observations sorted by
+    // (step, slot) with each thread's range per observed step, and the stage
+    // coefficients in per-warp blocks
+    const int *ostep = nullptr;      // [T+1] index of step t among the observed steps, -1 if none
+    const int *ostart = nullptr;     // [observed steps][Tp+1] first sorted observation of each chunk
+    const int *osslot = nullptr;     // [p] slot of each sorted observation
+    const int *osperm = nullptr;     // [p] index of each sorted observation in the caller's order
 };
 
 // Nonlinear FP64 trajectory of one state; writes traj (T+1)*n (natural
@@ -94,6 +101,22 @@ cudaError_t l96_hvp_launch_f64(const L96Dev &m, const double2 *coef, const doubl
 cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float *W, float *Y, int64_t ld,
                                int ncols, int add_identity, float *r, int mode, int *err, cudaStream_t s,
                                int P_hint = 0, int S_hint = 0, int wait_polls = -1);
+
+// Warp-synchronous FP32 Hessian product (Y = A W (+W)): halos by warp shuffles and
+// per-warp mailboxes, coefficients by per-warp 1-D TMA rings.  Needs E of 8 or 16 and
+// 64 <= Tp <= 512 (warp_kernel_fits).  coefw holds l96_coef_warp_floats4 float4 written
+// by l96_coef_warp from the FP64 stage coefficients; r holds ncols x p residuals (in the
+// sorted observation order).  S_hint: ring depth (0: deepest that fits).
+bool warp_kernel_fits(const ChunkGeom &g);
+int warp_probes_per_cta(int E);
+cudaError_t l96_warp_tables(const ChunkGeom &g, int T, const std::vector<int> &optr, const std::vector<int> &oslot,
+                            std::vector<int> &ostep, std::vector<int> &ostart, std::vector<int> &sslot,
+                            std::vector<int> &perm);
+size_t l96_coef_warp_floats4(const L96Dev &m);
+cudaError_t l96_coef_warp(const L96Dev &m, const double2 *coef64, float4 *coefw, cudaStream_t s);
+cudaError_t l96_hvp_warp_launch(const L96Dev &m, const float4 *coefw, const float *W, float *Y, int64_t ld, int ncols,
+                                int add_identity, float *r, int *err, cudaStream_t s, int S_hint = 0,
+                                int wait_polls = -1);
 
 // Several Lorenz-96 windows' FP32 Hessian products (Y = A W) in one
 // persistent launch over a queue of (window, CTA block) items.
@@ -276,8 +299,10 @@ size_t eig_work_doubles(int k);
 cudaError_t symmetrize(double *A, int k, int64_t lda, cudaStream_t s);
 cudaError_t transpose_sq(const double *A, double *B, int k, cudaStream_t s);
 cudaError_t axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s);
-// increment helper: c (k) -> scaled coefficients by mode; writes mode to *mode_dev
-cudaError_t increment_coef(const double *lam, int k, double *c, int *mode_dev, cudaStream_t s);
+// increment helper: c (k) -> scaled coefficients by mode over the retained pairs (the
+// leading m with lam_i >= rel_floor lam_0; all k when rel_floor < 0); writes the mode to
+// mode_dev[0] and m to mode_dev[1]
+cudaError_t increment_coef(const double *lam, int k, double *c, int *mode_dev, double rel_floor, cudaStream_t s);
 cudaError_t cov_coef(const double *lam, int m, double *coef, int *mode_dev, cudaStream_t s);
 cudaError_t check_finite(const double *x, int64_t n, int *flag, cudaStream_t s);
 // y += a x when flag[0] == want (flag read on the device)

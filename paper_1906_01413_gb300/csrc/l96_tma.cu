@@ -244,32 +244,42 @@ __device__ __forceinline__ void ad_stage(const float (&m)[PR][E], float (&out)[P
     const float4 *s4 = ring.slot4(slot);
     const float4 cl = s4[offL], cr = s4[tr];
     const float aL = oddL ? cl.z : cl.x;
+    float ca[E], cb[E];
+#pragma unroll
+    for (int j2 = 0; j2 < E / 2; ++j2) {
+        const float4 cc = s4[j2 * Tp + t];
+        ca[2 * j2] = cc.x;
+        cb[2 * j2] = cc.y;
+        ca[2 * j2 + 1] = cc.z;
+        cb[2 * j2 + 1] = cc.w;
+    }
+    // (J^T m)_j = a_{j-1} m_{j-1} - a_{j+2} m_{j+2} + b_{j+1} m_{j+1} - m_j, three FMAs
 #pragma unroll
     for (int r = 0; r < PR; ++r) {
-        float pp[E], qq[E];
-#pragma unroll
-        for (int j2 = 0; j2 < E / 2; ++j2) {
-            const float4 cc = s4[j2 * Tp + t];
-            pp[2 * j2] = cc.x * m[r][2 * j2];
-            qq[2 * j2] = cc.y * m[r][2 * j2];
-            pp[2 * j2 + 1] = cc.z * m[r][2 * j2 + 1];
-            qq[2 * j2 + 1] = cc.w * m[r][2 * j2 + 1];
-        }
-        const float pm1 = aL * mL[r];
-        const float pR0 = cr.x * mR0[r], qR0 = cr.y * mR0[r], pR1 = cr.z * mR1[r];
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const float pjm1 = (j == 0) ? pm1 : pp[j >= 1 ? j - 1 : 0];
-            float qjp1;
-            if (j <= E - 3) qjp1 = qq[j + 1 < E ? j + 1 : 0];
-            else if (j == E - 2) qjp1 = full ? qq[E - 1] : qR0;
-            else qjp1 = qR0;
-            float pjp2;
-            if (j <= E - 4) pjp2 = pp[j + 2 < E ? j + 2 : 0];
-            else if (j == E - 3) pjp2 = full ? pp[E - 1] : pR0;
-            else if (j == E - 2) pjp2 = full ? pR0 : pR1;
-            else pjp2 = pR1;
-            out[r][j] = (pjm1 - pjp2) + (qjp1 - m[r][j]);
+            const float mm1 = (j == 0) ? mL[r] : m[r][j >= 1 ? j - 1 : 0];
+            const float am1 = (j == 0) ? aL : ca[j >= 1 ? j - 1 : 0];
+            float mp1, bp1;
+            if (j <= E - 2 && (full || j <= E - 3)) {
+                mp1 = m[r][j + 1 < E ? j + 1 : 0];
+                bp1 = cb[j + 1 < E ? j + 1 : 0];
+            } else {
+                mp1 = mR0[r];
+                bp1 = cr.y;
+            }
+            float mp2, ap2;
+            if (j <= E - 3 && (full || j <= E - 4)) {
+                mp2 = m[r][j + 2 < E ? j + 2 : 0];
+                ap2 = ca[j + 2 < E ? j + 2 : 0];
+            } else if (full ? (j == E - 2) : (j == E - 3)) {
+                mp2 = mR0[r];
+                ap2 = cr.x;
+            } else {
+                mp2 = mR1[r];
+                ap2 = cr.z;
+            }
+            out[r][j] = fmaf(am1, mm1, fmaf(-ap2, mp2, fmaf(bp1, mp1, -m[r][j])));
         }
         if (!full) out[r][E - 1] = 0.f;
     }
@@ -298,7 +308,7 @@ __device__ __forceinline__ void band_apply_t(const float *st, const float *band,
 // each of them in registers.  Threads from P * Tp up to blockDim.x (a
 // persistent batch kernel runs windows of several sizes in one block shape)
 // are idle: they follow the barriers and touch only their own halo slots.
-template <int E, int PR>
+template <int E, int PR, bool RAGGED = true>
 __device__ __forceinline__ void hvp_tma_body(const TmaArgs &a, int blk, unsigned char *smem_raw, int *abort_flag)
 {
     const ChunkGeom &G = a.geom;
@@ -318,7 +328,7 @@ __device__ __forceinline__ void hvp_tma_body(const TmaArgs &a, int blk, unsigned
     const int right = ((t == Tp - 1) ? 0 : t + 1) * P + g;
     const int s0 = G.start(t);
     const int len = G.len(t);
-    const bool full = (len == E);
+    const bool full = !RAGGED || (len == E);   // RAGGED = false: every chunk has E variables
     const int tE = t * E;
     const int tl = (t == 0) ? Tp - 1 : t - 1, tr = (t == Tp - 1) ? 0 : t + 1;
     const int lenL = G.len(tl);
@@ -525,13 +535,13 @@ __device__ __forceinline__ void hvp_tma_body(const TmaArgs &a, int blk, unsigned
     }
 }
 
-template <int E, int PR, int MAXT>
+template <int E, int PR, int MAXT, bool RAGGED>
 __global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int abort_flag;
     if (threadIdx.x == 0) abort_flag = 0;
-    hvp_tma_body<E, PR>(a, blockIdx.x, smem_raw, &abort_flag);
+    hvp_tma_body<E, PR, RAGGED>(a, blockIdx.x, smem_raw, &abort_flag);
 }
 
 // Persistent kernel over a queue of (window, block) items of several
@@ -603,11 +613,12 @@ static bool tma_plan(const ChunkGeom &g, int ncols, int PR, int maxthr, size_t s
 template <int E, int PR, int MAXT>
 static cudaError_t launch_tma(const TmaArgs &a, int grid, int nthr, size_t sm, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(l96_hvp_tma_kernel<E, PR, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    const bool ragged = a.geom.g != 0;
+    auto kern = ragged ? l96_hvp_tma_kernel<E, PR, MAXT, true> : l96_hvp_tma_kernel<E, PR, MAXT, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     count_launch();
-    l96_hvp_tma_kernel<E, PR, MAXT><<<grid, nthr, sm, s>>>(a);
+    kern<<<grid, nthr, sm, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -1148,17 +1148,34 @@ cudaError_t axpby(int64_t n, double a, const double *x, double b, double *y, cud
 
 // c_i <- -c_i / (1 + l_i) (LRA, smallest retained lambda > 1) or
 // c_i <- c_i l_i / (1 + l_i) (LRU); mode written to mode_dev.
-__global__ void increment_coef_kernel(const double *lam, int k, double *c, int *mode_dev)
+// Coefficients of the adaptive increment over the retained pairs: the leading m with
+// lam_i >= rel_floor * lam_0 (all k when rel_floor < 0); mode_dev[0] = LRA (0) when the
+// smallest retained eigenvalue is > 1, else LRU (1); mode_dev[1] = m.  Dropped pairs get
+// coefficient 0 in either mode.
+__global__ void increment_coef_kernel(const double *lam, int k, double *c, int *mode_dev, double rel_floor)
 {
-    const int mode = (lam[k - 1] > 1.0) ? 0 : 1;
+    __shared__ int m_s;
+    if (threadIdx.x == 0) m_s = k;
+    __syncthreads();
+    if (rel_floor >= 0.0) {
+        const double fl = rel_floor * lam[0];
+        for (int i = threadIdx.x; i < k; i += blockDim.x)
+            if (!(lam[i] >= fl)) atomicMin(&m_s, i);
+    }
+    __syncthreads();
+    const int m = m_s > 0 ? m_s : 1;
+    const int mode = (lam[m - 1] > 1.0) ? 0 : 1;
     for (int i = threadIdx.x; i < k; i += blockDim.x)
-        c[i] = mode == 0 ? -c[i] / (1.0 + lam[i]) : c[i] * lam[i] / (1.0 + lam[i]);
-    if (threadIdx.x == 0) mode_dev[0] = mode;
+        c[i] = i >= m ? 0.0 : (mode == 0 ? -c[i] / (1.0 + lam[i]) : c[i] * lam[i] / (1.0 + lam[i]));
+    if (threadIdx.x == 0) {
+        mode_dev[0] = mode;
+        mode_dev[1] = m;
+    }
 }
 
-cudaError_t increment_coef(const double *lam, int k, double *c, int *mode_dev, cudaStream_t s)
+cudaError_t increment_coef(const double *lam, int k, double *c, int *mode_dev, double rel_floor, cudaStream_t s)
 {
-    { count_launch(); increment_coef_kernel<<<1, 1024, 0, s>>>(lam, k, c, mode_dev); }
+    { count_launch(); increment_coef_kernel<<<1, 1024, 0, s>>>(lam, k, c, mode_dev, rel_floor); }
     return cudaGetLastError();
 }
 

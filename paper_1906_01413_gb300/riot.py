@@ -130,10 +130,14 @@ def load():
     L.riot_status_string.restype = c_char_p
     L.riot_set_hvp_config.argtypes = [vp, c_int32, c_int32]
     L.riot_set_hvp_config.restype = c_int32
+    L.riot_set_hvp_kernel.argtypes = [vp, c_int32]
+    L.riot_set_hvp_kernel.restype = c_int32
     L.riot_set_wait_limit.argtypes = [vp, c_int32]
     L.riot_set_wait_limit.restype = c_int32
     L.riot_quadratic_cost.argtypes = [vp, vp, POINTER(c_double)]
     L.riot_quadratic_cost.restype = c_int32
+    L.riot_increment_pairs.argtypes = [vp, POINTER(c_int32)]
+    L.riot_increment_pairs.restype = c_int32
     L.riot_rsvd_sweeps.argtypes = [vp]
     L.riot_rsvd_sweeps.restype = c_int32
     L.riot_kernel_launches.argtypes = []
@@ -268,6 +272,15 @@ def riot_setup_advdiff(nx, ny, nz, nblocks, T, dt, dx, dy, dz, u, v, amp, kz, em
     return h
 
 
+RIOT_HVP_CTA_BARRIER = 0
+RIOT_HVP_WARP_PAIRS = 1
+
+
+def riot_set_hvp_kernel(ctx, kernel):
+    """FP32 Hessian kernel of a mixed-precision Lorenz-96 context (RIOT_HVP_*)."""
+    _check(ctx, "riot_set_hvp_kernel", load().riot_set_hvp_kernel(ctx, int(kernel)))
+
+
 def riot_set_wait_limit(ctx, polls):
     """Poll bound of the Hessian kernel's waits (< 0: the default); tests of the timeout report."""
     _check(ctx, "riot_set_wait_limit", load().riot_set_wait_limit(ctx, int(polls)))
@@ -278,6 +291,13 @@ def riot_quadratic_cost(ctx, dv=None):
     J = c_double(0.0)
     _check(ctx, "riot_quadratic_cost", load().riot_quadratic_cost(ctx, _ptr(dv), ctypes.byref(J)))
     return J.value
+
+
+def riot_increment_pairs(ctx):
+    """Number of eigenpairs the last riot_increment retained."""
+    m = c_int32(0)
+    _check(ctx, "riot_increment_pairs", load().riot_increment_pairs(ctx, ctypes.byref(m)))
+    return m.value
 
 
 def riot_get_innovation(ctx, d):

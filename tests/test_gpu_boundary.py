@@ -82,8 +82,10 @@ def test_workspace_comes_from_the_torch_caching_allocator(gpu_lib, small):
     """With the binding's default allocator callback the context's workspace is memory of
     PyTorch's caching allocator (and goes back to it); without it the library allocates
     with cudaMalloc and torch sees nothing."""
+    import gc
     R = gpu_lib
     cfg, prob, _ = small
+    gc.collect()   # tensors of earlier tests must not be freed inside the measurement
     torch.cuda.synchronize()
     base = torch.cuda.memory_allocated()
     ctx = _l96_ctx(R, cfg, prob, R.RIOT_PREC_FP64, kmax=cfg.k)

@@ -154,21 +154,31 @@ def test_hvp_fp64_ragged_sizes(gpu_lib, n, T, every, frac, dup):
 
 @pytest.mark.parametrize("n,T,every,frac,dup", [(16, 4, 1, 1.0, False), (41, 9, 2, 0.3, True),
                                                 (100, 13, 3, 0.5, False), (257, 7, 1, 0.1, True),
+                                                (1000, 6, 2, 0.25, False), (1001, 5, 1, 0.3, True),
+                                                (2047, 4, 1, 0.2, False),
                                                 (4096, 6, 2, 0.25, False), (5001, 5, 1, 0.05, True),
                                                 (8192, 3, 1, 0.1, False)])
-def test_hvp_fp32_ragged_sizes(gpu_lib, n, T, every, frac, dup):
-    # FP32 kernel with streamed stage coefficients: every chunk width (E = 4, 8,
-    # 16), ragged last chunks, duplicate observations and several probes per CTA.
+@pytest.mark.parametrize("kernel", ["cta_barrier", "warp_pairs"])
+def test_hvp_fp32_ragged_sizes(gpu_lib, n, T, every, frac, dup, kernel):
+    # FP32 kernels with streamed stage coefficients: every chunk width (E = 4, 8,
+    # 16), ragged last chunks, a last warp with fewer than 32 live lanes (n = 1000,
+    # 1001), duplicate observations and several probes per CTA.  "cta_barrier" is
+    # the default kernel, "warp_pairs" the one whose warps meet only their
+    # neighbours (where it fits, n >= 1000 here; elsewhere the default runs).
     R = gpu_lib
     sv = 0.5 + np.arange(n) / n
     prob = _random_problem(n, T, 2.5, frac, every, seed=n + 1, sigma_vec=sv, dup=dup)
     traj = orc.trajectory(prob, prob.x_b)
     ctx = _ctx(R, prob, 2.5, sigma_vec=sv, kmax=16, precision=R.RIOT_PREC_MIXED)
+    if kernel == "warp_pairs":
+        R.riot_set_hvp_kernel(ctx.h, R.RIOT_HVP_WARP_PAIRS)
     R.riot_outer_begin(ctx.h, _t(prob.x_b))
     W = np.random.default_rng(2).standard_normal((n, 13)).astype(np.float32).astype(np.float64)
     ref = orc.hvp(prob, traj, W)
     Y = _hvp_gpu(R, ctx, W, torch.float32)
     assert _col_rel_err(Y, ref).max() < 2e-5
+    Y1 = _hvp_gpu(R, ctx, W, torch.float32, add_identity=True)
+    assert _col_rel_err(Y1, ref + W).max() < 2e-5
     ctx.close()
 
 
@@ -314,7 +324,14 @@ def test_mixed_precision_small(gpu_lib, small):
     rel = np.abs(lam - st["lam"]) / st["lam"][0]
     assert rel.max() < 1e-4
     assert (np.abs(lam[lead] - st["lam"][lead]) / st["lam"][lead]).max() < 1e-3
-    assert np.linalg.norm(dv - st["dv"]) <= 1e-3 * np.linalg.norm(st["dv"])
+    # An FP32 product carries an absolute error near 2^-24 lambda_1 in every direction, so the
+    # eigenvalues below it (here down to 6e-8, against 2^-24 lambda_1 = 1.7e-4) are not
+    # resolved and the LRU weights lambda / (1 + lambda) of those directions are off by up to
+    # that much: the increment's relative error is bounded by about 2^-24 lambda_1, not by the
+    # 1e-4 asked (rounding only the oracle's products to FP32 already gives 5.8e-5).  The cost
+    # reduction, second order in that error, is held to 1e-6 (test_gpu_boundary).
+    bound = 2.0 * 2.0 ** -24 * st["lam"][0]
+    assert np.linalg.norm(dv - st["dv"]) <= bound * np.linalg.norm(st["dv"])
     ctx.close()
 
 
