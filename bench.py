@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batch of 96 windows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned sketch proposal leg")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned inner-loop leg")
+    ap.add_argument("--no-deflated", action="store_true", help="skip the deflated multi-level mixed-precision leg")
     ap.add_argument("--clock-log", default=None,
                     help="CSV of the nvidia-smi clock samples taken during the timed steps (%%d: rank); "
                          "default: a file in the temporary directory")
@@ -162,8 +163,9 @@ def build_problem(R, torch, cfg, dev, precision, kmax):
     return workloads.l96_twin(R, torch, cfg, dev, precision, kmax)
 
 
-def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False):
+def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False, k=None):
     """Per-step CUDA-event times of riot_rsvd + riot_increment (L2 flushed between steps)."""
+    k = cfg.k if k is None else k
     s = torch.cuda.current_stream()
     times, phases = [], []
     for i in range(warmup + steps):
@@ -174,7 +176,7 @@ def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False)
             torch.cuda.profiler.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        lam = R.riot_rsvd(ctx.h, cfg.k, cfg.q, sketch_stream=configs.STREAM_SKETCH0)
+        lam = R.riot_rsvd(ctx.h, k, cfg.q, sketch_stream=configs.STREAM_SKETCH0)
         mode = R.riot_increment(ctx.h, dv)
         e1.record(s)
         torch.cuda.synchronize()
@@ -186,6 +188,43 @@ def time_inner_loop(R, torch, ctx, cfg, steps, warmup, flush, dv, profile=False)
             ph["jacobi_sweeps"] = R.riot_rsvd_sweeps(ctx.h)
             phases.append(ph)
     return times, phases, lam, mode
+
+
+DEFLATED_LEVELS = (256, 320)
+
+
+def bench_deflated(R, torch, cfg, dev, flush, warmup, steps, levels=DEFLATED_LEVELS):
+    """The deflated multi-level mixed-precision eigendecomposition (riot_rsvd_deflated) plus the
+    increment on the same window: per-step CUDA-event times, the cost reduction of its increment
+    (Eq. 3 in FP64) and its pairs."""
+    kmax = sum(levels)
+    ctx, xb, _ = build_problem(R, torch, cfg, dev, R.RIOT_PREC_MIXED, kmax)
+    R.riot_outer_begin(ctx.h, xb)
+    dv = torch.empty(cfg.n, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream()
+    times = []
+    for i in range(warmup + steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        lam = R.riot_rsvd_deflated(ctx.h, list(levels), cfg.q, 0.0, configs.STREAM_SKETCH0, kmax=kmax)
+        mode = R.riot_increment(ctx.h, dv)
+        e1.record(s)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            times.append(e0.elapsed_time(e1))
+    red = R.riot_quadratic_cost(ctx.h) - R.riot_quadratic_cost(ctx.h, dv)
+    ph = R.riot_rsvd_timings(ctx.h)
+    ctx.close()
+    ms = statistics.mean(times)
+    hvps = (cfg.q + 1) * sum(levels)
+    return {"what": "riot_rsvd_deflated: levels of %s columns, q = %d, each on the operator deflated by the "
+                    "pairs kept before (FP32 products, two-pass FP32 projections), then riot_increment"
+                    % (list(levels), cfg.q),
+            "ms_per_step": ms, "hvps_per_step": hvps, "value": hvps / (ms * 1e-3), "unit": UNIT,
+            "pairs": int(lam.size), "mode": int(mode), "lambda1": float(lam[0]), "lambda_min": float(lam[-1]),
+            "cost_reduction": red, "phases_ms": ph}
 
 
 def bench_precond(R, torch, ctx, xb, cfg, flush, dv, warmup, steps, plain_ms):
@@ -721,6 +760,10 @@ def main():
 
     ph = {key: statistics.mean(p_[key] for p_ in phases) for key in phases[0]}
     hvp_launch_ms = ph["hvp"] / (q + 1)
+    # cost reduction J~(0) - J~(dv) of the mixed increment (Eq. 3, FP64 tangent-linear pass)
+    red_mixed = R.riot_quadratic_cost(ctx.h) - R.riot_quadratic_cost(ctx.h, dv)
+    pairs_mixed = R.riot_increment_pairs(ctx.h)
+    dv_mixed = dv.double().cpu().numpy().copy()
     taps = band_width(n, cfg.ell)
     flop_hvp = hvp_flops(n, T, p, taps)
     achieved = flop_hvp * k / (hvp_launch_ms * 1e-3) / 1e12
@@ -768,21 +811,65 @@ def main():
     if not args.no_bc:
         bc = bench_bc_transport(R, torch, dev, flush, float(peaks.get("hbm_gbs", 6800.0)))
 
+    # ---- deflated multi-level mixed precision (the same window) --------------------------
+    deflated = None
+    if not args.no_deflated:
+        ctx.close()
+        ctx = None
+        deflated = bench_deflated(R, torch, cfg, dev, flush, 1, max(3, args.steps // 3))
+
     # ---- plain FP64 GPU form -----------------------------------------------------------
     fp64 = None
-    if args.fp64_steps > 0:
+    if ctx is not None:
         ctx.close()
+    if args.fp64_steps > 0:
         ctx64, xb64, _ = build_problem(R, torch, cfg, dev, R.RIOT_PREC_FP64, k)
         R.riot_outer_begin(ctx64.h, xb64)
-        t64, ph64, lam64, _ = time_inner_loop(R, torch, ctx64, cfg, args.fp64_steps, 1, flush, dv)
+        t64, ph64, lam64, mode64 = time_inner_loop(R, torch, ctx64, cfg, args.fp64_steps, 1, flush, dv)
         ms64 = statistics.mean(t64)
+        red64 = R.riot_quadratic_cost(ctx64.h) - R.riot_quadratic_cost(ctx64.h, dv)
+        dv64 = dv.double().cpu().numpy()
+        lead = lam64 >= 2.0 ** -24 * lam64[0]
         fp64 = {"ms_per_step": ms64, "value": hvps_per_step / (ms64 * 1e-3), "unit": UNIT,
                 "hvp_ms": statistics.mean(p_["hvp"] for p_ in ph64),
+                "mode": int(mode64), "cost_reduction": red64,
                 "speedup_of_mixed": ms64 / ms,
-                "lambda1_rel_diff_mixed_vs_fp64": float(abs(lam[0] - lam64[0]) / abs(lam64[0]))}
+                "lambda1_rel_diff_mixed_vs_fp64": float(abs(lam[0] - lam64[0]) / abs(lam64[0])),
+                "leading_lambda_rel_diff_mixed_vs_fp64": float(np.max(np.abs(lam[lead] - lam64[lead]) / lam64[lead])),
+                "leading_lambdas": int(lead.sum()),
+                "increment_rel_diff_mixed_vs_fp64": float(np.linalg.norm(dv_mixed - dv64) / np.linalg.norm(dv64)),
+                "cost_reduction_rel_diff_mixed_vs_fp64": float(abs(red_mixed - red64) / abs(red64))}
+        if deflated:
+            # the FP64 form at the sketch size whose increment reaches the deflated path's reduction
+            # (the reduction grows about linearly with k on this window: every pair adds a similar
+            # share), to compare wall times at the same cost-function reduction
+            target = deflated["cost_reduction"]
+            k_eq = int(min(k, max(64, 8 * round(k * target / red64 / 8))))
+            t_eq, _, _, _ = time_inner_loop(R, torch, ctx64, cfg, args.fp64_steps, 1, flush, dv, k=k_eq)
+            red_eq = R.riot_quadratic_cost(ctx64.h) - R.riot_quadratic_cost(ctx64.h, dv)
+            # one secant step between (k_eq, red_eq) and (k, red64) towards the target
+            if k_eq < k and red64 != red_eq and abs(red_eq - target) > 0.005 * target:
+                k2 = int(min(k, max(64, 8 * round((k_eq + (target - red_eq) * (k - k_eq) / (red64 - red_eq)) / 8))))
+                if k2 != k_eq:
+                    t2, _, _, _ = time_inner_loop(R, torch, ctx64, cfg, args.fp64_steps, 1, flush, dv, k=k2)
+                    red2 = R.riot_quadratic_cost(ctx64.h) - R.riot_quadratic_cost(ctx64.h, dv)
+                    if abs(red2 - target) < abs(red_eq - target):
+                        k_eq, t_eq, red_eq = k2, t2, red2
         ctx64.close()
-    else:
-        ctx.close()
+        fp64["equal_reduction"] = {
+            "fp64": {"ms": ms64, "cost_reduction": red64},
+            "mixed_plain": {"ms": ms, "cost_reduction": red_mixed, "pairs": pairs_mixed,
+                            "reduction_ratio": red_mixed / red64},
+        }
+        if deflated:
+            fp64["equal_reduction"]["mixed_deflated"] = {
+                "ms": deflated["ms_per_step"], "cost_reduction": deflated["cost_reduction"],
+                "pairs": deflated["pairs"], "reduction_ratio": deflated["cost_reduction"] / red64,
+                "speedup_vs_fp64_k512": ms64 / deflated["ms_per_step"]}
+            fp64["equal_reduction"]["fp64_at_equal_reduction"] = {
+                "k": k_eq, "ms": statistics.mean(t_eq), "cost_reduction": red_eq,
+                "deflated_mixed_speedup": statistics.mean(t_eq) / deflated["ms_per_step"],
+                "deflated_reduction_over_this": deflated["cost_reduction"] / red_eq}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -802,6 +889,9 @@ def main():
                     "d2h_bytes_per_step": int(n * 8 + k * 8)},
             "gpu_launches": int(launches),
             "wall_s_timed": wall}
+    line["mixed_cost_reduction"] = {"value": red_mixed, "pairs_retained": pairs_mixed}
+    if deflated:
+        line["deflated_mixed"] = deflated
     if fp64:
         line["fp64_gpu_form"] = fp64
     if bc:

@@ -235,6 +235,39 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
 riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream,
                       const void *Omega_dev, double *lambda_out);
 
+/* Deflated multi-level randomized eigendecomposition for mixed-precision
+ * contexts (an extension of Algorithm 3 for FP32 Hessian products; the paper
+ * has no counterpart).  An FP32 product carries an absolute error of about
+ * 2^-24 lambda_1 |w|, so riot_rsvd in RIOT_PREC_MIXED resolves only the pairs
+ * above that; on strongly unstable windows the rest of the spectrum carries
+ * much of the cost reduction.  That error lies almost entirely in the leading
+ * eigen-directions, so projecting them out recovers the next part of the
+ * spectrum.  Level l = 0 .. nlevels-1 runs Algorithm 3 (q power iterations)
+ * with min(kcols[l], kmax - m, n - m) columns of a sketch of its own (Philox
+ * stream sketch_stream with its top four bits replaced by l) on the deflated
+ * operator P A P, P = I - U U^T with U the m pairs kept by the levels before
+ * (P = I at level 0); every block is projected by P, in two passes of FP32
+ * tensor-core GEMMs, before and after each FP32 Hessian product.  A level
+ * keeps its leading pairs with lambda >= rel_floor times its largest one
+ * (rel_floor <= 0: 2^-24, the absolute error of its FP32 products of unit
+ * vectors) and, after level 0, above 1.  The levels stop early when one's
+ * largest eigenvalue is below 1 or below 2^-53 lambda_1 (unresolved even by
+ * FP64 products).  The m pairs of all levels, sorted by decreasing
+ * eigenvalue, become the context's pairs for riot_increment and
+ * riot_analysis_cov_lowrank (all m are retained).  lambda_out (host, room for
+ * kmax doubles, may be NULL) and m_out (may be NULL) receive them;
+ * synchronises.  1 <= nlevels <= 8; 1 <= kcols[0] <= min(kmax, n); later
+ * kcols in [0, kmax].  Requires riot_outer_begin and a RIOT_PREC_MIXED
+ * context without spectral preconditioner.
+ * Measured on 4096-variable, 200-step windows (spectra over twelve to
+ * thirteen decades): two levels ({256, 320}) reach 0.93 to 1.01 of the cost
+ * reduction of the FP64 rank-512 increment; deeper levels reach eigenvalues
+ * whose FP32 Ritz vectors are no longer accurate (the part of the products'
+ * error outside the kept subspace is then of their size) and the increment's
+ * cost rises, so two levels are the depth to use. */
+riot_status riot_rsvd_deflated(riot_ctx *ctx, int32_t nlevels, const int32_t *kcols, int32_t q, double rel_floor,
+                               int64_t sketch_stream, double *lambda_out, int32_t *m_out);
+
 /* Adaptive increment (Algorithm 3, Eqs. 8-11): with c = U^T g over the
  * retained pairs,
  * LRA (mode 0) when the smallest retained eigenvalue is > 1:

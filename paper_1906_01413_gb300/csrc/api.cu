@@ -11,6 +11,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -66,6 +67,12 @@ struct riot_ctx {
     int *info = nullptr;  // [0..9] CholeskyQR passes, [10] K Cholesky, [12..13] Jacobi, [14] mode
     int *errflag = nullptr;  // set by a kernel whose bounded wait ran out
     int have_traj = 0, have_rsvd = 0, k_last = 0, v_init = 0, jacobi_sweeps = 0;
+    // deflated two-level eigendecomposition (riot_rsvd_deflated), allocated at its first call:
+    // the level-1 Ritz vectors kept (FP64 and FP32), then the combined pairs before sorting
+    int deflated = 0;   // the current pairs came from riot_rsvd_deflated (all are retained)
+    double *Ud64 = nullptr;
+    float *Ud32 = nullptr;
+    int *perm = nullptr;
     // FP32 Hessian products are formed as 2^-scale_exp A (R^-1 scaled by 2^-scale_rinv in
     // rinv32, the input and output by 2^-scale_in through sig32) so that windows whose
     // tangent-linear growth exceeds the FP32 range stay finite; eigenvalues are scaled
@@ -1172,8 +1179,9 @@ riot_status increment_queue(riot_ctx *ctx, int k)
     CU(gemm('T', 'N', k, 1, n, 1.0, ctx->U, 'd', n, ctx->g, 'd', n, 0.0, ctx->cvec, 'd', k, s));
     // FP32 products determine Ritz values only down to about 2^-24 lambda_1 (their rounding,
     // carried by the leading growth of the window): on the mixed path smaller pairs are not
-    // retained.  The FP64 path retains all k (Algorithm 3).
-    const double floor = ctx->prec == RIOT_PREC_MIXED ? ldexp(1.0, -24) : -1.0;
+    // retained.  The FP64 path retains all k (Algorithm 3); the deflated eigendecomposition
+    // has already applied the rule level by level.
+    const double floor = (ctx->prec == RIOT_PREC_MIXED && !ctx->deflated) ? ldexp(1.0, -24) : -1.0;
     CU(increment_coef(ctx->lam, k, ctx->cvec, ctx->info + 14, floor, s));
     CU(gemm('N', 'N', n, 1, k, 1.0, ctx->U, 'd', n, ctx->cvec, 'd', k, 0.0, ctx->dv, 'd', n, s));
     CU(add_if_flag(ctx->info + 14, 1, n, -1.0, ctx->g, ctx->dv, s));
@@ -1486,6 +1494,7 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
     ctx->nev = 0;
     ctx->pc_ready = 0;
     ctx->pc_open = 0;
+    ctx->deflated = 0;
     ev_mark(ctx, -1);
     TRY(rsvd_begin(ctx, k, sketch_stream, Omega_dev));
     ev_mark(ctx, 0);
@@ -1500,6 +1509,115 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
     ev_mark(ctx, -2);
     TRY(rsvd_retry_k(ctx, k, lambda_out, rsvd_collect(ctx, k, lambda_out)));
     ctx->pc_open = 1;
+    return RIOT_OK;
+}
+
+// X (n x kcols FP32, ld n) <- (I - U1 U1^T) X with U1 the first m1 columns of Ud32, in two
+// passes (tensor-core FP32 GEMMs).  A Hessian product of a projected block is dominated by its
+// leftover U1 components (amplified by lambda_1); one FP32 pass leaves about 2^-24 sqrt(n) of
+// them, still above the smallest directions of the deflated operator, and a second pass takes
+// that leftover down by the same factor again (reorthogonalisation: twice is enough).
+static riot_status deflate_project(riot_ctx *ctx, float *X, int kcols, int m1)
+{
+    const int n = ctx->n;
+    for (int pass = 0; pass < 2; ++pass) {
+        CU(sketch_gemm(ctx, 'T', 'N', m1, kcols, n, ctx->Ud32, n, X, n, ctx->N32, m1));
+        CU(sketch_gemm(ctx, 'N', 'N', n, kcols, m1, ctx->Ud32, n, ctx->N32, m1, X, n, -1.f, 1.f));
+    }
+    return RIOT_OK;
+}
+
+riot_status riot_rsvd_deflated(riot_ctx *ctx, int32_t nlevels, const int32_t *kcols, int32_t q, double rel_floor,
+                               int64_t sketch_stream, double *lambda_out, int32_t *m_out)
+{
+    if (!ctx) return RIOT_EINVAL;
+    if (ctx->prec != RIOT_PREC_MIXED) return fail(ctx, RIOT_EINVAL, "riot_rsvd_deflated: mixed-precision contexts only");
+    if (!ctx->pc_m.empty()) return fail(ctx, RIOT_ESTATE, "riot_rsvd_deflated: not with the spectral preconditioner");
+    if (nlevels < 1 || nlevels > 8 || !kcols) return fail(ctx, RIOT_EINVAL, "nlevels = %d outside [1, 8]", nlevels);
+    TRY(rsvd_check_args(ctx, kcols[0], q));
+    for (int l = 1; l < nlevels; ++l)
+        if (kcols[l] < 0 || kcols[l] > ctx->kmax) return fail(ctx, RIOT_EINVAL, "kcols[%d] = %d outside [0, kmax]", l, kcols[l]);
+    if (ctx->pc_dirty) return fail(ctx, RIOT_ESTATE, "riot_rsvd after riot_precond_push needs riot_outer_begin first");
+    // default floor: 2^-24 of the level's largest eigenvalue, the absolute error of a level's
+    // FP32 products of unit vectors
+    const double fl = rel_floor > 0.0 ? rel_floor : ldexp(1.0, -24);
+    CU(cudaSetDevice(ctx->dev));
+    const int n = ctx->n;
+    cudaStream_t s = ctx->s;
+    if (!ctx->Ud64) {
+        riot_status st;
+        if ((st = dalloc(ctx, &ctx->Ud64, (size_t)n * ctx->kmax)) || (st = dalloc(ctx, &ctx->Ud32, (size_t)n * ctx->kmax)) ||
+            (st = dalloc(ctx, &ctx->perm, (size_t)ctx->kmax))) {
+            ctx->Ud64 = nullptr;
+            return st;
+        }
+    }
+    ctx->nev = 0;
+    ctx->pc_ready = 0;
+    ctx->pc_open = 0;
+    ctx->deflated = 0;
+    float *W32 = (float *)ctx->Wblk, *Y32 = (float *)ctx->Yblk;
+    std::vector<double> lam_all;
+    int m = 0;   // pairs kept so far: columns [0, m) of Ud64 (FP64) and Ud32 (FP32)
+    ev_mark(ctx, -1);
+    for (int l = 0; l < nlevels; ++l) {
+        int kl = kcols[l];
+        if (kl > ctx->kmax - m) kl = ctx->kmax - m;
+        if (kl > n - m) kl = n - m;
+        if (kl < 1) break;
+        // level l: Algorithm 3 on P A P, P = I - U_m U_m^T the projector off the pairs kept so
+        // far (the identity at level 0), from a sketch of its own (stream sketch_stream, its
+        // top bits replaced by the level)
+        CU(cudaMemsetAsync(ctx->info, 0, sizeof(int) * 32, s));
+        TRY(clear_timeout(ctx));
+        CU(normal_launch(ctx->seed, (uint32_t)sketch_stream ^ ((uint32_t)l << 28), n, kl, n, 0, W32, s));
+        if (m > 0) TRY(deflate_project(ctx, W32, kl, m));
+        ev_mark(ctx, 0);
+        TRY(hvp(ctx, W32, Y32, n, kl, 0));
+        if (m > 0) TRY(deflate_project(ctx, Y32, kl, m));
+        for (int it = 0; it < q; ++it) {
+            ev_mark(ctx, 1);
+            TRY(rsvd_power(ctx, kl));
+            if (m > 0) TRY(deflate_project(ctx, W32, kl, m));
+            ev_mark(ctx, 0);
+            TRY(hvp(ctx, W32, Y32, n, kl, 0));
+            if (m > 0) TRY(deflate_project(ctx, Y32, kl, m));
+        }
+        TRY(rsvd_end(ctx, kl, true));
+        std::vector<double> lam(kl);
+        TRY(rsvd_retry_k(ctx, kl, lam.data(), rsvd_collect(ctx, kl, lam.data())));
+        // a level whose largest eigenvalue is below 1, or below what even FP64 products resolve
+        // (2^-53 lambda_1), adds nothing: stop
+        if (l > 0 && !(lam[0] > 1.0 && lam[0] > ldexp(lam_all[0], -53))) break;
+        // keep the pairs this level's FP32 products resolve: lambda >= rel_floor * its largest
+        // (and > 1 after level 0, so that the adaptive rule keeps LRA where level 0 had it)
+        int ml = 0;
+        while (ml < kl && lam[ml] >= fl * lam[0] && (l == 0 || lam[ml] > 1.0)) ++ml;
+        if (l == 0 && ml < 1) ml = 1;
+        if (ml == 0) break;
+        CU(cudaMemcpyAsync(ctx->Ud64 + (size_t)n * m, ctx->U, sizeof(double) * (size_t)n * ml, cudaMemcpyDeviceToDevice,
+                           s));
+        if (l + 1 < nlevels) CU(convert_block(ctx->U, 'd', n, ctx->Ud32 + (size_t)n * m, 'f', n, n, ml, s));
+        lam_all.insert(lam_all.end(), lam.begin(), lam.begin() + ml);
+        m += ml;
+    }
+    // ---- the pairs of every level, by decreasing eigenvalue
+    std::vector<int> perm(m);
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return lam_all[a] > lam_all[b]; });
+    std::vector<double> lam_sorted(m);
+    for (int i = 0; i < m; ++i) lam_sorted[i] = lam_all[perm[i]];
+    CU(cudaMemcpyAsync(ctx->perm, perm.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ctx->lam, lam_sorted.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CU(gather_cols(ctx->Ud64, n, ctx->perm, m, n, ctx->U, n, s));
+    ev_mark(ctx, -2);
+    CU(cudaStreamSynchronize(s));   // the host arrays go out of scope
+    ctx->k_last = m;
+    ctx->have_rsvd = 1;
+    ctx->deflated = 1;
+    ctx->pc_open = 1;
+    if (lambda_out) memcpy(lambda_out, lam_sorted.data(), sizeof(double) * m);
+    if (m_out) *m_out = m;
     return RIOT_OK;
 }
 
@@ -2083,6 +2201,7 @@ riot_status riot_rsvd_proposal(riot_ctx *ctx, int32_t k, int32_t q, int64_t sket
     cudaStream_t s = ctx->s;
     float *W32 = (float *)ctx->Wblk, *Y32 = (float *)ctx->Yblk;
     ctx->nev = 0;
+    ctx->deflated = 0;
     ev_mark(ctx, -1);
     int used = 0;
     double rho = -1.0;

@@ -335,6 +335,9 @@ cudaError_t scale_rows(int m, int ncols, int64_t ld, const double *coef, void *T
 // Y = a X + b Y on n rows of ncols columns at ld, float or double
 cudaError_t axpby_cols(int64_t n, int ncols, int64_t ld, double a, const void *X, double b, void *Y, int is_double,
                        cudaStream_t s);
+// out[:, j] = in[:, perm[j]] for m columns of n doubles (perm on the device; out must not alias in)
+cudaError_t gather_cols(const double *in, int64_t ldi, const int *perm, int m, int64_t n, double *out, int64_t ldo,
+                        cudaStream_t s);
 // largest-magnitude entry of each of the k columns made positive
 cudaError_t fix_col_signs(double *U, int64_t n, int k, int64_t ld, cudaStream_t s);
 

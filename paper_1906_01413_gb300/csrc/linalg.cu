@@ -1422,6 +1422,27 @@ cudaError_t obs_quad_cost(int64_t p, const double *d, const double *r, const dou
     return cudaGetLastError();
 }
 
+// out[:, j] = in[:, perm[j]] for m columns of n doubles
+__global__ void gather_cols_kernel(const double *in, int64_t ldi, const int *perm, int m, int64_t n, double *out,
+                                   int64_t ldo)
+{
+    const int j = blockIdx.y;
+    const double *src = in + (int64_t)perm[j] * ldi;
+    double *dst = out + (int64_t)j * ldo;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+cudaError_t gather_cols(const double *in, int64_t ldi, const int *perm, int m, int64_t n, double *out, int64_t ldo,
+                        cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    int bx = (int)((n + 255) / 256);
+    if (bx > 64) bx = 64;
+    { count_launch(); gather_cols_kernel<<<dim3(bx, m), 256, 0, s>>>(in, ldi, perm, m, n, out, ldo); }
+    return cudaGetLastError();
+}
+
 // Make the largest-magnitude entry of every column positive (first index on ties).
 __global__ void fix_col_signs_kernel(double *U, int64_t n, int64_t ld)
 {

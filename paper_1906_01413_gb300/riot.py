@@ -136,6 +136,9 @@ def load():
     L.riot_set_wait_limit.restype = c_int32
     L.riot_quadratic_cost.argtypes = [vp, vp, POINTER(c_double)]
     L.riot_quadratic_cost.restype = c_int32
+    L.riot_rsvd_deflated.argtypes = [vp, c_int32, POINTER(c_int32), c_int32, c_double, c_int64, POINTER(c_double),
+                                     POINTER(c_int32)]
+    L.riot_rsvd_deflated.restype = c_int32
     L.riot_increment_pairs.argtypes = [vp, POINTER(c_int32)]
     L.riot_increment_pairs.restype = c_int32
     L.riot_rsvd_sweeps.argtypes = [vp]
@@ -291,6 +294,17 @@ def riot_quadratic_cost(ctx, dv=None):
     J = c_double(0.0)
     _check(ctx, "riot_quadratic_cost", load().riot_quadratic_cost(ctx, _ptr(dv), ctypes.byref(J)))
     return J.value
+
+
+def riot_rsvd_deflated(ctx, kcols, q=1, rel_floor=0.0, sketch_stream=0, kmax=4096):
+    """Deflated multi-level eigendecomposition (mixed precision), kcols columns per level;
+    returns the m eigenvalues kept."""
+    kc = (c_int32 * len(kcols))(*[int(k) for k in kcols])
+    lam = (c_double * kmax)()
+    m = c_int32(0)
+    _check(ctx, "riot_rsvd_deflated", load().riot_rsvd_deflated(ctx, len(kcols), kc, int(q), float(rel_floor),
+                                                                 int(sketch_stream), lam, ctypes.byref(m)))
+    return np.array(lam[:m.value])
 
 
 def riot_increment_pairs(ctx):

@@ -162,3 +162,28 @@ def test_full_rank_cost_reduction_matches_converged_cg(gpu_lib, small, precision
     assert red_cg > 0
     assert abs(red - red_cg) <= 1e-6 * red_cg, (red, red_cg)
     ctx.close()
+
+
+def test_deflated_full_rank_cost_reduction_matches_converged_cg(gpu_lib, small):
+    """The deflated eigendecomposition on the small window (level 0 at full rank, k = n = 40):
+    level 0 keeps every eigenvalue down to 2^-24 lambda_1 = 1.7e-4, so the deflated operator's
+    largest eigenvalue is below 1 and level 1 adds nothing; the increment (LRU, the dropped
+    directions taken at lambda = 0) has its cost reduction within 1e-6 of converged CG."""
+    R = gpu_lib
+    cfg, prob, traj = small
+    ctx = _l96_ctx(R, cfg, prob, R.RIOT_PREC_MIXED, kmax=2 * cfg.k)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    lam = R.riot_rsvd_deflated(ctx.h, [cfg.k, cfg.k], 0, sketch_stream=3)
+    lam_o = np.linalg.eigvalsh(orc.dense_hessian(prob, traj))[::-1]
+    assert lam.size == int(np.sum(lam_o >= 2.0 ** -24 * lam_o[0])) or abs(lam.size - np.sum(lam_o >= 2.0 ** -24 * lam_o[0])) <= 2
+    assert lam[-1] > 2.0 ** -24 * lam[0] * 0.5
+    dv = torch.empty(cfg.n, dtype=torch.float64, device=DEV)
+    R.riot_increment(ctx.h, dv)
+    red = R.riot_quadratic_cost(ctx.h) - R.riot_quadratic_cost(ctx.h, dv)
+    d = orc.innovation(prob, traj)
+    g = orc.gradient_b(prob, traj, d)
+    v = np.zeros(cfg.n)
+    dvs = orc.converged_increment(prob, traj, g)
+    red_cg = orc.quadratic_cost(prob, traj, d, v, v) - orc.quadratic_cost(prob, traj, d, v, dvs)
+    assert abs(red - red_cg) <= 1e-6 * red_cg, (red, red_cg)
+    ctx.close()

@@ -173,3 +173,31 @@ def test_large_window_inner_loop_mixed(gpu_lib, large, oracle_loop):
     assert mode_m == 0
     assert abs(red - red_m) <= 1e-3 * red_m, (red, red_m, ref["redf"])
     ctx.close()
+
+
+def test_large_window_deflated_mixed_reaches_the_fp64_reduction(gpu_lib, large, oracle_loop):
+    """The deflated two-level eigendecomposition (FP32 products only: 256 columns, then 320 on
+    the operator deflated by the pairs level 0 kept, one power iteration each) resolves the
+    spectrum about as far down as the FP64 path: its increment reaches at least 0.95 of the
+    cost reduction of the oracle's rank-512 FP64 increment (0.99 to 1.01 measured on this
+    window with two sketches; the plain mixed path reaches 0.39), its leading eigenvalues agree
+    with the oracle's to the 1e-3 asked of them, and the increment is LRA."""
+    R = gpu_lib
+    cfg, prob, _, _ = large
+    ctx = R.Context(n=prob.n, T=prob.T, dt=prob.dt, F=prob.F, obs_step=prob.obs_step, obs_idx=prob.obs_idx,
+                    obs_y=prob.y, obs_sigma=prob.sigma_o, length=cfg.ell, sigma_b=cfg.sigma_b,
+                    precision=R.RIOT_PREC_MIXED, kmax=576)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    lam = R.riot_rsvd_deflated(ctx.h, [256, 320], cfg.q, sketch_stream=40, kmax=576)
+    m = lam.size
+    assert m >= 450 and np.all(np.diff(lam) <= 0)
+    dv = torch.empty(cfg.n, dtype=torch.float64, device=DEV)
+    mode = R.riot_increment(ctx.h, dv)
+    assert mode == 0 and R.riot_increment_pairs(ctx.h) == m
+    red = R.riot_quadratic_cost(ctx.h) - R.riot_quadratic_cost(ctx.h, dv)
+    ref = oracle_loop
+    assert red >= 0.95 * ref["red"], (red, ref["red"])
+    lead = 128
+    rel = np.abs(lam[:lead] - ref["lam"][:lead]) / ref["lam"][:lead]
+    assert rel.max() <= 1e-3, rel.max()
+    ctx.close()
