@@ -35,11 +35,32 @@ from synth import advdiff as bc_synth  # noqa: E402
 from synth import configs  # noqa: E402
 
 WORKLOAD = "l96_n4096_F8_T200_obs25pct_every4_k512_q1"
-# DRAM bytes (read + write) from one ncu capture of the current kernels, summarised under
-# profiles/: one 512-column Hessian launch of the workload above, and one RK4 step of one
-# tracer column on the 192 x 192 x 30 grid (a 32-column launch / 32).
-L96_HVP_DRAM_BYTES_PER_LAUNCH = 53.4912e6 + 69.8212e6
-BC_STEP_DRAM_BYTES_PER_COLUMN = (146.62656e6 + 103.566336e6) / 32
+import hashlib
+import re
+
+# DRAM bytes (read + write) of the dominant kernels come from the ncu summaries under
+# profiles/ (one 512-column Hessian launch of the workload above; one RK4 step of 32 tracer
+# columns on the 192 x 192 x 30 grid).  Each summary records the sha256 of the kernel's
+# source file at capture time; a summary whose source has changed since is stale and the
+# bench reports traffic null instead of an old number.
+PROFILES = os.path.join(ROOT, "profiles")
+KERNEL_SOURCES = os.path.join(ROOT, "paper_1906_01413_gb300", "csrc")
+
+
+def profiled_traffic(summary, source):
+    """(bytes per unit, capture note) from a profiles/ summary, or (None, why) when stale."""
+    try:
+        text = open(os.path.join(PROFILES, summary)).read()
+        want = hashlib.sha256(open(os.path.join(KERNEL_SOURCES, source), "rb").read()).hexdigest()
+    except OSError as e:
+        return None, "no summary: %s" % e
+    h = re.search(r"source sha256: ([0-9a-f]{64})", text)
+    b = re.search(r"dram bytes per unit: ([0-9.eE+]+)", text)
+    if not h or not b:
+        return None, "summary %s has no source hash or byte count" % summary
+    if h.group(1) != want:
+        return None, "stale: %s changed since the capture in %s" % (source, summary)
+    return float(b.group(1)), summary
 METRIC = "RIOT inner-loop Hessian-vector products per second (inner-loop wall time)"
 UNIT = "HVP/s"
 
@@ -58,10 +79,14 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned sketch proposal leg")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned inner-loop leg")
     ap.add_argument("--no-deflated", action="store_true", help="skip the deflated multi-level mixed-precision leg")
+    ap.add_argument("--no-comparators", action="store_true",
+                    help="skip the paper's other inner loops (Algorithms 1, 2 and 4) on the same window")
     ap.add_argument("--clock-log", default=None,
                     help="CSV of the nvidia-smi clock samples taken during the timed steps (%%d: rank); "
                          "default: a file in the temporary directory")
-    ap.add_argument("--only", choices=["bc", "batch", "learned", "varcg", "varbl", "psas"], default=None,
+    ap.add_argument("--hvp-kernel", choices=["cta_barrier", "warp_pairs"], default="cta_barrier",
+                    help="FP32 Hessian kernel of --only hvp")
+    ap.add_argument("--only", choices=["bc", "batch", "learned", "varcg", "varbl", "psas", "hvp"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling)")
     ap.add_argument("--bc-cols", type=int, default=128, help="sketch columns per tracer Hessian call")
     ap.add_argument("--profile", action="store_true",
@@ -274,6 +299,7 @@ def bench_comparator(R, torch, dev, flush, which, warmup, steps):
             * g.abs().mean()
         B0 = B0.contiguous()
     times, info = [], {}
+    dv = torch.empty(n, dtype=torch.float64, device=dev)
     for i in range(warmup + steps):
         if which == "psas" and i:
             R.riot_outer_begin(ctx.h, xb, torch.zeros_like(xb))
@@ -282,22 +308,54 @@ def bench_comparator(R, torch, dev, flush, which, warmup, steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
         if which == "varcg":
-            theta, used = R.riot_varcg(ctx.h, 64)
+            theta, used = R.riot_varcg(ctx.h, 64, dv)
             info = {"m": used, "hvps": used, "theta1": float(theta.max())}
         elif which == "varbl":
-            theta, nb = R.riot_varbl(ctx.h, l, m, B0)
+            theta, nb = R.riot_varbl(ctx.h, l, m, B0, dv)
             info = {"l": l, "m": nb, "hvps": l * nb, "theta1": float(theta[0])}
         else:
-            lam, mode = R.riot_psas(ctx.h, 512, 1, sketch_stream=configs.STREAM_SKETCH0)
+            lam, mode = R.riot_psas(ctx.h, 512, 1, sketch_stream=configs.STREAM_SKETCH0, dv=dv)
             info = {"m": 512, "q": 1, "p": int(p), "dual_products": 2 * 512, "lambda1": float(lam[0]), "mode": mode}
+        e1.record(s)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            times.append(e0.elapsed_time(e1))
+    # cost reduction J~(0) - J~(dv) of the leg's increment (Eq. 3, FP64)
+    red = R.riot_quadratic_cost(ctx.h) - R.riot_quadratic_cost(ctx.h, dv)
+    ctx.close()
+    ms = statistics.mean(times)
+    units = info.get("hvps", info.get("dual_products", 0))
+    return {"leg": which, "workload": WORKLOAD, "ms_per_call": ms, "products_per_s": units / (ms * 1e-3),
+            "cost_reduction": red, **info}
+
+
+def bench_hvp(R, torch, dev, flush, kernel, warmup, steps):
+    """512 Hessian-vector products of the large Lorenz-96 window in one riot_hessian_apply (the
+    inner loop's dominant launch), timed alone with CUDA events after an L2 flush."""
+    cfg = configs.l96_large()
+    ctx, xb, p = build_problem(R, torch, cfg, dev, R.RIOT_PREC_MIXED, cfg.k)
+    R.riot_set_hvp_kernel(ctx.h, R.RIOT_HVP_WARP_PAIRS if kernel == "warp_pairs" else R.RIOT_HVP_CTA_BARRIER)
+    R.riot_outer_begin(ctx.h, xb)
+    W = torch.empty(cfg.k, cfg.n, dtype=torch.float32, device=dev)
+    R.riot_draw_normal(cfg.seed, configs.STREAM_SKETCH0, cfg.n, cfg.k, W)
+    Y = torch.empty_like(W)
+    s = torch.cuda.current_stream()
+    times = []
+    for i in range(warmup + steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        R.riot_hessian_apply(ctx.h, W, Y)
         e1.record(s)
         torch.cuda.synchronize()
         if i >= warmup:
             times.append(e0.elapsed_time(e1))
     ctx.close()
     ms = statistics.mean(times)
-    units = info.get("hvps", info.get("dual_products", 0))
-    return {"leg": which, "workload": WORKLOAD, "ms_per_call": ms, "products_per_s": units / (ms * 1e-3), **info}
+    flop = hvp_flops(cfg.n, cfg.T, p, band_width(cfg.n, cfg.ell)) * cfg.k
+    return {"kernel": kernel, "workload": WORKLOAD, "ms_per_launch": ms, "tflops": flop / (ms * 1e-3) / 1e12,
+            "hvps_per_launch": cfg.k}
 
 
 def build_bc_problem(R, torch, cfg, dev, precision, kmax):
@@ -331,13 +389,16 @@ def bench_bc_transport(R, torch, dev, flush, hbm_peak, ncols=128, reps=2):
     ms = statistics.mean(times)
     ncells = cfg.nx * cfg.ny * cfg.nz
     bytes_per_hvp = 8.0 * ncells * cfg.T * 2
+    # measured DRAM bytes of one step of one column, times the 2T steps of a product
+    step_bytes, bc_note = profiled_traffic("adv_step_kernel_bc_192x192x30_P32.md", "advdiff.cu")
+    bc_traffic = None if step_bytes is None else step_bytes * 2 * cfg.T
     achieved = bytes_per_hvp * ncols / (ms * 1e-3) / 1e9
     return {"workload": "bc_%dx%dx%d_T%d_obs%d_blocks%d" % (cfg.nx, cfg.ny, cfg.nz, cfg.T, p, cfg.nblocks),
             "value": ncols / (ms * 1e-3), "unit": "HVP/s", "ms_per_hvp": ms / ncols, "columns_per_call": ncols,
             "dtype": "f32",
             "roofline": {"bound": "hbm", "kernel": "adv_step_kernel<float,32,32,4> (whole product timed)",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "traffic": BC_STEP_DRAM_BYTES_PER_COLUMN * 2 * cfg.T, "bytes_per_hvp": bytes_per_hvp,
+                         "traffic": bc_traffic, "traffic_source": bc_note, "bytes_per_hvp": bytes_per_hvp,
                          "bytes_basis": "one FP32 read and write of the tracer per RK4 step, TL and AD"}}
 
 
@@ -722,6 +783,8 @@ def main():
             out = bench_learned_sketch(R, torch, dev)
         elif args.only in ("varcg", "varbl", "psas"):
             out = bench_comparator(R, torch, dev, flush, args.only, args.warmup, max(1, args.steps))
+        elif args.only == "hvp":
+            out = bench_hvp(R, torch, dev, flush, args.hvp_kernel, args.warmup, max(1, args.steps))
         elif args.only == "bc":
             out = bench_bc_transport(R, torch, dev, flush, float(peaks.get("hbm_gbs", 6800.0)), ncols=args.bc_cols,
                                      reps=max(1, args.steps))
@@ -772,6 +835,7 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
+    l96_traffic, l96_traffic_note = profiled_traffic("l96_hvp_tma_kernel_n4096_T200_k512.md", "l96_tma.cu")
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
@@ -807,6 +871,14 @@ def main():
     batch = None
     if not args.no_batch:
         batch = bench_batch(R, torch, dev, args.warmup, max(3, args.steps // 3))
+    comparators = None
+    if not args.no_comparators:
+        comparators = {}
+        for which in ("varcg", "varbl", "psas"):
+            try:
+                comparators[which] = bench_comparator(R, torch, dev, flush, which, 1, 2)
+            except R.RiotError as e:   # keep the headline line; report the leg's failure in it
+                comparators[which] = {"error": str(e)}
     bc = None
     if not args.no_bc:
         bc = bench_bc_transport(R, torch, dev, flush, float(peaks.get("hbm_gbs", 6800.0)))
@@ -882,7 +954,7 @@ def main():
             "phases_ms": ph,
             "roofline": {"bound": "alu", "kernel": "l96_hvp_tma_kernel<8,2,512>", "achieved": achieved,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                         "traffic": L96_HVP_DRAM_BYTES_PER_LAUNCH,
+                         "traffic": l96_traffic, "traffic_source": l96_traffic_note,
                          "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sm_count, sm_max),
                          "flop_per_hvp": flop_hvp, "hvp_per_launch": k, "launch_ms": hvp_launch_ms},
             "e2e": {"value": world * hvps_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(n * k * 4),
@@ -890,6 +962,14 @@ def main():
             "gpu_launches": int(launches),
             "wall_s_timed": wall}
     line["mixed_cost_reduction"] = {"value": red_mixed, "pairs_retained": pairs_mixed}
+    if comparators:
+        line["paper_comparison"] = {
+            "what": "the paper's inner loops on the same window, each one call after an L2 flush: RIOT "
+                    "(Algorithm 3, the headline) and its deflated mixed form against VarCG (Algorithm 1, "
+                    "64 sequential Lanczos steps), VarBL (Algorithm 2, 8 block steps of 64) and RIOT-PSAS "
+                    "(Algorithm 4, 512 dual columns, FP64 dual products); cost reduction of Eq. 3 in FP64",
+            "riot_mixed": {"ms_per_call": ms, "cost_reduction": red_mixed},
+            **comparators}
     if deflated:
         line["deflated_mixed"] = deflated
     if fp64:

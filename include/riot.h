@@ -377,8 +377,8 @@ riot_status riot_set_wait_limit(riot_ctx *ctx, int32_t polls);
  * the value; this synchronises.  Requires riot_outer_begin. */
 riot_status riot_quadratic_cost(riot_ctx *ctx, const double *dv_dev, double *J_out);
 
-/* Number of eigenpairs the last riot_increment retained (m <= k, see
- * riot_increment).  Synchronises. */
+/* Number of eigenpairs the last increment retained (m <= k, see
+ * riot_increment; after riot_increment or a batch inner loop).  Synchronises. */
 riot_status riot_increment_pairs(riot_ctx *ctx, int32_t *m_out);
 
 /* Number of Jacobi sweeps of the last successful riot_rsvd (-1: no context). */

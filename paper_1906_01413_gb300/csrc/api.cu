@@ -79,6 +79,7 @@ struct riot_ctx {
     // back in FP64.
     int scale_exp = 0, scale_in = 0, scale_rinv = 0;
     int k_shift = 0;   // shift the K normal equations (set for one retry after a failed solve)
+    int qr_shift_all = 0;   // every FP64 CholeskyQR pass shifted (set for one retry of a rank-deficient block)
     double *nrm = nullptr;   // 4 doubles of norm accumulators
     // Spectral preconditioner of Algorithm 3 (riot_precond_*): P_k = P'_1 ... P'_{k-1},
     // P'_j = I + V_j diag(c_j) V_j^T with c_j = (lambda_j + 1)^-1/2 - 1 (its inverse takes
@@ -294,7 +295,7 @@ riot_status cholqr64(riot_ctx *ctx, double *X, int k, int shifted, int info_base
         CU(gram_lower(n, k, X, 'd', n, ctx->G, k, ctx->s, ctx->gws, 8 * (size_t)ctx->kmax * ctx->kmax));
         CU(equilibrate(ctx->G, k, k, X, 'd', n, n, ctx->cvec, ctx->s));
         const double u = ldexp(1.0, -53);
-        const double shift = (pass < shifted) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
+        const double shift = (pass < shifted || ctx->qr_shift_all) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
         CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
         CU(trsm_right_lt(X, n, k, n, ctx->G, k, ctx->s, ctx->gws));
     }
@@ -1484,13 +1485,9 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
     return check_timeout(ctx);
 }
 
-riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const void *Omega_dev,
-                      double *lambda_out)
+static riot_status rsvd_run(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const void *Omega_dev,
+                            double *lambda_out)
 {
-    if (!ctx) return RIOT_EINVAL;
-    TRY(rsvd_check_args(ctx, k, q));
-    if (ctx->pc_dirty) return fail(ctx, RIOT_ESTATE, "riot_rsvd after riot_precond_push needs riot_outer_begin first");
-    CU(cudaSetDevice(ctx->dev));
     ctx->nev = 0;
     ctx->pc_ready = 0;
     ctx->pc_open = 0;
@@ -1510,6 +1507,27 @@ riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream
     TRY(rsvd_retry_k(ctx, k, lambda_out, rsvd_collect(ctx, k, lambda_out)));
     ctx->pc_open = 1;
     return RIOT_OK;
+}
+
+riot_status riot_rsvd(riot_ctx *ctx, int32_t k, int32_t q, int64_t sketch_stream, const void *Omega_dev,
+                      double *lambda_out)
+{
+    if (!ctx) return RIOT_EINVAL;
+    TRY(rsvd_check_args(ctx, k, q));
+    if (ctx->pc_dirty) return fail(ctx, RIOT_ESTATE, "riot_rsvd after riot_precond_push needs riot_outer_begin first");
+    CU(cudaSetDevice(ctx->dev));
+    riot_status st = rsvd_run(ctx, k, q, sketch_stream, Omega_dev, lambda_out);
+    if (st == RIOT_ENOTSPD && ctx->prec == RIOT_PREC_FP64) {
+        // a CholeskyQR pass met a non-positive pivot: in working precision the block has fewer
+        // independent columns than k (more sketch columns than the Hessian's numerical rank,
+        // seen on windows with k >= 0.75 n).  Redo the inner loop with every pass shifted: the
+        // basis then spans the block's range plus rounding-level directions, which give
+        // eigenvalues of K near zero, as the completion of the oracle's Householder basis does.
+        ctx->qr_shift_all = 1;
+        st = rsvd_run(ctx, k, q, sketch_stream, Omega_dev, lambda_out);
+        ctx->qr_shift_all = 0;
+    }
+    return st;
 }
 
 // X (n x kcols FP32, ld n) <- (I - U1 U1^T) X with U1 the first m1 columns of Ud32, in two
@@ -1645,7 +1663,7 @@ int32_t riot_rsvd_sweeps(const riot_ctx *ctx) { return ctx ? ctx->jacobi_sweeps 
 riot_status riot_increment_pairs(riot_ctx *ctx, int32_t *m_out)
 {
     if (!ctx || !m_out) return RIOT_EINVAL;
-    if (!ctx->pc_ready) return fail(ctx, RIOT_ESTATE, "riot_increment_pairs before riot_increment");
+    if (!ctx->have_rsvd) return fail(ctx, RIOT_ESTATE, "riot_increment_pairs before an inner loop");
     CU(cudaSetDevice(ctx->dev));
     CU(cudaMemcpyAsync(m_out, ctx->info + 15, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));

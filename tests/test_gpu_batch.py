@@ -176,3 +176,61 @@ def test_window_beyond_any_fp32_scaling_is_refused(gpu_lib):
     lam = R.riot_rsvd(ctx.h, cfg.k, cfg.q, sketch_stream=3)
     assert np.all(np.isfinite(lam)) and lam[0] > 1e70
     ctx.close()
+
+
+def _oracle_windows():
+    # three uneven windows small enough for the oracle: every chunk width the batch kernel
+    # sees below 512 variables, ragged chunks, different T and k
+    spec = [(61, 9, 8, 10.0), (150, 30, 48, 9.0), (333, 17, 64, 12.0)]
+    return [configs.L96Config(name="ow%d" % i, n=n, F=F, T=T, obs_every=2, obs_frac=0.3, obs_layout="random",
+                              ell=4.0, k=k, q=1, spinup=200, seed=configs.BASE_SEED + 700 + i)
+            for i, (n, T, k, F) in enumerate(spec)]
+
+
+def test_batch_kernel_matches_the_oracle(gpu_lib):
+    """One graph-captured batch inner loop of three uneven windows (one persistent Hessian
+    launch per application) against the FP64 oracle run on the same FP32 sketches.  The FP32
+    products' error is of order 2^-24 lambda_1, so by Weyl's inequality the eigenvalues with
+    lambda >= 1000 2^-24 lambda_1 are held to the 1e-3 asked of the leading eigenvalues (the
+    ones nearer the 2^-24 lambda_1 floor, still kept by the mixed increment, can be off by
+    about a percent); the increment of each window, over the pairs it kept, has its cost
+    reduction within 1e-3 of that of the oracle's increment restricted to the same pairs
+    (second order in the increment's error)."""
+    from oracle import problem, riot as orc
+    from synth import philox
+    R = gpu_lib
+    cfgs = _oracle_windows()
+    probs = [problem.build(c) for c in cfgs]
+    ctxs = []
+    for c, p in zip(cfgs, probs):
+        ctx = R.Context(n=p.n, T=p.T, dt=p.dt, F=p.F, obs_step=p.obs_step, obs_idx=p.obs_idx, obs_y=p.y,
+                        obs_sigma=p.sigma_o, length=c.ell, sigma_b=c.sigma_b, precision=R.RIOT_PREC_MIXED, kmax=c.k)
+        R.riot_outer_begin(ctx.h, torch.tensor(p.x_b, device=DEV))
+        ctxs.append(ctx)
+    b = R.riot_batch_create([ctx.h for ctx in ctxs], [c.k for c in cfgs], 1)
+    st = R.riot_batch_run(b, len(cfgs), sketch_stream=configs.STREAM_SKETCH0, use_graph=True)
+    assert st == [0] * len(cfgs)
+    for c, p, ctx in zip(cfgs, probs, ctxs):
+        lam, _, v = _state(R, ctx, c.n, c.k)
+        m = R.riot_increment_pairs(ctx.h)
+        dv = torch.tensor(v, device=DEV)          # v started at 0: v = the increment
+        red = R.riot_quadratic_cost(ctx.h) - R.riot_quadratic_cost(ctx.h, dv)
+        # the oracle on the same sketch: seed 0, stream STREAM_SKETCH0, FP32-rounded
+        Om = philox.normals(0, configs.STREAM_SKETCH0, c.n * c.k).reshape(c.k, c.n)
+        Om = Om.astype(np.float32).astype(np.float64).T
+        traj = orc.trajectory(p, p.x_b)
+        lo, Uo, _ = orc.rsvd(p, traj, Om, q=1)
+        assert m == int(np.sum(lam >= 2.0 ** -24 * lam[0]))
+        lead = lo >= 1e3 * 2.0 ** -24 * lo[0]
+        assert lead.sum() >= 4
+        rel = np.abs(lam[lead] - lo[lead]) / np.abs(lo[lead])
+        assert rel.max() <= 1e-3, (c.name, rel.max())
+        d = orc.innovation(p, traj)
+        g = orc.gradient_b(p, traj, d)
+        dvo, mode_o = orc.increment(lo[:m], Uo[:, :m], g)
+        z = np.zeros(c.n)
+        red_o = orc.quadratic_cost(p, traj, d, z, z) - orc.quadratic_cost(p, traj, d, z, dvo)
+        assert abs(red - red_o) <= 1e-3 * abs(red_o), (c.name, red, red_o)
+    R.riot_batch_destroy(b)
+    for ctx in ctxs:
+        ctx.close()
