@@ -530,7 +530,7 @@ riot_status riot_varbl(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev
                        int32_t *blocks_used);
 
 /* RIOT-PSAS (Appendix, Algorithm 4): one cycle of the observation-space dual
- * at the state of the last riot_outer_begin (Lorenz-96 contexts).  With
+ * at the state of the last riot_outer_begin (either model).  With
  * S = L_{R^-1} = diag(1/sigma_o) (R diagonal) it decomposes the p x p
  * A_dual = S H B H^T S by the randomized steps of Algorithm 3 on a p x m
  * sketch (Omega_dev: p x m FP64 column-major on the device, or NULL to draw it
@@ -543,12 +543,14 @@ riot_status riot_varbl(riot_ctx *ctx, int32_t l, int32_t m, const double *B0_dev
  * x = x_b + B H^T dw, i.e. v = L^T H^T dw in the context's x = x_b + L v
  * (the listing writes x_{k-1} + B H^T dw, which counts x_{k-1} - x_b twice
  * from the second cycle on; both agree in the first).  Each product by
- * A_dual is one adjoint launch from the forcing S w, L L^T, and one
- * tangent-linear launch over all m columns, in FP64 on either precision.
+ * A_dual is one adjoint integration from the forcing S w, L L^T, and one
+ * tangent-linear integration, in FP64 on either precision: Lorenz-96 one
+ * launch of each over all m columns; the tracer model batches of the
+ * columns its product workspace holds in FP64.
  * lambda_out (host, m, may be NULL): eigenvalues of A_dual, descending;
  * dv_dev (n, may be NULL): the change of v; mode_out (may be NULL): 0 LRA,
  * 1 LRU.  RIOT_ESTATE before riot_outer_begin or with preconditioner
- * factors; RIOT_EINVAL for another model, m outside [1, min(kmax, p)] or q
+ * factors; RIOT_EINVAL for m outside [1, min(kmax, p)] or q
  * outside [0, 64]; RIOT_ENOTSPD if the basis or the solve for K fails.
  * Allocates its observation-space workspace (6 p kmax doubles) at the first
  * call.  Synchronises.  Call riot_outer_begin() before the next cycle. */

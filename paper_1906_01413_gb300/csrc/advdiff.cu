@@ -515,7 +515,91 @@ cudaError_t hvp_batch(const AdvDev &m, const R *W, R *Y, long long ld, int P, in
     return cudaSuccess;
 }
 
+// The two halves of a product on P columns, for the observation-space dual of Algorithm 4:
+// tangent linear r = R^-1 H' L w (ld ldw, r with stride p) and adjoint z = L^T H'^T f from an
+// observation-space forcing f (stride p; z at ld ldz).
+template <typename R>
+cudaError_t tl_batch(const AdvDev &m, const R *W, long long ldw, int P, R *r, cudaStream_t s)
+{
+    cudaError_t e;
+    const long long n = m.n, nyx = (long long)m.ny * m.nx;
+    R *cA = (R *)m.cA, *cB = (R *)m.cB, *src = (R *)m.src, *tmp = (R *)m.tmp;
+    const size_t cells = (size_t)P * m.ncells;
+    if ((e = sep_apply<R>(m, W, ldw, src, n, P, tmp, s)) != cudaSuccess) return e;
+    if ((e = colscale<R>(src, n, Tab<R>::Es(m), src, n, (int)n, P, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cA, 0, cells * sizeof(R), s)) != cudaSuccess) return e;
+    for (int t = 0; t < m.T; ++t) {
+        const int b = (int)(((long long)t * m.nb) / m.T);
+        if ((e = step<R>(m, cA, cB, P, src + b * nyx, n, nullptr, 0, false, s)) != cudaSuccess) return e;
+        R *sw = cA;
+        cA = cB;
+        cB = sw;
+        if ((e = gather<R>(m, cA, P, t + 1, r, m.p, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t ad_batch(const AdvDev &m, const R *f, int P, R *Z, long long ldz, cudaStream_t s)
+{
+    cudaError_t e;
+    const long long n = m.n, nyx = (long long)m.ny * m.nx;
+    R *cA = (R *)m.cA, *cB = (R *)m.cB, *ebar = (R *)m.ebar, *tmp = (R *)m.tmp;
+    const size_t cells = (size_t)P * m.ncells;
+    if ((e = cudaMemsetAsync(cA, 0, cells * sizeof(R), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ebar, 0, (size_t)P * n * sizeof(R), s)) != cudaSuccess) return e;
+    for (int t = m.T - 1; t >= 0; --t) {
+        if ((e = scatter<R>(m, cA, P, t + 1, f, m.p, s)) != cudaSuccess) return e;
+        const int b = (int)(((long long)t * m.nb) / m.T);
+        if ((e = step<R>(m, cA, cB, P, nullptr, 0, ebar + b * nyx, n, true, s)) != cudaSuccess) return e;
+        R *sw = cA;
+        cA = cB;
+        cB = sw;
+    }
+    if ((e = colscale<R>(ebar, n, Tab<R>::Es(m), ebar, n, (int)n, P, s)) != cudaSuccess) return e;
+    return sep_apply<R>(m, ebar, n, Z, ldz, P, tmp, s);
+}
+
 }  // namespace
+
+cudaError_t adv_tl(const AdvDev &m, const double *W, int64_t ld, int ncols, double *r, cudaStream_t s)
+{
+    for (int c0 = 0; c0 < ncols; c0 += m.Pws64) {
+        const int P = ncols - c0 < m.Pws64 ? ncols - c0 : m.Pws64;
+        cudaError_t e = tl_batch<double>(m, W + (size_t)c0 * ld, ld, P, r + (size_t)c0 * m.p, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t adv_ad(const AdvDev &m, const double *f, int ncols, double *Z, int64_t ld, cudaStream_t s)
+{
+    for (int c0 = 0; c0 < ncols; c0 += m.Pws64) {
+        const int P = ncols - c0 < m.Pws64 ? ncols - c0 : m.Pws64;
+        cudaError_t e = ad_batch<double>(m, f + (size_t)c0 * m.p, P, Z + (size_t)c0 * ld, ld, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t adv_ad_obs(const AdvDev &m, const double *f, double *z, cudaStream_t s)
+{
+    cudaError_t e;
+    const long long n = m.n, nyx = (long long)m.ny * m.nx;
+    double *cA = m.c64A, *cB = m.c64B;
+    if ((e = cudaMemsetAsync(cA, 0, (size_t)m.ncells * sizeof(double), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.ebar64, 0, (size_t)n * sizeof(double), s)) != cudaSuccess) return e;
+    for (int t = m.T - 1; t >= 0; --t) {
+        if ((e = scatter<double>(m, cA, 1, t + 1, f, m.p, s)) != cudaSuccess) return e;
+        const int bk = (int)(((long long)t * m.nb) / m.T);
+        if ((e = step<double>(m, cA, cB, 1, nullptr, 0, m.ebar64 + bk * nyx, n, true, s)) != cudaSuccess) return e;
+        double *sw = cA;
+        cA = cB;
+        cB = sw;
+    }
+    if ((e = colscale<double>(m.ebar64, n, m.Es64, m.ebar64, n, (int)n, 1, s)) != cudaSuccess) return e;
+    return sep_apply<double>(m, m.ebar64, n, z, n, 1, m.tmp64, s);
+}
 
 cudaError_t adv_hvp(const AdvDev &m, bool fp64, const void *W, void *Y, int64_t ld, int ncols, int add_identity,
                     void *r, cudaStream_t s)

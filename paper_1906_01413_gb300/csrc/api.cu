@@ -717,12 +717,15 @@ riot_status setup_advdiff(riot_ctx *ctx, const riot_model_desc *model, const rio
     a.Pmax64 = ctx->kmax < 64 ? ctx->kmax : 64;
     a.Pmax = fp64 ? a.Pmax64 : (ctx->kmax < 128 ? ctx->kmax : 128);
     const size_t P = (size_t)a.Pmax;
+    // bytes per cell (per control) of the batch workspace: at least one FP64 probe
+    const size_t wsb = P * rs > sizeof(double) ? P * rs : sizeof(double);
+    a.Pws64 = (int)(wsb / sizeof(double));
     char *cA = nullptr, *cB = nullptr, *src = nullptr, *ebar = nullptr, *tmp = nullptr;
-    TRY(dalloc(ctx, &cA, P * ncells * rs));
-    TRY(dalloc(ctx, &cB, P * ncells * rs));
-    TRY(dalloc(ctx, &src, P * n * rs));
-    TRY(dalloc(ctx, &ebar, P * n * rs));
-    TRY(dalloc(ctx, &tmp, P * n * rs));
+    TRY(dalloc(ctx, &cA, wsb * ncells));
+    TRY(dalloc(ctx, &cB, wsb * ncells));
+    TRY(dalloc(ctx, &src, wsb * n));
+    TRY(dalloc(ctx, &ebar, wsb * n));
+    TRY(dalloc(ctx, &tmp, wsb * n));
     a.cA = cA;
     a.cB = cB;
     a.src = src;
@@ -2543,18 +2546,24 @@ static riot_status psas_alloc(riot_ctx *ctx)
     return RIOT_OK;
 }
 
-// Y = A_dual W = S H B H^T S W for m <= kmax observation-space columns (ld p), FP64:
-// the adjoint from the forcing S w and L^T (Hessian kernel mode 1), then L, the tangent
-// linear model and R^-1 H (mode 2), then sigma_o (S R = diag(sigma_o)).  ctx->U holds the
-// n x m intermediate L^T H^T S W.
+// Y = A_dual W = S H B H^T S W for m <= kmax observation-space columns (ld p), FP64 on either
+// precision: the adjoint from the forcing S w and L^T, then L, the tangent linear model and
+// R^-1 H, then sigma_o (S R = diag(sigma_o)).  ctx->U holds the n x m intermediate
+// L^T H^T S W (Lorenz-96: Hessian kernel modes 1 and 2; tracer: the two halves of the
+// batched product).
 static riot_status dual_hvp(riot_ctx *ctx, const double *W, double *Y, int m)
 {
     const int n = ctx->n, p = ctx->p;
     cudaStream_t s = ctx->s;
     CU(cudaMemcpyAsync(ctx->psF, W, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
     CU(scale_rows(p, m, p, ctx->psS, ctx->psF, 1, s));
-    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->U, n, m, 0, ctx->psF, 1, s));
-    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, ctx->U, nullptr, n, m, 0, ctx->psR, 2, s));
+    if (ctx->model == RIOT_MODEL_ADVDIFF) {
+        CU(adv_ad(ctx->a, ctx->psF, m, ctx->U, n, s));
+        CU(adv_tl(ctx->a, ctx->U, n, m, ctx->psR, s));
+    } else {
+        CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->U, n, m, 0, ctx->psF, 1, s));
+        CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, ctx->U, nullptr, n, m, 0, ctx->psR, 2, s));
+    }
     CU(cudaMemcpyAsync(Y, ctx->psR, sizeof(double) * (size_t)p * m, cudaMemcpyDeviceToDevice, s));
     CU(scale_rows(p, m, p, ctx->psSig, Y, 1, s));
     return RIOT_OK;
@@ -2564,7 +2573,6 @@ riot_status riot_psas(riot_ctx *ctx, int32_t m, int32_t q, int64_t sketch_stream
                       double *lambda_out, double *dv_dev, int32_t *mode_out)
 {
     if (!ctx) return RIOT_EINVAL;
-    if (ctx->model != RIOT_MODEL_L96) return fail(ctx, RIOT_EINVAL, "riot_psas: Lorenz-96 contexts only");
     if (!ctx->have_traj) return fail(ctx, RIOT_ESTATE, "riot_psas before riot_outer_begin");
     if (m < 1 || m > ctx->kmax || m > ctx->p)
         return fail(ctx, RIOT_EINVAL, "m = %d outside [1, min(kmax = %d, p = %d)]", m, ctx->kmax, ctx->p);
@@ -2580,7 +2588,8 @@ riot_status riot_psas(riot_ctx *ctx, int32_t m, int32_t q, int64_t sketch_stream
     // b' = H (x_b - x) = H L (-v): the tangent linear model of -v (mode 2 gives R^-1 H L (-v))
     CU(cudaMemcpyAsync(ctx->tmp, ctx->v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     CU(scal(n, -1.0, ctx->tmp, s));
-    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, ctx->tmp, nullptr, n, 1, 0, ctx->psR, 2, s));
+    if (ctx->model == RIOT_MODEL_ADVDIFF) CU(adv_tl_obs(ctx->a, ctx->tmp, ctx->psR, s));
+    else CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, ctx->tmp, nullptr, n, 1, 0, ctx->psR, 2, s));
     CU(mul(p, ctx->psS, ctx->d, ctx->psr, s));                 // S (H(x) - y)
     CU(mul(p, ctx->psSig, ctx->psR, ctx->psw, s));             // S b' = sigma_o (R^-1 b')
     CU(axpby(p, -1.0, ctx->psw, -1.0, ctx->psr, s));           // r = -S (H(x) - y) - S b'
@@ -2638,8 +2647,9 @@ riot_status riot_psas(riot_ctx *ctx, int32_t m, int32_t q, int64_t sketch_stream
         CU(gemm('N', 'N', p, 1, m, -1.0, ctx->psU, 'd', p, ctx->psc, 'd', m, 1.0, ctx->psw, 'd', p, s));
     }
     CU(mul(p, ctx->psS, ctx->psw, ctx->psF, s));               // dw = S w
-    // x = x_b + B H^T dw = x_b + L v with v = L^T H^T dw (mode 1); dv = v_new - v
-    CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->tmp, n, 1, 0, ctx->psF, 1, s));
+    // x = x_b + B H^T dw = x_b + L v with v = L^T H^T dw (one adjoint run); dv = v_new - v
+    if (ctx->model == RIOT_MODEL_ADVDIFF) CU(adv_ad_obs(ctx->a, ctx->psF, ctx->tmp, s));
+    else CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, nullptr, ctx->tmp, n, 1, 0, ctx->psF, 1, s));
     CU(cudaMemcpyAsync(ctx->dv, ctx->tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     CU(axpby(n, -1.0, ctx->v, 1.0, ctx->dv, s));
     CU(cudaMemcpyAsync(ctx->v, ctx->tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));

@@ -168,8 +168,8 @@ struct AdvDev {
     const double *Eb = nullptr;       // [n] background emissions
     double *Es64 = nullptr;           // [n] E / dz at the current control
     float *Es32 = nullptr;
-    // batch workspace (Pmax probes of the context precision)
-    int Pmax = 0, Pmax64 = 0;
+    // batch workspace (Pmax probes of the context precision; the same bytes hold Pws64 FP64 probes)
+    int Pmax = 0, Pmax64 = 0, Pws64 = 0;
     void *cA = nullptr, *cB = nullptr, *src = nullptr, *ebar = nullptr, *tmp = nullptr;
     // FP64 outer-loop workspace
     double *c64A = nullptr, *c64B = nullptr, *ebar64 = nullptr, *tmp64 = nullptr;   // tmp64: Pmax64 * n
@@ -183,6 +183,14 @@ cudaError_t adv_hvp(const AdvDev &m, bool fp64, const void *W, void *Y, int64_t 
 // jo += 1/2 sum d^2 / sigma^2 (atomic), rd = R^-1 d, b = L^T H'^T R^-1 d.
 cudaError_t adv_outer(const AdvDev &m, const double *x, double *d, double *jo, double *rd, double *b,
                       cudaStream_t s);
+// The halves of a product in FP64 on either precision, over ncols columns (Pws64 at a time, in
+// the batch workspace): the tangent linear r = R^-1 H' L w (W at ld, r: ncols x p) and the
+// adjoint z = L^T H'^T f from an observation-space forcing (f: ncols x p, Z at ld); for the
+// dual of Algorithm 4.
+cudaError_t adv_tl(const AdvDev &m, const double *W, int64_t ld, int ncols, double *r, cudaStream_t s);
+cudaError_t adv_ad(const AdvDev &m, const double *f, int ncols, double *Z, int64_t ld, cudaStream_t s);
+// z = L^T H'^T f for one FP64 observation-space forcing (outer-loop workspace)
+cudaError_t adv_ad_obs(const AdvDev &m, const double *f, double *z, cudaStream_t s);
 // Tangent-linear observation residuals of one FP64 column w: r = R^-1 H' (L w), the forward
 // half of a Hessian product (uses the outer-loop workspace; p doubles out).
 cudaError_t adv_tl_obs(const AdvDev &m, const double *w, double *r, cudaStream_t s);

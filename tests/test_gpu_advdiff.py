@@ -226,3 +226,49 @@ def test_bad_descriptors_are_rejected(gpu_lib):
                              dy=cfg.dy, dz=cfg.dz, u=prob.m.u, v=v_bad, amp=prob.m.amp, kz=prob.m.kz,
                              emis_b=prob.m.Eb, obs_step=prob.obs.step, obs_pos=prob.obs.pos, obs_y=prob.y,
                              obs_sigma=prob.sigma_o, length=cfg.ell, sigma_b=cfg.sigma_b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_grid_products_against_the_oracle(gpu_lib, precision):
+    """Two Hessian-vector products on the full 192 x 192 x 30 grid (240 steps, 8000 observations,
+    n = 147 456) against the FP64 oracle's, sampled at 512 seeded positions per column
+    (tests/golden/bc_large_products.json, written by the oracle alone; unit sigma_o).  FP64: the
+    operations differ only in order, 1e-10 of the column norm as on the small grids.  FP32: the
+    transport is linear and dissipative, so rounding errors add like a random walk over the 8T
+    stages of the forward and backward passes: 16 sqrt(8T) 2^-24 = 4.2e-5 (the same derivation as
+    the Lorenz-96 products, without a trajectory term)."""
+    import json
+    import os
+    R = gpu_lib
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bc_large_products.json")) as f:
+        gold = json.load(f)
+    cfg = S.bc_large()
+    m = A.model_from_config(cfg)
+    step, pos = cfg.tracks()
+    obs = A.make_obs(m, step, pos)
+    p = step.size
+    Lop = A.exp_separable_sqrt(cfg.nx, cfg.ny, cfg.nblocks, cfg.dx, cfg.dy, cfg.ell, cfg.sigma_b)
+    x_b = Lop.apply(cfg.background_perturbation())
+    prec = R.RIOT_PREC_FP64 if precision == "fp64" else R.RIOT_PREC_MIXED
+    ctx = R.Context(nx=cfg.nx, ny=cfg.ny, nz=cfg.nz, nblocks=cfg.nblocks, T=cfg.T, dt=cfg.dt, dx=cfg.dx,
+                    dy=cfg.dy, dz=cfg.dz, u=m.u, v=m.v, amp=m.amp, kz=m.kz, emis_b=m.Eb, obs_step=obs.step,
+                    obs_pos=obs.pos, obs_y=np.zeros(p), obs_sigma=np.ones(p), length=cfg.ell,
+                    sigma_b=cfg.sigma_b, precision=prec, kmax=2)
+    assert gold["n"] == ctx.n and gold["p"] == p
+    R.riot_outer_begin(ctx.h, _t(x_b))
+    cols = gold["columns"]
+    W = cfg.sketch(0, k=cols)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    Wt = _t(W, dt)
+    Y = torch.empty_like(Wt)
+    R.riot_hessian_apply(ctx.h, Wt, Y)
+    got = Y.double().cpu().numpy()
+    idx = np.asarray(gold["sample_index"])
+    vals = gold["values"] if precision == "fp64" else gold["values_f32_input"]
+    norms = gold["norm"] if precision == "fp64" else gold["norm_f32_input"]
+    tol = 1e-10 if precision == "fp64" else 16 * np.sqrt(8 * cfg.T) * 2.0 ** -24
+    for j in range(cols):
+        ref = np.asarray(vals[j])
+        assert np.linalg.norm(got[j, idx] - ref) <= tol * np.linalg.norm(ref), (j, np.linalg.norm(got[j, idx] - ref) / np.linalg.norm(ref))
+        assert abs(np.linalg.norm(got[j]) - norms[j]) <= tol * norms[j]
+    ctx.close()

@@ -123,3 +123,56 @@ def test_psas_arguments_and_state(gpu_lib):
     lam, mode = R.riot_psas(ctx.h, 6, 1, sketch_stream=5)    # a drawn sketch
     assert lam.size == 6 and np.all(np.diff(lam) <= 0) and mode in (0, 1)
     ctx.close()
+
+
+# --- the tracer-transport problem ---------------------------------------------------------
+
+def _bc_ctx(R, cfg, prob, precision, kmax, exact_rr=False):
+    m = prob.m
+    return R.Context(nx=cfg.nx, ny=cfg.ny, nz=cfg.nz, nblocks=cfg.nblocks, T=cfg.T, dt=cfg.dt, dx=cfg.dx,
+                     dy=cfg.dy, dz=cfg.dz, u=m.u, v=m.v, amp=m.amp, kz=m.kz, emis_b=m.Eb,
+                     obs_step=prob.obs.step, obs_pos=prob.obs.pos, obs_y=prob.y, obs_sigma=prob.sigma_o,
+                     length=cfg.ell, sigma_b=cfg.sigma_b, precision=precision, kmax=kmax, exact_rr=exact_rr)
+
+
+def _bc_oracle_cycles(AD, prob, m, q, streams, exact_rr=False):
+    x, out = prob.x_b.copy(), []
+    for stream in streams:
+        st = AD.psas_outer_step(prob, x, _omega(prob.p, m, stream).T, q=q, exact_rr=exact_rr)
+        out.append(st)
+        x = st["x_next"]
+    return out
+
+
+@pytest.fixture(scope="module")
+def bc_small():
+    from oracle import advdiff as AD
+    from synth import advdiff as S
+    cfg = S.bc_small()
+    return AD, cfg, AD.build(cfg)
+
+
+@pytest.mark.parametrize("precision,m,q,exact_rr,streams", [
+    ("fp64", 16, 1, False, [90, 91]),     # lambda_16 = 2.9: LRA
+    ("fp64", 48, 1, False, [92]),         # lambda_48 = 0.05: LRU
+    ("mixed", 48, 1, False, [92]),        # the dual runs in FP64 on a mixed context too
+    ("fp64", 24, 0, True, [93]),
+])
+def test_tracer_cycles_match_oracle(gpu_lib, bc_small, precision, m, q, exact_rr, streams):
+    """The tracer window of 384 controls and 240 observations (rank of A_dual about 120):
+    eigenvalues to 1e-8 of the largest and the updated controls to 1e-7 of the increment,
+    as on the Lorenz-96 windows below full rank.  The second cycle starts from the state the
+    first one left (the outer loop's linearisation moves with x: E = E_b exp(x))."""
+    R = gpu_lib
+    AD, cfg, prob = bc_small
+    ref = _bc_oracle_cycles(AD, prob, m, q, streams, exact_rr=exact_rr)
+    prec = R.RIOT_PREC_FP64 if precision == "fp64" else R.RIOT_PREC_MIXED
+    ctx = _bc_ctx(R, cfg, prob, prec, kmax=max(m, 48), exact_rr=exact_rr)
+    got = _cycles(R, ctx, prob, m, q, streams)
+    for c, (a, b) in enumerate(zip(got, ref)):
+        assert abs(b["lam"][-1] - 1.0) > 0.05
+        np.testing.assert_allclose(a["lam"], b["lam"], rtol=0, atol=1e-8 * b["lam"][0], err_msg=str(c))
+        assert a["mode"] == b["mode"], c
+        dx = b["x_next"] - (prob.x_b if c == 0 else ref[c - 1]["x_next"])
+        np.testing.assert_allclose(a["x"], b["x_next"], rtol=0, atol=1e-7 * np.abs(dx).max(), err_msg=str(c))
+    ctx.close()
