@@ -397,10 +397,134 @@ cudaError_t put_block_inverses(float *L32, int k, int64_t ldl, const double *din
     return cudaGetLastError();
 }
 
+// X <- X L^-T for the rows of an m x k FP32 block in one launch (the triangular solve of a
+// CholeskyQR pass; L holds the factor below its diagonal blocks and the block inverses on
+// them, see put_block_inverses).  Rows are independent, so a CTA owns 32 rows for all k
+// columns in shared memory (column-major over the 32 rows, four rows per float4) and sweeps
+// the block columns left to right: block J takes X_J - sum_{l<J} Y_l L_Jl^T and is then
+// multiplied by the block inverse.  The 32 x 32 blocks of L stream through a ring of four
+// shared-memory buffers filled by cp.async (4-byte copies, so any leading dimension works),
+// three blocks ahead of the one in use.
+constexpr int kTrsmRows = 32;
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl)
+{
+    constexpr int R = kTrsmRows;
+    extern __shared__ __align__(16) float trsm_sm[];
+    float *Ys = trsm_sm;                          // [k][R]
+    float *ring = trsm_sm + (size_t)k * R;        // [4][32 kk][32 ci]
+    const int t = threadIdx.x, cj = t & 31, g = t >> 5;
+    const int r0 = blockIdx.x * R;
+    const int nb = (k + 31) / 32, nblk = nb * (nb + 1) / 2;
+    for (int e = t; e < k * R; e += blockDim.x) {
+        const int c = e / R, r = e - c * R;
+        Ys[e] = (r0 + r < m) ? X[(r0 + r) + (int64_t)c * ldx] : 0.f;
+    }
+    // block b of the sweep is (J, l), l = 0..J (l = J: the diagonal block)
+    int iJ = 0, il = 0;   // the next block to issue
+    auto issue = [&](int slot) {
+        if (iJ < nb) {
+            float *buf = ring + slot * 1024;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = t + 256 * q, ci = e & 31, kk = e >> 5;
+                const int row = 32 * iJ + ci, col = 32 * il + kk;
+                if (row < k && col < k) cp_async4(buf + kk * 32 + ci, L + row + (int64_t)col * ldl);
+                else buf[kk * 32 + ci] = 0.f;
+            }
+            if (++il > iJ) {
+                ++iJ;
+                il = 0;
+            }
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    issue(1);
+    issue(2);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int J = 0, l = 0;
+    for (int b = 0; b < nblk; ++b) {
+        cp_async_wait<2>();
+        __syncthreads();
+        issue((b + 3) & 3);
+        const float *buf = ring + (b & 3) * 1024;
+        const int colJ = 32 * J + cj;
+        if (l == 0) {
+            if (colJ < k) {
+                const float4 x4 = *reinterpret_cast<const float4 *>(Ys + (size_t)colJ * R + 4 * g);
+                acc[0] = x4.x; acc[1] = x4.y; acc[2] = x4.z; acc[3] = x4.w;
+            } else {
+                acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+            }
+        }
+        if (l < J) {
+            const float *yb = Ys + (size_t)(32 * l) * R + 4 * g;
+#pragma unroll 8
+            for (int kk = 0; kk < 32; ++kk) {
+                const float a = buf[kk * 32 + cj];
+                const float4 y4 = *reinterpret_cast<const float4 *>(yb + kk * R);
+                acc[0] = fmaf(-y4.x, a, acc[0]);
+                acc[1] = fmaf(-y4.y, a, acc[1]);
+                acc[2] = fmaf(-y4.z, a, acc[2]);
+                acc[3] = fmaf(-y4.w, a, acc[3]);
+            }
+            ++l;
+        } else {
+            // diagonal: the right-hand side through shared memory, then times the block inverse
+            if (colJ < k) *reinterpret_cast<float4 *>(Ys + (size_t)colJ * R + 4 * g) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            __syncthreads();
+            const int jb = (k - 32 * J < 32) ? k - 32 * J : 32;
+            float o[4] = {0.f, 0.f, 0.f, 0.f};
+            const float *yb = Ys + (size_t)(32 * J) * R + 4 * g;
+            for (int kk = 0; kk < jb; ++kk) {
+                const float a = buf[kk * 32 + cj];
+                const float4 y4 = *reinterpret_cast<const float4 *>(yb + kk * R);
+                o[0] = fmaf(y4.x, a, o[0]);
+                o[1] = fmaf(y4.y, a, o[1]);
+                o[2] = fmaf(y4.z, a, o[2]);
+                o[3] = fmaf(y4.w, a, o[3]);
+            }
+            __syncthreads();
+            if (colJ < k) *reinterpret_cast<float4 *>(Ys + (size_t)colJ * R + 4 * g) = make_float4(o[0], o[1], o[2], o[3]);
+            ++J;
+            l = 0;
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int e = t; e < k * R; e += blockDim.x) {
+        const int c = e / R, r = e - c * R;
+        if (r0 + r < m) X[(r0 + r) + (int64_t)c * ldx] = Ys[e];
+    }
+}
+
 // X <- X L^-T (X m x k FP32) where the diagonal blocks of L hold their inverses
-// (put_block_inverses) and the blocks below them the factor itself.
+// (put_block_inverses) and the blocks below them the factor itself: one launch of the
+// row-block kernel when the rows of a block fit in shared memory, else one block column
+// per launch pair.
 cudaError_t strsm_right_lt_inv(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s)
 {
+    if (m <= 0 || k <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float) * ((size_t)k * kTrsmRows + 4 * 1024);
+    if (smem <= 227 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(strsm_lt_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        strsm_lt_rows_kernel<<<(m + kTrsmRows - 1) / kTrsmRows, 256, smem, s>>>(X, m, k, ldx, L, ldl);
+        return cudaGetLastError();
+    }
     for (int J = 0; J < k; J += 32) {
         const int jb = (k - J < 32) ? k - J : 32;
         count_launch();
@@ -471,142 +595,156 @@ __global__ void shift_diag_kernel(double *G, int k, int64_t ldg, double shift_sc
     for (int i = threadIdx.x; i < k; i += blockDim.x) G[i + i * ldg] += sh;
 }
 
-// Inverse of a lower-triangular jb x jb block held in shared memory: thread
-// c (< jb) solves L y = e_c by right-looking substitution (independent
-// chains per column); rinv holds 1/L_ii.  Writes Linv (ld NB) to out.
-__device__ void tri_inverse_smem(const double (*a)[NB + 1], const double *rinv, int jb, double *out)
+// Cholesky of the jb x jb diagonal block at (J, J) by one CTA of 256 threads (the factor
+// only; the block inverses follow in one launch per factorisation).  FP64 issue costs about
+// 64 cycles per warp instruction on this GPU and the library rsqrt about 430, so the block
+// is a chain of jb pivots: thread 0 alone carries it (the next pivot from the current
+// column and its reciprocal square root) while warps 1..7 apply the rank-1 update of the
+// trailing triangle, one barrier per column.  The entries are enumerated from the
+// bottom-right corner, so the trailing triangle of the last m columns is a prefix of the
+// enumeration and stays spread over the update threads as it shrinks.  The updates use the
+// unscaled columns and 1 / d_j (l_ij l_cj = a_ij a_cj / d_j); the factor is scaled at the
+// end.  The first failing pivot is recorded in info (1-based); the factorisation continues
+// with pivot 1.
+__global__ void __launch_bounds__(256) potrf_kernel(double *G, int64_t ldg, int J, int jb, int *info)
 {
-    const int c = threadIdx.x;
-    if (c < NB) {
-        double v[NB];
-#pragma unroll
-        for (int i = 0; i < NB; ++i) v[i] = (i == c) ? 1.0 : 0.0;
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            if (i >= c && i < jb) {
-                v[i] *= rinv[i];
-#pragma unroll
-                for (int l = i + 1; l < NB; ++l)
-                    if (l < jb) v[l] = fma(-a[l][i], v[i], v[l]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < NB; ++i) out[i + NB * c] = (i >= c && i < jb && c < jb) ? v[i] : 0.0;
+    constexpr int kTri = NB * (NB - 1) / 2;   // entries of the trailing triangle after column 0
+    __shared__ double As[NB][NB + 1];
+    __shared__ double rsq[NB], rv[NB];
+    const int t = threadIdx.x, u = t - 32;
+    for (int e = t; e < NB * NB; e += blockDim.x) {
+        const int i = e & (NB - 1), c = e / NB;
+        As[i][c] = (i < jb && c < jb) ? (c <= i ? G[(J + i) + (int64_t)(J + c) * ldg] : 0.0) : (i == c ? 1.0 : 0.0);
     }
-}
-
-// Cholesky of the jb x jb diagonal block at (J, J) by one CTA of 128 threads,
-// then the inverse of the factor, written to dinv (NB x NB, column-major).
-// Factorisation: thread t holds row t / 4 of the block in registers, columns
-// t % 4 + 4 s (s < 8); per column j the pivot and the new column of L go
-// through shared memory (double-buffered, two barriers per column), and a
-// warp issues the FP64 update of a column slot only when some lane of it has
-// work: FP64 issue is the cost on this GPU.  Inverse: with L in shared
-// memory, four lanes per column c solve L x = e_c by forward substitution
-// (rows split by i mod 4, x_j passed by shuffles), so no block barrier is
-// needed.  The first failing pivot is recorded in info (1-based); the
-// factorisation continues with pivot 1.
-__global__ void __launch_bounds__(128) potrf_inv_kernel(double *G, int64_t ldg, int J, int jb, int *info, double *dinv)
-{
-    __shared__ double colb[2][NB];   // l_ij of column j, rows i > j
-    __shared__ double piv[2];
-    __shared__ double Ls[NB][NB + 1];
-    __shared__ double rinv[NB];
-    const int t = threadIdx.x, i = t >> 2, q = t & 3, w = t >> 5;
-    double a[NB / 4];
+    // this thread's entries e = u, u + 224, u + 448: (a, b), 0 <= a <= b, b-major from the
+    // corner, at row 31 - a and column 31 - b; active while b < m
+    int ei[3], ec[3], eb[3];
 #pragma unroll
-    for (int s = 0; s < NB / 4; ++s) {
-        const int c = 4 * s + q;
-        a[s] = (i < jb && c <= i) ? G[(J + i) + (int64_t)(J + c) * ldg] : 0.0;
-    }
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        if (j >= jb) break;
-        const int b = j & 1;
-        if (i == j && q == (j & 3)) {
-            double d = a[j >> 2];
-            if (!(d > 0.0) || !isfinite(d)) {
-                if (info[0] == 0) info[0] = J + j + 1;
-                d = 1.0;
-            }
-            const double r = rsqrt(d);
-            a[j >> 2] = d * r;
-            piv[b] = r;
-            rinv[j] = r;
+    for (int q = 0; q < 3; ++q) {
+        const int e = u + 224 * q;
+        ei[q] = ec[q] = 0;
+        eb[q] = NB;
+        if (u >= 0 && e < kTri) {
+            int b = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+            while ((b + 1) * (b + 2) / 2 <= e) ++b;
+            while (b > 0 && b * (b + 1) / 2 > e) --b;
+            const int a = e - b * (b + 1) / 2;
+            ei[q] = NB - 1 - a;
+            ec[q] = NB - 1 - b;
+            eb[q] = b;
         }
-        __syncthreads();
-        if (i > j && q == (j & 3)) {
-            a[j >> 2] *= piv[b];
-            colb[b][i] = a[j >> 2];
-        }
-        __syncthreads();
-        if (8 * w + 7 > j && i > j) {
-            const double lij = colb[b][i];
-#pragma unroll
-            for (int s = 0; s < NB / 4; ++s) {
-                const int c = 4 * s + q;
-                if (4 * s + 3 > j && 4 * s <= 8 * w + 7) {   // warp-uniform: some lane may have c in (j, i]
-                    if (c > j && c <= i) a[s] = fma(-lij, colb[b][c], a[s]);
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < NB / 4; ++s) {
-        const int c = 4 * s + q;
-        const double v = (i < jb && c < jb && c <= i) ? a[s] : 0.0;
-        Ls[i][c] = v;
-        if (i < jb && c < jb) G[(J + i) + (int64_t)(J + c) * ldg] = v;
     }
     __syncthreads();
-    // column c = t / 4 of X = L^-1; lane q keeps rows i = q + 4 s
-    {
-        const int c = t >> 2;
-        double xv[NB / 4];
-#pragma unroll
-        for (int s = 0; s < NB / 4; ++s) xv[s] = (4 * s + q == c) ? 1.0 : 0.0;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            if (j >= jb) break;
-            // x_j = x_j / l_jj is held by lane j % 4 of this column's group, slot j / 4
-            double xj = 0.0;
-            if (q == (j & 3)) {
-                xv[j >> 2] *= rinv[j];
-                xj = xv[j >> 2];
+    if (t == 0) {
+        double d = As[0][0];
+        if (!(d > 0.0) || !isfinite(d)) {
+            atomicCAS(info, 0, J + 1);
+            d = 1.0;
+        }
+        As[0][0] = d;
+        const double r = rsqrt(d);
+        rv[0] = r;
+        rsq[0] = r * r;
+    }
+    __syncthreads();
+    for (int j = 0; j < NB - 1; ++j) {
+        const int m = NB - 1 - j;
+        if (t == 0) {
+            // pivot j + 1 after this column's update (its entry is updated here only)
+            const double a = As[j + 1][j];
+            double d = fma(-a, a * rsq[j], As[j + 1][j + 1]);
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (j + 1 < jb) atomicCAS(info, 0, J + j + 2);
+                d = 1.0;
             }
-            xj = __shfl_sync(0xffffffffu, xj, (t & 31 & ~3) | (j & 3));
-            if (j >= 8 * w) {      // warp-uniform: columns of this warp are 8 w .. 8 w + 7 <= j possible
+            As[j + 1][j + 1] = d;
+            const double r = rsqrt(d);
+            rv[j + 1] = r;
+            rsq[j + 1] = r * r;
+        } else if (u >= 0) {
+            const double r2 = rsq[j];
 #pragma unroll
-                for (int s = 0; s < NB / 4; ++s) {
-                    const int r = 4 * s + q;
-                    if (4 * s + 3 > j) {
-                        if (r > j && c <= j) xv[s] = fma(-Ls[r][j], xj, xv[s]);
-                    }
-                }
+            for (int q = 0; q < 3; ++q) {
+                const int i = ei[q], c = ec[q];
+                if (eb[q] < m && !(c == j + 1 && i == j + 1)) As[i][c] = fma(-As[i][j], As[c][j] * r2, As[i][c]);
             }
         }
-#pragma unroll
-        for (int s = 0; s < NB / 4; ++s) {
-            const int r = 4 * s + q;
-            dinv[r + NB * c] = (r >= c && r < jb && c < jb) ? xv[s] : 0.0;
-        }
+        __syncthreads();
+    }
+    for (int e = t; e < NB * NB; e += blockDim.x) {
+        const int i = e & (NB - 1), c = e / NB;
+        if (i < jb && c < jb && c <= i) G[(J + i) + (int64_t)(J + c) * ldg] = As[i][c] * rv[c];
     }
 }
 
-// Inverses of all diagonal blocks of a factored lower-triangular k x k L.
-__global__ void __launch_bounds__(32) trtri_diag_kernel(const double *L, int k, int64_t ldl, double *dinv)
+// A21 <- A21 L11^-T for the m2 rows below the diagonal block (L11 at L, factored): one warp
+// per row, lane l holds column l.  Column c is final once the earlier columns are subtracted;
+// with the columns of L11 pre-scaled by 1 / l_cc, each step is one shuffle of the unscaled
+// x_c and one FMA on the later lanes (a chain of jb steps per row, all rows in parallel), and
+// every lane is scaled by 1 / l_ll at the end.
+__global__ void __launch_bounds__(128) panel_trsm_kernel(double *A21, int m2, int64_t lda, const double *L, int64_t ldl,
+                                                         int jb)
+{
+    __shared__ double Ls[NB][NB + 1];   // L_lc / l_cc below the diagonal
+    __shared__ double rv[NB];
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) rv[i] = (i < jb) ? 1.0 / L[i + (int64_t)i * ldl] : 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e & (NB - 1), c = e / NB;
+        Ls[i][c] = (i < jb && c < i) ? L[i + (int64_t)c * ldl] * rv[c] : 0.0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= m2) return;
+    double x = (lane < jb) ? A21[r + (int64_t)lane * lda] : 0.0;
+#pragma unroll
+    for (int c = 0; c < NB - 1; ++c) {
+        const double xc = __shfl_sync(0xffffffffu, x, c);
+        if (lane > c) x = fma(-Ls[lane][c], xc, x);
+    }
+    if (lane < jb) A21[r + (int64_t)lane * lda] = x * rv[lane];
+}
+
+// Inverses of all diagonal blocks of a factored lower-triangular k x k L (one CTA of 256
+// threads per block, written to dinv, NB x NB column-major each).  Column c of X = L^-1 by
+// right-looking substitution with lane = column: the rows are split over the 8 warps (rows
+// g, g + 8, ...), so a step is one multiply by the warp that owns row i, a barrier, and at
+// most four FMAs per warp on the rows below.
+__global__ void __launch_bounds__(256) trtri_diag_kernel(const double *L, int k, int64_t ldl, double *dinv)
 {
     __shared__ double a[NB][NB + 1];
+    __shared__ double xs[NB][NB + 1];   // row i of X, published when final
     __shared__ double rinv[NB];
     const int J = blockIdx.x * NB;
     const int jb = (k - J < NB) ? k - J : NB;
-    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
-        const int i = e % jb, c = e / jb;
-        a[i][c] = L[(J + i) + (int64_t)(J + c) * ldl];
+    const int t = threadIdx.x, c = t & 31, g = t >> 5;
+    for (int e = t; e < NB * NB; e += blockDim.x) {
+        const int i = e & (NB - 1), j = e / NB;
+        a[i][j] = (i < jb && j < jb) ? L[(J + i) + (int64_t)(J + j) * ldl] : 0.0;
     }
-    for (int i = threadIdx.x; i < jb; i += blockDim.x) rinv[i] = 1.0 / L[(J + i) + (int64_t)(J + i) * ldl];
+    for (int i = t; i < NB; i += blockDim.x) rinv[i] = (i < jb) ? 1.0 / L[(J + i) + (int64_t)(J + i) * ldl] : 0.0;
     __syncthreads();
-    tri_inverse_smem(a, rinv, jb, dinv + (int64_t)blockIdx.x * NB * NB);
+    double v[NB / 8];
+#pragma unroll
+    for (int s = 0; s < NB / 8; ++s) v[s] = (8 * s + g == c) ? 1.0 : 0.0;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        if (g == (i & 7)) {
+            v[i >> 3] *= rinv[i];
+            xs[i][c] = v[i >> 3];
+        }
+        __syncthreads();
+        const double xi = xs[i][c];
+#pragma unroll
+        for (int s = 0; s < NB / 8; ++s)
+            if (8 * s + g > i) v[s] = fma(-a[8 * s + g][i], xi, v[s]);
+    }
+    double *out = dinv + (int64_t)blockIdx.x * NB * NB;
+#pragma unroll
+    for (int s = 0; s < NB / 8; ++s) {
+        const int r = 8 * s + g;
+        out[r + NB * c] = (r >= c && r < jb && c < jb) ? v[s] : 0.0;
+    }
 }
 
 // X[r, 0:jb] <- X[r, 0:jb] M^T (trans = 1) or X[r, 0:jb] M (trans = 0) in
@@ -707,26 +845,28 @@ cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *inf
     if (shift_scale > 0.0) { count_launch(); shift_diag_kernel<<<1, 1024, 0, s>>>(G, k, ldg, shift_scale); }
     for (int J = 0; J < k; J += NB) {
         const int jb = (k - J < NB) ? k - J : NB;
-        double *inv = dinv + (int64_t)(J / NB) * NB * NB;
-        { count_launch(); potrf_inv_kernel<<<1, 128, 0, s>>>(G, ldg, J, jb, info, inv); }
+        { count_launch(); potrf_kernel<<<1, 256, 0, s>>>(G, ldg, J, jb, info); }
         const int m2 = k - J - jb;
         if (m2 > 0) {
             double *A21 = G + (J + jb) + (int64_t)J * ldg;
             // A21 <- A21 L11^-T
-            { count_launch(); trmm_rows_kernel<<<(m2 + 7) / 8, 256, 0, s>>>(A21, m2, ldg, inv, jb, 1); }
+            { count_launch(); panel_trsm_kernel<<<(m2 + 3) / 4, 128, 0, s>>>(A21, m2, ldg, G + J + (int64_t)J * ldg, ldg, jb); }
             // A22 -= A21 A21^T, lower tiles only (the factorisation never reads above the diagonal)
             double *A22 = G + (J + jb) + (int64_t)(J + jb) * ldg;
             e = gemm16('N', 'T', m2, m2, jb, -1.0, A21, ldg, A21, ldg, 1.0, A22, ldg, s, 1);
             if (e != cudaSuccess) return e;
         }
     }
+    // the block inverses that the triangular solves multiply by
+    count_launch();
+    trtri_diag_kernel<<<(k + NB - 1) / NB, 256, 0, s>>>(G, k, ldg, dinv);
     return cudaGetLastError();
 }
 
 cudaError_t trtri_diag(const double *L, int k, int64_t ldl, double *dinv, cudaStream_t s)
 {
     count_launch();
-    trtri_diag_kernel<<<(k + NB - 1) / NB, 32, 0, s>>>(L, k, ldl, dinv);
+    trtri_diag_kernel<<<(k + NB - 1) / NB, 256, 0, s>>>(L, k, ldl, dinv);
     return cudaGetLastError();
 }
 
