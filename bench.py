@@ -869,7 +869,20 @@ def main():
     l96_traffic, l96_traffic_note = profiled_traffic("l96_hvp_tma_kernel_n4096_T200_k512.md", "l96_tma.cu")
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32_nominal = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
+    try:   # FP32 / FP64 FMA throughput and FP64 latencies of this GPU, measured by the library
+        alu = R.riot_measure_peaks(dev.index or 0)
+    except R.RiotError as e:
+        alu = {"error": str(e)}
+    fp32_peak = alu.get("fp32_tflops", fp32_nominal)
+    fp32_basis = ("measured: FP32 FMA throughput of riot_measure_peaks (8 independent chains per thread, "
+                  "4 x 256 threads per SM), nominal %d SMs x 128 lanes x 2 x %.0f MHz = %.1f TFLOP/s"
+                  % (sm_count, sm_max, fp32_nominal)) if "fp32_tflops" in alu else \
+        "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sm_count, sm_max)
+    # FP64 work of the k x k chain (orth, K, eig) at algorithmic counts: 8 Cholesky factorisations
+    # (k^3 / 3), M M^T (k^3) and N M^T (2 k^3), 4 triangular solves on k x k (k^3), the
+    # tridiagonalisation and the accumulation of its Q (4/3 k^3 each), 2 eigenvector Grams (k^3)
+    fp64_chain_flop = (8.0 / 3 + 3 + 4 + 8.0 / 3 + 2) * float(k) ** 3
 
     # ---- end to end through the C ABI with host buffers ------------------------------
     Om_host = torch.from_numpy(cfg.sketch(0).astype(np.float32)).pin_memory()
@@ -990,13 +1003,22 @@ def main():
             "roofline": {"bound": "alu", "kernel": "l96_hvp_tma_kernel<8,2,512>", "achieved": achieved,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "traffic": l96_traffic, "traffic_source": l96_traffic_note,
-                         "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sm_count, sm_max),
+                         "peak_basis": fp32_basis,
                          "flop_per_hvp": flop_hvp, "hvp_per_launch": k, "launch_ms": hvp_launch_ms},
             "e2e": {"value": world * hvps_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(n * k * 4),
                     "d2h_bytes_per_step": int(n * 8 + k * 8)},
             "gpu_launches": int(launches),
             "wall_s_timed": wall}
     line["mixed_cost_reduction"] = {"value": red_mixed, "pairs_retained": pairs_mixed}
+    chain_ms = ph["orth"] + ph["kmat"] + ph["eig"]
+    line["fp64_chain"] = {
+        "what": "the k x k FP64 linear algebra of the inner loop (CholeskyQR factorisations, K, eigensolver): "
+                "latency-bound on this GPU (FP64 FMA latency and the serial pivots / reflectors)",
+        "ms": chain_ms, "share_of_step": chain_ms / ms, "fp64_flop": fp64_chain_flop,
+        "achieved_tflops": fp64_chain_flop / (chain_ms * 1e-3) / 1e12,
+        "peak_tflops": alu.get("fp64_tflops"),
+        "frac": (fp64_chain_flop / (chain_ms * 1e-3) / 1e12 / alu["fp64_tflops"]) if "fp64_tflops" in alu else None,
+        "measured_alu": alu}
     if comparators:
         line["paper_comparison"] = {
             "what": "the paper's inner loops on the same window, each one call after an L2 flush: RIOT "

@@ -388,6 +388,20 @@ int32_t riot_rsvd_sweeps(const riot_ctx *ctx);
  * contexts); a benchmark reads it before and after a timed region. */
 uint64_t riot_kernel_launches(void);
 
+/* Measured arithmetic peaks of GPU `device` (a measurement utility for the
+ * roofline fractions of the ALU-bound kernels, not part of the method):
+ *   out[0] FP64 FMA throughput, TFLOP/s (eight independent FMA chains per
+ *          thread, four CTAs of 256 threads per SM, best of three launches
+ *          timed with CUDA events after one warm-up);
+ *   out[1] FP32 FMA throughput, TFLOP/s (the same kernel in FP32);
+ *   out[2] FP64 FMA latency, SM cycles per dependent FMA (one thread);
+ *   out[3] FP64 rsqrt latency, SM cycles per dependent rsqrt + add;
+ *   out[4] FP64 division latency, SM cycles per dependent division + add.
+ * Writes min(nout, 5) values.  Runs on its own stream, allocates about
+ * 2 MB for the run, synchronises; takes about 30 ms.  RIOT_EINVAL for a null
+ * out or nout < 1, RIOT_ECUDA for a CUDA error. */
+riot_status riot_measure_peaks(int32_t device, double *out, int32_t nout);
+
 /* ---- Batches of windows ------------------------------------------------------
  * Many independent Lorenz-96 windows (contexts of any n, T, observations and
  * k) run their inner loops together: the Hessian products of all windows in

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libriot.so")
-SOURCES = ["l96.cu", "l96_tma.cu", "l96_warp.cu", "advdiff.cu", "sketchnet.cu", "tc_gemm.cu", "rng.cu", "linalg.cu", "eig.cu", "api.cu"]
+SOURCES = ["l96.cu", "l96_tma.cu", "l96_warp.cu", "advdiff.cu", "sketchnet.cu", "tc_gemm.cu", "rng.cu", "linalg.cu", "eig.cu", "peaks.cu", "api.cu"]
 HEADERS = ["internal.h"]
 ARCH = ["-gencode=arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -427,10 +427,13 @@ __global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int
     const int t = threadIdx.x, cj = t & 31, g = t >> 5;
     const int r0 = blockIdx.x * R;
     const int nb = (k + 31) / 32, nblk = nb * (nb + 1) / 2;
+    // the rows, all in flight at once (one group, completed with the first block of L)
     for (int e = t; e < k * R; e += blockDim.x) {
         const int c = e / R, r = e - c * R;
-        Ys[e] = (r0 + r < m) ? X[(r0 + r) + (int64_t)c * ldx] : 0.f;
+        if (r0 + r < m) cp_async4(Ys + e, X + (r0 + r) + (int64_t)c * ldx);
+        else Ys[e] = 0.f;
     }
+    cp_async_commit();
     // block b of the sweep is (J, l), l = 0..J (l = J: the diagonal block)
     int iJ = 0, il = 0;   // the next block to issue
     auto issue = [&](int slot) {
@@ -606,22 +609,29 @@ __global__ void shift_diag_kernel(double *G, int k, int64_t ldg, double shift_sc
 // unscaled columns and 1 / d_j (l_ij l_cj = a_ij a_cj / d_j); the factor is scaled at the
 // end.  The first failing pivot is recorded in info (1-based); the factorisation continues
 // with pivot 1.
-__global__ void __launch_bounds__(256) potrf_kernel(double *G, int64_t ldg, int J, int jb, int *info)
+__device__ __forceinline__ bool positive_finite(double d)
+{
+    const long long bits = __double_as_longlong(d);
+    return bits > 0 && bits < 0x7ff0000000000000LL;
+}
+
+// The factorisation of a block held in shared memory (As, padded with the identity to NB x NB),
+// by all 256 threads of the CTA; writes the factor to G at (J, J).  Warps 0 and 4 share a
+// sub-partition (and its FP64 unit, one warp instruction per ~64 cycles): warp 0 carries the
+// pivot chain and warp 4 stays idle, so no update instruction queues ahead of the chain.
+__device__ void potrf_smem(double (*As)[NB + 1], double *rsq, double *rv, double *G, int64_t ldg, int J, int jb,
+                           int *info)
 {
     constexpr int kTri = NB * (NB - 1) / 2;   // entries of the trailing triangle after column 0
-    __shared__ double As[NB][NB + 1];
-    __shared__ double rsq[NB], rv[NB];
-    const int t = threadIdx.x, u = t - 32;
-    for (int e = t; e < NB * NB; e += blockDim.x) {
-        const int i = e & (NB - 1), c = e / NB;
-        As[i][c] = (i < jb && c < jb) ? (c <= i ? G[(J + i) + (int64_t)(J + c) * ldg] : 0.0) : (i == c ? 1.0 : 0.0);
-    }
-    // this thread's entries e = u, u + 224, u + 448: (a, b), 0 <= a <= b, b-major from the
+    constexpr int kUpd = 192;                 // update threads: warps 1, 2, 3, 5, 6, 7
+    const int t = threadIdx.x, w = t >> 5;
+    const int u = (w == 0 || w == 4) ? -1 : (w < 4 ? t - 32 : t - 64);
+    // this thread's entries e = u, u + 192, u + 384: (a, b), 0 <= a <= b, b-major from the
     // corner, at row 31 - a and column 31 - b; active while b < m
     int ei[3], ec[3], eb[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const int e = u + 224 * q;
+        const int e = u + kUpd * q;
         ei[q] = ec[q] = 0;
         eb[q] = NB;
         if (u >= 0 && e < kTri) {
@@ -634,10 +644,9 @@ __global__ void __launch_bounds__(256) potrf_kernel(double *G, int64_t ldg, int 
             eb[q] = b;
         }
     }
-    __syncthreads();
     if (t == 0) {
         double d = As[0][0];
-        if (!(d > 0.0) || !isfinite(d)) {
+        if (!positive_finite(d)) {
             atomicCAS(info, 0, J + 1);
             d = 1.0;
         }
@@ -650,10 +659,11 @@ __global__ void __launch_bounds__(256) potrf_kernel(double *G, int64_t ldg, int 
     for (int j = 0; j < NB - 1; ++j) {
         const int m = NB - 1 - j;
         if (t == 0) {
-            // pivot j + 1 after this column's update (its entry is updated here only)
+            // pivot j + 1 after this column's update (its entry is updated here only); a
+            // positive finite double is a bit pattern strictly between 0 and +inf
             const double a = As[j + 1][j];
             double d = fma(-a, a * rsq[j], As[j + 1][j + 1]);
-            if (!(d > 0.0) || !isfinite(d)) {
+            if (!positive_finite(d)) {
                 if (j + 1 < jb) atomicCAS(info, 0, J + j + 2);
                 d = 1.0;
             }
@@ -675,6 +685,97 @@ __global__ void __launch_bounds__(256) potrf_kernel(double *G, int64_t ldg, int 
         const int i = e & (NB - 1), c = e / NB;
         if (i < jb && c < jb && c <= i) G[(J + i) + (int64_t)(J + c) * ldg] = As[i][c] * rv[c];
     }
+}
+
+__global__ void __launch_bounds__(256) potrf_kernel(double *G, int64_t ldg, int J, int jb, int *info)
+{
+    __shared__ double As[NB][NB + 1];
+    __shared__ double rsq[NB], rv[NB];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e & (NB - 1), c = e / NB;
+        As[i][c] = (i < jb && c < jb) ? (c <= i ? G[(J + i) + (int64_t)(J + c) * ldg] : 0.0) : (i == c ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    potrf_smem(As, rsq, rv, G, ldg, J, jb, info);
+}
+
+// One step of the blocked Cholesky after the panel of block column J (rows J + jb.. solved):
+// the trailing update A22 -= A21 A21^T in 16 x 16 lower tiles, fused with the next diagonal
+// block.  CTA (0, 0) updates the jb2 x jb2 block at the top of A22 itself and factors it at
+// once, while the other CTAs update the rest (the tiles of that block are skipped), so the
+// next pivot chain starts without waiting for the whole trailing update.
+__global__ void __launch_bounds__(256) chol_trail_kernel(double *G, int64_t ldg, int k, int J, int jb, int *info)
+{
+    const int r0 = J + jb, m2 = k - r0;
+    const int bx = blockIdx.x, by = blockIdx.y, t = threadIdx.x;
+    __shared__ double As[NB][NB + 1];
+    __shared__ double Ps[NB][NB + 1];
+    __shared__ double rsq[NB], rv[NB];
+    if (bx == 0 && by == 0) {
+        const int jb2 = m2 < NB ? m2 : NB;
+        for (int e = t; e < NB * NB; e += blockDim.x) {
+            const int i = e & (NB - 1), c = e / NB;
+            As[i][c] = (i < jb2 && c < jb2) ? (c <= i ? G[(r0 + i) + (int64_t)(r0 + c) * ldg] : 0.0) : (i == c ? 1.0 : 0.0);
+            Ps[i][c] = (i < jb2 && c < jb) ? G[(r0 + i) + (int64_t)(J + c) * ldg] : 0.0;
+        }
+        __syncthreads();
+        // the block's own update, lower triangle (entries row-major: e -> (i, c), c <= i)
+        double upd[3];
+        int ui[3], uc[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int e = t + 256 * q;
+            ui[q] = -1;
+            uc[q] = 0;
+            upd[q] = 0.0;
+            if (e < NB * (NB + 1) / 2) {
+                int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                while (i > 0 && i * (i + 1) / 2 > e) --i;
+                ui[q] = i;
+                uc[q] = e - i * (i + 1) / 2;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (ui[q] >= 0) {
+                const int i = ui[q], c = uc[q];
+                double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+                for (int kk = 0; kk < NB; kk += 2) {
+                    a0 = fma(Ps[i][kk], Ps[c][kk], a0);
+                    a1 = fma(Ps[i][kk + 1], Ps[c][kk + 1], a1);
+                }
+                upd[q] = a0 + a1;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (ui[q] >= 0 && ui[q] < jb2) As[ui[q]][uc[q]] -= upd[q];
+        __syncthreads();
+        potrf_smem(As, rsq, rv, G, ldg, r0, jb2, info);
+        return;
+    }
+    if (by > bx || (bx < 2 && by < 2)) return;
+    // tile (bx, by) of A22: rows r0 + 16 bx.., columns r0 + 16 by.. (As, Ps as [kk][16] stores)
+    const int tx = t & 15, ty = t >> 4;
+    const int mi = r0 + 16 * bx, nj = r0 + 16 * by;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int e = t + 256 * q, i = e & 15, kk = e >> 4;
+        As[kk][i] = (16 * bx + i < m2 && kk < jb) ? G[(mi + i) + (int64_t)(J + kk) * ldg] : 0.0;
+        Ps[kk][i] = (16 * by + i < m2 && kk < jb) ? G[(nj + i) + (int64_t)(J + kk) * ldg] : 0.0;
+    }
+    __syncthreads();
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < NB; kk += 2) {
+        a0 = fma(As[kk][tx], Ps[kk][ty], a0);
+        a1 = fma(As[kk + 1][tx], Ps[kk + 1][ty], a1);
+    }
+    const int i = 16 * bx + tx, j = 16 * by + ty;
+    if (i < m2 && j < m2 && j <= i) G[(r0 + i) + (int64_t)(r0 + j) * ldg] -= a0 + a1;
 }
 
 // A21 <- A21 L11^-T for the m2 rows below the diagonal block (L11 at L, factored): one warp
@@ -843,19 +944,17 @@ cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *inf
     cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (shift_scale > 0.0) { count_launch(); shift_diag_kernel<<<1, 1024, 0, s>>>(G, k, ldg, shift_scale); }
+    // potrf of block 0, then per block column: the panel below it, and the trailing update
+    // fused with the factorisation of the next diagonal block
+    { count_launch(); potrf_kernel<<<1, 256, 0, s>>>(G, ldg, 0, k < NB ? k : NB, info); }
     for (int J = 0; J < k; J += NB) {
         const int jb = (k - J < NB) ? k - J : NB;
-        { count_launch(); potrf_kernel<<<1, 256, 0, s>>>(G, ldg, J, jb, info); }
         const int m2 = k - J - jb;
-        if (m2 > 0) {
-            double *A21 = G + (J + jb) + (int64_t)J * ldg;
-            // A21 <- A21 L11^-T
-            { count_launch(); panel_trsm_kernel<<<(m2 + 3) / 4, 128, 0, s>>>(A21, m2, ldg, G + J + (int64_t)J * ldg, ldg, jb); }
-            // A22 -= A21 A21^T, lower tiles only (the factorisation never reads above the diagonal)
-            double *A22 = G + (J + jb) + (int64_t)(J + jb) * ldg;
-            e = gemm16('N', 'T', m2, m2, jb, -1.0, A21, ldg, A21, ldg, 1.0, A22, ldg, s, 1);
-            if (e != cudaSuccess) return e;
-        }
+        if (m2 <= 0) break;
+        double *A21 = G + (J + jb) + (int64_t)J * ldg;
+        { count_launch(); panel_trsm_kernel<<<(m2 + 3) / 4, 128, 0, s>>>(A21, m2, ldg, G + J + (int64_t)J * ldg, ldg, jb); }
+        const int nt = (m2 + 15) / 16;
+        { count_launch(); chol_trail_kernel<<<dim3(nt, nt), 256, 0, s>>>(G, ldg, k, J, jb, info); }
     }
     // the block inverses that the triangular solves multiply by
     count_launch();

@@ -145,6 +145,8 @@ def load():
     L.riot_rsvd_sweeps.restype = c_int32
     L.riot_kernel_launches.argtypes = []
     L.riot_kernel_launches.restype = c_uint64
+    L.riot_measure_peaks.argtypes = [c_int32, POINTER(c_double), c_int32]
+    L.riot_measure_peaks.restype = c_int32
     L.riot_destroy.argtypes = [vp]
     L.riot_destroy.restype = None
     L.riot_batch_create.argtypes = [POINTER(vp), POINTER(vp), c_int32, POINTER(c_int32), c_int32, vp]
@@ -410,6 +412,15 @@ def riot_rsvd_sweeps(ctx):
 
 def riot_kernel_launches():
     return int(load().riot_kernel_launches())
+
+
+def riot_measure_peaks(device=0):
+    """Measured FP64 / FP32 FMA throughput (TFLOP/s) and FP64 FMA, rsqrt and division latencies
+    (SM cycles) of a GPU, as a dict."""
+    out = (c_double * 5)()
+    _check(None, "riot_measure_peaks", load().riot_measure_peaks(int(device), out, 5))
+    keys = ("fp64_tflops", "fp32_tflops", "fp64_fma_cycles", "fp64_rsqrt_cycles", "fp64_div_cycles")
+    return dict(zip(keys, (float(v) for v in out)))
 
 
 def riot_destroy(ctx):
