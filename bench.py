@@ -390,13 +390,13 @@ def bench_bc_transport(R, torch, dev, flush, hbm_peak, ncols=128, reps=2):
     ncells = cfg.nx * cfg.ny * cfg.nz
     bytes_per_hvp = 8.0 * ncells * cfg.T * 2
     # measured DRAM bytes of one step of one column, times the 2T steps of a product
-    step_bytes, bc_note = profiled_traffic("adv_step_kernel_bc_192x192x30_P32.md", "advdiff.cu")
+    step_bytes, bc_note = profiled_traffic("adv_step_f2_kernel_bc_192x192x30_P32.md", "advdiff.cu")
     bc_traffic = None if step_bytes is None else step_bytes * 2 * cfg.T
     achieved = bytes_per_hvp * ncols / (ms * 1e-3) / 1e9
     return {"workload": "bc_%dx%dx%d_T%d_obs%d_blocks%d" % (cfg.nx, cfg.ny, cfg.nz, cfg.T, p, cfg.nblocks),
             "value": ncols / (ms * 1e-3), "unit": "HVP/s", "ms_per_hvp": ms / ncols, "columns_per_call": ncols,
             "dtype": "f32",
-            "roofline": {"bound": "hbm", "kernel": "adv_step_kernel<float,32,32,4> (whole product timed)",
+            "roofline": {"bound": "hbm", "kernel": "adv_step_f2_kernel<15,32,8> (whole product timed)",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                          "traffic": bc_traffic, "traffic_source": bc_note, "bytes_per_hvp": bytes_per_hvp,
                          "bytes_basis": "one FP32 read and write of the tracer per RK4 step, TL and AD"}}

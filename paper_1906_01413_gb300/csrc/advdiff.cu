@@ -149,6 +149,141 @@ __global__ void __launch_bounds__((TX + 2 * kHalo) * (TY + 2 * kHalo), 1) adv_st
     }
 }
 
+// FP32 stepper: nested RK4 on pairs of levels with packed FP32x2 arithmetic.  For the
+// linear autonomous tendency f(w) = A w + s of one step, RK4 gives c+ = P(hA) c + h Q(hA) s,
+// P and Q the Taylor polynomials of degree 4 and 3 of exp(z) and (exp(z) - 1) / z.  Nested
+// (Horner), that is w <- c + a (A w + s) for a = h/4, h/3, h/2, h from w = c, the last w being
+// c+: the same four applications of A as the classical stages, with one state array besides
+// c instead of two.  The adjoint P(hA^T) lam is the same recursion with A^T and no source;
+// the input of its last stage is Q(hA^T) lam, so the source adjoint is h times its level 0.
+// Levels are held in pairs (2p, 2p + 1) (padded with zero coefficients beyond nz) and
+// combined by packed FP32x2 instructions, one instruction for two levels; the shared planes
+// hold the pairs, so a horizontal neighbour fetch is one 64-bit load for two levels.  (Pairs
+// (p, p + NZP), whose vertical neighbours are whole pairs, measured slower: the renamed
+// stage inputs cost registers.)  Tiles and halo as in adv_step_kernel.
+struct StepArgsF2 {
+    float2 amp2[16];   // (amp of level 2p, of level 2p + 1); 0 beyond nz
+    float2 ku2[16];    // Kz / dz^2 on the face above each level of the pair
+    float2 kl2[16];    // on the face below
+    float2 nkd2[16];   // -(ku + kl)
+    const float *cin;
+    float *cout;
+    long long pstride;
+    const float *src;
+    long long sstride;
+    float *ebar;
+    long long estride;
+    const float *u, *v;
+    int nx, ny, nz;
+    float h, rdx, rdy;
+};
+
+// registers per thread that still fit one CTA of `threads` on an SM (registers go to warps in
+// groups of four, in steps of 8 per thread)
+constexpr int regs_for(int threads)
+{
+    return ((65536 / ((threads + 127) / 128 * 128)) / 8 * 8) > 255 ? 255 : (65536 / ((threads + 127) / 128 * 128)) / 8 * 8;
+}
+
+template <int NZP, int TX, int TY, bool ADJ>
+__global__ void __maxnreg__(regs_for((TX + 2 * kHalo) * (TY + 2 * kHalo))) adv_step_f2_kernel(StepArgsF2 a)
+{
+    constexpr int RX = TX + 2 * kHalo, RY = TY + 2 * kHalo, PL = RX * RY;
+    extern __shared__ __align__(16) unsigned char adv2_smem[];
+    float2 *S0 = reinterpret_cast<float2 *>(adv2_smem);   // [2][NZP][RY][RX]
+    const int tid = threadIdx.x;
+    const int rx = tid % RX, ry = tid / RX;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    int gx = (x0 - kHalo + rx) % nx;
+    if (gx < 0) gx += nx;
+    const int gy = y0 - kHalo + ry;
+    const bool valid = gy >= 0 && gy < ny;
+    const size_t plane = (size_t)nx * ny;
+    const size_t col = valid ? (size_t)gy * nx + gx : 0;
+    float c0 = 0.f, cE = 0.f, cW = 0.f, cN = 0.f, cS = 0.f;
+    if (valid) {
+        const float uL = a.u[col], uR = a.u[(size_t)gy * nx + (gx + 1 == nx ? 0 : gx + 1)];
+        const float vS = a.v[col], vN = a.v[col + nx];
+        const float uLp = fmaxf(uL, 0.f), uLm = fminf(uL, 0.f);
+        const float uRp = fmaxf(uR, 0.f), uRm = fminf(uR, 0.f);
+        const float vSp = fmaxf(vS, 0.f), vSm = fminf(vS, 0.f);
+        const float vNp = fmaxf(vN, 0.f), vNm = fminf(vN, 0.f);
+        c0 = (uLm - uRp) * a.rdx + (vSm - vNp) * a.rdy;
+        if (!ADJ) {
+            cE = -uRm * a.rdx;
+            cW = uLp * a.rdx;
+            cN = -vNm * a.rdy;
+            cS = vSp * a.rdy;
+        } else {
+            cE = uRp * a.rdx;
+            cW = -uLm * a.rdx;
+            cN = vNp * a.rdy;
+            cS = -vSm * a.rdy;
+        }
+    }
+    const float2 C0 = make_float2(c0, c0), CE = make_float2(cE, cE), CW = make_float2(cW, cW);
+    const float2 CN = make_float2(cN, cN), CS = make_float2(cS, cS);
+    const size_t pb = (size_t)blockIdx.z * a.pstride;
+    float2 c[NZP], w[NZP];
+#pragma unroll
+    for (int p = 0; p < NZP; ++p) {
+        const int z0 = 2 * p, z1 = 2 * p + 1;
+        c[p].x = (valid && z0 < nz) ? a.cin[pb + z0 * plane + col] : 0.f;
+        c[p].y = (valid && z1 < nz) ? a.cin[pb + z1 * plane + col] : 0.f;
+        w[p] = c[p];
+    }
+    float s0 = 0.f;
+    if (!ADJ && valid && a.src) s0 = a.src[(size_t)blockIdx.z * a.sstride + col];
+    float e0 = 0.f;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        float2 *S = S0 + (st & 1) * NZP * PL;
+        // the stage input on the region of this stage grown by one column; rows beyond the
+        // walls publish their zeros
+        if (rx >= st && rx < RX - st && ry >= st && ry < RY - st) {
+#pragma unroll
+            for (int p = 0; p < NZP; ++p) S[p * PL + ry * RX + rx] = w[p];
+        }
+        if (ADJ && st == 3) e0 = w[0].x;
+        __syncthreads();
+        if (valid && rx > st && rx < RX - st - 1 && ry > st && ry < RY - st - 1) {
+            const float al = (st == 0) ? 0.25f * a.h : (st == 1) ? a.h / 3.f : (st == 2) ? 0.5f * a.h : a.h;
+            const float2 AL = make_float2(al, al);
+            float below = 0.f;   // the stage input of level 2p - 1
+#pragma unroll
+            for (int p = 0; p < NZP; ++p) {
+                const float2 wo = w[p];
+                const float2 *Sp = S + p * PL + ry * RX + rx;
+                float2 hor = __fmul2_rn(C0, wo);
+                hor = __ffma2_rn(CE, Sp[1], hor);
+                hor = __ffma2_rn(CW, Sp[-1], hor);
+                hor = __ffma2_rn(CN, Sp[RX], hor);
+                hor = __ffma2_rn(CS, Sp[-RX], hor);
+                const float2 up = make_float2(wo.y, (p + 1 < NZP) ? w[p + 1].x : 0.f);
+                const float2 dn = make_float2(below, wo.x);
+                float2 k = __fmul2_rn(a.amp2[p], hor);
+                k = __ffma2_rn(a.ku2[p], up, k);
+                k = __ffma2_rn(a.kl2[p], dn, k);
+                k = __ffma2_rn(a.nkd2[p], wo, k);
+                if (!ADJ && p == 0) k.x += s0;
+                w[p] = __ffma2_rn(AL, k, c[p]);
+                below = wo.y;
+            }
+        }
+    }
+    const int ix = rx - kHalo, iy = ry - kHalo;
+    if (valid && ix >= 0 && ix < TX && iy >= 0 && iy < TY && x0 + ix < nx) {
+#pragma unroll
+        for (int p = 0; p < NZP; ++p) {
+            const int z0 = 2 * p, z1 = 2 * p + 1;
+            if (z0 < nz) a.cout[pb + z0 * plane + col] = w[p].x;
+            if (z1 < nz) a.cout[pb + z1 * plane + col] = w[p].y;
+        }
+        if (ADJ && a.ebar) a.ebar[(size_t)blockIdx.z * a.estride + col] += a.h * e0;
+    }
+}
+
 template <typename R>
 __global__ void obs_gather_kernel(const R *c, long long pstride, int o0, int no, const int *cell, const R *w,
                                   const R *rinv, R *r, long long rstride)
@@ -346,10 +481,67 @@ cudaError_t step_nz(const StepArgs<R> &a, int P, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int NZP, int TX, int TY, bool ADJ>
+cudaError_t step_f2_nz(const StepArgsF2 &a, int P, cudaStream_t s)
+{
+    constexpr int RX = TX + 2 * kHalo, RY = TY + 2 * kHalo;
+    const size_t smem = sizeof(float2) * 2 * (size_t)NZP * RX * RY;
+    auto kern = adv_step_f2_kernel<NZP, TX, TY, ADJ>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, P);
+    kern<<<grid, RX * RY, smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// FP32 steps: the packed nested kernel (levels in pairs; 32 x 8 tiles of 640 threads up to 30
+// levels, 24 x 8 tiles of 512 threads with 128 registers for 32 levels; measured on the
+// 30-level grid, 32 x 8 tiles at 96 registers beat 24 x 8 at 128, and beat a persistent form
+// that prefetched the next tile's input into the free plane, whose loop spilled registers)
+cudaError_t step_f32(const AdvDev &m, const float *cin, float *cout, int P, const float *src, long long sstride,
+                     float *ebar, long long estride, bool adj, cudaStream_t s)
+{
+    StepArgsF2 a;
+    const int nzp = m.nz <= 8 ? 4 : m.nz <= 16 ? 8 : m.nz <= 30 ? 15 : 16;
+    for (int p = 0; p < 16; ++p) {
+        const int z0 = 2 * p, z1 = 2 * p + 1;
+        auto kz = [&](int l) { return (l > 0 && l < m.nz) ? (float)(m.kz_h[l] / (m.dz * m.dz)) : 0.f; };
+        a.amp2[p] = make_float2(z0 < m.nz ? (float)m.amp_h[z0] : 0.f, z1 < m.nz ? (float)m.amp_h[z1] : 0.f);
+        a.ku2[p] = make_float2(kz(z0 + 1), kz(z1 + 1));
+        a.kl2[p] = make_float2(kz(z0), kz(z1));
+        a.nkd2[p] = make_float2(-(a.ku2[p].x + a.kl2[p].x), -(a.ku2[p].y + a.kl2[p].y));
+    }
+    a.cin = cin;
+    a.cout = cout;
+    a.pstride = m.ncells;
+    a.src = src;
+    a.sstride = sstride;
+    a.ebar = ebar;
+    a.estride = estride;
+    a.u = m.u32;
+    a.v = m.v32;
+    a.nx = m.nx;
+    a.ny = m.ny;
+    a.nz = m.nz;
+    a.h = (float)m.dt;
+    a.rdx = (float)(1.0 / m.dx);
+    a.rdy = (float)(1.0 / m.dy);
+    if (nzp == 4) return adj ? step_f2_nz<4, 32, 8, true>(a, P, s) : step_f2_nz<4, 32, 8, false>(a, P, s);
+    if (nzp == 8) return adj ? step_f2_nz<8, 32, 8, true>(a, P, s) : step_f2_nz<8, 32, 8, false>(a, P, s);
+    if (nzp == 15) return adj ? step_f2_nz<15, 32, 8, true>(a, P, s) : step_f2_nz<15, 32, 8, false>(a, P, s);
+    return adj ? step_f2_nz<16, 24, 8, true>(a, P, s) : step_f2_nz<16, 24, 8, false>(a, P, s);
+}
+
 template <typename R>
 cudaError_t step(const AdvDev &m, const R *cin, R *cout, int P, const R *src, long long sstride, R *ebar,
                  long long estride, bool adj, cudaStream_t s)
 {
+    if constexpr (sizeof(R) == sizeof(float)) return step_f32(m, cin, cout, P, src, sstride, ebar, estride, adj, s);
     StepArgs<R> a;
     a.cin = cin;
     a.cout = cout;
