@@ -77,6 +77,10 @@ def parse():
     ap.add_argument("--no-bc", action="store_true", help="skip the tracer-transport Hessian products")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch of 96 windows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned sketch proposal leg")
+    ap.add_argument("--learned-windows", type=int, default=64,
+                    help="training windows of the learned sketch leg (the workload names 2000: about 3 minutes "
+                         "of data generation)")
+    ap.add_argument("--learned-steps", type=int, default=500, help="training steps (batches of 8 windows)")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned inner-loop leg")
     ap.add_argument("--no-deflated", action="store_true", help="skip the deflated multi-level mixed-precision leg")
     ap.add_argument("--no-comparators", action="store_true",
@@ -811,7 +815,7 @@ def main():
         if args.profile:
             torch.cuda.profiler.start()
         if args.only == "learned":
-            out = bench_learned_sketch(R, torch, dev)
+            out = bench_learned_sketch(R, torch, dev, n_train=args.learned_windows, steps=args.learned_steps)
         elif args.only in ("varcg", "varbl", "psas"):
             out = bench_comparator(R, torch, dev, flush, args.only, args.warmup, max(1, args.steps))
         elif args.only == "hvp":
@@ -911,7 +915,7 @@ def main():
     # ---- tracer-transport inversion (workload 3): Hessian products on the full grid ----
     learned = None
     if not args.no_learned:
-        learned = bench_learned_sketch(R, torch, dev)
+        learned = bench_learned_sketch(R, torch, dev, n_train=args.learned_windows, steps=args.learned_steps)
     batch = None
     if not args.no_batch:
         batch = bench_batch(R, torch, dev, args.warmup, max(3, args.steps // 3))
