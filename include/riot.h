@@ -352,11 +352,17 @@ riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t r
  *    through its own ring, and meets only its two neighbouring warps, at a
  *    hardware named barrier per pair, after the elements that need no other
  *    thread's values (windows with 8 or 16 variables per thread and 64 to 512
- *    threads per column; others keep the default).
- * Measured on the 4096-variable, 200-step window: the default is faster
- * (the per-warp ring bookkeeping costs more instructions than the CTA barrier
- * costs waiting). */
-enum { RIOT_HVP_CTA_BARRIER = 0, RIOT_HVP_WARP_PAIRS = 1 };
+ *    threads per column; others keep the default);
+ *  RIOT_HVP_WARP_SHUFFLE: RIOT_HVP_WARP_PAIRS with the halo passed by warp
+ *    shuffles between the lanes of a warp, only the two edge lanes of each
+ *    warp going through shared memory.
+ * The two warp kernels give the same products bit for bit.  Measured on the
+ * 4096-variable, 200-step window (512 products per launch): 2.7 ms for the
+ * default, 3.0 ms with warp pairs, 3.4 ms with shuffles (the per-warp ring
+ * bookkeeping costs more instructions than the CTA barrier costs waiting,
+ * and the shuffles issue as many instructions as the shared-memory halo they
+ * replace while lengthening the path to the barrier). */
+enum { RIOT_HVP_CTA_BARRIER = 0, RIOT_HVP_WARP_PAIRS = 1, RIOT_HVP_WARP_SHUFFLE = 2 };
 riot_status riot_set_hvp_kernel(riot_ctx *ctx, int32_t kernel);
 
 /* Bound of every wait of the mixed-precision Hessian kernels (on a stage copy,

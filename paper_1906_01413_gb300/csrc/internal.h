@@ -116,7 +116,7 @@ size_t l96_coef_warp_floats4(const L96Dev &m);
 cudaError_t l96_coef_warp(const L96Dev &m, const double2 *coef64, float4 *coefw, cudaStream_t s);
 cudaError_t l96_hvp_warp_launch(const L96Dev &m, const float4 *coefw, const float *W, float *Y, int64_t ld, int ncols,
                                 int add_identity, float *r, int *err, cudaStream_t s, int S_hint = 0,
-                                int wait_polls = -1);
+                                int wait_polls = -1, bool shuffle = false);
 
 // Several Lorenz-96 windows' FP32 Hessian products (Y = A W) in one
 // persistent launch over a queue of (window, CTA block) items.

@@ -8,10 +8,11 @@
 //    variables (chunk t of the ring of n variables) of each probe in registers.
 //  * The periodic stencil's neighbours (i-2, i-1, i+1) cross chunk boundaries
 //    through a double-buffered shared-memory halo (each thread publishes the three
-//    values its neighbours need).  Instead of a CTA-wide barrier per stage, a warp
-//    meets only its two neighbouring warps, at a hardware named barrier per pair,
-//    and only after it has computed the elements of its chunks that need no value
-//    of another thread.
+//    values its neighbours need), or (SHFL) by warp shuffles between the lanes of a
+//    warp, only the two edge lanes of a warp publishing theirs for the neighbouring
+//    warps.  Instead of a CTA-wide barrier per stage, a warp meets only its two
+//    neighbouring warps, at a hardware named barrier per pair, and only after it has
+//    computed the elements of its chunks that need no value of another thread.
 //  * Every warp streams the stage coefficients (a, b) = (X_{i-1}, X_{i+1} - X_{i-2})
 //    of its own chunks, plus one pair of each neighbouring warp, from a per-warp
 //    contiguous block of global memory into its own ring of S shared-memory
@@ -220,7 +221,7 @@ __device__ __forceinline__ void band_apply_w(const float *st, const float *band,
     }
 }
 
-template <int E, int PR, bool RAGGED>
+template <int E, int PR, bool RAGGED, bool SHFL>
 __global__ void __launch_bounds__(512, 1) l96_hvp_warp_kernel(const WarpArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -324,13 +325,20 @@ __global__ void __launch_bounds__(512, 1) l96_hvp_warp_kernel(const WarpArgs a)
             }
 #pragma unroll 1
         for (int stg = 0; stg < 4; ++stg, ++c, ring.advance()) {
-            // publish the values the neighbouring threads need (last two valid, first)
+            // the values the neighbouring threads need (last two valid, first): published in
+            // shared memory (SHFL: shuffled inside the warp, published by the two edge lanes only)
             float *Hb = H + (size_t)(c & 1) * 3 * PR * nthr;
+            float v0[PR], v1[PR], v2[PR];
 #pragma unroll
             for (int r = 0; r < PR; ++r) {
-                Hb[(0 * PR + r) * nthr + tid] = full ? s[r][E - 2] : s[r][E - 3];
-                Hb[(1 * PR + r) * nthr + tid] = full ? s[r][E - 1] : s[r][E - 2];
-                Hb[(2 * PR + r) * nthr + tid] = s[r][0];
+                v0[r] = full ? s[r][E - 2] : s[r][E - 3];
+                v1[r] = full ? s[r][E - 1] : s[r][E - 2];
+                v2[r] = s[r][0];
+                if (!SHFL || lane == 0 || lane == rlane) {
+                    Hb[(0 * PR + r) * nthr + tid] = v0[r];
+                    Hb[(1 * PR + r) * nthr + tid] = v1[r];
+                    Hb[(2 * PR + r) * nthr + tid] = v2[r];
+                }
             }
             float m2[PR], m1[PR], p1[PR];
             ring.wait(c, abort_v, err);
@@ -353,13 +361,25 @@ __global__ void __launch_bounds__(512, 1) l96_hvp_warp_kernel(const WarpArgs a)
 #pragma unroll
                 for (int r = 0; r < PR; ++r)
                     kk[r][j] = fmaf(ca[j], s[r][j + 1] - s[r][j - 2], fmaf(cb[j], s[r][j - 1], -s[r][j]));
-            // ... then meet the neighbouring warps and take the neighbours' values
+            // ... then the neighbours' values from shared memory behind the pair barriers
+            // (SHFL: shuffles inside the warp, shared memory for the edge lanes only: lane 0
+            // from the warp before, the last live lane from the warp after)
+            if constexpr (SHFL) {
+#pragma unroll
+                for (int r = 0; r < PR; ++r) {
+                    m2[r] = __shfl_up_sync(0xffffffffu, v0[r], 1);
+                    m1[r] = __shfl_up_sync(0xffffffffu, v1[r], 1);
+                    p1[r] = __shfl_down_sync(0xffffffffu, v2[r], 1);
+                }
+            }
             meet_neighbours(w, wl);
 #pragma unroll
             for (int r = 0; r < PR; ++r) {
-                m2[r] = Hb[(0 * PR + r) * nthr + left];
-                m1[r] = Hb[(1 * PR + r) * nthr + left];
-                p1[r] = Hb[(2 * PR + r) * nthr + right];
+                if (!SHFL || lane == 0) {
+                    m2[r] = Hb[(0 * PR + r) * nthr + left];
+                    m1[r] = Hb[(1 * PR + r) * nthr + left];
+                }
+                if (!SHFL || lane >= rlane) p1[r] = Hb[(2 * PR + r) * nthr + right];
             }
 #pragma unroll
             for (int j = 0; j < E; ++j) {
@@ -431,11 +451,17 @@ __global__ void __launch_bounds__(512, 1) l96_hvp_warp_kernel(const WarpArgs a)
 #pragma unroll 1
         for (int stg = 0; stg < 4; ++stg, ++c, ring.advance()) {
             float *Hb = H + (size_t)(c & 1) * 3 * PR * nthr;
+            float u0[PR], u1[PR], u2[PR];
 #pragma unroll
             for (int r = 0; r < PR; ++r) {
-                Hb[(0 * PR + r) * nthr + tid] = full ? lk[r][E - 1] : lk[r][E - 2];
-                Hb[(1 * PR + r) * nthr + tid] = lk[r][0];
-                Hb[(2 * PR + r) * nthr + tid] = lk[r][1];
+                u0[r] = full ? lk[r][E - 1] : lk[r][E - 2];
+                u1[r] = lk[r][0];
+                u2[r] = lk[r][1];
+                if (!SHFL || lane == 0 || lane == rlane) {
+                    Hb[(0 * PR + r) * nthr + tid] = u0[r];
+                    Hb[(1 * PR + r) * nthr + tid] = u1[r];
+                    Hb[(2 * PR + r) * nthr + tid] = u2[r];
+                }
             }
             float mL[PR], mR0[PR], mR1[PR];
             ring.wait(c, abort_v, err);
@@ -463,12 +489,22 @@ __global__ void __launch_bounds__(512, 1) l96_hvp_warp_kernel(const WarpArgs a)
                 for (int r = 0; r < PR; ++r)
                     ls[r][j] = fmaf(ca[j - 1], lk[r][j - 1],
                                     fmaf(-ca[j + 2], lk[r][j + 2], fmaf(cb[j + 1], lk[r][j + 1], -lk[r][j])));
+            if constexpr (SHFL) {
+#pragma unroll
+                for (int r = 0; r < PR; ++r) {
+                    mL[r] = __shfl_up_sync(0xffffffffu, u0[r], 1);
+                    mR0[r] = __shfl_down_sync(0xffffffffu, u1[r], 1);
+                    mR1[r] = __shfl_down_sync(0xffffffffu, u2[r], 1);
+                }
+            }
             meet_neighbours(w, wl);
 #pragma unroll
             for (int r = 0; r < PR; ++r) {
-                mL[r] = Hb[(0 * PR + r) * nthr + left];
-                mR0[r] = Hb[(1 * PR + r) * nthr + right];
-                mR1[r] = Hb[(2 * PR + r) * nthr + right];
+                if (!SHFL || lane == 0) mL[r] = Hb[(0 * PR + r) * nthr + left];
+                if (!SHFL || lane >= rlane) {
+                    mR0[r] = Hb[(1 * PR + r) * nthr + right];
+                    mR1[r] = Hb[(2 * PR + r) * nthr + right];
+                }
             }
 #pragma unroll
             for (int r = 0; r < PR; ++r) {
@@ -608,14 +644,14 @@ size_t warp_smem_bytes(int NW, int S, int slot4, int PR, int Np)
     return bars + ring + (size_t)2 * 3 * PR * 32 * NW * 4;
 }
 
-template <int E, int PR, bool RAGGED>
+template <int E, int PR, bool RAGGED, bool SHFL>
 cudaError_t launch_warp(const WarpArgs &a, int grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(l96_hvp_warp_kernel<E, PR, RAGGED>,
+    cudaError_t e = cudaFuncSetAttribute(l96_hvp_warp_kernel<E, PR, RAGGED, SHFL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    l96_hvp_warp_kernel<E, PR, RAGGED><<<grid, 32 * a.nwarps, smem, s>>>(a);
+    l96_hvp_warp_kernel<E, PR, RAGGED, SHFL><<<grid, 32 * a.nwarps, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -678,7 +714,8 @@ size_t l96_coef_warp_floats4(const L96Dev &m)
 }
 
 cudaError_t l96_hvp_warp_launch(const L96Dev &m, const float4 *coefw, const float *W, float *Y, int64_t ld, int ncols,
-                                int add_identity, float *r, int *err, cudaStream_t s, int S_hint, int wait_polls)
+                                int add_identity, float *r, int *err, cudaStream_t s, int S_hint, int wait_polls,
+                                bool shuffle)
 {
     if (ncols <= 0) return cudaSuccess;
     if (!warp_kernel_fits(m.geom)) return cudaErrorInvalidConfiguration;
@@ -718,8 +755,14 @@ cudaError_t l96_hvp_warp_launch(const L96Dev &m, const float4 *coefw, const floa
     a.S = S;
     const int grid = (ncols + PR - 1) / PR;
     const bool ragged = m.geom.g != 0;
-    if (E == 8) return ragged ? launch_warp<8, 2, true>(a, grid, smem, s) : launch_warp<8, 2, false>(a, grid, smem, s);
-    return ragged ? launch_warp<16, 1, true>(a, grid, smem, s) : launch_warp<16, 1, false>(a, grid, smem, s);
+    if (shuffle) {
+        if (E == 8)
+            return ragged ? launch_warp<8, 2, true, true>(a, grid, smem, s) : launch_warp<8, 2, false, true>(a, grid, smem, s);
+        return ragged ? launch_warp<16, 1, true, true>(a, grid, smem, s) : launch_warp<16, 1, false, true>(a, grid, smem, s);
+    }
+    if (E == 8)
+        return ragged ? launch_warp<8, 2, true, false>(a, grid, smem, s) : launch_warp<8, 2, false, false>(a, grid, smem, s);
+    return ragged ? launch_warp<16, 1, true, false>(a, grid, smem, s) : launch_warp<16, 1, false, false>(a, grid, smem, s);
 }
 
 }  // namespace riot

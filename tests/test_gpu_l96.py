@@ -158,7 +158,7 @@ def test_hvp_fp64_ragged_sizes(gpu_lib, n, T, every, frac, dup):
                                                 (2047, 4, 1, 0.2, False),
                                                 (4096, 6, 2, 0.25, False), (5001, 5, 1, 0.05, True),
                                                 (8192, 3, 1, 0.1, False)])
-@pytest.mark.parametrize("kernel", ["cta_barrier", "warp_pairs"])
+@pytest.mark.parametrize("kernel", ["cta_barrier", "warp_pairs", "warp_shuffle"])
 def test_hvp_fp32_ragged_sizes(gpu_lib, n, T, every, frac, dup, kernel):
     # FP32 kernels with streamed stage coefficients: every chunk width (E = 4, 8,
     # 16), ragged last chunks, a last warp with fewer than 32 live lanes (n = 1000,
@@ -170,8 +170,8 @@ def test_hvp_fp32_ragged_sizes(gpu_lib, n, T, every, frac, dup, kernel):
     prob = _random_problem(n, T, 2.5, frac, every, seed=n + 1, sigma_vec=sv, dup=dup)
     traj = orc.trajectory(prob, prob.x_b)
     ctx = _ctx(R, prob, 2.5, sigma_vec=sv, kmax=16, precision=R.RIOT_PREC_MIXED)
-    if kernel == "warp_pairs":
-        R.riot_set_hvp_kernel(ctx.h, R.RIOT_HVP_WARP_PAIRS)
+    if kernel != "cta_barrier":
+        R.riot_set_hvp_kernel(ctx.h, R.RIOT_HVP_WARP_PAIRS if kernel == "warp_pairs" else R.RIOT_HVP_WARP_SHUFFLE)
     R.riot_outer_begin(ctx.h, _t(prob.x_b))
     W = np.random.default_rng(2).standard_normal((n, 13)).astype(np.float32).astype(np.float64)
     ref = orc.hvp(prob, traj, W)
@@ -179,6 +179,23 @@ def test_hvp_fp32_ragged_sizes(gpu_lib, n, T, every, frac, dup, kernel):
     assert _col_rel_err(Y, ref).max() < 2e-5
     Y1 = _hvp_gpu(R, ctx, W, torch.float32, add_identity=True)
     assert _col_rel_err(Y1, ref + W).max() < 2e-5
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [1000, 4096])
+def test_warp_halo_by_shuffles_is_bitwise_equal(gpu_lib, n):
+    """The warp-pair kernel with its halo passed by warp shuffles gives the products of the
+    shared-memory halo bit for bit (the same values reach the same arithmetic)."""
+    R = gpu_lib
+    prob = _random_problem(n, 12, 2.5, 0.25, 2, seed=n + 5)
+    ctx = _ctx(R, prob, 2.5, kmax=8, precision=R.RIOT_PREC_MIXED)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    W = np.random.default_rng(4).standard_normal((n, 8))
+    R.riot_set_hvp_kernel(ctx.h, R.RIOT_HVP_WARP_PAIRS)
+    Ya = _hvp_gpu(R, ctx, W, torch.float32)
+    R.riot_set_hvp_kernel(ctx.h, R.RIOT_HVP_WARP_SHUFFLE)
+    Yb = _hvp_gpu(R, ctx, W, torch.float32)
+    np.testing.assert_array_equal(Ya, Yb)
     ctx.close()
 
 
