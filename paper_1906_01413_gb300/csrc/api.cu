@@ -1045,7 +1045,7 @@ riot_status rsvd_eig(riot_ctx *ctx, int k)
         CU(jacobi_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, ctx->s));
     else
         CU(tridiag_eig(ctx->Km, k, ctx->lam, ctx->Z, ctx->jwork, ctx->info + 12, ctx->s,
-                       ctx->prec == RIOT_PREC_MIXED));
+                       ctx->prec == RIOT_PREC_MIXED, ctx->prec == RIOT_PREC_MIXED ? ctx->errflag : nullptr));
     if (ctx->scale_exp) CU(scal(k, ldexp(1.0, ctx->scale_exp), ctx->lam, ctx->s));
     return RIOT_OK;
 }

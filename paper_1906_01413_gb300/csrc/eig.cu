@@ -669,7 +669,7 @@ __global__ void eig_sort_kernel(const double *w, const double *Zt, int k, double
 }  // namespace
 
 cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *work, int *info, cudaStream_t s,
-                        bool fp32_vectors)
+                        bool fp32_vectors, int *tc_err)
 {
     const size_t kk = (size_t)k * k;
     double *A = work, *Qt = work + kk, *Zt = work + 2 * kk, *Zs = work + 3 * kk;
@@ -728,12 +728,35 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
     // within about 1e-7, enough for vectors that are used in FP32 (fp32_vectors).
     // The Grams are split over K in the LU scratch of the inverse iteration.
     const int shifted = fp32_vectors ? 1 : 2;
-    for (int pass = 0; pass <= shifted; ++pass) {
-        const double shift =
-            pass < shifted ? 11.0 * ((double)k * k + (double)k * (k + 1)) * ldexp(1.0, -53) : 0.0;
-        if ((err = gram_lower(k, k, Zt, 'd', k, Zs, k, s, u0, 4 * kk)) != cudaSuccess) return err;
-        if ((err = cholesky(Zs, k, k, shift, info + (pass < shifted ? 0 : 1), dinv, s)) != cudaSuccess) return err;
-        if ((err = trsm_right_lt(Zt, k, k, k, Zs, k, s, dinv)) != cudaSuccess) return err;
+    if (fp32_vectors && tc_err) {
+        // vectors consumed in FP32: orthonormalise their FP32 rounding as the mixed path's
+        // CholeskyQR does (exact tensor-core Gram, FP64 Cholesky, one-launch FP32 solve); the
+        // LU scratch holds the FP32 copy and factor, the Gram's split integers, and pq the
+        // equilibration scales
+        float *Zt32 = (float *)ml, *L32 = (float *)u2;
+        if ((err = convert_block(Zt, 'd', k, Zt32, 'f', k, k, k, s)) != cudaSuccess) return err;
+        for (int pass = 0; pass <= shifted; ++pass) {
+            const double shift = pass < shifted
+                                     ? fmax(11.0 * ((double)k * k + (double)k * (k + 1)) * ldexp(1.0, -53),
+                                            ldexp(1.0, -29) / k)
+                                     : 0.0;
+            if ((err = tc_gram_f32(k, k, Zt32, k, Zs, k, u0, tc_err, s)) != cudaSuccess) return err;
+            if ((err = equilibrate(Zs, k, k, Zt32, 'f', k, k, pq, s)) != cudaSuccess) return err;
+            if ((err = cholesky(Zs, k, k, shift, info + (pass < shifted ? 0 : 1), dinv, s)) != cudaSuccess) return err;
+            if ((err = convert_block(Zs, 'd', k, L32, 'f', k, k, k, s)) != cudaSuccess) return err;
+            if ((err = put_block_inverses(L32, k, k, dinv, s)) != cudaSuccess) return err;
+            if ((err = strsm_right_lt_inv(Zt32, k, k, k, L32, k, s)) != cudaSuccess) return err;
+        }
+        if ((err = convert_block(Zt32, 'f', k, Zt, 'd', k, k, k, s)) != cudaSuccess) return err;
+    } else {
+        for (int pass = 0; pass <= shifted; ++pass) {
+            const double shift =
+                pass < shifted ? 11.0 * ((double)k * k + (double)k * (k + 1)) * ldexp(1.0, -53) : 0.0;
+            if ((err = gram_lower(k, k, Zt, 'd', k, Zs, k, s, u0, 4 * kk)) != cudaSuccess) return err;
+            if ((err = cholesky(Zs, k, k, shift, info + (pass < shifted ? 0 : 1), dinv, s)) != cudaSuccess)
+                return err;
+            if ((err = trsm_right_lt(Zt, k, k, k, Zs, k, s, dinv)) != cudaSuccess) return err;
+        }
     }
     count_launch();
     eig_sort_kernel<<<k, 128, 0, s>>>(wrq, Zt, k, lam, Zs);

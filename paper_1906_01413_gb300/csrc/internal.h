@@ -299,9 +299,11 @@ size_t jacobi_work_doubles(int k);
 // lam: eigenvalues descending; Z (k x k): eigenvectors.  info[0..1] != 0 if
 // the final orthonormalisation of the eigenvectors failed.
 // fp32_vectors: the eigenvectors are consumed in FP32, so their orthonormalisation
-// stops at about 1e-7 (one shifted CholeskyQR pass less)
+// stops at about 1e-7 (one shifted CholeskyQR pass less); with tc_err (the flag of the
+// tensor-core kernels' bounded waits) it runs on their FP32 rounding with the exact
+// tensor-core Gram and the one-launch FP32 solve, as the mixed path's CholeskyQR does
 cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *work, int *info, cudaStream_t s,
-                        bool fp32_vectors = false);
+                        bool fp32_vectors = false, int *tc_err = nullptr);
 size_t eig_work_doubles(int k);
 // elementwise helpers
 cudaError_t symmetrize(double *A, int k, int64_t lda, cudaStream_t s);
