@@ -56,18 +56,27 @@ __global__ void eig_init_kernel(const double *K, int k, double *A, double *Qt)
     }
 }
 
-// Block-wide sum of one value per thread (blockDim.x = 256); every thread gets it.
+// Block-wide sum of one value per thread (blockDim.x = 256); every thread gets it.  An
+// FP64 instruction occupies its sub-partition's FP64 unit for about 64 cycles whatever the
+// active lanes, and warps w and w + 4 share a sub-partition: the upper four warps hand their
+// values to the lower four, which run one shuffle tree each (one per sub-partition), and one
+// thread adds the four partial sums.  red: kRedDoubles doubles of shared memory.
+constexpr int kRedDoubles = 136;
+
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
-    v = warp_sum(v);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     __syncthreads();   // red is free again
-    if (lane == 0) red[wib] = v;
+    if (wib >= 4) red[threadIdx.x - 128] = v;
     __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) t += red[w];
-    return t;
+    if (wib < 4) {
+        v = warp_sum(v + red[threadIdx.x]);
+        if (lane == 0) red[128 + wib] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) red[132] = (red[128] + red[129]) + (red[130] + red[131]);
+    __syncthreads();
+    return red[132];
 }
 
 // Householder reflector of x = col[r0..k-1], computed by the whole CTA (every
@@ -111,7 +120,7 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
     cg::grid_group grid = cg::this_grid();
     extern __shared__ double sm[];
     double *vcur = sm, *vnext = sm + k, *w = sm + 2 * k, *colj = sm + 3 * k, *red = sm + 4 * k;
-    double *own = sm + 4 * k + 8 + (size_t)(threadIdx.x >> 5) * k;   // RES: this warp's column
+    double *own = sm + 4 * k + kRedDoubles + (size_t)(threadIdx.x >> 5) * k;   // RES: this warp's column
     __shared__ double bcur_s, bnext_s, enext_s;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -694,7 +703,7 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
         const int grid = num_sms();   // one CTA per SM keeps the grid barrier short
         // columns resident in shared memory when every column has a warp of its own
         const bool res = 2 * k <= grid * 8;
-        const size_t smem = sizeof(double) * (4 * (size_t)k + 8 + (res ? 8 * (size_t)k : 0));
+        const size_t smem = sizeof(double) * (4 * (size_t)k + kRedDoubles + (res ? 8 * (size_t)k : 0));
         const void *fn = res ? (const void *)tridiag_kernel<true> : (const void *)tridiag_kernel<false>;
         if ((err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return err;
