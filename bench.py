@@ -88,7 +88,8 @@ def parse():
     ap.add_argument("--clock-log", default=None,
                     help="CSV of the nvidia-smi clock samples taken during the timed steps (%%d: rank); "
                          "default: a file in the temporary directory")
-    ap.add_argument("--hvp-kernel", choices=["cta_barrier", "warp_pairs", "warp_shuffle"], default="cta_barrier",
+    ap.add_argument("--hvp-kernel", choices=["cta_barrier", "warp_pairs", "warp_shuffle", "cta_two_per_sm"],
+                    default="cta_barrier",
                     help="FP32 Hessian kernel of --only hvp")
     ap.add_argument("--only", choices=["bc", "batch", "learned", "varcg", "varbl", "psas", "hvp"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling)")
@@ -338,8 +339,8 @@ def bench_hvp(R, torch, dev, flush, kernel, warmup, steps):
     inner loop's dominant launch), timed alone with CUDA events after an L2 flush."""
     cfg = configs.l96_large()
     ctx, xb, p = build_problem(R, torch, cfg, dev, R.RIOT_PREC_MIXED, cfg.k)
-    R.riot_set_hvp_kernel(ctx.h, {"warp_pairs": R.RIOT_HVP_WARP_PAIRS, "warp_shuffle": R.RIOT_HVP_WARP_SHUFFLE}.get(
-        kernel, R.RIOT_HVP_CTA_BARRIER))
+    R.riot_set_hvp_kernel(ctx.h, {"warp_pairs": R.RIOT_HVP_WARP_PAIRS, "warp_shuffle": R.RIOT_HVP_WARP_SHUFFLE,
+                                  "cta_two_per_sm": R.RIOT_HVP_CTA_TWO_PER_SM}.get(kernel, R.RIOT_HVP_CTA_BARRIER))
     R.riot_outer_begin(ctx.h, xb)
     W = torch.empty(cfg.k, cfg.n, dtype=torch.float32, device=dev)
     R.riot_draw_normal(cfg.seed, configs.STREAM_SKETCH0, cfg.n, cfg.k, W)

@@ -355,14 +355,19 @@ riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t r
  *    threads per column; others keep the default);
  *  RIOT_HVP_WARP_SHUFFLE: RIOT_HVP_WARP_PAIRS with the halo passed by warp
  *    shuffles between the lanes of a warp, only the two edge lanes of each
- *    warp going through shared memory.
+ *    warp going through shared memory;
+ *  RIOT_HVP_CTA_TWO_PER_SM: the default kernel with one probe per thread
+ *    (64 registers) and two CTAs per SM (windows with 8 variables per thread;
+ *    others keep the default).
  * The two warp kernels give the same products bit for bit.  Measured on the
  * 4096-variable, 200-step window (512 products per launch): 2.7 ms for the
- * default, 3.0 ms with warp pairs, 3.4 ms with shuffles (the per-warp ring
+ * default, 3.0 ms with warp pairs, 3.4 ms with shuffles, 3.4 ms with two CTAs
+ * per SM (each CTA streams the whole coefficient stream for half the probes,
+ * through a ring of two slots; the per-warp ring
  * bookkeeping costs more instructions than the CTA barrier costs waiting,
  * and the shuffles issue as many instructions as the shared-memory halo they
  * replace while lengthening the path to the barrier). */
-enum { RIOT_HVP_CTA_BARRIER = 0, RIOT_HVP_WARP_PAIRS = 1, RIOT_HVP_WARP_SHUFFLE = 2 };
+enum { RIOT_HVP_CTA_BARRIER = 0, RIOT_HVP_WARP_PAIRS = 1, RIOT_HVP_WARP_SHUFFLE = 2, RIOT_HVP_CTA_TWO_PER_SM = 3 };
 riot_status riot_set_hvp_kernel(riot_ctx *ctx, int32_t kernel);
 
 /* Bound of every wait of the mixed-precision Hessian kernels (on a stage copy,

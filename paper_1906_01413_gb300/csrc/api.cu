@@ -263,14 +263,14 @@ riot_status hvp(riot_ctx *ctx, const void *W, void *Y, int64_t ld, int ncols, in
         if (ctx->prec == RIOT_PREC_FP64)
             CU(l96_hvp_launch_f64(ctx->m, ctx->coef64, (const double *)w, (double *)yv, ld, nc, add_identity,
                                   (double *)ctx->rscr, 0, ctx->s));
-        else if (ctx->coefw && ctx->hvp_kernel != RIOT_HVP_CTA_BARRIER)
+        else if (ctx->coefw && (ctx->hvp_kernel == RIOT_HVP_WARP_PAIRS || ctx->hvp_kernel == RIOT_HVP_WARP_SHUFFLE))
             CU(l96_hvp_warp_launch(ctx->m, ctx->coefw, (const float *)w, (float *)yv, ld, nc, add_identity,
                                    (float *)ctx->rscr, ctx->errflag, ctx->s, ctx->hvp_S, ctx->wait_polls,
                                    ctx->hvp_kernel == RIOT_HVP_WARP_SHUFFLE));
         else
             CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, add_identity,
                                   (float *)ctx->rscr, 0, ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S,
-                                  ctx->wait_polls));
+                                  ctx->wait_polls, ctx->hvp_kernel == RIOT_HVP_CTA_TWO_PER_SM));
     }
     return RIOT_OK;
 }
@@ -1475,13 +1475,14 @@ riot_status riot_hessian_apply_noalloc(riot_ctx *ctx, const void *W_dev, void *Y
                                   (double *)scr, 0, ctx->s));
         else {
             const int ai = ctx->scale_exp ? 0 : add_identity;
-            if (ctx->coefw && ctx->hvp_kernel != RIOT_HVP_CTA_BARRIER)
+            if (ctx->coefw && (ctx->hvp_kernel == RIOT_HVP_WARP_PAIRS || ctx->hvp_kernel == RIOT_HVP_WARP_SHUFFLE))
                 CU(l96_hvp_warp_launch(ctx->m, ctx->coefw, (const float *)w, (float *)yv, ld, nc, ai, (float *)scr,
                                        ctx->errflag, ctx->s, ctx->hvp_S, ctx->wait_polls,
                                        ctx->hvp_kernel == RIOT_HVP_WARP_SHUFFLE));
             else
                 CU(l96_hvp_tma_launch(ctx->m, ctx->coef32, (const float *)w, (float *)yv, ld, nc, ai, (float *)scr, 0,
-                                      ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S, ctx->wait_polls));
+                                      ctx->errflag, ctx->s, ctx->hvp_P, ctx->hvp_S, ctx->wait_polls,
+                                      ctx->hvp_kernel == RIOT_HVP_CTA_TWO_PER_SM));
             if (ctx->scale_exp)
                 CU(scale_add_cols(ctx->n, nc, ld, ldexp(1.0, ctx->scale_exp), yv, add_identity ? w : nullptr, 0,
                                   ctx->s));
@@ -1688,7 +1689,8 @@ riot_status riot_set_hvp_config(riot_ctx *ctx, int32_t probes_per_cta, int32_t r
 riot_status riot_set_hvp_kernel(riot_ctx *ctx, int32_t kernel)
 {
     if (!ctx) return RIOT_EINVAL;
-    if (kernel != RIOT_HVP_CTA_BARRIER && kernel != RIOT_HVP_WARP_PAIRS && kernel != RIOT_HVP_WARP_SHUFFLE)
+    if (kernel != RIOT_HVP_CTA_BARRIER && kernel != RIOT_HVP_WARP_PAIRS && kernel != RIOT_HVP_WARP_SHUFFLE &&
+        kernel != RIOT_HVP_CTA_TWO_PER_SM)
         return fail(ctx, RIOT_EINVAL, "unknown Hessian kernel %d", kernel);
     ctx->hvp_kernel = kernel;
     return RIOT_OK;

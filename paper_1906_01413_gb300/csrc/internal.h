@@ -100,7 +100,7 @@ cudaError_t l96_hvp_launch_f64(const L96Dev &m, const double2 *coef, const doubl
 // (about 2^20 polls); >= 0: that many polls (tests of the timeout report).
 cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float *W, float *Y, int64_t ld,
                                int ncols, int add_identity, float *r, int mode, int *err, cudaStream_t s,
-                               int P_hint = 0, int S_hint = 0, int wait_polls = -1);
+                               int P_hint = 0, int S_hint = 0, int wait_polls = -1, bool two_per_sm = false);
 
 // Warp-synchronous FP32 Hessian product (Y = A W (+W)): halos by warp shuffles and
 // per-warp mailboxes, coefficients by per-warp 1-D TMA rings.  Needs E of 8 or 16 and

@@ -535,8 +535,8 @@ __device__ __forceinline__ void hvp_tma_body(const TmaArgs &a, int blk, unsigned
     }
 }
 
-template <int E, int PR, int MAXT, bool RAGGED>
-__global__ void __launch_bounds__(MAXT, 1) l96_hvp_tma_kernel(const TmaArgs a)
+template <int E, int PR, int MAXT, bool RAGGED, int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB) l96_hvp_tma_kernel(const TmaArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int abort_flag;
@@ -610,11 +610,11 @@ static bool tma_plan(const ChunkGeom &g, int ncols, int PR, int maxthr, size_t s
     return false;
 }
 
-template <int E, int PR, int MAXT>
+template <int E, int PR, int MAXT, int MINB = 1>
 static cudaError_t launch_tma(const TmaArgs &a, int grid, int nthr, size_t sm, cudaStream_t s)
 {
     const bool ragged = a.geom.g != 0;
-    auto kern = ragged ? l96_hvp_tma_kernel<E, PR, MAXT, true> : l96_hvp_tma_kernel<E, PR, MAXT, false>;
+    auto kern = ragged ? l96_hvp_tma_kernel<E, PR, MAXT, true, MINB> : l96_hvp_tma_kernel<E, PR, MAXT, false, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     count_launch();
@@ -624,18 +624,22 @@ static cudaError_t launch_tma(const TmaArgs &a, int grid, int nthr, size_t sm, c
 
 cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float *W, float *Y, int64_t ld, int ncols,
                                int add_identity, float *r, int mode, int *err, cudaStream_t s, int P_hint, int S_hint,
-                               int wait_polls)
+                               int wait_polls, bool two_per_sm)
 {
     if (ncols <= 0) return cudaSuccess;
-    int dev = 0, smem_optin = 0;
+    int dev = 0, smem_optin = 0, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     const int E = m.geom.E;
-    // two probes per thread (registers) for E <= 8: 512-thread CTAs
-    const int PR = (E <= 8) ? 2 : 1;
+    // two probes per thread (registers) for E <= 8: 512-thread CTAs, one per SM; two_per_sm
+    // (E = 8): one probe per thread in 64 registers, two CTAs per SM sharing its shared memory
+    const bool pair = two_per_sm && E == 8;
+    const int PR = (E <= 8 && !pair) ? 2 : 1;
     const int maxthr = 512;
+    const size_t smem_max = pair ? (size_t)smem_sm / 2 - 1024 : (size_t)smem_optin - 1024;
     int P = 1, S = 2;
-    if (!tma_plan(m.geom, ncols, PR, maxthr, (size_t)smem_optin - 1024, P_hint, S_hint, &P, &S))
+    if (!tma_plan(m.geom, ncols, PR, maxthr, smem_max, P_hint, S_hint, &P, &S))
         return cudaErrorInvalidConfiguration;
     TmaArgs a;
     a.geom = m.geom;
@@ -667,7 +671,7 @@ cudaError_t l96_hvp_tma_launch(const L96Dev &m, const float2 *coef, const float 
     const int grid = (ncols + per_cta - 1) / per_cta;
     switch (E) {
     case 4: return launch_tma<4, 2, 512>(a, grid, nthr, sm, s);
-    case 8: return launch_tma<8, 2, 512>(a, grid, nthr, sm, s);
+    case 8: return pair ? launch_tma<8, 1, 512, 2>(a, grid, nthr, sm, s) : launch_tma<8, 2, 512>(a, grid, nthr, sm, s);
     case 16: return launch_tma<16, 1, 512>(a, grid, nthr, sm, s);
     default: return cudaErrorInvalidValue;
     }

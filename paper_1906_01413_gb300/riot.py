@@ -280,6 +280,7 @@ def riot_setup_advdiff(nx, ny, nz, nblocks, T, dt, dx, dy, dz, u, v, amp, kz, em
 RIOT_HVP_CTA_BARRIER = 0
 RIOT_HVP_WARP_PAIRS = 1
 RIOT_HVP_WARP_SHUFFLE = 2
+RIOT_HVP_CTA_TWO_PER_SM = 3
 
 
 def riot_set_hvp_kernel(ctx, kernel):

@@ -158,7 +158,7 @@ def test_hvp_fp64_ragged_sizes(gpu_lib, n, T, every, frac, dup):
                                                 (2047, 4, 1, 0.2, False),
                                                 (4096, 6, 2, 0.25, False), (5001, 5, 1, 0.05, True),
                                                 (8192, 3, 1, 0.1, False)])
-@pytest.mark.parametrize("kernel", ["cta_barrier", "warp_pairs", "warp_shuffle"])
+@pytest.mark.parametrize("kernel", ["cta_barrier", "warp_pairs", "warp_shuffle", "cta_two_per_sm"])
 def test_hvp_fp32_ragged_sizes(gpu_lib, n, T, every, frac, dup, kernel):
     # FP32 kernels with streamed stage coefficients: every chunk width (E = 4, 8,
     # 16), ragged last chunks, a last warp with fewer than 32 live lanes (n = 1000,
@@ -171,7 +171,8 @@ def test_hvp_fp32_ragged_sizes(gpu_lib, n, T, every, frac, dup, kernel):
     traj = orc.trajectory(prob, prob.x_b)
     ctx = _ctx(R, prob, 2.5, sigma_vec=sv, kmax=16, precision=R.RIOT_PREC_MIXED)
     if kernel != "cta_barrier":
-        R.riot_set_hvp_kernel(ctx.h, R.RIOT_HVP_WARP_PAIRS if kernel == "warp_pairs" else R.RIOT_HVP_WARP_SHUFFLE)
+        R.riot_set_hvp_kernel(ctx.h, {"warp_pairs": R.RIOT_HVP_WARP_PAIRS, "warp_shuffle": R.RIOT_HVP_WARP_SHUFFLE,
+                                      "cta_two_per_sm": R.RIOT_HVP_CTA_TWO_PER_SM}[kernel])
     R.riot_outer_begin(ctx.h, _t(prob.x_b))
     W = np.random.default_rng(2).standard_normal((n, 13)).astype(np.float32).astype(np.float64)
     ref = orc.hvp(prob, traj, W)
