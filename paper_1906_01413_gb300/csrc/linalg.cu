@@ -969,9 +969,116 @@ cudaError_t trtri_diag(const double *L, int k, int64_t ldl, double *dinv, cudaSt
     return cudaGetLastError();
 }
 
+// X <- X L^-T (LT) or X L^-1 in one launch, FP64: rows are independent, so a CTA of four
+// warps owns four rows (one per warp: a sub-partition each, since FP64 throughput per
+// sub-partition bounds this kernel) for all k columns in shared memory and sweeps the block
+// columns (forward for L^-T, backward for L^-1): block J takes X_J minus the finished blocks
+// times the matching blocks of L, then the block inverse from cholesky.  The 32 x 32 blocks of
+// L go through a shared buffer (coalesced copy, then read along either index), the next one
+// fetched into registers while the current one is used.
+template <bool LT>
+__global__ void __launch_bounds__(128) dtrsm_rows_kernel(double *X, int m, int k, int64_t ldx, const double *L,
+                                                         int64_t ldl, const double *dinv)
+{
+    extern __shared__ double dtrsm_sm[];
+    double *ys = dtrsm_sm;                                                                   // [4][k]
+    double (*Ls)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dtrsm_sm + 4 * (size_t)k);   // [2 NB][NB + 1]
+    const int t = threadIdx.x, r = t >> 5, c = t & 31;
+    const int r0 = blockIdx.x * 4;
+    const int nb = (k + NB - 1) / NB;
+    for (int e = t; e < 4 * k; e += blockDim.x) {
+        const int cc = e >> 2, rr = e & 3;
+        ys[rr * k + cc] = (r0 + rr < m) ? X[(r0 + rr) + (int64_t)cc * ldx] : 0.0;
+    }
+    // targets T in sweep order; target T's source blocks q = 0 .. nsrc(T) - 1 are L_{T,q}
+    // (L^-T: q < T) or L_{nb-1-q, T} (L^-1); the next source block to fetch is (fT, fq)
+    auto nsrc = [&](int T) { return LT ? T : nb - 1 - T; };
+    auto src_block = [&](int T, int q, int &bi, int &bj) {
+        if (LT) { bi = T; bj = q; }
+        else { bi = nb - 1 - q; bj = T; }
+    };
+    int fT = LT ? 1 : nb - 2, fq = 0;
+    auto has_next = [&]() { return LT ? fT < nb : fT >= 0; };
+    auto advance = [&]() {
+        if (++fq == nsrc(fT)) {
+            fT += LT ? 1 : -1;
+            fq = 0;
+        }
+    };
+    double pre[8];
+    auto fetch = [&]() {
+        int bi, bj;
+        src_block(fT, fq, bi, bj);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = t + 128 * u, i = e & 31, j = e >> 5;
+            const int gi = NB * bi + i, gj = NB * bj + j;
+            pre[u] = (gi < k && gj < k) ? L[gi + (int64_t)gj * ldl] : 0.0;
+        }
+        advance();
+    };
+    if (has_next()) fetch();
+    __syncthreads();
+    int buf = 0;
+    for (int jj = 0; jj < nb; ++jj) {
+        const int T = LT ? jj : nb - 1 - jj;
+        const int colT = NB * T + c;
+        double acc0 = (colT < k) ? ys[r * k + colT] : 0.0, acc1 = 0.0;
+        for (int q = 0; q < nsrc(T); ++q) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = t + 128 * u;
+                Ls[buf * NB + (e & 31)][e >> 5] = pre[u];
+            }
+            __syncthreads();
+            if (has_next()) fetch();
+            int bi, bj;
+            src_block(T, q, bi, bj);
+            const double(*B)[NB + 1] = Ls + buf * NB;
+            const double *yb = ys + r * k + NB * (LT ? bj : bi);
+#pragma unroll 8
+            for (int kk = 0; kk < NB; kk += 2) {
+                const double b0 = LT ? B[c][kk] : B[kk][c], b1 = LT ? B[c][kk + 1] : B[kk + 1][c];
+                acc0 = fma(-yb[kk], b0, acc0);
+                acc1 = fma(-yb[kk + 1], b1, acc1);
+            }
+            buf ^= 1;
+        }
+        // diagonal: the right-hand side through shared memory, then times the block inverse
+        const double *D = dinv + (int64_t)T * NB * NB;   // column-major, lower
+        const int jb = (k - NB * T < NB) ? k - NB * T : NB;
+        __syncthreads();
+        if (colT < k) ys[r * k + colT] = acc0 + acc1;
+        __syncthreads();
+        double o = 0.0;
+        for (int kk = 0; kk < jb; ++kk) o = fma(ys[r * k + NB * T + kk], LT ? D[c + NB * kk] : D[kk + NB * c], o);
+        __syncthreads();
+        if (colT < k) ys[r * k + colT] = o;
+    }
+    __syncthreads();
+    for (int e = t; e < 4 * k; e += blockDim.x) {
+        const int cc = e >> 2, rr = e & 3;
+        if (r0 + rr < m) X[(r0 + rr) + (int64_t)cc * ldx] = ys[rr * k + cc];
+    }
+}
+
+static cudaError_t dtrsm_rows(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, const double *dinv,
+                              bool lt, cudaStream_t s)
+{
+    const size_t smem = sizeof(double) * (4 * (size_t)k + 2 * NB * (NB + 1));
+    auto kern = lt ? dtrsm_rows_kernel<true> : dtrsm_rows_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    kern<<<(m + 3) / 4, 128, smem, s>>>(X, m, k, ldx, L, ldl, dinv);
+    return cudaGetLastError();
+}
+
 cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s,
                           const double *dinv)
 {
+    if (m <= 0 || k <= 0) return cudaSuccess;
+    if (sizeof(double) * (4 * (size_t)k + 2 * NB * (NB + 1)) <= 227 * 1024) return dtrsm_rows(X, m, k, ldx, L, ldl, dinv, true, s);
     for (int J = 0; J < k; J += NB) {
         const int jb = (k - J < NB) ? k - J : NB;
         count_launch();
@@ -990,6 +1097,8 @@ cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L,
 cudaError_t trsm_right_l(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s,
                          const double *dinv)
 {
+    if (m <= 0 || k <= 0) return cudaSuccess;
+    if (sizeof(double) * (4 * (size_t)k + 2 * NB * (NB + 1)) <= 227 * 1024) return dtrsm_rows(X, m, k, ldx, L, ldl, dinv, false, s);
     const int nblk = (k + NB - 1) / NB;
     for (int b = nblk - 1; b >= 0; --b) {
         const int J = b * NB;
