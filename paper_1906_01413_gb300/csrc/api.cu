@@ -1105,7 +1105,7 @@ riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
         // K's products stay in FP64 on both paths: the solve with M M^T amplifies their
         // error by its condition number (sliced tensor-core products, exact to 2^-36 of each
         // column's maximum, moved lambda_1 of the large window by 5 %)
-        CU(gemm('N', 'T', k, k, k, 1.0, ctx->Mm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->G, 'd', k, s));
+        CU(syrk_lower(k, k, ctx->Mm, k, ctx->G, k, s));
         CU(gemm('N', 'T', k, k, k, 1.0, ctx->Nm, 'd', k, ctx->Mm, 'd', k, 0.0, ctx->Km, 'd', k, s));
         // M M^T is singular to working precision when the window's spectrum spans more than the
         // precision (A Q0 then loses Q0's trailing directions): a retry with a shift of the order
@@ -2620,7 +2620,7 @@ riot_status riot_psas(riot_ctx *ctx, int32_t m, int32_t q, int64_t sketch_stream
         CU(gemm('T', 'N', m, m, p, 1.0, ctx->psQ, 'd', p, ctx->psW, 'd', p, 0.0, ctx->Mm, 'd', m, s));
         CU(gemm('T', 'N', m, m, p, 1.0, ctx->psQ, 'd', p, ctx->psY, 'd', p, 0.0, ctx->Nm, 'd', m, s));
         for (int attempt = 0; attempt < 2; ++attempt) {
-            CU(gemm('N', 'T', m, m, m, 1.0, ctx->Mm, 'd', m, ctx->Mm, 'd', m, 0.0, ctx->G, 'd', m, s));
+            CU(syrk_lower(m, m, ctx->Mm, m, ctx->G, m, s));
             CU(gemm('N', 'T', m, m, m, 1.0, ctx->Nm, 'd', m, ctx->Mm, 'd', m, 0.0, ctx->Km, 'd', m, s));
             CU(cudaMemsetAsync(ctx->info + 10, 0, sizeof(int), s));
             CU(cholesky(ctx->G, m, m, attempt ? 8.0 * m * ldexp(1.0, -53) : 0.0, ctx->info + 10, ctx->gws, s));

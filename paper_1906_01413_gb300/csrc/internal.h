@@ -280,6 +280,8 @@ cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *inf
 size_t dinv_doubles(int k);
 // inverses of the diagonal blocks of a lower-triangular L (when not from cholesky)
 cudaError_t trtri_diag(const double *L, int k, int64_t ldl, double *dinv, cudaStream_t s);
+// C (lower triangle) = A A^T, A n x K, FP64
+cudaError_t syrk_lower(int n, int K, const double *A, int64_t lda, double *C, int64_t ldc, cudaStream_t s);
 // X <- X L^-T (X: m x k, L: k x k lower): right-side solve with diagonal-block inverses.
 cudaError_t trsm_right_lt(double *X, int m, int k, int64_t ldx, const double *L, int64_t ldl, cudaStream_t s,
                           const double *dinv);

@@ -542,6 +542,13 @@ cudaError_t strsm_right_lt_inv(float *X, int m, int k, int64_t ldx, const float 
     return cudaGetLastError();
 }
 
+// C (n x n, lower triangle only) = A A^T for A n x K (FP64): the normal-equations matrix of
+// the solve for K, which the Cholesky then reads from its lower triangle alone.
+cudaError_t syrk_lower(int n, int K, const double *A, int64_t lda, double *C, int64_t ldc, cudaStream_t s)
+{
+    return gemm16('N', 'T', n, n, K, 1.0, A, lda, A, lda, 0.0, C, ldc, s, 1);
+}
+
 // ---------------------------------------------------------------------------
 // Block conversion / copy
 // ---------------------------------------------------------------------------
