@@ -708,63 +708,60 @@ __global__ void __launch_bounds__(256) potrf_kernel(double *G, int64_t ldg, int 
 
 // One step of the blocked Cholesky after the panel of block column J (rows J + jb.. solved):
 // the trailing update A22 -= A21 A21^T in 16 x 16 lower tiles, fused with the next diagonal
-// block.  CTA (0, 0) updates the jb2 x jb2 block at the top of A22 itself and factors it at
-// once, while the other CTAs update the rest (the tiles of that block are skipped), so the
-// next pivot chain starts without waiting for the whole trailing update.
-__global__ void __launch_bounds__(256) chol_trail_kernel(double *G, int64_t ldg, int k, int J, int jb, int *info)
+// block.  The grid runs in clusters of 2 x 2 CTAs; cluster (0, 0) (whose other three CTAs
+// would be the block's own tiles or upper tiles) takes the next diagonal block: its four CTAs
+// each form a quarter of the block's update from the panel rows and write it into CTA 0's
+// shared memory (distributed shared memory), and after the cluster barrier CTA 0 applies it
+// and factors the block at once, while the other clusters update the rest of A22.  So the
+// next pivot chain starts after a quarter of the block's FP64 work instead of all of it.
+__global__ void __cluster_dims__(2, 2, 1) __launch_bounds__(256)
+    chol_trail_kernel(double *G, int64_t ldg, int k, int J, int jb, int *info)
 {
     const int r0 = J + jb, m2 = k - r0;
     const int bx = blockIdx.x, by = blockIdx.y, t = threadIdx.x;
     __shared__ double As[NB][NB + 1];
     __shared__ double Ps[NB][NB + 1];
+    __shared__ double Up[NB][NB + 1];
     __shared__ double rsq[NB], rv[NB];
-    if (bx == 0 && by == 0) {
+    if (bx < 2 && by < 2) {
+        cg::cluster_group cl = cg::this_cluster();
+        const unsigned rank = cl.block_rank();
         const int jb2 = m2 < NB ? m2 : NB;
         for (int e = t; e < NB * NB; e += blockDim.x) {
             const int i = e & (NB - 1), c = e / NB;
-            As[i][c] = (i < jb2 && c < jb2) ? (c <= i ? G[(r0 + i) + (int64_t)(r0 + c) * ldg] : 0.0) : (i == c ? 1.0 : 0.0);
             Ps[i][c] = (i < jb2 && c < jb) ? G[(r0 + i) + (int64_t)(J + c) * ldg] : 0.0;
+            if (rank == 0)
+                As[i][c] = (i < jb2 && c < jb2) ? (c <= i ? G[(r0 + i) + (int64_t)(r0 + c) * ldg] : 0.0)
+                                                : (i == c ? 1.0 : 0.0);
         }
         __syncthreads();
-        // the block's own update, lower triangle (entries row-major: e -> (i, c), c <= i)
-        double upd[3];
-        int ui[3], uc[3];
+        // lower-triangle entries e = 4 t' + rank (row-major: e -> (i, c), c <= i), 132 per CTA
+        double *up0 = cl.map_shared_rank(&Up[0][0], 0);
+        const int e = 4 * t + (int)rank;
+        if (t < 132 && e < NB * (NB + 1) / 2) {
+            int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+            while ((i + 1) * (i + 2) / 2 <= e) ++i;
+            while (i > 0 && i * (i + 1) / 2 > e) --i;
+            const int c = e - i * (i + 1) / 2;
+            double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int e = t + 256 * q;
-            ui[q] = -1;
-            uc[q] = 0;
-            upd[q] = 0.0;
-            if (e < NB * (NB + 1) / 2) {
-                int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-                while ((i + 1) * (i + 2) / 2 <= e) ++i;
-                while (i > 0 && i * (i + 1) / 2 > e) --i;
-                ui[q] = i;
-                uc[q] = e - i * (i + 1) / 2;
+            for (int kk = 0; kk < NB; kk += 2) {
+                a0 = fma(Ps[i][kk], Ps[c][kk], a0);
+                a1 = fma(Ps[i][kk + 1], Ps[c][kk + 1], a1);
             }
+            up0[i * (NB + 1) + c] = a0 + a1;
         }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            if (ui[q] >= 0) {
-                const int i = ui[q], c = uc[q];
-                double a0 = 0.0, a1 = 0.0;
-#pragma unroll
-                for (int kk = 0; kk < NB; kk += 2) {
-                    a0 = fma(Ps[i][kk], Ps[c][kk], a0);
-                    a1 = fma(Ps[i][kk + 1], Ps[c][kk + 1], a1);
-                }
-                upd[q] = a0 + a1;
-            }
+        cl.sync();   // every quarter of the update is in CTA 0's shared memory
+        if (rank != 0) return;
+        for (int e2 = t; e2 < NB * NB; e2 += blockDim.x) {
+            const int i = e2 & (NB - 1), c = e2 / NB;
+            if (i < jb2 && c <= i) As[i][c] -= Up[i][c];
         }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (ui[q] >= 0 && ui[q] < jb2) As[ui[q]][uc[q]] -= upd[q];
         __syncthreads();
         potrf_smem(As, rsq, rv, G, ldg, r0, jb2, info);
         return;
     }
-    if (by > bx || (bx < 2 && by < 2)) return;
+    if (by > bx) return;
     // tile (bx, by) of A22: rows r0 + 16 bx.., columns r0 + 16 by.. (As, Ps as [kk][16] stores)
     const int tx = t & 15, ty = t >> 4;
     const int mi = r0 + 16 * bx, nj = r0 + 16 * by;
@@ -960,7 +957,7 @@ cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *inf
         if (m2 <= 0) break;
         double *A21 = G + (J + jb) + (int64_t)J * ldg;
         { count_launch(); panel_trsm_kernel<<<(m2 + 3) / 4, 128, 0, s>>>(A21, m2, ldg, G + J + (int64_t)J * ldg, ldg, jb); }
-        const int nt = (m2 + 15) / 16;
+        const int nt = ((m2 + 15) / 16 + 1) & ~1;   // clusters of 2 x 2 CTAs
         { count_launch(); chol_trail_kernel<<<dim3(nt, nt), 256, 0, s>>>(G, ldg, k, J, jb, info); }
     }
     // the block inverses that the triangular solves multiply by
