@@ -178,6 +178,38 @@ def test_rsvd_mixed_leading_eigenvalues(gpu_lib):
     ctx.close()
 
 
+def test_rsvd_mixed_increment_and_cost_reduction(gpu_lib):
+    """The mixed tracer inner loop (16 x 12 x 6 box, k = 32, q = 1) against the FP64 oracle on
+    the FP32-rounded sketch.  Every retained eigenvalue is above the FP32 floor here, so both
+    sides use all 32 pairs.  FP32 products carry an error of at most eps = 16 sqrt(8T) 2^-24
+    of A's scale (the product bound of these tests, 1.3e-5 at T = 24), so the eigenpairs, the
+    adaptive weights and the increment move by at most about eps lambda_1 relative; the cost
+    reduction, second order in the increment's error, is held to 1e-4."""
+    R = gpu_lib
+    cfg = _cfg("small")
+    prob = A.build(cfg)
+    k, q = 32, 1
+    ctx = _ctx(R, cfg, prob, R.RIOT_PREC_MIXED, kmax=k)
+    R.riot_outer_begin(ctx.h, _t(prob.x_b))
+    Om = cfg.sketch(0, k=k)
+    lam = R.riot_rsvd(ctx.h, k, q, Omega=_t(Om, torch.float32))
+    dv = torch.empty(prob.n, dtype=torch.float64, device=DEV)
+    mode = R.riot_increment(ctx.h, dv)
+    assert R.riot_increment_pairs(ctx.h) == k
+    red = R.riot_quadratic_cost(ctx.h) - R.riot_quadratic_cost(ctx.h, dv)
+    res = A.outer_step(prob, prob.x_b, np.zeros(prob.n), Om.astype(np.float32).astype(np.float64).T, q=q)
+    eps = 16 * np.sqrt(8 * cfg.T) * 2.0 ** -24
+    assert mode == res["mode"]
+    dvo = res["dv"]
+    err = np.linalg.norm(dv.cpu().numpy() - dvo) / np.linalg.norm(dvo)
+    assert err <= eps * res["lam"][0], (err, eps * res["lam"][0])
+    z = np.zeros(prob.n)
+    d = A.innovation(prob, res["traj"])
+    red_o = A.quadratic_cost(prob, res["traj"], d, z, z) - A.quadratic_cost(prob, res["traj"], d, z, dvo)
+    assert red_o > 0 and abs(red - red_o) <= 1e-4 * red_o, (red, red_o)
+    ctx.close()
+
+
 def test_full_grid_properties(gpu_lib):
     """The 192 x 192 x 30 grid of the benchmark workload (shortened window):
     FP64 observations against the oracle, and symmetry of the FP32 Hessian
