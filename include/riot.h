@@ -407,9 +407,15 @@ uint64_t riot_kernel_launches(void);
  *   out[1] FP32 FMA throughput, TFLOP/s (the same kernel in FP32);
  *   out[2] FP64 FMA latency, SM cycles per dependent FMA (one thread);
  *   out[3] FP64 rsqrt latency, SM cycles per dependent rsqrt + add;
- *   out[4] FP64 division latency, SM cycles per dependent division + add.
- * Writes min(nout, 5) values.  Runs on its own stream, allocates about
- * 2 MB for the run, synchronises; takes about 30 ms.  RIOT_EINVAL for a null
+ *   out[4] FP64 division latency, SM cycles per dependent division + add;
+ *   out[5] latency of the refined reciprocal the FP64 k x k chains use (the
+ *          hardware approximation plus one third-order Newton step), SM
+ *          cycles per dependent reciprocal + add;
+ *   out[6] its largest error, in ulps of the correctly rounded reciprocal,
+ *          over 2^24 inputs of both signs log-uniform in [2^-1100, 2^1100]
+ *          and the range limits.
+ * Writes min(nout, 7) values.  Runs on its own stream, allocates about
+ * 2 MB for the run, synchronises; takes about 40 ms.  RIOT_EINVAL for a null
  * out or nout < 1, RIOT_ECUDA for a CUDA error. */
 riot_status riot_measure_peaks(int32_t device, double *out, int32_t nout);
 

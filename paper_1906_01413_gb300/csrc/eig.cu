@@ -22,6 +22,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "fp64_rcp.cuh"
 #include "internal.h"
 
 namespace cg = cooperative_groups;
@@ -60,10 +61,11 @@ __global__ void eig_init_kernel(const double *K, int k, double *A, double *Qt)
 // FP64 instruction occupies its sub-partition's FP64 unit for about 64 cycles whatever the
 // active lanes, and warps w and w + 4 share a sub-partition: the upper four warps hand their
 // values to the lower four, which run one shuffle tree each (one per sub-partition), and one
-// thread adds the four partial sums.  red: kRedDoubles doubles of shared memory.
+// thread adds the four partial sums (times `scale`, so that a scaled sum costs the other
+// threads nothing).  red: kRedDoubles doubles of shared memory.
 constexpr int kRedDoubles = 136;
 
-__device__ __forceinline__ double block_sum(double v, double *red)
+__device__ __forceinline__ double block_sum(double v, double *red, double scale = 1.0)
 {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     __syncthreads();   // red is free again
@@ -74,27 +76,34 @@ __device__ __forceinline__ double block_sum(double v, double *red)
         if (lane == 0) red[128 + wib] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) red[132] = (red[128] + red[129]) + (red[130] + red[131]);
+    if (threadIdx.x == 0) red[132] = scale * ((red[128] + red[129]) + (red[130] + red[131]));
     __syncthreads();
     return red[132];
 }
 
 // Householder reflector of x = col[r0..k-1], computed by the whole CTA (every
 // CTA forms the same one): H = I - beta v v^T, H x = e_out e_1; v goes to
-// vs[r0..k-1] (zero below r0).
+// vs[r0..k-1] (zero below r0).  v = x + sign(x0) ||x|| e_1 differs from x in
+// one entry, so the scalars (||x||, beta, that entry) are one thread's work and
+// the others copy x: FP64 work repeated on every thread costs issue slots of the
+// FP64 units that the serial chain waits for.  When x = 0, beta = 0 and H = I
+// whatever v holds.
 __device__ void block_house(const double *col, int k, int r0, double *vs, double *beta_out, double *e_out,
                             double *red)
 {
     double ss = 0.0;
     for (int l = r0 + threadIdx.x; l < k; l += blockDim.x) ss += col[l] * col[l];
     ss = block_sum(ss, red);
-    const double x0 = col[r0];
-    const double alpha = sqrt(ss);
-    const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
     for (int l = threadIdx.x; l < k; l += blockDim.x)
-        vs[l] = (l < r0 || alpha == 0.0) ? 0.0 : (l == r0 ? x0 + sgn * alpha : col[l]);
+        if (l != r0) vs[l] = (l < r0) ? 0.0 : col[l];
     if (threadIdx.x == 0) {
-        *beta_out = (alpha == 0.0) ? 0.0 : 1.0 / (alpha * (alpha + fabs(x0)));
+        const double x0 = col[r0];
+        // sqrt(ss) as ss / sqrt(ss): the library rsqrt and one multiplication (about 500
+        // cycles against 680 for sqrt on this GPU's FP64 chain)
+        const double alpha = (ss > 0.0) ? ss * rsqrt(ss) : 0.0;
+        const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
+        vs[r0] = x0 + sgn * alpha;
+        *beta_out = (alpha == 0.0) ? 0.0 : rcp_fast(alpha * (alpha + fabs(x0)));
         *e_out = (alpha == 0.0) ? 0.0 : -sgn * alpha;
     }
     __syncthreads();
@@ -109,11 +118,14 @@ __device__ void block_house(const double *col, int k, int r0, double *vs, double
 // the next column's p or q.  Column j + 1 itself is left to the CTAs (each
 // derives it), so no CTA writes what another still reads.  p and q are
 // double-buffered across the barrier.
-// RES (2k warps or more): warp i owns column i of A and warp k + i column i of
-// Q^T for the whole run, kept in shared memory; only the column every CTA needs
-// next (j + 2, published one step ahead), the last 2 x 2 block and Q^T at the
-// end go back to global memory.  Otherwise warps stride over the columns in
-// global memory (L2), four loads in flight per lane.
+// RES (k <= 4 x CTAs): warp w < 4 of CTA b owns column b + G w of A and warp
+// 4 + w column b + G w of Q^T (G CTAs) for the whole run, kept in shared memory,
+// so each sub-partition carries at most one A column (a rank-2 update, two FMAs
+// per row) and one Q^T column (rank 1), and the live A columns (>= j + 1) stay
+// spread over the CTAs as j grows; only the column every CTA needs next (j + 2,
+// published one step ahead), the last 2 x 2 block and Q^T at the end go back to
+// global memory.  Otherwise warps stride over the columns in global memory (L2),
+// four loads in flight per lane.
 template <bool RES>
 __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int k, double *pq, double *d, double *e)
 {
@@ -135,10 +147,12 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
         }
         return;
     }
-    // RES: owned column (A column gw, or Q^T column gw - k) into shared memory
-    const bool ownA = RES && gw < k, ownQ = RES && gw >= k && gw < 2 * k;
+    // RES: owned column (A column ocol for warps 0-3, Q^T column ocol for warps 4-7) into
+    // shared memory
+    const int wib = threadIdx.x >> 5, ocol = blockIdx.x + gridDim.x * (wib & 3);
+    const bool ownA = RES && wib < 4 && ocol < k, ownQ = RES && wib >= 4 && ocol < k;
     if (RES && (ownA || ownQ)) {
-        const double *src = ownA ? A + (int64_t)gw * k : Qt + (int64_t)(gw - k) * k;
+        const double *src = ownA ? A + (int64_t)ocol * k : Qt + (int64_t)ocol * k;
         for (int l = lane; l < k; l += 32) own[l] = src[l];
         __syncwarp();
     }
@@ -177,18 +191,20 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
                 colj[l] = (in && next) ? a[l] : 0.0;
             }
         }
-        double s = 0.0;   // same partition of l as the fetch above: no barrier needed in between
-        for (int l = threadIdx.x; l < k; l += blockDim.x)
-            if (l >= r0) s += vcur[l] * w[l];
-        const double kh = 0.5 * bt * block_sum(s, red);
-        for (int l = threadIdx.x; l < k; l += blockDim.x)
-            if (l >= r0) w[l] -= kh * vcur[l];
+        // same partition of l as the fetch above (no barrier needed in between), from the
+        // first l >= r0 of this thread's share: warps with no rows left issue nothing
+        const int tx = threadIdx.x, nt = blockDim.x;
+        const int lr = (tx >= r0) ? tx : tx + ((r0 - tx + nt - 1) / nt) * nt;
+        double s = 0.0;
+        for (int l = lr; l < k; l += blockDim.x) s += vcur[l] * w[l];
+        const double kh = block_sum(s, red, 0.5 * bt);
+        for (int l = lr; l < k; l += blockDim.x) w[l] = fma(-kh, vcur[l], w[l]);
         __syncthreads();
         double bn = 0.0;
         if (next) {
             // column r0 after this step's update, rows r0..; then reflector j + 1 from rows r0 + 1..
             const double wr = w[r0], vr = vcur[r0];
-            for (int l = r0 + threadIdx.x; l < k; l += blockDim.x) colj[l] -= vcur[l] * wr + w[l] * vr;
+            for (int l = r0 + threadIdx.x; l < k; l += blockDim.x) colj[l] = fma(-w[l], vr, fma(-vcur[l], wr, colj[l]));
             __syncthreads();
             block_house(colj, k, r0 + 1, vnext, &bnext_s, &enext_s, red);
             __syncthreads();
@@ -201,12 +217,12 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
         const int r1 = r0 + 1;
         double *pn = pq + (size_t)(par ^ 1) * k, *qn = pq + 2 * (size_t)k + (size_t)(par ^ 1) * k;
         if constexpr (RES) {
-            if (ownA && gw >= r0 && !(next && gw == r0)) {
-                const int i = gw;
+            if (ownA && ocol >= r0 && !(next && ocol == r0)) {
+                const int i = ocol;
                 const double vi = vcur[i], wi = w[i];
                 double t = 0.0;
                 for (int l = r0 + lane; l < k; l += 32) {
-                    const double x = own[l] - (vcur[l] * wi + w[l] * vi);
+                    const double x = fma(-w[l], vi, fma(-vcur[l], wi, own[l]));
                     own[l] = x;
                     if (l >= r1) t = fma(x, vnext[l], t);
                 }
@@ -221,7 +237,7 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
                     for (int l = r1 - 1 + lane; l < k; l += 32) dst[l] = own[l];
                 }
             } else if (ownQ) {
-                const int i = gw - k;
+                const int i = ocol;
                 const double qi = q[i];
                 double t = 0.0;
                 for (int l = r0 + lane; l < k; l += 32) {
@@ -250,7 +266,7 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
                         for (int u = 0; u < 4; ++u) {
                             const int l = l0 + 32 * u;
                             if (l < k) {
-                                x[u] -= vcur[l] * wi + w[l] * vi;
+                                x[u] = fma(-w[l], vi, fma(-vcur[l], wi, x[u]));
                                 col[l] = x[u];
                                 if (l >= r1) t = fma(x[u], vnext[l], t);
                             }
@@ -294,7 +310,7 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
     }
     if constexpr (RES) {
         if (ownQ) {
-            double *dst = Qt + (int64_t)(gw - k) * k;
+            double *dst = Qt + (int64_t)ocol * k;
             for (int l = lane; l < k; l += 32) dst[l] = own[l];
         }
     }
@@ -529,10 +545,10 @@ __device__ __forceinline__ double hash_uniform(uint32_t a, uint32_t b)
 
 // Inverse iteration for eigenvalue i of its block; scratch holds the LU of
 // T_b - w_i I in a strided layout (row l of thread i at l*k + i).  One FP64
-// division per row (the reciprocal of the pivot, kept for the back
-// substitution), so the three solves are multiply-adds only; values carried
-// from row to row stay in registers and the loads of the stored factors do not
-// wait on the arithmetic.
+// reciprocal per row (of the pivot, kept for the back substitution; the refined
+// hardware approximation, within one ulp), so the three solves are multiply-adds
+// only; values carried from row to row stay in registers and the loads of the
+// stored factors do not wait on the arithmetic.
 __global__ void inviter_kernel(const double *__restrict__ d, const double *__restrict__ e, const int *__restrict__ blo,
                                const int *__restrict__ bhi, int k, const double *__restrict__ w,
                                const double *__restrict__ tnorm, double *__restrict__ Z, double *__restrict__ u0,
@@ -560,7 +576,7 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
         const double a_next = d[lo + l + 1] - lam;
         const double c_next = (l + 1 < m - 1) ? e[lo + l + 1] : 0.0;
         if (fabs(a_cur) >= fabs(bl)) {
-            const double rp = 1.0 / ((a_cur == 0.0) ? tiny : a_cur);
+            const double rp = rcp_fast((a_cur == 0.0) ? tiny : a_cur);
             const double mult = bl * rp;
             u0[IDX(l)] = rp;
             u1[IDX(l)] = c_cur;
@@ -570,7 +586,7 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
             a_cur = a_next - mult * c_cur;
             c_cur = c_next;
         } else {
-            const double rp = 1.0 / bl;
+            const double rp = rcp_fast(bl);
             const double mult = a_cur * rp;
             u0[IDX(l)] = rp;
             u1[IDX(l)] = a_next;
@@ -581,7 +597,7 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
             c_cur = -mult * c_next;
         }
     }
-    u0[IDX(m - 1)] = 1.0 / ((fabs(a_cur) < tiny) ? (a_cur < 0.0 ? -tiny : tiny) : a_cur);
+    u0[IDX(m - 1)] = rcp_fast((fabs(a_cur) < tiny) ? (a_cur < 0.0 ? -tiny : tiny) : a_cur);
     // start vector: distinct pseudo-random values per eigenvalue
     for (int l = 0; l < m; ++l) z[lo + l] = hash_uniform((uint32_t)i, (uint32_t)l) + 1e-3;
     for (int iter = 0; iter < 3; ++iter) {

@@ -13,6 +13,7 @@
 
 #include <atomic>
 
+#include "fp64_rcp.cuh"
 #include "internal.h"
 
 namespace cg = cooperative_groups;
@@ -607,19 +608,33 @@ __global__ void shift_diag_kernel(double *G, int k, int64_t ldg, double shift_sc
 
 // Cholesky of the jb x jb diagonal block at (J, J) by one CTA of 256 threads (the factor
 // only; the block inverses follow in one launch per factorisation).  FP64 issue costs about
-// 64 cycles per warp instruction on this GPU and the library rsqrt about 430, so the block
-// is a chain of jb pivots: thread 0 alone carries it (the next pivot from the current
-// column and its reciprocal square root) while warps 1..7 apply the rank-1 update of the
-// trailing triangle, one barrier per column.  The entries are enumerated from the
-// bottom-right corner, so the trailing triangle of the last m columns is a prefix of the
-// enumeration and stays spread over the update threads as it shrinks.  The updates use the
-// unscaled columns and 1 / d_j (l_ij l_cj = a_ij a_cj / d_j); the factor is scaled at the
-// end.  The first failing pivot is recorded in info (1-based); the factorisation continues
-// with pivot 1.
+// 64 cycles per warp instruction on this GPU, so the block is a chain of jb pivots: thread 0
+// alone carries it while warps 1..7 apply the rank-1 update of the trailing triangle, one
+// barrier per column.  The chain needs only 1 / d_j: the next pivot is
+// d_(j+1) = a_(j+1,j+1) - a_(j+1,j)^2 / d_j and the updates use the unscaled columns
+// (l_ij l_cj = a_ij a_cj / d_j), so each step is two FMAs and a refined hardware reciprocal
+// (about 370 cycles against 560 with the library rsqrt and r * r); the square roots
+// 1 / sqrt(d_j) that scale the factor are taken once, for all columns at the end.  The
+// entries are enumerated from the bottom-right corner, so the trailing triangle of the last
+// m columns is a prefix of the enumeration and stays spread over the update threads as it
+// shrinks.  The first failing pivot is recorded in info (1-based); the factorisation
+// continues with pivot 1.
 __device__ __forceinline__ bool positive_finite(double d)
 {
     const long long bits = __double_as_longlong(d);
     return bits > 0 && bits < 0x7ff0000000000000LL;
+}
+
+// Rank-1 update of this thread's first NQ trailing-triangle entries by column j.
+template <int NQ>
+__device__ __forceinline__ void potrf_update(double (*As)[NB + 1], const int *ei, const int *ec, const int *eb, int j,
+                                             int m, double r2)
+{
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int i = ei[q], c = ec[q];
+        if (eb[q] < m && !(c == j + 1 && i == j + 1)) As[i][c] = fma(-As[i][j], As[c][j] * r2, As[i][c]);
+    }
 }
 
 // The factorisation of a block held in shared memory (As, padded with the identity to NB x NB),
@@ -651,6 +666,7 @@ __device__ void potrf_smem(double (*As)[NB + 1], double *rsq, double *rv, double
             eb[q] = b;
         }
     }
+    double rcur = 0.0;   // thread 0: 1 / d_j
     if (t == 0) {
         double d = As[0][0];
         if (!positive_finite(d)) {
@@ -658,9 +674,8 @@ __device__ void potrf_smem(double (*As)[NB + 1], double *rsq, double *rv, double
             d = 1.0;
         }
         As[0][0] = d;
-        const double r = rsqrt(d);
-        rv[0] = r;
-        rsq[0] = r * r;
+        rcur = rcp_fast(d);
+        rsq[0] = rcur;
     }
     __syncthreads();
     for (int j = 0; j < NB - 1; ++j) {
@@ -669,25 +684,30 @@ __device__ void potrf_smem(double (*As)[NB + 1], double *rsq, double *rv, double
             // pivot j + 1 after this column's update (its entry is updated here only); a
             // positive finite double is a bit pattern strictly between 0 and +inf
             const double a = As[j + 1][j];
-            double d = fma(-a, a * rsq[j], As[j + 1][j + 1]);
+            double d = fma(-a, a * rcur, As[j + 1][j + 1]);
             if (!positive_finite(d)) {
                 if (j + 1 < jb) atomicCAS(info, 0, J + j + 2);
                 d = 1.0;
             }
             As[j + 1][j + 1] = d;
-            const double r = rsqrt(d);
-            rv[j + 1] = r;
-            rsq[j + 1] = r * r;
+            rcur = rcp_fast(d);
+            rsq[j + 1] = rcur;
         } else if (u >= 0) {
+            // entries e >= 192 (b >= 19) are live only while j < 12 and e >= 384 (b >= 27)
+            // only while j < 4: the code for them is left out after that, not predicated off,
+            // since a predicated-off FP64 instruction still holds the sub-partition's unit
             const double r2 = rsq[j];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const int i = ei[q], c = ec[q];
-                if (eb[q] < m && !(c == j + 1 && i == j + 1)) As[i][c] = fma(-As[i][j], As[c][j] * r2, As[i][c]);
-            }
+            if (j < 4)
+                potrf_update<3>(As, ei, ec, eb, j, m, r2);
+            else if (j < 12)
+                potrf_update<2>(As, ei, ec, eb, j, m, r2);
+            else
+                potrf_update<1>(As, ei, ec, eb, j, m, r2);
         }
         __syncthreads();
     }
+    if (t < NB) rv[t] = rsqrt(As[t][t]);   // the pivots d_c (1 on the identity padding)
+    __syncthreads();
     for (int e = t; e < NB * NB; e += blockDim.x) {
         const int i = e & (NB - 1), c = e / NB;
         if (i < jb && c < jb && c <= i) G[(J + i) + (int64_t)(J + c) * ldg] = As[i][c] * rv[c];
@@ -792,7 +812,7 @@ __global__ void __launch_bounds__(128) panel_trsm_kernel(double *A21, int m2, in
 {
     __shared__ double Ls[NB][NB + 1];   // L_lc / l_cc below the diagonal
     __shared__ double rv[NB];
-    for (int i = threadIdx.x; i < NB; i += blockDim.x) rv[i] = (i < jb) ? 1.0 / L[i + (int64_t)i * ldl] : 0.0;
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) rv[i] = (i < jb) ? rcp_fast(L[i + (int64_t)i * ldl]) : 0.0;
     __syncthreads();
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int i = e & (NB - 1), c = e / NB;
@@ -827,7 +847,7 @@ __global__ void __launch_bounds__(256) trtri_diag_kernel(const double *L, int k,
         const int i = e & (NB - 1), j = e / NB;
         a[i][j] = (i < jb && j < jb) ? L[(J + i) + (int64_t)(J + j) * ldl] : 0.0;
     }
-    for (int i = t; i < NB; i += blockDim.x) rinv[i] = (i < jb) ? 1.0 / L[(J + i) + (int64_t)(J + i) * ldl] : 0.0;
+    for (int i = t; i < NB; i += blockDim.x) rinv[i] = (i < jb) ? rcp_fast(L[(J + i) + (int64_t)(J + i) * ldl]) : 0.0;
     __syncthreads();
     double v[NB / 8];
 #pragma unroll
@@ -840,9 +860,12 @@ __global__ void __launch_bounds__(256) trtri_diag_kernel(const double *L, int k,
         }
         __syncthreads();
         const double xi = xs[i][c];
+        // rows 8 s + g > i; the test 8 s + 7 > i is resolved at compile time, so slots with no
+        // row below i in any warp issue nothing (a predicated-off FP64 instruction still
+        // holds the sub-partition's unit)
 #pragma unroll
         for (int s = 0; s < NB / 8; ++s)
-            if (8 * s + g > i) v[s] = fma(-a[8 * s + g][i], xi, v[s]);
+            if (8 * s + 7 > i && 8 * s + g > i) v[s] = fma(-a[8 * s + g][i], xi, v[s]);
     }
     double *out = dinv + (int64_t)blockIdx.x * NB * NB;
 #pragma unroll

@@ -417,11 +417,13 @@ def riot_kernel_launches():
 
 
 def riot_measure_peaks(device=0):
-    """Measured FP64 / FP32 FMA throughput (TFLOP/s) and FP64 FMA, rsqrt and division latencies
-    (SM cycles) of a GPU, as a dict."""
-    out = (c_double * 5)()
-    _check(None, "riot_measure_peaks", load().riot_measure_peaks(int(device), out, 5))
-    keys = ("fp64_tflops", "fp32_tflops", "fp64_fma_cycles", "fp64_rsqrt_cycles", "fp64_div_cycles")
+    """Measured FP64 / FP32 FMA throughput (TFLOP/s), FP64 FMA, rsqrt, division and refined
+    reciprocal latencies (SM cycles) of a GPU and the refined reciprocal's largest error (ulps),
+    as a dict."""
+    out = (c_double * 7)()
+    _check(None, "riot_measure_peaks", load().riot_measure_peaks(int(device), out, 7))
+    keys = ("fp64_tflops", "fp32_tflops", "fp64_fma_cycles", "fp64_rsqrt_cycles", "fp64_div_cycles",
+            "fp64_rcp_fast_cycles", "fp64_rcp_fast_max_ulps")
     return dict(zip(keys, (float(v) for v in out)))
 
 

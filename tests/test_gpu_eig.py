@@ -84,3 +84,14 @@ def test_symm_eig_block_diagonal_splits(gpu_lib):
     np.testing.assert_allclose(lam, ref, rtol=0, atol=tol)
     assert np.abs(K @ Z - Z * lam).max() <= tol
     assert np.abs(Z.T @ Z - np.eye(k)).max() <= 1e-12
+
+
+def test_refined_reciprocal_within_one_ulp_and_faster(gpu_lib):
+    """The reciprocal on the FP64 chains (Cholesky pivots, the inverse iteration's LU, the
+    Householder reflectors): the hardware approximation refined by one third-order Newton
+    step must stay within one ulp of the correctly rounded 1 / x over 2^24 inputs spanning
+    the double range (and its limits), and must be shorter on the chain than the division."""
+    p = gpu_lib.riot_measure_peaks(0)
+    assert p["fp64_rcp_fast_max_ulps"] <= 1.0
+    assert 0.0 < p["fp64_rcp_fast_cycles"] < p["fp64_div_cycles"]
+    assert p["fp64_fma_cycles"] > 0.0 and p["fp64_tflops"] > 0.0 and p["fp32_tflops"] > p["fp64_tflops"]
