@@ -543,38 +543,29 @@ __device__ __forceinline__ double hash_uniform(uint32_t a, uint32_t b)
     return ((double)h + 0.5) * 2.3283064365386963e-10 - 0.5;
 }
 
-// Inverse iteration for eigenvalue i of its block; scratch holds the LU of
-// T_b - w_i I in a strided layout (row l of thread i at l*k + i).  One FP64
-// reciprocal per row (of the pivot, kept for the back substitution; the refined
-// hardware approximation, within one ulp), so the three solves are multiply-adds
-// only; values carried from row to row stay in registers and the loads of the
-// stored factors do not wait on the arithmetic.
-__global__ void inviter_kernel(const double *__restrict__ d, const double *__restrict__ e, const int *__restrict__ blo,
-                               const int *__restrict__ bhi, int k, const double *__restrict__ w,
-                               const double *__restrict__ tnorm, double *__restrict__ Z, double *__restrict__ u0,
-                               double *__restrict__ u1, double *__restrict__ u2, double *__restrict__ ml,
-                               unsigned char *__restrict__ piv, double *__restrict__ wout)
+// Inverse iteration for one eigenvalue lam of the block T_b = T[lo..lo+m-1] (dd, ee: its
+// diagonal and off-diagonal), by one thread: the LU with partial pivoting of T_b - lam I,
+// three solves from a pseudo-random start, normalisation and the Rayleigh quotient (written
+// to *wout).  Row l of the factors sits at index l * stride of u0, u1, u2, ml and piv; z
+// (unit stride, m entries) receives the eigenvector.  One FP64 reciprocal per row (of the
+// pivot, kept for the back substitution; the refined hardware approximation, within one
+// ulp), so the three solves are multiply-adds only; values carried from row to row stay in
+// registers and the loads of the stored factors do not wait on the arithmetic.
+__device__ __forceinline__ void inviter_one(uint32_t i, const double *dd, const double *ee, int m, double lam,
+                                            double tiny, double *u0, double *u1, double *u2, double *ml,
+                                            unsigned char *piv, int64_t stride, double *z, double *wout)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k) return;
-    const int lo = blo[i], hi = bhi[i], m = hi - lo + 1;
-    double *z = Z + (int64_t)i * k;
-    for (int l = 0; l < k; ++l)
-        if (l < lo || l > hi) z[l] = 0.0;
     if (m == 1) {
-        z[lo] = 1.0;
-        wout[i] = d[lo];
+        z[0] = 1.0;
+        *wout = dd[0];
         return;
     }
-    const double lam = w[i];
-    const double tiny = DBL_EPSILON * fmax(*tnorm, DBL_MIN);
-#define IDX(l) ((int64_t)(l) * k + i)
-    // LU with partial pivoting of the block minus lam I (rows 0..m-1 local); u0 keeps 1 / pivot
-    double a_cur = d[lo] - lam, c_cur = e[lo];
+#define IDX(l) ((int64_t)(l) * stride)
+    double a_cur = dd[0] - lam, c_cur = ee[0];
     for (int l = 0; l < m - 1; ++l) {
-        const double bl = e[lo + l];                 // sub-diagonal below a_cur
-        const double a_next = d[lo + l + 1] - lam;
-        const double c_next = (l + 1 < m - 1) ? e[lo + l + 1] : 0.0;
+        const double bl = ee[l];                     // sub-diagonal below a_cur
+        const double a_next = dd[l + 1] - lam;
+        const double c_next = (l + 1 < m - 1) ? ee[l + 1] : 0.0;
         if (fabs(a_cur) >= fabs(bl)) {
             const double rp = rcp_fast((a_cur == 0.0) ? tiny : a_cur);
             const double mult = bl * rp;
@@ -599,11 +590,11 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
     }
     u0[IDX(m - 1)] = rcp_fast((fabs(a_cur) < tiny) ? (a_cur < 0.0 ? -tiny : tiny) : a_cur);
     // start vector: distinct pseudo-random values per eigenvalue
-    for (int l = 0; l < m; ++l) z[lo + l] = hash_uniform((uint32_t)i, (uint32_t)l) + 1e-3;
+    for (int l = 0; l < m; ++l) z[l] = hash_uniform(i, (uint32_t)l) + 1e-3;
     for (int iter = 0; iter < 3; ++iter) {
         // forward: apply the row operations (row l + 1 carried in a register); the
         // stored factors of four rows are fetched before they are used
-        double carry = z[lo];
+        double carry = z[0];
         for (int l0 = 0; l0 < m - 1; l0 += 4) {
             double nx[4], mv[4];
             bool sv[4];
@@ -611,7 +602,7 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
             for (int u = 0; u < 4; ++u) {
                 const int l = l0 + u;
                 const bool in = l < m - 1;
-                nx[u] = in ? z[lo + l + 1] : 0.0;
+                nx[u] = in ? z[l + 1] : 0.0;
                 mv[u] = in ? ml[IDX(l)] : 0.0;
                 sv[u] = in && piv[IDX(l)] != 0;
             }
@@ -620,12 +611,12 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
                 const int l = l0 + u;
                 if (l < m - 1) {
                     const double r0v = sv[u] ? nx[u] : carry, r1v = sv[u] ? carry : nx[u];
-                    z[lo + l] = r0v;
+                    z[l] = r0v;
                     carry = r1v - mv[u] * r0v;
                 }
             }
         }
-        z[lo + m - 1] = carry;
+        z[m - 1] = carry;
         // backward substitution with U (1 / diagonal, u1, u2), four rows fetched ahead
         double x2 = 0.0, x1 = 0.0, big = 0.0;
         for (int l0 = m - 1; l0 >= 0; l0 -= 4) {
@@ -634,7 +625,7 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
             for (int u = 0; u < 4; ++u) {
                 const int l = l0 - u;
                 const bool in = l >= 0;
-                zv[u] = in ? z[lo + l] : 0.0;
+                zv[u] = in ? z[l] : 0.0;
                 a0[u] = in ? u0[IDX(l)] : 0.0;
                 a1[u] = in ? u1[IDX(l)] : 0.0;
                 a2[u] = in ? u2[IDX(l)] : 0.0;
@@ -644,7 +635,7 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
                 const int l = l0 - u;
                 if (l >= 0) {
                     const double xl = (zv[u] - a1[u] * x1 - a2[u] * x2) * a0[u];
-                    z[lo + l] = xl;
+                    z[l] = xl;
                     x2 = x1;
                     x1 = xl;
                     big = fmax(big, fabs(xl));
@@ -652,22 +643,183 @@ __global__ void inviter_kernel(const double *__restrict__ d, const double *__res
             }
         }
         const double sc = (big > 0.0 && isfinite(big)) ? 1.0 / big : 1.0;
-        for (int l = 0; l < m; ++l) z[lo + l] *= sc;
+        for (int l = 0; l < m; ++l) z[l] *= sc;
     }
+#undef IDX
     double nrm = 0.0;
-    for (int l = 0; l < m; ++l) nrm += z[lo + l] * z[lo + l];
+    for (int l = 0; l < m; ++l) nrm += z[l] * z[l];
     nrm = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
-    for (int l = 0; l < m; ++l) z[lo + l] *= nrm;
+    for (int l = 0; l < m; ++l) z[l] *= nrm;
     // Rayleigh quotient z^T T z refines the bracketed eigenvalue
     double rq = 0.0;
     for (int l = 0; l < m; ++l) {
-        double tz = d[lo + l] * z[lo + l];
-        if (l > 0) tz += e[lo + l - 1] * z[lo + l - 1];
-        if (l + 1 < m) tz += e[lo + l] * z[lo + l + 1];
-        rq += z[lo + l] * tz;
+        double tz = dd[l] * z[l];
+        if (l > 0) tz += ee[l - 1] * z[l - 1];
+        if (l + 1 < m) tz += ee[l] * z[l + 1];
+        rq += z[l] * tz;
     }
-    wout[i] = rq;
-#undef IDX
+    *wout = rq;
+}
+
+// Inverse iteration with the factors in global memory (strided: row l of eigenvalue i at
+// l * k + i) and the vector written in place, for k too large for the shared-memory form.
+__global__ void inviter_kernel(const double *__restrict__ d, const double *__restrict__ e, const int *__restrict__ blo,
+                               const int *__restrict__ bhi, int k, const double *__restrict__ w,
+                               const double *__restrict__ tnorm, double *__restrict__ Z, double *__restrict__ u0,
+                               double *__restrict__ u1, double *__restrict__ u2, double *__restrict__ ml,
+                               unsigned char *__restrict__ piv, double *__restrict__ wout)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    const int lo = blo[i], hi = bhi[i], m = hi - lo + 1;
+    double *z = Z + (int64_t)i * k;
+    for (int l = 0; l < k; ++l)
+        if (l < lo || l > hi) z[l] = 0.0;
+    const double tiny = DBL_EPSILON * fmax(*tnorm, DBL_MIN);
+    inviter_one((uint32_t)i, d + lo, e + lo, m, w[i], tiny, u0 + i, u1 + i, u2 + i, ml + i, piv + i, k, z + lo,
+                wout + i);
+}
+
+// |a| >= |b| and a == 0 for finite doubles, on the integer unit: the magnitude bits of
+// finite doubles order like unsigned integers (an FP64 compare would hold the FP64 unit)
+__device__ __forceinline__ bool mag_ge(double a, double b)
+{
+    return (__double_as_longlong(a) & 0x7fffffffffffffffLL) >= (__double_as_longlong(b) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool is_zero(double a) { return (__double_as_longlong(a) & 0x7fffffffffffffffLL) == 0; }
+
+// Inverse iteration for one eigenvalue by one warp, everything in shared memory (stride 1):
+// lane 0 carries the serial recurrences (the LU and the two substitutions), and the passes
+// that are elementwise or reductions (the scaling after each solve, the norm, the Rayleigh
+// quotient) run on all 32 lanes.  One lane alone issues one FP64 instruction per ~64 cycles
+// whether or not they depend on each other, so every FP64 instruction taken off lane 0's
+// row loop shortens the chain.  The arithmetic is that of inviter_one, except that the
+// largest entry is found after the back substitution instead of during it.
+__device__ __forceinline__ void inviter_warp(uint32_t i, const double *dd, const double *ee, int m, double lam,
+                                             double tiny, double *u0, double *u1, double *u2, double *ml,
+                                             unsigned char *piv, double *z, double *wout, int lane)
+{
+    if (m == 1) {
+        if (lane == 0) {
+            z[0] = 1.0;
+            *wout = dd[0];
+        }
+        return;
+    }
+    if (lane == 0) {
+        double a_cur = dd[0] - lam, c_cur = ee[0];
+        for (int l = 0; l < m - 1; ++l) {
+            const double bl = ee[l];
+            const double a_next = dd[l + 1] - lam;
+            const double c_next = (l + 1 < m - 1) ? ee[l + 1] : 0.0;
+            if (mag_ge(a_cur, bl)) {
+                const double rp = rcp_fast(is_zero(a_cur) ? tiny : a_cur);
+                const double mult = bl * rp;
+                u0[l] = rp;
+                u1[l] = c_cur;
+                u2[l] = 0.0;
+                ml[l] = mult;
+                piv[l] = 0;
+                a_cur = fma(-mult, c_cur, a_next);
+                c_cur = c_next;
+            } else {
+                const double rp = rcp_fast(bl);
+                const double mult = a_cur * rp;
+                u0[l] = rp;
+                u1[l] = a_next;
+                u2[l] = c_next;
+                ml[l] = mult;
+                piv[l] = 1;
+                a_cur = fma(-mult, a_next, c_cur);
+                c_cur = -mult * c_next;
+            }
+        }
+        u0[m - 1] = rcp_fast(mag_ge(a_cur, tiny) ? a_cur : (a_cur < 0.0 ? -tiny : tiny));
+    }
+    for (int l = lane; l < m; l += 32) z[l] = hash_uniform(i, (uint32_t)l) + 1e-3;
+    __syncwarp();
+    for (int iter = 0; iter < 3; ++iter) {
+        if (lane == 0) {
+            double carry = z[0];
+            for (int l = 0; l < m - 1; ++l) {
+                const double nx = z[l + 1], mv = ml[l];
+                const bool sv = piv[l] != 0;
+                const double r0v = sv ? nx : carry, r1v = sv ? carry : nx;
+                z[l] = r0v;
+                carry = fma(-mv, r0v, r1v);
+            }
+            z[m - 1] = carry;
+            double x2 = 0.0, x1 = 0.0;
+            for (int l = m - 1; l >= 0; --l) {
+                const double xl = fma(-u1[l], x1, fma(-u2[l], x2, z[l])) * u0[l];
+                z[l] = xl;
+                x2 = x1;
+                x1 = xl;
+            }
+        }
+        __syncwarp();
+        double big = 0.0;
+        for (int l = lane; l < m; l += 32) big = fmax(big, fabs(z[l]));
+        for (int off = 16; off > 0; off >>= 1) big = fmax(big, __shfl_xor_sync(0xffffffffu, big, off));
+        const double sc = (big > 0.0 && isfinite(big)) ? 1.0 / big : 1.0;
+        for (int l = lane; l < m; l += 32) z[l] *= sc;
+        __syncwarp();
+    }
+    double nrm = 0.0;
+    for (int l = lane; l < m; l += 32) nrm = fma(z[l], z[l], nrm);
+    nrm = warp_sum(nrm);
+    nrm = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
+    double rq = 0.0;
+    for (int l = lane; l < m; l += 32) {
+        const double zl = z[l] * nrm;
+        double tz = dd[l] * zl;
+        if (l > 0) tz = fma(ee[l - 1], z[l - 1] * nrm, tz);
+        if (l + 1 < m) tz = fma(ee[l], z[l + 1] * nrm, tz);
+        rq = fma(zl, tz, rq);
+    }
+    rq = warp_sum(rq);
+    __syncwarp();
+    for (int l = lane; l < m; l += 32) z[l] *= nrm;
+    if (lane == 0) *wout = rq;
+}
+
+// The same with T, the factors and the vector in shared memory: one warp per eigenvalue
+// (inviter_warp; the pivoting branches of different eigenvalues never diverge within a
+// warp, and the warp writes the column out), WPC warps per CTA sharing one copy of T.
+// Shared memory: 2 k doubles of T, then per warp u0, u1, u2, ml and z (k doubles each)
+// and piv (k bytes).
+template <int WPC>
+__global__ void __launch_bounds__(32 * WPC)
+    inviter_smem_kernel(const double *__restrict__ d, const double *__restrict__ e, const int *__restrict__ blo,
+                        const int *__restrict__ bhi, int k, const double *__restrict__ w,
+                        const double *__restrict__ tnorm, double *__restrict__ Z, double *__restrict__ wout)
+{
+    extern __shared__ double ism[];
+    double *ds = ism, *es = ism + k;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *base = ism + 2 * (size_t)k + (size_t)wib * 5 * k;
+    unsigned char *pv = reinterpret_cast<unsigned char *>(ism + 2 * (size_t)k + (size_t)WPC * 5 * k) + (size_t)wib * k;
+    for (int l = threadIdx.x; l < k; l += blockDim.x) {
+        ds[l] = d[l];
+        es[l] = (l + 1 < k) ? e[l] : 0.0;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * WPC + wib;
+    if (i >= k) return;   // no CTA barrier follows
+    const int lo = blo[i], hi = bhi[i], m = hi - lo + 1;
+    double *zs = base + 4 * (size_t)k;
+    const double tiny = DBL_EPSILON * fmax(*tnorm, DBL_MIN);
+    inviter_warp((uint32_t)i, ds + lo, es + lo, m, w[i], tiny, base, base + k, base + 2 * (size_t)k,
+                 base + 3 * (size_t)k, pv, zs, wout + i, lane);
+    __syncwarp();
+    double *z = Z + (int64_t)i * k;
+    for (int l = lane; l < k; l += 32) z[l] = (l >= lo && l <= hi) ? zs[l - lo] : 0.0;
+}
+
+// Shared memory of inviter_smem_kernel<wpc> for order k.
+inline size_t inviter_smem_bytes(int k, int wpc)
+{
+    return sizeof(double) * (2 + 5 * (size_t)wpc) * k + (size_t)wpc * k;
 }
 
 // Sort eigenvalues descending (stable by index) and gather the columns.
@@ -743,9 +895,28 @@ cudaError_t tridiag_eig(const double *K, int k, double *lam, double *Z, double *
         multisect_kernel<G, U><<<(int)(((int64_t)k * G + 127) / 128), 128, 0, s>>>(d, ds, e2s, blo, bhi, bstart,
                                                                                  nblocks, k, tnorm, tsc, counts, w);
     }
-    count_launch();
-    inviter_kernel<<<(k + 3) / 4, 4, 0, s>>>(d, e, blo, bhi, k, w, tnorm, Zt, u0, u1, u2, ml, piv, wrq);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    {
+        // inverse iteration in shared memory when the factors of one eigenvalue fit (k <= 5670),
+        // four eigenvalues per CTA where they fit (k <= 1417); else from global memory
+        const size_t lim = 227 * 1024;
+        count_launch();
+        if (inviter_smem_bytes(k, 4) <= lim) {
+            const size_t sm = inviter_smem_bytes(k, 4);
+            if ((err = cudaFuncSetAttribute(inviter_smem_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sm)) != cudaSuccess)
+                return err;
+            inviter_smem_kernel<4><<<(k + 3) / 4, 128, sm, s>>>(d, e, blo, bhi, k, w, tnorm, Zt, wrq);
+        } else if (inviter_smem_bytes(k, 1) <= lim) {
+            const size_t sm = inviter_smem_bytes(k, 1);
+            if ((err = cudaFuncSetAttribute(inviter_smem_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sm)) != cudaSuccess)
+                return err;
+            inviter_smem_kernel<1><<<k, 32, sm, s>>>(d, e, blo, bhi, k, w, tnorm, Zt, wrq);
+        } else {
+            inviter_kernel<<<(k + 3) / 4, 4, 0, s>>>(d, e, blo, bhi, k, w, tnorm, Zt, u0, u1, u2, ml, piv, wrq);
+        }
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
     // CholeskyQR on the eigenvectors of T: shifted passes (Fukaya et al. 2020), so that
     // eigenvalues clustered below the resolution eps ||T|| (whose inverse-iteration
     // vectors nearly coincide) still yield an orthonormal set, then a plain pass.  Two
