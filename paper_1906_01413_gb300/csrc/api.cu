@@ -98,6 +98,9 @@ struct riot_ctx {
     // S = diag(1 / sigma_o) and sigma_o, and p-vectors
     double *psW = nullptr, *psY = nullptr, *psQ = nullptr, *psU = nullptr, *psF = nullptr, *psR = nullptr;
     double *psS = nullptr, *psSig = nullptr, *psr = nullptr, *psw = nullptr, *psc = nullptr;
+    // Cholesky factorisations as one cooperative launch over every SM (cleared while a batch
+    // runs the windows' linear algebra on parallel streams)
+    bool chol_whole_gpu = true;
     // timing
     cudaEvent_t ev[32];
     int nev = 0;
@@ -297,7 +300,7 @@ riot_status cholqr64(riot_ctx *ctx, double *X, int k, int shifted, int info_base
         CU(equilibrate(ctx->G, k, k, X, 'd', n, n, ctx->cvec, ctx->s));
         const double u = ldexp(1.0, -53);
         const double shift = (pass < shifted || ctx->qr_shift_all) ? 11.0 * ((double)n * k + (double)k * (k + 1)) * u : 0.0;
-        CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
+        CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s, ctx->chol_whole_gpu));
         CU(trsm_right_lt(X, n, k, n, ctx->G, k, ctx->s, ctx->gws));
     }
     return RIOT_OK;
@@ -333,7 +336,7 @@ riot_status orth32(riot_ctx *ctx, const float *Y, int k, int info_base, int pass
         const double shift = (pass < shifted)
                                  ? fmax(11.0 * ((double)n * k + (double)k * (k + 1)) * u, ldexp(1.0, -29) / k)
                                  : 0.0;
-        CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s));
+        CU(cholesky(ctx->G, k, k, shift, ctx->info + info_base + pass, ctx->gws, ctx->s, ctx->chol_whole_gpu));
         CU(convert_block(ctx->G, 'd', k, ctx->L32, 'f', k, k, k, ctx->s));
         CU(put_block_inverses(ctx->L32, k, k, ctx->gws, ctx->s));
         CU(strsm_right_lt_inv(ctx->Q32, n, k, n, ctx->L32, k, ctx->s));
@@ -347,10 +350,14 @@ riot_status check_cholesky(riot_ctx *ctx, int base, int count, const char *what)
     if (count > 16) count = 16;
     CU(cudaMemcpyAsync(h, ctx->info + base, sizeof(int) * count, cudaMemcpyDeviceToHost, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
+        if (h[i] < 0)
+            return fail(ctx, RIOT_ETIMEOUT, "%s: a bounded wait of the cooperative Cholesky (pass %d) ran out", what,
+                        i);
         if (h[i] != 0)
             return fail(ctx, RIOT_ENOTSPD, "%s: Cholesky pass %d met a non-positive pivot at column %d", what, i,
                         h[i] - 1);
+    }
     return RIOT_OK;
 }
 
@@ -1111,7 +1118,7 @@ riot_status rsvd_end(riot_ctx *ctx, int k, bool with_eig)
         // precision (A Q0 then loses Q0's trailing directions): a retry with a shift of the order
         // of the Cholesky backward error (8 k u tr) keeps the solve defined (see rsvd_retry_k)
         const double ushift = ctx->k_shift ? 8.0 * k * ldexp(1.0, -53) : 0.0;
-        CU(cholesky(ctx->G, k, k, ushift, ctx->info + 10, ctx->gws, s));
+        CU(cholesky(ctx->G, k, k, ushift, ctx->info + 10, ctx->gws, s, ctx->chol_whole_gpu));
         CU(trsm_right_lt(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
         CU(trsm_right_l(ctx->Km, k, k, k, ctx->G, k, s, ctx->gws));
     }
@@ -1222,6 +1229,7 @@ riot_status batch_enqueue(riot_batch *b, int64_t sketch_stream)
         saved[w] = b->ctx[w]->s;
         b->ctx[w]->s = b->ws[w];
         b->ctx[w]->nev = 32;   // no phase events inside a batch
+        b->ctx[w]->chol_whole_gpu = false;
     }
     riot_status st = RIOT_OK;
     cudaError_t e = cudaSuccess;
@@ -1273,7 +1281,10 @@ riot_status batch_enqueue(riot_batch *b, int64_t sketch_stream)
         if (st != RIOT_OK) break;
         join();
     } while (0);
-    for (int w = 0; w < nw; ++w) b->ctx[w]->s = saved[w];
+    for (int w = 0; w < nw; ++w) {
+        b->ctx[w]->s = saved[w];
+        b->ctx[w]->chol_whole_gpu = true;
+    }
     if (st != RIOT_OK) return bfail(b, st, "batch: %s", "a window's inner-loop step failed (see its context)");
     if (e != cudaSuccess) return bfail(b, RIOT_ECUDA, "batch: %s", cudaGetErrorString(e));
     return RIOT_OK;
@@ -2623,7 +2634,8 @@ riot_status riot_psas(riot_ctx *ctx, int32_t m, int32_t q, int64_t sketch_stream
             CU(syrk_lower(m, m, ctx->Mm, m, ctx->G, m, s));
             CU(gemm('N', 'T', m, m, m, 1.0, ctx->Nm, 'd', m, ctx->Mm, 'd', m, 0.0, ctx->Km, 'd', m, s));
             CU(cudaMemsetAsync(ctx->info + 10, 0, sizeof(int), s));
-            CU(cholesky(ctx->G, m, m, attempt ? 8.0 * m * ldexp(1.0, -53) : 0.0, ctx->info + 10, ctx->gws, s));
+            CU(cholesky(ctx->G, m, m, attempt ? 8.0 * m * ldexp(1.0, -53) : 0.0, ctx->info + 10, ctx->gws, s,
+                        ctx->chol_whole_gpu));
             CU(trsm_right_lt(ctx->Km, m, m, m, ctx->G, m, s, ctx->gws));
             CU(trsm_right_l(ctx->Km, m, m, m, ctx->G, m, s, ctx->gws));
             int i10 = 0;

@@ -273,10 +273,14 @@ cudaError_t convert_block(const void *in, char tin, int64_t ldin, void *out, cha
                           int64_t rows, int cols, cudaStream_t s);
 // In-place blocked Cholesky of the k x k SPD matrix G (lower factor); adds
 // shift_scale * trace(G) to the diagonal first when shift_scale > 0.
-// info[0] = 0 on success, else 1 + first failing pivot.  dinv (dinv_doubles(k))
+// info[0] = 0 on success, else 1 + first failing pivot (-1: a bounded wait of the
+// cooperative form ran out).  dinv (dinv_doubles(k))
 // receives the inverses of the factor's 32 x 32 diagonal blocks, which the
-// triangular solves below use.
-cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *dinv, cudaStream_t s);
+// triangular solves below use.  whole_gpu: one cooperative launch over every SM
+// (the GPU runs nothing else meanwhile: a single window); else two launches per
+// block column with small grids, which windows on parallel streams can share.
+cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *dinv, cudaStream_t s,
+                     bool whole_gpu = true);
 size_t dinv_doubles(int k);
 // inverses of the diagonal blocks of a lower-triangular L (when not from cholesky)
 cudaError_t trtri_diag(const double *L, int k, int64_t ldl, double *dinv, cudaStream_t s);

@@ -403,10 +403,12 @@ cudaError_t put_block_inverses(float *L32, int k, int64_t ldl, const double *din
 // them, see put_block_inverses).  Rows are independent, so a CTA owns 32 rows for all k
 // columns in shared memory (column-major over the 32 rows, four rows per float4) and sweeps
 // the block columns left to right: block J takes X_J - sum_{l<J} Y_l L_Jl^T and is then
-// multiplied by the block inverse.  The 32 x 32 blocks of L stream through a ring of four
+// multiplied by the block inverse.  The 32 x 32 blocks of L stream through a ring of eight
 // shared-memory buffers filled by cp.async (4-byte copies, so any leading dimension works),
-// three blocks ahead of the one in use.
+// seven blocks ahead of the one in use (a block's arithmetic is shorter than an L2 round
+// trip).
 constexpr int kTrsmRows = 32;
+constexpr int kTrsmRing = 8;
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src)
 {
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int
     constexpr int R = kTrsmRows;
     extern __shared__ __align__(16) float trsm_sm[];
     float *Ys = trsm_sm;                          // [k][R]
-    float *ring = trsm_sm + (size_t)k * R;        // [4][32 kk][32 ci]
+    float *ring = trsm_sm + (size_t)k * R;        // [kTrsmRing][32 kk][32 ci]
     const int t = threadIdx.x, cj = t & 31, g = t >> 5;
     const int r0 = blockIdx.x * R;
     const int nb = (k + 31) / 32, nblk = nb * (nb + 1) / 2;
@@ -454,16 +456,15 @@ __global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int
         }
         cp_async_commit();
     };
-    issue(0);
-    issue(1);
-    issue(2);
+#pragma unroll
+    for (int q = 0; q < kTrsmRing - 1; ++q) issue(q);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     int J = 0, l = 0;
     for (int b = 0; b < nblk; ++b) {
-        cp_async_wait<2>();
+        cp_async_wait<kTrsmRing - 2>();
         __syncthreads();
-        issue((b + 3) & 3);
-        const float *buf = ring + (b & 3) * 1024;
+        issue((b + kTrsmRing - 1) % kTrsmRing);
+        const float *buf = ring + (b % kTrsmRing) * 1024;
         const int colJ = 32 * J + cj;
         if (l == 0) {
             if (colJ < k) {
@@ -521,7 +522,7 @@ __global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int
 cudaError_t strsm_right_lt_inv(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s)
 {
     if (m <= 0 || k <= 0) return cudaSuccess;
-    const size_t smem = sizeof(float) * ((size_t)k * kTrsmRows + 4 * 1024);
+    const size_t smem = sizeof(float) * ((size_t)k * kTrsmRows + kTrsmRing * 1024);
     if (smem <= 227 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(strsm_lt_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -835,12 +836,10 @@ __global__ void __launch_bounds__(128) panel_trsm_kernel(double *A21, int m2, in
 // right-looking substitution with lane = column: the rows are split over the 8 warps (rows
 // g, g + 8, ...), so a step is one multiply by the warp that owns row i, a barrier, and at
 // most four FMAs per warp on the rows below.
-__global__ void __launch_bounds__(256) trtri_diag_kernel(const double *L, int k, int64_t ldl, double *dinv)
+__device__ void trtri_block(const double *L, int k, int64_t ldl, double *dinv, int blk, double (*a)[NB + 1],
+                            double (*xs)[NB + 1], double *rinv)
 {
-    __shared__ double a[NB][NB + 1];
-    __shared__ double xs[NB][NB + 1];   // row i of X, published when final
-    __shared__ double rinv[NB];
-    const int J = blockIdx.x * NB;
+    const int J = blk * NB;
     const int jb = (k - J < NB) ? k - J : NB;
     const int t = threadIdx.x, c = t & 31, g = t >> 5;
     for (int e = t; e < NB * NB; e += blockDim.x) {
@@ -867,11 +866,193 @@ __global__ void __launch_bounds__(256) trtri_diag_kernel(const double *L, int k,
         for (int s = 0; s < NB / 8; ++s)
             if (8 * s + 7 > i && 8 * s + g > i) v[s] = fma(-a[8 * s + g][i], xi, v[s]);
     }
-    double *out = dinv + (int64_t)blockIdx.x * NB * NB;
+    double *out = dinv + (int64_t)blk * NB * NB;
 #pragma unroll
     for (int s = 0; s < NB / 8; ++s) {
         const int r = 8 * s + g;
         out[r + NB * c] = (r >= c && r < jb && c < jb) ? v[s] : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) trtri_diag_kernel(const double *L, int k, int64_t ldl, double *dinv)
+{
+    __shared__ double a[NB][NB + 1];
+    __shared__ double xs[NB][NB + 1];   // row i of X, published when final
+    __shared__ double rinv[NB];
+    trtri_block(L, k, ldl, dinv, blockIdx.x, a, xs, rinv);
+}
+
+// The whole blocked Cholesky in one cooperative launch (one CTA per SM; every CTA resident,
+// so grid barriers are safe), for a GPU that runs one factorisation at a time.  Per block
+// column J, with L_JJ factored:
+//   1. panel: every warp of the grid solves rows of A21 <- A21 L_JJ^-T (one warp per row,
+//      as panel_trsm_kernel); grid barrier;
+//   2. CTAs 1..8 each form a slice of the next diagonal block's update from the first rows
+//      of the solved panel and count it on a flag; CTA 0 (holding the block since step 1)
+//      waits for the count, subtracts, and factors the block (potrf_smem: the pivot chain),
+//      while CTAs 1.. update the rest of the trailing matrix in 16 x 16 tiles (rows below the
+//      next diagonal block, every column from it on); grid barrier.
+// The launches of the multi-kernel form (a panel and a fused trailing step per block column)
+// each paid a launch and a ramp; here a block column costs two grid barriers and one flag.
+// The flag's wait is bounded (info = -1 if it ever ran out, which needs a CTA that is not
+// resident, and the cooperative launch rules that out).  The block inverses come last, one
+// block per CTA.
+constexpr int kCoopSlices = 8;
+constexpr long long kCoopPollLimit = 1LL << 22;   // a few seconds of polls (an L2 round trip and a 64 ns sleep each)
+
+__global__ void __launch_bounds__(256, 1) chol_coop_kernel(double *G, int64_t ldg, int k, int *info, double *dinv)
+{
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double As[NB][NB + 1];
+    __shared__ double Ps[NB][NB + 1];
+    __shared__ double rsq[NB], rv[NB];
+    const int t = threadIdx.x, lane = t & 31;
+    const int nblk = (k + NB - 1) / NB;
+    const int ns = (gridDim.x - 1 < kCoopSlices) ? (int)gridDim.x - 1 : kCoopSlices;   // CTAs forming the update
+    unsigned *dcount = reinterpret_cast<unsigned *>(dinv + NB * (NB + 1) / 2 + 1);       // after the 528 slots
+    if (blockIdx.x == 0 && t == 0) *dcount = 0u;   // visible to all after the first grid barrier
+    if (blockIdx.x == 0) {
+        const int jb0 = k < NB ? k : NB;
+        for (int e = t; e < NB * NB; e += blockDim.x) {
+            const int i = e & (NB - 1), c = e / NB;
+            As[i][c] = (i < jb0 && c < jb0) ? (c <= i ? G[i + (int64_t)c * ldg] : 0.0) : (i == c ? 1.0 : 0.0);
+        }
+        __syncthreads();
+        potrf_smem(As, rsq, rv, G, ldg, 0, jb0, info);
+    }
+    grid.sync();
+    for (int J = 0; J + 1 < nblk; ++J) {
+        const int c0 = J * NB, jb = (k - c0 < NB) ? k - c0 : NB;
+        const int r0 = c0 + jb, m2 = k - r0;
+        const int jb2 = m2 < NB ? m2 : NB;
+        // 1. panel rows r0 + gw, r0 + gw + W, ... (W warps in the grid).  Every load a CTA
+        // needs is issued before the first use: this warp's first row, the factor L_JJ, and
+        // (CTA 0) the next diagonal block, final since the previous trailing update.
+        const int W = gridDim.x * (blockDim.x >> 5);
+        const int gw0 = blockIdx.x * (blockDim.x >> 5);
+        if (blockIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < NB * NB / 256; ++q) {
+                const int e = t + 256 * q, i = e & (NB - 1), c = e / NB;
+                As[i][c] = (i < jb2 && c < jb2) ? (c <= i ? G[(r0 + i) + (int64_t)(r0 + c) * ldg] : 0.0)
+                                                : (i == c ? 1.0 : 0.0);
+            }
+        }
+        if (gw0 < m2) {
+            const double *L = G + c0 + (int64_t)c0 * ldg;
+            const int rf = gw0 + (t >> 5);
+            const double xf = (rf < m2 && lane < jb) ? G[(r0 + rf) + (int64_t)(c0 + lane) * ldg] : 0.0;
+            double lv[NB * NB / 256];
+#pragma unroll
+            for (int q = 0; q < NB * NB / 256; ++q) {
+                const int e = t + 256 * q, i = e & (NB - 1), c = e / NB;
+                lv[q] = (i < jb && c <= i) ? L[i + (int64_t)c * ldg] : 0.0;
+            }
+            if (t < NB) rv[t] = (t < jb) ? rcp_fast(L[t + (int64_t)t * ldg]) : 0.0;
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < NB * NB / 256; ++q) {
+                const int e = t + 256 * q, i = e & (NB - 1), c = e / NB;
+                Ps[i][c] = (c < i) ? lv[q] * rv[c] : 0.0;
+            }
+            __syncthreads();
+            for (int r = rf; r < m2; r += W) {
+                double *row = G + (r0 + r) + (int64_t)c0 * ldg;
+                double x = (r == rf) ? xf : ((lane < jb) ? row[(int64_t)lane * ldg] : 0.0);
+#pragma unroll
+                for (int c = 0; c < NB - 1; ++c) {
+                    const double xc = __shfl_sync(0xffffffffu, x, c);
+                    if (lane > c) x = fma(-Ps[lane][c], xc, x);
+                }
+                if (lane < jb) row[(int64_t)lane * ldg] = x * rv[lane];
+            }
+        }
+        grid.sync();
+        // 2. next diagonal block (CTA 0) and the rest of the trailing update (CTAs 1..).  The
+        // block's own update (528 dot products of length 32, about 4 us of FP64 issue on one
+        // SM) is formed in slices by CTAs 1..ns into dinv (free until the block inverses) and
+        // counted on a flag; CTA 0 waits for the count, subtracts, and runs the pivot chain.
+        if (blockIdx.x == 0) {
+            if (t == 0) {
+                const unsigned target = (unsigned)(ns * (J + 1));
+                long long polls = 0;
+                while (*(volatile unsigned *)dcount < target && ++polls < kCoopPollLimit) __nanosleep(64);
+                if (polls >= kCoopPollLimit) atomicCAS(info, 0, -1);   // cannot happen with every CTA resident
+                __threadfence();
+            }
+            __syncthreads();
+            for (int e = t; e < NB * (NB + 1) / 2; e += blockDim.x) {
+                int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                while (i > 0 && i * (i + 1) / 2 > e) --i;
+                const int c = e - i * (i + 1) / 2;
+                if (i < jb2) As[i][c] -= __ldcg(dinv + e);
+            }
+            __syncthreads();
+            potrf_smem(As, rsq, rv, G, ldg, r0, jb2, info);
+        } else {
+            if (blockIdx.x <= ns) {
+                // slice blockIdx.x - 1: entries [e0, e0 + per), one thread per entry, in the
+                // summation order of chol_trail_kernel (so both forms give the same factor)
+                const int per = (NB * (NB + 1) / 2 + ns - 1) / ns, e0 = (blockIdx.x - 1) * per;
+#pragma unroll
+                for (int q = 0; q < NB * NB / 256; ++q) {
+                    const int e = t + 256 * q, i = e & (NB - 1), c = e / NB;
+                    Ps[i][c] = (i < jb2 && c < jb) ? G[(r0 + i) + (int64_t)(c0 + c) * ldg] : 0.0;
+                }
+                __syncthreads();
+                const int e = e0 + t;
+                if (t < per && e < NB * (NB + 1) / 2) {
+                    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                    while (i > 0 && i * (i + 1) / 2 > e) --i;
+                    const int c = e - i * (i + 1) / 2;
+                    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+                    for (int kk = 0; kk < NB; kk += 2) {
+                        a0 = fma(Ps[i][kk], Ps[c][kk], a0);
+                        a1 = fma(Ps[i][kk + 1], Ps[c][kk + 1], a1);
+                    }
+                    dinv[e] = a0 + a1;
+                }
+                __threadfence();
+                __syncthreads();
+                if (t == 0) atomicAdd(dcount, 1u);
+            }
+            // tiles: rows r0 + jb2 + 16 tr.. (m3 rows), columns r0 + 16 tc.. (m2 columns); a
+            // tile holds a lower entry only if tc <= tr + 2
+            const int m3 = m2 - jb2, nr = (m3 + 15) / 16, nc = (m2 + 15) / 16;
+            const int tx = t & 15, ty = t >> 4;
+            for (int tt = blockIdx.x - 1; tt < nr * nc; tt += gridDim.x - 1) {
+                const int tr = tt / nc, tc = tt - tr * nc;
+                if (tc > tr + 2) continue;   // uniform over the CTA
+                const int mi = r0 + jb2 + 16 * tr, nj = r0 + 16 * tc;
+                __syncthreads();   // the previous tile's reads of As / Ps are done
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int e = t + 256 * q, i = e & 15, kk = e >> 4;
+                    As[kk][i] = (mi + i < k && kk < jb) ? G[(mi + i) + (int64_t)(c0 + kk) * ldg] : 0.0;
+                    Ps[kk][i] = (nj + i < k && kk < jb) ? G[(nj + i) + (int64_t)(c0 + kk) * ldg] : 0.0;
+                }
+                __syncthreads();
+                const int i = mi + tx, j = nj + ty;
+                if (i < k && j <= i) {
+                    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+                    for (int kk = 0; kk < NB; kk += 2) {
+                        a0 = fma(As[kk][tx], Ps[kk][ty], a0);
+                        a1 = fma(As[kk + 1][tx], Ps[kk + 1][ty], a1);
+                    }
+                    G[i + (int64_t)j * ldg] -= a0 + a1;
+                }
+            }
+        }
+        grid.sync();
+    }
+    // block inverses, one block per CTA (As, Ps, rv as the work arrays)
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+        __syncthreads();
+        trtri_block(G, k, ldg, dinv, b, As, Ps, rv);
     }
 }
 
@@ -966,11 +1147,18 @@ __global__ void trsm_rows_l_kernel(double *X, int m, int64_t ldx, const double *
 
 size_t dinv_doubles(int k) { return (size_t)((k + NB - 1) / NB) * NB * NB; }
 
-cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *dinv, cudaStream_t s)
+cudaError_t cholesky(double *G, int k, int64_t ldg, double shift_scale, int *info, double *dinv, cudaStream_t s,
+                     bool whole_gpu)
 {
     cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (shift_scale > 0.0) { count_launch(); shift_diag_kernel<<<1, 1024, 0, s>>>(G, k, ldg, shift_scale); }
+    if (whole_gpu && k > NB) {
+        void *args[] = {(void *)&G, (void *)&ldg, (void *)&k, (void *)&info, (void *)&dinv};
+        count_launch();
+        e = cudaLaunchCooperativeKernel((const void *)chol_coop_kernel, num_sms(), 256, args, 0, s);
+        return e;
+    }
     // potrf of block 0, then per block column: the panel below it, and the trailing update
     // fused with the factorisation of the next diagonal block
     { count_launch(); potrf_kernel<<<1, 256, 0, s>>>(G, ldg, 0, k < NB ? k : NB, info); }
