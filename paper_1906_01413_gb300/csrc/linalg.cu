@@ -441,13 +441,15 @@ __global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int
     int iJ = 0, il = 0;   // the next block to issue
     auto issue = [&](int slot) {
         if (iJ < nb) {
+            // element (ci = lane, kk = warp + 8 q) of block (iJ, il)
             float *buf = ring + slot * 1024;
+            const int row = 32 * iJ + cj;
+            const float *src = L + row + (int64_t)(32 * il + g) * ldl;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int e = t + 256 * q, ci = e & 31, kk = e >> 5;
-                const int row = 32 * iJ + ci, col = 32 * il + kk;
-                if (row < k && col < k) cp_async4(buf + kk * 32 + ci, L + row + (int64_t)col * ldl);
-                else buf[kk * 32 + ci] = 0.f;
+                const int kk = g + 8 * q, col = 32 * il + kk;
+                if (row < k && col < k) cp_async4(buf + kk * 32 + cj, src + (int64_t)(8 * q) * ldl);
+                else buf[kk * 32 + cj] = 0.f;
             }
             if (++il > iJ) {
                 ++iJ;
@@ -475,15 +477,25 @@ __global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int
             }
         }
         if (l < J) {
+            // eight steps of L and Y fetched before their 32 FMAs (shared-memory latency
+            // hidden by the batch rather than by other warps: one CTA of 8 warps per SM)
             const float *yb = Ys + (size_t)(32 * l) * R + 4 * g;
-#pragma unroll 8
-            for (int kk = 0; kk < 32; ++kk) {
-                const float a = buf[kk * 32 + cj];
-                const float4 y4 = *reinterpret_cast<const float4 *>(yb + kk * R);
-                acc[0] = fmaf(-y4.x, a, acc[0]);
-                acc[1] = fmaf(-y4.y, a, acc[1]);
-                acc[2] = fmaf(-y4.z, a, acc[2]);
-                acc[3] = fmaf(-y4.w, a, acc[3]);
+#pragma unroll
+            for (int k0 = 0; k0 < 32; k0 += 8) {
+                float a[8];
+                float4 y4[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    a[u] = buf[(k0 + u) * 32 + cj];
+                    y4[u] = *reinterpret_cast<const float4 *>(yb + (k0 + u) * R);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    acc[0] = fmaf(-y4[u].x, a[u], acc[0]);
+                    acc[1] = fmaf(-y4[u].y, a[u], acc[1]);
+                    acc[2] = fmaf(-y4[u].z, a[u], acc[2]);
+                    acc[3] = fmaf(-y4[u].w, a[u], acc[3]);
+                }
             }
             ++l;
         } else {
