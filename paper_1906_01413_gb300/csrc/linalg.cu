@@ -937,11 +937,12 @@ __global__ void __launch_bounds__(256, 1) chol_coop_kernel(double *G, int64_t ld
         const int c0 = J * NB, jb = (k - c0 < NB) ? k - c0 : NB;
         const int r0 = c0 + jb, m2 = k - r0;
         const int jb2 = m2 < NB ? m2 : NB;
-        // 1. panel rows r0 + gw, r0 + gw + W, ... (W warps in the grid).  Every load a CTA
-        // needs is issued before the first use: this warp's first row, the factor L_JJ, and
-        // (CTA 0) the next diagonal block, final since the previous trailing update.
+        // 1. panel rows: row r to CTA r mod G, warp (r / G) mod 8, so that the rows (one
+        // warp's FP64 chain each) spread over every sub-partition before any takes a second.
+        // Every load a CTA needs is issued before the first use: this warp's first row, the
+        // factor L_JJ, and (CTA 0) the next diagonal block, final since the previous trailing
+        // update.
         const int W = gridDim.x * (blockDim.x >> 5);
-        const int gw0 = blockIdx.x * (blockDim.x >> 5);
         if (blockIdx.x == 0) {
 #pragma unroll
             for (int q = 0; q < NB * NB / 256; ++q) {
@@ -950,9 +951,9 @@ __global__ void __launch_bounds__(256, 1) chol_coop_kernel(double *G, int64_t ld
                                                 : (i == c ? 1.0 : 0.0);
             }
         }
-        if (gw0 < m2) {
+        if ((int)blockIdx.x < m2) {
             const double *L = G + c0 + (int64_t)c0 * ldg;
-            const int rf = gw0 + (t >> 5);
+            const int rf = blockIdx.x + gridDim.x * (t >> 5);
             const double xf = (rf < m2 && lane < jb) ? G[(r0 + rf) + (int64_t)(c0 + lane) * ldg] : 0.0;
             double lv[NB * NB / 256];
 #pragma unroll
