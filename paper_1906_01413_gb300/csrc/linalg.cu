@@ -407,7 +407,7 @@ cudaError_t put_block_inverses(float *L32, int k, int64_t ldl, const double *din
 // shared-memory buffers filled by cp.async (4-byte copies, so any leading dimension works),
 // seven blocks ahead of the one in use (a block's arithmetic is shorter than an L2 round
 // trip).
-constexpr int kTrsmRows = 32;
+constexpr int kTrsmRows = 32;   // rows per CTA of the tall form
 constexpr int kTrsmRing = 8;
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src)
@@ -421,9 +421,38 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-__global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl)
+// RPT consecutive rows of one column of the row block in shared memory (a float4 for four)
+template <int RPT>
+__device__ __forceinline__ void ld_rows(const float *p, float *v)
 {
-    constexpr int R = kTrsmRows;
+    if constexpr (RPT == 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) v[i] = p[i];
+    }
+}
+
+template <int RPT>
+__device__ __forceinline__ void st_rows(float *p, const float *v)
+{
+    if constexpr (RPT == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) p[i] = v[i];
+    }
+}
+
+// RPT rows per thread (R = 8 RPT rows per CTA): 4 for tall blocks, 1 when the rows are too few
+// to give every SM a CTA of 32 (the sweep's length per CTA is the same either way, so the CTA
+// with a quarter of the rows takes about a quarter of the time).
+template <int RPT>
+__global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int k, int64_t ldx, const float *L,
+                                                            int64_t ldl)
+{
+    constexpr int R = 8 * RPT;
     extern __shared__ __align__(16) float trsm_sm[];
     float *Ys = trsm_sm;                          // [k][R]
     float *ring = trsm_sm + (size_t)k * R;        // [kTrsmRing][32 kk][32 ci]
@@ -460,7 +489,9 @@ __global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int
     };
 #pragma unroll
     for (int q = 0; q < kTrsmRing - 1; ++q) issue(q);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) acc[i] = 0.f;
     int J = 0, l = 0;
     for (int b = 0; b < nblk; ++b) {
         cp_async_wait<kTrsmRing - 2>();
@@ -470,51 +501,48 @@ __global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int
         const int colJ = 32 * J + cj;
         if (l == 0) {
             if (colJ < k) {
-                const float4 x4 = *reinterpret_cast<const float4 *>(Ys + (size_t)colJ * R + 4 * g);
-                acc[0] = x4.x; acc[1] = x4.y; acc[2] = x4.z; acc[3] = x4.w;
+                ld_rows<RPT>(Ys + (size_t)colJ * R + RPT * g, acc);
             } else {
-                acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) acc[i] = 0.f;
             }
         }
         if (l < J) {
-            // eight steps of L and Y fetched before their 32 FMAs (shared-memory latency
-            // hidden by the batch rather than by other warps: one CTA of 8 warps per SM)
-            const float *yb = Ys + (size_t)(32 * l) * R + 4 * g;
+            // eight steps of L and Y fetched before their FMAs (shared-memory latency hidden by
+            // the batch rather than by other warps: one CTA of 8 warps per SM)
+            const float *yb = Ys + (size_t)(32 * l) * R + RPT * g;
 #pragma unroll
             for (int k0 = 0; k0 < 32; k0 += 8) {
-                float a[8];
-                float4 y4[8];
+                float a[8], y[8][RPT];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     a[u] = buf[(k0 + u) * 32 + cj];
-                    y4[u] = *reinterpret_cast<const float4 *>(yb + (k0 + u) * R);
+                    ld_rows<RPT>(yb + (k0 + u) * R, y[u]);
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    acc[0] = fmaf(-y4[u].x, a[u], acc[0]);
-                    acc[1] = fmaf(-y4[u].y, a[u], acc[1]);
-                    acc[2] = fmaf(-y4[u].z, a[u], acc[2]);
-                    acc[3] = fmaf(-y4[u].w, a[u], acc[3]);
-                }
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int i = 0; i < RPT; ++i) acc[i] = fmaf(-y[u][i], a[u], acc[i]);
             }
             ++l;
         } else {
             // diagonal: the right-hand side through shared memory, then times the block inverse
-            if (colJ < k) *reinterpret_cast<float4 *>(Ys + (size_t)colJ * R + 4 * g) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            if (colJ < k) st_rows<RPT>(Ys + (size_t)colJ * R + RPT * g, acc);
             __syncthreads();
             const int jb = (k - 32 * J < 32) ? k - 32 * J : 32;
-            float o[4] = {0.f, 0.f, 0.f, 0.f};
-            const float *yb = Ys + (size_t)(32 * J) * R + 4 * g;
+            float o[RPT];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) o[i] = 0.f;
+            const float *yb = Ys + (size_t)(32 * J) * R + RPT * g;
             for (int kk = 0; kk < jb; ++kk) {
                 const float a = buf[kk * 32 + cj];
-                const float4 y4 = *reinterpret_cast<const float4 *>(yb + kk * R);
-                o[0] = fmaf(y4.x, a, o[0]);
-                o[1] = fmaf(y4.y, a, o[1]);
-                o[2] = fmaf(y4.z, a, o[2]);
-                o[3] = fmaf(y4.w, a, o[3]);
+                float y[RPT];
+                ld_rows<RPT>(yb + kk * R, y);
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) o[i] = fmaf(y[i], a, o[i]);
             }
             __syncthreads();
-            if (colJ < k) *reinterpret_cast<float4 *>(Ys + (size_t)colJ * R + 4 * g) = make_float4(o[0], o[1], o[2], o[3]);
+            if (colJ < k) st_rows<RPT>(Ys + (size_t)colJ * R + RPT * g, o);
             ++J;
             l = 0;
         }
@@ -534,12 +562,16 @@ __global__ void __launch_bounds__(256) strsm_lt_rows_kernel(float *X, int m, int
 cudaError_t strsm_right_lt_inv(float *X, int m, int k, int64_t ldx, const float *L, int64_t ldl, cudaStream_t s)
 {
     if (m <= 0 || k <= 0) return cudaSuccess;
-    const size_t smem = sizeof(float) * ((size_t)k * kTrsmRows + kTrsmRing * 1024);
+    // 32 rows per CTA while that still gives ~every SM a CTA, else 8
+    const bool tall = m >= 32 * (num_sms() * 3 / 4);
+    const int R = tall ? kTrsmRows : 8;
+    const size_t smem = sizeof(float) * ((size_t)k * R + kTrsmRing * 1024);
     if (smem <= 227 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(strsm_lt_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto kern = tall ? strsm_lt_rows_kernel<4> : strsm_lt_rows_kernel<1>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         count_launch();
-        strsm_lt_rows_kernel<<<(m + kTrsmRows - 1) / kTrsmRows, 256, smem, s>>>(X, m, k, ldx, L, ldl);
+        kern<<<(m + R - 1) / R, 256, smem, s>>>(X, m, k, ldx, L, ldl);
         return cudaGetLastError();
     }
     for (int J = 0; J < k; J += 32) {
