@@ -88,8 +88,10 @@ __device__ __forceinline__ double block_sum(double v, double *red, double scale 
 // the others copy x: FP64 work repeated on every thread costs issue slots of the
 // FP64 units that the serial chain waits for.  When x = 0, beta = 0 and H = I
 // whatever v holds.
+// defer_beta: *beta_out receives the denominator alpha (alpha + |x0|) (0 when x = 0) instead
+// of beta, for a caller that forms the reciprocal off the critical path.
 __device__ void block_house(const double *col, int k, int r0, double *vs, double *beta_out, double *e_out,
-                            double *red)
+                            double *red, bool defer_beta = false)
 {
     double ss = 0.0;
     for (int l = r0 + threadIdx.x; l < k; l += blockDim.x) ss += col[l] * col[l];
@@ -103,7 +105,8 @@ __device__ void block_house(const double *col, int k, int r0, double *vs, double
         const double alpha = (ss > 0.0) ? ss * rsqrt(ss) : 0.0;
         const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
         vs[r0] = x0 + sgn * alpha;
-        *beta_out = (alpha == 0.0) ? 0.0 : rcp_fast(alpha * (alpha + fabs(x0)));
+        const double den = alpha * (alpha + fabs(x0));
+        *beta_out = (alpha == 0.0) ? 0.0 : (defer_beta ? den : rcp_fast(den));
         *e_out = (alpha == 0.0) ? 0.0 : -sgn * alpha;
     }
     __syncthreads();
@@ -206,9 +209,9 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
             const double wr = w[r0], vr = vcur[r0];
             for (int l = r0 + threadIdx.x; l < k; l += blockDim.x) colj[l] = fma(-w[l], vr, fma(-vcur[l], wr, colj[l]));
             __syncthreads();
-            block_house(colj, k, r0 + 1, vnext, &bnext_s, &enext_s, red);
+            block_house(colj, k, r0 + 1, vnext, &bnext_s, &enext_s, red, RES);
             __syncthreads();
-            bn = bnext_s;
+            if constexpr (!RES) bn = bnext_s;
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 d[r0] = colj[r0];
                 e[r0] = enext_s;
@@ -216,7 +219,16 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
         }
         const int r1 = r0 + 1;
         double *pn = pq + (size_t)(par ^ 1) * k, *qn = pq + 2 * (size_t)k + (size_t)(par ^ 1) * k;
+        // RES: beta of the next reflector is needed only when the dot products are published
+        // after the closing barrier, so a Q^T warp (the lighter update) forms its reciprocal
+        // while the columns are updated, and each warp keeps its sum until then
+        double tsum = 0.0;
+        double *pdst = nullptr;
         if constexpr (RES) {
+            if (next && threadIdx.x == 128) {
+                const double den = bnext_s;
+                bnext_s = (den == 0.0) ? 0.0 : rcp_fast(den);
+            }
             if (ownA && ocol >= r0 && !(next && ocol == r0)) {
                 const int i = ocol;
                 const double vi = vcur[i], wi = w[i];
@@ -227,8 +239,8 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
                     if (l >= r1) t = fma(x, vnext[l], t);
                 }
                 if (next) {
-                    t = warp_sum(t);
-                    if (lane == 0) pn[i] = bn * t;
+                    tsum = warp_sum(t);
+                    pdst = pn + i;
                 }
                 // the column every CTA derives at the next step, and the last 2 x 2 block
                 if (i == r1 || !next) {
@@ -246,8 +258,8 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
                     if (l >= r1) t = fma(x, vnext[l], t);
                 }
                 if (next) {
-                    t = warp_sum(t);
-                    if (lane == 0) qn[i] = bn * t;
+                    tsum = warp_sum(t);
+                    pdst = qn + i;
                 }
             }
         } else {
@@ -304,6 +316,10 @@ __global__ void __launch_bounds__(256) tridiag_kernel(double *A, double *Qt, int
         }
         // reflector j + 1 becomes the current one, once every warp of the CTA is done with both
         __syncthreads();
+        if constexpr (RES) {
+            if (next) bn = bnext_s;
+            if (pdst && lane == 0) *pdst = bn * tsum;
+        }
         for (int l = threadIdx.x; l < k; l += blockDim.x) vcur[l] = vnext[l];
         if (threadIdx.x == 0) bcur_s = bn;
         grid.sync();
